@@ -1,0 +1,457 @@
+// oracle.cpp — TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow FP64 CPU implementation of the CI-SCvx per-interval
+// discretization/linearization (Buckner & Elango, "GPU-Accelerated
+// Continuous-Time Successive Convexification for Contact-Implicit Legged
+// Locomotion").  It exists to check the CUDA library against.  Only tests/,
+// __graft_entry__.smoke() and bench.py (its CPU-baseline and reference legs)
+// may load it; the product package never links, imports or calls it, and it
+// shares no code, header or table with the product.
+//
+// What is computed, and where it comes from:
+//   rhs()       the augmented right-hand side (f, Omega): Newton-Euler per
+//               link in maximal coordinates, Sec. II-A Eq. (1); contact frame
+//               on flat ground y = 0 (normal (0,1), tangent (1,0)), Sec. II;
+//               integral path-constraint penalty Omega = M^g sabs+(g), Sec. IV-A
+//               Eq. (12), with one auxiliary state per contact.
+//   rk4_foh()   the time-dilated augmented system d x~/d tau = s (f, Omega) on
+//               tau in [0,1], Sec. IV-B Eq. (14), integrated in integral form
+//               Eq. (15) with a first-order-hold control u(tau) =
+//               (1 - tau) u_L + tau u_R (Sec. VI: FOH), by n_sub classical
+//               fixed-step RK4 steps.
+//   interval()  Internal Numerical Differentiation (Sec. VI): the Jacobian of
+//               the discrete RK4 map is obtained by running the very same RK4
+//               arithmetic on forward-mode dual numbers seeded in
+//               (x~_k, u_L, u_R, s).  Outputs A = dF/dx~, B- = dF/du_L,
+//               B+ = dF/du_R, S = dF/ds.
+//   discretize() every interval k of the multiple-shooting grid, independently:
+//               defect_k = F~(x~_k, U_k, s_k) - x~_{k+1} (Eq. (17b)) and
+//               penalty_k = y(1) - y_k (the increments that Eq. (13) bounds).
+//   vjp()       gradient of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k
+//               contracted from the IND blocks (J^T times the cotangent).
+//   linear_interval()  the same integrator and IND applied to a linear
+//               right-hand side A_c x + B_c u (used only to pin the integrator).
+//
+// Readings of points the paper leaves open (one auxiliary state per contact,
+// pseudo-Huber ramp h(z) = sqrt(1 + max(z,0)^2) - 1, joint reaction forces and
+// contact forces (lambda_n, lambda_t+, lambda_t-) as FOH inputs, N intervals
+// on N+1 nodes, classical RK4 instead of the paper's RKF tableau) are listed
+// in the project's design notes; this file follows them.
+//
+// Build: g++ -O2 -std=c++17 -shared -fPIC -pthread oracle.cpp -o liboracle.so
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers with a run-time number of tangent directions.
+// ---------------------------------------------------------------------------
+constexpr int MAXC = 192;   // max tangent directions (n_x~ + 2 n_u + 1)
+thread_local int g_nd = 0;  // active directions for this thread
+
+struct Dual {
+  double v;
+  double d[MAXC];
+  Dual() : v(0.0) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }
+  Dual(double x) : v(x) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }  // NOLINT
+};
+
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v + b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v - b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+inline Dual operator-(const Dual& a) {
+  Dual r; r.v = -a.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v * b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.v * b.d[i] + b.v * a.d[i];
+  return r;
+}
+inline Dual operator*(double a, const Dual& b) {
+  Dual r; r.v = a * b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a * b.d[i];
+  return r;
+}
+inline Dual operator*(const Dual& a, double b) { return b * a; }
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v / b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);
+  return r;
+}
+inline Dual operator/(const Dual& a, double b) {
+  Dual r; r.v = a.v / b;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] / b;
+  return r;
+}
+inline Dual operator+(double a, const Dual& b) { Dual r = b; r.v += a; return r; }
+inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
+inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
+inline Dual operator-(double a, const Dual& b) { Dual r = -b; r.v += a; return r; }
+
+inline Dual sin(const Dual& a) {
+  Dual r; r.v = std::sin(a.v);
+  const double c = std::cos(a.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = c * a.d[i];
+  return r;
+}
+inline Dual cos(const Dual& a) {
+  Dual r; r.v = std::cos(a.v);
+  const double s = -std::sin(a.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = s * a.d[i];
+  return r;
+}
+inline Dual sqrt(const Dual& a) {
+  Dual r; r.v = std::sqrt(a.v);
+  const double k = 0.5 / r.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = k * a.d[i];
+  return r;
+}
+inline double value(const Dual& a) { return a.v; }
+
+inline double sin(double a) { return std::sin(a); }
+inline double cos(double a) { return std::cos(a); }
+inline double sqrt(double a) { return std::sqrt(a); }
+inline double value(double a) { return a; }
+
+// ramp max(z, 0) (Sec. II notation); derivative 0 for z <= 0.
+template <class T> T ramp(const T& z) { return value(z) > 0.0 ? z : T(0.0); }
+
+// Pseudo-Huber ramp with unit steepness, h(z) = sqrt(1 + max(z,0)^2) - 1,
+// written as p^2 / (1 + sqrt(1 + p^2)) with p = max(z,0), which is the same
+// number without the cancellation near p = 0.  h = 0 exactly for z <= 0, as
+// the CTCS condition y_{k+1} = y_k needs (Sec. IV-A).
+template <class T> T sabs_plus(const T& z) {
+  const T p = ramp(z);
+  return (p * p) / (1.0 + sqrt(1.0 + p * p));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Model description (the oracle's own layout; filled in from Python).
+// ---------------------------------------------------------------------------
+extern "C" {
+typedef struct {
+  int nb, nj, nc;
+  const double* mass;     // [nb]
+  const double* inertia;  // [nb]  rotational inertia about the centre of mass
+  const int* jparent;     // [nj]
+  const int* jchild;      // [nj]
+  const double* jrho_p;   // [nj][2] joint anchor in the parent body frame
+  const double* jrho_c;   // [nj][2] joint anchor in the child body frame
+  const int* cbody;       // [nc]
+  const double* crho;     // [nc][2] contact point in the body frame
+  const double* cmu;      // [nc] friction coefficient
+  double g;               // gravity magnitude, acting along -y
+} OracleModel;
+}
+
+namespace {
+
+int nx_of(const OracleModel& M) { return 6 * M.nb; }
+int nxt_of(const OracleModel& M) { return 6 * M.nb + M.nc; }
+int nu_of(const OracleModel& M) { return 3 * M.nj + 3 * M.nc; }
+
+// World-frame lever arm r = R(theta) rho, R = [[cos, -sin], [sin, cos]].
+template <class T>
+void lever_arm(const T& theta, const double* rho, T& rx, T& ry) {
+  const T c = cos(theta), s = sin(theta);
+  rx = c * rho[0] - s * rho[1];
+  ry = s * rho[0] + c * rho[1];
+}
+
+// Planar cross product r x F = r_x F_y - r_y F_x.
+template <class T>
+T cross2(const T& rx, const T& ry, const T& fx, const T& fy) { return rx * fy - ry * fx; }
+
+// Augmented right-hand side (f(x,u), Omega(x,u)) — NOT yet multiplied by s.
+// State x~ = (q_1..q_nb, v_1..v_nb, y_1..y_nc) with q_b = (p_x, p_y, theta),
+// v_b = (v_x, v_y, omega).  Input u = (tau_1..tau_nj, lambda_1x, lambda_1y,
+// ..., lambda_njx, lambda_njy, [lambda_n, lambda_t+, lambda_t-] per contact).
+//
+// Eq. (1): q' = v; M v' = W + J_c^T R_c phi_c + grad C^T lambda.  Here M is
+// diag(m, m, I) per link, W holds gravity and the joint torques, the joint
+// reaction force lambda_j acts +lambda_j on the child at its anchor and
+// -lambda_j on the parent at its anchor (grad C^T lambda for the revolute
+// constraint C = p_c + R_c rho_c - p_p - R_p rho_p), the joint torque tau_j
+// acts +tau_j on the child and -tau_j on the parent, and contact force
+// (lambda_t+ - lambda_t-, lambda_n) acts at the contact point.
+// Eq. (12): Omega_i = sum over the contact's path constraints g <= 0 of
+// h(g), with g = (-lambda_n, -lambda_t+, -lambda_t-, -phi_i(q),
+// lambda_t+ + lambda_t- - mu lambda_n), phi_i the signed distance to y = 0.
+template <class T>
+void rhs(const OracleModel& M, const T* xt, const T* u, T* out) {
+  const int nb = M.nb, nj = M.nj, nc = M.nc;
+  std::vector<T> Fx(nb, T(0.0)), Fy(nb, T(0.0)), Tq(nb, T(0.0));
+  for (int b = 0; b < nb; ++b) Fy[b] = T(-M.mass[b] * M.g);
+  for (int j = 0; j < nj; ++j) {
+    const int p = M.jparent[j], c = M.jchild[j];
+    const T& tau = u[j];
+    const T& lx = u[nj + 2 * j];
+    const T& ly = u[nj + 2 * j + 1];
+    T rcx, rcy, rpx, rpy;
+    lever_arm(xt[3 * c + 2], M.jrho_c + 2 * j, rcx, rcy);
+    lever_arm(xt[3 * p + 2], M.jrho_p + 2 * j, rpx, rpy);
+    Fx[c] = Fx[c] + lx;
+    Fy[c] = Fy[c] + ly;
+    Tq[c] = Tq[c] + cross2(rcx, rcy, lx, ly) + tau;
+    Fx[p] = Fx[p] - lx;
+    Fy[p] = Fy[p] - ly;
+    Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) - tau;
+  }
+  for (int i = 0; i < nc; ++i) {
+    const int b = M.cbody[i];
+    const T& ln = u[3 * nj + 3 * i];
+    const T& ltp = u[3 * nj + 3 * i + 1];
+    const T& ltm = u[3 * nj + 3 * i + 2];
+    T rx, ry;
+    lever_arm(xt[3 * b + 2], M.crho + 2 * i, rx, ry);
+    const T fx = ltp - ltm;  // tangent (1, 0)
+    const T fy = ln;         // normal (0, 1)
+    Fx[b] = Fx[b] + fx;
+    Fy[b] = Fy[b] + fy;
+    Tq[b] = Tq[b] + cross2(rx, ry, fx, fy);
+    const T phi = xt[3 * b + 1] + ry;  // signed distance of the contact point to y = 0
+    out[6 * nb + i] = sabs_plus(-ln) + sabs_plus(-ltp) + sabs_plus(-ltm) + sabs_plus(-phi) +
+                      sabs_plus(ltp + ltm - M.cmu[i] * ln);
+  }
+  for (int b = 0; b < nb; ++b) {
+    for (int k = 0; k < 3; ++k) out[3 * b + k] = xt[3 * nb + 3 * b + k];
+    out[3 * nb + 3 * b + 0] = Fx[b] / M.mass[b];
+    out[3 * nb + 3 * b + 1] = Fy[b] / M.mass[b];
+    out[3 * nb + 3 * b + 2] = Tq[b] / M.inertia[b];
+  }
+}
+
+// n_sub classical RK4 steps of d x/d tau = s F(x, u(tau)) on tau in [0,1],
+// u(tau) = (1 - tau) u_L + tau u_R (first-order hold), Eqs. (14)-(15).
+template <class T, class RHS>
+void rk4_foh(const RHS& F, int nxt, int nu, const T* x0, const T* uL, const T* uR, const T& s,
+             int nsub, T* x1) {
+  static const double c[4] = {0.0, 0.5, 0.5, 1.0};
+  static const double w[4] = {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0};
+  const double h = 1.0 / nsub;
+  std::vector<T> x(x0, x0 + nxt), xs(nxt), k(nxt), acc(nxt), u(nu), fv(nxt);
+  for (int i = 0; i < nsub; ++i) {
+    for (int r = 0; r < nxt; ++r) acc[r] = T(0.0);
+    for (int j = 0; j < 4; ++j) {
+      const double tau = (i + c[j]) * h;
+      for (int r = 0; r < nxt; ++r) xs[r] = (j == 0) ? x[r] : x[r] + (c[j] * h) * k[r];
+      for (int q = 0; q < nu; ++q) u[q] = (1.0 - tau) * uL[q] + tau * uR[q];
+      F(xs.data(), u.data(), fv.data());
+      for (int r = 0; r < nxt; ++r) k[r] = s * fv[r];
+      for (int r = 0; r < nxt; ++r) acc[r] = acc[r] + w[j] * k[r];
+    }
+    for (int r = 0; r < nxt; ++r) x[r] = x[r] + h * acc[r];
+  }
+  for (int r = 0; r < nxt; ++r) x1[r] = x[r];
+}
+
+// IND on one interval: seed duals in (x~_k, u_L, u_R, s), run rk4_foh, read
+// the tangents.  Direction order: x~ (nxt), u_L (nu), u_R (nu), s (1).
+template <class RHSD>
+int ind_interval(const RHSD& F, int nxt, int nu, int nsub, const double* x0, const double* uL,
+                 const double* uR, double s, double* x1, double* A, double* Bm, double* Bp,
+                 double* S) {
+  const int C = nxt + 2 * nu + 1;
+  if (C > MAXC) return 1;
+  g_nd = C;
+  std::vector<Dual> X0(nxt), UL(nu), UR(nu), X1(nxt);
+  for (int r = 0; r < nxt; ++r) { X0[r] = Dual(x0[r]); X0[r].d[r] = 1.0; }
+  for (int q = 0; q < nu; ++q) {
+    UL[q] = Dual(uL[q]); UL[q].d[nxt + q] = 1.0;
+    UR[q] = Dual(uR[q]); UR[q].d[nxt + nu + q] = 1.0;
+  }
+  Dual Sd(s); Sd.d[C - 1] = 1.0;
+  rk4_foh<Dual>(F, nxt, nu, X0.data(), UL.data(), UR.data(), Sd, nsub, X1.data());
+  for (int r = 0; r < nxt; ++r) {
+    if (x1) x1[r] = X1[r].v;
+    if (A) for (int c = 0; c < nxt; ++c) A[r * nxt + c] = X1[r].d[c];
+    if (Bm) for (int q = 0; q < nu; ++q) Bm[r * nu + q] = X1[r].d[nxt + q];
+    if (Bp) for (int q = 0; q < nu; ++q) Bp[r * nu + q] = X1[r].d[nxt + nu + q];
+    if (S) S[r] = X1[r].d[C - 1];
+  }
+  return 0;
+}
+
+int model_ok(const OracleModel* M) {
+  if (!M || M->nb < 1 || M->nj < 0 || M->nc < 0) return 0;
+  for (int j = 0; j < M->nj; ++j)
+    if (M->jparent[j] < 0 || M->jparent[j] >= M->nb || M->jchild[j] < 0 || M->jchild[j] >= M->nb)
+      return 0;
+  for (int i = 0; i < M->nc; ++i)
+    if (M->cbody[i] < 0 || M->cbody[i] >= M->nb) return 0;
+  return 1;
+}
+
+// Controls of interval k: node layout U[N+1][nu] (u_L = U_k, u_R = U_{k+1});
+// interval layout U[N][2][nu] (u_L, u_R per interval; FOH may jump at nodes,
+// Sec. VI).
+void controls_of(int layout, int nu, const double* U, long k, const double** uL,
+                 const double** uR) {
+  if (layout == 0) { *uL = U + k * nu; *uR = U + (k + 1) * nu; }
+  else { *uL = U + 2 * k * nu; *uR = U + (2 * k + 1) * nu; }
+}
+
+template <class Fn>
+void parallel_for(long n, int nthreads, const Fn& fn) {
+  if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
+  nthreads = (int)std::min<long>(nthreads, std::max<long>(n, 1));
+  if (nthreads <= 1) { for (long k = 0; k < n; ++k) fn(k); return; }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t)
+    pool.emplace_back([&, t]() { for (long k = t; k < n; k += nthreads) fn(k); });
+  for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
+extern "C" {
+
+// Dimensions n_x~ = 6 n_b + n_c, n_u = 3 n_j + 3 n_c.
+int oracle_dims(const OracleModel* M, int* nxt, int* nu) {
+  if (!model_ok(M)) return 1;
+  *nxt = nxt_of(*M);
+  *nu = nu_of(*M);
+  return 0;
+}
+
+// Unscaled augmented right-hand side (f, Omega) at one point.
+int oracle_rhs(const OracleModel* M, const double* xt, const double* u, double* out) {
+  if (!model_ok(M)) return 1;
+  rhs<double>(*M, xt, u, out);
+  return 0;
+}
+
+// The nonlinear flow map F~(x~_0, u_L, u_R, s) of one interval, plain FP64.
+int oracle_flow(const OracleModel* M, int nsub, const double* x0, const double* uL,
+                const double* uR, double s, double* x1) {
+  if (!model_ok(M) || nsub < 1) return 1;
+  auto F = [M](const double* x, const double* u, double* o) { rhs<double>(*M, x, u, o); };
+  rk4_foh<double>(F, nxt_of(*M), nu_of(*M), x0, uL, uR, s, nsub, x1);
+  return 0;
+}
+
+// One interval: x~(1) and its IND Jacobian blocks A [nxt][nxt], B-/B+ [nxt][nu], S [nxt].
+int oracle_interval(const OracleModel* M, int nsub, const double* x0, const double* uL,
+                    const double* uR, double s, double* x1, double* A, double* Bm, double* Bp,
+                    double* S) {
+  if (!model_ok(M) || nsub < 1) return 1;
+  auto F = [M](const Dual* x, const Dual* u, Dual* o) { rhs<Dual>(*M, x, u, o); };
+  return ind_interval(F, nxt_of(*M), nu_of(*M), nsub, x0, uL, uR, s, x1, A, Bm, Bp, S);
+}
+
+// All N intervals of a multiple-shooting grid (independently, Eq. (17b)).
+// X [N+1][nxt]; U per layout; s [N].  Outputs: A [N][nxt][nxt], Bm/Bp
+// [N][nxt][nu], S [N][nxt], defect [N][nxt], penalty [N][nc].  Any output
+// pointer may be NULL.
+int oracle_discretize(const OracleModel* M, int N, int nsub, int layout, const double* X,
+                      const double* U, const double* s, double* A, double* Bm, double* Bp,
+                      double* S, double* defect, double* penalty, int nthreads) {
+  if (!model_ok(M) || N < 1 || nsub < 1 || (layout != 0 && layout != 1)) return 1;
+  const int nxt = nxt_of(*M), nu = nu_of(*M), nx = nx_of(*M), nc = M->nc;
+  if (nxt + 2 * nu + 1 > MAXC) return 1;
+  int err = 0;
+  parallel_for(N, nthreads, [&](long k) {
+    const double *uL, *uR;
+    controls_of(layout, nu, U, k, &uL, &uR);
+    std::vector<double> x1(nxt);
+    const size_t a = (size_t)k * nxt * nxt, b = (size_t)k * nxt * nu, v = (size_t)k * nxt;
+    if (oracle_interval(M, nsub, X + k * nxt, uL, uR, s[k], x1.data(), A ? A + a : nullptr,
+                        Bm ? Bm + b : nullptr, Bp ? Bp + b : nullptr, S ? S + v : nullptr))
+      err = 1;
+    if (defect)
+      for (int r = 0; r < nxt; ++r) defect[v + r] = x1[r] - X[(k + 1) * nxt + r];
+    if (penalty)
+      for (int i = 0; i < nc; ++i) penalty[(size_t)k * nc + i] = x1[nx + i] - X[k * nxt + nx + i];
+  });
+  return err;
+}
+
+// Gradient of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k with respect
+// to X, U and s, contracted from the IND blocks:
+//   lambda_k = w_k + (rho_k placed on the y rows)          (cotangent of x~(1))
+//   dL/dx~_k    += A_k^T lambda_k,  minus rho_k on the y rows (penalty_k subtracts y_k),
+//   dL/dx~_{k+1} -= w_k                                       (defect_k subtracts x~_{k+1}),
+//   dL/du_L,k = B-_k^T lambda_k,  dL/du_R,k = B+_k^T lambda_k,  dL/ds_k = S_k . lambda_k.
+// Node layout sums the u_L part of interval k and the u_R part of interval
+// k-1 into node k.  gX [N+1][nxt], gU like U, gs [N]; L (scalar) may be NULL.
+int oracle_vjp(const OracleModel* M, int N, int nsub, int layout, const double* X,
+               const double* U, const double* s, const double* w, const double* rho, double* gX,
+               double* gU, double* gs, double* L, int nthreads) {
+  if (!model_ok(M) || N < 1 || nsub < 1 || (layout != 0 && layout != 1)) return 1;
+  const int nxt = nxt_of(*M), nu = nu_of(*M), nx = nx_of(*M), nc = M->nc;
+  std::vector<double> A((size_t)N * nxt * nxt), Bm((size_t)N * nxt * nu), Bp((size_t)N * nxt * nu),
+      S((size_t)N * nxt), D((size_t)N * nxt), P((size_t)N * (nc > 0 ? nc : 1));
+  if (oracle_discretize(M, N, nsub, layout, X, U, s, A.data(), Bm.data(), Bp.data(), S.data(),
+                        D.data(), P.data(), nthreads))
+    return 1;
+  const long nU = (layout == 0) ? (long)(N + 1) * nu : (long)2 * N * nu;
+  std::fill(gX, gX + (size_t)(N + 1) * nxt, 0.0);
+  std::fill(gU, gU + nU, 0.0);
+  double Ltot = 0.0;
+  std::vector<double> lam(nxt);
+  for (long k = 0; k < N; ++k) {
+    for (int r = 0; r < nxt; ++r) lam[r] = w[k * nxt + r];
+    for (int i = 0; i < nc; ++i) lam[nx + i] += rho[k * nc + i];
+    const double* Ak = A.data() + (size_t)k * nxt * nxt;
+    const double* Bmk = Bm.data() + (size_t)k * nxt * nu;
+    const double* Bpk = Bp.data() + (size_t)k * nxt * nu;
+    for (int c = 0; c < nxt; ++c) {
+      double acc = 0.0;
+      for (int r = 0; r < nxt; ++r) acc += Ak[r * nxt + c] * lam[r];
+      gX[k * nxt + c] += acc;
+    }
+    for (int i = 0; i < nc; ++i) gX[k * nxt + nx + i] -= rho[k * nc + i];
+    for (int r = 0; r < nxt; ++r) gX[(k + 1) * nxt + r] -= w[k * nxt + r];
+    double* gL = (layout == 0) ? gU + k * nu : gU + 2 * k * nu;
+    double* gR = (layout == 0) ? gU + (k + 1) * nu : gU + (2 * k + 1) * nu;
+    for (int q = 0; q < nu; ++q) {
+      double aL = 0.0, aR = 0.0;
+      for (int r = 0; r < nxt; ++r) { aL += Bmk[r * nu + q] * lam[r]; aR += Bpk[r * nu + q] * lam[r]; }
+      gL[q] += aL;
+      gR[q] += aR;
+    }
+    double as = 0.0;
+    for (int r = 0; r < nxt; ++r) as += S[k * nxt + r] * lam[r];
+    gs[k] = as;
+    for (int r = 0; r < nxt; ++r) Ltot += w[k * nxt + r] * D[k * nxt + r];
+    for (int i = 0; i < nc; ++i) Ltot += rho[k * nc + i] * P[k * nc + i];
+  }
+  if (L) *L = Ltot;
+  return 0;
+}
+
+// The same integrator and IND on a linear right-hand side F(x,u) = Ac x + Bc u
+// (Ac [n][n], Bc [n][m], row-major).  Used only to pin rk4_foh/IND against
+// closed forms.
+int oracle_linear_interval(int n, int m, const double* Ac, const double* Bc, int nsub,
+                           const double* x0, const double* uL, const double* uR, double s,
+                           double* x1, double* A, double* Bm, double* Bp, double* S) {
+  if (n < 1 || m < 0 || nsub < 1 || n + 2 * m + 1 > MAXC) return 1;
+  auto F = [=](const Dual* x, const Dual* u, Dual* o) {
+    for (int r = 0; r < n; ++r) {
+      Dual acc(0.0);
+      for (int c = 0; c < n; ++c) acc = acc + Ac[r * n + c] * x[c];
+      for (int q = 0; q < m; ++q) acc = acc + Bc[r * m + q] * u[q];
+      o[r] = acc;
+    }
+  };
+  return ind_interval(F, n, m, nsub, x0, uL, uR, s, x1, A, Bm, Bp, S);
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+"""The oracle's pins reject plausible mistakes (no GPU).
+
+Each case plants one error in a copy of ``oracle/oracle.cpp`` (a dropped term,
+a flipped sign, a wrong index, a transposed rotation, a wrong quadrature
+weight ...), builds it in a temporary directory, and runs the pin suites
+against that build through ``CISCVX_ORACLE_LIB``.  The pins must fail for
+every planted error; the real oracle must pass (the other test files).
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
+PINS = ["tests/test_oracle_integrator.py", "tests/test_oracle_physics.py", "tests/test_oracle_vjp.py"]
+
+MUTATIONS = [
+    ("parent joint torque sign", "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) - tau;",
+     "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) + tau;"),
+    ("parent joint force sign", "Fx[p] = Fx[p] - lx;", "Fx[p] = Fx[p] + lx;"),
+    ("child anchor taken from parent", "lever_arm(xt[3 * c + 2], M.jrho_c + 2 * j, rcx, rcy);",
+     "lever_arm(xt[3 * c + 2], M.jrho_p + 2 * j, rcx, rcy);"),
+    ("cross product sign", "T cross2(const T& rx, const T& ry, const T& fx, const T& fy) { return rx * fy - ry * fx; }",
+     "T cross2(const T& rx, const T& ry, const T& fx, const T& fy) { return ry * fx - rx * fy; }"),
+    ("rotation transposed", "rx = c * rho[0] - s * rho[1];\n  ry = s * rho[0] + c * rho[1];",
+     "rx = c * rho[0] + s * rho[1];\n  ry = -s * rho[0] + c * rho[1];"),
+    ("gravity dropped", "Fy[b] = T(-M.mass[b] * M.g);", "Fy[b] = T(0.0);"),
+    ("gravity sign", "Fy[b] = T(-M.mass[b] * M.g);", "Fy[b] = T(M.mass[b] * M.g);"),
+    ("contact tangent sign", "const T fx = ltp - ltm;", "const T fx = ltm - ltp;"),
+    ("inertia replaced by mass", "Tq[b] / M.inertia[b];", "Tq[b] / M.mass[b];"),
+    ("q' = v index", "out[3 * b + k] = xt[3 * nb + 3 * b + k];", "out[3 * b + k] = xt[3 * nb + 3 * b];"),
+    ("signed distance uses r_x", "const T phi = xt[3 * b + 1] + ry;", "const T phi = xt[3 * b + 1] + rx;"),
+    ("friction cone sign", "sabs_plus(ltp + ltm - M.cmu[i] * ln)", "sabs_plus(ltp + ltm + M.cmu[i] * ln)"),
+    ("penalty without ramp", "const T p = ramp(z);", "const T p = z;"),
+    ("pseudo-Huber constant", "(p * p) / (1.0 + sqrt(1.0 + p * p))", "(p * p) / (2.0 + sqrt(1.0 + p * p))"),
+    ("FOH weights swapped", "u[q] = (1.0 - tau) * uL[q] + tau * uR[q];",
+     "u[q] = tau * uL[q] + (1.0 - tau) * uR[q];"),
+    ("RK4 weights", "w[4] = {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0}",
+     "w[4] = {1.0 / 8.0, 3.0 / 8.0, 3.0 / 8.0, 1.0 / 8.0}"),
+    ("RK4 stage node", "c[4] = {0.0, 0.5, 0.5, 1.0}", "c[4] = {0.0, 0.5, 0.5, 0.5}"),
+    ("dilation dropped", "k[r] = s * fv[r];", "k[r] = fv[r];"),
+    ("dual product rule term", "r.d[i] = a.v * b.d[i] + b.v * a.d[i];", "r.d[i] = a.v * b.d[i];"),
+    ("dual sin derivative", "const double c = std::cos(a.v);", "const double c = -std::cos(a.v);"),
+    ("dual sqrt derivative", "const double k = 0.5 / r.v;", "const double k = 1.0 / r.v;"),
+    ("u_R seed column", "UR[q].d[nxt + nu + q] = 1.0;", "UR[q].d[nxt + q] = 1.0;"),
+    ("s seed", "Sd.d[C - 1] = 1.0;", "Sd.d[C - 1] = 0.5;"),
+    ("defect subtracts x_k", "defect[v + r] = x1[r] - X[(k + 1) * nxt + r];",
+     "defect[v + r] = x1[r] - X[k * nxt + r];"),
+    ("penalty subtracts y_{k+1}", "penalty[(size_t)k * nc + i] = x1[nx + i] - X[k * nxt + nx + i];",
+     "penalty[(size_t)k * nc + i] = x1[nx + i] - X[(k + 1) * nxt + nx + i];"),
+    ("VJP drops -rho on y_k", "gX[k * nxt + nx + i] -= rho[k * nc + i];", "gX[k * nxt + nx + i] -= 0.0;"),
+    ("VJP node layout u_R", "double* gR = (layout == 0) ? gU + (k + 1) * nu",
+     "double* gR = (layout == 0) ? gU + k * nu"),
+    ("VJP node coupling", "gX[(k + 1) * nxt + r] -= w[k * nxt + r];", "gX[(k + 1) * nxt + r] += w[k * nxt + r];"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_reject_planted_error(name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
+    with tempfile.TemporaryDirectory() as tmp:
+        mpath = os.path.join(tmp, "oracle_mut.cpp")
+        lpath = os.path.join(tmp, "liboracle_mut.so")
+        open(mpath, "w").write(src.replace(old, new))
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-pthread", mpath,
+                               "-o", lpath])
+        env = dict(os.environ, CISCVX_ORACLE_LIB=lpath)
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
