@@ -1,0 +1,213 @@
+/*
+ * ciscvx.h — C ABI of the CI-SCvx discretization/linearization library (GB300, sm_103a).
+ *
+ * The library computes, for every interval k of a multiple-shooting grid and
+ * independently of the other intervals, the integral form of the time-dilated
+ * augmented system (Buckner & Elango, Sec. IV-B, Eqs. (14)-(15))
+ *
+ *     x~(1) = F~(x~_k, U_k, s_k),   d x~ / d tau = s_k (f(x,u), Omega(x,u)),  tau in [0,1],
+ *
+ * with a first-order-hold control u(tau) = (1 - tau) u_L + tau u_R (Sec. VI),
+ * integrated by n_sub classical RK4 steps, and its Jacobian blocks (Internal
+ * Numerical Differentiation, Sec. VI)
+ *
+ *     A_k = dF~/dx~_k,  B-_k = dF~/du_L,  B+_k = dF~/du_R,  S_k = dF~/ds_k,
+ *
+ * the defects of the dynamics constraint Eq. (17b), defect_k = x~(1) - x~_{k+1},
+ * and the increments of the path-constraint penalty states that Eq. (13)
+ * bounds, penalty_k = y(1) - y_k.  It also returns the vector-Jacobian product
+ * of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k with respect to all
+ * node states, controls and dilation factors.
+ *
+ * Model (Sec. II-A, Eq. (1)): planar links in maximal coordinates, link b has
+ * q_b = (p_x, p_y, theta), v_b = (v_x, v_y, omega), mass matrix diag(m, m, I).
+ * Revolute joint j (parent p, child c) carries a joint torque tau_j (+tau on
+ * the child, -tau on the parent) and a world-frame reaction force
+ * lambda_j = (lambda_x, lambda_y) (+lambda on the child at its anchor,
+ * -lambda on the parent at its anchor); both are FOH inputs.  Contact i on
+ * flat ground y = 0 (normal (0,1), tangent (1,0)) at a body-frame point of one
+ * link carries inputs (lambda_n, lambda_t+, lambda_t-): world force
+ * (lambda_t+ - lambda_t-, lambda_n).  Gravity acts along -y.  A body-frame
+ * point rho sits at p + R(theta) rho, R = [[cos, -sin], [sin, cos]].
+ * Auxiliary state (Sec. IV-A, Eq. (12)): one state y_i per contact with
+ * y_i' = Omega_i = sum over g in (-lambda_n, -lambda_t+, -lambda_t-, -phi_i(q),
+ * lambda_t+ + lambda_t- - mu lambda_n) of h(g), h(z) = sqrt(1 + max(z,0)^2) - 1,
+ * phi_i the signed distance of the contact point to the ground.
+ *
+ * Layouts (row-major, FP64 unless stated):
+ *   state  x~ = (q_1..q_nb, v_1..v_nb, y_1..y_nc),  n_x~ = 6 n_b + n_c
+ *   input  u  = (tau_1..tau_nj, lambda_1x, lambda_1y, .., lambda_njx, lambda_njy,
+ *                [lambda_n, lambda_t+, lambda_t-] per contact),  n_u = 3 n_j + 3 n_c
+ *   X [N+1][n_x~] node states;  s [N] dilation factors
+ *   U  CISCVX_FOH_NODE: [N+1][n_u], u_L = U_k, u_R = U_{k+1}
+ *      CISCVX_FOH_INTERVAL: [N][2][n_u], (u_L, u_R) per interval (may jump at nodes)
+ *   A [N][n_x~][n_x~], Bm/Bp [N][n_x~][n_u], S [N][n_x~]: FP64 for CISCVX_FP64,
+ *      FP32 for CISCVX_FP32_PHI
+ *   defect [N][n_x~], penalty [N][n_c], z [N][n_x~]: always FP64
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller (unless stated),
+ *     valid for the duration of the asynchronous work; the library keeps no
+ *     reference to them after the call returns.
+ *   - Compute calls are asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) and allocate no memory; scratch memory, where an
+ *     operation needs it, is a caller-provided workspace sized by
+ *     ciscvx_workspace_size().
+ *   - Argument errors are reported synchronously by the return value, with a
+ *     message from ciscvx_last_error() (thread-local); nothing is launched.
+ *   - Errors found on the device (non-finite results) set bits in the
+ *     model's/plan's device status word; ciscvx_sync_status() reads and clears it.
+ */
+#ifndef CISCVX_H_
+#define CISCVX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CISCVX_VERSION_MAJOR 0
+#define CISCVX_VERSION_MINOR 1
+
+typedef enum {
+  CISCVX_OK = 0,
+  CISCVX_EINVAL = 1,       /* invalid argument (null pointer, size, index, layout) */
+  CISCVX_ENOMEM = 2,       /* host or device allocation failed (create calls only) */
+  CISCVX_ECUDA = 3,        /* a CUDA runtime call failed */
+  CISCVX_ENONFINITE = 4,   /* the device produced a non-finite state or block */
+  CISCVX_ETIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+  CISCVX_EUNSUPPORTED = 6  /* valid request outside this build's limits */
+} ciscvx_status;
+
+typedef enum {
+  CISCVX_FP64 = 0,      /* state, penalty and Phi blocks in FP64 */
+  CISCVX_FP32_PHI = 1,  /* Phi blocks (A, B-, B+, S) propagated and stored in FP32;
+                           state, defect and penalty stay FP64 */
+  CISCVX_TF32_TC = 2,   /* reserved: tensor-core Phi products; returns EUNSUPPORTED */
+  CISCVX_BF16_TC = 3    /* reserved: tensor-core Phi products; returns EUNSUPPORTED */
+} ciscvx_precision;
+
+typedef enum {
+  CISCVX_FOH_NODE = 0,     /* U [N+1][n_u]: controls shared by neighbouring intervals */
+  CISCVX_FOH_INTERVAL = 1  /* U [N][2][n_u]: per-interval (u_L, u_R) */
+} ciscvx_u_layout;
+
+/* Limits of this build (ciscvx_model_create / ciscvx_discretize_vjp return
+ * CISCVX_EUNSUPPORTED beyond them). */
+#define CISCVX_MAX_BODIES 32          /* links per model */
+#define CISCVX_MAX_INPUTS_PER_BODY 15 /* inputs acting on one link (<= 4 joints + 1 contact) */
+#define CISCVX_MAX_VJP_SUBSTEPS 64    /* RK4 substeps per interval in the VJP */
+
+/* ---------------------------------------------------------------- model --- */
+
+typedef struct {
+  double mass;     /* > 0 */
+  double inertia;  /* rotational inertia about the centre of mass, > 0 */
+} ciscvx_body_desc;
+
+typedef struct {
+  int parent, child;        /* link indices, distinct, in [0, n_bodies) */
+  double rho_parent[2];     /* joint anchor in the parent's body frame */
+  double rho_child[2];      /* joint anchor in the child's body frame */
+} ciscvx_joint_desc;
+
+typedef struct {
+  int body;                 /* link carrying the contact point (at most one contact per link) */
+  double rho[2];            /* contact point in the link's body frame */
+  double mu;                /* friction coefficient, >= 0 */
+} ciscvx_contact_desc;
+
+typedef struct {
+  int n_bodies, n_joints, n_contacts;
+  const ciscvx_body_desc* bodies;       /* [n_bodies] host memory */
+  const ciscvx_joint_desc* joints;      /* [n_joints] host memory (may be NULL if 0) */
+  const ciscvx_contact_desc* contacts;  /* [n_contacts] host memory (may be NULL if 0) */
+  double gravity;                       /* magnitude, acting along -y, finite */
+} ciscvx_model_desc;
+
+typedef struct ciscvx_model ciscvx_model;
+
+/* Model of Sec. II-A / Sec. IV-A (see the file header).  Copies the host
+ * description, builds the per-link device tables on the current CUDA device
+ * and allocates the model's device status word.  *out receives an opaque
+ * handle owned by the caller (free with ciscvx_model_destroy).  Errors:
+ * EINVAL (null, counts < 0, n_bodies < 1, bad indices, non-positive mass or
+ * inertia, parent == child, non-finite values), EUNSUPPORTED (limits above,
+ * two contacts on one link), ENOMEM / ECUDA (allocation). */
+ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** out);
+
+/* Frees the model's device tables.  NULL is a no-op.  No work using the model
+ * may be in flight. */
+void ciscvx_model_destroy(ciscvx_model* model);
+
+/* n_x = 6 n_b (x~ without the auxiliary states), n_y = n_c, n_u = 3 n_j + 3 n_c.
+ * Any output pointer may be NULL.  EINVAL on a null model. */
+ciscvx_status ciscvx_model_dims(const ciscvx_model* model, int* n_x, int* n_y, int* n_u);
+
+/* ------------------------------------------------------------ workspace --- */
+
+typedef enum { CISCVX_OP_DISCRETIZE = 0, CISCVX_OP_VJP = 1 } ciscvx_op;
+
+/* Bytes of device scratch memory that `op` needs for N intervals (0 if none).
+ * EINVAL on null pointers, N < 1 or an unknown op/layout. */
+ciscvx_status ciscvx_workspace_size(const ciscvx_model* model, ciscvx_op op, int N,
+                                    ciscvx_u_layout layout, size_t* bytes);
+
+/* ----------------------------------------------------------- discretize --- */
+
+/* Linearized discretization of Eqs. (14)-(15) and (17b) on every interval
+ * k = 0..N-1 (see the file header for what is computed and all layouts).
+ *   X [N+1][n_x~], U per `layout`, s [N]: inputs (FP64, device).
+ *   A, Bm, Bp, S: outputs in the dtype of `precision` (device); A and S are
+ *     required; Bm/Bp may be NULL only when n_u == 0.
+ *   defect [N][n_x~], penalty [N][n_c]: FP64 outputs (device); penalty may be
+ *     NULL when n_c == 0.
+ *   z: optional FP64 affine term z_k = x~(1) - A x~_k - B- u_L - B+ u_R - S s_k
+ *     (NULL to skip).
+ *   workspace/ws_bytes: ignored (the operation needs none); pass NULL, 0.
+ * Errors: EINVAL (nulls, N < 1, n_sub < 1, unknown layout/precision),
+ * EUNSUPPORTED (tensor-core precisions), ECUDA (launch failure). */
+ciscvx_status ciscvx_discretize(const ciscvx_model* model, int N, int n_sub,
+                                ciscvx_precision precision, ciscvx_u_layout layout,
+                                const double* X, const double* U, const double* s, void* A,
+                                void* Bm, void* Bp, void* S, double* defect, double* penalty,
+                                double* z, void* workspace, size_t ws_bytes, void* stream);
+
+/* Vector-Jacobian product of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k
+ * (defect and penalty as above) with respect to X, U and s, by the discrete
+ * adjoint of the RK4 substeps with the state checkpointed at every substep
+ * start and the stages recomputed.
+ *   w [N][n_x~], rho [N][n_c] (FP64, device; rho may be NULL when n_c == 0).
+ *   gX [N+1][n_x~], gU like U, gs [N]: FP64 outputs (device), overwritten.
+ *   L: optional FP64 scalar on the device (NULL to skip).
+ *   precision: CISCVX_FP64 (adjoint in FP64) or CISCVX_FP32_PHI (adjoint
+ *     cotangents in FP32; the checkpointed state stays FP64).
+ *   workspace: device scratch of at least ciscvx_workspace_size(CISCVX_OP_VJP)
+ *     bytes, 16-byte aligned; its contents are overwritten.
+ * Errors: as ciscvx_discretize, plus EINVAL for a missing/short workspace and
+ * EUNSUPPORTED for n_sub > CISCVX_MAX_VJP_SUBSTEPS. */
+ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* model, int N, int n_sub,
+                                    ciscvx_precision precision, ciscvx_u_layout layout,
+                                    const double* X, const double* U, const double* s,
+                                    const double* w, const double* rho, double* gX, double* gU,
+                                    double* gs, double* L, void* workspace, size_t ws_bytes,
+                                    void* stream);
+
+/* Waits for `stream`, then reads and clears the model's device status word.
+ * Returns CISCVX_OK, or CISCVX_ENONFINITE if any call since the last read
+ * produced a non-finite state or block; ECUDA if the stream reports an error. */
+ciscvx_status ciscvx_sync_status(const ciscvx_model* model, void* stream);
+
+/* Thread-local description of the last error returned on this thread ("" if none). */
+const char* ciscvx_last_error(void);
+
+/* Library version as MAJOR * 1000 + MINOR. */
+int ciscvx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CISCVX_H_ */

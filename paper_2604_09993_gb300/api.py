@@ -1,0 +1,270 @@
+"""Thin Python binding of ``libciscvx.so`` (include/ciscvx.h) with the same entry point names.
+
+Argument marshalling only: tensors are passed to the C ABI as raw device
+pointers on PyTorch's current CUDA stream; every step of the computation runs
+in the library's CUDA kernels.  There is no fallback: if the library is not
+built or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libciscvx.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(7)
+PRECISION = {"fp64": 0, "fp32_phi": 1, "tf32_tc": 2, "bf16_tc": 3}
+LAYOUT = {"node": 0, "interval": 1}
+OP_DISCRETIZE, OP_VJP = 0, 1
+
+# Every symbol include/ciscvx.h declares.
+EXPORTS = (
+    "ciscvx_version", "ciscvx_last_error", "ciscvx_model_create", "ciscvx_model_destroy",
+    "ciscvx_model_dims", "ciscvx_workspace_size", "ciscvx_discretize", "ciscvx_discretize_vjp",
+    "ciscvx_sync_status",
+)
+
+
+class CiscvxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ciscvx status {status}: {msg}")
+        self.status = status
+
+
+class _Body(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("inertia", ctypes.c_double)]
+
+
+class _Joint(ctypes.Structure):
+    _fields_ = [("parent", ctypes.c_int), ("child", ctypes.c_int),
+                ("rho_parent", ctypes.c_double * 2), ("rho_child", ctypes.c_double * 2)]
+
+
+class _Contact(ctypes.Structure):
+    _fields_ = [("body", ctypes.c_int), ("rho", ctypes.c_double * 2), ("mu", ctypes.c_double)]
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_bodies", ctypes.c_int), ("n_joints", ctypes.c_int),
+                ("n_contacts", ctypes.c_int), ("bodies", ctypes.POINTER(_Body)),
+                ("joints", ctypes.POINTER(_Joint)), ("contacts", ctypes.POINTER(_Contact)),
+                ("gravity", ctypes.c_double)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load(path: str | None = None):
+    """Open the library (it must have been built, e.g. by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    lib.ciscvx_version.restype = ctypes.c_int
+    lib.ciscvx_last_error.restype = ctypes.c_char_p
+    lib.ciscvx_model_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(_vp)]
+    lib.ciscvx_model_destroy.argtypes = [_vp]
+    lib.ciscvx_model_destroy.restype = None
+    lib.ciscvx_model_dims.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
+    lib.ciscvx_workspace_size.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_size_t)]
+    lib.ciscvx_discretize.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                      ctypes.c_size_t, _vp]
+    lib.ciscvx_discretize_vjp.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                          _vp, _vp, ctypes.c_size_t, _vp]
+    lib.ciscvx_sync_status.argtypes = [_vp, _vp]
+    for f in ("ciscvx_model_create", "ciscvx_model_dims", "ciscvx_workspace_size",
+              "ciscvx_discretize", "ciscvx_discretize_vjp", "ciscvx_sync_status"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != OK:
+        raise CiscvxError(st, _lib.ciscvx_last_error().decode())
+
+
+def _get(robot, key):
+    return robot[key] if isinstance(robot, dict) else getattr(robot, key)
+
+
+class Model:
+    """``ciscvx_model`` built from a robot description (synth.Robot or a dict
+    with mass, inertia, joint_*, contact_*, gravity)."""
+
+    def __init__(self, robot):
+        lib = load()
+        mass = np.asarray(_get(robot, "mass"), dtype=np.float64)
+        inertia = np.asarray(_get(robot, "inertia"), dtype=np.float64)
+        jp = np.asarray(_get(robot, "joint_parent"), dtype=np.int64)
+        jc = np.asarray(_get(robot, "joint_child"), dtype=np.int64)
+        rp = np.asarray(_get(robot, "joint_rho_parent"), dtype=np.float64).reshape(-1, 2)
+        rc = np.asarray(_get(robot, "joint_rho_child"), dtype=np.float64).reshape(-1, 2)
+        cb = np.asarray(_get(robot, "contact_body"), dtype=np.int64)
+        cr = np.asarray(_get(robot, "contact_rho"), dtype=np.float64).reshape(-1, 2)
+        cm = np.asarray(_get(robot, "contact_mu"), dtype=np.float64)
+        nb, nj, nc = len(mass), len(jp), len(cb)
+        self._bodies = (_Body * max(nb, 1))(*[_Body(mass[i], inertia[i]) for i in range(nb)])
+        self._joints = (_Joint * max(nj, 1))(*[
+            _Joint(int(jp[j]), int(jc[j]), (ctypes.c_double * 2)(*rp[j]), (ctypes.c_double * 2)(*rc[j]))
+            for j in range(nj)])
+        self._contacts = (_Contact * max(nc, 1))(*[
+            _Contact(int(cb[i]), (ctypes.c_double * 2)(*cr[i]), cm[i]) for i in range(nc)])
+        desc = _Desc(nb, nj, nc, self._bodies, self._joints, self._contacts,
+                     float(_get(robot, "gravity")))
+        h = _vp()
+        _check(lib.ciscvx_model_create(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        nx, ny, nu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.ciscvx_model_dims(h, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nu)))
+        self.nx, self.ny, self.nu = nx.value, ny.value, nu.value
+        self.nxt = self.nx + self.ny
+        self.nb = nb
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ciscvx_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, name, dtype):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def workspace_size(model: Model, op: int, N: int, layout: str = "node") -> int:
+    n = ctypes.c_size_t()
+    _check(load().ciscvx_workspace_size(model.handle, op, int(N), LAYOUT[layout], ctypes.byref(n)))
+    return n.value
+
+
+def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layout: str = "node",
+               want_z: bool = False, out: dict | None = None):
+    """ciscvx_discretize on device tensors.  Returns dict A, Bm, Bp, S, defect, penalty (, z)."""
+    import torch
+    f64 = torch.float64
+    _need(X, "X", f64); _need(U, "U", f64); _need(s, "s", f64)
+    N = s.shape[0]
+    nxt, nu, nc = model.nxt, model.nu, model.ny
+    pdt = f64 if precision == "fp64" else torch.float32
+    dev = X.device
+    if out is None:
+        out = {
+            "A": torch.empty((N, nxt, nxt), dtype=pdt, device=dev),
+            "Bm": torch.empty((N, nxt, nu), dtype=pdt, device=dev),
+            "Bp": torch.empty((N, nxt, nu), dtype=pdt, device=dev),
+            "S": torch.empty((N, nxt), dtype=pdt, device=dev),
+            "defect": torch.empty((N, nxt), dtype=f64, device=dev),
+            "penalty": torch.empty((N, nc), dtype=f64, device=dev),
+        }
+        if want_z:
+            out["z"] = torch.empty((N, nxt), dtype=f64, device=dev)
+    _check(load().ciscvx_discretize(
+        model.handle, int(N), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X), _ptr(U),
+        _ptr(s), _ptr(out["A"]), _ptr(out["Bm"]) if nu else None, _ptr(out["Bp"]) if nu else None,
+        _ptr(out["S"]), _ptr(out["defect"]), _ptr(out["penalty"]) if nc else None,
+        _ptr(out.get("z")), None, 0, _stream()))
+    return out
+
+
+def discretize_vjp(model: Model, X, U, s, w, rho, n_sub: int, precision: str = "fp64",
+                   layout: str = "node", workspace=None, want_L: bool = True):
+    """ciscvx_discretize_vjp on device tensors.  Returns (gX, gU, gs, L or None)."""
+    import torch
+    f64 = torch.float64
+    for t, nm in ((X, "X"), (U, "U"), (s, "s"), (w, "w")):
+        _need(t, nm, f64)
+    if model.ny:
+        _need(rho, "rho", f64)
+    N = s.shape[0]
+    need = workspace_size(model, OP_VJP, N, layout)
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
+    gX = torch.empty_like(X)
+    gU = torch.empty_like(U)
+    gs = torch.empty_like(s)
+    L = torch.empty((), dtype=f64, device=X.device) if want_L else None
+    _check(load().ciscvx_discretize_vjp(
+        model.handle, int(N), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X), _ptr(U),
+        _ptr(s), _ptr(w), _ptr(rho) if model.ny else None, _ptr(gX), _ptr(gU) if model.nu else None,
+        _ptr(gs), _ptr(L), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream()))
+    return gX, gU, gs, L
+
+
+def sync_status(model: Model):
+    """Waits for the current stream and raises if the device flagged a non-finite result."""
+    _check(load().ciscvx_sync_status(model.handle, _stream()))
+
+
+def _make_function():
+    import torch
+
+    class Discretize(torch.autograd.Function):
+        """(X, U, s) -> (defect, penalty) through ciscvx_discretize; the backward
+        pass is ciscvx_discretize_vjp with cotangents w = dL/ddefect and
+        rho = dL/dpenalty (the adjoint kernel, not autograd tracing)."""
+
+        @staticmethod
+        def forward(ctx, X, U, s, model, n_sub, precision, layout):
+            out = discretize(model, X, U, s, n_sub, precision, layout)
+            ctx.save_for_backward(X, U, s)
+            ctx.cfg = (model, n_sub, precision, layout)
+            return out["defect"], out["penalty"]
+
+        @staticmethod
+        def backward(ctx, gdef, gpen):
+            X, U, s = ctx.saved_tensors
+            model, n_sub, precision, layout = ctx.cfg
+            w = torch.zeros((s.shape[0], model.nxt), dtype=X.dtype, device=X.device) \
+                if gdef is None else gdef.contiguous()
+            rho = torch.zeros((s.shape[0], model.ny), dtype=X.dtype, device=X.device) \
+                if gpen is None else gpen.contiguous()
+            gX, gU, gs, _ = discretize_vjp(model, X, U, s, w, rho, n_sub, precision, layout,
+                                           want_L=False)
+            return gX, gU, gs, None, None, None, None
+
+    return Discretize
+
+
+_Discretize = None
+
+
+def discretize_fn(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layout: str = "node"):
+    """Differentiable (defect, penalty) = F(X, U, s) (torch.autograd.Function)."""
+    global _Discretize
+    if _Discretize is None:
+        _Discretize = _make_function()
+    return _Discretize.apply(X, U, s, model, n_sub, precision, layout)

@@ -1,0 +1,273 @@
+// api.cu — host side of the C ABI declared in include/ciscvx.h.
+//
+// Validation, the per-link device tables (coefficients of every input on every
+// link, see common.cuh), the device status word, thread-local error messages
+// and the launches.  Compute calls allocate nothing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+
+using namespace ciscvx;
+
+struct ciscvx_model {
+  DevModel host;        // host copy of the device tables
+  DevModel* dev;        // device copy
+  unsigned* status;     // device status word
+  int device;           // CUDA device the tables live on
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+ciscvx_status fail(ciscvx_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+ciscvx_status ok() {
+  g_err.clear();
+  return CISCVX_OK;
+}
+
+bool finite2(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]); }
+
+// Adds input `q` acting on link `b` with the given coefficients.
+ciscvx_status add_input(DevModel& M, int b, int q, double ax, double ay, double p, double qq,
+                        double t) {
+  DevBody& B = M.body[b];
+  if (B.nin >= MAXIN)
+    return fail(CISCVX_EUNSUPPORTED, "link %d has more than %d inputs acting on it", b, MAXIN);
+  const int i = B.nin++;
+  B.idx[i] = q;
+  B.ax[i] = ax; B.ay[i] = ay; B.p[i] = p; B.q[i] = qq; B.t[i] = t;
+  return CISCVX_OK;
+}
+
+ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
+  std::memset(&M, 0, sizeof M);
+  const int nb = d->n_bodies, nj = d->n_joints, nc = d->n_contacts;
+  M.nb = nb; M.nj = nj; M.nc = nc;
+  M.nxt = 6 * nb + nc;
+  M.nu = 3 * nj + 3 * nc;
+  M.g = d->gravity;
+  for (int b = 0; b < nb; ++b) {
+    M.body[b].contact = -1;
+    M.body[b].cin = -1;
+  }
+  for (int b = 0; b < nb; ++b) {
+    const double m = d->bodies[b].mass, I = d->bodies[b].inertia;
+    if (!(std::isfinite(m) && m > 0) || !(std::isfinite(I) && I > 0))
+      return fail(CISCVX_EINVAL, "link %d: mass and inertia must be finite and > 0", b);
+  }
+  for (int j = 0; j < nj; ++j) {
+    const ciscvx_joint_desc& J = d->joints[j];
+    if (J.parent < 0 || J.parent >= nb || J.child < 0 || J.child >= nb || J.parent == J.child)
+      return fail(CISCVX_EINVAL, "joint %d: parent/child must be distinct links in [0,%d)", j, nb);
+    if (!finite2(J.rho_parent) || !finite2(J.rho_child))
+      return fail(CISCVX_EINVAL, "joint %d: non-finite anchor", j);
+    const int c = J.child, p = J.parent;
+    const double mc = d->bodies[c].mass, Ic = d->bodies[c].inertia;
+    const double mp = d->bodies[p].mass, Ip = d->bodies[p].inertia;
+    const double cx = J.rho_child[0], cy = J.rho_child[1];
+    const double px = J.rho_parent[0], py = J.rho_parent[1];
+    ciscvx_status st;
+    // torque: +tau on the child, -tau on the parent
+    if ((st = add_input(M, c, j, 0, 0, 0, 0, 1.0 / Ic))) return st;
+    if ((st = add_input(M, p, j, 0, 0, 0, 0, -1.0 / Ip))) return st;
+    // lambda_x: +e_x on the child at rho_c, -e_x on the parent at rho_p
+    //   rho x e_x = -rho_y, rho . e_x = rho_x
+    if ((st = add_input(M, c, nj + 2 * j, 1.0 / mc, 0, -cy / Ic, cx / Ic, 0))) return st;
+    if ((st = add_input(M, p, nj + 2 * j, -1.0 / mp, 0, py / Ip, -px / Ip, 0))) return st;
+    // lambda_y: rho x e_y = rho_x, rho . e_y = rho_y
+    if ((st = add_input(M, c, nj + 2 * j + 1, 0, 1.0 / mc, cx / Ic, cy / Ic, 0))) return st;
+    if ((st = add_input(M, p, nj + 2 * j + 1, 0, -1.0 / mp, -px / Ip, -py / Ip, 0))) return st;
+  }
+  for (int i = 0; i < nc; ++i) {
+    const ciscvx_contact_desc& C = d->contacts[i];
+    if (C.body < 0 || C.body >= nb) return fail(CISCVX_EINVAL, "contact %d: bad link %d", i, C.body);
+    if (!finite2(C.rho) || !std::isfinite(C.mu) || C.mu < 0)
+      return fail(CISCVX_EINVAL, "contact %d: non-finite point or negative mu", i);
+    DevBody& B = M.body[C.body];
+    if (B.contact >= 0)
+      return fail(CISCVX_EUNSUPPORTED, "link %d carries more than one contact", C.body);
+    B.contact = i;
+    B.cin = 3 * nj + 3 * i;
+    B.crho[0] = C.rho[0]; B.crho[1] = C.rho[1];
+    B.mu = C.mu;
+    const double m = d->bodies[C.body].mass, I = d->bodies[C.body].inertia;
+    const double rx = C.rho[0], ry = C.rho[1];
+    ciscvx_status st;
+    // lambda_n: +e_y;  lambda_t+: +e_x;  lambda_t-: -e_x
+    if ((st = add_input(M, C.body, B.cin, 0, 1.0 / m, rx / I, ry / I, 0))) return st;
+    if ((st = add_input(M, C.body, B.cin + 1, 1.0 / m, 0, -ry / I, rx / I, 0))) return st;
+    if ((st = add_input(M, C.body, B.cin + 2, -1.0 / m, 0, ry / I, -rx / I, 0))) return st;
+  }
+  // VJP slots: link b's inputs occupy slots [slot0, slot0 + nin)
+  int slot = 0;
+  for (int b = 0; b < nb; ++b) {
+    M.body[b].slot0 = slot;
+    for (int i = 0; i < M.body[b].nin; ++i) {
+      const int q = M.body[b].idx[i];
+      if (M.in_n[q] >= 2) return fail(CISCVX_EINVAL, "input %d acts on more than two links", q);
+      M.in_slot[q][M.in_n[q]++] = slot + i;
+    }
+    slot += M.body[b].nin;
+  }
+  M.nslot = slot;
+  return CISCVX_OK;
+}
+
+bool layout_ok(int layout) { return layout == CISCVX_FOH_NODE || layout == CISCVX_FOH_INTERVAL; }
+
+ciscvx_status check_common(const ciscvx_model* m, int N, int n_sub, int precision, int layout,
+                           const double* X, const double* U, const double* s) {
+  if (!m) return fail(CISCVX_EINVAL, "null model");
+  if (N < 1) return fail(CISCVX_EINVAL, "N must be >= 1 (got %d)", N);
+  if (n_sub < 1) return fail(CISCVX_EINVAL, "n_sub must be >= 1 (got %d)", n_sub);
+  if (!layout_ok(layout)) return fail(CISCVX_EINVAL, "unknown control layout %d", layout);
+  if (precision == CISCVX_TF32_TC || precision == CISCVX_BF16_TC)
+    return fail(CISCVX_EUNSUPPORTED, "tensor-core precisions are not provided by this build");
+  if (precision != CISCVX_FP64 && precision != CISCVX_FP32_PHI)
+    return fail(CISCVX_EINVAL, "unknown precision %d", precision);
+  if (!X || !s || (m->host.nu > 0 && !U)) return fail(CISCVX_EINVAL, "null input array");
+  return CISCVX_OK;
+}
+
+ciscvx_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(CISCVX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+int ciscvx_version(void) { return CISCVX_VERSION_MAJOR * 1000 + CISCVX_VERSION_MINOR; }
+
+const char* ciscvx_last_error(void) { return g_err.c_str(); }
+
+ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** out) {
+  if (!desc || !out) return fail(CISCVX_EINVAL, "null argument");
+  *out = nullptr;
+  if (desc->n_bodies < 1 || desc->n_joints < 0 || desc->n_contacts < 0)
+    return fail(CISCVX_EINVAL, "need n_bodies >= 1, n_joints >= 0, n_contacts >= 0");
+  if (!desc->bodies || (desc->n_joints > 0 && !desc->joints) ||
+      (desc->n_contacts > 0 && !desc->contacts))
+    return fail(CISCVX_EINVAL, "null body/joint/contact array");
+  if (desc->n_bodies > MAXB || desc->n_joints > MAXJ || desc->n_contacts > MAXB)
+    return fail(CISCVX_EUNSUPPORTED, "at most %d links, %d joints, %d contacts", MAXB, MAXJ, MAXB);
+  if (!std::isfinite(desc->gravity)) return fail(CISCVX_EINVAL, "non-finite gravity");
+  ciscvx_model* m = new (std::nothrow) ciscvx_model;
+  if (!m) return fail(CISCVX_ENOMEM, "host allocation failed");
+  ciscvx_status st = build_tables(desc, m->host);
+  if (st != CISCVX_OK) { delete m; return st; }
+  m->dev = nullptr;
+  m->status = nullptr;
+  cudaGetDevice(&m->device);
+  cudaError_t e = cudaMalloc(&m->dev, sizeof(DevModel));
+  if (e == cudaSuccess) e = cudaMalloc(&m->status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    if (m->dev) cudaFree(m->dev);
+    if (m->status) cudaFree(m->status);
+    delete m;
+    return e == cudaErrorMemoryAllocation ? fail(CISCVX_ENOMEM, "device allocation failed")
+                                          : cuda_fail(e, "model upload");
+  }
+  *out = m;
+  return ok();
+}
+
+void ciscvx_model_destroy(ciscvx_model* m) {
+  if (!m) return;
+  if (m->dev) cudaFree(m->dev);
+  if (m->status) cudaFree(m->status);
+  delete m;
+}
+
+ciscvx_status ciscvx_model_dims(const ciscvx_model* m, int* n_x, int* n_y, int* n_u) {
+  if (!m) return fail(CISCVX_EINVAL, "null model");
+  if (n_x) *n_x = 6 * m->host.nb;
+  if (n_y) *n_y = m->host.nc;
+  if (n_u) *n_u = m->host.nu;
+  return ok();
+}
+
+ciscvx_status ciscvx_workspace_size(const ciscvx_model* m, ciscvx_op op, int N,
+                                    ciscvx_u_layout layout, size_t* bytes) {
+  if (!m || !bytes) return fail(CISCVX_EINVAL, "null argument");
+  if (N < 1) return fail(CISCVX_EINVAL, "N must be >= 1");
+  if (!layout_ok(layout)) return fail(CISCVX_EINVAL, "unknown control layout %d", (int)layout);
+  if (op == CISCVX_OP_DISCRETIZE) *bytes = 0;
+  else if (op == CISCVX_OP_VJP)
+    *bytes = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
+  else return fail(CISCVX_EINVAL, "unknown op %d", (int)op);
+  return ok();
+}
+
+ciscvx_status ciscvx_discretize(const ciscvx_model* m, int N, int n_sub,
+                                ciscvx_precision precision, ciscvx_u_layout layout,
+                                const double* X, const double* U, const double* s, void* A,
+                                void* Bm, void* Bp, void* S, double* defect, double* penalty,
+                                double* z, void* workspace, size_t ws_bytes, void* stream) {
+  (void)workspace; (void)ws_bytes;
+  ciscvx_status st = check_common(m, N, n_sub, precision, layout, X, U, s);
+  if (st != CISCVX_OK) return st;
+  if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
+  if (m->host.nu > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
+  if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
+  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, X, U, s, A,
+                                    Bm, Bp, S, defect, penalty, z, m->status,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
+  return ok();
+}
+
+ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
+                                    ciscvx_precision precision, ciscvx_u_layout layout,
+                                    const double* X, const double* U, const double* s,
+                                    const double* w, const double* rho, double* gX, double* gU,
+                                    double* gs, double* L, void* workspace, size_t ws_bytes,
+                                    void* stream) {
+  ciscvx_status st = check_common(m, N, n_sub, precision, layout, X, U, s);
+  if (st != CISCVX_OK) return st;
+  if (n_sub > MAXSUB_VJP)
+    return fail(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (got %d)", MAXSUB_VJP, n_sub);
+  if (!w || (m->host.nc > 0 && !rho)) return fail(CISCVX_EINVAL, "null cotangent array");
+  if (!gX || !gs || (m->host.nu > 0 && !gU)) return fail(CISCVX_EINVAL, "null gradient array");
+  const size_t need = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
+  if (!workspace || ws_bytes < need)
+    return fail(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
+  if (((uintptr_t)workspace & 15) != 0) return fail(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+  cudaError_t e = launch_vjp(m->dev, m->host.nb, m->host.nxt, m->host.nu, m->host.nslot, N, n_sub,
+                             precision, layout, X, U, s, w, rho, gX, gU, gs, L, workspace,
+                             m->status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
+  return ok();
+}
+
+ciscvx_status ciscvx_sync_status(const ciscvx_model* m, void* stream) {
+  if (!m) return fail(CISCVX_EINVAL, "null model");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, m->status, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (h & ST_NONFINITE) return fail(CISCVX_ENONFINITE, "non-finite state or block produced");
+  return ok();
+}
+
+}  // extern "C"

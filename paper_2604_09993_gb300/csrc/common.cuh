@@ -1,0 +1,97 @@
+// common.cuh — device-side model tables and helpers shared by the CI-SCvx kernels.
+//
+// Structure the kernels exploit (all exact consequences of the model in
+// include/ciscvx.h, Sec. II-A Eq. (1) with joint reaction forces as inputs):
+//
+//  * Links are decoupled: link b's accelerations depend only on its own angle
+//    and on the inputs acting on it, so every link is an independent ODE and
+//    the Jacobian blocks are block-sparse by link.
+//  * Translation: v' = s a(tau), p' = s v with a(tau) affine in tau under the
+//    first-order hold.  RK4 integrates this polynomial trajectory exactly, so
+//    p(1), v(1) and their derivatives have closed forms.
+//  * Rotation: with r = R(theta) rho, r x F = cos(theta) (rho x F) - sin(theta)
+//    (rho . F), so omega' = cos(theta) P(tau) - sin(theta) Q(tau) + T(tau) with
+//    P, Q, T linear in u and hence affine in tau.  The sensitivity of (theta,
+//    omega) to input k is p_k Psi_c + q_k Psi_s + t_k Psi_1, where Psi_c,
+//    Psi_s, Psi_1 are the tangents driven by cos(theta) w(tau), -sin(theta)
+//    w(tau), w(tau) with w = 1 - tau (u_L) or tau (u_R): the RK4 tangent
+//    recursion is linear in its forcing, so superposition is exact.  Nine
+//    tangent columns (theta_0, omega_0, s and six basis forcings) cover every
+//    input of a link.
+//  * The contact penalty state of a foot link depends on the foot's p_y and
+//    theta and on its three contact inputs; its row is a quadrature of the
+//    stage sensitivities with the RK4 weights.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ciscvx.h"
+
+namespace ciscvx {
+
+constexpr int MAXB = CISCVX_MAX_BODIES;
+constexpr int MAXIN = CISCVX_MAX_INPUTS_PER_BODY;
+constexpr int MAXJ = 2 * MAXB;          // joints per model (<= 4 per link)
+constexpr int MAXU = 3 * MAXJ + 3 * MAXB;
+constexpr int MAXSUB_VJP = CISCVX_MAX_VJP_SUBSTEPS;
+
+// device status bits
+constexpr unsigned ST_NONFINITE = 1u;
+
+// Per-link program: the inputs acting on the link with their coefficients
+// (already divided by m or I), and the link's contact if it has one.
+struct DevBody {
+  int nin;           // inputs acting on this link
+  int contact;       // contact index, or -1
+  int cin;           // input index of the contact's lambda_n (lambda_t+ = cin+1, lambda_t- = cin+2)
+  int slot0;         // first VJP partial slot of this link within an interval
+  double crho[2];    // contact point (body frame)
+  double mu;         // friction coefficient
+  double pad_;
+  int idx[MAXIN + 1];  // input index per slot
+  double ax[MAXIN + 1];  // dv_x/du   (sigma/m for an x force, else 0)
+  double ay[MAXIN + 1];  // dv_y/du   (sigma/m for a y force, else 0)
+  double p[MAXIN + 1];   // d(omega')/du coefficient of cos(theta): sigma (rho x e)/I
+  double q[MAXIN + 1];   // coefficient of -sin(theta): sigma (rho . e)/I
+  double t[MAXIN + 1];   // torque coefficient: sigma/I
+};
+
+struct DevModel {
+  int nb, nj, nc, nxt, nu, nslot;   // nslot = sum of nin over links
+  double g;
+  int in_n[MAXU];        // per input: number of (link, slot) contributions (1 or 2)
+  int in_slot[MAXU][2];  // per input: partial slots that contribute
+  DevBody body[MAXB];
+};
+
+// Pseudo-Huber ramp h(z) = sqrt(1 + p^2) - 1 = p^2 / (1 + sqrt(1 + p^2)),
+// p = max(z, 0), and its derivative h'(z) = p / sqrt(1 + p^2).
+__device__ __forceinline__ void huber(double z, double& H, double& D) {
+  const double p = fmax(z, 0.0);
+  const double r = sqrt(fma(p, p, 1.0));
+  H = (p * p) / (1.0 + r);
+  D = p / r;
+}
+
+__device__ __forceinline__ double rk_c(int j) { return j == 0 ? 0.0 : (j == 3 ? 1.0 : 0.5); }
+__device__ __forceinline__ double rk_w(int j) {
+  return (j == 0 || j == 3) ? (1.0 / 6.0) : (2.0 / 6.0);
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+}  // namespace ciscvx
+
+// Launchers (defined in disc.cu / vjp.cu), called by the host API in api.cu.
+namespace ciscvx {
+cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int prec, int layout,
+                              const double* X, const double* U, const double* s, void* A,
+                              void* Bm, void* Bp, void* S, double* defect, double* penalty,
+                              double* z, unsigned* status, cudaStream_t st);
+cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, int N, int nsub,
+                       int prec, int layout, const double* X, const double* U, const double* s,
+                       const double* w, const double* rho, double* gX, double* gU, double* gs,
+                       double* L, void* ws, unsigned* status, cudaStream_t st);
+size_t vjp_workspace_bytes(int nb, int nu, int nslot, int N, int layout);
+}  // namespace ciscvx
