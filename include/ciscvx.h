@@ -195,6 +195,36 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* model, int N, int n_sub,
                                     double* gs, double* L, void* workspace, size_t ws_bytes,
                                     void* stream);
 
+/* ------------------------------------------------ allocation-free VJP --- */
+
+/* Bytes of device scratch the library keeps for ciscvx_discretize_vjp_static. */
+#define CISCVX_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* The same VJP as ciscvx_discretize_vjp, for callers that cannot allocate
+ * device memory when they call it.  The paper has no counterpart; this is a
+ * deployment convenience.  Typical callers: a model-predictive-control loop
+ * that re-linearizes every few milliseconds (cudaMalloc there can synchronize
+ * the device and has unbounded latency), or a solver embedded in a framework
+ * that owns all device memory through its own pool.
+ *   Arguments are those of ciscvx_discretize_vjp without the workspace: the
+ *   caller still passes all inputs and outputs (device pointers).
+ *   Scratch: a static array of CISCVX_STATIC_SCRATCH_BYTES inside the library,
+ *   held on every GPU that loads the library until the process exits.  The
+ *   first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   Calls share the one array: calls whose work overlaps on the GPU (other
+ *   streams or host threads) race; serialize them.  Nothing in the array
+ *   needs clearing (every scratch element is written before it is read).
+ *   Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: as ciscvx_discretize_vjp, and CISCVX_EUNSUPPORTED when N intervals
+ * of this model need more scratch than CISCVX_STATIC_SCRATCH_BYTES
+ * (ciscvx_workspace_size(CISCVX_OP_VJP) tells how much). */
+ciscvx_status ciscvx_discretize_vjp_static(const ciscvx_model* model, int N, int n_sub,
+                                           ciscvx_precision precision, ciscvx_u_layout layout,
+                                           const double* X, const double* U, const double* s,
+                                           const double* w, const double* rho, double* gX,
+                                           double* gU, double* gs, double* L, void* stream);
+
 /* Waits for `stream`, then reads and clears the model's device status word.
  * Returns CISCVX_OK, or CISCVX_ENONFINITE if any call since the last read
  * produced a non-finite state or block; ECUDA if the stream reports an error. */

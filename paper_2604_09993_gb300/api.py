@@ -24,7 +24,7 @@ OP_DISCRETIZE, OP_VJP = 0, 1
 EXPORTS = (
     "ciscvx_version", "ciscvx_last_error", "ciscvx_model_create", "ciscvx_model_destroy",
     "ciscvx_model_dims", "ciscvx_workspace_size", "ciscvx_discretize", "ciscvx_discretize_vjp",
-    "ciscvx_sync_status",
+    "ciscvx_sync_status", "ciscvx_discretize_vjp_static",
 )
 
 
@@ -83,8 +83,12 @@ def load(path: str | None = None):
                                           ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                           _vp, _vp, ctypes.c_size_t, _vp]
     lib.ciscvx_sync_status.argtypes = [_vp, _vp]
+    lib.ciscvx_discretize_vjp_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                 _vp, _vp, _vp]
     for f in ("ciscvx_model_create", "ciscvx_model_dims", "ciscvx_workspace_size",
-              "ciscvx_discretize", "ciscvx_discretize_vjp", "ciscvx_sync_status"):
+              "ciscvx_discretize", "ciscvx_discretize_vjp", "ciscvx_sync_status",
+              "ciscvx_discretize_vjp_static"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -221,6 +225,27 @@ def discretize_vjp(model: Model, X, U, s, w, rho, n_sub: int, precision: str = "
         _ptr(s), _ptr(w), _ptr(rho) if model.ny else None, _ptr(gX), _ptr(gU) if model.nu else None,
         _ptr(gs), _ptr(L), _ptr(workspace), workspace.numel() * workspace.element_size(),
         _stream()))
+    return gX, gU, gs, L
+
+
+def discretize_vjp_static(model: Model, X, U, s, w, rho, n_sub: int, precision: str = "fp64",
+                          layout: str = "node", want_L: bool = True):
+    """ciscvx_discretize_vjp_static: the VJP with the library's built-in scratch
+    (no workspace, no device allocation inside the call).  Returns (gX, gU, gs, L or None)."""
+    import torch
+    f64 = torch.float64
+    for t, nm in ((X, "X"), (U, "U"), (s, "s"), (w, "w")):
+        _need(t, nm, f64)
+    if model.ny:
+        _need(rho, "rho", f64)
+    gX = torch.empty_like(X)
+    gU = torch.empty_like(U)
+    gs = torch.empty_like(s)
+    L = torch.empty((), dtype=f64, device=X.device) if want_L else None
+    _check(load().ciscvx_discretize_vjp_static(
+        model.handle, int(s.shape[0]), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X),
+        _ptr(U), _ptr(s), _ptr(w), _ptr(rho) if model.ny else None, _ptr(gX),
+        _ptr(gU) if model.nu else None, _ptr(gs), _ptr(L), _stream()))
     return gX, gU, gs, L
 
 

@@ -150,6 +150,17 @@ ciscvx_status cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
+// Sets this thread's last-error message for entry points defined in other files.
+ciscvx_status ciscvx::set_error(ciscvx_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
 extern "C" {
 
 int ciscvx_version(void) { return CISCVX_VERSION_MAJOR * 1000 + CISCVX_VERSION_MINOR; }

@@ -94,4 +94,6 @@ cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, i
                        const double* w, const double* rho, double* gX, double* gU, double* gs,
                        double* L, void* ws, unsigned* status, cudaStream_t st);
 size_t vjp_workspace_bytes(int nb, int nu, int nslot, int N, int layout);
+// Records a formatted last-error message (thread-local) and returns st.
+ciscvx_status set_error(ciscvx_status st, const char* fmt, ...);
 }  // namespace ciscvx
