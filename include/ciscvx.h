@@ -195,6 +195,124 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* model, int N, int n_sub,
                                     double* gs, double* L, void* workspace, size_t ws_bytes,
                                     void* stream);
 
+/* ---------------------------------------------------------------- batch --- */
+/*
+ * Many independent problem instances (different robots, horizons N and
+ * substep counts, e.g. random restarts or homotopy sweeps) linearized by one
+ * persistent launch.  A plan fixes the instances and packs their arrays back
+ * to back in instance order: instance i's X starts at element offset
+ * sum_{j<i} (N_j + 1) n_x~_j of the packed X buffer, and likewise for every
+ * other array (ciscvx_batch_offsets gives each instance's offsets,
+ * ciscvx_batch_sizes the buffer lengths).  Within an instance the layouts are
+ * those of ciscvx_discretize / ciscvx_discretize_vjp.
+ *
+ * Work decomposition: intervals of instances that share (model, n_sub) are
+ * grouped 32 at a time (a group may span instances), one group x one link is a
+ * work item for one warp, and items are ordered by estimated cost, largest
+ * first.  A persistent grid pulls items from a device counter.  The launch
+ * sequence (counter reset + kernel) is captured once into a CUDA graph per
+ * set of buffers and replayed.
+ */
+
+typedef struct ciscvx_batch_plan ciscvx_batch_plan;
+
+/* Launch shape of the batched kernels (chosen by ciscvx_batch_autotune or given). */
+typedef struct {
+  int warps_per_cta;  /* 1, 2, 4 or 8 */
+  int ctas_per_sm;    /* > 0: persistent grid of ctas_per_sm x SMs CTAs pulling items from a
+                         queue; 0: one warp per work item */
+  int lpt_order;      /* 1: items ordered by decreasing estimated cost; 0: instance order */
+  int use_graph;      /* 1: capture the launch sequence in a CUDA graph and replay it */
+} ciscvx_tune;
+
+/* Element counts of the packed buffers (or, from ciscvx_batch_offsets, the
+ * element offsets of one instance inside them).  A/Bm/Bp/S in the plan's Phi
+ * dtype; everything else FP64.  L has one element per instance. */
+typedef struct {
+  size_t X, U, s, A, B, S, defect, penalty, L;
+} ciscvx_batch_sizes;
+
+typedef struct {
+  const double* X;   /* packed inputs (device) */
+  const double* U;
+  const double* s;
+  void* A;           /* packed outputs (device); Bm/Bp may be NULL only if every n_u == 0 */
+  void* Bm;
+  void* Bp;
+  void* S;
+  double* defect;
+  double* penalty;   /* may be NULL only if every n_c == 0 */
+} ciscvx_batch_io;
+
+typedef struct {
+  const double* X;   /* packed inputs (device) */
+  const double* U;
+  const double* s;
+  const double* w;   /* cotangents, packed like defect */
+  const double* rho; /* packed like penalty */
+  double* gX;        /* packed like X */
+  double* gU;        /* packed like U */
+  double* gs;        /* packed like s */
+  double* L;         /* [n_inst] per-instance L, or NULL */
+} ciscvx_batch_vjp_io;
+
+/* Builds the work decomposition for n_inst instances: instance i uses
+ * models[model_idx[i]] with N[i] intervals and n_sub[i] substeps.  All arrays
+ * are host memory, copied; the models must outlive the plan and live on the
+ * current device.  tune may be NULL (defaults: 4 warps/CTA, persistent with
+ * 2 CTAs/SM, cost order, graph).  Allocates the plan's device tables (this
+ * is the only allocating batch call besides autotuning's timing buffers).
+ * Errors: EINVAL (nulls, n_inst < 1, bad indices, N < 1, n_sub < 1, layout,
+ * precision), EUNSUPPORTED (tensor-core precisions), ENOMEM/ECUDA. */
+ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_models,
+                                       const int* model_idx, const int* N, const int* n_sub,
+                                       int n_inst, ciscvx_precision precision,
+                                       ciscvx_u_layout layout, const ciscvx_tune* tune,
+                                       ciscvx_batch_plan** out);
+
+/* Frees the plan (no work using it may be in flight).  NULL is a no-op. */
+void ciscvx_batch_plan_destroy(ciscvx_batch_plan* plan);
+
+/* Lengths (elements) of the packed buffers. */
+ciscvx_status ciscvx_batch_sizes_get(const ciscvx_batch_plan* plan, ciscvx_batch_sizes* out);
+
+/* Element offsets of instance `inst` inside the packed buffers. */
+ciscvx_status ciscvx_batch_offsets(const ciscvx_batch_plan* plan, int inst, ciscvx_batch_sizes* out);
+
+/* Current launch shape of the plan. */
+ciscvx_status ciscvx_batch_get_tune(const ciscvx_batch_plan* plan, ciscvx_tune* out);
+
+/* Linearized discretization (as ciscvx_discretize) of every interval of every
+ * instance, asynchronously on `stream`.  With use_graph the first call for a
+ * given io captures the launch sequence into a graph (on a private stream of
+ * the plan) and every call replays it on `stream`; make that first call
+ * outside any capture of your own.  Errors: EINVAL (null io or required
+ * pointer), ECUDA. */
+ciscvx_status ciscvx_batch_discretize(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
+                                      void* stream);
+
+/* Bytes of device scratch ciscvx_batch_discretize_vjp needs. */
+ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* plan, size_t* bytes);
+
+/* VJP (as ciscvx_discretize_vjp) of every instance; L receives one value per
+ * instance.  workspace: device, >= ciscvx_batch_vjp_workspace_size bytes,
+ * 16-byte aligned.  Errors: EINVAL, EUNSUPPORTED (n_sub > CISCVX_MAX_VJP_SUBSTEPS
+ * in some instance), ECUDA. */
+ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_vjp_io* io,
+                                          void* workspace, size_t ws_bytes, void* stream);
+
+/* Times candidate launch shapes of ciscvx_batch_discretize on the given
+ * buffers (their outputs are overwritten), keeps the fastest in the plan and
+ * returns it in *chosen (may be NULL).  Results are cached per process by
+ * (models' topology, substep counts, precision, device name); a cached choice
+ * is reused without timing.  Synchronizes `stream`.  Errors: as
+ * ciscvx_batch_discretize. */
+ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
+                                    void* stream, ciscvx_tune* chosen);
+
+/* As ciscvx_sync_status, for the plan's status word. */
+ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* plan, void* stream);
+
 /* ------------------------------------------------ allocation-free VJP --- */
 
 /* Bytes of device scratch the library keeps for ciscvx_discretize_vjp_static. */

@@ -31,11 +31,16 @@ class _CModel(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile ``oracle.cpp`` into ``liboracle.so`` next to it (g++, -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
-                               _SRC, "-o", tmp])
-        os.replace(tmp, _LIB)
+    stale = lambda: not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)  # noqa: E731
+    if force or stale():
+        import fcntl
+        with open(_LIB + ".lock", "w") as lk:
+            fcntl.flock(lk, fcntl.LOCK_EX)  # one build at a time (parallel test workers)
+            if force or stale():
+                tmp = _LIB + f".tmp{os.getpid()}"
+                subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
+                                       _SRC, "-o", tmp])
+                os.replace(tmp, _LIB)
     return _LIB
 
 

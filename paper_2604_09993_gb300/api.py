@@ -25,7 +25,31 @@ EXPORTS = (
     "ciscvx_version", "ciscvx_last_error", "ciscvx_model_create", "ciscvx_model_destroy",
     "ciscvx_model_dims", "ciscvx_workspace_size", "ciscvx_discretize", "ciscvx_discretize_vjp",
     "ciscvx_sync_status", "ciscvx_discretize_vjp_static",
+    "ciscvx_batch_plan_create", "ciscvx_batch_plan_destroy", "ciscvx_batch_sizes_get",
+    "ciscvx_batch_offsets", "ciscvx_batch_get_tune", "ciscvx_batch_discretize",
+    "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp", "ciscvx_batch_autotune",
+    "ciscvx_batch_sync_status",
 )
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("lpt_order", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class _Sizes(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_size_t) for k in ("X", "U", "s", "A", "B", "S", "defect", "penalty", "L")]
+
+
+class _BatchIO(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("X", "U", "s", "A", "Bm", "Bp", "S", "defect", "penalty")]
+
+
+class _BatchVjpIO(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("X", "U", "s", "w", "rho", "gX", "gU", "gs", "L")]
 
 
 class CiscvxError(RuntimeError):
@@ -86,9 +110,26 @@ def load(path: str | None = None):
     lib.ciscvx_discretize_vjp_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                                  _vp, _vp, _vp]
+    P = ctypes.POINTER
+    lib.ciscvx_batch_plan_create.argtypes = [P(_vp), ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
+                                             P(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, P(Tune), P(_vp)]
+    lib.ciscvx_batch_plan_destroy.argtypes = [_vp]
+    lib.ciscvx_batch_plan_destroy.restype = None
+    lib.ciscvx_batch_sizes_get.argtypes = [_vp, P(_Sizes)]
+    lib.ciscvx_batch_offsets.argtypes = [_vp, ctypes.c_int, P(_Sizes)]
+    lib.ciscvx_batch_get_tune.argtypes = [_vp, P(Tune)]
+    lib.ciscvx_batch_discretize.argtypes = [_vp, P(_BatchIO), _vp]
+    lib.ciscvx_batch_vjp_workspace_size.argtypes = [_vp, P(ctypes.c_size_t)]
+    lib.ciscvx_batch_discretize_vjp.argtypes = [_vp, P(_BatchVjpIO), _vp, ctypes.c_size_t, _vp]
+    lib.ciscvx_batch_autotune.argtypes = [_vp, P(_BatchIO), _vp, P(Tune)]
+    lib.ciscvx_batch_sync_status.argtypes = [_vp, _vp]
     for f in ("ciscvx_model_create", "ciscvx_model_dims", "ciscvx_workspace_size",
               "ciscvx_discretize", "ciscvx_discretize_vjp", "ciscvx_sync_status",
-              "ciscvx_discretize_vjp_static"):
+              "ciscvx_discretize_vjp_static", "ciscvx_batch_plan_create", "ciscvx_batch_sizes_get",
+              "ciscvx_batch_offsets", "ciscvx_batch_get_tune", "ciscvx_batch_discretize",
+              "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp",
+              "ciscvx_batch_autotune", "ciscvx_batch_sync_status"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -293,3 +334,130 @@ def discretize_fn(model: Model, X, U, s, n_sub: int, precision: str = "fp64", la
     if _Discretize is None:
         _Discretize = _make_function()
     return _Discretize.apply(X, U, s, model, n_sub, precision, layout)
+
+
+class BatchPlan:
+    """``ciscvx_batch_plan``: n instances, instance i using ``models[model_idx[i]]``
+    with ``N[i]`` intervals and ``n_sub[i]`` substeps; arrays are packed back to
+    back in instance order (see include/ciscvx.h)."""
+
+    def __init__(self, models, model_idx, N, n_sub, precision="fp32_phi", layout="node",
+                 tune: dict | None = None):
+        lib = load()
+        self.models = list(models)
+        self.model_idx = np.asarray(model_idx, dtype=np.int32)
+        self.N = np.asarray(N, dtype=np.int32)
+        self.n_sub = np.asarray(n_sub, dtype=np.int32)
+        self.n_inst = len(self.model_idx)
+        self.precision, self.layout = precision, layout
+        hs = (_vp * len(self.models))(*[m.handle for m in self.models])
+        ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))  # noqa: E731
+        t = Tune(**tune) if tune else None
+        h = _vp()
+        _check(lib.ciscvx_batch_plan_create(hs, len(self.models), ip(self.model_idx), ip(self.N),
+                                            ip(self.n_sub), self.n_inst, PRECISION[precision],
+                                            LAYOUT[layout], ctypes.byref(t) if t else None,
+                                            ctypes.byref(h)))
+        self._h = h
+        sz = _Sizes()
+        _check(lib.ciscvx_batch_sizes_get(h, ctypes.byref(sz)))
+        self.sizes = {k: getattr(sz, k) for k, _ in _Sizes._fields_}
+        offs = []
+        for i in range(self.n_inst):
+            o = _Sizes()
+            _check(lib.ciscvx_batch_offsets(h, i, ctypes.byref(o)))
+            offs.append({k: getattr(o, k) for k, _ in _Sizes._fields_})
+        self.offsets = offs
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tune(self):
+        t = Tune()
+        _check(load().ciscvx_batch_get_tune(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def alloc_outputs(self, device):
+        import torch
+        pdt = torch.float64 if self.precision == "fp64" else torch.float32
+        z = self.sizes
+        return {
+            "A": torch.empty(max(z["A"], 1), dtype=pdt, device=device),
+            "Bm": torch.empty(max(z["B"], 1), dtype=pdt, device=device),
+            "Bp": torch.empty(max(z["B"], 1), dtype=pdt, device=device),
+            "S": torch.empty(max(z["S"], 1), dtype=pdt, device=device),
+            "defect": torch.empty(max(z["defect"], 1), dtype=torch.float64, device=device),
+            "penalty": torch.empty(max(z["penalty"], 1), dtype=torch.float64, device=device),
+        }
+
+    def _io(self, X, U, s, out):
+        return _BatchIO(*[t.data_ptr() for t in (X, U, s, out["A"], out["Bm"], out["Bp"], out["S"],
+                                                 out["defect"], out["penalty"])])
+
+    def discretize(self, X, U, s, out=None):
+        """ciscvx_batch_discretize on packed device tensors; returns the packed outputs."""
+        if out is None:
+            out = self.alloc_outputs(X.device)
+        io = self._io(X, U, s, out)
+        _check(load().ciscvx_batch_discretize(self._h, ctypes.byref(io), _stream()))
+        return out
+
+    def autotune(self, X, U, s, out=None):
+        if out is None:
+            out = self.alloc_outputs(X.device)
+        io = self._io(X, U, s, out)
+        t = Tune()
+        _check(load().ciscvx_batch_autotune(self._h, ctypes.byref(io), _stream(), ctypes.byref(t)))
+        return t.as_dict()
+
+    def vjp_workspace_size(self):
+        n = ctypes.c_size_t()
+        _check(load().ciscvx_batch_vjp_workspace_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def discretize_vjp(self, X, U, s, w, rho, workspace=None, want_L=True, out=None):
+        """ciscvx_batch_discretize_vjp; returns dict gX, gU, gs, L (per instance)."""
+        import torch
+        need = self.vjp_workspace_size()
+        if workspace is None or workspace.numel() * workspace.element_size() < need:
+            workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
+        if out is None:
+            out = {"gX": torch.empty_like(X), "gU": torch.empty_like(U), "gs": torch.empty_like(s),
+                   "L": torch.empty(self.n_inst, dtype=torch.float64, device=X.device) if want_L else None}
+        io = _BatchVjpIO(*[None if t is None else t.data_ptr()
+                           for t in (X, U, s, w, rho, out["gX"], out["gU"], out["gs"], out["L"])])
+        _check(load().ciscvx_batch_discretize_vjp(self._h, ctypes.byref(io), _ptr(workspace),
+                                                  workspace.numel() * workspace.element_size(),
+                                                  _stream()))
+        return out
+
+    def sync_status(self):
+        _check(load().ciscvx_batch_sync_status(self._h, _stream()))
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ciscvx_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- packing helpers (host numpy) --
+    def pack(self, arrays, key, total_key=None):
+        """Packs per-instance numpy arrays into one flat array in instance order."""
+        total = self.sizes[total_key or key]
+        flat = np.empty(max(total, 1), dtype=np.float64)
+        for i, a in enumerate(arrays):
+            o = self.offsets[i][key]
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+            flat[o:o + a.size] = a
+        return flat
+
+    def unpack(self, flat, key, i, shape):
+        o = self.offsets[i][key]
+        n = int(np.prod(shape))
+        return np.asarray(flat[o:o + n]).reshape(shape)

@@ -46,6 +46,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     """Compile (if stale) and return the path of ``libciscvx.so``."""
     if not force and up_to_date():
         return LIB
+    import fcntl
+    os.makedirs(os.path.join(HERE, "_build"), exist_ok=True)
+    with open(os.path.join(HERE, "_build", ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)  # one build at a time (parallel test workers)
+        if not force and up_to_date():
+            return LIB
+        return _build_locked(verbose, ptxas_info)
+
+
+def _build_locked(verbose, ptxas_info):
     nvcc = nvcc_path()
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)

@@ -14,13 +14,6 @@
 
 using namespace ciscvx;
 
-struct ciscvx_model {
-  DevModel host;        // host copy of the device tables
-  DevModel* dev;        // device copy
-  unsigned* status;     // device status word
-  int device;           // CUDA device the tables live on
-};
-
 namespace {
 
 thread_local std::string g_err;

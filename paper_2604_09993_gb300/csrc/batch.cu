@@ -1,0 +1,624 @@
+// batch.cu — batched heterogeneous discretization and VJP (many independent
+// instances: different robots, horizons N and substep counts) in one launch.
+//
+// Work decomposition (built on the host when the plan is created):
+//  * bucket = (model, n_sub); every interval of every instance in the bucket
+//    is an entry (instance, k);
+//  * group = 32 consecutive entries of one bucket (may span instances), so a
+//    warp's 32 lanes run the same link program with the same trip counts;
+//  * item = group x link; items are ordered by estimated cost (n_sub, doubled
+//    for foot links), largest first, and a persistent grid pulls them from a
+//    device counter (no waits: each warp takes the next index with one
+//    atomicAdd and stops when the list is exhausted).
+// The launch sequence (counter reset + kernel) is captured into a CUDA graph
+// once per set of buffers and replayed.  An autotuner times launch shapes.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "disc_link.cuh"
+#include "vjp_link.cuh"
+
+namespace ciscvx {
+
+struct DevInst {
+  int model, N, nsub, pad_;
+  long long x, u, s, a, b, v, p;  // element offsets: X/gX, U/gU, s/gs, A, Bm/Bp, S/defect/w, penalty/rho
+  long long part, pb;             // VJP workspace offsets: per-input partials, per-(interval, link) partials
+};
+
+struct BatchCommon {
+  const DevModel* const* models;
+  const DevInst* inst;
+  const int2* entries;   // (instance, k)
+  const int4* groups;    // (model, nsub, first entry, count)
+  const int2* items;     // (group, link)
+  int n_items;
+  int persistent;
+  int* queue;
+  unsigned* status;
+  int layout;
+};
+
+__device__ __forceinline__ int next_item(const BatchCommon& c, int& local_iter) {
+  if (!c.persistent) {
+    const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    return local_iter++ == 0 ? w : c.n_items;
+  }
+  int it = 0;
+  if ((threadIdx.x & 31) == 0) it = atomicAdd(c.queue, 1);
+  return __shfl_sync(0xffffffffu, it, 0);
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(256) k_batch_disc(BatchCommon c, const double* __restrict__ X,
+                                                    const double* __restrict__ U,
+                                                    const double* __restrict__ s, TP* A, TP* Bm,
+                                                    TP* Bp, TP* S, double* defect,
+                                                    double* penalty) {
+  const int lane = threadIdx.x & 31;
+  int iter = 0;
+  for (;;) {
+    const int item = next_item(c, iter);
+    if (item >= c.n_items) break;
+    const int2 it = c.items[item];
+    const int4 g = c.groups[it.x];
+    if (lane < g.w) {
+      const DevModel& M = *c.models[g.x];
+      const int b = it.y;
+      const int2 e = c.entries[g.z + lane];
+      const DevInst& I = c.inst[e.x];
+      const long k = e.y;
+      const int nxt = M.nxt, nu = M.nu, nc = M.nc;
+      const double* Xi = X + I.x;
+      const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
+      const double* uR = uL + nu;
+      TP* Ak = A + I.a + (size_t)k * nxt * nxt;
+      TP* Bmk = Bm ? Bm + I.b + (size_t)k * nxt * nu : nullptr;
+      TP* Bpk = Bp ? Bp + I.b + (size_t)k * nxt * nu : nullptr;
+      TP* Sk = S + I.v + (size_t)k * nxt;
+      double* dk = defect + I.v + (size_t)k * nxt;
+      double* pk = penalty ? penalty + I.p + (size_t)k * nc : nullptr;
+      if (M.body[b].contact >= 0)
+        disc_link<TP, true>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, Ak,
+                            Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
+      else
+        disc_link<TP, false>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, Ak,
+                             Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
+    }
+  }
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(256) k_batch_vjp(BatchCommon c, const double* __restrict__ X,
+                                                   const double* __restrict__ U,
+                                                   const double* __restrict__ s,
+                                                   const double* __restrict__ w,
+                                                   const double* __restrict__ rho, double* gX,
+                                                   double* part, double* ps, double* pL) {
+  const int lane = threadIdx.x & 31;
+  int iter = 0;
+  for (;;) {
+    const int item = next_item(c, iter);
+    if (item >= c.n_items) break;
+    const int2 it = c.items[item];
+    const int4 g = c.groups[it.x];
+    if (lane < g.w) {
+      const DevModel& M = *c.models[g.x];
+      const int b = it.y;
+      const int2 e = c.entries[g.z + lane];
+      const DevInst& I = c.inst[e.x];
+      const long k = e.y;
+      const int N = I.N, nxt = M.nxt, nu = M.nu, nc = M.nc, nb = M.nb;
+      const double* Xi = X + I.x;
+      const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
+      const double* uR = uL + nu;
+      const double* wi = w + I.v;
+      const DevBody& B = M.body[b];
+      const double rc = (B.contact >= 0) ? rho[I.p + k * nc + B.contact] : 0.0;
+      const double* wkm1 = (k > 0) ? wi + (k - 1) * nxt : nullptr;
+      double* gXi = gX + I.x;
+      double* gXN = (k == N - 1) ? gXi + (size_t)N * nxt : nullptr;
+      double* pp = part + I.part + (size_t)k * M.nslot * 2;
+      double* psk = ps + I.pb + k * nb;
+      double* pLk = pL + I.pb + k * nb;
+      if (B.contact >= 0)
+        vjp_link<TP, true>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
+                           wi + k * nxt, wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk,
+                           c.status);
+      else
+        vjp_link<TP, false>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
+                            wi + k * nxt, wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk,
+                            c.status);
+    }
+  }
+}
+
+constexpr int FINB = 256;
+
+// One CTA per instance: dL/dU (node layout sums the u_L part of interval k and
+// the u_R part of interval k-1), dL/ds and L, all in a fixed summation order.
+__global__ void __launch_bounds__(FINB) k_batch_vjp_finish(const DevModel* const* models,
+                                                           const DevInst* inst, int layout,
+                                                           const double* __restrict__ part,
+                                                           const double* __restrict__ ps,
+                                                           const double* __restrict__ pL,
+                                                           double* gU, double* gs, double* L) {
+  __shared__ double red[FINB];
+  const DevInst I = inst[blockIdx.x];
+  const DevModel& M = *models[I.model];
+  const int nu = M.nu, nslot = M.nslot, nb = M.nb, N = I.N;
+  const double* P = part + I.part;
+  const long nrow = (layout == CISCVX_FOH_NODE) ? (long)N + 1 : 2L * N;
+  for (long idx = threadIdx.x; idx < nrow * nu; idx += FINB) {
+    const long r = idx / nu;
+    const int q = (int)(idx - r * nu);
+    const int n = M.in_n[q];
+    double v = 0.0;
+    if (layout == CISCVX_FOH_NODE) {
+      if (r < N) for (int t = 0; t < n; ++t) v += P[(size_t)r * nslot * 2 + 2 * M.in_slot[q][t]];
+      if (r > 0) for (int t = 0; t < n; ++t) v += P[(size_t)(r - 1) * nslot * 2 + 2 * M.in_slot[q][t] + 1];
+    } else {
+      const long k = r >> 1;
+      const int side = (int)(r & 1);
+      for (int t = 0; t < n; ++t) v += P[(size_t)k * nslot * 2 + 2 * M.in_slot[q][t] + side];
+    }
+    gU[I.u + idx] = v;
+  }
+  double Lacc = 0.0;
+  for (int k = threadIdx.x; k < N; k += FINB) {
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      v += ps[I.pb + (long)k * nb + b];
+      Lacc += pL[I.pb + (long)k * nb + b];
+    }
+    gs[I.s + k] = v;
+  }
+  if (L) {
+    red[threadIdx.x] = Lacc;
+    __syncthreads();
+    for (int o = FINB / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) L[blockIdx.x] = red[0];
+  }
+}
+
+}  // namespace ciscvx
+
+using namespace ciscvx;
+
+struct ciscvx_batch_plan {
+  int n_inst = 0, n_models = 0, prec = 0, layout = 0, device = 0, sm_count = 0, max_nsub = 0;
+  bool all_nu0 = true, all_nc0 = true;
+  std::vector<const ciscvx_model*> models;
+  std::vector<DevInst> inst;
+  ciscvx_batch_sizes sizes{};
+  size_t part_total = 0, pb_total = 0;
+  int n_items = 0;
+  std::vector<int2> items_lpt, items_nat;
+  std::string key;
+  // device tables
+  const DevModel** d_models = nullptr;
+  DevInst* d_inst = nullptr;
+  int2* d_entries = nullptr;
+  int4* d_groups = nullptr;
+  int2* d_items_lpt = nullptr;
+  int2* d_items_nat = nullptr;
+  int* d_queue = nullptr;  // [0]: discretize, [1]: vjp
+  unsigned* d_status = nullptr;
+  ciscvx_tune tune{4, 2, 1, 1};
+  // graph cache
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ciscvx_batch_io graph_io{};
+  ciscvx_tune graph_tune{};
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, ciscvx_tune> g_tune_cache;
+
+bool tune_ok(const ciscvx_tune& t) {
+  return (t.warps_per_cta == 1 || t.warps_per_cta == 2 || t.warps_per_cta == 4 ||
+          t.warps_per_cta == 8) &&
+         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32;
+}
+
+void free_plan(ciscvx_batch_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  cudaFree(p->d_models);
+  cudaFree(p->d_inst);
+  cudaFree(p->d_entries);
+  cudaFree(p->d_groups);
+  cudaFree(p->d_items_lpt);
+  cudaFree(p->d_items_nat);
+  cudaFree(p->d_queue);
+  cudaFree(p->d_status);
+  delete p;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  const size_t n = std::max<size_t>(v.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)dst, n);
+  if (e == cudaSuccess && !v.empty())
+    e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot) {
+  BatchCommon c;
+  c.models = p->d_models;
+  c.inst = p->d_inst;
+  c.entries = p->d_entries;
+  c.groups = p->d_groups;
+  c.items = p->tune.lpt_order ? p->d_items_lpt : p->d_items_nat;
+  c.n_items = p->n_items;
+  c.persistent = p->tune.ctas_per_sm > 0;
+  c.queue = p->d_queue + queue_slot;
+  c.status = p->d_status;
+  c.layout = p->layout;
+  return c;
+}
+
+void grid_of(const ciscvx_batch_plan* p, unsigned& blocks, unsigned& threads) {
+  threads = 32u * (unsigned)p->tune.warps_per_cta;
+  if (p->tune.ctas_per_sm > 0) {
+    blocks = (unsigned)(p->sm_count * p->tune.ctas_per_sm);
+  } else {
+    blocks = (unsigned)((p->n_items + p->tune.warps_per_cta - 1) / p->tune.warps_per_cta);
+  }
+  if (blocks == 0) blocks = 1;
+}
+
+cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStream_t st) {
+  BatchCommon c = common_of(p, 0);
+  if (c.persistent) {
+    cudaError_t e = cudaMemsetAsync(p->d_queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
+  unsigned blocks, threads;
+  grid_of(p, blocks, threads);
+  if (p->prec == CISCVX_FP64)
+    k_batch_disc<double><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (double*)io->A,
+                                                     (double*)io->Bm, (double*)io->Bp,
+                                                     (double*)io->S, io->defect, io->penalty);
+  else
+    k_batch_disc<float><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (float*)io->A,
+                                                    (float*)io->Bm, (float*)io->Bp, (float*)io->S,
+                                                    io->defect, io->penalty);
+  return cudaGetLastError();
+}
+
+bool same_io(const ciscvx_batch_io& a, const ciscvx_batch_io& b) {
+  return std::memcmp(&a, &b, sizeof a) == 0;
+}
+
+bool same_tune(const ciscvx_tune& a, const ciscvx_tune& b) {
+  return std::memcmp(&a, &b, sizeof a) == 0;
+}
+
+ciscvx_status check_io(const ciscvx_batch_plan* p, const ciscvx_batch_io* io) {
+  if (!p || !io) return set_error(CISCVX_EINVAL, "null plan or io");
+  if (!io->X || !io->s || !io->A || !io->S || !io->defect)
+    return set_error(CISCVX_EINVAL, "null required buffer in ciscvx_batch_io");
+  if (!p->all_nu0 && (!io->U || !io->Bm || !io->Bp))
+    return set_error(CISCVX_EINVAL, "null U / Bm / Bp");
+  if (!p->all_nc0 && !io->penalty) return set_error(CISCVX_EINVAL, "null penalty");
+  return CISCVX_OK;
+}
+
+std::string model_signature(const DevModel& M) {
+  std::string s = std::to_string(M.nb) + "." + std::to_string(M.nj) + "." + std::to_string(M.nc);
+  for (int b = 0; b < M.nb; ++b)
+    s += "/" + std::to_string(M.body[b].nin) + (M.body[b].contact >= 0 ? "f" : "");
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_models,
+                                       const int* model_idx, const int* N, const int* n_sub,
+                                       int n_inst, ciscvx_precision precision,
+                                       ciscvx_u_layout layout, const ciscvx_tune* tune,
+                                       ciscvx_batch_plan** out) {
+  if (!out) return set_error(CISCVX_EINVAL, "null out");
+  *out = nullptr;
+  if (!models || n_models < 1 || !model_idx || !N || !n_sub || n_inst < 1)
+    return set_error(CISCVX_EINVAL, "need models, n_models >= 1, n_inst >= 1 and per-instance arrays");
+  if (layout != CISCVX_FOH_NODE && layout != CISCVX_FOH_INTERVAL)
+    return set_error(CISCVX_EINVAL, "unknown control layout %d", (int)layout);
+  if (precision == CISCVX_TF32_TC || precision == CISCVX_BF16_TC)
+    return set_error(CISCVX_EUNSUPPORTED, "tensor-core precisions are not provided by this build");
+  if (precision != CISCVX_FP64 && precision != CISCVX_FP32_PHI)
+    return set_error(CISCVX_EINVAL, "unknown precision %d", (int)precision);
+  if (tune && !tune_ok(*tune)) return set_error(CISCVX_EINVAL, "invalid ciscvx_tune");
+  for (int m = 0; m < n_models; ++m)
+    if (!models[m]) return set_error(CISCVX_EINVAL, "null model %d", m);
+  for (int i = 0; i < n_inst; ++i) {
+    if (model_idx[i] < 0 || model_idx[i] >= n_models)
+      return set_error(CISCVX_EINVAL, "instance %d: model index %d out of range", i, model_idx[i]);
+    if (N[i] < 1 || n_sub[i] < 1)
+      return set_error(CISCVX_EINVAL, "instance %d: N and n_sub must be >= 1", i);
+  }
+  ciscvx_batch_plan* p = new (std::nothrow) ciscvx_batch_plan;
+  if (!p) return set_error(CISCVX_ENOMEM, "host allocation failed");
+  p->n_inst = n_inst;
+  p->n_models = n_models;
+  p->prec = precision;
+  p->layout = layout;
+  p->models.assign(models, models + n_models);
+  if (tune) p->tune = *tune;
+  cudaGetDevice(&p->device);
+  cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+  if (p->sm_count < 1) p->sm_count = 1;
+
+  // packed offsets, instance order
+  p->inst.resize(n_inst);
+  ciscvx_batch_sizes& z = p->sizes;
+  std::memset(&z, 0, sizeof z);
+  for (int i = 0; i < n_inst; ++i) {
+    const DevModel& M = models[model_idx[i]]->host;
+    DevInst& I = p->inst[i];
+    I.model = model_idx[i];
+    I.N = N[i];
+    I.nsub = n_sub[i];
+    I.x = (long long)z.X; I.u = (long long)z.U; I.s = (long long)z.s; I.a = (long long)z.A;
+    I.b = (long long)z.B; I.v = (long long)z.S; I.p = (long long)z.penalty;
+    I.part = (long long)p->part_total;
+    I.pb = (long long)p->pb_total;
+    const size_t n = (size_t)N[i], nxt = M.nxt, nu = M.nu, nc = M.nc;
+    z.X += (n + 1) * nxt;
+    z.U += (layout == CISCVX_FOH_NODE ? (n + 1) : 2 * n) * nu;
+    z.s += n;
+    z.A += n * nxt * nxt;
+    z.B += n * nxt * nu;
+    z.S += n * nxt;
+    z.defect += n * nxt;
+    z.penalty += n * nc;
+    p->part_total += n * (size_t)M.nslot * 2;
+    p->pb_total += n * (size_t)M.nb;
+    p->max_nsub = std::max(p->max_nsub, n_sub[i]);
+    if (nu) p->all_nu0 = false;
+    if (nc) p->all_nc0 = false;
+  }
+  z.L = (size_t)n_inst;
+
+  // buckets (model, n_sub) -> entries -> groups of 32 -> items (group x link)
+  std::map<std::pair<int, int>, std::vector<int>> buckets;
+  for (int i = 0; i < n_inst; ++i) buckets[{model_idx[i], n_sub[i]}].push_back(i);
+  std::vector<int2> entries;
+  std::vector<int4> groups;
+  std::vector<std::pair<long long, int2>> costed;
+  std::string key = std::to_string(precision) + "|" + std::to_string(layout) + "|";
+  for (auto& kv : buckets) {
+    const int m = kv.first.first, ns = kv.first.second;
+    const DevModel& M = models[m]->host;
+    const int first = (int)entries.size();
+    for (int i : kv.second)
+      for (int k = 0; k < N[i]; ++k) entries.push_back(make_int2(i, k));
+    const int cnt = (int)entries.size() - first;
+    for (int g0 = 0; g0 < cnt; g0 += 32) {
+      const int gi = (int)groups.size();
+      groups.push_back(make_int4(m, ns, first + g0, std::min(32, cnt - g0)));
+      for (int b = 0; b < M.nb; ++b)
+        costed.push_back({(long long)ns * (M.body[b].contact >= 0 ? 2 : 1), make_int2(gi, b)});
+    }
+    int lg = 0;
+    while ((1 << lg) < cnt) ++lg;
+    key += model_signature(M) + "@" + std::to_string(ns) + "x2^" + std::to_string(lg) + ";";
+  }
+  p->key = key;
+  p->n_items = (int)costed.size();
+  for (auto& c : costed) p->items_nat.push_back(c.second);
+  std::stable_sort(costed.begin(), costed.end(),
+                   [](const std::pair<long long, int2>& a, const std::pair<long long, int2>& b) {
+                     return a.first > b.first;
+                   });
+  for (auto& c : costed) p->items_lpt.push_back(c.second);
+
+  std::vector<const DevModel*> dm(n_models);
+  for (int m = 0; m < n_models; ++m) dm[m] = models[m]->dev;
+  cudaError_t e = upload(&p->d_models, dm);
+  if (e == cudaSuccess) e = upload(&p->d_inst, p->inst);
+  if (e == cudaSuccess) e = upload(&p->d_entries, entries);
+  if (e == cudaSuccess) e = upload(&p->d_groups, groups);
+  if (e == cudaSuccess) e = upload(&p->d_items_lpt, p->items_lpt);
+  if (e == cudaSuccess) e = upload(&p->d_items_nat, p->items_nat);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_queue, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return set_error(e == cudaErrorMemoryAllocation ? CISCVX_ENOMEM : CISCVX_ECUDA,
+                     "plan upload: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return CISCVX_OK;
+}
+
+void ciscvx_batch_plan_destroy(ciscvx_batch_plan* plan) { free_plan(plan); }
+
+ciscvx_status ciscvx_batch_sizes_get(const ciscvx_batch_plan* p, ciscvx_batch_sizes* out) {
+  if (!p || !out) return set_error(CISCVX_EINVAL, "null argument");
+  *out = p->sizes;
+  return CISCVX_OK;
+}
+
+ciscvx_status ciscvx_batch_offsets(const ciscvx_batch_plan* p, int i, ciscvx_batch_sizes* out) {
+  if (!p || !out) return set_error(CISCVX_EINVAL, "null argument");
+  if (i < 0 || i >= p->n_inst) return set_error(CISCVX_EINVAL, "instance %d out of range", i);
+  const DevInst& I = p->inst[i];
+  out->X = (size_t)I.x; out->U = (size_t)I.u; out->s = (size_t)I.s; out->A = (size_t)I.a;
+  out->B = (size_t)I.b; out->S = (size_t)I.v; out->defect = (size_t)I.v;
+  out->penalty = (size_t)I.p; out->L = (size_t)i;
+  return CISCVX_OK;
+}
+
+ciscvx_status ciscvx_batch_get_tune(const ciscvx_batch_plan* p, ciscvx_tune* out) {
+  if (!p || !out) return set_error(CISCVX_EINVAL, "null argument");
+  *out = p->tune;
+  return CISCVX_OK;
+}
+
+ciscvx_status ciscvx_batch_discretize(ciscvx_batch_plan* p, const ciscvx_batch_io* io,
+                                      void* stream) {
+  ciscvx_status st = check_io(p, io);
+  if (st != CISCVX_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!p->tune.use_graph) {
+    e = launch_disc(p, io, s);
+    if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    return CISCVX_OK;
+  }
+  if (!p->exec || !same_io(p->graph_io, *io) || !same_tune(p->graph_tune, p->tune)) {
+    if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = launch_disc(p, io, p->cap);
+      e = cudaStreamEndCapture(p->cap, &g);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->exec = nullptr;
+      return set_error(CISCVX_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    p->graph_io = *io;
+    p->graph_tune = p->tune;
+  }
+  e = cudaGraphLaunch(p->exec, s);
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+  return CISCVX_OK;
+}
+
+ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* p, size_t* bytes) {
+  if (!p || !bytes) return set_error(CISCVX_EINVAL, "null argument");
+  *bytes = sizeof(double) * (p->part_total + 2 * p->pb_total);
+  return CISCVX_OK;
+}
+
+ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io,
+                                          void* workspace, size_t ws_bytes, void* stream) {
+  if (!p || !io) return set_error(CISCVX_EINVAL, "null plan or io");
+  if (!io->X || !io->s || !io->w || !io->gX || !io->gs)
+    return set_error(CISCVX_EINVAL, "null required buffer in ciscvx_batch_vjp_io");
+  if (!p->all_nu0 && (!io->U || !io->gU)) return set_error(CISCVX_EINVAL, "null U / gU");
+  if (!p->all_nc0 && !io->rho) return set_error(CISCVX_EINVAL, "null rho");
+  if (p->max_nsub > MAXSUB_VJP)
+    return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (plan has %d)",
+                     MAXSUB_VJP, p->max_nsub);
+  const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
+  if (!workspace || ws_bytes < need)
+    return set_error(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
+  if (((uintptr_t)workspace & 15) != 0) return set_error(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* part = (double*)workspace;
+  double* ps = part + p->part_total;
+  double* pL = ps + p->pb_total;
+  BatchCommon c = common_of(p, 1);
+  cudaError_t e = cudaSuccess;
+  if (c.persistent) e = cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), s);
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "queue reset: %s", cudaGetErrorString(e));
+  unsigned blocks, threads;
+  grid_of(p, blocks, threads);
+  if (p->prec == CISCVX_FP64)
+    k_batch_vjp<double><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX,
+                                                   part, ps, pL);
+  else
+    k_batch_vjp<float><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX,
+                                                  part, ps, pL);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    k_batch_vjp_finish<<<p->n_inst, FINB, 0, s>>>(p->d_models, p->d_inst, p->layout, part, ps, pL,
+                                                  io->gU, io->gs, io->L);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch vjp launch: %s", cudaGetErrorString(e));
+  return CISCVX_OK;
+}
+
+ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* p, const ciscvx_batch_io* io, void* stream,
+                                    ciscvx_tune* chosen) {
+  ciscvx_status st = check_io(p, io);
+  if (st != CISCVX_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int keep_graph = p->tune.use_graph;
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, p->device);
+  const std::string key = std::string(prop.name) + "|" + p->key;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      p->tune = it->second;
+      p->tune.use_graph = keep_graph;
+      if (chosen) *chosen = p->tune;
+      return CISCVX_OK;
+    }
+  }
+  static const ciscvx_tune cands[] = {
+      {4, 2, 1, 0}, {8, 1, 1, 0}, {2, 4, 1, 0}, {1, 8, 1, 0}, {4, 0, 1, 0}, {8, 0, 1, 0},
+      {4, 2, 0, 0}, {4, 4, 1, 0},
+  };
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_error(CISCVX_ECUDA, "event creation failed");
+  float best = 1e30f;
+  ciscvx_tune bt = p->tune;
+  cudaError_t e = cudaSuccess;
+  for (const ciscvx_tune& c : cands) {
+    p->tune = c;
+    e = launch_disc(p, io, s);  // warm-up
+    if (e != cudaSuccess) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_disc(p, io, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bt = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  bt.use_graph = keep_graph;
+  p->tune = bt;
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = bt;
+  }
+  if (chosen) *chosen = bt;
+  return CISCVX_OK;
+}
+
+ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* p, void* stream) {
+  if (!p) return set_error(CISCVX_EINVAL, "null plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, p->d_status, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "status read: %s", cudaGetErrorString(e));
+  if (h & ST_NONFINITE) return set_error(CISCVX_ENONFINITE, "non-finite state or block produced");
+  return CISCVX_OK;
+}
+
+}  // extern "C"

@@ -83,6 +83,14 @@ __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
 }  // namespace ciscvx
 
+// The opaque model handle of the C ABI.
+struct ciscvx_model {
+  ciscvx::DevModel host;  // host copy of the device tables
+  ciscvx::DevModel* dev;  // device copy
+  unsigned* status;       // device status word
+  int device;             // CUDA device the tables live on
+};
+
 // Launchers (defined in disc.cu / vjp.cu), called by the host API in api.cu.
 namespace ciscvx {
 cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int prec, int layout,

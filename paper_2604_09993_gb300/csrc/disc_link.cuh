@@ -1,0 +1,308 @@
+// disc_link.cuh — one link of one interval of the linearized discretization
+// (Sec. IV-B Eqs. (14)-(15), Eq. (17b); IND + FOH, Sec. VI), shared by the
+// single-instance and the batched kernels.  See common.cuh for the structure
+// it exploits and disc.cu for the thread mapping.
+#pragma once
+#include "common.cuh"
+
+namespace ciscvx {
+
+template <typename TP>
+struct Tangents {
+  TP Pt[9], Pw[9];   // rotation tangents: theta row, omega row
+  TP Qp[5], Qv[5];   // foot p_y/v_y tangents: columns py0, vy0, s, L, R
+  TP Yr[9], Yp[5], Yd[6];  // foot penalty row: rotation columns, p_y columns, direct contact inputs
+};
+
+// One link of one interval.  xk/xk1: node states k and k+1; uL/uR: FOH
+// controls; A/Bm/Bp/S/defect/pen/z: this interval's output blocks.
+template <typename TP, bool FOOT>
+__device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, double sd,
+                                          const double* __restrict__ xk,
+                                          const double* __restrict__ xk1,
+                                          const double* __restrict__ uL,
+                                          const double* __restrict__ uR, TP* __restrict__ A,
+                                          TP* __restrict__ Bm, TP* __restrict__ Bp,
+                                          TP* __restrict__ S, double* __restrict__ defect,
+                                          double* __restrict__ pen, double* __restrict__ z,
+                                          unsigned* status) {
+  const DevBody& B = M.body[b];
+  const int nb = M.nb, nxt = M.nxt, nu = M.nu;
+  const double g = M.g;
+  const int nin = B.nin;
+
+  // Input sums at the interval ends (the forces/torques are linear in u).
+  double AxL = 0, AxR = 0, AyL = 0, AyR = 0, PL = 0, PR = 0, QL = 0, QR = 0, TL = 0, TR = 0;
+  for (int i = 0; i < nin; ++i) {
+    const int q = B.idx[i];
+    const double a = uL[q], c = uR[q];
+    AxL = fma(B.ax[i], a, AxL); AxR = fma(B.ax[i], c, AxR);
+    AyL = fma(B.ay[i], a, AyL); AyR = fma(B.ay[i], c, AyR);
+    PL = fma(B.p[i], a, PL); PR = fma(B.p[i], c, PR);
+    QL = fma(B.q[i], a, QL); QR = fma(B.q[i], c, QR);
+    TL = fma(B.t[i], a, TL); TR = fma(B.t[i], c, TR);
+  }
+  const int rpx = 3 * b, rpy = rpx + 1, rth = rpx + 2;
+  const int rvx = 3 * nb + 3 * b, rvy = rvx + 1, rom = rvx + 2;
+  const double px0 = xk[rpx], py0 = xk[rpy], th0 = xk[rth];
+  const double vx0 = xk[rvx], vy0 = xk[rvy], om0 = xk[rom];
+
+  // Translation in closed form (exact for RK4: polynomial of degree <= 3 in tau).
+  const double axm = 0.5 * (AxL + AxR), ax3 = AxL * (1.0 / 3.0) + AxR * (1.0 / 6.0);
+  const double aym = 0.5 * (AyL + AyR) - g, ay3 = AyL * (1.0 / 3.0) + AyR * (1.0 / 6.0) - 0.5 * g;
+  const double px1 = px0 + sd * vx0 + sd * sd * ax3, vx1 = vx0 + sd * axm;
+  const double py1 = py0 + sd * vy0 + sd * sd * ay3, vy1 = vy0 + sd * aym;
+
+  constexpr bool foot = FOOT;  // B.contact >= 0; warp-uniform, dispatched by the kernel
+  const int cin = B.cin;
+  double lnL = 0, lnD = 0, tpL = 0, tpD = 0, tmL = 0, tmD = 0;
+  if (foot) {
+    lnL = uL[cin]; lnD = uR[cin] - lnL;
+    tpL = uL[cin + 1]; tpD = uR[cin + 1] - tpL;
+    tmL = uL[cin + 2]; tmD = uR[cin + 2] - tmL;
+  }
+  const double mu = B.mu, crx = B.crho[0], cry = B.crho[1];
+  const double dP = PR - PL, dQ = QR - QL, dT = TR - TL, dAy = AyR - AyL;
+
+  Tangents<TP> tg;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) { tg.Pt[c] = TP(0); tg.Pw[c] = TP(0); tg.Yr[c] = TP(0); }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) { tg.Qp[c] = TP(0); tg.Qv[c] = TP(0); tg.Yp[c] = TP(0); }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) tg.Yd[c] = TP(0);
+  tg.Pt[0] = TP(1); tg.Pw[1] = TP(1);
+  tg.Qp[0] = TP(1); tg.Qv[1] = TP(1);
+
+  const double h = 1.0 / nsub;
+  const TP hP = TP(h), sdP = TP(sd);
+  double th = th0, om = om0, py = py0, vy = vy0, Yom = 0.0;
+
+  for (int i = 0; i < nsub; ++i) {
+    // ---- state stages (FP64) ----
+    TP cw[4], swL[4], sath[4], fc[4], fs[4], oms[4], wdt[4], tau[4];
+    TP gr[4], gp[4], vys[4], ays[4], dl0[4], dl1[4], dl2[4];
+    double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const double cj = rk_c(j), wj = rk_w(j);
+      const double tj = (i + cj) * h;
+      const double ths = (j == 0) ? th : fma(cj * h, kth, th);
+      const double ws = (j == 0) ? om : fma(cj * h, kom, om);
+      double sn, cs;
+      sincos(ths, &sn, &cs);
+      const double P = fma(tj, dP, PL), Q = fma(tj, dQ, QL), T = fma(tj, dT, TL);
+      const double wdot = fma(cs, P, fma(-sn, Q, T));
+      kth = sd * ws;
+      kom = sd * wdot;
+      ath_ = fma(wj, kth, ath_);
+      aom_ = fma(wj, kom, aom_);
+      cw[j] = TP(cs);
+      swL[j] = TP(sn);
+      sath[j] = TP(-sd * fma(sn, P, cs * Q));  // s * d(omega')/d(theta)
+      oms[j] = TP(ws);
+      wdt[j] = TP(wdot);
+      tau[j] = TP(tj);
+      if (foot) {
+        const double pys = (j == 0) ? py : fma(cj * h, kpy, py);
+        const double vs = (j == 0) ? vy : fma(cj * h, kvy, vy);
+        const double ay = fma(tj, dAy, AyL) - g;
+        kpy = sd * vs;
+        kvy = sd * ay;
+        apy = fma(wj, kpy, apy);
+        avy = fma(wj, kvy, avy);
+        const double rx = cs * crx - sn * cry;
+        const double ry = sn * crx + cs * cry;
+        const double ln = fma(tj, lnD, lnL), ltp = fma(tj, tpD, tpL), ltm = fma(tj, tmD, tmL);
+        double H1, D1, H2, D2, H3, D3, H4, D4, H5, D5;
+        huber(-ln, H1, D1);
+        huber(-ltp, H2, D2);
+        huber(-ltm, H3, D3);
+        huber(-(pys + ry), H4, D4);
+        huber(ltp + ltm - mu * ln, H5, D5);
+        Yom = fma(h * wj, H1 + H2 + H3 + H4 + H5, Yom);
+        gp[j] = TP(-sd * D4);       // s dOmega/dp_y
+        gr[j] = TP(-sd * D4 * rx);  // s dOmega/dtheta
+        vys[j] = TP(vs);
+        ays[j] = TP(ay);
+        dl0[j] = TP(sd * (-D1 - mu * D5));
+        dl1[j] = TP(sd * (-D2 + D5));
+        dl2[j] = TP(sd * (-D3 + D5));
+      }
+    }
+    th = fma(h, ath_, th);
+    om = fma(h, aom_, om);
+    if (foot) { py = fma(h, apy, py); vy = fma(h, avy, vy); }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      fc[j] = sdP * cw[j];
+      fs[j] = -sdP * swL[j];
+    }
+
+    // ---- rotation tangents: 9 columns, 4 stages each ----
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const TP T0 = tg.Pt[c], W0 = tg.Pw[c];
+      TP kT = TP(0), kW = TP(0), aT = TP(0), aW = TP(0), ya = TP(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const TP cjh = TP(rk_c(j) * h), wj = TP(rk_w(j));
+        const TP Ts = (j == 0) ? T0 : T0 + cjh * kT;
+        const TP Ws = (j == 0) ? W0 : W0 + cjh * kW;
+        const TP wl = TP(1) - tau[j], wr = tau[j];
+        TP fT = TP(0), fW = TP(0);
+        if (c == 2) { fT = oms[j]; fW = wdt[j]; }
+        else if (c == 3) fW = fc[j] * wl;
+        else if (c == 4) fW = fs[j] * wl;
+        else if (c == 5) fW = sdP * wl;
+        else if (c == 6) fW = fc[j] * wr;
+        else if (c == 7) fW = fs[j] * wr;
+        else if (c == 8) fW = sdP * wr;
+        kT = sdP * Ws + fT;
+        kW = sath[j] * Ts + fW;
+        aT += wj * kT;
+        aW += wj * kW;
+        if (foot) ya += wj * gr[j] * Ts;
+      }
+      tg.Pt[c] = T0 + hP * aT;
+      tg.Pw[c] = W0 + hP * aW;
+      if (foot) tg.Yr[c] += hP * ya;
+    }
+
+    // ---- foot: p_y channel tangents and the penalty row ----
+    if (foot) {
+      TP y0 = TP(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) y0 += TP(rk_w(j)) * gp[j];
+      tg.Yp[0] += hP * y0;  // p_y0 column: stage tangent of p_y is 1
+#pragma unroll
+      for (int c = 1; c < 5; ++c) {
+        const TP P0 = tg.Qp[c], V0 = tg.Qv[c];
+        TP kP = TP(0), kV = TP(0), aP = TP(0), aV = TP(0), ya = TP(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const TP cjh = TP(rk_c(j) * h), wj = TP(rk_w(j));
+          const TP Ps = (j == 0) ? P0 : P0 + cjh * kP;
+          const TP Vs = (j == 0) ? V0 : V0 + cjh * kV;
+          TP fP = TP(0), fV = TP(0);
+          if (c == 2) { fP = vys[j]; fV = ays[j]; }
+          else if (c == 3) fV = sdP * (TP(1) - tau[j]);
+          else if (c == 4) fV = sdP * tau[j];
+          kP = sdP * Vs + fP;
+          kV = fV;
+          aP += wj * kP;
+          aV += wj * kV;
+          ya += wj * gp[j] * Ps;
+        }
+        tg.Qp[c] = P0 + hP * aP;
+        tg.Qv[c] = V0 + hP * aV;
+        tg.Yp[c] += hP * ya;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const TP hw = hP * TP(rk_w(j));
+        const TP wl = TP(1) - tau[j], wr = tau[j];
+        tg.Yd[0] += hw * dl0[j] * wl; tg.Yd[3] += hw * dl0[j] * wr;
+        tg.Yd[1] += hw * dl1[j] * wl; tg.Yd[4] += hw * dl1[j] * wr;
+        tg.Yd[2] += hw * dl2[j] * wl; tg.Yd[5] += hw * dl2[j] * wr;
+      }
+    }
+  }
+
+  // ------------------------------------------------------------ outputs ---
+  const TP one = TP(1), zero = TP(0);
+  const TP sdT = TP(sd), s2_3 = TP(sd * sd / 3.0), s2_6 = TP(sd * sd / 6.0), s_2 = TP(0.5 * sd);
+  // A: zero this link's rows, then the structural entries
+  TP* a1 = A + (size_t)rpx * nxt;
+  TP* a2 = A + (size_t)rvx * nxt;
+  for (int c = 0; c < 3 * nxt; ++c) { a1[c] = zero; a2[c] = zero; }
+  A[(size_t)rpx * nxt + rpx] = one; A[(size_t)rpx * nxt + rvx] = sdT;
+  A[(size_t)rpy * nxt + rpy] = one; A[(size_t)rpy * nxt + rvy] = sdT;
+  A[(size_t)rth * nxt + rth] = tg.Pt[0]; A[(size_t)rth * nxt + rom] = tg.Pt[1];
+  A[(size_t)rvx * nxt + rvx] = one;
+  A[(size_t)rvy * nxt + rvy] = one;
+  A[(size_t)rom * nxt + rth] = tg.Pw[0]; A[(size_t)rom * nxt + rom] = tg.Pw[1];
+  // S
+  const double Spx = vx0 + 2.0 * sd * ax3, Spy = vy0 + 2.0 * sd * ay3;
+  S[rpx] = TP(Spx); S[rvx] = TP(axm);
+  S[rpy] = TP(Spy); S[rvy] = TP(aym);
+  S[rth] = tg.Pt[2]; S[rom] = tg.Pw[2];
+  // B-, B+
+  if (nu > 0) {
+    TP* m1 = Bm + (size_t)rpx * nu; TP* m2 = Bm + (size_t)rvx * nu;
+    TP* p1 = Bp + (size_t)rpx * nu; TP* p2 = Bp + (size_t)rvx * nu;
+    for (int c = 0; c < 3 * nu; ++c) { m1[c] = zero; m2[c] = zero; p1[c] = zero; p2[c] = zero; }
+    for (int i = 0; i < nin; ++i) {
+      const int q = B.idx[i];
+      const TP ax = TP(B.ax[i]), ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
+      Bm[(size_t)rpx * nu + q] = ax * s2_3; Bp[(size_t)rpx * nu + q] = ax * s2_6;
+      Bm[(size_t)rvx * nu + q] = ax * s_2;  Bp[(size_t)rvx * nu + q] = ax * s_2;
+      Bm[(size_t)rpy * nu + q] = ay * s2_3; Bp[(size_t)rpy * nu + q] = ay * s2_6;
+      Bm[(size_t)rvy * nu + q] = ay * s_2;  Bp[(size_t)rvy * nu + q] = ay * s_2;
+      Bm[(size_t)rth * nu + q] = pc * tg.Pt[3] + qc * tg.Pt[4] + tc * tg.Pt[5];
+      Bp[(size_t)rth * nu + q] = pc * tg.Pt[6] + qc * tg.Pt[7] + tc * tg.Pt[8];
+      Bm[(size_t)rom * nu + q] = pc * tg.Pw[3] + qc * tg.Pw[4] + tc * tg.Pw[5];
+      Bp[(size_t)rom * nu + q] = pc * tg.Pw[6] + qc * tg.Pw[7] + tc * tg.Pw[8];
+    }
+  }
+  // defect (Eq. (17b))
+  defect[rpx] = px1 - xk1[rpx]; defect[rpy] = py1 - xk1[rpy]; defect[rth] = th - xk1[rth];
+  defect[rvx] = vx1 - xk1[rvx]; defect[rvy] = vy1 - xk1[rvy]; defect[rom] = om - xk1[rom];
+  double chk = px1 + py1 + th + vx1 + vy1 + om + Spx + Spy;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) chk += double(tg.Pt[c]) + double(tg.Pw[c]);
+
+  int ry_ = -1;
+  double y1 = 0.0;
+  if (foot) {
+    ry_ = 6 * nb + B.contact;
+    const double y0 = xk[ry_];
+    y1 = y0 + sd * Yom;
+    pen[B.contact] = sd * Yom;
+    defect[ry_] = y1 - xk1[ry_];
+    TP* ay_ = A + (size_t)ry_ * nxt;
+    for (int c = 0; c < nxt; ++c) ay_[c] = zero;
+    ay_[rpy] = tg.Yp[0]; ay_[rvy] = tg.Yp[1];
+    ay_[rth] = tg.Yr[0]; ay_[rom] = tg.Yr[1];
+    ay_[ry_] = one;
+    S[ry_] = TP(Yom) + tg.Yr[2] + tg.Yp[2];
+    if (nu > 0) {
+      TP* bm = Bm + (size_t)ry_ * nu;
+      TP* bp = Bp + (size_t)ry_ * nu;
+      for (int c = 0; c < nu; ++c) { bm[c] = zero; bp[c] = zero; }
+      for (int i = 0; i < nin; ++i) {
+        const int q = B.idx[i];
+        const TP ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
+        TP vm = pc * tg.Yr[3] + qc * tg.Yr[4] + tc * tg.Yr[5] + ay * tg.Yp[3];
+        TP vp = pc * tg.Yr[6] + qc * tg.Yr[7] + tc * tg.Yr[8] + ay * tg.Yp[4];
+        const int d = q - cin;
+        if (d >= 0 && d < 3) { vm += tg.Yd[d]; vp += tg.Yd[3 + d]; }
+        bm[q] = vm;
+        bp[q] = vp;
+      }
+    }
+    chk += y1 + double(S[ry_]);
+  }
+  if (!finite_d(chk)) atomicOr(status, ST_NONFINITE);
+
+  // optional affine term z = x~(1) - A x~_k - B- u_L - B+ u_R - S s (with the returned blocks)
+  if (z) {
+    const int rows[7] = {rpx, rpy, rth, rvx, rvy, rom, ry_};
+    const double x1v[7] = {px1, py1, th, vx1, vy1, om, y1};
+    const int nr = foot ? 7 : 6;
+    for (int t = 0; t < nr; ++t) {
+      const int r = rows[t];
+      double acc = x1v[t] - double(S[r]) * sd;
+      // A's nonzeros in this row lie in this link's columns (and y_r for the y row)
+      const int cols[7] = {rpx, rpy, rth, rvx, rvy, rom, ry_};
+      for (int u = 0; u < nr; ++u) acc -= double(A[(size_t)r * nxt + cols[u]]) * xk[cols[u]];
+      for (int i = 0; i < nin; ++i) {
+        const int q = B.idx[i];
+        acc -= double(Bm[(size_t)r * nu + q]) * uL[q] + double(Bp[(size_t)r * nu + q]) * uR[q];
+      }
+      z[r] = acc;
+    }
+  }
+}
+
+}  // namespace ciscvx

@@ -194,15 +194,31 @@ def gait_pose(robot: Robot, phase, torso_x):
     return q
 
 
+_POSE_CACHE: dict = {}
+
+
+def _gait_poses(robot: Robot, N):
+    """gait_pose at phases 2 pi k / N, k = 0..N, with the torso at x = 0 (cached)."""
+    key = (robot.name, robot.mass.tobytes(), robot.length.tobytes(), N)
+    if key not in _POSE_CACHE:
+        _POSE_CACHE[key] = np.stack([gait_pose(robot, 2.0 * np.pi * k / max(N, 1), 0.0)
+                                     for k in range(N + 1)])
+    return _POSE_CACHE[key]
+
+
 def node_states(robot: Robot, N, s, noise_q, noise_v, speed=1.0):
-    """Nominal node poses (gait, zero velocity, y = 0) plus the given noise."""
-    X = np.zeros((N + 1, robot.nxt))
-    t = np.concatenate([[0.0], np.cumsum(s)])
+    """Nominal node poses (gait, zero velocity, y = 0) plus the given noise.
+    The torso advances along x at `speed` times the dilated time t_k = sum s;
+    moving the torso translates every link rigidly, so the cached poses are
+    shifted in x."""
     nb = robot.nb
-    for k in range(N + 1):
-        q = gait_pose(robot, 2.0 * np.pi * k / max(N, 1), speed * t[k] if robot.torso_horizontal else 0.0)
-        X[k, : 3 * nb] = q.reshape(-1) + noise_q[k]
-        X[k, 3 * nb: 6 * nb] = noise_v[k]
+    q = _gait_poses(robot, N).copy()  # [N+1, nb, 3]
+    if robot.torso_horizontal:
+        t = np.concatenate([[0.0], np.cumsum(s)])
+        q[:, :, 0] += speed * t[:, None]
+    X = np.zeros((N + 1, robot.nxt))
+    X[:, : 3 * nb] = q.reshape(N + 1, -1) + noise_q
+    X[:, 3 * nb: 6 * nb] = noise_v
     return X
 
 

@@ -1,0 +1,231 @@
+"""GPU parity of the batched heterogeneous form (ciscvx_batch_*) against the oracle.
+
+Small mixed batches are checked instance by instance in full under every launch
+shape (persistent / one warp per item, cost / instance order, with and without
+the CUDA graph) and after autotuning.  The full-size workloads — 1024 mixed
+instances and the 4096 x 400 x 20 sweep — are checked on sampled instances and
+intervals the oracle computes one by one.  Tolerances as in the single-instance
+tests.
+"""
+import numpy as np
+import pytest
+
+from _util import TOL_FP32_PHI, TOL_FP64, block_err
+from paper_2604_09993_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TUNES = [
+    None,
+    {"warps_per_cta": 4, "ctas_per_sm": 0, "lpt_order": 1, "use_graph": 0},
+    {"warps_per_cta": 1, "ctas_per_sm": 8, "lpt_order": 0, "use_graph": 1},
+    {"warps_per_cta": 8, "ctas_per_sm": 1, "lpt_order": 1, "use_graph": 0},
+]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import oracle
+    from paper_2604_09993_gb300 import api, build
+    build.build()
+    oracle.build()
+    api.load()
+    return torch, oracle, api
+
+
+def _small_mixed(seed=3, n=24):
+    rng = np.random.default_rng(seed)
+    robots = [synth.hopper(rng), synth.biped(rng), synth.cheetah7(rng)]
+    styles = [dict(q_noise=0.05, u_dist="uniform"), dict(q_noise=0.1, u_dist="normal"),
+              dict(q_noise=0.1, u_dist="normal")]
+    probs, midx = [], []
+    for i in range(n):
+        m = int(rng.integers(0, 3))
+        N = int(rng.integers(1, 71))
+        ns = int(rng.choice([1, 3, 5]))
+        probs.append(synth.draw_instance(robots[m], rng, N, ns, s_range=(0.05, 0.15),
+                                         with_cotangents=True, **styles[m]))
+        midx.append(m)
+    return robots, probs, midx
+
+
+def _packed(plan, probs, dev, torch, layout="node"):
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X = t(plan.pack([p.X for p in probs], "X"))
+    U = t(plan.pack([p.U if layout == "node" else p.U_interval() for p in probs], "U"))
+    s = t(plan.pack([p.s for p in probs], "s"))
+    w = t(plan.pack([p.w for p in probs], "defect"))
+    rho = t(plan.pack([p.rho for p in probs], "penalty"))
+    return X, U, s, w, rho
+
+
+def _check_instance(plan, out, i, p, ref, precision):
+    nxt, nu, nc, N = p.robot.nxt, p.robot.nu, p.robot.nc, p.N
+    shapes = {"A": ("A", (N, nxt, nxt)), "Bm": ("B", (N, nxt, nu)), "Bp": ("B", (N, nxt, nu)),
+              "S": ("S", (N, nxt)), "defect": ("defect", (N, nxt)), "penalty": ("penalty", (N, nc))}
+    tol_phi = TOL_FP64 if precision == "fp64" else TOL_FP32_PHI
+    for k, (okey, shape) in shapes.items():
+        got = plan.unpack(out[k], okey, i, shape)
+        tol = tol_phi if k in ("A", "Bm", "Bp", "S") else TOL_FP64
+        e = block_err(got, ref[k])
+        assert e <= tol, (i, k, e)
+
+
+@pytest.mark.parametrize("tune", TUNES)
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_small_mixed_batch_discretize(env, tune, precision):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    robots, probs, midx = _small_mixed()
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
+                         precision=precision, tune=tune)
+    X, U, s, _, _ = _packed(plan, probs, dev, torch)
+    out = plan.discretize(X, U, s)
+    out = plan.discretize(X, U, s, out=out)  # replay (graph path when enabled)
+    plan.sync_status()
+    host = {k: v.double().cpu().numpy() for k, v in out.items()}
+    for i, p in enumerate(probs):
+        ref = oracle.discretize(p.robot.as_dict(), p.X, p.U, p.s, p.n_sub)
+        _check_instance(plan, host, i, p, ref, precision)
+
+
+@pytest.mark.parametrize("layout", ["node", "interval"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32_phi", 1e-4)])
+def test_small_mixed_batch_vjp(env, layout, precision, tol):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    robots, probs, midx = _small_mixed(seed=5)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
+                         precision=precision, layout=layout)
+    X, U, s, w, rho = _packed(plan, probs, dev, torch, layout)
+    g = plan.discretize_vjp(X, U, s, w, rho)
+    plan.sync_status()
+    gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
+    for i, p in enumerate(probs):
+        Ui = p.U if layout == "node" else p.U_interval()
+        rX, rU, rs, rL = oracle.vjp(p.robot.as_dict(), p.X, Ui, p.s, p.w, p.rho, p.n_sub, layout=layout)
+        assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= tol, i
+        assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= tol, i
+        assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= tol, i
+        assert abs(L[i] - rL) <= tol * max(1.0, abs(rL)), i
+
+
+def test_autotune_keeps_results(env):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    robots, probs, midx = _small_mixed(seed=8, n=40)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
+                         precision="fp32_phi")
+    X, U, s, _, _ = _packed(plan, probs, dev, torch)
+    chosen = plan.autotune(X, U, s)
+    assert chosen["warps_per_cta"] in (1, 2, 4, 8) and chosen["ctas_per_sm"] >= 0
+    plan2 = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
+                          precision="fp32_phi")
+    assert plan2.autotune(X, U, s) == chosen  # cached per process
+    out = plan.discretize(X, U, s)
+    host = {k: v.double().cpu().numpy() for k, v in out.items()}
+    for i in (0, 7, 19, 39):
+        p = probs[i]
+        _check_instance(plan, host, i, p, oracle.discretize(p.robot.as_dict(), p.X, p.U, p.s, p.n_sub),
+                        "fp32_phi")
+
+
+def test_batch_errors(env):
+    torch, oracle, api = env
+    robots, probs, midx = _small_mixed(n=3)
+    models = [api.Model(r) for r in robots]
+    with pytest.raises(api.CiscvxError) as e:
+        api.BatchPlan(models, [0, 5, 1], [2, 2, 2], [1, 1, 1])
+    assert e.value.status == api.EINVAL
+    with pytest.raises(api.CiscvxError) as e:
+        api.BatchPlan(models, [0, 1, 2], [2, 0, 2], [1, 1, 1])
+    assert e.value.status == api.EINVAL
+    with pytest.raises(api.CiscvxError) as e:
+        api.BatchPlan(models, [0, 1, 2], [2, 2, 2], [1, 1, 1], precision="bf16_tc")
+    assert e.value.status == api.EUNSUPPORTED
+    plan = api.BatchPlan(models, [0, 1, 2], [2, 2, 2], [1, 65, 1])
+    dev = torch.device("cuda:0")
+    z = torch.zeros(1024, dtype=torch.float64, device=dev)
+    with pytest.raises(api.CiscvxError) as e:
+        plan.discretize_vjp(z, z, z, z, z)
+    assert e.value.status == api.EUNSUPPORTED
+
+
+def test_mixed_1024_sampled(env):
+    """1024 instances, hopper:biped:chain = 1:1:2, N ~ U{10..200}, n_sub in {4,8,16}, FP32 Phi."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    b = synth.mixed_batch(seed=0)
+    probs = [b.instance(i) for i in range(len(b))]
+    models = [api.Model(r) for r in b.robots]
+    plan = api.BatchPlan(models, b.model_idx, b.Ns, b.n_subs, precision="fp32_phi")
+    X, U, s, w, rho = _packed(plan, probs, dev, torch)
+    plan.autotune(X, U, s)
+    out = plan.discretize(X, U, s)
+    g = plan.discretize_vjp(X, U, s, w, rho)
+    plan.sync_status()
+    host = {k: v.double().cpu().numpy() for k, v in out.items()}
+    gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
+    rng = np.random.default_rng(1)
+    for i in sorted(rng.choice(len(b), 12, replace=False)):
+        p = probs[i]
+        R = p.robot.as_dict()
+        _check_instance(plan, host, i, p, oracle.discretize(R, p.X, p.U, p.s, p.n_sub), "fp32_phi")
+        rX, rU, rs, rL = oracle.vjp(R, p.X, p.U, p.s, p.w, p.rho, p.n_sub)
+        assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= 1e-4
+        assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
+        assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= 1e-4
+        assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
+
+
+def test_sweep_4096x400x20_sampled(env):
+    """The 4096-instance sweep at full size (FP32 Phi): sampled intervals checked one by one,
+    four instances' VJPs checked whole; a graph replay reproduces the outputs bit for bit."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    b = synth.cheetah_sweep(seed=0)
+    model = api.Model(b.robots[0])
+    plan = api.BatchPlan([model], b.model_idx, b.Ns, b.n_subs, precision="fp32_phi")
+    probs = [b.instance(i) for i in range(len(b))]
+    X, U, s, w, rho = _packed(plan, probs, dev, torch)
+    out = plan.discretize(X, U, s)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(2)
+    inst = sorted(rng.choice(len(b), 8, replace=False)) + [0, len(b) - 1]
+    R = b.robots[0].as_dict()
+    nxt, nu = b.robots[0].nxt, b.robots[0].nu
+    for i in inst:
+        p = probs[i]
+        o = plan.offsets[i]
+        for k in sorted(set(rng.choice(p.N, 6, replace=False).tolist() + [0, p.N - 1])):
+            x1, A, Bm, Bp, S = oracle.interval(R, p.n_sub, p.X[k], p.U[k], p.U[k + 1], p.s[k])
+            a0 = o["A"] + k * nxt * nxt
+            b0 = o["B"] + k * nxt * nu
+            v0 = o["S"] + k * nxt
+            assert block_err(out["A"][a0:a0 + nxt * nxt].double().cpu().numpy(), A.ravel()) <= TOL_FP32_PHI
+            assert block_err(out["Bm"][b0:b0 + nxt * nu].double().cpu().numpy(), Bm.ravel()) <= TOL_FP32_PHI
+            assert block_err(out["Bp"][b0:b0 + nxt * nu].double().cpu().numpy(), Bp.ravel()) <= TOL_FP32_PHI
+            assert block_err(out["S"][v0:v0 + nxt].double().cpu().numpy(), S) <= TOL_FP32_PHI
+            d = out["defect"][v0:v0 + nxt].cpu().numpy()
+            assert block_err(d, x1 - p.X[k + 1]) <= TOL_FP64
+    # replay reproduces bit for bit
+    d0 = out["defect"].clone()
+    a0 = out["A"][: 10 * nxt * nxt].clone()
+    plan.discretize(X, U, s, out=out)
+    torch.cuda.synchronize()
+    assert torch.equal(out["defect"], d0) and torch.equal(out["A"][: 10 * nxt * nxt], a0)
+    del out
+    g = plan.discretize_vjp(X, U, s, w, rho)
+    plan.sync_status()
+    gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
+    for i in (0, 1234, 4095):
+        p = probs[i]
+        rX, rU, rs, rL = oracle.vjp(R, p.X, p.U, p.s, p.w, p.rho, p.n_sub, threads=0)
+        assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= 1e-4
+        assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
+        assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= 1e-4
+        assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
