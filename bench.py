@@ -3,19 +3,20 @@
 
 One step = one pass of the whole hot path over one batch of synthetic input:
 the linearized discretization (A, B-, B+, S, defects, penalty increments) of
-every interval plus the adjoint VJP of L = sum w.defect + rho.penalty, with
-inputs resident in HBM.  value = intervals linearized (STM + VJP) per second.
+every interval of every instance plus the adjoint VJP of
+L = sum w.defect + rho.penalty, with inputs resident in HBM.
+value = intervals linearized (STM + VJP) per second.
+
+Default workload: 4096 instances of the 7-link chain, N = 400 intervals,
+20 RK4 substeps, s ~ U[0.01, 0.05], FP32 Phi with FP64 state (batched plan,
+persistent launch in a CUDA graph).  The plain FP64 GPU path runs the same
+workload as the comparator (`fp64_path`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
 Multi-GPU (torchrun, one rank per GPU): every rank processes its own batch
-(instances are independent, no collective on the data path) -> weak scaling;
+(instances are independent; no collective on the data path) -> weak scaling;
 value = total intervals over all ranks / max rank time.
-
-Also reported: the plain FP64 GPU path's throughput on the same workload, the
-FP64-pipe roofline of the dominant kernel (CUDA events on its stream), an
-end-to-end number through the public API with host buffers, the FP64 oracle
-on the host cores (cpu_baseline), and SM clocks sampled during the timed region.
 """
 from __future__ import annotations
 
@@ -28,8 +29,6 @@ import sys
 import tempfile
 import time
 
-import numpy as np
-
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -38,19 +37,22 @@ from paper_2604_09993_gb300 import synth  # noqa: E402
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
 # x 2 flop x 2.07 GHz (a microbenchmark measured 1.196 TFLOP/s at 1.99 GHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_BYTES = 126 * 2 ** 20
 
 WORKLOADS = {
-    # 7-link chain (HalfCheetah-shaped), N = 50, 10 RK4 substeps, one instance
-    "cheetah7-n50-sub10": dict(kind="single", make=lambda: synth.cheetah_n50(seed=0)),
+    "cheetah7-sweep-4096x400x20": dict(kind="batch", make=lambda n: synth.cheetah_sweep(seed=0, n_inst=n),
+                                       instances=4096),
+    "mixed-1024": dict(kind="batch", make=lambda n: synth.mixed_batch(seed=0, n_inst=n), instances=1024),
+    "cheetah7-n50-sub10": dict(kind="single", make=lambda n: synth.cheetah_n50(seed=0), instances=1),
 }
-DEFAULT_WORKLOAD = "cheetah7-n50-sub10"
+DEFAULT_WORKLOAD = "cheetah7-sweep-4096x400x20"
 
-# Executed FP64 flops per interval of the dominant kernel (ncu SASS counters
-# dfma*2 + dadd + dmul, per launch / intervals), see profiles/.
+# Executed FP64 flops per interval of each kernel (ncu SASS counters
+# 2*DFMA + DADD + DMUL of one launch / intervals of that launch), recorded in
+# profiles/; keyed by (robot, n_sub, kernel, precision).
 FLOPS_PER_INTERVAL = {
-    ("cheetah7-n50-sub10", "discretize", "fp32_phi"): 42_900,
-    ("cheetah7-n50-sub10", "discretize", "fp64"): 84_400,
-    ("cheetah7-n50-sub10", "vjp", "fp32_phi"): 73_300,
+    ("cheetah7", 20, "discretize", "fp32_phi"): 40_300,
+    ("cheetah7", 20, "vjp", "fp32_phi"): 45_400,
 }
 
 
@@ -62,12 +64,10 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms while active."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while active."""
 
     def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.path = None
+        self.index, self.proc, self.path = index, None, None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -103,80 +103,176 @@ class ClockSampler:
             os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda v: float(v) if v.replace(".", "", 1).isdigit() else None  # noqa: E731
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
 
 
 # ---------------------------------------------------------------------------
-# our implementation
+# workloads
 # ---------------------------------------------------------------------------
+class BatchWorkload:
+    """Instances packed for a batch plan; one plan per precision (autotuned)."""
+
+    def __init__(self, spec, n_inst, dev):
+        import torch
+        from paper_2604_09993_gb300 import api
+        self.api, self.torch, self.dev = api, torch, dev
+        self.batch = spec["make"](n_inst)
+        b = self.batch
+        self.models = [api.Model(r) for r in b.robots]
+        probs = [b.instance(i) for i in range(len(b))]
+        self.robot_name = b.robots[0].name if len(b.robots) == 1 else "mixed"
+        self.n_sub = int(b.n_subs[0]) if len(set(b.n_subs.tolist())) == 1 else None
+        self.intervals = int(b.Ns.sum())
+        self.plans = {}
+        p0 = self.plan("fp32_phi")
+        t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+        self.X = t(p0.pack([p.X for p in probs], "X"))
+        self.U = t(p0.pack([p.U for p in probs], "U"))
+        self.s = t(p0.pack([p.s for p in probs], "s"))
+        self.w = t(p0.pack([p.w for p in probs], "defect"))
+        self.rho = t(p0.pack([p.rho for p in probs], "penalty"))
+        del probs
+        self.out, self.gout, self.ws = {}, {}, None
+
+    def plan(self, prec):
+        if prec not in self.plans:
+            b = self.batch
+            self.plans[prec] = self.api.BatchPlan(self.models, b.model_idx, b.Ns, b.n_subs, precision=prec)
+        return self.plans[prec]
+
+    def prepare(self, prec):
+        pl = self.plan(prec)
+        if prec not in self.out:
+            self.out[prec] = pl.alloc_outputs(self.dev)
+            pl.autotune(self.X, self.U, self.s, out=self.out[prec])
+        need = pl.vjp_workspace_size()
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = self.torch.empty(need, dtype=self.torch.uint8, device=self.dev)
+
+    def free(self, prec):
+        self.out.pop(prec, None)
+        self.gout.pop(prec, None)
+        self.torch.cuda.empty_cache()
+
+    def disc(self, prec):
+        self.plan(prec).discretize(self.X, self.U, self.s, out=self.out[prec])
+
+    def vjp(self, prec):
+        pl = self.plan(prec)
+        self.gout[prec] = pl.discretize_vjp(self.X, self.U, self.s, self.w, self.rho, workspace=self.ws,
+                                            out=self.gout.get(prec))
+
+    def step(self, prec):
+        self.disc(prec)
+        self.vjp(prec)
+
+    def check_status(self):
+        for pl in self.plans.values():
+            pl.sync_status()
+
+    def tune(self, prec):
+        return self.plan(prec).tune()
+
+    # end to end through the public API with host buffers
+    def e2e_setup(self, prec):
+        torch = self.torch
+        self.host_in = {k: getattr(self, k).cpu().pin_memory() for k in ("X", "U", "s", "w", "rho")}
+        self.dev_in = {k: torch.empty_like(getattr(self, k)) for k in ("X", "U", "s", "w", "rho")}
+        outs = dict(self.out[prec])
+        outs.update({k: v for k, v in self.gout[prec].items() if v is not None})
+        self.host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in outs.items()}
+        h2d = sum(v.numel() * v.element_size() for v in self.host_in.values())
+        d2h = sum(v.numel() * v.element_size() for v in self.host_out.values())
+        return h2d, d2h
+
+    def e2e_step(self, prec):
+        for k, v in self.host_in.items():
+            self.dev_in[k].copy_(v, non_blocking=True)
+        d = self.dev_in
+        pl = self.plan(prec)
+        pl.discretize(d["X"], d["U"], d["s"], out=self.out[prec])
+        g = pl.discretize_vjp(d["X"], d["U"], d["s"], d["w"], d["rho"], workspace=self.ws,
+                              out=self.gout[prec])
+        for k, v in self.host_out.items():
+            src = self.out[prec][k] if k in self.out[prec] else g[k]
+            v.copy_(src, non_blocking=True)
+
+    def e2e_free(self):
+        self.host_in = self.host_out = self.dev_in = None
+
+
 class SingleWorkload:
     """One instance through ciscvx_discretize + ciscvx_discretize_vjp."""
 
-    def __init__(self, prob, dev):
+    def __init__(self, spec, n_inst, dev):
         import torch
         from paper_2604_09993_gb300 import api
-        self.api, self.torch, self.p = api, torch, prob
+        self.api, self.torch, self.dev = api, torch, dev
+        prob = spec["make"](1)
         self.model = api.Model(prob.robot)
         t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
         self.X, self.U, self.s, self.w, self.rho = (t(prob.X), t(prob.U), t(prob.s), t(prob.w), t(prob.rho))
-        self.intervals = prob.N
-        self.n_sub = prob.n_sub
-        self.out = {}
+        self.intervals, self.n_sub, self.robot_name = prob.N, prob.n_sub, prob.robot.name
+        self.out, self.gout = {}, {}
         self.ws = torch.empty(api.workspace_size(self.model, api.OP_VJP, prob.N), dtype=torch.uint8, device=dev)
 
-    def disc(self, precision):
-        if precision not in self.out:
-            self.out[precision] = self.api.discretize(self.model, self.X, self.U, self.s, self.n_sub, precision)
-        else:
-            self.api.discretize(self.model, self.X, self.U, self.s, self.n_sub, precision, out=self.out[precision])
+    def prepare(self, prec):
+        if prec not in self.out:
+            self.out[prec] = self.api.discretize(self.model, self.X, self.U, self.s, self.n_sub, prec)
+            self.vjp(prec)
 
-    def vjp(self, precision):
-        self.api.discretize_vjp(self.model, self.X, self.U, self.s, self.w, self.rho, self.n_sub, precision,
-                                workspace=self.ws)
+    def free(self, prec):
+        pass
 
-    def step(self, precision):
-        self.disc(precision)
-        self.vjp(precision)
+    def disc(self, prec):
+        self.api.discretize(self.model, self.X, self.U, self.s, self.n_sub, prec, out=self.out[prec])
 
-    def e2e_step(self, host, precision):
-        """Public API with host buffers: H2D of the inputs, compute, D2H of every output."""
-        torch = self.torch
-        X = host["X"].to(self.X.device, non_blocking=True)
-        U = host["U"].to(self.X.device, non_blocking=True)
-        s = host["s"].to(self.X.device, non_blocking=True)
-        w = host["w"].to(self.X.device, non_blocking=True)
-        rho = host["rho"].to(self.X.device, non_blocking=True)
-        out = self.api.discretize(self.model, X, U, s, self.n_sub, precision)
-        gX, gU, gs, L = self.api.discretize_vjp(self.model, X, U, s, w, rho, self.n_sub, precision, workspace=self.ws)
-        res = dict(out, gX=gX, gU=gU, gs=gs, L=L)
-        for k, v in res.items():
-            host["out_" + k].copy_(v, non_blocking=True)
-        return res
+    def vjp(self, prec):
+        gX, gU, gs, L = self.api.discretize_vjp(self.model, self.X, self.U, self.s, self.w, self.rho,
+                                                self.n_sub, prec, workspace=self.ws)
+        self.gout[prec] = {"gX": gX, "gU": gU, "gs": gs, "L": L}
 
-    def host_buffers(self):
-        torch = self.torch
-        h = {}
-        for k in ("X", "U", "s", "w", "rho"):
-            h[k] = getattr(self, k).cpu().pin_memory()
-        return h
-
-    def alloc_host_outputs(self, host, res):
-        for k, v in res.items():
-            host["out_" + k] = torch_empty_pinned(self.torch, v)
+    def step(self, prec):
+        self.disc(prec)
+        self.vjp(prec)
 
     def check_status(self):
         self.api.sync_status(self.model)
 
+    def tune(self, prec):
+        return None
 
-def torch_empty_pinned(torch, like):
-    return torch.empty(like.shape, dtype=like.dtype, pin_memory=True)
+    def e2e_setup(self, prec):
+        torch = self.torch
+        self.host_in = {k: getattr(self, k).cpu().pin_memory() for k in ("X", "U", "s", "w", "rho")}
+        outs = dict(self.out[prec])
+        outs.update(self.gout[prec])
+        self.host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in outs.items()}
+        return (sum(v.numel() * v.element_size() for v in self.host_in.values()),
+                sum(v.numel() * v.element_size() for v in self.host_out.values()))
+
+    def e2e_step(self, prec):
+        d = {k: v.to(self.dev, non_blocking=True) for k, v in self.host_in.items()}
+        out = self.api.discretize(self.model, d["X"], d["U"], d["s"], self.n_sub, prec)
+        gX, gU, gs, L = self.api.discretize_vjp(self.model, d["X"], d["U"], d["s"], d["w"], d["rho"],
+                                                self.n_sub, prec, workspace=self.ws)
+        res = dict(out, gX=gX, gU=gU, gs=gs, L=L)
+        for k, v in self.host_out.items():
+            v.copy_(res[k], non_blocking=True)
+
+    def e2e_free(self):
+        self.host_in = self.host_out = None
 
 
+# ---------------------------------------------------------------------------
+# timing
+# ---------------------------------------------------------------------------
 def time_steps(torch, fn, steps, warmup, stream):
     for _ in range(warmup):
         fn()
@@ -192,7 +288,7 @@ def time_steps(torch, fn, steps, warmup, stream):
 
 
 def kernel_time(torch, fn, reps, stream):
-    """Average duration of one call of fn (a single kernel launch sequence) with events on its stream."""
+    """Mean duration of fn's launches with CUDA events on the launching stream."""
     ts = []
     for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -205,28 +301,32 @@ def kernel_time(torch, fn, reps, stream):
     return statistics.mean(ts)
 
 
-def cpu_baseline(name, seconds_budget=15.0):
-    """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
+def cpu_baseline(name, budget_s=12.0):
+    """The FP64 oracle, as it stands, on all host cores over a bounded sample of the workload."""
     import oracle
     oracle.build()
     spec = WORKLOADS[name]
-    prob = spec["make"]()
     cores = os.cpu_count() or 1
-    R = prob.robot.as_dict()
     t0 = time.perf_counter()
-    n_done = 0
-    reps = 0
-    while True:
-        oracle.discretize(R, prob.X, prob.U, prob.s, prob.n_sub, threads=cores)
-        oracle.vjp(R, prob.X, prob.U, prob.s, prob.w, prob.rho, prob.n_sub, threads=cores)
-        n_done += prob.N
-        reps += 1
-        if time.perf_counter() - t0 > min(seconds_budget, 10.0) or reps >= 200:
+    n_int, n_inst = 0, 0
+    if spec["kind"] == "single":
+        p = spec["make"](1)
+        it = (p for _ in range(100000))
+    else:
+        b = spec["make"](spec["instances"])
+        it = (b.instance(i) for i in range(len(b)))
+    for p in it:
+        R = p.robot.as_dict()
+        oracle.discretize(R, p.X, p.U, p.s, p.n_sub, threads=cores)
+        oracle.vjp(R, p.X, p.U, p.s, p.w, p.rho, p.n_sub, threads=cores)
+        n_int += p.N
+        n_inst += 1
+        if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": n_done / dt, "unit": "intervals/s", "cores": cores, "kind": "oracle",
-            "sample": f"{reps} passes of the full {prob.N}-interval instance (STM by dual-number IND + "
-                      f"Phi-contracted VJP), {cores} threads"}
+    return {"value": n_int / dt, "unit": "intervals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_inst} instance pass(es) of the workload ({n_int} intervals): dual-number "
+                      f"IND linearization + Phi-contracted VJP, FP64, {cores} threads"}
 
 
 def run_ours(args):
@@ -242,7 +342,8 @@ def run_ours(args):
     build.build()
     api.load()
     spec = WORKLOADS[args.workload]
-    wl = SingleWorkload(spec["make"](), dev)
+    n_inst = args.instances or spec["instances"]
+    wl = (BatchWorkload if spec["kind"] == "batch" else SingleWorkload)(spec, n_inst, dev)
     stream = torch.cuda.current_stream()
     prec = args.precision
 
@@ -252,67 +353,86 @@ def run_ours(args):
             tdist.barrier()
         torch.cuda.synchronize()
 
-    # plain FP64 comparator and the headline path
-    barrier()
-    t64 = time_steps(torch, lambda: wl.step("fp64"), args.steps, args.warmup, stream)
+    def max_over_ranks(vals):
+        if world == 1:
+            return vals
+        import torch.distributed as tdist
+        tt = torch.tensor(vals, device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        return tt.tolist()
+
+    # plain FP64 GPU path (comparator)
+    t64 = kd64 = None
+    if not args.no_fp64 and prec != "fp64":
+        wl.prepare("fp64")
+        barrier()
+        t64 = time_steps(torch, lambda: wl.step("fp64"), args.steps, args.warmup, stream)
+        barrier()
+        kd64 = kernel_time(torch, lambda: wl.disc("fp64"), 3, stream)
+        t64, kd64 = max_over_ranks([t64, kd64])
+        wl.free("fp64")
+    # headline path
+    wl.prepare(prec)
+    wl.step(prec)
     barrier()
     with ClockSampler(lrank) as cs:
         barrier()
         t = time_steps(torch, lambda: wl.step(prec), args.steps, args.warmup, stream)
         barrier()
     clocks = cs.summary()
+    kd = kernel_time(torch, lambda: wl.disc(prec), 5, stream)
+    kv = kernel_time(torch, lambda: wl.vjp(prec), 5, stream)
     wl.check_status()
-    if world > 1:
-        import torch.distributed as tdist
-        tt = torch.tensor([t, t64], device=dev)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        t, t64 = tt.tolist()
+    t, kd, kv = max_over_ranks([t, kd, kv])
     units = wl.intervals * world
     value = units * args.steps / t
-    value64 = units * args.steps / t64
 
-    # dominant kernel: time the discretize and the VJP launches separately
-    kd = kernel_time(torch, lambda: wl.disc(prec), 10, stream)
-    kv = kernel_time(torch, lambda: wl.vjp(prec), 10, stream)
     dom, kt = ("discretize", kd) if kd >= kv else ("vjp", kv)
-    fpi = FLOPS_PER_INTERVAL.get((args.workload, dom, prec))
-    roof = {"bound": "alu", "kernel": f"k_{dom}<{'float' if prec == 'fp32_phi' else 'double'}>",
+    kname = {"discretize": "k_batch_disc" if spec["kind"] == "batch" else "k_discretize",
+             "vjp": "k_batch_vjp" if spec["kind"] == "batch" else "k_vjp"}[dom]
+    fpi = FLOPS_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec))
+    roof = {"bound": "alu", "kernel": f"{kname}<{'float' if prec == 'fp32_phi' else 'double'}>",
             "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4), "peak_source": "derived FP64 pipe",
-            "launch_ms": kt * 1e3, "traffic": None}
+            "launch_ms": kt * 1e3, "discretize_ms": kd * 1e3, "vjp_ms": kv * 1e3, "traffic": None}
     if fpi:
         ach = fpi * wl.intervals / kt / 1e12
         roof.update(achieved=ach, frac=ach / FP64_PEAK_TFLOPS)
     else:
         roof.update(achieved=None, frac=None)
 
-    # end to end through the public API with host buffers
-    host = wl.host_buffers()
-    out = api.discretize(wl.model, wl.X, wl.U, wl.s, wl.n_sub, prec)
-    gX, gU, gs, L = api.discretize_vjp(wl.model, wl.X, wl.U, wl.s, wl.w, wl.rho, wl.n_sub, prec, workspace=wl.ws)
-    res0 = dict(out, gX=gX, gU=gU, gs=gs, L=L)
-    wl.alloc_host_outputs(host, res0)
-    te = time_steps(torch, lambda: wl.e2e_step(host, prec), args.steps, min(args.warmup, 3), stream)
-    h2d = sum(host[k].numel() * host[k].element_size() for k in ("X", "U", "s", "w", "rho"))
-    d2h = sum(v.numel() * v.element_size() for v in res0.values())
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d, d2h = wl.e2e_setup(prec)
+        ke = max(1, args.steps // 2)
+        te = time_steps(torch, lambda: wl.e2e_step(prec), ke, 1, stream)
+        te, = max_over_ranks([te])
+        e2e = {"value": units * ke / te, "unit": "intervals/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+        wl.e2e_free()
 
     if rank != 0:
         return
+    in_bytes = sum(getattr(wl, k).numel() * 8 for k in ("X", "U", "s", "w", "rho"))
     line = {
         "metric": "linearized intervals/s (STM + adjoint VJP)",
         "value": value, "unit": "intervals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 state / f32 Phi" if prec == "fp32_phi" else "f64",
-        "data": "synthetic (seeded robots, no dataset)",
-        "config": {"workload": args.workload, "precision": prec, "instances": 1,
+        "dtype": "f64 state + f32 Phi/adjoint" if prec == "fp32_phi" else "f64",
+        "data": "synthetic (seeded robots; no dataset)",
+        "config": {"workload": args.workload, "precision": prec, "instances_per_gpu": n_inst,
                    "intervals_per_gpu": wl.intervals, "n_sub": wl.n_sub,
-                   "l2": "inputs+outputs below L2: cold-cache not enforced"},
-        "fp64_path": {"value": value64, "ms_per_step": t64 / args.steps * 1e3,
-                      "speedup": value / value64},
-        "gpu_launches": args.steps * (1 + 3),
+                   "l2": ("inputs larger than L2" if in_bytes > L2_BYTES else "inputs below L2 (not flushed)"),
+                   "tune": wl.tune(prec)},
+        "fp64_path": None if t64 is None else {
+            "value": units * args.steps / t64, "ms_per_step": t64 / args.steps * 1e3,
+            "discretize_ms": kd64 * 1e3, "headline_speedup": t64 / t},
+        # launches of this library per timed step: batch = graph (memset + disc) + vjp + finish;
+        # single = disc + vjp + gU + gs + L
+        "gpu_launches": args.steps * (4 if spec["kind"] == "batch" else 5),
         "roofline": roof,
-        "e2e": {"value": units * args.steps / te, "unit": "intervals/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -321,22 +441,19 @@ def run_ours(args):
 
 
 def run_reference(args):
+    """The oracle as the reference arm, timed on the host cores (bounded sample per step)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cb = cpu_baseline(args.workload)
-    per_step = []
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, seconds_budget=2.0)
-    for _ in range(args.steps):
-        per_step.append(cpu_baseline(args.workload, seconds_budget=2.0)["value"])
-    v = statistics.mean(per_step)
+        cpu_baseline(args.workload, budget_s=1.0)
+    vals = [cpu_baseline(args.workload, budget_s=3.0) for _ in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
     line = {"impl": "reference", "metric": "linearized intervals/s (STM + adjoint VJP)", "value": v,
             "unit": "intervals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded robots, no dataset)",
-            "config": {"workload": args.workload},
-            "cpu_baseline": dict(cb, value=v),
+            "data": "synthetic (seeded robots; no dataset)", "config": {"workload": args.workload},
+            "cpu_baseline": dict(vals[-1], value=v),
             "e2e": {"value": v, "unit": "intervals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -344,12 +461,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--instances", type=int, default=0, help="override the workload's instance count")
     ap.add_argument("--precision", default="fp32_phi", choices=["fp64", "fp32_phi"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -74,6 +74,69 @@ __device__ __forceinline__ void huber(double z, double& H, double& D) {
   D = p / r;
 }
 
+// Value only: h(z) in FP64 (the penalty state needs it to FP64 accuracy).
+// Lanes with z <= 0 skip the square root and the division.
+__device__ __forceinline__ double huber_value(double z) {
+  double H = 0.0;
+  if (z > 0.0) {
+    const double r = sqrt(fma(z, z, 1.0));
+    H = (z * z) / (1.0 + r);
+  }
+  return H;
+}
+
+// Value in FP32 (adjoint weights only; the penalty state itself uses the FP64 value).
+__device__ __forceinline__ float huber_value(float z) {
+  const float p = fmaxf(z, 0.0f);
+  return (p * p) / (1.0f + sqrtf(fmaf(p, p, 1.0f)));
+}
+
+// Derivative only, in the tangent precision: h'(z) = p / sqrt(1 + p^2).
+__device__ __forceinline__ float huber_slope(float z) {
+  const float p = fmaxf(z, 0.0f);
+  return p * rsqrtf(fmaf(p, p, 1.0f));
+}
+__device__ __forceinline__ double huber_slope(double z) {
+  const double p = fmax(z, 0.0);
+  return p / sqrt(fma(p, p, 1.0));
+}
+
+// (sin, cos) of theta + d from (sin theta, cos theta) by angle addition, with
+// sin d and cos d from their Taylor series (through d^11 and d^12).  For
+// |d| <= 0.2 the truncation error is below 2e-19, far under FP64 rounding of
+// the result.  Returns false (outputs untouched) when |d| > 0.2.
+constexpr double ROT_DMAX = 0.2;
+__device__ __forceinline__ bool rotate_small(double s0, double c0, double d, double& s,
+                                             double& c) {
+  if (!(fabs(d) <= ROT_DMAX)) return false;
+  const double x = d * d;
+  // sin d = d (1 - x/3! + x^2/5! - x^3/7! + x^4/9! - x^5/11!)
+  double ps = -1.0 / 39916800.0;
+  ps = fma(ps, x, 1.0 / 362880.0);
+  ps = fma(ps, x, -1.0 / 5040.0);
+  ps = fma(ps, x, 1.0 / 120.0);
+  ps = fma(ps, x, -1.0 / 6.0);
+  ps = fma(ps, x, 1.0);
+  const double sd = d * ps;
+  // cos d = 1 - x/2! + x^2/4! - x^3/6! + x^4/8! - x^5/10! + x^6/12!
+  double pc = 1.0 / 479001600.0;
+  pc = fma(pc, x, -1.0 / 3628800.0);
+  pc = fma(pc, x, 1.0 / 40320.0);
+  pc = fma(pc, x, -1.0 / 720.0);
+  pc = fma(pc, x, 1.0 / 24.0);
+  pc = fma(pc, x, -0.5);
+  const double cd = fma(pc, x, 1.0);
+  s = fma(s0, cd, c0 * sd);
+  c = fma(c0, cd, -(s0 * sd));
+  return true;
+}
+
+// (sin, cos) of th = theta0 + d given those of theta0; falls back to sincos(th).
+__device__ __forceinline__ void sincos_step(double th, double s0, double c0, double d, double& s,
+                                            double& c) {
+  if (!rotate_small(s0, c0, d, s, c)) sincos(th, &s, &c);
+}
+
 __device__ __forceinline__ double rk_c(int j) { return j == 0 ? 0.0 : (j == 3 ? 1.0 : 0.5); }
 __device__ __forceinline__ double rk_w(int j) {
   return (j == 0 || j == 3) ? (1.0 / 6.0) : (2.0 / 6.0);

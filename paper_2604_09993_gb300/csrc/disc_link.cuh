@@ -2,17 +2,69 @@
 // (Sec. IV-B Eqs. (14)-(15), Eq. (17b); IND + FOH, Sec. VI), shared by the
 // single-instance and the batched kernels.  See common.cuh for the structure
 // it exploits and disc.cu for the thread mapping.
+//
+// FP64 work is what bounds these kernels on this GPU, so the state side avoids
+// every FP64 instruction it can:
+//  * sin/cos of the stage angles are chained by angle addition from the
+//    substep start (rotate_small), with sincos only for large increments;
+//  * the four penalty terms that depend on the inputs alone are evaluated once
+//    per distinct stage time (two per substep: the midpoint serves stages 2
+//    and 3, the end point serves stage 4 and the next substep's stage 1);
+//  * derivatives of the penalty terms are evaluated in the tangent precision;
+//  * in FP32-Phi mode the tangent recursion takes its stage data from an FP32
+//    copy of the stage recursion that is re-anchored on the FP64 state at the
+//    start of every substep (a handful of conversions per substep instead of
+//    several per stage).
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ciscvx {
 
 template <typename TP>
 struct Tangents {
-  TP Pt[9], Pw[9];   // rotation tangents: theta row, omega row
-  TP Qp[5], Qv[5];   // foot p_y/v_y tangents: columns py0, vy0, s, L, R
+  TP Pt[9], Pw[9];         // rotation tangents: theta row, omega row
+  TP Qp[5], Qv[5];         // foot p_y/v_y tangents: columns py0, vy0, s, L, R
   TP Yr[9], Yp[5], Yd[6];  // foot penalty row: rotation columns, p_y columns, direct contact inputs
 };
+
+// Penalty terms that depend on the inputs alone, at one stage time.
+template <typename TP>
+struct InputPenalty {
+  double H;       // sum of the four h(g) values (FP64; 0 unless requested)
+  TP Hp;          // the same sum in the tangent precision (adjoint weights)
+  TP d0, d1, d2;  // s * dOmega/d(lambda_n, lambda_t+, lambda_t-) (tangent precision)
+};
+
+// H64: evaluate the FP64 values (the penalty state); the tangent-precision
+// slopes (and values, for FP32) are always evaluated.
+template <typename TP, bool H64 = true>
+__device__ __forceinline__ InputPenalty<TP> input_penalty(double t, TP tP, double sd, TP sdP,
+                                                          double mu, TP muP, const double* L,
+                                                          const double* D, const TP* LP,
+                                                          const TP* DP) {
+  InputPenalty<TP> r;
+  r.H = 0.0;
+  if (H64) {
+    const double ln = fma(t, D[0], L[0]), ltp = fma(t, D[1], L[1]), ltm = fma(t, D[2], L[2]);
+    r.H = huber_value(-ln) + huber_value(-ltp) + huber_value(-ltm) +
+          huber_value(ltp + ltm - mu * ln);
+  }
+  const TP lnP = LP[0] + tP * DP[0], ltpP = LP[1] + tP * DP[1], ltmP = LP[2] + tP * DP[2];
+  if constexpr (std::is_same<TP, float>::value)
+    r.Hp = huber_value(-lnP) + huber_value(-ltpP) + huber_value(-ltmP) +
+           huber_value(ltpP + ltmP - muP * lnP);
+  else
+    r.Hp = TP(r.H);
+  const TP D1 = huber_slope(-lnP), D2 = huber_slope(-ltpP), D3 = huber_slope(-ltmP);
+  const TP D5 = huber_slope(ltpP + ltmP - muP * lnP);
+  r.d0 = sdP * (-D1 - muP * D5);
+  r.d1 = sdP * (-D2 + D5);
+  r.d2 = sdP * (-D3 + D5);
+  (void)sd;
+  return r;
+}
 
 // One link of one interval.  xk/xk1: node states k and k+1; uL/uR: FOH
 // controls; A/Bm/Bp/S/defect/pen/z: this interval's output blocks.
@@ -26,6 +78,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
                                           TP* __restrict__ S, double* __restrict__ defect,
                                           double* __restrict__ pen, double* __restrict__ z,
                                           unsigned* status) {
+  constexpr bool F32 = std::is_same<TP, float>::value;
   const DevBody& B = M.body[b];
   const int nb = M.nb, nxt = M.nxt, nu = M.nu;
   const double g = M.g;
@@ -55,14 +108,23 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
 
   constexpr bool foot = FOOT;  // B.contact >= 0; warp-uniform, dispatched by the kernel
   const int cin = B.cin;
-  double lnL = 0, lnD = 0, tpL = 0, tpD = 0, tmL = 0, tmD = 0;
+  double cL[3] = {0, 0, 0}, cD[3] = {0, 0, 0};  // contact inputs at tau = 0 and their increments
+  TP cLP[3], cDP[3];
   if (foot) {
-    lnL = uL[cin]; lnD = uR[cin] - lnL;
-    tpL = uL[cin + 1]; tpD = uR[cin + 1] - tpL;
-    tmL = uL[cin + 2]; tmD = uR[cin + 2] - tmL;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      cL[m] = uL[cin + m];
+      cD[m] = uR[cin + m] - cL[m];
+      cLP[m] = TP(cL[m]);
+      cDP[m] = TP(cD[m]);
+    }
   }
   const double mu = B.mu, crx = B.crho[0], cry = B.crho[1];
+  const TP muP = TP(mu), crxP = TP(crx), cryP = TP(cry);
   const double dP = PR - PL, dQ = QR - QL, dT = TR - TL, dAy = AyR - AyL;
+  // tangent-precision copies of the input sums
+  const TP PLP = TP(PL), dPP = TP(dP), QLP = TP(QL), dQP = TP(dQ), TLP = TP(TL), dTP = TP(dT);
+  const TP AyLP = TP(AyL), dAyP = TP(dAy), gP = TP(g);
 
   Tangents<TP> tg;
 #pragma unroll
@@ -77,67 +139,101 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   const double h = 1.0 / nsub;
   const TP hP = TP(h), sdP = TP(sd);
   double th = th0, om = om0, py = py0, vy = vy0, Yom = 0.0;
+  double sth, cth;  // sin/cos of th at the substep start (chained)
+  sincos(th, &sth, &cth);
+  InputPenalty<TP> ip0;  // input penalty at the substep start
+  if (foot) ip0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
 
   for (int i = 0; i < nsub; ++i) {
     // ---- state stages (FP64) ----
-    TP cw[4], swL[4], sath[4], fc[4], fs[4], oms[4], wdt[4], tau[4];
+    TP cw[4], sw[4], sath[4], oms[4], wdt[4], tau[4];
     TP gr[4], gp[4], vys[4], ays[4], dl0[4], dl1[4], dl2[4];
+    InputPenalty<TP> ipm, ip1;
+    if (foot) {
+      ipm = input_penalty<TP>((i + 0.5) * h, TP((i + 0.5) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      ip1 = input_penalty<TP>((i + 1.0) * h, TP((i + 1.0) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+    }
+    // FP32 copy of the stage recursion, anchored on the FP64 state (FP32-Phi mode)
+    const TP thA = TP(th), omA = TP(om), pyA = TP(py), vyA = TP(vy);
+    TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0);
     double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const double cj = rk_c(j), wj = rk_w(j);
       const double tj = (i + cj) * h;
-      const double ths = (j == 0) ? th : fma(cj * h, kth, th);
+      const double dth = cj * h * kth;
+      const double ths = th + dth;
       const double ws = (j == 0) ? om : fma(cj * h, kom, om);
       double sn, cs;
-      sincos(ths, &sn, &cs);
+      if (j == 0) { sn = sth; cs = cth; }
+      else sincos_step(ths, sth, cth, dth, sn, cs);
       const double P = fma(tj, dP, PL), Q = fma(tj, dQ, QL), T = fma(tj, dT, TL);
       const double wdot = fma(cs, P, fma(-sn, Q, T));
       kth = sd * ws;
       kom = sd * wdot;
       ath_ = fma(wj, kth, ath_);
       aom_ = fma(wj, kom, aom_);
-      cw[j] = TP(cs);
-      swL[j] = TP(sn);
-      sath[j] = TP(-sd * fma(sn, P, cs * Q));  // s * d(omega')/d(theta)
-      oms[j] = TP(ws);
-      wdt[j] = TP(wdot);
-      tau[j] = TP(tj);
+      double pys = 0.0, vs = 0.0;
       if (foot) {
-        const double pys = (j == 0) ? py : fma(cj * h, kpy, py);
-        const double vs = (j == 0) ? vy : fma(cj * h, kvy, vy);
+        pys = (j == 0) ? py : fma(cj * h, kpy, py);
+        vs = (j == 0) ? vy : fma(cj * h, kvy, vy);
         const double ay = fma(tj, dAy, AyL) - g;
         kpy = sd * vs;
         kvy = sd * ay;
         apy = fma(wj, kpy, apy);
         avy = fma(wj, kvy, avy);
-        const double rx = cs * crx - sn * cry;
-        const double ry = sn * crx + cs * cry;
-        const double ln = fma(tj, lnD, lnL), ltp = fma(tj, tpD, tpL), ltm = fma(tj, tmD, tmL);
-        double H1, D1, H2, D2, H3, D3, H4, D4, H5, D5;
-        huber(-ln, H1, D1);
-        huber(-ltp, H2, D2);
-        huber(-ltm, H3, D3);
-        huber(-(pys + ry), H4, D4);
-        huber(ltp + ltm - mu * ln, H5, D5);
-        Yom = fma(h * wj, H1 + H2 + H3 + H4 + H5, Yom);
-        gp[j] = TP(-sd * D4);       // s dOmega/dp_y
-        gr[j] = TP(-sd * D4 * rx);  // s dOmega/dtheta
-        vys[j] = TP(vs);
-        ays[j] = TP(ay);
-        dl0[j] = TP(sd * (-D1 - mu * D5));
-        dl1[j] = TP(sd * (-D2 + D5));
-        dl2[j] = TP(sd * (-D3 + D5));
+        const double ry = fma(sn, crx, cs * cry);
+        const InputPenalty<TP>& ipj = (j == 0) ? ip0 : (j == 3 ? ip1 : ipm);
+        Yom = fma(h * wj, ipj.H + huber_value(-(pys + ry)), Yom);
+        dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
+      }
+      // stage data for the tangent recursion
+      const TP cjh = TP(cj * h);
+      TP csP, snP, PP, QP, TT, wsP, pysP = TP(0), vsP = TP(0);
+      if constexpr (F32) {
+        const TP tP = TP(tj);
+        const TP thsP = (j == 0) ? thA : thA + cjh * kthA;
+        wsP = (j == 0) ? omA : omA + cjh * komA;
+        sincosf(thsP, &snP, &csP);
+        PP = PLP + tP * dPP; QP = QLP + tP * dQP; TT = TLP + tP * dTP;
+        tau[j] = tP;
+        if (foot) {
+          pysP = (j == 0) ? pyA : pyA + cjh * kpyA;
+          vsP = (j == 0) ? vyA : vyA + cjh * kvyA;
+        }
+      } else {
+        csP = cs; snP = sn; PP = P; QP = Q; TT = T; wsP = ws; pysP = pys; vsP = vs;
+        tau[j] = tj;
+      }
+      const TP wdP = csP * PP - snP * QP + TT;
+      cw[j] = csP;
+      sw[j] = snP;
+      sath[j] = -sdP * (snP * PP + csP * QP);  // s * d(omega')/d(theta)
+      oms[j] = wsP;
+      wdt[j] = wdP;
+      if constexpr (F32) { kthA = sdP * wsP; komA = sdP * wdP; }
+      if (foot) {
+        const TP ayP = AyLP + tau[j] * dAyP - gP;
+        if constexpr (F32) { kpyA = sdP * vsP; kvyA = sdP * ayP; }
+        const TP rxP = csP * crxP - snP * cryP;
+        const TP ryP = snP * crxP + csP * cryP;
+        const TP D4 = huber_slope(-(pysP + ryP));
+        gp[j] = -sdP * D4;        // s dOmega/dp_y
+        gr[j] = -sdP * D4 * rxP;  // s dOmega/dtheta
+        vys[j] = vsP;
+        ays[j] = ayP;
       }
     }
-    th = fma(h, ath_, th);
-    om = fma(h, aom_, om);
-    if (foot) { py = fma(h, apy, py); vy = fma(h, avy, vy); }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      fc[j] = sdP * cw[j];
-      fs[j] = -sdP * swL[j];
+    const double Dth = h * ath_;
+    {
+      double s1, c1;
+      sincos_step(th + Dth, sth, cth, Dth, s1, c1);
+      sth = s1;
+      cth = c1;
     }
+    th += Dth;
+    om = fma(h, aom_, om);
+    if (foot) { py = fma(h, apy, py); vy = fma(h, avy, vy); ip0 = ip1; }
 
     // ---- rotation tangents: 9 columns, 4 stages each ----
 #pragma unroll
@@ -152,11 +248,11 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         const TP wl = TP(1) - tau[j], wr = tau[j];
         TP fT = TP(0), fW = TP(0);
         if (c == 2) { fT = oms[j]; fW = wdt[j]; }
-        else if (c == 3) fW = fc[j] * wl;
-        else if (c == 4) fW = fs[j] * wl;
+        else if (c == 3) fW = sdP * cw[j] * wl;
+        else if (c == 4) fW = -sdP * sw[j] * wl;
         else if (c == 5) fW = sdP * wl;
-        else if (c == 6) fW = fc[j] * wr;
-        else if (c == 7) fW = fs[j] * wr;
+        else if (c == 6) fW = sdP * cw[j] * wr;
+        else if (c == 7) fW = -sdP * sw[j] * wr;
         else if (c == 8) fW = sdP * wr;
         kT = sdP * Ws + fT;
         kW = sath[j] * Ts + fW;
@@ -294,8 +390,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       const int r = rows[t];
       double acc = x1v[t] - double(S[r]) * sd;
       // A's nonzeros in this row lie in this link's columns (and y_r for the y row)
-      const int cols[7] = {rpx, rpy, rth, rvx, rvy, rom, ry_};
-      for (int u = 0; u < nr; ++u) acc -= double(A[(size_t)r * nxt + cols[u]]) * xk[cols[u]];
+      for (int u = 0; u < nr; ++u) acc -= double(A[(size_t)r * nxt + rows[u]]) * xk[rows[u]];
       for (int i = 0; i < nin; ++i) {
         const int q = B.idx[i];
         acc -= double(Bm[(size_t)r * nu + q]) * uL[q] + double(Bp[(size_t)r * nu + q]) * uR[q];

@@ -1,7 +1,21 @@
 // vjp_link.cuh — one link of one interval of the discrete-adjoint VJP, shared
 // by the single-instance and the batched kernels (see vjp.cu).
+//
+// Forward sweep: the FP64 state, checkpointing (theta, omega, sin theta,
+// cos theta) — and (p_y, v_y) for a foot link — at every substep start.
+// Backward sweep: per substep, the four stages are recomputed from the
+// checkpoint and the transposed stage Jacobians are applied in the adjoint
+// precision TP.
+//  * FP64 adjoint: the stages are recomputed in FP64 (sin/cos chained as in
+//    the forward kernel) and the penalty quadrature (for L) is taken there.
+//  * FP32 adjoint: the penalty quadrature is taken in the forward sweep on the
+//    FP64 stages, and the backward sweep recomputes the stages in FP32 from
+//    the FP64 checkpoints, so it issues no FP64 instruction at all.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
+#include "disc_link.cuh"
 
 namespace ciscvx {
 
@@ -16,6 +30,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
                                          double* __restrict__ gXk, double* __restrict__ gXN,
                                          double* __restrict__ part, double* __restrict__ ps,
                                          double* __restrict__ pL, unsigned* status) {
+  constexpr bool F32 = std::is_same<TP, float>::value;
   const DevBody& B = M.body[b];
   const int nb = M.nb;
   const double g = M.g;
@@ -40,47 +55,73 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   const double py1 = py0 + sd * vy0 + sd * sd * ay3, vy1 = vy0 + sd * aym;
   const double dP = PR - PL, dQ = QR - QL, dT = TR - TL, dAy = AyR - AyL;
   const int cin = B.cin;
-  double lnL = 0, lnD = 0, tpL = 0, tpD = 0, tmL = 0, tmD = 0;
+  double cL[3] = {0, 0, 0}, cD[3] = {0, 0, 0};
+  TP cLP[3], cDP[3];
   if (FOOT) {
-    lnL = uL[cin]; lnD = uR[cin] - lnL;
-    tpL = uL[cin + 1]; tpD = uR[cin + 1] - tpL;
-    tmL = uL[cin + 2]; tmD = uR[cin + 2] - tmL;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      cL[m] = uL[cin + m];
+      cD[m] = uR[cin + m] - cL[m];
+      cLP[m] = TP(cL[m]);
+      cDP[m] = TP(cD[m]);
+    }
   }
   const double mu = B.mu, crx = B.crho[0], cry = B.crho[1];
+  const TP muP = TP(mu), crxP = TP(crx), cryP = TP(cry);
+  const TP PLP = TP(PL), dPP = TP(dP), QLP = TP(QL), dQP = TP(dQ), TLP = TP(TL), dTP = TP(dT);
+  const TP AyLP = TP(AyL), dAyP = TP(dAy), gP = TP(g);
   const double h = 1.0 / nsub;
+  const TP sdP = TP(sd), hP = TP(h);
 
-  // ---- forward sweep: checkpoints and x~(1) ----
-  double ck_th[MAXSUB_VJP], ck_om[MAXSUB_VJP], ck_py[FOOT ? MAXSUB_VJP : 1],
-      ck_vy[FOOT ? MAXSUB_VJP : 1];
-  double th = th0, om = om0, py = py0, vy = vy0, Yom = 0.0;
+  // ---- forward sweep: FP64 state and checkpoints ----
+  double ck_th[MAXSUB_VJP], ck_om[MAXSUB_VJP], ck_s[MAXSUB_VJP], ck_c[MAXSUB_VJP];
+  double ck_py[FOOT ? MAXSUB_VJP : 1], ck_vy[FOOT ? MAXSUB_VJP : 1];
+  double th = th0, om = om0, py = py0, vy = vy0;
+  double sth, cth;
+  sincos(th, &sth, &cth);
+  // FP32 adjoint: the penalty quadrature is taken here, on the FP64 forward
+  // stages, so that the backward sweep needs no FP64 work at all.
+  constexpr bool PEN_FWD = FOOT && F32;
+  double Yom = 0.0;
+  InputPenalty<TP> fp0, fpm, fp1;
+  if (PEN_FWD) fp0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
   for (int i = 0; i < nsub; ++i) {
-    ck_th[i] = th; ck_om[i] = om;
+    ck_th[i] = th; ck_om[i] = om; ck_s[i] = sth; ck_c[i] = cth;
     if (FOOT) { ck_py[i] = py; ck_vy[i] = vy; }
+    if (PEN_FWD) {
+      fpm = input_penalty<TP>((i + 0.5) * h, TP((i + 0.5) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      fp1 = input_penalty<TP>((i + 1.0) * h, TP((i + 1.0) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+    }
     double kth = 0, kom = 0, ath = 0, aom = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const double cj = rk_c(j), wj = rk_w(j), tj = (i + cj) * h;
-      const double ths = (j == 0) ? th : fma(cj * h, kth, th);
+      const double dth = cj * h * kth;
       const double ws = (j == 0) ? om : fma(cj * h, kom, om);
       double sn, cs;
-      sincos(ths, &sn, &cs);
+      if (j == 0) { sn = sth; cs = cth; }
+      else sincos_step(th + dth, sth, cth, dth, sn, cs);
       const double wdot = fma(cs, fma(tj, dP, PL), fma(-sn, fma(tj, dQ, QL), fma(tj, dT, TL)));
       kth = sd * ws; kom = sd * wdot;
       ath = fma(wj, kth, ath); aom = fma(wj, kom, aom);
       if (FOOT) {
-        const double pys = (j == 0) ? py : fma(cj * h, kpy, py);
         const double vs = (j == 0) ? vy : fma(cj * h, kvy, vy);
+        if (PEN_FWD) {
+          const double pys = (j == 0) ? py : fma(cj * h, kpy, py);
+          const InputPenalty<TP>& ipj = (j == 0) ? fp0 : (j == 3 ? fp1 : fpm);
+          Yom = fma(h * wj, ipj.H + huber_value(-(pys + fma(sn, crx, cs * cry))), Yom);
+        }
         kpy = sd * vs; kvy = sd * (fma(tj, dAy, AyL) - g);
         apy = fma(wj, kpy, apy); avy = fma(wj, kvy, avy);
-        const double ry = sn * crx + cs * cry;
-        const double ln = fma(tj, lnD, lnL), ltp = fma(tj, tpD, tpL), ltm = fma(tj, tmD, tmL);
-        double H1, D1, H2, D2, H3, D3, H4, D4, H5, D5;
-        huber(-ln, H1, D1); huber(-ltp, H2, D2); huber(-ltm, H3, D3);
-        huber(-(pys + ry), H4, D4); huber(ltp + ltm - mu * ln, H5, D5);
-        Yom = fma(h * wj, H1 + H2 + H3 + H4 + H5, Yom);
       }
     }
-    th = fma(h, ath, th); om = fma(h, aom, om);
+    if (PEN_FWD) fp0 = fp1;
+    const double Dth = h * ath;
+    double s1, c1;
+    sincos_step(th + Dth, sth, cth, Dth, s1, c1);
+    sth = s1; cth = c1;
+    th += Dth;
+    om = fma(h, aom, om);
     if (FOOT) { py = fma(h, apy, py); vy = fma(h, avy, vy); }
   }
 
@@ -90,64 +131,97 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   double wy = 0.0, lam_y = 0.0;
   if (FOOT) { ry_ = 6 * nb + B.contact; wy = wk[ry_]; lam_y = wy + rho_c; }
 
-  // L share: w . defect over this link's rows (+ rho . penalty)
-  double Lp = wpx * (px1 - xk1[rpx]) + wpy * (py1 - xk1[rpy]) + wth * (th - xk1[rth]) +
-              wvx * (vx1 - xk1[rvx]) + wvy * (vy1 - xk1[rvy]) + wom * (om - xk1[rom]);
-  if (FOOT) {
-    const double pen = sd * Yom;
-    Lp += wy * (xk[ry_] + pen - xk1[ry_]) + rho_c * pen;
-  }
-
   // ---- backward sweep ----
   TP lth = TP(wth), lom = TP(wom), lpy = TP(0), lvy = TP(0);
-  const TP ly = TP(lam_y), sdP = TP(sd), hP = TP(h);
+  const TP ly = TP(lam_y);
   TP gsd = TP(0), gPL = TP(0), gPR = TP(0), gQL = TP(0), gQR = TP(0), gTL = TP(0), gTR = TP(0);
   TP gAyL = TP(0), gAyR = TP(0), gd[6] = {TP(0), TP(0), TP(0), TP(0), TP(0), TP(0)};
+  // input penalty at the end of the current substep (FP64 values only for the
+  // FP64 adjoint, which takes the penalty quadrature here, last substep first)
+  InputPenalty<TP> ipE;
+  if (FOOT) ipE = input_penalty<TP, !F32>(1.0, TP(1), sd, sdP, mu, muP, cL, cD, cLP, cDP);
   for (int i = nsub - 1; i >= 0; --i) {
-    // recompute the four stages of substep i from its checkpoint
     TP cs_[4], sn_[4], sath[4], oms[4], wdt[4], tau[4];
     TP gr[4], gp[4], vys[4], ays[4], om_pen[4], dl0[4], dl1[4], dl2[4];
+    InputPenalty<TP> ipS, ipM;
+    if (FOOT) {
+      ipM = input_penalty<TP, !F32>((i + 0.5) * h, TP((i + 0.5) * h), sd, sdP, mu, muP, cL, cD, cLP,
+                                    cDP);
+      ipS = input_penalty<TP, !F32>(i * h, TP(i * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+    }
     {
-      const double thc = ck_th[i], omc = ck_om[i];
+      const double thc = ck_th[i], omc = ck_om[i], stc = ck_s[i], ctc = ck_c[i];
       double pyc = 0, vyc = 0;
       if (FOOT) { pyc = ck_py[i]; vyc = ck_vy[i]; }
+      const TP thA = TP(thc), omA = TP(omc), pyA = TP(pyc), vyA = TP(vyc);
+      TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0);
       double kth = 0, kom = 0, kpy = 0, kvy = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const double cj = rk_c(j), tj = (i + cj) * h;
-        const double ths = (j == 0) ? thc : fma(cj * h, kth, thc);
-        const double ws = (j == 0) ? omc : fma(cj * h, kom, omc);
-        double sn, cs;
-        sincos(ths, &sn, &cs);
-        const double P = fma(tj, dP, PL), Q = fma(tj, dQ, QL), T = fma(tj, dT, TL);
-        const double wdot = fma(cs, P, fma(-sn, Q, T));
-        kth = sd * ws; kom = sd * wdot;
-        cs_[j] = TP(cs); sn_[j] = TP(sn);
-        sath[j] = TP(-sd * fma(sn, P, cs * Q));
-        oms[j] = TP(ws); wdt[j] = TP(wdot); tau[j] = TP(tj);
+        const double cj = rk_c(j), wj = rk_w(j), tj = (i + cj) * h;
+        const TP cjh = TP(cj * h);
+        // FP64 stage state: needed for the penalty values (and for the FP64 adjoint)
+        double cs = ctc, sn = stc, P = 0, Q = 0, T = 0, ws = omc, wdot = 0, pys = pyc, vs = vyc;
+        if (!F32) {
+          const double dth = cj * h * kth;
+          ws = (j == 0) ? omc : fma(cj * h, kom, omc);
+          if (j > 0) sincos_step(thc + dth, stc, ctc, dth, sn, cs);
+          P = fma(tj, dP, PL); Q = fma(tj, dQ, QL); T = fma(tj, dT, TL);
+          wdot = fma(cs, P, fma(-sn, Q, T));
+          kth = sd * ws; kom = sd * wdot;
+          if (FOOT) {
+            pys = (j == 0) ? pyc : fma(cj * h, kpy, pyc);
+            vs = (j == 0) ? vyc : fma(cj * h, kvy, vyc);
+            kpy = sd * vs; kvy = sd * (fma(tj, dAy, AyL) - g);
+            const double ry = fma(sn, crx, cs * cry);
+            const InputPenalty<TP>& ipj = (j == 0) ? ipS : (j == 3 ? ipE : ipM);
+            const double Om = ipj.H + huber_value(-(pys + ry));
+            Yom = fma(h * wj, Om, Yom);
+            om_pen[j] = TP(Om);
+            dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
+          }
+        }
+        TP csP, snP, PP, QP, TT, wsP, pysP = TP(0), vsP = TP(0);
+        if constexpr (F32) {
+          const TP tP = TP(tj);
+          const TP thsP = (j == 0) ? thA : thA + cjh * kthA;
+          wsP = (j == 0) ? omA : omA + cjh * komA;
+          sincosf(thsP, &snP, &csP);
+          PP = PLP + tP * dPP; QP = QLP + tP * dQP; TT = TLP + tP * dTP;
+          tau[j] = tP;
+          if (FOOT) {
+            pysP = (j == 0) ? pyA : pyA + cjh * kpyA;
+            vsP = (j == 0) ? vyA : vyA + cjh * kvyA;
+          }
+        } else {
+          csP = cs; snP = sn; PP = P; QP = Q; TT = T; wsP = ws; pysP = pys; vsP = vs;
+          tau[j] = tj;
+        }
+        const TP wdP = csP * PP - snP * QP + TT;
+        cs_[j] = csP; sn_[j] = snP;
+        sath[j] = -sdP * (snP * PP + csP * QP);
+        oms[j] = wsP; wdt[j] = wdP;
+        if constexpr (F32) { kthA = sdP * wsP; komA = sdP * wdP; }
         if (FOOT) {
-          const double pys = (j == 0) ? pyc : fma(cj * h, kpy, pyc);
-          const double vs = (j == 0) ? vyc : fma(cj * h, kvy, vyc);
-          const double ay = fma(tj, dAy, AyL) - g;
-          kpy = sd * vs; kvy = sd * ay;
-          const double rx = cs * crx - sn * cry, ry = sn * crx + cs * cry;
-          const double ln = fma(tj, lnD, lnL), ltp = fma(tj, tpD, tpL), ltm = fma(tj, tmD, tmL);
-          double H1, D1, H2, D2, H3, D3, H4, D4, H5, D5;
-          huber(-ln, H1, D1); huber(-ltp, H2, D2); huber(-ltm, H3, D3);
-          huber(-(pys + ry), H4, D4); huber(ltp + ltm - mu * ln, H5, D5);
-          gp[j] = TP(-sd * D4);
-          gr[j] = TP(-sd * D4 * rx);
-          vys[j] = TP(vs); ays[j] = TP(ay);
-          om_pen[j] = TP(H1 + H2 + H3 + H4 + H5);
-          dl0[j] = TP(sd * (-D1 - mu * D5));
-          dl1[j] = TP(sd * (-D2 + D5));
-          dl2[j] = TP(sd * (-D3 + D5));
+          const TP ayP = AyLP + tau[j] * dAyP - gP;
+          if constexpr (F32) { kpyA = sdP * vsP; kvyA = sdP * ayP; }
+          const TP rxP = csP * crxP - snP * cryP, ryP = snP * crxP + csP * cryP;
+          const TP D4 = huber_slope(-(pysP + ryP));
+          gp[j] = -sdP * D4;
+          gr[j] = -sdP * D4 * rxP;
+          vys[j] = vsP; ays[j] = ayP;
+          if constexpr (F32) {
+            const InputPenalty<TP>& ipj = (j == 0) ? ipS : (j == 3 ? ipE : ipM);
+            om_pen[j] = ipj.Hp + huber_value(-(pysP + ryP));
+            dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
+          }
         }
       }
     }
+    if (FOOT) ipE = ipS;
     // transposed stages j = 3..0
     TP mth = TP(0), mom = TP(0), mpy = TP(0), mvy = TP(0);  // mu_{j+1}
-    TP sth = TP(0), som = TP(0), spy = TP(0), svy = TP(0);  // sum of mu_j
+    TP sth_ = TP(0), som = TP(0), spy = TP(0), svy = TP(0);  // sum of mu_j
 #pragma unroll
     for (int j = 3; j >= 0; --j) {
       const TP hw = hP * TP(rk_w(j));
@@ -176,10 +250,18 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
         gd[2] += inj * dl2[j] * wl; gd[5] += inj * dl2[j] * wr;
         mpy = npy; mvy = nvy; spy += npy; svy += nvy;
       }
-      mth = nth; mom = nom; sth += nth; som += nom;
+      mth = nth; mom = nom; sth_ += nth; som += nom;
     }
-    lth += sth; lom += som;
+    lth += sth_; lom += som;
     if (FOOT) { lpy += spy; lvy += svy; }
+  }
+
+  // L share: w . defect over this link's rows (+ rho . penalty)
+  double Lp = wpx * (px1 - xk1[rpx]) + wpy * (py1 - xk1[rpy]) + wth * (th - xk1[rth]) +
+              wvx * (vx1 - xk1[rvx]) + wvy * (vy1 - xk1[rvy]) + wom * (om - xk1[rom]);
+  if (FOOT) {
+    const double pen = sd * Yom;
+    Lp += wy * (xk[ry_] + pen - xk1[ry_]) + rho_c * pen;
   }
 
   // ---- translation: transposed closed forms ----
