@@ -39,11 +39,14 @@ from paper_2604_09993_gb300 import synth  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 126 * 2 ** 20
 
+# make(n_inst, seed): rank r of a multi-GPU run uses seed r (its own independent batch)
 WORKLOADS = {
-    "cheetah7-sweep-4096x400x20": dict(kind="batch", make=lambda n: synth.cheetah_sweep(seed=0, n_inst=n),
-                                       instances=4096),
-    "mixed-1024": dict(kind="batch", make=lambda n: synth.mixed_batch(seed=0, n_inst=n), instances=1024),
-    "cheetah7-n50-sub10": dict(kind="single", make=lambda n: synth.cheetah_n50(seed=0), instances=1),
+    "cheetah7-sweep-4096x400x20": dict(kind="batch", instances=4096,
+                                       make=lambda n, seed=0: synth.cheetah_sweep(seed=seed, n_inst=n)),
+    "mixed-1024": dict(kind="batch", instances=1024,
+                       make=lambda n, seed=0: synth.mixed_batch(seed=seed, n_inst=n)),
+    "cheetah7-n50-sub10": dict(kind="single", instances=1,
+                               make=lambda n, seed=0: synth.cheetah_n50(seed=seed)),
 }
 DEFAULT_WORKLOAD = "cheetah7-sweep-4096x400x20"
 
@@ -118,11 +121,11 @@ class ClockSampler:
 class BatchWorkload:
     """Instances packed for a batch plan; one plan per precision (autotuned)."""
 
-    def __init__(self, spec, n_inst, dev):
+    def __init__(self, spec, n_inst, dev, seed=0):
         import torch
         from paper_2604_09993_gb300 import api
         self.api, self.torch, self.dev = api, torch, dev
-        self.batch = spec["make"](n_inst)
+        self.batch = spec["make"](n_inst, seed)
         b = self.batch
         self.models = [api.Model(r) for r in b.robots]
         probs = [b.instance(i) for i in range(len(b))]
@@ -210,11 +213,11 @@ class BatchWorkload:
 class SingleWorkload:
     """One instance through ciscvx_discretize + ciscvx_discretize_vjp."""
 
-    def __init__(self, spec, n_inst, dev):
+    def __init__(self, spec, n_inst, dev, seed=0):
         import torch
         from paper_2604_09993_gb300 import api
         self.api, self.torch, self.dev = api, torch, dev
-        prob = spec["make"](1)
+        prob = spec["make"](1, seed)
         self.model = api.Model(prob.robot)
         t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
         self.X, self.U, self.s, self.w, self.rho = (t(prob.X), t(prob.U), t(prob.s), t(prob.w), t(prob.rho))
@@ -343,7 +346,7 @@ def run_ours(args):
     api.load()
     spec = WORKLOADS[args.workload]
     n_inst = args.instances or spec["instances"]
-    wl = (BatchWorkload if spec["kind"] == "batch" else SingleWorkload)(spec, n_inst, dev)
+    wl = (BatchWorkload if spec["kind"] == "batch" else SingleWorkload)(spec, n_inst, dev, seed=rank)
     stream = torch.cuda.current_stream()
     prec = args.precision
 
@@ -354,12 +357,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(vals):
-        if world == 1:
-            return vals
-        import torch.distributed as tdist
-        tt = torch.tensor(vals, device=dev)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        return tt.tolist()
+        from paper_2604_09993_gb300 import dist as pdist
+        return pdist.max_over_ranks(vals, device=dev)
 
     # plain FP64 GPU path (comparator)
     t64 = kd64 = None

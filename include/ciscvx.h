@@ -223,6 +223,9 @@ typedef struct {
                          queue; 0: one warp per work item */
   int lpt_order;      /* 1: items ordered by decreasing estimated cost; 0: instance order */
   int use_graph;      /* 1: capture the launch sequence in a CUDA graph and replay it */
+  int occupancy;      /* register cap of the kernels: 0 none (8 warps/SM), 1 <= 168 registers
+                         (12 warps/SM), 2 <= 128 registers (16 warps/SM); 1 and 2 need
+                         warps_per_cta <= 4 */
 } ciscvx_tune;
 
 /* Element counts of the packed buffers (or, from ciscvx_batch_offsets, the
@@ -260,7 +263,7 @@ typedef struct {
  * models[model_idx[i]] with N[i] intervals and n_sub[i] substeps.  All arrays
  * are host memory, copied; the models must outlive the plan and live on the
  * current device.  tune may be NULL (defaults: 4 warps/CTA, persistent with
- * 2 CTAs/SM, cost order, graph).  Allocates the plan's device tables (this
+ * 2 CTAs/SM, cost order, graph, no register cap).  Allocates the plan's device tables (this
  * is the only allocating batch call besides autotuning's timing buffers).
  * Errors: EINVAL (nulls, n_inst < 1, bad indices, N < 1, n_sub < 1, layout,
  * precision), EUNSUPPORTED (tensor-core precisions), ENOMEM/ECUDA. */

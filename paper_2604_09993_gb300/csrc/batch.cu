@@ -55,8 +55,14 @@ __device__ __forceinline__ int next_item(const BatchCommon& c, int& local_iter) 
   return __shfl_sync(0xffffffffu, it, 0);
 }
 
-template <typename TP>
-__global__ void __launch_bounds__(256) k_batch_disc(BatchCommon c, const double* __restrict__ X,
+// Launch bounds per occupancy variant: (threads per CTA, min CTAs per SM).
+template <int OCC> struct Occ;
+template <> struct Occ<0> { static constexpr int T = 256, B = 1; };  // no register cap
+template <> struct Occ<1> { static constexpr int T = 128, B = 3; };  // <= 168 registers
+template <> struct Occ<2> { static constexpr int T = 128, B = 4; };  // <= 128 registers
+
+template <typename TP, int OCC>
+__global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCommon c, const double* __restrict__ X,
                                                     const double* __restrict__ U,
                                                     const double* __restrict__ s, TP* A, TP* Bm,
                                                     TP* Bp, TP* S, double* defect,
@@ -94,8 +100,8 @@ __global__ void __launch_bounds__(256) k_batch_disc(BatchCommon c, const double*
   }
 }
 
-template <typename TP>
-__global__ void __launch_bounds__(256) k_batch_vjp(BatchCommon c, const double* __restrict__ X,
+template <typename TP, int OCC>
+__global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_vjp(BatchCommon c, const double* __restrict__ X,
                                                    const double* __restrict__ U,
                                                    const double* __restrict__ s,
                                                    const double* __restrict__ w,
@@ -213,7 +219,7 @@ struct ciscvx_batch_plan {
   int2* d_items_nat = nullptr;
   int* d_queue = nullptr;  // [0]: discretize, [1]: vjp
   unsigned* d_status = nullptr;
-  ciscvx_tune tune{4, 2, 1, 1};
+  ciscvx_tune tune{4, 2, 1, 1, 0};
   // graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -229,7 +235,8 @@ std::map<std::string, ciscvx_tune> g_tune_cache;
 bool tune_ok(const ciscvx_tune& t) {
   return (t.warps_per_cta == 1 || t.warps_per_cta == 2 || t.warps_per_cta == 4 ||
           t.warps_per_cta == 8) &&
-         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32;
+         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && t.occupancy >= 0 && t.occupancy <= 2 &&
+         (t.occupancy == 0 || t.warps_per_cta <= 4);
 }
 
 void free_plan(ciscvx_batch_plan* p) {
@@ -289,14 +296,21 @@ cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStr
   }
   unsigned blocks, threads;
   grid_of(p, blocks, threads);
-  if (p->prec == CISCVX_FP64)
-    k_batch_disc<double><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (double*)io->A,
-                                                     (double*)io->Bm, (double*)io->Bp,
-                                                     (double*)io->S, io->defect, io->penalty);
-  else
-    k_batch_disc<float><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (float*)io->A,
-                                                    (float*)io->Bm, (float*)io->Bp, (float*)io->S,
-                                                    io->defect, io->penalty);
+#define CISCVX_DISC(TP, OCC)                                                                  \
+  k_batch_disc<TP, OCC><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (TP*)io->A,        \
+                                                    (TP*)io->Bm, (TP*)io->Bp, (TP*)io->S,       \
+                                                    io->defect, io->penalty)
+  const int occ = p->tune.occupancy;
+  if (p->prec == CISCVX_FP64) {
+    if (occ == 1) CISCVX_DISC(double, 1);
+    else if (occ == 2) CISCVX_DISC(double, 2);
+    else CISCVX_DISC(double, 0);
+  } else {
+    if (occ == 1) CISCVX_DISC(float, 1);
+    else if (occ == 2) CISCVX_DISC(float, 2);
+    else CISCVX_DISC(float, 0);
+  }
+#undef CISCVX_DISC
   return cudaGetLastError();
 }
 
@@ -538,12 +552,20 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_bat
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "queue reset: %s", cudaGetErrorString(e));
   unsigned blocks, threads;
   grid_of(p, blocks, threads);
-  if (p->prec == CISCVX_FP64)
-    k_batch_vjp<double><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX,
-                                                   part, ps, pL);
-  else
-    k_batch_vjp<float><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX,
-                                                  part, ps, pL);
+#define CISCVX_VJP(TP, OCC)                                                                   \
+  k_batch_vjp<TP, OCC><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX, \
+                                                  part, ps, pL)
+  const int occ = p->tune.occupancy;
+  if (p->prec == CISCVX_FP64) {
+    if (occ == 1) CISCVX_VJP(double, 1);
+    else if (occ == 2) CISCVX_VJP(double, 2);
+    else CISCVX_VJP(double, 0);
+  } else {
+    if (occ == 1) CISCVX_VJP(float, 1);
+    else if (occ == 2) CISCVX_VJP(float, 2);
+    else CISCVX_VJP(float, 0);
+  }
+#undef CISCVX_VJP
   e = cudaGetLastError();
   if (e == cudaSuccess)
     k_batch_vjp_finish<<<p->n_inst, FINB, 0, s>>>(p->d_models, p->d_inst, p->layout, part, ps, pL,
@@ -573,8 +595,9 @@ ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* p, const ciscvx_batch_io*
     }
   }
   static const ciscvx_tune cands[] = {
-      {4, 2, 1, 0}, {8, 1, 1, 0}, {2, 4, 1, 0}, {1, 8, 1, 0}, {4, 0, 1, 0}, {8, 0, 1, 0},
-      {4, 2, 0, 0}, {4, 4, 1, 0},
+      {4, 2, 1, 0, 0}, {8, 1, 1, 0, 0}, {2, 4, 1, 0, 0}, {1, 8, 1, 0, 0}, {4, 0, 1, 0, 0},
+      {4, 2, 0, 0, 0}, {4, 3, 1, 0, 1}, {2, 6, 1, 0, 1}, {4, 4, 1, 0, 2}, {2, 8, 1, 0, 2},
+      {4, 0, 1, 0, 1}, {4, 0, 1, 0, 2},
   };
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

@@ -79,6 +79,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
                                           double* __restrict__ pen, double* __restrict__ z,
                                           unsigned* status) {
   constexpr bool F32 = std::is_same<TP, float>::value;
+  const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
   const int nb = M.nb, nxt = M.nxt, nu = M.nu;
   const double g = M.g;
@@ -136,9 +137,12 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   tg.Pt[0] = TP(1); tg.Pw[1] = TP(1);
   tg.Qp[0] = TP(1); tg.Qv[1] = TP(1);
 
-  const double h = 1.0 / nsub;
-  const TP hP = TP(h), sdP = TP(sd);
+  const double h = 1.0 / nsub, h2 = 0.5 * h;
+  const TP hP = TP(h), sdP = TP(sd), h2P = TP(h2);
+  const TP cjhP[4] = {TP(0), h2P, h2P, hP};
   double th = th0, om = om0, py = py0, vy = vy0, Yom = 0.0;
+  double ti = 0.0;  // tau at the substep start (running sum; rounding ~1e-16 per step)
+  TP tiP = TP(0);
   double sth, cth;  // sin/cos of th at the substep start (chained)
   sincos(th, &sth, &cth);
   InputPenalty<TP> ip0;  // input penalty at the substep start
@@ -148,10 +152,12 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     // ---- state stages (FP64) ----
     TP cw[4], sw[4], sath[4], oms[4], wdt[4], tau[4];
     TP gr[4], gp[4], vys[4], ays[4], dl0[4], dl1[4], dl2[4];
+    const double tm = ti + h2, te = ti + h;
+    const TP tmP = tiP + h2P, teP = tiP + hP;
     InputPenalty<TP> ipm, ip1;
     if (foot) {
-      ipm = input_penalty<TP>((i + 0.5) * h, TP((i + 0.5) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
-      ip1 = input_penalty<TP>((i + 1.0) * h, TP((i + 1.0) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      ipm = input_penalty<TP>(tm, tmP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      ip1 = input_penalty<TP>(te, teP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
     // FP32 copy of the stage recursion, anchored on the FP64 state (FP32-Phi mode)
     const TP thA = TP(th), omA = TP(om), pyA = TP(py), vyA = TP(vy);
@@ -159,14 +165,15 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const double cj = rk_c(j), wj = rk_w(j);
-      const double tj = (i + cj) * h;
-      const double dth = cj * h * kth;
+      const double wj = rk_w(j);
+      const double cjh = (j == 0) ? 0.0 : (j == 3 ? h : h2);
+      const double tj = (j == 0) ? ti : (j == 3 ? te : tm);
+      const double dth = cjh * kth;
       const double ths = th + dth;
-      const double ws = (j == 0) ? om : fma(cj * h, kom, om);
+      const double ws = (j == 0) ? om : fma(cjh, kom, om);
       double sn, cs;
       if (j == 0) { sn = sth; cs = cth; }
-      else sincos_step(ths, sth, cth, dth, sn, cs);
+      else sincos_step(ths, sth, cth, dth, amask, sn, cs);
       const double P = fma(tj, dP, PL), Q = fma(tj, dQ, QL), T = fma(tj, dT, TL);
       const double wdot = fma(cs, P, fma(-sn, Q, T));
       kth = sd * ws;
@@ -175,8 +182,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       aom_ = fma(wj, kom, aom_);
       double pys = 0.0, vs = 0.0;
       if (foot) {
-        pys = (j == 0) ? py : fma(cj * h, kpy, py);
-        vs = (j == 0) ? vy : fma(cj * h, kvy, vy);
+        pys = (j == 0) ? py : fma(cjh, kpy, py);
+        vs = (j == 0) ? vy : fma(cjh, kvy, vy);
         const double ay = fma(tj, dAy, AyL) - g;
         kpy = sd * vs;
         kvy = sd * ay;
@@ -188,18 +195,18 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
       }
       // stage data for the tangent recursion
-      const TP cjh = TP(cj * h);
+      const TP cjhT = cjhP[j];
       TP csP, snP, PP, QP, TT, wsP, pysP = TP(0), vsP = TP(0);
       if constexpr (F32) {
-        const TP tP = TP(tj);
-        const TP thsP = (j == 0) ? thA : thA + cjh * kthA;
-        wsP = (j == 0) ? omA : omA + cjh * komA;
+        const TP tP = (j == 0) ? tiP : (j == 3 ? teP : tmP);
+        const TP thsP = (j == 0) ? thA : thA + cjhT * kthA;
+        wsP = (j == 0) ? omA : omA + cjhT * komA;
         sincosf(thsP, &snP, &csP);
         PP = PLP + tP * dPP; QP = QLP + tP * dQP; TT = TLP + tP * dTP;
         tau[j] = tP;
         if (foot) {
-          pysP = (j == 0) ? pyA : pyA + cjh * kpyA;
-          vsP = (j == 0) ? vyA : vyA + cjh * kvyA;
+          pysP = (j == 0) ? pyA : pyA + cjhT * kpyA;
+          vsP = (j == 0) ? vyA : vyA + cjhT * kvyA;
         }
       } else {
         csP = cs; snP = sn; PP = P; QP = Q; TT = T; wsP = ws; pysP = pys; vsP = vs;
@@ -227,13 +234,15 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     const double Dth = h * ath_;
     {
       double s1, c1;
-      sincos_step(th + Dth, sth, cth, Dth, s1, c1);
+      sincos_step(th + Dth, sth, cth, Dth, amask, s1, c1);
       sth = s1;
       cth = c1;
     }
     th += Dth;
     om = fma(h, aom_, om);
     if (foot) { py = fma(h, apy, py); vy = fma(h, avy, vy); ip0 = ip1; }
+    ti = te;
+    tiP = teP;
 
     // ---- rotation tangents: 9 columns, 4 stages each ----
 #pragma unroll
@@ -242,7 +251,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       TP kT = TP(0), kW = TP(0), aT = TP(0), aW = TP(0), ya = TP(0);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const TP cjh = TP(rk_c(j) * h), wj = TP(rk_w(j));
+        const TP cjh = cjhP[j], wj = TP(rk_w(j));
         const TP Ts = (j == 0) ? T0 : T0 + cjh * kT;
         const TP Ws = (j == 0) ? W0 : W0 + cjh * kW;
         const TP wl = TP(1) - tau[j], wr = tau[j];
@@ -277,7 +286,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         TP kP = TP(0), kV = TP(0), aP = TP(0), aV = TP(0), ya = TP(0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const TP cjh = TP(rk_c(j) * h), wj = TP(rk_w(j));
+          const TP cjh = cjhP[j], wj = TP(rk_w(j));
           const TP Ps = (j == 0) ? P0 : P0 + cjh * kP;
           const TP Vs = (j == 0) ? V0 : V0 + cjh * kV;
           TP fP = TP(0), fV = TP(0);

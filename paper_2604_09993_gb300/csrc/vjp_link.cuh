@@ -31,6 +31,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
                                          double* __restrict__ part, double* __restrict__ ps,
                                          double* __restrict__ pL, unsigned* status) {
   constexpr bool F32 = std::is_same<TP, float>::value;
+  const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
   const int nb = M.nb;
   const double g = M.g;
@@ -70,8 +71,9 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   const TP muP = TP(mu), crxP = TP(crx), cryP = TP(cry);
   const TP PLP = TP(PL), dPP = TP(dP), QLP = TP(QL), dQP = TP(dQ), TLP = TP(TL), dTP = TP(dT);
   const TP AyLP = TP(AyL), dAyP = TP(dAy), gP = TP(g);
-  const double h = 1.0 / nsub;
-  const TP sdP = TP(sd), hP = TP(h);
+  const double h = 1.0 / nsub, h2 = 0.5 * h;
+  const TP sdP = TP(sd), hP = TP(h), h2P = TP(h2);
+  const TP cjhP[4] = {TP(0), h2P, h2P, hP};
 
   // ---- forward sweep: FP64 state and checkpoints ----
   double ck_th[MAXSUB_VJP], ck_om[MAXSUB_VJP], ck_s[MAXSUB_VJP], ck_c[MAXSUB_VJP];
@@ -85,29 +87,34 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   double Yom = 0.0;
   InputPenalty<TP> fp0, fpm, fp1;
   if (PEN_FWD) fp0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+  double ti = 0.0;  // tau at the substep start (running sum)
+  TP tiP = TP(0);
   for (int i = 0; i < nsub; ++i) {
     ck_th[i] = th; ck_om[i] = om; ck_s[i] = sth; ck_c[i] = cth;
     if (FOOT) { ck_py[i] = py; ck_vy[i] = vy; }
+    const double tm = ti + h2, te = ti + h;
     if (PEN_FWD) {
-      fpm = input_penalty<TP>((i + 0.5) * h, TP((i + 0.5) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
-      fp1 = input_penalty<TP>((i + 1.0) * h, TP((i + 1.0) * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      fpm = input_penalty<TP>(tm, tiP + h2P, sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      fp1 = input_penalty<TP>(te, tiP + hP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
     double kth = 0, kom = 0, ath = 0, aom = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const double cj = rk_c(j), wj = rk_w(j), tj = (i + cj) * h;
-      const double dth = cj * h * kth;
-      const double ws = (j == 0) ? om : fma(cj * h, kom, om);
+      const double wj = rk_w(j);
+      const double cjh = (j == 0) ? 0.0 : (j == 3 ? h : h2);
+      const double tj = (j == 0) ? ti : (j == 3 ? te : tm);
+      const double dth = cjh * kth;
+      const double ws = (j == 0) ? om : fma(cjh, kom, om);
       double sn, cs;
       if (j == 0) { sn = sth; cs = cth; }
-      else sincos_step(th + dth, sth, cth, dth, sn, cs);
+      else sincos_step(th + dth, sth, cth, dth, amask, sn, cs);
       const double wdot = fma(cs, fma(tj, dP, PL), fma(-sn, fma(tj, dQ, QL), fma(tj, dT, TL)));
       kth = sd * ws; kom = sd * wdot;
       ath = fma(wj, kth, ath); aom = fma(wj, kom, aom);
       if (FOOT) {
-        const double vs = (j == 0) ? vy : fma(cj * h, kvy, vy);
+        const double vs = (j == 0) ? vy : fma(cjh, kvy, vy);
         if (PEN_FWD) {
-          const double pys = (j == 0) ? py : fma(cj * h, kpy, py);
+          const double pys = (j == 0) ? py : fma(cjh, kpy, py);
           const InputPenalty<TP>& ipj = (j == 0) ? fp0 : (j == 3 ? fp1 : fpm);
           Yom = fma(h * wj, ipj.H + huber_value(-(pys + fma(sn, crx, cs * cry))), Yom);
         }
@@ -118,11 +125,13 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
     if (PEN_FWD) fp0 = fp1;
     const double Dth = h * ath;
     double s1, c1;
-    sincos_step(th + Dth, sth, cth, Dth, s1, c1);
+    sincos_step(th + Dth, sth, cth, Dth, amask, s1, c1);
     sth = s1; cth = c1;
     th += Dth;
     om = fma(h, aom, om);
     if (FOOT) { py = fma(h, apy, py); vy = fma(h, avy, vy); }
+    ti = te;
+    tiP = tiP + hP;
   }
 
   // cotangents of x~(1): w_k (+ rho on the penalty state)
@@ -140,14 +149,16 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   // FP64 adjoint, which takes the penalty quadrature here, last substep first)
   InputPenalty<TP> ipE;
   if (FOOT) ipE = input_penalty<TP, !F32>(1.0, TP(1), sd, sdP, mu, muP, cL, cD, cLP, cDP);
-  for (int i = nsub - 1; i >= 0; --i) {
+  double di = (double)(nsub - 1);
+  for (int i = nsub - 1; i >= 0; --i, di -= 1.0) {
     TP cs_[4], sn_[4], sath[4], oms[4], wdt[4], tau[4];
     TP gr[4], gp[4], vys[4], ays[4], om_pen[4], dl0[4], dl1[4], dl2[4];
+    const double tsb = di * h, tmb = tsb + h2, teb = tsb + h;  // substep start / midpoint / end
+    const TP tsP = TP(tsb), tmP = tsP + h2P, teP = tsP + hP;
     InputPenalty<TP> ipS, ipM;
     if (FOOT) {
-      ipM = input_penalty<TP, !F32>((i + 0.5) * h, TP((i + 0.5) * h), sd, sdP, mu, muP, cL, cD, cLP,
-                                    cDP);
-      ipS = input_penalty<TP, !F32>(i * h, TP(i * h), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      ipM = input_penalty<TP, !F32>(tmb, tmP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      ipS = input_penalty<TP, !F32>(tsb, tsP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
     {
       const double thc = ck_th[i], omc = ck_om[i], stc = ck_s[i], ctc = ck_c[i];
@@ -158,20 +169,22 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
       double kth = 0, kom = 0, kpy = 0, kvy = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const double cj = rk_c(j), wj = rk_w(j), tj = (i + cj) * h;
-        const TP cjh = TP(cj * h);
-        // FP64 stage state: needed for the penalty values (and for the FP64 adjoint)
+        const double wj = rk_w(j);
+        const double cjd = (j == 0) ? 0.0 : (j == 3 ? h : h2);
+        const double tj = (j == 0) ? tsb : (j == 3 ? teb : tmb);
+        const TP cjh = cjhP[j];
+        // FP64 stage state (FP64 adjoint only)
         double cs = ctc, sn = stc, P = 0, Q = 0, T = 0, ws = omc, wdot = 0, pys = pyc, vs = vyc;
         if (!F32) {
-          const double dth = cj * h * kth;
-          ws = (j == 0) ? omc : fma(cj * h, kom, omc);
-          if (j > 0) sincos_step(thc + dth, stc, ctc, dth, sn, cs);
+          const double dth = cjd * kth;
+          ws = (j == 0) ? omc : fma(cjd, kom, omc);
+          if (j > 0) sincos_step(thc + dth, stc, ctc, dth, amask, sn, cs);
           P = fma(tj, dP, PL); Q = fma(tj, dQ, QL); T = fma(tj, dT, TL);
           wdot = fma(cs, P, fma(-sn, Q, T));
           kth = sd * ws; kom = sd * wdot;
           if (FOOT) {
-            pys = (j == 0) ? pyc : fma(cj * h, kpy, pyc);
-            vs = (j == 0) ? vyc : fma(cj * h, kvy, vyc);
+            pys = (j == 0) ? pyc : fma(cjd, kpy, pyc);
+            vs = (j == 0) ? vyc : fma(cjd, kvy, vyc);
             kpy = sd * vs; kvy = sd * (fma(tj, dAy, AyL) - g);
             const double ry = fma(sn, crx, cs * cry);
             const InputPenalty<TP>& ipj = (j == 0) ? ipS : (j == 3 ? ipE : ipM);
@@ -183,7 +196,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
         }
         TP csP, snP, PP, QP, TT, wsP, pysP = TP(0), vsP = TP(0);
         if constexpr (F32) {
-          const TP tP = TP(tj);
+          const TP tP = (j == 0) ? tsP : (j == 3 ? teP : tmP);
           const TP thsP = (j == 0) ? thA : thA + cjh * kthA;
           wsP = (j == 0) ? omA : omA + cjh * komA;
           sincosf(thsP, &snP, &csP);

@@ -17,9 +17,11 @@ pytestmark = pytest.mark.gpu
 
 TUNES = [
     None,
-    {"warps_per_cta": 4, "ctas_per_sm": 0, "lpt_order": 1, "use_graph": 0},
-    {"warps_per_cta": 1, "ctas_per_sm": 8, "lpt_order": 0, "use_graph": 1},
-    {"warps_per_cta": 8, "ctas_per_sm": 1, "lpt_order": 1, "use_graph": 0},
+    {"warps_per_cta": 4, "ctas_per_sm": 0, "lpt_order": 1, "use_graph": 0, "occupancy": 0},
+    {"warps_per_cta": 1, "ctas_per_sm": 8, "lpt_order": 0, "use_graph": 1, "occupancy": 0},
+    {"warps_per_cta": 8, "ctas_per_sm": 1, "lpt_order": 1, "use_graph": 0, "occupancy": 0},
+    {"warps_per_cta": 4, "ctas_per_sm": 3, "lpt_order": 1, "use_graph": 1, "occupancy": 1},
+    {"warps_per_cta": 2, "ctas_per_sm": 0, "lpt_order": 1, "use_graph": 0, "occupancy": 2},
 ]
 
 
