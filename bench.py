@@ -54,8 +54,18 @@ DEFAULT_WORKLOAD = "cheetah7-sweep-4096x400x20"
 # 2*DFMA + DADD + DMUL of one launch / intervals of that launch), recorded in
 # profiles/; keyed by (robot, n_sub, kernel, precision).
 FLOPS_PER_INTERVAL = {
-    ("cheetah7", 20, "discretize", "fp32_phi"): 40_300,
-    ("cheetah7", 20, "vjp", "fp32_phi"): 45_400,
+    ("cheetah7", 20, "discretize", "fp32_phi"): 30_521,
+    ("cheetah7", 20, "vjp", "fp32_phi"): 31_566,
+    ("cheetah7", 20, "discretize", "fp64"): 126_397,
+    ("cheetah7", 20, "vjp", "fp64"): 87_665,
+}
+# DRAM bytes (read + write) per interval of each kernel from the same captures
+# (256 instances x 400 intervals; traffic scales with the intervals processed).
+DRAM_BYTES_PER_INTERVAL = {
+    ("cheetah7", 20, "discretize", "fp32_phi"): (380.4e6 + 1922.2e6) / 102400,
+    ("cheetah7", 20, "vjp", "fp32_phi"): (99.0e6 + 116.4e6) / 102400,
+    ("cheetah7", 20, "discretize", "fp64"): (376.0e6 + 3644.2e6) / 102400,
+    ("cheetah7", 20, "vjp", "fp64"): (581.0e6 + 750.8e6) / 102400,
 }
 
 
@@ -390,9 +400,12 @@ def run_ours(args):
     kname = {"discretize": "k_batch_disc" if spec["kind"] == "batch" else "k_discretize",
              "vjp": "k_batch_vjp" if spec["kind"] == "batch" else "k_vjp"}[dom]
     fpi = FLOPS_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec))
+    bpi = DRAM_BYTES_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec))
     roof = {"bound": "alu", "kernel": f"{kname}<{'float' if prec == 'fp32_phi' else 'double'}>",
             "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4), "peak_source": "derived FP64 pipe",
-            "launch_ms": kt * 1e3, "discretize_ms": kd * 1e3, "vjp_ms": kv * 1e3, "traffic": None}
+            "launch_ms": kt * 1e3, "discretize_ms": kd * 1e3, "vjp_ms": kv * 1e3,
+            "traffic": None if bpi is None else bpi * wl.intervals,
+            "traffic_source": None if bpi is None else "ncu dram bytes of a 102400-interval launch, scaled"}
     if fpi:
         ach = fpi * wl.intervals / kt / 1e12
         roof.update(achieved=ach, frac=ach / FP64_PEAK_TFLOPS)

@@ -161,6 +161,20 @@ __device__ __forceinline__ double rk_w(int j) {
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
+// Threads per CTA for the single-instance kernels: with few warps (small N)
+// one warp per CTA spreads them over separate SMs, each with its own FP64
+// units, which shortens the latency-bound critical path; otherwise 4 warps.
+inline int single_cta_threads(long warps) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms = n > 0 ? n : 1;
+  }
+  return warps < 4L * sms ? 32 : 128;
+}
+
 }  // namespace ciscvx
 
 // The opaque model handle of the C ABI.

@@ -52,7 +52,7 @@ cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int p
                               void* Bm, void* Bp, void* S, double* defect, double* penalty,
                               double* z, unsigned* status, cudaStream_t st) {
   const long warps = (long)((N + 31) / 32) * nb;
-  const int threads = 128;
+  const int threads = single_cta_threads(warps);
   const long blocks = (warps * 32 + threads - 1) / threads;
   if (prec == CISCVX_FP64)
     k_discretize<double><<<(unsigned)blocks, threads, 0, st>>>(

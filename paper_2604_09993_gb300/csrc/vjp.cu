@@ -11,7 +11,7 @@
 // Mapping as in the forward kernel: one warp = 32 intervals x one link.  Each
 // lane writes its link's rows of gX directly and its per-input partials (the
 // link's share of dL/du_L, dL/du_R), its share of dL/ds and of L to the
-// workspace; k_vjp_finish sums the partials in a fixed order (no atomics),
+// workspace; k_vjp_gu / k_vjp_gs / k_vjp_L sum the partials in a fixed order (no atomics),
 // including the node-layout sum dL/dU_k = (u_L part of interval k) + (u_R part
 // of interval k-1).
 #include "vjp_link.cuh"
@@ -147,13 +147,14 @@ cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, i
   (void)nxt;
   VjpWs ws = vjp_ws_split(ws_ptr, nb, nslot, N);
   const long warps = (long)((N + 31) / 32) * nb;
-  const long blocks = (warps * 32 + 127) / 128;
+  const int threads = single_cta_threads(warps);
+  const long blocks = (warps * 32 + threads - 1) / threads;
   if (prec == CISCVX_FP64)
-    k_vjp<double><<<(unsigned)blocks, 128, 0, st>>>(dM, N, nsub, layout, X, U, s, w, rho, gX, ws,
-                                                    status);
+    k_vjp<double><<<(unsigned)blocks, threads, 0, st>>>(dM, N, nsub, layout, X, U, s, w, rho, gX,
+                                                        ws, status);
   else
-    k_vjp<float><<<(unsigned)blocks, 128, 0, st>>>(dM, N, nsub, layout, X, U, s, w, rho, gX, ws,
-                                                   status);
+    k_vjp<float><<<(unsigned)blocks, threads, 0, st>>>(dM, N, nsub, layout, X, U, s, w, rho, gX,
+                                                       ws, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (nu > 0) {

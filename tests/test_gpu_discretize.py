@@ -156,3 +156,48 @@ def test_argument_errors(env):
         with pytest.raises(api.CiscvxError) as e:
             api.discretize(m, X, U, s, 4, prec)
         assert e.value.status == api.EUNSUPPORTED
+
+
+def _edge_robots():
+    rng = np.random.default_rng(12)
+    h = synth.hopper(rng).as_dict()
+    no_contact = dict(h, contact_body=np.zeros(0, dtype=np.int32), contact_rho=np.zeros((0, 2)),
+                      contact_mu=np.zeros(0))
+    lone = {"mass": np.array([1.7]), "inertia": np.array([0.05]),
+            "joint_parent": np.zeros(0, dtype=np.int32), "joint_child": np.zeros(0, dtype=np.int32),
+            "joint_rho_parent": np.zeros((0, 2)), "joint_rho_child": np.zeros((0, 2)),
+            "contact_body": np.zeros(0, dtype=np.int32), "contact_rho": np.zeros((0, 2)),
+            "contact_mu": np.zeros(0), "gravity": synth.GRAVITY}
+    return {"no_contact": no_contact, "lone_link": lone}
+
+
+@pytest.mark.parametrize("which", ["no_contact", "lone_link"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_models_without_contacts_or_inputs(env, which, precision):
+    """n_c = 0 (no penalty state) and n_u = 0 (no inputs at all, empty B blocks)."""
+    torch, oracle, api = env
+    R = _edge_robots()[which]
+    nb, nj = len(R["mass"]), len(R["joint_parent"])
+    nxt, nu = 6 * nb, 3 * nj
+    rng = np.random.default_rng(3)
+    N, n_sub = 37, 4
+    X = rng.uniform(-0.5, 0.5, (N + 1, nxt))
+    U = rng.standard_normal((N + 1, nu))
+    s = rng.uniform(0.05, 0.15, N)
+    dev = torch.device("cuda:0")
+    m = api.Model(R)
+    assert (m.nx, m.ny, m.nu) == (nxt, 0, nu)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    out = api.discretize(m, t(X), t(U), t(s), n_sub, precision)
+    api.sync_status(m)
+    got = {k: v.double().cpu().numpy() for k, v in out.items()}
+    ref = oracle.discretize(R, X, U, s, n_sub)
+    _check(got, ref, precision)
+    w = rng.standard_normal((N, nxt))
+    gX, gU, gs, L = api.discretize_vjp(m, t(X), t(U), t(s), t(w), None, n_sub, precision)
+    rX, rU, rs, rL = oracle.vjp(R, X, U, s, w, np.zeros((N, 0)), n_sub)
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    assert block_err(gX.cpu().numpy(), rX) <= tol
+    assert block_err(gU.cpu().numpy(), rU) <= tol
+    assert block_err(gs.cpu().numpy(), rs) <= tol
+    assert abs(float(L) - rL) <= tol * max(1.0, abs(rL))
