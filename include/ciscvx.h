@@ -313,6 +313,30 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_
 ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
                                     void* stream, ciscvx_tune* chosen);
 
+/* End-to-end run on HOST buffers, pipelined: the instances are split into
+ * n_chunks consecutive chunks of balanced cost; for each chunk the inputs are
+ * copied host -> device, the chunk is linearized (and its VJP taken if
+ * host_vjp is not NULL), and its outputs are copied device -> host, on three
+ * plan-owned streams so that one chunk's copies overlap its neighbours'
+ * compute.  The call is asynchronous: `stream` waits for the last copy.
+ *   host: packed host arrays in the layout of ciscvx_batch_io (inputs X, U, s;
+ *     outputs A, Bm, Bp, S, defect, penalty); pinned memory lets the copies
+ *     overlap (pageable memory still gives correct results).
+ *   dev: device buffers of the full packed sizes, used as staging.
+ *   host_vjp / dev_vjp: NULL, or the VJP cotangents (w, rho: host inputs) and
+ *     gradients (gX, gU, gs, L: host outputs) with their device buffers; their
+ *     X, U, s fields are ignored (host/dev are used).  workspace as for
+ *     ciscvx_batch_discretize_vjp.
+ * The first call with a new n_chunks builds the chunked work tables and
+ * streams (device allocation); later calls with the same n_chunks allocate
+ * nothing.  Errors: EINVAL (null buffers, n_chunks outside [1, n_inst], short
+ * workspace), EUNSUPPORTED (VJP with n_sub > CISCVX_MAX_VJP_SUBSTEPS), ECUDA. */
+ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
+                                    const ciscvx_batch_io* host, const ciscvx_batch_io* dev,
+                                    const ciscvx_batch_vjp_io* host_vjp,
+                                    const ciscvx_batch_vjp_io* dev_vjp, void* workspace,
+                                    size_t ws_bytes, void* stream);
+
 /* As ciscvx_sync_status, for the plan's status word. */
 ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* plan, void* stream);
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "ciscvx_batch_plan_create", "ciscvx_batch_plan_destroy", "ciscvx_batch_sizes_get",
     "ciscvx_batch_offsets", "ciscvx_batch_get_tune", "ciscvx_batch_discretize",
     "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp", "ciscvx_batch_autotune",
-    "ciscvx_batch_sync_status",
+    "ciscvx_batch_sync_status", "ciscvx_batch_run_host",
 )
 
 
@@ -124,6 +124,9 @@ def load(path: str | None = None):
     lib.ciscvx_batch_discretize_vjp.argtypes = [_vp, P(_BatchVjpIO), _vp, ctypes.c_size_t, _vp]
     lib.ciscvx_batch_autotune.argtypes = [_vp, P(_BatchIO), _vp, P(Tune)]
     lib.ciscvx_batch_sync_status.argtypes = [_vp, _vp]
+    lib.ciscvx_batch_run_host.argtypes = [_vp, ctypes.c_int, P(_BatchIO), P(_BatchIO), P(_BatchVjpIO),
+                                          P(_BatchVjpIO), _vp, ctypes.c_size_t, _vp]
+    lib.ciscvx_batch_run_host.restype = ctypes.c_int
     for f in ("ciscvx_model_create", "ciscvx_model_dims", "ciscvx_workspace_size",
               "ciscvx_discretize", "ciscvx_discretize_vjp", "ciscvx_sync_status",
               "ciscvx_discretize_vjp_static", "ciscvx_batch_plan_create", "ciscvx_batch_sizes_get",
@@ -431,6 +434,30 @@ class BatchPlan:
                                                   workspace.numel() * workspace.element_size(),
                                                   _stream()))
         return out
+
+    def run_host(self, host_in, host_out, dev_in, dev_out, n_chunks=8, host_vjp=None, dev_vjp=None,
+                 workspace=None):
+        """ciscvx_batch_run_host: pipelined H2D -> linearize (-> VJP) -> D2H over chunks.
+
+        host_in / dev_in: dicts X, U, s (host pinned / device tensors); host_out /
+        dev_out: dicts A, Bm, Bp, S, defect, penalty; host_vjp / dev_vjp: dicts
+        w, rho, gX, gU, gs, L (optional).  Asynchronous on the current stream."""
+        p = lambda d, k: None if d is None or d.get(k) is None else d[k].data_ptr()  # noqa: E731
+        hio = _BatchIO(*[p(host_in, "X"), p(host_in, "U"), p(host_in, "s")] +
+                       [p(host_out, k) for k in ("A", "Bm", "Bp", "S", "defect", "penalty")])
+        dio = _BatchIO(*[p(dev_in, "X"), p(dev_in, "U"), p(dev_in, "s")] +
+                       [p(dev_out, k) for k in ("A", "Bm", "Bp", "S", "defect", "penalty")])
+        hv = dv = None
+        ws_ptr, ws_bytes = None, 0
+        if host_vjp is not None:
+            keys = ("X", "U", "s", "w", "rho", "gX", "gU", "gs", "L")
+            hv = _BatchVjpIO(*[p(host_vjp, k) for k in keys])
+            dv = _BatchVjpIO(*[p(dev_vjp, k) for k in keys])
+            ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+        _check(load().ciscvx_batch_run_host(self._h, int(n_chunks), ctypes.byref(hio), ctypes.byref(dio),
+                                            ctypes.byref(hv) if hv else None,
+                                            ctypes.byref(dv) if dv else None, ws_ptr, ws_bytes,
+                                            _stream()))
 
     def sync_status(self):
         _check(load().ciscvx_batch_sync_status(self._h, _stream()))

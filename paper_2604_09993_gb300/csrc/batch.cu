@@ -200,6 +200,20 @@ __global__ void __launch_bounds__(FINB) k_batch_vjp_finish(const DevModel* const
 
 using namespace ciscvx;
 
+// Work tables for the instances split into consecutive chunks (the pipelined
+// host executor runs chunk by chunk; one chunk = the whole batch otherwise).
+struct ChunkTables {
+  int K = 0;                        // number of chunks these tables describe
+  int2* d_entries = nullptr;
+  int4* d_groups = nullptr;
+  int2* d_items_lpt = nullptr;
+  int2* d_items_nat = nullptr;
+  std::vector<int> item_off;        // [K+1] items of chunk c: [item_off[c], item_off[c+1])
+  std::vector<int> inst_off;        // [K+1] instances of chunk c
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> ev;      // 1 start + 3 per chunk
+};
+
 struct ciscvx_batch_plan {
   int n_inst = 0, n_models = 0, prec = 0, layout = 0, device = 0, sm_count = 0, max_nsub = 0;
   bool all_nu0 = true, all_nc0 = true;
@@ -220,6 +234,7 @@ struct ciscvx_batch_plan {
   int* d_queue = nullptr;  // [0]: discretize, [1]: vjp
   unsigned* d_status = nullptr;
   ciscvx_tune tune{4, 2, 1, 1, 0};
+  ChunkTables chunks;  // tables of the last chunk count used by ciscvx_batch_run_host
   // graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -239,8 +254,21 @@ bool tune_ok(const ciscvx_tune& t) {
          (t.occupancy == 0 || t.warps_per_cta <= 4);
 }
 
+void free_chunks(ChunkTables& t) {
+  cudaFree(t.d_entries);
+  cudaFree(t.d_groups);
+  cudaFree(t.d_items_lpt);
+  cudaFree(t.d_items_nat);
+  for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+  if (t.s_in) cudaStreamDestroy(t.s_in);
+  if (t.s_comp) cudaStreamDestroy(t.s_comp);
+  if (t.s_out) cudaStreamDestroy(t.s_out);
+  t = ChunkTables();
+}
+
 void free_plan(ciscvx_batch_plan* p) {
   if (!p) return;
+  free_chunks(p->chunks);
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->cap) cudaStreamDestroy(p->cap);
   cudaFree(p->d_models);
@@ -263,6 +291,58 @@ cudaError_t upload(T** dst, const std::vector<T>& v) {
   return e;
 }
 
+// Host work decomposition of instances [inst_off[c], inst_off[c+1]) for each
+// chunk c: bucket (model, n_sub) -> entries (instance, k) -> groups of 32 ->
+// items (group x link), items of each chunk contiguous, in cost order (lpt) or
+// in bucket order (nat).  Also returns the tuning key of the whole batch.
+struct HostDecomp {
+  std::vector<int2> entries, items_lpt, items_nat;
+  std::vector<int4> groups;
+  std::vector<int> item_off;
+  std::string key;
+};
+
+std::string model_signature(const DevModel& M);
+
+HostDecomp decompose(const ciscvx_batch_plan* p, const std::vector<int>& inst_off) {
+  HostDecomp d;
+  const int K = (int)inst_off.size() - 1;
+  d.item_off.push_back(0);
+  for (int c = 0; c < K; ++c) {
+    std::map<std::pair<int, int>, std::vector<int>> buckets;
+    for (int i = inst_off[c]; i < inst_off[c + 1]; ++i)
+      buckets[{p->inst[i].model, p->inst[i].nsub}].push_back(i);
+    std::vector<std::pair<long long, int2>> costed;
+    for (auto& kv : buckets) {
+      const int m = kv.first.first, ns = kv.first.second;
+      const DevModel& M = p->models[m]->host;
+      const int first = (int)d.entries.size();
+      for (int i : kv.second)
+        for (int k = 0; k < p->inst[i].N; ++k) d.entries.push_back(make_int2(i, k));
+      const int cnt = (int)d.entries.size() - first;
+      for (int g0 = 0; g0 < cnt; g0 += 32) {
+        const int gi = (int)d.groups.size();
+        d.groups.push_back(make_int4(m, ns, first + g0, std::min(32, cnt - g0)));
+        for (int b = 0; b < M.nb; ++b)
+          costed.push_back({(long long)ns * (M.body[b].contact >= 0 ? 2 : 1), make_int2(gi, b)});
+      }
+      if (K == 1) {
+        int lg = 0;
+        while ((1 << lg) < cnt) ++lg;
+        d.key += model_signature(M) + "@" + std::to_string(ns) + "x2^" + std::to_string(lg) + ";";
+      }
+    }
+    for (auto& x : costed) d.items_nat.push_back(x.second);
+    std::stable_sort(costed.begin(), costed.end(),
+                     [](const std::pair<long long, int2>& a, const std::pair<long long, int2>& b) {
+                       return a.first > b.first;
+                     });
+    for (auto& x : costed) d.items_lpt.push_back(x.second);
+    d.item_off.push_back((int)d.items_lpt.size());
+  }
+  return d;
+}
+
 BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot) {
   BatchCommon c;
   c.models = p->d_models;
@@ -278,24 +358,35 @@ BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot) {
   return c;
 }
 
-void grid_of(const ciscvx_batch_plan* p, unsigned& blocks, unsigned& threads) {
+// BatchCommon for chunk c of the chunked tables.
+BatchCommon common_chunk(const ciscvx_batch_plan* p, int queue_slot, int c) {
+  BatchCommon b = common_of(p, queue_slot);
+  const ChunkTables& t = p->chunks;
+  b.entries = t.d_entries;
+  b.groups = t.d_groups;
+  b.items = (p->tune.lpt_order ? t.d_items_lpt : t.d_items_nat) + t.item_off[c];
+  b.n_items = t.item_off[c + 1] - t.item_off[c];
+  return b;
+}
+
+void grid_for(const ciscvx_batch_plan* p, int n_items, unsigned& blocks, unsigned& threads) {
   threads = 32u * (unsigned)p->tune.warps_per_cta;
   if (p->tune.ctas_per_sm > 0) {
     blocks = (unsigned)(p->sm_count * p->tune.ctas_per_sm);
   } else {
-    blocks = (unsigned)((p->n_items + p->tune.warps_per_cta - 1) / p->tune.warps_per_cta);
+    blocks = (unsigned)((n_items + p->tune.warps_per_cta - 1) / p->tune.warps_per_cta);
   }
   if (blocks == 0) blocks = 1;
 }
 
-cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStream_t st) {
-  BatchCommon c = common_of(p, 0);
+cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_io* io,
+                          cudaStream_t st) {
   if (c.persistent) {
-    cudaError_t e = cudaMemsetAsync(p->d_queue, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(c.queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
   }
   unsigned blocks, threads;
-  grid_of(p, blocks, threads);
+  grid_for(p, c.n_items, blocks, threads);
 #define CISCVX_DISC(TP, OCC)                                                                  \
   k_batch_disc<TP, OCC><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (TP*)io->A,        \
                                                     (TP*)io->Bm, (TP*)io->Bp, (TP*)io->S,       \
@@ -312,6 +403,41 @@ cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStr
   }
 #undef CISCVX_DISC
   return cudaGetLastError();
+}
+
+cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStream_t st) {
+  return launch_disc_c(p, common_of(p, 0), io, st);
+}
+
+// VJP kernel over the items of `c`, then the per-instance finish over
+// instances [i0, i1) (their partials are complete once the kernel is done).
+cudaError_t launch_vjp_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_vjp_io* io,
+                         double* part, double* ps, double* pL, int i0, int i1, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  unsigned blocks, threads;
+  grid_for(p, c.n_items, blocks, threads);
+#define CISCVX_VJP(TP, OCC)                                                                   \
+  k_batch_vjp<TP, OCC><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX, \
+                                                  part, ps, pL)
+  const int occ = p->tune.occupancy;
+  if (p->prec == CISCVX_FP64) {
+    if (occ == 1) CISCVX_VJP(double, 1);
+    else if (occ == 2) CISCVX_VJP(double, 2);
+    else CISCVX_VJP(double, 0);
+  } else {
+    if (occ == 1) CISCVX_VJP(float, 1);
+    else if (occ == 2) CISCVX_VJP(float, 2);
+    else CISCVX_VJP(float, 0);
+  }
+#undef CISCVX_VJP
+  e = cudaGetLastError();
+  if (e == cudaSuccess && i1 > i0)
+    k_batch_vjp_finish<<<i1 - i0, FINB, 0, s>>>(p->d_models, p->d_inst + i0, p->layout, part, ps,
+                                                pL, io->gU, io->gs, io->L ? io->L + i0 : nullptr);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
 }
 
 bool same_io(const ciscvx_batch_io& a, const ciscvx_batch_io& b) {
@@ -410,38 +536,14 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   }
   z.L = (size_t)n_inst;
 
-  // buckets (model, n_sub) -> entries -> groups of 32 -> items (group x link)
-  std::map<std::pair<int, int>, std::vector<int>> buckets;
-  for (int i = 0; i < n_inst; ++i) buckets[{model_idx[i], n_sub[i]}].push_back(i);
-  std::vector<int2> entries;
-  std::vector<int4> groups;
-  std::vector<std::pair<long long, int2>> costed;
-  std::string key = std::to_string(precision) + "|" + std::to_string(layout) + "|";
-  for (auto& kv : buckets) {
-    const int m = kv.first.first, ns = kv.first.second;
-    const DevModel& M = models[m]->host;
-    const int first = (int)entries.size();
-    for (int i : kv.second)
-      for (int k = 0; k < N[i]; ++k) entries.push_back(make_int2(i, k));
-    const int cnt = (int)entries.size() - first;
-    for (int g0 = 0; g0 < cnt; g0 += 32) {
-      const int gi = (int)groups.size();
-      groups.push_back(make_int4(m, ns, first + g0, std::min(32, cnt - g0)));
-      for (int b = 0; b < M.nb; ++b)
-        costed.push_back({(long long)ns * (M.body[b].contact >= 0 ? 2 : 1), make_int2(gi, b)});
-    }
-    int lg = 0;
-    while ((1 << lg) < cnt) ++lg;
-    key += model_signature(M) + "@" + std::to_string(ns) + "x2^" + std::to_string(lg) + ";";
-  }
-  p->key = key;
-  p->n_items = (int)costed.size();
-  for (auto& c : costed) p->items_nat.push_back(c.second);
-  std::stable_sort(costed.begin(), costed.end(),
-                   [](const std::pair<long long, int2>& a, const std::pair<long long, int2>& b) {
-                     return a.first > b.first;
-                   });
-  for (auto& c : costed) p->items_lpt.push_back(c.second);
+  // work decomposition of the whole batch (one chunk)
+  HostDecomp dec = decompose(p, {0, n_inst});
+  p->key = std::to_string(precision) + "|" + std::to_string(layout) + "|" + dec.key;
+  p->n_items = (int)dec.items_lpt.size();
+  p->items_lpt = dec.items_lpt;
+  p->items_nat = dec.items_nat;
+  const std::vector<int2>& entries = dec.entries;
+  const std::vector<int4>& groups = dec.groups;
 
   std::vector<const DevModel*> dm(n_models);
   for (int m = 0; m < n_models; ++m) dm[m] = models[m]->dev;
@@ -546,31 +648,7 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_bat
   double* part = (double*)workspace;
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
-  BatchCommon c = common_of(p, 1);
-  cudaError_t e = cudaSuccess;
-  if (c.persistent) e = cudaMemsetAsync(p->d_queue + 1, 0, sizeof(int), s);
-  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "queue reset: %s", cudaGetErrorString(e));
-  unsigned blocks, threads;
-  grid_of(p, blocks, threads);
-#define CISCVX_VJP(TP, OCC)                                                                   \
-  k_batch_vjp<TP, OCC><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX, \
-                                                  part, ps, pL)
-  const int occ = p->tune.occupancy;
-  if (p->prec == CISCVX_FP64) {
-    if (occ == 1) CISCVX_VJP(double, 1);
-    else if (occ == 2) CISCVX_VJP(double, 2);
-    else CISCVX_VJP(double, 0);
-  } else {
-    if (occ == 1) CISCVX_VJP(float, 1);
-    else if (occ == 2) CISCVX_VJP(float, 2);
-    else CISCVX_VJP(float, 0);
-  }
-#undef CISCVX_VJP
-  e = cudaGetLastError();
-  if (e == cudaSuccess)
-    k_batch_vjp_finish<<<p->n_inst, FINB, 0, s>>>(p->d_models, p->d_inst, p->layout, part, ps, pL,
-                                                  io->gU, io->gs, io->L);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaError_t e = launch_vjp_c(p, common_of(p, 1), io, part, ps, pL, 0, p->n_inst, s);
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch vjp launch: %s", cudaGetErrorString(e));
   return CISCVX_OK;
 }
@@ -628,6 +706,150 @@ ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* p, const ciscvx_batch_io*
     g_tune_cache[key] = bt;
   }
   if (chosen) *chosen = bt;
+  return CISCVX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Element offsets of instance i in the packed buffers (i == n_inst: the totals).
+ciscvx_batch_sizes offsets_of(const ciscvx_batch_plan* p, int i) {
+  if (i >= p->n_inst) return p->sizes;
+  const DevInst& I = p->inst[i];
+  ciscvx_batch_sizes o;
+  o.X = (size_t)I.x; o.U = (size_t)I.u; o.s = (size_t)I.s; o.A = (size_t)I.a; o.B = (size_t)I.b;
+  o.S = (size_t)I.v; o.defect = (size_t)I.v; o.penalty = (size_t)I.p; o.L = (size_t)i;
+  return o;
+}
+
+// Chunk tables for K chunks of consecutive instances with balanced estimated
+// cost (N * n_sub * links), built once per K and kept in the plan.
+cudaError_t ensure_chunks(ciscvx_batch_plan* p, int K) {
+  ChunkTables& t = p->chunks;
+  if (t.K == K) return cudaSuccess;
+  free_chunks(t);
+  std::vector<double> cum(p->n_inst + 1, 0.0);
+  for (int i = 0; i < p->n_inst; ++i)
+    cum[i + 1] = cum[i] + (double)p->inst[i].N * p->inst[i].nsub * p->models[p->inst[i].model]->host.nb;
+  std::vector<int> off(K + 1, 0);
+  off[K] = p->n_inst;
+  for (int c = 1; c < K; ++c) {
+    const double target = cum[p->n_inst] * c / K;
+    int i = (int)(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
+    off[c] = std::min(std::max(i, off[c - 1] + 1), p->n_inst - (K - c));
+  }
+  HostDecomp d = decompose(p, off);
+  cudaError_t e = upload(&t.d_entries, d.entries);
+  if (e == cudaSuccess) e = upload(&t.d_groups, d.groups);
+  if (e == cudaSuccess) e = upload(&t.d_items_lpt, d.items_lpt);
+  if (e == cudaSuccess) e = upload(&t.d_items_nat, d.items_nat);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_out, cudaStreamNonBlocking);
+  for (int k = 0; k < 1 + 3 * K && e == cudaSuccess; ++k) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) t.ev.push_back(ev);
+  }
+  if (e != cudaSuccess) { free_chunks(t); return e; }
+  t.K = K;
+  t.item_off = d.item_off;
+  t.inst_off = off;
+  return cudaSuccess;
+}
+
+cudaError_t copy_range(void* dst, const void* src, size_t elem, size_t lo, size_t hi,
+                       cudaMemcpyKind kind, cudaStream_t st) {
+  if (hi <= lo || !dst || !src) return cudaSuccess;
+  return cudaMemcpyAsync((char*)dst + lo * elem, (const char*)src + lo * elem, (hi - lo) * elem,
+                         kind, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ciscvx_batch_io* host,
+                                    const ciscvx_batch_io* dev, const ciscvx_batch_vjp_io* host_vjp,
+                                    const ciscvx_batch_vjp_io* dev_vjp, void* workspace,
+                                    size_t ws_bytes, void* stream) {
+  ciscvx_status st = check_io(p, dev);
+  if (st != CISCVX_OK) return st;
+  if (!host || !host->X || !host->s || !host->A || !host->S || !host->defect)
+    return set_error(CISCVX_EINVAL, "null required host buffer");
+  if (!p->all_nu0 && (!host->U || !host->Bm || !host->Bp)) return set_error(CISCVX_EINVAL, "null host U / Bm / Bp");
+  if (!p->all_nc0 && !host->penalty) return set_error(CISCVX_EINVAL, "null host penalty");
+  if (n_chunks < 1 || n_chunks > p->n_inst)
+    return set_error(CISCVX_EINVAL, "n_chunks must be in [1, %d]", p->n_inst);
+  const bool vjp = host_vjp != nullptr;
+  double *part = nullptr, *ps = nullptr, *pL = nullptr;
+  if (vjp) {
+    if (!dev_vjp || !host_vjp->w || !host_vjp->gX || !host_vjp->gs || !dev_vjp->w || !dev_vjp->gX ||
+        !dev_vjp->gs)
+      return set_error(CISCVX_EINVAL, "null VJP buffer");
+    if (!p->all_nu0 && (!host_vjp->gU || !dev_vjp->gU)) return set_error(CISCVX_EINVAL, "null gU");
+    if (!p->all_nc0 && (!host_vjp->rho || !dev_vjp->rho)) return set_error(CISCVX_EINVAL, "null rho");
+    if (p->max_nsub > MAXSUB_VJP)
+      return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps", MAXSUB_VJP);
+    const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 15) != 0)
+      return set_error(CISCVX_EINVAL, "16-byte aligned workspace of %zu bytes needed", need);
+    part = (double*)workspace;
+    ps = part + p->part_total;
+    pL = ps + p->pb_total;
+  }
+  cudaError_t e = ensure_chunks(p, n_chunks);
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "chunk tables: %s", cudaGetErrorString(e));
+  ChunkTables& t = p->chunks;
+  cudaStream_t user = (cudaStream_t)stream;
+  const size_t phi = (p->prec == CISCVX_FP64) ? sizeof(double) : sizeof(float);
+  const size_t d8 = sizeof(double);
+  // the device-side VJP io: inputs/outputs in the device buffers
+  ciscvx_batch_vjp_io dv{};
+  if (vjp) {
+    dv = *dev_vjp;
+    dv.X = dev->X; dv.U = dev->U; dv.s = dev->s;
+  }
+  e = cudaEventRecord(t.ev[0], user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_in, t.ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_comp, t.ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_out, t.ev[0], 0);
+  for (int c = 0; c < n_chunks && e == cudaSuccess; ++c) {
+    const int i0 = t.inst_off[c], i1 = t.inst_off[c + 1];
+    const ciscvx_batch_sizes a = offsets_of(p, i0), b = offsets_of(p, i1);
+    cudaEvent_t ev_in = t.ev[1 + 3 * c], ev_comp = t.ev[2 + 3 * c], ev_out = t.ev[3 + 3 * c];
+    // host -> device: this chunk's inputs
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+    e = copy_range((void*)dev->X, host->X, d8, a.X, b.X, h2d, t.s_in);
+    if (e == cudaSuccess) e = copy_range((void*)dev->U, host->U, d8, a.U, b.U, h2d, t.s_in);
+    if (e == cudaSuccess) e = copy_range((void*)dev->s, host->s, d8, a.s, b.s, h2d, t.s_in);
+    if (vjp && e == cudaSuccess) e = copy_range((void*)dev_vjp->w, host_vjp->w, d8, a.defect, b.defect, h2d, t.s_in);
+    if (vjp && e == cudaSuccess) e = copy_range((void*)dev_vjp->rho, host_vjp->rho, d8, a.penalty, b.penalty, h2d, t.s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, t.s_in);
+    // compute
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_comp, ev_in, 0);
+    if (e == cudaSuccess) e = launch_disc_c(p, common_chunk(p, 0, c), dev, t.s_comp);
+    if (vjp && e == cudaSuccess) e = launch_vjp_c(p, common_chunk(p, 1, c), &dv, part, ps, pL, i0, i1, t.s_comp);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_comp, t.s_comp);
+    // device -> host: this chunk's outputs
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_out, ev_comp, 0);
+    if (e == cudaSuccess) e = copy_range(host->A, dev->A, phi, a.A, b.A, d2h, t.s_out);
+    if (e == cudaSuccess) e = copy_range(host->Bm, dev->Bm, phi, a.B, b.B, d2h, t.s_out);
+    if (e == cudaSuccess) e = copy_range(host->Bp, dev->Bp, phi, a.B, b.B, d2h, t.s_out);
+    if (e == cudaSuccess) e = copy_range(host->S, dev->S, phi, a.S, b.S, d2h, t.s_out);
+    if (e == cudaSuccess) e = copy_range(host->defect, dev->defect, d8, a.defect, b.defect, d2h, t.s_out);
+    if (e == cudaSuccess) e = copy_range(host->penalty, dev->penalty, d8, a.penalty, b.penalty, d2h, t.s_out);
+    if (vjp) {
+      if (e == cudaSuccess) e = copy_range(host_vjp->gX, dev_vjp->gX, d8, a.X, b.X, d2h, t.s_out);
+      if (e == cudaSuccess) e = copy_range(host_vjp->gU, dev_vjp->gU, d8, a.U, b.U, d2h, t.s_out);
+      if (e == cudaSuccess) e = copy_range(host_vjp->gs, dev_vjp->gs, d8, a.s, b.s, d2h, t.s_out);
+      if (e == cudaSuccess) e = copy_range(host_vjp->L, dev_vjp->L, d8, a.L, b.L, d2h, t.s_out);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out, t.s_out);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, t.ev[3 * n_chunks], 0);
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "pipelined run: %s", cudaGetErrorString(e));
   return CISCVX_OK;
 }
 

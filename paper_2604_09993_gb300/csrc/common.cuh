@@ -154,6 +154,32 @@ __device__ __forceinline__ void sincos_step(double th, double s0, double c0, dou
   if (!rotate_small(s0, c0, d, short_tier, s, c)) sincos(th, &s, &c);
 }
 
+// Zero `count` elements starting at each active lane's own pointer `base`,
+// with the lanes of `active` writing every chunk together (consecutive lanes
+// write consecutive 16-byte vectors when the chunk is 16-byte aligned and a
+// whole number of vectors long, else consecutive elements).  A __syncwarp
+// after it orders these writes before the lanes' own writes to the same rows.
+template <typename T>
+__device__ __forceinline__ void warp_zero_chunks(T* base, int count, unsigned active) {
+  const int lane = threadIdx.x & 31;
+  const int rank = __popc(active & ((1u << lane) - 1u));  // position among active lanes
+  const int nact = __popc(active);
+  unsigned m = active;
+  while (m) {
+    const int t = __ffs(m) - 1;
+    m &= m - 1;
+    T* p = (T*)__shfl_sync(active, (unsigned long long)base, t);
+    const size_t bytes = (size_t)count * sizeof(T);
+    if ((((size_t)p) & 15) == 0 && (bytes & 15) == 0) {
+      float4* v = (float4*)p;
+      const int nv = (int)(bytes >> 4);
+      for (int i = rank; i < nv; i += nact) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int i = rank; i < count; i += nact) p[i] = T(0);
+    }
+  }
+}
+
 __device__ __forceinline__ double rk_c(int j) { return j == 0 ? 0.0 : (j == 3 ? 1.0 : 0.5); }
 __device__ __forceinline__ double rk_w(int j) {
   return (j == 0 || j == 3) ? (1.0 / 6.0) : (2.0 / 6.0);

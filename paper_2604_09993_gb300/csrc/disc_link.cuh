@@ -315,12 +315,27 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   }
 
   // ------------------------------------------------------------ outputs ---
-  const TP one = TP(1), zero = TP(0);
+  const TP one = TP(1);
   const TP sdT = TP(sd), s2_3 = TP(sd * sd / 3.0), s2_6 = TP(sd * sd / 6.0), s_2 = TP(0.5 * sd);
-  // A: zero this link's rows, then the structural entries
-  TP* a1 = A + (size_t)rpx * nxt;
-  TP* a2 = A + (size_t)rvx * nxt;
-  for (int c = 0; c < 3 * nxt; ++c) { a1[c] = zero; a2[c] = zero; }
+  // Zero this link's rows of A, B-, B+ (and the contact's row) cooperatively,
+  // then write the structural entries.
+  warp_zero_chunks(A + (size_t)rpx * nxt, 3 * nxt, amask);
+  warp_zero_chunks(A + (size_t)rvx * nxt, 3 * nxt, amask);
+  if (nu > 0) {
+    warp_zero_chunks(Bm + (size_t)rpx * nu, 3 * nu, amask);
+    warp_zero_chunks(Bm + (size_t)rvx * nu, 3 * nu, amask);
+    warp_zero_chunks(Bp + (size_t)rpx * nu, 3 * nu, amask);
+    warp_zero_chunks(Bp + (size_t)rvx * nu, 3 * nu, amask);
+  }
+  if (foot) {
+    const int ry = 6 * nb + B.contact;
+    warp_zero_chunks(A + (size_t)ry * nxt, nxt, amask);
+    if (nu > 0) {
+      warp_zero_chunks(Bm + (size_t)ry * nu, nu, amask);
+      warp_zero_chunks(Bp + (size_t)ry * nu, nu, amask);
+    }
+  }
+  __syncwarp(amask);
   A[(size_t)rpx * nxt + rpx] = one; A[(size_t)rpx * nxt + rvx] = sdT;
   A[(size_t)rpy * nxt + rpy] = one; A[(size_t)rpy * nxt + rvy] = sdT;
   A[(size_t)rth * nxt + rth] = tg.Pt[0]; A[(size_t)rth * nxt + rom] = tg.Pt[1];
@@ -334,9 +349,6 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   S[rth] = tg.Pt[2]; S[rom] = tg.Pw[2];
   // B-, B+
   if (nu > 0) {
-    TP* m1 = Bm + (size_t)rpx * nu; TP* m2 = Bm + (size_t)rvx * nu;
-    TP* p1 = Bp + (size_t)rpx * nu; TP* p2 = Bp + (size_t)rvx * nu;
-    for (int c = 0; c < 3 * nu; ++c) { m1[c] = zero; m2[c] = zero; p1[c] = zero; p2[c] = zero; }
     for (int i = 0; i < nin; ++i) {
       const int q = B.idx[i];
       const TP ax = TP(B.ax[i]), ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
@@ -366,7 +378,6 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     pen[B.contact] = sd * Yom;
     defect[ry_] = y1 - xk1[ry_];
     TP* ay_ = A + (size_t)ry_ * nxt;
-    for (int c = 0; c < nxt; ++c) ay_[c] = zero;
     ay_[rpy] = tg.Yp[0]; ay_[rvy] = tg.Yp[1];
     ay_[rth] = tg.Yr[0]; ay_[rom] = tg.Yr[1];
     ay_[ry_] = one;
@@ -374,7 +385,6 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     if (nu > 0) {
       TP* bm = Bm + (size_t)ry_ * nu;
       TP* bp = Bp + (size_t)ry_ * nu;
-      for (int c = 0; c < nu; ++c) { bm[c] = zero; bp[c] = zero; }
       for (int i = 0; i < nin; ++i) {
         const int q = B.idx[i];
         const TP ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);

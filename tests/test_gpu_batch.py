@@ -231,3 +231,49 @@ def test_sweep_4096x400x20_sampled(env):
         assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
         assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= 1e-4
         assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
+
+
+@pytest.mark.parametrize("n_chunks", [1, 3, 24])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_run_host_pipelined_matches_device_path(env, n_chunks, precision):
+    """ciscvx_batch_run_host on pinned host buffers gives the device path's outputs.
+
+    Chunking regroups which intervals share a warp, and the warp votes on the
+    Taylor tier of the angle chain, so the two agree to rounding (FP64 values
+    within 1e-12 of each other, FP32 blocks within 1e-6), not bit for bit;
+    with one chunk the decomposition is the same and they are identical."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    robots, probs, midx = _small_mixed(seed=11)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
+                         precision=precision)
+    X, U, s, w, rho = _packed(plan, probs, dev, torch)
+    ref = plan.discretize(X, U, s)
+    ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=dev)
+    gref = plan.discretize_vjp(X, U, s, w, rho, workspace=ws)
+    torch.cuda.synchronize()
+    pin = lambda t: t.cpu().pin_memory()  # noqa: E731
+    host_in = {"X": pin(X), "U": pin(U), "s": pin(s)}
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ref.items()}
+    host_vjp = {"w": pin(w), "rho": pin(rho)}
+    host_vjp.update({k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in gref.items()})
+    dev_in = {k: torch.empty_like(v) for k, v in (("X", X), ("U", U), ("s", s))}
+    dev_out = {k: torch.empty_like(v) for k, v in ref.items()}
+    dev_vjp = {"w": torch.empty_like(w), "rho": torch.empty_like(rho)}
+    dev_vjp.update({k: torch.empty_like(v) for k, v in gref.items()})
+    for _ in range(2):  # second call reuses the chunk tables
+        for v in host_out.values():
+            v.fill_(float("nan"))
+        plan.run_host(host_in, host_out, dev_in, dev_out, n_chunks=n_chunks, host_vjp=host_vjp,
+                      dev_vjp=dev_vjp, workspace=ws)
+        torch.cuda.current_stream().synchronize()
+        plan.sync_status()
+        for k, v in list(ref.items()) + list(gref.items()):
+            got = (host_out if k in host_out else host_vjp)[k]
+            if n_chunks == 1:
+                assert torch.equal(got, v.cpu()), k
+            else:
+                tol = 1e-6 if v.dtype == torch.float32 else 1e-12
+                assert not torch.isnan(got).any(), k
+                assert block_err(got.double().numpy(), v.double().cpu().numpy()) <= tol, k
