@@ -277,3 +277,48 @@ def test_run_host_pipelined_matches_device_path(env, n_chunks, precision):
                 tol = 1e-6 if v.dtype == torch.float32 else 1e-12
                 assert not torch.isnan(got).any(), k
                 assert block_err(got.double().numpy(), v.double().cpu().numpy()) <= tol, k
+
+
+def test_sweep_precision_report_16_instances(env, capsys):
+    """Per-block maximum relative error of A_k, B-_k, B+_k, S_k (and defect,
+    penalty) against the FP64 oracle on the first 16 instances of the sweep
+    (400 intervals x 20 substeps each), every interval checked, for the FP64
+    and the FP32-Phi paths.  Two measures per block: block-normwise
+    max_k max|dX_k| / max|X_k|, and elementwise max |dX| / max(|X|, 1e-12 max|X_k|)."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    b = synth.cheetah_sweep(seed=0, n_inst=16)
+    probs = [b.instance(i) for i in range(len(b))]
+    model = api.Model(b.robots[0])
+    R = b.robots[0].as_dict()
+    refs = [oracle.discretize(R, p.X, p.U, p.s, p.n_sub, threads=0) for p in probs]
+    report = {}
+    for precision in ("fp64", "fp32_phi"):
+        plan = api.BatchPlan([model], b.model_idx, b.Ns, b.n_subs, precision=precision)
+        X, U, s, _, _ = _packed(plan, probs, dev, torch)
+        out = {k: v.double().cpu().numpy() for k, v in plan.discretize(X, U, s).items()}
+        rows = {}
+        for key, okey in (("A", "A"), ("Bm", "B"), ("Bp", "B"), ("S", "S"), ("defect", "defect"),
+                          ("penalty", "penalty")):
+            bw, ew = 0.0, 0.0
+            for i, p in enumerate(probs):
+                ref = refs[i][key]
+                got = plan.unpack(out[key], okey, i, ref.shape)
+                for k in range(p.N):
+                    r, g = ref[k], got[k]
+                    sc = np.abs(r).max()
+                    if sc == 0.0:
+                        continue
+                    d = np.abs(g - r)
+                    bw = max(bw, d.max() / sc)
+                    ew = max(ew, (d / np.maximum(np.abs(r), 1e-12 * sc)).max())
+            rows[key] = (bw, ew)
+        report[precision] = rows
+    with capsys.disabled():
+        print("\nper-block max relative error vs FP64 oracle, 16 x 400 x 20 sweep subset")
+        for precision, rows in report.items():
+            print(precision, " ".join(f"{k}: block {v[0]:.2e} elem {v[1]:.2e}" for k, v in rows.items()))
+    for k, (bw, _) in report["fp64"].items():
+        assert bw <= TOL_FP64, (k, bw)
+    for k, (bw, _) in report["fp32_phi"].items():
+        assert bw <= (TOL_FP32_PHI if k in ("A", "Bm", "Bp", "S") else TOL_FP64), (k, bw)
