@@ -129,7 +129,11 @@ class ClockSampler:
 # workloads
 # ---------------------------------------------------------------------------
 class BatchWorkload:
-    """Instances packed for a batch plan; one plan per precision (autotuned)."""
+    """Instances packed for a batch plan; one plan per (precision, output format), autotuned.
+
+    fmt "dense" writes the full A/B-/B+ blocks, "compact" only their structural
+    nonzeros (ciscvx_model_pattern order); S, defect, penalty and the VJP are
+    the same in both."""
 
     def __init__(self, spec, n_inst, dev, seed=0):
         import torch
@@ -153,71 +157,74 @@ class BatchWorkload:
         del probs
         self.out, self.gout, self.ws = {}, {}, None
 
-    def plan(self, prec):
-        if prec not in self.plans:
+    def plan(self, prec, fmt="dense"):
+        if (prec, fmt) not in self.plans:
             b = self.batch
-            self.plans[prec] = self.api.BatchPlan(self.models, b.model_idx, b.Ns, b.n_subs, precision=prec)
-        return self.plans[prec]
+            self.plans[(prec, fmt)] = self.api.BatchPlan(self.models, b.model_idx, b.Ns, b.n_subs,
+                                                         precision=prec, out_format=fmt)
+        return self.plans[(prec, fmt)]
 
-    def prepare(self, prec):
-        pl = self.plan(prec)
-        if prec not in self.out:
-            self.out[prec] = pl.alloc_outputs(self.dev)
-            pl.autotune(self.X, self.U, self.s, out=self.out[prec])
+    def prepare(self, prec, fmt="dense"):
+        pl = self.plan(prec, fmt)
+        if (prec, fmt) not in self.out:
+            self.out[(prec, fmt)] = pl.alloc_outputs(self.dev)
+            pl.autotune(self.X, self.U, self.s, out=self.out[(prec, fmt)])
         need = pl.vjp_workspace_size()
         if self.ws is None or self.ws.numel() < need:
             self.ws = self.torch.empty(need, dtype=self.torch.uint8, device=self.dev)
 
-    def free(self, prec):
-        self.out.pop(prec, None)
-        self.gout.pop(prec, None)
+    def free(self, prec, fmt="dense"):
+        self.out.pop((prec, fmt), None)
+        self.gout.pop((prec, fmt), None)
         self.torch.cuda.empty_cache()
 
-    def disc(self, prec):
-        self.plan(prec).discretize(self.X, self.U, self.s, out=self.out[prec])
+    def disc(self, prec, fmt="dense"):
+        self.plan(prec, fmt).discretize(self.X, self.U, self.s, out=self.out[(prec, fmt)])
 
-    def vjp(self, prec):
-        pl = self.plan(prec)
-        self.gout[prec] = pl.discretize_vjp(self.X, self.U, self.s, self.w, self.rho, workspace=self.ws,
-                                            out=self.gout.get(prec))
+    def vjp(self, prec, fmt="dense"):
+        pl = self.plan(prec, fmt)
+        self.gout[(prec, fmt)] = pl.discretize_vjp(self.X, self.U, self.s, self.w, self.rho,
+                                                   workspace=self.ws, out=self.gout.get((prec, fmt)))
 
-    def step(self, prec):
-        self.disc(prec)
-        self.vjp(prec)
+    def step(self, prec, fmt="dense"):
+        self.disc(prec, fmt)
+        self.vjp(prec, fmt)
 
     def check_status(self):
         for pl in self.plans.values():
             pl.sync_status()
 
-    def tune(self, prec):
-        return self.plan(prec).tune()
+    def tune(self, prec, fmt="dense"):
+        return self.plan(prec, fmt).tune()
 
     # end to end through the public API with host buffers: ciscvx_batch_run_host
     # (chunked, H2D / compute / D2H overlapped on three streams)
     E2E_CHUNKS = 16
 
-    def e2e_setup(self, prec):
+    def e2e_setup(self, prec, fmt="dense"):
         torch = self.torch
         self.host_in = {k: getattr(self, k).cpu().pin_memory() for k in ("X", "U", "s", "w", "rho")}
         self.dev_in = {k: torch.empty_like(getattr(self, k)) for k in ("X", "U", "s", "w", "rho")}
-        outs = dict(self.out[prec])
-        outs.update({k: v for k, v in self.gout[prec].items() if v is not None})
+        outs = dict(self.out[(prec, fmt)])
+        outs.update({k: v for k, v in self.gout[(prec, fmt)].items() if v is not None})
         self.host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in outs.items()}
         h2d = sum(v.numel() * v.element_size() for v in self.host_in.values())
         d2h = sum(v.numel() * v.element_size() for v in self.host_out.values())
         return h2d, d2h
 
-    def e2e_step(self, prec):
+    def e2e_step(self, prec, fmt="dense"):
         h, d = self.host_in, self.dev_in
-        ho, g = self.host_out, self.gout[prec]
+        ho, g = self.host_out, self.gout[(prec, fmt)]
         host_vjp = {"w": h["w"], "rho": h["rho"], "gX": ho["gX"], "gU": ho["gU"], "gs": ho["gs"], "L": ho["L"]}
         dev_vjp = {"w": d["w"], "rho": d["rho"], "gX": g["gX"], "gU": g["gU"], "gs": g["gs"], "L": g["L"]}
-        self.plan(prec).run_host({k: h[k] for k in ("X", "U", "s")}, ho, {k: d[k] for k in ("X", "U", "s")},
-                                 self.out[prec], n_chunks=self.E2E_CHUNKS, host_vjp=host_vjp,
-                                 dev_vjp=dev_vjp, workspace=self.ws)
+        self.plan(prec, fmt).run_host({k: h[k] for k in ("X", "U", "s")}, ho,
+                                      {k: d[k] for k in ("X", "U", "s")}, self.out[(prec, fmt)],
+                                      n_chunks=self.E2E_CHUNKS, host_vjp=host_vjp, dev_vjp=dev_vjp,
+                                      workspace=self.ws)
 
     def e2e_free(self):
         self.host_in = self.host_out = self.dev_in = None
+        self.torch.cuda.empty_cache()
 
 
 class SingleWorkload:
@@ -413,15 +420,38 @@ def run_ours(args):
         roof.update(achieved=None, frac=None)
 
     # end to end through the public API with host (pinned) buffers
-    e2e = None
-    if not args.no_e2e:
-        h2d, d2h = wl.e2e_setup(prec)
+    def measure_e2e(fmt):
+        h2d, d2h = wl.e2e_setup(prec, fmt) if fmt != "dense" else wl.e2e_setup(prec)
         ke = max(1, args.steps // 2)
-        te = time_steps(torch, lambda: wl.e2e_step(prec), ke, 1, stream)
+        step = (lambda: wl.e2e_step(prec, fmt)) if fmt != "dense" else (lambda: wl.e2e_step(prec))
+        te = time_steps(torch, step, ke, 1, stream)
         te, = max_over_ranks([te])
-        e2e = {"value": units * ke / te, "unit": "intervals/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
         wl.e2e_free()
+        return {"value": units * ke / te, "unit": "intervals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h}
+
+    e2e = None if args.no_e2e else measure_e2e("dense")
+
+    # the same step with compact outputs (structural nonzeros of A, B-, B+ only)
+    compact = None
+    if spec["kind"] == "batch" and not args.no_compact:
+        wl.free(prec)
+        wl.prepare(prec, "compact")
+        wl.step(prec, "compact")
+        barrier()
+        tc = time_steps(torch, lambda: wl.step(prec, "compact"), args.steps, args.warmup, stream)
+        barrier()
+        kdc = kernel_time(torch, lambda: wl.disc(prec, "compact"), 5, stream)
+        wl.check_status()
+        tc, kdc = max_over_ranks([tc, kdc])
+        pc = wl.plan(prec, "compact")
+        compact = {"value": units * args.steps / tc, "ms_per_step": tc / args.steps * 1e3,
+                   "discretize_ms": kdc * 1e3,
+                   "output_bytes_per_interval": sum(
+                       v.numel() * v.element_size() for v in wl.out[(prec, "compact")].values()) / wl.intervals,
+                   "tune": pc.tune(),
+                   "e2e": None if args.no_e2e else measure_e2e("compact")}
+        wl.free(prec, "compact")
 
     if rank != 0:
         return
@@ -445,6 +475,7 @@ def run_ours(args):
         "gpu_launches": args.steps * (4 if spec["kind"] == "batch" else 5),
         "roofline": roof,
         "e2e": e2e,
+        "compact_outputs": compact,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -482,6 +513,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compact", action="store_true", help="skip the compact-output measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

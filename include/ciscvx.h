@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 1
+#define CISCVX_VERSION_MINOR 2
 
 typedef enum {
   CISCVX_OK = 0,
@@ -93,6 +93,12 @@ typedef enum {
   CISCVX_FOH_NODE = 0,     /* U [N+1][n_u]: controls shared by neighbouring intervals */
   CISCVX_FOH_INTERVAL = 1  /* U [N][2][n_u]: per-interval (u_L, u_R) */
 } ciscvx_u_layout;
+
+typedef enum {
+  CISCVX_OUT_DENSE = 0,   /* A [N][n_x~][n_x~], Bm/Bp [N][n_x~][n_u] (structural zeros stored) */
+  CISCVX_OUT_COMPACT = 1  /* A [N][nnz_A], Bm/Bp [N][nnz_B]: structural nonzeros only, in the
+                             order of ciscvx_model_pattern; S, defect, penalty, z as for dense */
+} ciscvx_out_format;
 
 /* Limits of this build (ciscvx_model_create / ciscvx_discretize_vjp return
  * CISCVX_EUNSUPPORTED beyond them). */
@@ -146,6 +152,37 @@ void ciscvx_model_destroy(ciscvx_model* model);
  * Any output pointer may be NULL.  EINVAL on a null model. */
 ciscvx_status ciscvx_model_dims(const ciscvx_model* model, int* n_x, int* n_y, int* n_u);
 
+/* Structural nonzero pattern of A_k and of B-_k / B+_k (shared by both) for
+ * the model `desc` describes.  Host computation only: needs no GPU and no
+ * model handle.  The dynamics of Sec. II-A couple the links only through the
+ * joint forces, which are inputs, so A_k is block diagonal per link (plus the
+ * row of the contact's penalty state), and input q enters only the rows of
+ * the links it acts on.  The pattern holds every entry that can be nonzero
+ * for some (x~, U, s); entries outside it are exactly zero for all inputs.
+ * (On a link that no input acts on, (om,th) is in the pattern but always 0.)
+ * Compact outputs (CISCVX_OUT_COMPACT) store, per interval, the values of the
+ * pattern's entries in this order:
+ *   A: for each link b in order: (px,px) (px,vx) (py,py) (py,vy) (th,th)
+ *      (th,om) (vx,vx) (vy,vy) (om,th) (om,om), then, if a contact sits on
+ *      b, (y,py) (y,th) (y,vy) (y,om) (y,y); px/py/th = rows 3b, 3b+1, 3b+2,
+ *      vx/vy/om = rows 3n_b + 3b + (0, 1, 2), y = row 6n_b + (contact index);
+ *   B: for each link b in order, for each input q acting on b (for each
+ *      joint j in increasing index that has b as parent or child: tau_j,
+ *      lambda_jx, lambda_jy; then, if a contact sits on b, its lambda_n,
+ *      lambda_t+, lambda_t-): (px,q) if q has an x force component,
+ *      (py,q) if a y component, (th,q), (vx,q) if x, (vy,q) if y, (om,q),
+ *      then (y,q) if a contact sits on b.
+ * Call with NULL arrays to get the counts; then a_row/a_col receive nnz_A
+ * and b_row/b_col nnz_B int32 indices (host memory, caller-owned).  Any of
+ * nnz_a, nnz_b may be NULL.  Errors: as ciscvx_model_create for the
+ * description (EINVAL, EUNSUPPORTED). */
+ciscvx_status ciscvx_model_pattern(const ciscvx_model_desc* desc, int* nnz_a, int* nnz_b,
+                                   int32_t* a_row, int32_t* a_col, int32_t* b_row,
+                                   int32_t* b_col);
+
+/* Pattern sizes of a created model (as ciscvx_model_pattern).  EINVAL on a null model. */
+ciscvx_status ciscvx_model_nnz(const ciscvx_model* model, int* nnz_a, int* nnz_b);
+
 /* ------------------------------------------------------------ workspace --- */
 
 typedef enum { CISCVX_OP_DISCRETIZE = 0, CISCVX_OP_VJP = 1 } ciscvx_op;
@@ -174,6 +211,17 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* model, int N, int n_sub,
                                 const double* X, const double* U, const double* s, void* A,
                                 void* Bm, void* Bp, void* S, double* defect, double* penalty,
                                 double* z, void* workspace, size_t ws_bytes, void* stream);
+
+/* ciscvx_discretize with compact A, Bm, Bp (CISCVX_OUT_COMPACT): A [N][nnz_A],
+ * Bm/Bp [N][nnz_B] in the precision's dtype, values in ciscvx_model_pattern's
+ * order; every other argument as for ciscvx_discretize.  The values are those
+ * ciscvx_discretize stores at the pattern's positions (same arithmetic), and
+ * no structural zero is written.  Errors: as ciscvx_discretize. */
+ciscvx_status ciscvx_discretize_compact(const ciscvx_model* model, int N, int n_sub,
+                                        ciscvx_precision precision, ciscvx_u_layout layout,
+                                        const double* X, const double* U, const double* s,
+                                        void* A, void* Bm, void* Bp, void* S, double* defect,
+                                        double* penalty, double* z, void* stream);
 
 /* Vector-Jacobian product of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k
  * (defect and penalty as above) with respect to X, U and s, by the discrete
@@ -230,7 +278,8 @@ typedef struct {
 
 /* Element counts of the packed buffers (or, from ciscvx_batch_offsets, the
  * element offsets of one instance inside them).  A/Bm/Bp/S in the plan's Phi
- * dtype; everything else FP64.  L has one element per instance. */
+ * dtype; everything else FP64.  L has one element per instance.  With compact
+ * outputs an instance's A holds N nnz_A values and its Bm/Bp N nnz_B. */
 typedef struct {
   size_t X, U, s, A, B, S, defect, penalty, L;
 } ciscvx_batch_sizes;
@@ -262,16 +311,16 @@ typedef struct {
 /* Builds the work decomposition for n_inst instances: instance i uses
  * models[model_idx[i]] with N[i] intervals and n_sub[i] substeps.  All arrays
  * are host memory, copied; the models must outlive the plan and live on the
- * current device.  tune may be NULL (defaults: 4 warps/CTA, persistent with
+ * current device.  format: dense or compact A/Bm/Bp for every instance.  tune may be NULL (defaults: 4 warps/CTA, persistent with
  * 2 CTAs/SM, cost order, graph, no register cap).  Allocates the plan's device tables (this
  * is the only allocating batch call besides autotuning's timing buffers).
  * Errors: EINVAL (nulls, n_inst < 1, bad indices, N < 1, n_sub < 1, layout,
- * precision), EUNSUPPORTED (tensor-core precisions), ENOMEM/ECUDA. */
+ * precision, format), EUNSUPPORTED (tensor-core precisions), ENOMEM/ECUDA. */
 ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_models,
                                        const int* model_idx, const int* N, const int* n_sub,
                                        int n_inst, ciscvx_precision precision,
-                                       ciscvx_u_layout layout, const ciscvx_tune* tune,
-                                       ciscvx_batch_plan** out);
+                                       ciscvx_u_layout layout, ciscvx_out_format format,
+                                       const ciscvx_tune* tune, ciscvx_batch_plan** out);
 
 /* Frees the plan (no work using it may be in flight).  NULL is a no-op. */
 void ciscvx_batch_plan_destroy(ciscvx_batch_plan* plan);

@@ -29,7 +29,9 @@ EXPORTS = (
     "ciscvx_batch_offsets", "ciscvx_batch_get_tune", "ciscvx_batch_discretize",
     "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp", "ciscvx_batch_autotune",
     "ciscvx_batch_sync_status", "ciscvx_batch_run_host",
+    "ciscvx_model_pattern", "ciscvx_model_nnz", "ciscvx_discretize_compact",
 )
+FORMAT = {"dense": 0, "compact": 1}
 
 
 class Tune(ctypes.Structure):
@@ -107,13 +109,20 @@ def load(path: str | None = None):
                                           ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                           _vp, _vp, ctypes.c_size_t, _vp]
     lib.ciscvx_sync_status.argtypes = [_vp, _vp]
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    lib.ciscvx_model_pattern.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), I32, I32, I32, I32]
+    lib.ciscvx_model_nnz.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.ciscvx_discretize_compact.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                              _vp, _vp, _vp]
     lib.ciscvx_discretize_vjp_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                                  _vp, _vp, _vp]
     P = ctypes.POINTER
     lib.ciscvx_batch_plan_create.argtypes = [P(_vp), ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
                                              P(ctypes.c_int), ctypes.c_int, ctypes.c_int,
-                                             ctypes.c_int, P(Tune), P(_vp)]
+                                             ctypes.c_int, ctypes.c_int, P(Tune), P(_vp)]
     lib.ciscvx_batch_plan_destroy.argtypes = [_vp]
     lib.ciscvx_batch_plan_destroy.restype = None
     lib.ciscvx_batch_sizes_get.argtypes = [_vp, P(_Sizes)]
@@ -132,7 +141,8 @@ def load(path: str | None = None):
               "ciscvx_discretize_vjp_static", "ciscvx_batch_plan_create", "ciscvx_batch_sizes_get",
               "ciscvx_batch_offsets", "ciscvx_batch_get_tune", "ciscvx_batch_discretize",
               "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp",
-              "ciscvx_batch_autotune", "ciscvx_batch_sync_status"):
+              "ciscvx_batch_autotune", "ciscvx_batch_sync_status", "ciscvx_model_pattern",
+              "ciscvx_model_nnz", "ciscvx_discretize_compact"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -147,12 +157,10 @@ def _get(robot, key):
     return robot[key] if isinstance(robot, dict) else getattr(robot, key)
 
 
-class Model:
-    """``ciscvx_model`` built from a robot description (synth.Robot or a dict
-    with mass, inertia, joint_*, contact_*, gravity)."""
+class _DescHolder:
+    """A ``ciscvx_model_desc`` for a robot description, with the host arrays it points to."""
 
     def __init__(self, robot):
-        lib = load()
         mass = np.asarray(_get(robot, "mass"), dtype=np.float64)
         inertia = np.asarray(_get(robot, "inertia"), dtype=np.float64)
         jp = np.asarray(_get(robot, "joint_parent"), dtype=np.int64)
@@ -169,16 +177,48 @@ class Model:
             for j in range(nj)])
         self._contacts = (_Contact * max(nc, 1))(*[
             _Contact(int(cb[i]), (ctypes.c_double * 2)(*cr[i]), cm[i]) for i in range(nc)])
-        desc = _Desc(nb, nj, nc, self._bodies, self._joints, self._contacts,
-                     float(_get(robot, "gravity")))
+        self.desc = _Desc(nb, nj, nc, self._bodies, self._joints, self._contacts,
+                          float(_get(robot, "gravity")))
+        self.nb = nb
+
+
+def model_pattern(robot):
+    """ciscvx_model_pattern (host only, no GPU): the structural nonzeros of A and
+    of B-/B+ in compact order, as int32 arrays (a_row, a_col, b_row, b_col)."""
+    lib = load()
+    d = _DescHolder(robot)
+    na, nb_ = ctypes.c_int(), ctypes.c_int()
+    _check(lib.ciscvx_model_pattern(ctypes.byref(d.desc), ctypes.byref(na), ctypes.byref(nb_),
+                                    None, None, None, None))
+    arrs = [np.zeros(max(n, 1), dtype=np.int32) for n in (na.value, na.value, nb_.value, nb_.value)]
+    ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for a in arrs]
+    _check(lib.ciscvx_model_pattern(ctypes.byref(d.desc), None, None, *ptrs))
+    return arrs[0][:na.value], arrs[1][:na.value], arrs[2][:nb_.value], arrs[3][:nb_.value]
+
+
+class Model:
+    """``ciscvx_model`` built from a robot description (synth.Robot or a dict
+    with mass, inertia, joint_*, contact_*, gravity)."""
+
+    def __init__(self, robot):
+        lib = load()
+        self._d = _DescHolder(robot)
         h = _vp()
-        _check(lib.ciscvx_model_create(ctypes.byref(desc), ctypes.byref(h)))
+        _check(lib.ciscvx_model_create(ctypes.byref(self._d.desc), ctypes.byref(h)))
         self._h = h
         nx, ny, nu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib.ciscvx_model_dims(h, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nu)))
         self.nx, self.ny, self.nu = nx.value, ny.value, nu.value
         self.nxt = self.nx + self.ny
-        self.nb = nb
+        self.nb = self._d.nb
+        na, nbb = ctypes.c_int(), ctypes.c_int()
+        _check(lib.ciscvx_model_nnz(h, ctypes.byref(na), ctypes.byref(nbb)))
+        self.nnz_a, self.nnz_b = na.value, nbb.value
+        self._robot = robot
+
+    def pattern(self):
+        """(a_row, a_col, b_row, b_col) of the compact outputs (see model_pattern)."""
+        return model_pattern(self._robot)
 
     @property
     def handle(self):
@@ -244,6 +284,37 @@ def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layou
         _ptr(s), _ptr(out["A"]), _ptr(out["Bm"]) if nu else None, _ptr(out["Bp"]) if nu else None,
         _ptr(out["S"]), _ptr(out["defect"]), _ptr(out["penalty"]) if nc else None,
         _ptr(out.get("z")), None, 0, _stream()))
+    return out
+
+
+def discretize_compact(model: Model, X, U, s, n_sub: int, precision: str = "fp64",
+                       layout: str = "node", want_z: bool = False, out: dict | None = None):
+    """ciscvx_discretize_compact: as discretize, with A (N, nnz_a) and Bm/Bp
+    (N, nnz_b) holding the structural nonzeros in Model.pattern() order."""
+    import torch
+    f64 = torch.float64
+    _need(X, "X", f64); _need(U, "U", f64); _need(s, "s", f64)
+    N = s.shape[0]
+    nxt, nc = model.nxt, model.ny
+    pdt = f64 if precision == "fp64" else torch.float32
+    dev = X.device
+    if out is None:
+        out = {
+            "A": torch.empty((N, model.nnz_a), dtype=pdt, device=dev),
+            "Bm": torch.empty((N, model.nnz_b), dtype=pdt, device=dev),
+            "Bp": torch.empty((N, model.nnz_b), dtype=pdt, device=dev),
+            "S": torch.empty((N, nxt), dtype=pdt, device=dev),
+            "defect": torch.empty((N, nxt), dtype=f64, device=dev),
+            "penalty": torch.empty((N, nc), dtype=f64, device=dev),
+        }
+        if want_z:
+            out["z"] = torch.empty((N, nxt), dtype=f64, device=dev)
+    nzb = model.nnz_b > 0
+    _check(load().ciscvx_discretize_compact(
+        model.handle, int(N), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X), _ptr(U),
+        _ptr(s), _ptr(out["A"]), _ptr(out["Bm"]) if nzb else None, _ptr(out["Bp"]) if nzb else None,
+        _ptr(out["S"]), _ptr(out["defect"]), _ptr(out["penalty"]) if nc else None,
+        _ptr(out.get("z")), _stream()))
     return out
 
 
@@ -345,21 +416,22 @@ class BatchPlan:
     back in instance order (see include/ciscvx.h)."""
 
     def __init__(self, models, model_idx, N, n_sub, precision="fp32_phi", layout="node",
-                 tune: dict | None = None):
+                 tune: dict | None = None, out_format: str = "dense"):
         lib = load()
         self.models = list(models)
         self.model_idx = np.asarray(model_idx, dtype=np.int32)
         self.N = np.asarray(N, dtype=np.int32)
         self.n_sub = np.asarray(n_sub, dtype=np.int32)
         self.n_inst = len(self.model_idx)
-        self.precision, self.layout = precision, layout
+        self.precision, self.layout, self.out_format = precision, layout, out_format
         hs = (_vp * len(self.models))(*[m.handle for m in self.models])
         ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))  # noqa: E731
         t = Tune(**tune) if tune else None
         h = _vp()
         _check(lib.ciscvx_batch_plan_create(hs, len(self.models), ip(self.model_idx), ip(self.N),
                                             ip(self.n_sub), self.n_inst, PRECISION[precision],
-                                            LAYOUT[layout], ctypes.byref(t) if t else None,
+                                            LAYOUT[layout], FORMAT[out_format],
+                                            ctypes.byref(t) if t else None,
                                             ctypes.byref(h)))
         self._h = h
         sz = _Sizes()

@@ -118,7 +118,67 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
     slot += M.body[b].nin;
   }
   M.nslot = slot;
+  // compact output offsets (see common.cuh for the entry order)
+  int aoff = 0, boff = 0;
+  for (int b = 0; b < nb; ++b) {
+    DevBody& B = M.body[b];
+    B.a_off = aoff;
+    B.b_off = boff;
+    aoff += A_PER_LINK + (B.contact >= 0 ? A_PER_FOOT : 0);
+    for (int i = 0; i < B.nin; ++i)
+      boff += 2 + (B.ax[i] != 0.0 ? 2 : 0) + (B.ay[i] != 0.0 ? 2 : 0) + (B.contact >= 0 ? 1 : 0);
+  }
+  M.nnzA = aoff;
+  M.nnzB = boff;
   return CISCVX_OK;
+}
+
+// Checks of the description that come before the tables are built.
+ciscvx_status check_desc(const ciscvx_model_desc* desc) {
+  if (desc->n_bodies < 1 || desc->n_joints < 0 || desc->n_contacts < 0)
+    return fail(CISCVX_EINVAL, "need n_bodies >= 1, n_joints >= 0, n_contacts >= 0");
+  if (!desc->bodies || (desc->n_joints > 0 && !desc->joints) ||
+      (desc->n_contacts > 0 && !desc->contacts))
+    return fail(CISCVX_EINVAL, "null body/joint/contact array");
+  if (desc->n_bodies > MAXB || desc->n_joints > MAXJ || desc->n_contacts > MAXB)
+    return fail(CISCVX_EUNSUPPORTED, "at most %d links, %d joints, %d contacts", MAXB, MAXJ, MAXB);
+  if (!std::isfinite(desc->gravity)) return fail(CISCVX_EINVAL, "non-finite gravity");
+  return CISCVX_OK;
+}
+
+// The compact pattern of the built tables, in the order the kernels store it
+// (see common.cuh); the arrays may be null.
+void fill_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int32_t* bc) {
+  const int nb = M.nb;
+  for (int b = 0; b < nb; ++b) {
+    const DevBody& B = M.body[b];
+    const int px = 3 * b, py = px + 1, th = px + 2;
+    const int vx = 3 * nb + 3 * b, vy = vx + 1, om = vx + 2;
+    const int y = B.contact >= 0 ? 6 * nb + B.contact : -1;
+    const int arow[15] = {px, px, py, py, th, th, vx, vy, om, om, y, y, y, y, y};
+    const int acol[15] = {px, vx, py, vy, th, om, vx, vy, th, om, py, th, vy, om, y};
+    const int na = A_PER_LINK + (y >= 0 ? A_PER_FOOT : 0);
+    for (int j = 0; j < na; ++j) {
+      if (ar) ar[B.a_off + j] = arow[j];
+      if (ac) ac[B.a_off + j] = acol[j];
+    }
+    int o = B.b_off;
+    for (int i = 0; i < B.nin; ++i) {
+      const bool nx = B.ax[i] != 0.0, ny = B.ay[i] != 0.0;
+      int rows[7], n = 0;
+      if (nx) rows[n++] = px;
+      if (ny) rows[n++] = py;
+      rows[n++] = th;
+      if (nx) rows[n++] = vx;
+      if (ny) rows[n++] = vy;
+      rows[n++] = om;
+      if (y >= 0) rows[n++] = y;
+      for (int t = 0; t < n; ++t, ++o) {
+        if (br) br[o] = rows[t];
+        if (bc) bc[o] = B.idx[i];
+      }
+    }
+  }
 }
 
 bool layout_ok(int layout) { return layout == CISCVX_FOH_NODE || layout == CISCVX_FOH_INTERVAL; }
@@ -163,17 +223,11 @@ const char* ciscvx_last_error(void) { return g_err.c_str(); }
 ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** out) {
   if (!desc || !out) return fail(CISCVX_EINVAL, "null argument");
   *out = nullptr;
-  if (desc->n_bodies < 1 || desc->n_joints < 0 || desc->n_contacts < 0)
-    return fail(CISCVX_EINVAL, "need n_bodies >= 1, n_joints >= 0, n_contacts >= 0");
-  if (!desc->bodies || (desc->n_joints > 0 && !desc->joints) ||
-      (desc->n_contacts > 0 && !desc->contacts))
-    return fail(CISCVX_EINVAL, "null body/joint/contact array");
-  if (desc->n_bodies > MAXB || desc->n_joints > MAXJ || desc->n_contacts > MAXB)
-    return fail(CISCVX_EUNSUPPORTED, "at most %d links, %d joints, %d contacts", MAXB, MAXJ, MAXB);
-  if (!std::isfinite(desc->gravity)) return fail(CISCVX_EINVAL, "non-finite gravity");
+  ciscvx_status st = check_desc(desc);
+  if (st != CISCVX_OK) return st;
   ciscvx_model* m = new (std::nothrow) ciscvx_model;
   if (!m) return fail(CISCVX_ENOMEM, "host allocation failed");
-  ciscvx_status st = build_tables(desc, m->host);
+  st = build_tables(desc, m->host);
   if (st != CISCVX_OK) { delete m; return st; }
   m->dev = nullptr;
   m->status = nullptr;
@@ -198,6 +252,31 @@ void ciscvx_model_destroy(ciscvx_model* m) {
   if (m->dev) cudaFree(m->dev);
   if (m->status) cudaFree(m->status);
   delete m;
+}
+
+ciscvx_status ciscvx_model_pattern(const ciscvx_model_desc* desc, int* nnz_a, int* nnz_b,
+                                   int32_t* a_row, int32_t* a_col, int32_t* b_row,
+                                   int32_t* b_col) {
+  if (!desc) return fail(CISCVX_EINVAL, "null description");
+  ciscvx_status st = check_desc(desc);
+  if (st != CISCVX_OK) return st;
+  DevModel* M = new (std::nothrow) DevModel;
+  if (!M) return fail(CISCVX_ENOMEM, "host allocation failed");
+  st = build_tables(desc, *M);
+  if (st == CISCVX_OK) {
+    if (nnz_a) *nnz_a = M->nnzA;
+    if (nnz_b) *nnz_b = M->nnzB;
+    fill_pattern(*M, a_row, a_col, b_row, b_col);
+  }
+  delete M;
+  return st == CISCVX_OK ? ok() : st;
+}
+
+ciscvx_status ciscvx_model_nnz(const ciscvx_model* m, int* nnz_a, int* nnz_b) {
+  if (!m) return fail(CISCVX_EINVAL, "null model");
+  if (nnz_a) *nnz_a = m->host.nnzA;
+  if (nnz_b) *nnz_b = m->host.nnzB;
+  return ok();
 }
 
 ciscvx_status ciscvx_model_dims(const ciscvx_model* m, int* n_x, int* n_y, int* n_u) {
@@ -231,8 +310,25 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* m, int N, int n_sub,
   if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
   if (m->host.nu > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
-  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, X, U, s, A,
-                                    Bm, Bp, S, defect, penalty, z, m->status,
+  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, false, X, U,
+                                    s, A, Bm, Bp, S, defect, penalty, z, m->status,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
+  return ok();
+}
+
+ciscvx_status ciscvx_discretize_compact(const ciscvx_model* m, int N, int n_sub,
+                                        ciscvx_precision precision, ciscvx_u_layout layout,
+                                        const double* X, const double* U, const double* s,
+                                        void* A, void* Bm, void* Bp, void* S, double* defect,
+                                        double* penalty, double* z, void* stream) {
+  ciscvx_status st = check_common(m, N, n_sub, precision, layout, X, U, s);
+  if (st != CISCVX_OK) return st;
+  if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
+  if (m->host.nnzB > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
+  if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
+  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, true, X, U,
+                                    s, A, Bm, Bp, S, defect, penalty, z, m->status,
                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
   return ok();

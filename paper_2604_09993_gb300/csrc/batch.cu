@@ -61,7 +61,8 @@ template <> struct Occ<0> { static constexpr int T = 256, B = 1; };  // no regis
 template <> struct Occ<1> { static constexpr int T = 128, B = 3; };  // <= 168 registers
 template <> struct Occ<2> { static constexpr int T = 128, B = 4; };  // <= 128 registers
 
-template <typename TP, int OCC>
+// CMP: compact A/Bm/Bp (structural nonzeros only; strides nnzA / nnzB).
+template <typename TP, int OCC, bool CMP>
 __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCommon c, const double* __restrict__ X,
                                                     const double* __restrict__ U,
                                                     const double* __restrict__ s, TP* A, TP* Bm,
@@ -84,18 +85,20 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCo
       const double* Xi = X + I.x;
       const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
       const double* uR = uL + nu;
-      TP* Ak = A + I.a + (size_t)k * nxt * nxt;
-      TP* Bmk = Bm ? Bm + I.b + (size_t)k * nxt * nu : nullptr;
-      TP* Bpk = Bp ? Bp + I.b + (size_t)k * nxt * nu : nullptr;
+      const size_t sa = CMP ? (size_t)M.nnzA : (size_t)nxt * nxt;
+      const size_t sb = CMP ? (size_t)M.nnzB : (size_t)nxt * nu;
+      TP* Ak = A + I.a + k * sa;
+      TP* Bmk = Bm ? Bm + I.b + k * sb : nullptr;
+      TP* Bpk = Bp ? Bp + I.b + k * sb : nullptr;
       TP* Sk = S + I.v + (size_t)k * nxt;
       double* dk = defect + I.v + (size_t)k * nxt;
       double* pk = penalty ? penalty + I.p + (size_t)k * nc : nullptr;
       if (M.body[b].contact >= 0)
-        disc_link<TP, true>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, Ak,
-                            Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
+        disc_link<TP, true, CMP>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
+                                 Ak, Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
       else
-        disc_link<TP, false>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, Ak,
-                             Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
+        disc_link<TP, false, CMP>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
+                                  Ak, Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
     }
   }
 }
@@ -216,6 +219,7 @@ struct ChunkTables {
 
 struct ciscvx_batch_plan {
   int n_inst = 0, n_models = 0, prec = 0, layout = 0, device = 0, sm_count = 0, max_nsub = 0;
+  bool compact = false;  // CISCVX_OUT_COMPACT
   bool all_nu0 = true, all_nc0 = true;
   std::vector<const ciscvx_model*> models;
   std::vector<DevInst> inst;
@@ -387,10 +391,15 @@ cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const cisc
   }
   unsigned blocks, threads;
   grid_for(p, c.n_items, blocks, threads);
-#define CISCVX_DISC(TP, OCC)                                                                  \
-  k_batch_disc<TP, OCC><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (TP*)io->A,        \
-                                                    (TP*)io->Bm, (TP*)io->Bp, (TP*)io->S,       \
-                                                    io->defect, io->penalty)
+#define CISCVX_DISC1(TP, OCC, CMP)                                                            \
+  k_batch_disc<TP, OCC, CMP><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (TP*)io->A,   \
+                                                         (TP*)io->Bm, (TP*)io->Bp, (TP*)io->S,  \
+                                                         io->defect, io->penalty)
+#define CISCVX_DISC(TP, OCC)                     \
+  do {                                           \
+    if (p->compact) CISCVX_DISC1(TP, OCC, true); \
+    else CISCVX_DISC1(TP, OCC, false);           \
+  } while (0)
   const int occ = p->tune.occupancy;
   if (p->prec == CISCVX_FP64) {
     if (occ == 1) CISCVX_DISC(double, 1);
@@ -402,6 +411,7 @@ cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const cisc
     else CISCVX_DISC(float, 0);
   }
 #undef CISCVX_DISC
+#undef CISCVX_DISC1
   return cudaGetLastError();
 }
 
@@ -472,8 +482,8 @@ extern "C" {
 ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_models,
                                        const int* model_idx, const int* N, const int* n_sub,
                                        int n_inst, ciscvx_precision precision,
-                                       ciscvx_u_layout layout, const ciscvx_tune* tune,
-                                       ciscvx_batch_plan** out) {
+                                       ciscvx_u_layout layout, ciscvx_out_format format,
+                                       const ciscvx_tune* tune, ciscvx_batch_plan** out) {
   if (!out) return set_error(CISCVX_EINVAL, "null out");
   *out = nullptr;
   if (!models || n_models < 1 || !model_idx || !N || !n_sub || n_inst < 1)
@@ -484,6 +494,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     return set_error(CISCVX_EUNSUPPORTED, "tensor-core precisions are not provided by this build");
   if (precision != CISCVX_FP64 && precision != CISCVX_FP32_PHI)
     return set_error(CISCVX_EINVAL, "unknown precision %d", (int)precision);
+  if (format != CISCVX_OUT_DENSE && format != CISCVX_OUT_COMPACT)
+    return set_error(CISCVX_EINVAL, "unknown output format %d", (int)format);
   if (tune && !tune_ok(*tune)) return set_error(CISCVX_EINVAL, "invalid ciscvx_tune");
   for (int m = 0; m < n_models; ++m)
     if (!models[m]) return set_error(CISCVX_EINVAL, "null model %d", m);
@@ -499,6 +511,7 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   p->n_models = n_models;
   p->prec = precision;
   p->layout = layout;
+  p->compact = (format == CISCVX_OUT_COMPACT);
   p->models.assign(models, models + n_models);
   if (tune) p->tune = *tune;
   cudaGetDevice(&p->device);
@@ -523,8 +536,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     z.X += (n + 1) * nxt;
     z.U += (layout == CISCVX_FOH_NODE ? (n + 1) : 2 * n) * nu;
     z.s += n;
-    z.A += n * nxt * nxt;
-    z.B += n * nxt * nu;
+    z.A += n * (p->compact ? (size_t)M.nnzA : nxt * nxt);
+    z.B += n * (p->compact ? (size_t)M.nnzB : nxt * nu);
     z.S += n * nxt;
     z.defect += n * nxt;
     z.penalty += n * nc;
@@ -538,7 +551,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
 
   // work decomposition of the whole batch (one chunk)
   HostDecomp dec = decompose(p, {0, n_inst});
-  p->key = std::to_string(precision) + "|" + std::to_string(layout) + "|" + dec.key;
+  p->key = std::to_string(precision) + "|" + std::to_string(layout) + "|" +
+           (p->compact ? "c|" : "d|") + dec.key;
   p->n_items = (int)dec.items_lpt.size();
   p->items_lpt = dec.items_lpt;
   p->items_nat = dec.items_nat;

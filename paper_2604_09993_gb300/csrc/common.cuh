@@ -46,6 +46,8 @@ struct DevBody {
   int contact;       // contact index, or -1
   int cin;           // input index of the contact's lambda_n (lambda_t+ = cin+1, lambda_t- = cin+2)
   int slot0;         // first VJP partial slot of this link within an interval
+  int a_off;         // first entry of this link in the compact A values of an interval
+  int b_off;         // first entry of this link in the compact B-/B+ values of an interval
   double crho[2];    // contact point (body frame)
   double mu;         // friction coefficient
   double pad_;
@@ -57,8 +59,19 @@ struct DevBody {
   double t[MAXIN + 1];   // torque coefficient: sigma/I
 };
 
+// Compact outputs keep only the structural nonzeros of A and B-/B+, per
+// interval, link by link (rows px, py, th, vx, vy, om of link b, y of its
+// contact).  Link b's A entries, at a_off: (px,px) (px,vx) (py,py) (py,vy)
+// (th,th) (th,om) (vx,vx) (vy,vy) (om,th) (om,om), then for a foot link
+// (y,py) (y,th) (y,vy) (y,om) (y,y).  Link b's B entries, at b_off, for each
+// of its inputs q in slot order: (px,q) if the input has an x force
+// component, (py,q) if it has a y component, (th,q), (vx,q) if x, (vy,q) if
+// y, (om,q), then (y,q) for a foot link.  B- and B+ share the pattern.
+constexpr int A_PER_LINK = 10, A_PER_FOOT = 5;
+
 struct DevModel {
   int nb, nj, nc, nxt, nu, nslot;   // nslot = sum of nin over links
+  int nnzA, nnzB;                    // structural nonzeros of A and of B-/B+ (compact outputs)
   double g;
   int in_n[MAXU];        // per input: number of (link, slot) contributions (1 or 2)
   int in_slot[MAXU][2];  // per input: partial slots that contribute
@@ -214,7 +227,7 @@ struct ciscvx_model {
 // Launchers (defined in disc.cu / vjp.cu), called by the host API in api.cu.
 namespace ciscvx {
 cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int prec, int layout,
-                              const double* X, const double* U, const double* s, void* A,
+                              bool compact, const double* X, const double* U, const double* s, void* A,
                               void* Bm, void* Bp, void* S, double* defect, double* penalty,
                               double* z, unsigned* status, cudaStream_t st);
 cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, int N, int nsub,

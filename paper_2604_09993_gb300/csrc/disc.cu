@@ -12,7 +12,8 @@
 
 namespace ciscvx {
 
-template <typename TP>
+// CMP: compact A/Bm/Bp (structural nonzeros only; strides nnzA / nnzB).
+template <typename TP, bool CMP>
 __global__ void __launch_bounds__(128) k_discretize(const DevModel* __restrict__ Mp, int N,
                                                     int nsub, int layout,
                                                     const double* __restrict__ X,
@@ -32,36 +33,39 @@ __global__ void __launch_bounds__(128) k_discretize(const DevModel* __restrict__
   const int nxt = M.nxt, nu = M.nu, nc = M.nc;
   const double* uL = (layout == CISCVX_FOH_NODE) ? U + k * nu : U + 2 * k * nu;
   const double* uR = uL + nu;
-  TP* Ak = A + (size_t)k * nxt * nxt;
-  TP* Bmk = Bm ? Bm + (size_t)k * nxt * nu : nullptr;
-  TP* Bpk = Bp ? Bp + (size_t)k * nxt * nu : nullptr;
+  const size_t sa = CMP ? (size_t)M.nnzA : (size_t)nxt * nxt;
+  const size_t sb = CMP ? (size_t)M.nnzB : (size_t)nxt * nu;
+  TP* Ak = A + k * sa;
+  TP* Bmk = Bm ? Bm + k * sb : nullptr;
+  TP* Bpk = Bp ? Bp + k * sb : nullptr;
   TP* Sk = S + (size_t)k * nxt;
   double* dk = defect + (size_t)k * nxt;
   double* pk = penalty ? penalty + (size_t)k * nc : nullptr;
   double* zk = z ? z + (size_t)k * nxt : nullptr;
   if (M.body[b].contact >= 0)
-    disc_link<TP, true>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL, uR, Ak, Bmk, Bpk,
-                        Sk, dk, pk, zk, status);
+    disc_link<TP, true, CMP>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL, uR, Ak, Bmk,
+                             Bpk, Sk, dk, pk, zk, status);
   else
-    disc_link<TP, false>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL, uR, Ak, Bmk, Bpk,
-                         Sk, dk, pk, zk, status);
+    disc_link<TP, false, CMP>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL, uR, Ak, Bmk,
+                              Bpk, Sk, dk, pk, zk, status);
 }
 
 cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int prec, int layout,
-                              const double* X, const double* U, const double* s, void* A,
-                              void* Bm, void* Bp, void* S, double* defect, double* penalty,
-                              double* z, unsigned* status, cudaStream_t st) {
+                              bool compact, const double* X, const double* U, const double* s,
+                              void* A, void* Bm, void* Bp, void* S, double* defect,
+                              double* penalty, double* z, unsigned* status, cudaStream_t st) {
   const long warps = (long)((N + 31) / 32) * nb;
   const int threads = single_cta_threads(warps);
   const long blocks = (warps * 32 + threads - 1) / threads;
-  if (prec == CISCVX_FP64)
-    k_discretize<double><<<(unsigned)blocks, threads, 0, st>>>(
-        dM, N, nsub, layout, X, U, s, (double*)A, (double*)Bm, (double*)Bp, (double*)S, defect,
-        penalty, z, status);
-  else
-    k_discretize<float><<<(unsigned)blocks, threads, 0, st>>>(
-        dM, N, nsub, layout, X, U, s, (float*)A, (float*)Bm, (float*)Bp, (float*)S, defect,
-        penalty, z, status);
+#define CISCVX_K(TP, CMP)                                                                    \
+  k_discretize<TP, CMP><<<(unsigned)blocks, threads, 0, st>>>(                                \
+      dM, N, nsub, layout, X, U, s, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, defect, penalty, z, status)
+  if (prec == CISCVX_FP64) {
+    if (compact) CISCVX_K(double, true); else CISCVX_K(double, false);
+  } else {
+    if (compact) CISCVX_K(float, true); else CISCVX_K(float, false);
+  }
+#undef CISCVX_K
   return cudaGetLastError();
 }
 

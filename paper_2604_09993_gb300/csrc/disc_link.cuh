@@ -68,7 +68,10 @@ __device__ __forceinline__ InputPenalty<TP> input_penalty(double t, TP tP, doubl
 
 // One link of one interval.  xk/xk1: node states k and k+1; uL/uR: FOH
 // controls; A/Bm/Bp/S/defect/pen/z: this interval's output blocks.
-template <typename TP, bool FOOT>
+// CMP: A, Bm, Bp point at this interval's compact values (structural
+// nonzeros only, at the link's offsets; see common.cuh) instead of its dense
+// blocks.
+template <typename TP, bool FOOT, bool CMP = false>
 __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, double sd,
                                           const double* __restrict__ xk,
                                           const double* __restrict__ xk1,
@@ -102,10 +105,12 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   const double vx0 = xk[rvx], vy0 = xk[rvy], om0 = xk[rom];
 
   // Translation in closed form (exact for RK4: polynomial of degree <= 3 in tau).
-  const double axm = 0.5 * (AxL + AxR), ax3 = AxL * (1.0 / 3.0) + AxR * (1.0 / 6.0);
-  const double aym = 0.5 * (AyL + AyR) - g, ay3 = AyL * (1.0 / 3.0) + AyR * (1.0 / 6.0) - 0.5 * g;
-  const double px1 = px0 + sd * vx0 + sd * sd * ax3, vx1 = vx0 + sd * axm;
-  const double py1 = py0 + sd * vy0 + sd * sd * ay3, vy1 = vy0 + sd * aym;
+  // (explicit fma: the same rounding in every instantiation of this function)
+  const double axm = 0.5 * (AxL + AxR), ax3 = fma(AxL, 1.0 / 3.0, AxR * (1.0 / 6.0));
+  const double aym = fma(0.5, AyL + AyR, -g), ay3 = fma(AyL, 1.0 / 3.0, fma(AyR, 1.0 / 6.0, -0.5 * g));
+  const double sd2 = sd * sd;
+  const double px1 = fma(sd2, ax3, fma(sd, vx0, px0)), vx1 = fma(sd, axm, vx0);
+  const double py1 = fma(sd2, ay3, fma(sd, vy0, py0)), vy1 = fma(sd, aym, vy0);
 
   constexpr bool foot = FOOT;  // B.contact >= 0; warp-uniform, dispatched by the kernel
   const int cin = B.cin;
@@ -317,49 +322,96 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   // ------------------------------------------------------------ outputs ---
   const TP one = TP(1);
   const TP sdT = TP(sd), s2_3 = TP(sd * sd / 3.0), s2_6 = TP(sd * sd / 6.0), s_2 = TP(0.5 * sd);
-  // Zero this link's rows of A, B-, B+ (and the contact's row) cooperatively,
-  // then write the structural entries.
-  warp_zero_chunks(A + (size_t)rpx * nxt, 3 * nxt, amask);
-  warp_zero_chunks(A + (size_t)rvx * nxt, 3 * nxt, amask);
-  if (nu > 0) {
-    warp_zero_chunks(Bm + (size_t)rpx * nu, 3 * nu, amask);
-    warp_zero_chunks(Bm + (size_t)rvx * nu, 3 * nu, amask);
-    warp_zero_chunks(Bp + (size_t)rpx * nu, 3 * nu, amask);
-    warp_zero_chunks(Bp + (size_t)rvx * nu, 3 * nu, amask);
-  }
-  if (foot) {
-    const int ry = 6 * nb + B.contact;
-    warp_zero_chunks(A + (size_t)ry * nxt, nxt, amask);
+  const int ry = foot ? 6 * nb + B.contact : -1;
+  if constexpr (!CMP) {
+    // Zero this link's rows of A, B-, B+ (and the contact's row) cooperatively,
+    // then write the structural entries.
+    warp_zero_chunks(A + (size_t)rpx * nxt, 3 * nxt, amask);
+    warp_zero_chunks(A + (size_t)rvx * nxt, 3 * nxt, amask);
     if (nu > 0) {
-      warp_zero_chunks(Bm + (size_t)ry * nu, nu, amask);
-      warp_zero_chunks(Bp + (size_t)ry * nu, nu, amask);
+      warp_zero_chunks(Bm + (size_t)rpx * nu, 3 * nu, amask);
+      warp_zero_chunks(Bm + (size_t)rvx * nu, 3 * nu, amask);
+      warp_zero_chunks(Bp + (size_t)rpx * nu, 3 * nu, amask);
+      warp_zero_chunks(Bp + (size_t)rvx * nu, 3 * nu, amask);
     }
+    if (foot) {
+      warp_zero_chunks(A + (size_t)ry * nxt, nxt, amask);
+      if (nu > 0) {
+        warp_zero_chunks(Bm + (size_t)ry * nu, nu, amask);
+        warp_zero_chunks(Bp + (size_t)ry * nu, nu, amask);
+      }
+    }
+    __syncwarp(amask);
   }
-  __syncwarp(amask);
-  A[(size_t)rpx * nxt + rpx] = one; A[(size_t)rpx * nxt + rvx] = sdT;
-  A[(size_t)rpy * nxt + rpy] = one; A[(size_t)rpy * nxt + rvy] = sdT;
-  A[(size_t)rth * nxt + rth] = tg.Pt[0]; A[(size_t)rth * nxt + rom] = tg.Pt[1];
-  A[(size_t)rvx * nxt + rvx] = one;
-  A[(size_t)rvy * nxt + rvy] = one;
-  A[(size_t)rom * nxt + rth] = tg.Pw[0]; A[(size_t)rom * nxt + rom] = tg.Pw[1];
+  // Entry (r, c) of A, the j-th compact A entry of this link (order in common.cuh).
+  TP* const Ac = A + (CMP ? B.a_off : 0);
+  auto a_put = [&](int r, int c, int j, TP v) {
+    if constexpr (CMP) Ac[j] = v; else A[(size_t)r * nxt + c] = v;
+  };
+  a_put(rpx, rpx, 0, one); a_put(rpx, rvx, 1, sdT);
+  a_put(rpy, rpy, 2, one); a_put(rpy, rvy, 3, sdT);
+  a_put(rth, rth, 4, tg.Pt[0]); a_put(rth, rom, 5, tg.Pt[1]);
+  a_put(rvx, rvx, 6, one);
+  a_put(rvy, rvy, 7, one);
+  a_put(rom, rth, 8, tg.Pw[0]); a_put(rom, rom, 9, tg.Pw[1]);
   // S
-  const double Spx = vx0 + 2.0 * sd * ax3, Spy = vy0 + 2.0 * sd * ay3;
+  const double Spx = fma(2.0 * sd, ax3, vx0), Spy = fma(2.0 * sd, ay3, vy0);
   S[rpx] = TP(Spx); S[rvx] = TP(axm);
   S[rpy] = TP(Spy); S[rvy] = TP(aym);
   S[rth] = tg.Pt[2]; S[rom] = tg.Pw[2];
-  // B-, B+
+
+  // Optional affine term z = x~(1) - A x~_k - B- u_L - B+ u_R - S s, formed from
+  // the stored (rounded) block values: rows px, py, th, vx, vy, om, y.
+  const bool wz = (z != nullptr);
+  double zr[7];
+  if (wz) {
+    zr[0] = px1 - double(S[rpx]) * sd - xk[rpx] - double(sdT) * xk[rvx];
+    zr[1] = py1 - double(S[rpy]) * sd - xk[rpy] - double(sdT) * xk[rvy];
+    zr[2] = th - double(S[rth]) * sd - double(tg.Pt[0]) * xk[rth] - double(tg.Pt[1]) * xk[rom];
+    zr[3] = vx1 - double(S[rvx]) * sd - xk[rvx];
+    zr[4] = vy1 - double(S[rvy]) * sd - xk[rvy];
+    zr[5] = om - double(S[rom]) * sd - double(tg.Pw[0]) * xk[rth] - double(tg.Pw[1]) * xk[rom];
+  }
+  // B-, B+: per input q of this link (slot order), entries in rows px (if the
+  // input pushes along x), py (along y), th, vx, vy, om, then y for a foot.
+  // nzx/nzy: the input has an x/y force component (tested on the bit pattern).
   if (nu > 0) {
+    int o = B.b_off;
     for (int i = 0; i < nin; ++i) {
       const int q = B.idx[i];
+      const bool nzx = abs_bits(B.ax[i]) != 0ull, nzy = abs_bits(B.ay[i]) != 0ull;
       const TP ax = TP(B.ax[i]), ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
-      Bm[(size_t)rpx * nu + q] = ax * s2_3; Bp[(size_t)rpx * nu + q] = ax * s2_6;
-      Bm[(size_t)rvx * nu + q] = ax * s_2;  Bp[(size_t)rvx * nu + q] = ax * s_2;
-      Bm[(size_t)rpy * nu + q] = ay * s2_3; Bp[(size_t)rpy * nu + q] = ay * s2_6;
-      Bm[(size_t)rvy * nu + q] = ay * s_2;  Bp[(size_t)rvy * nu + q] = ay * s_2;
-      Bm[(size_t)rth * nu + q] = pc * tg.Pt[3] + qc * tg.Pt[4] + tc * tg.Pt[5];
-      Bp[(size_t)rth * nu + q] = pc * tg.Pt[6] + qc * tg.Pt[7] + tc * tg.Pt[8];
-      Bm[(size_t)rom * nu + q] = pc * tg.Pw[3] + qc * tg.Pw[4] + tc * tg.Pw[5];
-      Bp[(size_t)rom * nu + q] = pc * tg.Pw[6] + qc * tg.Pw[7] + tc * tg.Pw[8];
+      const TP bmpx = ax * s2_3, bppx = ax * s2_6, bvx = ax * s_2;
+      const TP bmpy = ay * s2_3, bppy = ay * s2_6, bvy = ay * s_2;
+      const TP bmth = pc * tg.Pt[3] + qc * tg.Pt[4] + tc * tg.Pt[5];
+      const TP bpth = pc * tg.Pt[6] + qc * tg.Pt[7] + tc * tg.Pt[8];
+      const TP bmom = pc * tg.Pw[3] + qc * tg.Pw[4] + tc * tg.Pw[5];
+      const TP bpom = pc * tg.Pw[6] + qc * tg.Pw[7] + tc * tg.Pw[8];
+      if constexpr (CMP) {
+        if (nzx) { Bm[o] = bmpx; Bp[o] = bppx; ++o; }
+        if (nzy) { Bm[o] = bmpy; Bp[o] = bppy; ++o; }
+        Bm[o] = bmth; Bp[o] = bpth; ++o;
+        if (nzx) { Bm[o] = bvx; Bp[o] = bvx; ++o; }
+        if (nzy) { Bm[o] = bvy; Bp[o] = bvy; ++o; }
+        Bm[o] = bmom; Bp[o] = bpom; ++o;
+        if (foot) ++o;  // the y entry, written below
+      } else {
+        Bm[(size_t)rpx * nu + q] = bmpx; Bp[(size_t)rpx * nu + q] = bppx;
+        Bm[(size_t)rvx * nu + q] = bvx;  Bp[(size_t)rvx * nu + q] = bvx;
+        Bm[(size_t)rpy * nu + q] = bmpy; Bp[(size_t)rpy * nu + q] = bppy;
+        Bm[(size_t)rvy * nu + q] = bvy;  Bp[(size_t)rvy * nu + q] = bvy;
+        Bm[(size_t)rth * nu + q] = bmth; Bp[(size_t)rth * nu + q] = bpth;
+        Bm[(size_t)rom * nu + q] = bmom; Bp[(size_t)rom * nu + q] = bpom;
+      }
+      if (wz) {
+        const double a = uL[q], c = uR[q];
+        zr[0] -= double(bmpx) * a + double(bppx) * c;
+        zr[1] -= double(bmpy) * a + double(bppy) * c;
+        zr[2] -= double(bmth) * a + double(bpth) * c;
+        zr[3] -= double(bvx) * a + double(bvx) * c;
+        zr[4] -= double(bvy) * a + double(bvy) * c;
+        zr[5] -= double(bmom) * a + double(bpom) * c;
+      }
     }
   }
   // defect (Eq. (17b))
@@ -369,22 +421,24 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
 #pragma unroll
   for (int c = 0; c < 9; ++c) chk += double(tg.Pt[c]) + double(tg.Pw[c]);
 
-  int ry_ = -1;
   double y1 = 0.0;
   if (foot) {
-    ry_ = 6 * nb + B.contact;
-    const double y0 = xk[ry_];
-    y1 = y0 + sd * Yom;
+    const double y0 = xk[ry];
+    y1 = fma(sd, Yom, y0);
     pen[B.contact] = sd * Yom;
-    defect[ry_] = y1 - xk1[ry_];
-    TP* ay_ = A + (size_t)ry_ * nxt;
-    ay_[rpy] = tg.Yp[0]; ay_[rvy] = tg.Yp[1];
-    ay_[rth] = tg.Yr[0]; ay_[rom] = tg.Yr[1];
-    ay_[ry_] = one;
-    S[ry_] = TP(Yom) + tg.Yr[2] + tg.Yp[2];
+    defect[ry] = y1 - xk1[ry];
+    a_put(ry, rpy, 10, tg.Yp[0]);
+    a_put(ry, rth, 11, tg.Yr[0]);
+    a_put(ry, rvy, 12, tg.Yp[1]);
+    a_put(ry, rom, 13, tg.Yr[1]);
+    a_put(ry, ry, 14, one);
+    const TP Sy = TP(Yom) + tg.Yr[2] + tg.Yp[2];
+    S[ry] = Sy;
+    if (wz)
+      zr[6] = y1 - double(Sy) * sd - double(tg.Yp[0]) * xk[rpy] - double(tg.Yr[0]) * xk[rth] -
+              double(tg.Yp[1]) * xk[rvy] - double(tg.Yr[1]) * xk[rom] - xk[ry];
     if (nu > 0) {
-      TP* bm = Bm + (size_t)ry_ * nu;
-      TP* bp = Bp + (size_t)ry_ * nu;
+      int o = B.b_off;
       for (int i = 0; i < nin; ++i) {
         const int q = B.idx[i];
         const TP ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
@@ -392,30 +446,25 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         TP vp = pc * tg.Yr[6] + qc * tg.Yr[7] + tc * tg.Yr[8] + ay * tg.Yp[4];
         const int d = q - cin;
         if (d >= 0 && d < 3) { vm += tg.Yd[d]; vp += tg.Yd[3 + d]; }
-        bm[q] = vm;
-        bp[q] = vp;
+        if constexpr (CMP) {
+          o += 3 + (abs_bits(B.ax[i]) != 0ull ? 2 : 0) + (abs_bits(B.ay[i]) != 0ull ? 2 : 0);
+          Bm[o - 1] = vm;
+          Bp[o - 1] = vp;
+        } else {
+          Bm[(size_t)ry * nu + q] = vm;
+          Bp[(size_t)ry * nu + q] = vp;
+        }
+        if (wz) zr[6] -= double(vm) * uL[q] + double(vp) * uR[q];
       }
     }
-    chk += y1 + double(S[ry_]);
+    chk += y1 + double(Sy);
   }
   if (!finite_d(chk)) atomicOr(status, ST_NONFINITE);
 
-  // optional affine term z = x~(1) - A x~_k - B- u_L - B+ u_R - S s (with the returned blocks)
-  if (z) {
-    const int rows[7] = {rpx, rpy, rth, rvx, rvy, rom, ry_};
-    const double x1v[7] = {px1, py1, th, vx1, vy1, om, y1};
-    const int nr = foot ? 7 : 6;
-    for (int t = 0; t < nr; ++t) {
-      const int r = rows[t];
-      double acc = x1v[t] - double(S[r]) * sd;
-      // A's nonzeros in this row lie in this link's columns (and y_r for the y row)
-      for (int u = 0; u < nr; ++u) acc -= double(A[(size_t)r * nxt + rows[u]]) * xk[rows[u]];
-      for (int i = 0; i < nin; ++i) {
-        const int q = B.idx[i];
-        acc -= double(Bm[(size_t)r * nu + q]) * uL[q] + double(Bp[(size_t)r * nu + q]) * uR[q];
-      }
-      z[r] = acc;
-    }
+  if (wz) {
+    z[rpx] = zr[0]; z[rpy] = zr[1]; z[rth] = zr[2];
+    z[rvx] = zr[3]; z[rvy] = zr[4]; z[rom] = zr[5];
+    if (foot) z[ry] = zr[6];
   }
 }
 
