@@ -17,6 +17,8 @@ from .oracle import (  # noqa: F401
     flow,
     interval,
     linear_interval,
+    node,
+    node_value,
     rhs,
     vjp,
 )

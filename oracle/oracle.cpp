@@ -31,6 +31,10 @@
 //               contracted from the IND blocks (J^T times the cotangent).
 //   linear_interval()  the same integrator and IND applied to a linear
 //               right-hand side A_c x + B_c u (used only to pin the integrator).
+//   node()      the node constraints of Eqs. (17e)-(17f): the impact map G~
+//               (Eq. (6a) with the joint impulse eliminated, Sec. II-B) and the
+//               Fischer-Burmeister-relaxed impulse conditions Theta^delta
+//               (Eqs. (6b)-(6e), (16)), with Jacobians by dual numbers.
 //
 // Readings of points the paper leaves open (one auxiliary state per contact,
 // pseudo-Huber ramp h(z) = sqrt(1 + max(z,0)^2) - 1, joint reaction forces and
@@ -452,6 +456,207 @@ int oracle_linear_interval(int n, int m, const double* Ac, const double* Bc, int
     }
   };
   return ind_interval(F, n, m, nsub, x0, uL, uR, s, x1, A, Bm, Bp, S);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Node constraints: the impact map G~ and the relaxed impulse complementarity
+// Theta^delta imposed at every grid node (Sec. IV-C, Eqs. (17e)-(17f)), with
+// their Jacobians by the same forward-mode dual numbers.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Pseudo-Huber absolute value / norm with unit steepness (Sec. II notation):
+// sqrt(1 + x^2) - 1 (in the plane the tangential impulse is a scalar, so the
+// smooth norm and the smooth absolute value are the same function).
+template <class T> T smooth_abs(const T& x) { return sqrt(1.0 + x * x) - 1.0; }
+
+// Fischer-Burmeister relaxation, Eq. (16): FB^delta(a, b) = a + b - sqrt(a^2 + b^2 + delta).
+template <class T> T fischer_burmeister(const T& a, const T& b, double delta) {
+  return a + b - sqrt(a * a + b * b + delta);
+}
+
+// Solves the dense system K x = r (n x n, row-major, overwritten) by Gaussian
+// elimination with partial pivoting on the values.
+template <class T> void dense_solve(int n, std::vector<T>& K, std::vector<T>& r) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(value(K[i * n + c])) > std::fabs(value(K[piv * n + c]))) piv = i;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) std::swap(K[c * n + j], K[piv * n + j]);
+      std::swap(r[c], r[piv]);
+    }
+    for (int i = c + 1; i < n; ++i) {
+      const T f = K[i * n + c] / K[c * n + c];
+      for (int j = c; j < n; ++j) K[i * n + j] = K[i * n + j] - f * K[c * n + j];
+      r[i] = r[i] - f * r[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    T acc = r[c];
+    for (int j = c + 1; j < n; ++j) acc = acc - K[c * n + j] * r[j];
+    r[c] = acc / K[c * n + c];
+  }
+}
+
+// G~(x~+, x~-, Phi) and Theta^delta(x+, x-, Phi, Gamma) at one node.
+//
+// Impact dynamics Eq. (6a): M (v+ - v-) = J_c^T R_c Phi + grad C^T Lambda.
+// The joint impulse Lambda is eliminated with the post-impact joint
+// constraint at the velocity level, grad C v+ = 0 (Sec. II-B):
+//   w = v- + M^-1 J_c^T R_c Phi,  K = grad C M^-1 grad C^T,  Lambda = -K^-1 grad C w,
+// and G~ stacks q+ - q- (pose continuity), M (v+ - v-) - J_c^T R_c Phi -
+// grad C^T Lambda, and y+ - y- (auxiliary-state continuity).  Every
+// kinematic quantity is taken at the pre-impact pose q-.  M = diag(m, m, I)
+// per link; on flat ground R_c maps (Phi_t, Phi_n) to the world impulse
+// (Phi_t, Phi_n).
+//
+// Theta collects, per contact i, the Fischer-Burmeister relaxations
+// (Eq. (16)) of the impulse conditions Eqs. (6b)-(6e) and the sign
+// conditions that go with them:
+//   FB(Phi_n, phi),  FB(Phi_n, |c|~),  FB(Phi_n, |lambda^c|~),  FB(Gamma, rho),
+//   -Phi_n, -phi, -Gamma, -rho,
+// with phi the signed distance of the contact point, c = n^T J_c (v+ + e v-)
+// its normal velocity after impact plus e times before (Eq. (6c)),
+// lambda^c = t^T J_c v+ + Gamma d||Phi_t||~/dPhi_t (Eq. (6d)),
+// rho = |mu Phi_n|~ - ||Phi_t||~ (Eq. (6e)); |.|~ the pseudo-Huber absolute
+// value, which turns each "Phi_n times a signed quantity = 0" into the
+// complementarity 0 <= Phi_n perp |quantity|~ >= 0.
+template <class T>
+void node_eval(const OracleModel& M, const T* xp, const T* xm, const T* Phi, const T* Gam,
+               double delta, const double* e, T* g, T* th) {
+  const int nb = M.nb, nj = M.nj, nc = M.nc, nq = 3 * nb;
+  const T* qm = xm;
+  const T* vm = xm + nq;
+  const T* vp = xp + nq;
+  std::vector<double> minv(nq);
+  for (int b = 0; b < nb; ++b) {
+    minv[3 * b] = minv[3 * b + 1] = 1.0 / M.mass[b];
+    minv[3 * b + 2] = 1.0 / M.inertia[b];
+  }
+  // grad C (2 nj x nq): C_j = p_c + R(theta_c) rho_c - p_p - R(theta_p) rho_p.
+  std::vector<T> G((size_t)2 * nj * nq, T(0.0));
+  for (int j = 0; j < nj; ++j) {
+    const int c = M.jchild[j], p = M.jparent[j];
+    T rcx, rcy, rpx, rpy;
+    lever_arm(qm[3 * c + 2], M.jrho_c + 2 * j, rcx, rcy);
+    lever_arm(qm[3 * p + 2], M.jrho_p + 2 * j, rpx, rpy);
+    // d(R rho)/dtheta = (-r_y, r_x)
+    G[(2 * j) * nq + 3 * c] = G[(2 * j) * nq + 3 * c] + 1.0;
+    G[(2 * j + 1) * nq + 3 * c + 1] = G[(2 * j + 1) * nq + 3 * c + 1] + 1.0;
+    G[(2 * j) * nq + 3 * c + 2] = G[(2 * j) * nq + 3 * c + 2] - rcy;
+    G[(2 * j + 1) * nq + 3 * c + 2] = G[(2 * j + 1) * nq + 3 * c + 2] + rcx;
+    G[(2 * j) * nq + 3 * p] = G[(2 * j) * nq + 3 * p] - 1.0;
+    G[(2 * j + 1) * nq + 3 * p + 1] = G[(2 * j + 1) * nq + 3 * p + 1] - 1.0;
+    G[(2 * j) * nq + 3 * p + 2] = G[(2 * j) * nq + 3 * p + 2] + rpy;
+    G[(2 * j + 1) * nq + 3 * p + 2] = G[(2 * j + 1) * nq + 3 * p + 2] - rpx;
+  }
+  // J_c^T R_c Phi as a generalized impulse (nq), and the contact lever arms.
+  std::vector<T> Jphi(nq, T(0.0)), crx(nc), cry(nc);
+  for (int i = 0; i < nc; ++i) {
+    const int b = M.cbody[i];
+    lever_arm(qm[3 * b + 2], M.crho + 2 * i, crx[i], cry[i]);
+    const T& pt = Phi[2 * i];
+    const T& pn = Phi[2 * i + 1];
+    Jphi[3 * b] = Jphi[3 * b] + pt;
+    Jphi[3 * b + 1] = Jphi[3 * b + 1] + pn;
+    Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], pt, pn);
+  }
+  // Lambda = -K^-1 grad C w.
+  std::vector<T> w(nq);
+  for (int a = 0; a < nq; ++a) w[a] = vm[a] + minv[a] * Jphi[a];
+  std::vector<T> K((size_t)4 * nj * nj, T(0.0)), lam(2 * nj, T(0.0));
+  for (int r = 0; r < 2 * nj; ++r) {
+    for (int c2 = 0; c2 < 2 * nj; ++c2) {
+      T acc(0.0);
+      for (int a = 0; a < nq; ++a) acc = acc + G[r * nq + a] * minv[a] * G[c2 * nq + a];
+      K[r * 2 * nj + c2] = acc;
+    }
+    T acc(0.0);
+    for (int a = 0; a < nq; ++a) acc = acc + G[r * nq + a] * w[a];
+    lam[r] = acc;
+  }
+  if (nj > 0) dense_solve(2 * nj, K, lam);
+  for (int r = 0; r < 2 * nj; ++r) lam[r] = -lam[r];
+  // G~
+  for (int a = 0; a < nq; ++a) g[a] = xp[a] - xm[a];
+  for (int a = 0; a < nq; ++a) {
+    T acc = (1.0 / minv[a]) * (vp[a] - vm[a]) - Jphi[a];
+    for (int r = 0; r < 2 * nj; ++r) acc = acc - G[r * nq + a] * lam[r];
+    g[nq + a] = acc;
+  }
+  for (int i = 0; i < nc; ++i) g[2 * nq + i] = xp[2 * nq + i] - xm[2 * nq + i];
+  // Theta
+  for (int i = 0; i < nc; ++i) {
+    const int b = M.cbody[i];
+    const T& pt = Phi[2 * i];
+    const T& pn = Phi[2 * i + 1];
+    const T phi = qm[3 * b + 1] + cry[i];
+    // contact-point velocity p' + omega x r = (v_x - omega r_y, v_y + omega r_x)
+    const T vtp = vp[3 * b] - vp[3 * b + 2] * cry[i];
+    const T vnp = vp[3 * b + 1] + vp[3 * b + 2] * crx[i];
+    const T vnm = vm[3 * b + 1] + vm[3 * b + 2] * crx[i];
+    const T cn = vnp + e[i] * vnm;
+    const T lc = vtp + Gam[i] * (pt / sqrt(1.0 + pt * pt));
+    const T rho = smooth_abs(M.cmu[i] * pn) - smooth_abs(pt);
+    T* o = th + 8 * i;
+    o[0] = fischer_burmeister(pn, phi, delta);
+    o[1] = fischer_burmeister(pn, smooth_abs(cn), delta);
+    o[2] = fischer_burmeister(pn, smooth_abs(lc), delta);
+    o[3] = fischer_burmeister(Gam[i], rho, delta);
+    o[4] = -pn;
+    o[5] = -phi;
+    o[6] = -Gam[i];
+    o[7] = -rho;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// Node constraints at n nodes.  Xp, Xm [n][nxt] post-/pre-impact states,
+// Phi [n][2 nc] contact impulses (Phi_t, Phi_n) per contact, Gam [n][nc]
+// multipliers, delta > 0, e [nc] restitution coefficients.  Outputs (any may
+// be NULL): g [n][nxt] = G~, theta [n][8 nc] = Theta^delta, and their full
+// Jacobians with respect to z = (x~+, x~-, Phi, Gamma) (2 nxt + 3 nc
+// columns): Jg [n][nxt][ncol], Jth [n][8 nc][ncol].
+int oracle_node(const OracleModel* M, int n, const double* Xp, const double* Xm,
+                const double* Phi, const double* Gam, double delta, const double* e, double* g,
+                double* theta, double* Jg, double* Jth, int nthreads) {
+  if (!model_ok(M) || n < 1 || !(delta > 0.0)) return 1;
+  const int nxt = nxt_of(*M), nc = M->nc, ncol = 2 * nxt + 3 * nc;
+  if (ncol > MAXC) return 1;
+  parallel_for(n, nthreads, [&](long k) {
+    g_nd = ncol;
+    std::vector<Dual> xp(nxt), xm(nxt), ph(2 * nc), gm(nc), gv(nxt), tv(8 * nc);
+    for (int r = 0; r < nxt; ++r) {
+      xp[r] = Dual(Xp[k * nxt + r]); xp[r].d[r] = 1.0;
+      xm[r] = Dual(Xm[k * nxt + r]); xm[r].d[nxt + r] = 1.0;
+    }
+    for (int i = 0; i < 2 * nc; ++i) { ph[i] = Dual(Phi[k * 2 * nc + i]); ph[i].d[2 * nxt + i] = 1.0; }
+    for (int i = 0; i < nc; ++i) { gm[i] = Dual(Gam[k * nc + i]); gm[i].d[2 * nxt + 2 * nc + i] = 1.0; }
+    node_eval<Dual>(*M, xp.data(), xm.data(), ph.data(), gm.data(), delta, e, gv.data(), tv.data());
+    for (int r = 0; r < nxt; ++r) {
+      if (g) g[k * nxt + r] = gv[r].v;
+      if (Jg) for (int c = 0; c < ncol; ++c) Jg[((size_t)k * nxt + r) * ncol + c] = gv[r].d[c];
+    }
+    for (int r = 0; r < 8 * nc; ++r) {
+      if (theta) theta[k * 8 * nc + r] = tv[r].v;
+      if (Jth) for (int c = 0; c < ncol; ++c) Jth[((size_t)k * 8 * nc + r) * ncol + c] = tv[r].d[c];
+    }
+  });
+  return 0;
+}
+
+// The same G~ and Theta in plain FP64 (no derivatives), for finite differences.
+int oracle_node_value(const OracleModel* M, const double* xp, const double* xm, const double* Phi,
+                      const double* Gam, double delta, const double* e, double* g, double* theta) {
+  if (!model_ok(M) || !(delta > 0.0)) return 1;
+  node_eval<double>(*M, xp, xm, Phi, Gam, delta, e, g, theta);
+  return 0;
 }
 
 }  // extern "C"

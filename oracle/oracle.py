@@ -67,8 +67,13 @@ def _load():
             lib.oracle_linear_interval.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp,
                                                    ctypes.c_int, _dp, _dp, _dp, ctypes.c_double,
                                                    _dp, _dp, _dp, _dp, _dp]
+            lib.oracle_node.argtypes = [ctypes.POINTER(_CModel), ctypes.c_int, _dp, _dp, _dp, _dp,
+                                        ctypes.c_double, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+            lib.oracle_node_value.argtypes = [ctypes.POINTER(_CModel), _dp, _dp, _dp, _dp,
+                                              ctypes.c_double, _dp, _dp, _dp]
             for f in ("oracle_dims", "oracle_rhs", "oracle_flow", "oracle_interval",
-                      "oracle_discretize", "oracle_vjp", "oracle_linear_interval"):
+                      "oracle_discretize", "oracle_vjp", "oracle_linear_interval", "oracle_node",
+                      "oracle_node_value"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -223,3 +228,43 @@ def linear_interval(Ac, Bc, n_sub, x0, uL, uR, s):
                                           _d(uR), float(s), _d(x1), _d(A), _d(Bm), _d(Bp),
                                           _d(S)), "linear_interval")
     return x1, A, Bm, Bp, S
+
+
+def _nonempty(a):
+    a = _f64(a)
+    return a if a.size else np.zeros(1)
+
+
+def node(model, Xp, Xm, Phi, Gam, delta, e, threads=0):
+    """Node constraints G~ and Theta^delta at n nodes with their Jacobians.
+
+    Returns dict g [n, nxt], theta [n, 8 nc], Jg [n, nxt, ncol], Jth [n, 8 nc, ncol]
+    with columns z = (x~+ (nxt), x~- (nxt), Phi (2 nc: Phi_t, Phi_n per contact),
+    Gamma (nc))."""
+    m = _model(model)
+    Xp, Xm = _f64(Xp), _f64(Xm)
+    n = Xp.shape[0]
+    nc = m.nc
+    ncol = 2 * m.nxt + 3 * nc
+    Phi = _nonempty(np.asarray(Phi, dtype=np.float64).reshape(n, 2 * nc))
+    Gam = _nonempty(np.asarray(Gam, dtype=np.float64).reshape(n, nc))
+    e = _nonempty(np.asarray(e, dtype=np.float64).reshape(nc))
+    out = {"g": np.empty((n, m.nxt)), "theta": np.empty((n, 8 * nc)),
+           "Jg": np.empty((n, m.nxt, ncol)), "Jth": np.empty((n, 8 * nc, ncol))}
+    th = out["theta"] if nc else np.empty(1)
+    jth = out["Jth"] if nc else np.empty(1)
+    _check(_load().oracle_node(m.ptr, n, _d(Xp), _d(Xm), _d(Phi), _d(Gam), float(delta), _d(e),
+                               _d(out["g"]), _d(th), _d(out["Jg"]), _d(jth), int(threads)), "node")
+    return out
+
+
+def node_value(model, xp, xm, Phi, Gam, delta, e):
+    """G~ and Theta^delta at one node in plain FP64 (for finite differences)."""
+    m = _model(model)
+    nc = m.nc
+    g = np.empty(m.nxt)
+    th = np.empty(max(8 * nc, 1))
+    _check(_load().oracle_node_value(m.ptr, _d(_f64(xp)), _d(_f64(xm)), _d(_nonempty(Phi)),
+                                     _d(_nonempty(Gam)), float(delta), _d(_nonempty(e)), _d(g),
+                                     _d(th)), "node_value")
+    return g, th[:8 * nc]

@@ -15,7 +15,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
-PINS = ["tests/test_oracle_integrator.py", "tests/test_oracle_physics.py", "tests/test_oracle_vjp.py"]
+PINS = ["tests/test_oracle_integrator.py", "tests/test_oracle_physics.py", "tests/test_oracle_vjp.py",
+        "tests/test_oracle_node.py"]
 
 MUTATIONS = [
     ("parent joint torque sign", "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) - tau;",
@@ -55,6 +56,29 @@ MUTATIONS = [
     ("VJP node layout u_R", "double* gR = (layout == 0) ? gU + (k + 1) * nu",
      "double* gR = (layout == 0) ? gU + k * nu"),
     ("VJP node coupling", "gX[(k + 1) * nxt + r] -= w[k * nxt + r];", "gX[(k + 1) * nxt + r] += w[k * nxt + r];"),
+    # node constraints (impact map and relaxed impulse conditions)
+    ("joint impulse sign", "for (int r = 0; r < 2 * nj; ++r) lam[r] = -lam[r];",
+     "for (int r = 0; r < 2 * nj; ++r) lam[r] = lam[r];"),
+    ("grad C parent angle column", "G[(2 * j) * nq + 3 * p + 2] = G[(2 * j) * nq + 3 * p + 2] + rpy;",
+     "G[(2 * j) * nq + 3 * p + 2] = G[(2 * j) * nq + 3 * p + 2] - rpy;"),
+    ("K without M^-1", "acc = acc + G[r * nq + a] * minv[a] * G[c2 * nq + a];",
+     "acc = acc + G[r * nq + a] * G[c2 * nq + a];"),
+    ("impulse left out of w", "w[a] = vm[a] + minv[a] * Jphi[a];", "w[a] = vm[a];"),
+    ("contact impulse moment", "Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], pt, pn);",
+     "Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], pn, pt);"),
+    ("pose continuity sign", "for (int a = 0; a < nq; ++a) g[a] = xp[a] - xm[a];",
+     "for (int a = 0; a < nq; ++a) g[a] = xp[a] + xm[a];"),
+    ("restitution dropped", "const T cn = vnp + e[i] * vnm;", "const T cn = vnp;"),
+    ("tangential velocity from v-", "const T vtp = vp[3 * b] - vp[3 * b + 2] * cry[i];",
+     "const T vtp = vm[3 * b] - vm[3 * b + 2] * cry[i];"),
+    ("normal velocity lever arm", "const T vnp = vp[3 * b + 1] + vp[3 * b + 2] * crx[i];",
+     "const T vnp = vp[3 * b + 1] + vp[3 * b + 2] * cry[i];"),
+    ("smooth-norm gradient", "(pt / sqrt(1.0 + pt * pt))", "(pt)"),
+    ("Fischer-Burmeister sign", "return a + b - sqrt(a * a + b * b + delta);",
+     "return a + b + sqrt(a * a + b * b + delta) - 2.0 * sqrt(delta);"),
+    ("friction cone without mu", "const T rho = smooth_abs(M.cmu[i] * pn) - smooth_abs(pt);",
+     "const T rho = smooth_abs(pn) - smooth_abs(pt);"),
+    ("Gamma seed column", "gm[i].d[2 * nxt + 2 * nc + i] = 1.0;", "gm[i].d[2 * nxt + i] = 1.0;"),
 ]
 
 
