@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 2
+#define CISCVX_VERSION_MINOR 3
 
 typedef enum {
   CISCVX_OK = 0,
@@ -388,6 +388,78 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
 
 /* As ciscvx_sync_status, for the plan's status word. */
 ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* plan, void* stream);
+
+/* ----------------------------------------------------- node constraints --- */
+/*
+ * The constraints the transcription imposes at every grid node k = 0..n-1
+ * (Sec. IV-C, Eqs. (17e)-(17f)), for pre-impact state x~-_k, post-impact
+ * state x~+_k, contact impulses Phi_k and impulse multipliers Gamma_k:
+ *
+ *   G~(x~+, x~-, Phi) = 0: the impact map of Eq. (6a) with the joint impulse
+ *     eliminated by the post-impact joint constraint grad C v+ = 0 (Sec. II-B):
+ *       rows q:  q+ - q-                                       (3 n_b)
+ *       rows v:  M (v+ - v-) - J_c^T Phi + grad C^T mu,         (3 n_b)
+ *                mu = K^-1 grad C (v- + M^-1 J_c^T Phi),  K = grad C M^-1 grad C^T
+ *       rows y:  y+ - y-                                       (n_c)
+ *     with M = diag(m, m, I) per link, J_c the contact-point Jacobians, and
+ *     every kinematic quantity at the pre-impact pose q-.  On flat ground the
+ *     contact-frame impulse (Phi_t, Phi_n) is the world impulse.
+ *   Theta^delta(x+, x-, Phi, Gamma) <= 0: per contact i, 8 rows, the
+ *     Fischer-Burmeister relaxation FB(a,b) = a + b - sqrt(a^2 + b^2 + delta)
+ *     (Eq. (16)) of the impulse conditions Eqs. (6b)-(6e), then the sign
+ *     conditions that go with them:
+ *       FB(Phi_n, phi), FB(Phi_n, |c|~), FB(Phi_n, |lambda^c|~), FB(Gamma, rho),
+ *       -Phi_n, -phi, -Gamma, -rho,
+ *     phi the signed distance of the contact point (at q-), c = its normal
+ *     velocity under v+ plus e_i times that under v- (Eq. (6c)),
+ *     lambda^c = its tangential velocity under v+ + Gamma Phi_t / sqrt(1 + Phi_t^2)
+ *     (Eq. (6d)), rho = |mu Phi_n|~ - |Phi_t|~ (Eq. (6e)), and
+ *     |x|~ = sqrt(1 + x^2) - 1 the pseudo-Huber absolute value (norm).
+ *     "Phi_n times a signed quantity = 0" (Eqs. (6c), (6d)) is relaxed as the
+ *     complementarity of Phi_n with the quantity's pseudo-Huber magnitude.
+ *
+ * With the single penalty state per contact of this model, the remaining node
+ * constraint Psi (Eq. (17c)) is the linear y-_{k+1} - y+_k <= epsilon and
+ * needs no linearization.
+ */
+
+/* Theta rows per contact, and the local variables its Jacobian is taken in. */
+#define CISCVX_NODE_THETA_ROWS 8
+#define CISCVX_NODE_THETA_COLS 10
+/* Joints per model the node kernel supports. */
+#define CISCVX_NODE_MAX_JOINTS 12
+
+typedef struct {
+  double delta;               /* Fischer-Burmeister relaxation, finite, > 0 */
+  const double* restitution;  /* [n_c] host memory: e_i >= 0 finite (NULL if n_c == 0) */
+} ciscvx_node_params;
+
+/* Node constraints and their Jacobians at n_nodes nodes (lane = node; FP64).
+ *   Xp, Xm [n][n_x~]: post- and pre-impact states; Phi [n][2 n_c] impulses
+ *     (Phi_t, Phi_n) per contact; Gam [n][n_c] multipliers (device; Phi and
+ *     Gam may be NULL when n_c == 0).
+ *   g [n][n_x~]: G~ (device, required).
+ *   Jacobian blocks of G~ (device; each may be NULL to skip it):
+ *     Gvm  [n][3 n_b][3 n_b]: d(v rows)/d v-   (symmetric: -M P)
+ *     Gth  [n][3 n_b][n_b]  : d(v rows)/d theta-_b (the other pose
+ *                             coordinates do not enter the v rows)
+ *     Gphi [n][3 n_b][2 n_c]: d(v rows)/d Phi
+ *   The remaining blocks are constant and not stored: d(q rows)/dq+ = I,
+ *   d(q rows)/dq- = -I, d(v rows)/dv+ = M, d(y rows)/dy+ = I,
+ *   d(y rows)/dy- = -I, all others 0 (G~ does not depend on Gamma).
+ *   theta [n][n_c][8]: Theta^delta (device; required when n_c > 0).
+ *   dtheta [n][n_c][8][10] (device, may be NULL): each contact's rows
+ *     differentiated in the local variables of the link carrying it, in the
+ *     order (p_y-, theta-, v_x+, v_y+, omega+, v_y-, omega-, Phi_t, Phi_n,
+ *     Gamma); Theta's derivatives in every other variable are 0.
+ * Errors: EINVAL (nulls, n_nodes < 1, delta or restitution invalid),
+ * EUNSUPPORTED (more than CISCVX_NODE_MAX_JOINTS joints, or a link that is the
+ * child of two joints: the joint graph must be a forest), ECUDA. */
+ciscvx_status ciscvx_node_linearize(const ciscvx_model* model, int n_nodes, const double* Xp,
+                                    const double* Xm, const double* Phi, const double* Gam,
+                                    const ciscvx_node_params* params, double* g, double* Gvm,
+                                    double* Gth, double* Gphi, double* theta, double* dtheta,
+                                    void* stream);
 
 /* ------------------------------------------------ allocation-free VJP --- */
 

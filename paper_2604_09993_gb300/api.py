@@ -30,6 +30,7 @@ EXPORTS = (
     "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp", "ciscvx_batch_autotune",
     "ciscvx_batch_sync_status", "ciscvx_batch_run_host",
     "ciscvx_model_pattern", "ciscvx_model_nnz", "ciscvx_discretize_compact",
+    "ciscvx_node_linearize",
 )
 FORMAT = {"dense": 0, "compact": 1}
 
@@ -52,6 +53,10 @@ class _BatchIO(ctypes.Structure):
 
 class _BatchVjpIO(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("X", "U", "s", "w", "rho", "gX", "gU", "gs", "L")]
+
+
+class _NodeParams(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("restitution", ctypes.POINTER(ctypes.c_double))]
 
 
 class CiscvxError(RuntimeError):
@@ -113,6 +118,9 @@ def load(path: str | None = None):
     lib.ciscvx_model_pattern.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), I32, I32, I32, I32]
     lib.ciscvx_model_nnz.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.ciscvx_node_linearize.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                          ctypes.POINTER(_NodeParams), _vp, _vp, _vp, _vp, _vp,
+                                          _vp, _vp]
     lib.ciscvx_discretize_compact.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _vp, _vp]
@@ -142,7 +150,7 @@ def load(path: str | None = None):
               "ciscvx_batch_offsets", "ciscvx_batch_get_tune", "ciscvx_batch_discretize",
               "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp",
               "ciscvx_batch_autotune", "ciscvx_batch_sync_status", "ciscvx_model_pattern",
-              "ciscvx_model_nnz", "ciscvx_discretize_compact"):
+              "ciscvx_model_nnz", "ciscvx_discretize_compact", "ciscvx_node_linearize"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -315,6 +323,39 @@ def discretize_compact(model: Model, X, U, s, n_sub: int, precision: str = "fp64
         _ptr(s), _ptr(out["A"]), _ptr(out["Bm"]) if nzb else None, _ptr(out["Bp"]) if nzb else None,
         _ptr(out["S"]), _ptr(out["defect"]), _ptr(out["penalty"]) if nc else None,
         _ptr(out.get("z")), _stream()))
+    return out
+
+
+def node_linearize(model: Model, Xp, Xm, Phi, Gam, delta: float, restitution,
+                   jacobians: bool = True, out: dict | None = None):
+    """ciscvx_node_linearize: node constraints G~ / Theta^delta and their Jacobians.
+
+    Xp, Xm [n, nxt], Phi [n, 2 nc], Gam [n, nc]: device float64 tensors;
+    restitution: nc host floats.  Returns dict g, theta and, with jacobians,
+    Gvm, Gth, Gphi, dtheta (layouts in include/ciscvx.h)."""
+    import torch
+    f64 = torch.float64
+    _need(Xp, "Xp", f64); _need(Xm, "Xm", f64)
+    n = Xp.shape[0]
+    nq, nc, nb = 3 * model.nb, model.ny, model.nb
+    dev = Xp.device
+    if nc:
+        _need(Phi, "Phi", f64); _need(Gam, "Gam", f64)
+    if out is None:
+        out = {"g": torch.empty((n, model.nxt), dtype=f64, device=dev),
+               "theta": torch.empty((n, nc, 8), dtype=f64, device=dev)}
+        if jacobians:
+            out.update(Gvm=torch.empty((n, nq, nq), dtype=f64, device=dev),
+                       Gth=torch.empty((n, nq, nb), dtype=f64, device=dev),
+                       Gphi=torch.empty((n, nq, 2 * nc), dtype=f64, device=dev),
+                       dtheta=torch.empty((n, nc, 8, 10), dtype=f64, device=dev))
+    e = (ctypes.c_double * max(nc, 1))(*[float(v) for v in np.asarray(restitution, dtype=np.float64).reshape(-1)])
+    prm = _NodeParams(float(delta), e)
+    has = lambda k: _ptr(out[k]) if out.get(k) is not None and (nc or k not in ("theta", "Gphi", "dtheta")) else None  # noqa: E731
+    _check(load().ciscvx_node_linearize(
+        model.handle, int(n), _ptr(Xp), _ptr(Xm), _ptr(Phi) if nc else None, _ptr(Gam) if nc else None,
+        ctypes.byref(prm), _ptr(out["g"]), has("Gvm"), has("Gth"), has("Gphi"), has("theta"),
+        has("dtheta"), _stream()))
     return out
 
 

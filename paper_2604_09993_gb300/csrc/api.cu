@@ -54,9 +54,23 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   M.nxt = 6 * nb + nc;
   M.nu = 3 * nj + 3 * nc;
   M.g = d->gravity;
+  M.tree = 1;
   for (int b = 0; b < nb; ++b) {
     M.body[b].contact = -1;
     M.body[b].cin = -1;
+    M.mass[b] = d->bodies[b].mass;
+    M.inertia[b] = d->bodies[b].inertia;
+    M.minv[b] = 1.0 / d->bodies[b].mass;
+    M.iinv[b] = 1.0 / d->bodies[b].inertia;
+  }
+  for (int j = 0; j < nj; ++j) {
+    const ciscvx_joint_desc& J = d->joints[j];
+    M.jpar[j] = J.parent;
+    M.jchi[j] = J.child;
+    M.jrp[j][0] = J.rho_parent[0]; M.jrp[j][1] = J.rho_parent[1];
+    M.jrc[j][0] = J.rho_child[0]; M.jrc[j][1] = J.rho_child[1];
+    for (int i = 0; i < j; ++i)
+      if (d->joints[i].child == J.child) M.tree = 0;
   }
   for (int b = 0; b < nb; ++b) {
     const double m = d->bodies[b].mass, I = d->bodies[b].inertia;
@@ -354,6 +368,39 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
                              precision, layout, X, U, s, w, rho, gX, gU, gs, L, workspace,
                              m->status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
+  return ok();
+}
+
+ciscvx_status ciscvx_node_linearize(const ciscvx_model* m, int n, const double* Xp,
+                                    const double* Xm, const double* Phi, const double* Gam,
+                                    const ciscvx_node_params* params, double* g, double* Gvm,
+                                    double* Gth, double* Gphi, double* theta, double* dtheta,
+                                    void* stream) {
+  if (!m || !params) return fail(CISCVX_EINVAL, "null model or params");
+  if (n < 1) return fail(CISCVX_EINVAL, "n_nodes must be >= 1 (got %d)", n);
+  const DevModel& M = m->host;
+  if (!M.tree)
+    return fail(CISCVX_EUNSUPPORTED, "node constraints need every link to be the child of at most one joint");
+  if (M.nj > NODE_MAXJ)
+    return fail(CISCVX_EUNSUPPORTED, "node constraints support at most %d joints", NODE_MAXJ);
+  if (!(std::isfinite(params->delta) && params->delta > 0.0))
+    return fail(CISCVX_EINVAL, "delta must be finite and > 0");
+  if (!Xp || !Xm || !g) return fail(CISCVX_EINVAL, "null state or residual array");
+  if (M.nc > 0 && (!Phi || !Gam || !theta || !params->restitution))
+    return fail(CISCVX_EINVAL, "null impulse, multiplier, theta or restitution array");
+  NodeParams P;
+  std::memset(&P, 0, sizeof P);
+  P.delta = params->delta;
+  for (int i = 0; i < M.nc; ++i) {
+    const double e = params->restitution[i];
+    if (!(std::isfinite(e) && e >= 0.0)) return fail(CISCVX_EINVAL, "restitution %d must be finite and >= 0", i);
+    P.e[i] = e;
+  }
+  if (node_smem_per_warp(M) > 200u * 1024u)
+    return fail(CISCVX_EUNSUPPORTED, "model too large for the node kernel's shared memory");
+  cudaError_t e = launch_node(M, m->dev, n, Xp, Xm, Phi, Gam, P, g, Gvm, Gth, Gphi, theta, dtheta,
+                              m->status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "node launch");
   return ok();
 }
 

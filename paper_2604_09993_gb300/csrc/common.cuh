@@ -72,7 +72,13 @@ constexpr int A_PER_LINK = 10, A_PER_FOOT = 5;
 struct DevModel {
   int nb, nj, nc, nxt, nu, nslot;   // nslot = sum of nin over links
   int nnzA, nnzB;                    // structural nonzeros of A and of B-/B+ (compact outputs)
+  int tree;                          // every link is the child of at most one joint
   double g;
+  // joints and link inertia (node constraints: impact map)
+  int jpar[MAXJ], jchi[MAXJ];
+  double jrp[MAXJ][2], jrc[MAXJ][2];  // anchors in the parent / child body frame
+  double mass[MAXB], inertia[MAXB];
+  double minv[MAXB], iinv[MAXB];      // 1 / mass, 1 / inertia
   int in_n[MAXU];        // per input: number of (link, slot) contributions (1 or 2)
   int in_slot[MAXU][2];  // per input: partial slots that contribute
   DevBody body[MAXB];
@@ -235,6 +241,17 @@ cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, i
                        const double* w, const double* rho, double* gX, double* gU, double* gs,
                        double* L, void* ws, unsigned* status, cudaStream_t st);
 size_t vjp_workspace_bytes(int nb, int nu, int nslot, int N, int layout);
+// Node constraints (node.cu).
+struct NodeParams {
+  double delta;     // Fischer-Burmeister relaxation
+  double e[MAXB];   // restitution per contact
+};
+constexpr int NODE_MAXJ = 12;  // joints per model the node kernel supports
+size_t node_smem_per_warp(const DevModel& M);
+cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const double* Xp,
+                        const double* Xm, const double* Phi, const double* Gam,
+                        const NodeParams& P, double* g, double* Gvm, double* Gth, double* Gphi,
+                        double* theta, double* dtheta, unsigned* status, cudaStream_t st);
 // Records a formatted last-error message (thread-local) and returns st.
 ciscvx_status set_error(ciscvx_status st, const char* fmt, ...);
 }  // namespace ciscvx

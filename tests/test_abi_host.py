@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert lib.ciscvx_version() == 2
+    assert lib.ciscvx_version() == 3
 
 
 def test_null_arguments_rejected(lib):
@@ -50,6 +50,11 @@ def test_null_arguments_rejected(lib):
     n = ctypes.c_size_t()
     assert lib.ciscvx_workspace_size(None, 1, 10, 0, ctypes.byref(n)) == api.EINVAL
     assert lib.ciscvx_model_dims(None, None, None, None) == api.EINVAL
+    prm = api._NodeParams(1e-3, None)
+    assert lib.ciscvx_node_linearize(None, 4, None, None, None, None, ctypes.byref(prm), None,
+                                     None, None, None, None, None, None) == api.EINVAL
+    assert lib.ciscvx_discretize_compact(None, 10, 4, 0, 0, None, None, None, None, None, None,
+                                         None, None, None, None, None) == api.EINVAL
 
 
 def _desc(api, nb=2, joints=((0, 1),), contacts=((1,),), mass=1.0):

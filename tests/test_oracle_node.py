@@ -215,6 +215,16 @@ def test_node_jacobian_structure():
     assert not np.any(J[V, :nq]) and not np.any(J[V, 2 * nq:nxt])
     assert not np.any(J[V, nxt + 0:nxt + nq:3]) and not np.any(J[V, nxt + 1:nxt + nq:3])
     assert not np.any(J[V, nxt + 2 * nq:2 * nxt]) and not np.any(J[:, 2 * nxt + 2 * nc:])
+    # Theta depends on contact i's link only through (p_y-, theta-, v_x+, v_y+,
+    # omega+, v_y-, omega-) and on (Phi_t, Phi_n, Gamma) of contact i
+    Jt = out["Jth"][0]
+    for i, b in enumerate(R["contact_body"]):
+        cols = [nxt + 3 * b + 1, nxt + 3 * b + 2, nq + 3 * b, nq + 3 * b + 1, nq + 3 * b + 2,
+                nxt + nq + 3 * b + 1, nxt + nq + 3 * b + 2, 2 * nxt + 2 * i, 2 * nxt + 2 * i + 1,
+                2 * nxt + 2 * nc + i]
+        mask = np.ones(Jt.shape[1], bool)
+        mask[cols] = False
+        assert not np.any(Jt[8 * i:8 * i + 8][:, mask])
     Gvm = J[V, nxt + nq:nxt + 2 * nq]
     assert np.allclose(Gvm, Gvm.T, atol=1e-13)
     assert np.max(np.linalg.eigvalsh(Gvm)) <= 1e-12  # -M P is negative semidefinite
