@@ -29,6 +29,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -224,6 +226,43 @@ class BatchWorkload:
 
     def e2e_free(self):
         self.host_in = self.host_out = self.dev_in = None
+        self.torch.cuda.empty_cache()
+
+    # node constraints (impact map + relaxed impulse conditions) at every node
+    # of every instance: one ciscvx_node_linearize call per model over its
+    # instances' nodes (pre-impact states = the node states, post-impact =
+    # a seeded perturbation, impulses and multipliers seeded)
+    NODE_DELTA = 1e-3
+
+    def node_setup(self):
+        torch, b = self.torch, self.batch
+        p0 = self.plan("fp32_phi")
+        gen = torch.Generator(device=self.dev)
+        gen.manual_seed(1234)
+        self.node_jobs = []
+        for mi, m in enumerate(self.models):
+            inst = np.nonzero(b.model_idx == mi)[0]
+            if len(inst) == 0:
+                continue
+            # the node states of this model's instances, gathered (setup only, not timed)
+            idx = np.concatenate([np.arange(p0.offsets[i]["X"], p0.offsets[i]["X"] + (int(b.Ns[i]) + 1) * m.nxt)
+                                  for i in inst])
+            n = len(idx) // m.nxt
+            Xm = self.X[torch.from_numpy(idx).to(self.dev)].view(n, m.nxt).contiguous()
+            Xp = (Xm + 0.1 * torch.randn(Xm.shape, generator=gen, device=self.dev, dtype=torch.float64)).contiguous()
+            Phi = torch.randn((n, 2 * m.ny), generator=gen, device=self.dev, dtype=torch.float64)
+            Gam = torch.rand((n, m.ny), generator=gen, device=self.dev, dtype=torch.float64)
+            e = np.full(m.ny, 0.3)
+            out = self.api.node_linearize(m, Xp, Xm, Phi, Gam, self.NODE_DELTA, e)
+            self.node_jobs.append((m, Xp, Xm, Phi, Gam, e, out))
+        return sum(j[1].shape[0] for j in self.node_jobs)
+
+    def node_step(self):
+        for m, Xp, Xm, Phi, Gam, e, out in self.node_jobs:
+            self.api.node_linearize(m, Xp, Xm, Phi, Gam, self.NODE_DELTA, e, out=out)
+
+    def node_free(self):
+        self.node_jobs = None
         self.torch.cuda.empty_cache()
 
 
@@ -432,6 +471,21 @@ def run_ours(args):
 
     e2e = None if args.no_e2e else measure_e2e("dense")
 
+    # node constraints: every node of every instance, one call per model
+    nodes = None
+    if spec["kind"] == "batch" and not args.no_nodes:
+        wl.free(prec)
+        n_nodes = wl.node_setup()
+        barrier()
+        tn = time_steps(torch, wl.node_step, args.steps, args.warmup, stream)
+        barrier()
+        wl.check_status()
+        tn, = max_over_ranks([tn])
+        nodes = {"metric": "linearized nodes/s (impact map + relaxed impulse conditions, FP64)",
+                 "value": n_nodes * world * args.steps / tn, "unit": "nodes/s",
+                 "nodes_per_gpu": n_nodes, "ms_per_call": tn / args.steps * 1e3}
+        wl.node_free()
+
     # the same step with compact outputs (structural nonzeros of A, B-, B+ only)
     compact = None
     if spec["kind"] == "batch" and not args.no_compact:
@@ -476,6 +530,7 @@ def run_ours(args):
         "roofline": roof,
         "e2e": e2e,
         "compact_outputs": compact,
+        "node_constraints": nodes,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -514,6 +569,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compact", action="store_true", help="skip the compact-output measurement")
+    ap.add_argument("--no-nodes", action="store_true", help="skip the node-constraint measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

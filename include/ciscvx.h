@@ -426,8 +426,9 @@ ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* plan, void* stre
 /* Theta rows per contact, and the local variables its Jacobian is taken in. */
 #define CISCVX_NODE_THETA_ROWS 8
 #define CISCVX_NODE_THETA_COLS 10
-/* Joints per model the node kernel supports. */
+/* Joints per model, and joints attached to one link, the node kernel supports. */
 #define CISCVX_NODE_MAX_JOINTS 12
+#define CISCVX_NODE_MAX_JOINTS_PER_LINK 8
 
 typedef struct {
   double delta;               /* Fischer-Burmeister relaxation, finite, > 0 */
@@ -453,8 +454,9 @@ typedef struct {
  *     order (p_y-, theta-, v_x+, v_y+, omega+, v_y-, omega-, Phi_t, Phi_n,
  *     Gamma); Theta's derivatives in every other variable are 0.
  * Errors: EINVAL (nulls, n_nodes < 1, delta or restitution invalid),
- * EUNSUPPORTED (more than CISCVX_NODE_MAX_JOINTS joints, or a link that is the
- * child of two joints: the joint graph must be a forest), ECUDA. */
+ * EUNSUPPORTED (more than CISCVX_NODE_MAX_JOINTS joints or more than
+ * CISCVX_NODE_MAX_JOINTS_PER_LINK on one link, or a link that is the child of
+ * two joints: the joint graph must be a forest), ECUDA. */
 ciscvx_status ciscvx_node_linearize(const ciscvx_model* model, int n_nodes, const double* Xp,
                                     const double* Xm, const double* Phi, const double* Gam,
                                     const ciscvx_node_params* params, double* g, double* Gvm,

@@ -3,6 +3,7 @@
 // Validation, the per-link device tables (coefficients of every input on every
 // link, see common.cuh), the device status word, thread-local error messages
 // and the launches.  Compute calls allocate nothing.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -47,6 +48,62 @@ ciscvx_status add_input(DevModel& M, int b, int q, double ax, double ay, double 
   return CISCVX_OK;
 }
 
+// Symbolic part of the node kernel's factorization of K = C' M^-1 C'^T (for
+// forests of at most NODE_MAXJ joints): a children-first order of the joints
+// (depth-first post-order from the roots), each row's first stored column
+// (the earliest joint sharing a link with it) and the skyline offsets.
+void node_symbolic(DevModel& M) {
+  const int nj = M.nj, nb = M.nb;
+  if (!M.tree || nj > NODE_MAXJ) return;
+  for (int b = 0; b < nb; ++b)
+    if (M.nadj[b] > NODE_MAXADJ) return;
+  // joint whose child is link b (or -1)
+  int pj[MAXB];
+  for (int b = 0; b < nb; ++b) pj[b] = -1;
+  for (int j = 0; j < nj; ++j) pj[M.jchi[j]] = j;
+  int pos = 0;
+  bool done[MAXJ] = {false};
+  // iterative post-order: a joint is emitted once every joint hanging below its child link is
+  int stack[MAXJ], sp = 0;
+  for (int r = 0; r < nj; ++r) {
+    if (pj[M.jpar[r]] >= 0) continue;  // not a root
+    stack[sp++] = r;
+    while (sp > 0) {
+      const int j = stack[sp - 1];
+      int next = -1;
+      for (int c = 0; c < nj; ++c)
+        if (!done[c] && M.jpar[c] == M.jchi[j]) { next = c; break; }
+      if (next >= 0) { stack[sp++] = next; continue; }
+      done[j] = true;
+      M.nord[pos] = j;
+      M.npos[j] = pos++;
+      --sp;
+    }
+  }
+  for (int j = 0; j < nj; ++j)
+    if (!done[j]) { M.nord[pos] = j; M.npos[j] = pos++; }  // unreachable for a forest
+  const int nk = 2 * nj;
+  int off = 0;
+  for (int i = 0; i < nk; ++i) {
+    const int j = M.nord[i >> 1];
+    int first = M.npos[j];
+    for (int q = 0; q < nj; ++q) {
+      const bool share = M.jchi[q] == M.jchi[j] || M.jchi[q] == M.jpar[j] ||
+                         M.jpar[q] == M.jchi[j] || M.jpar[q] == M.jpar[j];
+      if (share && M.npos[q] < first) first = M.npos[q];
+    }
+    M.nf[i] = 2 * first;
+    M.noff[i] = off;
+    off += i - M.nf[i] + 1;
+  }
+  M.noff[nk] = off;
+  for (int b = 0; b < nb; ++b) {
+    int lo = nk;
+    for (int t = 0; t < M.nadj[b] && t < NODE_MAXADJ; ++t) lo = std::min(lo, 2 * M.npos[M.adj[b][t] >> 1]);
+    M.lmin[b] = lo;
+  }
+}
+
 ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   std::memset(&M, 0, sizeof M);
   const int nb = d->n_bodies, nj = d->n_joints, nc = d->n_contacts;
@@ -65,6 +122,13 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   }
   for (int j = 0; j < nj; ++j) {
     const ciscvx_joint_desc& J = d->joints[j];
+    for (int role = 0; role < 2; ++role) {
+      const int b = role ? J.parent : J.child;
+      if (b >= 0 && b < nb) {
+        if (M.nadj[b] < NODE_MAXADJ) M.adj[b][M.nadj[b]] = (j << 1) | role;
+        ++M.nadj[b];  // counts past NODE_MAXADJ mark the model as outside the node kernel
+      }
+    }
     M.jpar[j] = J.parent;
     M.jchi[j] = J.child;
     M.jrp[j][0] = J.rho_parent[0]; M.jrp[j][1] = J.rho_parent[1];
@@ -144,6 +208,7 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   }
   M.nnzA = aoff;
   M.nnzB = boff;
+  node_symbolic(M);
   return CISCVX_OK;
 }
 
@@ -383,6 +448,9 @@ ciscvx_status ciscvx_node_linearize(const ciscvx_model* m, int n, const double* 
     return fail(CISCVX_EUNSUPPORTED, "node constraints need every link to be the child of at most one joint");
   if (M.nj > NODE_MAXJ)
     return fail(CISCVX_EUNSUPPORTED, "node constraints support at most %d joints", NODE_MAXJ);
+  for (int b = 0; b < M.nb; ++b)
+    if (M.nadj[b] > NODE_MAXADJ)
+      return fail(CISCVX_EUNSUPPORTED, "node constraints support at most %d joints on one link", NODE_MAXADJ);
   if (!(std::isfinite(params->delta) && params->delta > 0.0))
     return fail(CISCVX_EINVAL, "delta must be finite and > 0");
   if (!Xp || !Xm || !g) return fail(CISCVX_EINVAL, "null state or residual array");
@@ -396,7 +464,7 @@ ciscvx_status ciscvx_node_linearize(const ciscvx_model* m, int n, const double* 
     if (!(std::isfinite(e) && e >= 0.0)) return fail(CISCVX_EINVAL, "restitution %d must be finite and >= 0", i);
     P.e[i] = e;
   }
-  if (node_smem_per_warp(M) > 200u * 1024u)
+  if (node_smem_per_warp(M) > 220u * 1024u)
     return fail(CISCVX_EUNSUPPORTED, "model too large for the node kernel's shared memory");
   cudaError_t e = launch_node(M, m->dev, n, Xp, Xm, Phi, Gam, P, g, Gvm, Gth, Gphi, theta, dtheta,
                               m->status, (cudaStream_t)stream);

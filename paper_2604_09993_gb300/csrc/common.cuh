@@ -35,6 +35,8 @@ constexpr int MAXIN = CISCVX_MAX_INPUTS_PER_BODY;
 constexpr int MAXJ = 2 * MAXB;          // joints per model (<= 4 per link)
 constexpr int MAXU = 3 * MAXJ + 3 * MAXB;
 constexpr int MAXSUB_VJP = CISCVX_MAX_VJP_SUBSTEPS;
+constexpr int NODE_MAXJ = CISCVX_NODE_MAX_JOINTS;             // joints the node kernel supports
+constexpr int NODE_MAXADJ = CISCVX_NODE_MAX_JOINTS_PER_LINK;  // joints on one link it supports
 
 // device status bits
 constexpr unsigned ST_NONFINITE = 1u;
@@ -79,6 +81,17 @@ struct DevModel {
   double jrp[MAXJ][2], jrc[MAXJ][2];  // anchors in the parent / child body frame
   double mass[MAXB], inertia[MAXB];
   double minv[MAXB], iinv[MAXB];      // 1 / mass, 1 / inertia
+  int nadj[MAXB];                     // joints attached to each link (node kernel)
+  int adj[MAXB][NODE_MAXADJ];         // (joint << 1) | (1 if the link is the joint's parent)
+  // Node kernel: K = C' M^-1 C'^T in skyline form.  Joints are ordered
+  // children first (post-order of the joint tree), so K's Cholesky factor has
+  // no fill outside each row's envelope [nf[i], i] (a forest's joint graph is
+  // chordal with that elimination order).  Row i = 2 * position + component.
+  int npos[MAXJ];                     // position of joint j in the order
+  int nord[MAXJ];                     // joint at each position
+  int nf[2 * NODE_MAXJ];              // first stored column of each row of K
+  int noff[2 * NODE_MAXJ + 1];        // offset of each row in the skyline storage
+  int lmin[MAXB];                     // first row of K touched by a joint on link b
   int in_n[MAXU];        // per input: number of (link, slot) contributions (1 or 2)
   int in_slot[MAXU][2];  // per input: partial slots that contribute
   DevBody body[MAXB];
@@ -246,7 +259,6 @@ struct NodeParams {
   double delta;     // Fischer-Burmeister relaxation
   double e[MAXB];   // restitution per contact
 };
-constexpr int NODE_MAXJ = 12;  // joints per model the node kernel supports
 size_t node_smem_per_warp(const DevModel& M);
 cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const double* Xp,
                         const double* Xm, const double* Phi, const double* Gam,
