@@ -25,12 +25,29 @@
 // joint lists, so no dense C' is formed.  FP64 throughout (the state
 // precision).
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 
 namespace ciscvx {
 
 namespace {
+
+// What the node kernel reads of a model, passed by value as a kernel
+// parameter (constant bank: uniform loads are broadcast from the constant
+// cache instead of going through L1).
+struct NodeTab {
+  int nb, nj, nc, nxt;
+  int nadj[MAXB];
+  unsigned char adj[MAXB][NODE_MAXADJ];  // (joint << 1) | (1 if the link is the joint's parent)
+  int npos[NODE_MAXJ], nord[NODE_MAXJ], jchi[NODE_MAXJ], jpar[NODE_MAXJ];
+  int nf[2 * NODE_MAXJ], noff[2 * NODE_MAXJ + 1];
+  int lmin[MAXB], contact[MAXB];
+  double jrc[NODE_MAXJ][2], jrp[NODE_MAXJ][2];
+  double mass[MAXB], inertia[MAXB], minv[MAXB], iinv[MAXB];
+  double crho[MAXB][2], mu[MAXB];
+  double delta, e[MAXB];
+};
 
 // Per-lane scratch layout (in doubles; each element is a row of 32 lanes).
 struct NodeLayout {
@@ -57,7 +74,7 @@ __host__ __device__ inline NodeLayout node_layout(int nb, int nj, int nc, int ns
 // Solves K x = x in place with the L D L^T factor (one multiply per row);
 // x is zero in rows before i0 (the caller zeroes them), so the forward pass
 // starts at row i0.
-__device__ __forceinline__ void ldl_solve(const DevModel& M, double* sm, const NodeLayout& Ly,
+__device__ __forceinline__ void ldl_solve(const NodeTab& M, double* sm, const NodeLayout& Ly,
                                           int nk, int i0) {
   for (int i = (i0 > 1 ? i0 : 1); i < nk; ++i) {
     double acc = SM(Ly.x + i);
@@ -74,7 +91,7 @@ __device__ __forceinline__ void ldl_solve(const DevModel& M, double* sm, const N
 }
 
 // (C'^T y) on link b, components 0..2, for the vector y at element offset yo.
-__device__ __forceinline__ void ct_link(const DevModel& M, const double* sm, const NodeLayout& Ly,
+__device__ __forceinline__ void ct_link(const NodeTab& M, const double* sm, const NodeLayout& Ly,
                                         int yo, int b, double& o0, double& o1, double& o2) {
   o0 = o1 = o2 = 0.0;
   for (int t = 0; t < M.nadj[b]; ++t) {
@@ -95,7 +112,7 @@ __device__ __forceinline__ void ct_link(const DevModel& M, const double* sm, con
 
 // x <- 0 except, for the joints on link b, s (e0 + perp . (0, 0) ...) as given by the
 // generalized vector (f0, f1, f2) on link b: x_j = s (f0, f1) + s perp_jb f2.
-__device__ __forceinline__ void c_link(const DevModel& M, double* sm, const NodeLayout& Ly, int nk,
+__device__ __forceinline__ void c_link(const NodeTab& M, double* sm, const NodeLayout& Ly, int nk,
                                        int b, double f0, double f1, double f2) {
   for (int r = 0; r < nk; ++r) SM(Ly.x + r) = 0.0;
   for (int t = 0; t < M.nadj[b]; ++t) {
@@ -122,15 +139,14 @@ __device__ __forceinline__ double sabs(double x, double& d) {
   return r - 1.0;
 }
 
-__global__ void __launch_bounds__(256) k_node(const DevModel* __restrict__ Mp, int n,
+__global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M, int n,
                                               const double* __restrict__ Xp,
                                               const double* __restrict__ Xm,
                                               const double* __restrict__ Phi,
-                                              const double* __restrict__ Gam, NodeParams P,
-                                              double* g, double* Gvm, double* Gth, double* Gphi,
+                                              const double* __restrict__ Gam, double* g,
+                                              double* Gvm, double* Gth, double* Gphi,
                                               double* theta, double* dtheta, unsigned* status) {
   extern __shared__ double smem[];
-  const DevModel& M = *Mp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -154,10 +170,10 @@ __global__ void __launch_bounds__(256) k_node(const DevModel* __restrict__ Mp, i
       SM(Ly.arm + 4 * j + 2 * role) = -ry;
       SM(Ly.arm + 4 * j + 2 * role + 1) = rx;
     }
-    const int ci = M.body[b].contact;
+    const int ci = M.contact[b];
     if (ci >= 0) {
-      SM(Ly.carm + 2 * ci) = c * M.body[b].crho[0] - s * M.body[b].crho[1];
-      SM(Ly.carm + 2 * ci + 1) = s * M.body[b].crho[0] + c * M.body[b].crho[1];
+      SM(Ly.carm + 2 * ci) = c * M.crho[b][0] - s * M.crho[b][1];
+      SM(Ly.carm + 2 * ci + 1) = s * M.crho[b][0] + c * M.crho[b][1];
     }
   }
 
@@ -202,7 +218,7 @@ __global__ void __launch_bounds__(256) k_node(const DevModel* __restrict__ Mp, i
   // w = v- + M^-1 J_c^T Phi on link b (generalized impulse of its contact)
   auto impulse = [&](int b, double& f0, double& f1, double& f2) {
     f0 = f1 = f2 = 0.0;
-    const int ci = M.body[b].contact;
+    const int ci = M.contact[b];
     if (ci >= 0) {
       const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
       f0 = ph[2 * ci];
@@ -280,7 +296,7 @@ __global__ void __launch_bounds__(256) k_node(const DevModel* __restrict__ Mp, i
     double* out = Gth + (size_t)k * nq * nb;
     for (int b = 0; b < nb; ++b) {
       double ab = 0.0;
-      const int ci = M.body[b].contact;
+      const int ci = M.contact[b];
       if (ci >= 0)
         ab = -fma(SM(Ly.carm + 2 * ci), ph[2 * ci], SM(Ly.carm + 2 * ci + 1) * ph[2 * ci + 1]);
       for (int t = 0; t < M.nadj[b]; ++t) {
@@ -316,7 +332,7 @@ __global__ void __launch_bounds__(256) k_node(const DevModel* __restrict__ Mp, i
   if (Gphi && nc > 0) {
     double* out = Gphi + (size_t)k * nq * 2 * nc;
     for (int b = 0; b < nb; ++b) {
-      const int ci = M.body[b].contact;
+      const int ci = M.contact[b];
       if (ci < 0) continue;
       const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
       for (int comp = 0; comp < 2; ++comp) {
@@ -341,11 +357,11 @@ __global__ void __launch_bounds__(256) k_node(const DevModel* __restrict__ Mp, i
   // Theta^delta per contact, and its Jacobian in the contact's local variables
   // (p_y-, theta-, v_x+, v_y+, omega+, v_y-, omega-, Phi_t, Phi_n, Gamma) of its link.
   for (int b = 0; b < nb; ++b) {
-    const int ci = M.body[b].contact;
+    const int ci = M.contact[b];
     if (ci < 0) continue;
     const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
-    const double pt = ph[2 * ci], pn = ph[2 * ci + 1], ga = gm[ci], e = P.e[ci];
-    const double mu = M.body[b].mu;
+    const double pt = ph[2 * ci], pn = ph[2 * ci + 1], ga = gm[ci], e = M.e[ci];
+    const double mu = M.mu[b];
     const double wp = xp[nq + 3 * b + 2], wm = xm[nq + 3 * b + 2];
     const double phi = xm[3 * b + 1] + ry;
     const double vtp = fma(-wp, ry, xp[nq + 3 * b]);
@@ -361,10 +377,10 @@ __global__ void __launch_bounds__(256) k_node(const DevModel* __restrict__ Mp, i
     const double rho = smn - spt;
     double f0a, f0b, f1a, f1b, f2a, f2b, f3a, f3b;
     double* th = theta + ((size_t)k * nc + ci) * 8;
-    th[0] = fb(pn, phi, P.delta, f0a, f0b);
-    th[1] = fb(pn, scn, P.delta, f1a, f1b);
-    th[2] = fb(pn, slc, P.delta, f2a, f2b);
-    th[3] = fb(ga, rho, P.delta, f3a, f3b);
+    th[0] = fb(pn, phi, M.delta, f0a, f0b);
+    th[1] = fb(pn, scn, M.delta, f1a, f1b);
+    th[2] = fb(pn, slc, M.delta, f2a, f2b);
+    th[3] = fb(ga, rho, M.delta, f3a, f3b);
     th[4] = -pn;
     th[5] = -phi;
     th[6] = -ga;
@@ -423,8 +439,33 @@ cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const dou
   if (e != cudaSuccess) return e;
   const int threads = 32 * wpc;
   const long blocks = (n + threads - 1) / threads;
-  k_node<<<(unsigned)blocks, threads, smem, st>>>(dM, n, Xp, Xm, Phi, Gam, P, g, Gvm, Gth, Gphi,
-                                                  theta, dtheta, status);
+  NodeTab T;
+  std::memset(&T, 0, sizeof T);
+  T.nb = Mh.nb; T.nj = Mh.nj; T.nc = Mh.nc; T.nxt = Mh.nxt;
+  for (int b = 0; b < Mh.nb; ++b) {
+    T.nadj[b] = Mh.nadj[b];
+    for (int t = 0; t < Mh.nadj[b]; ++t) T.adj[b][t] = (unsigned char)Mh.adj[b][t];
+    T.lmin[b] = Mh.lmin[b];
+    T.contact[b] = Mh.body[b].contact;
+    T.mass[b] = Mh.mass[b]; T.inertia[b] = Mh.inertia[b];
+    T.minv[b] = Mh.minv[b]; T.iinv[b] = Mh.iinv[b];
+    T.crho[b][0] = Mh.body[b].crho[0]; T.crho[b][1] = Mh.body[b].crho[1];
+    T.mu[b] = Mh.body[b].mu;
+  }
+  for (int j = 0; j < Mh.nj; ++j) {
+    T.npos[j] = Mh.npos[j]; T.nord[j] = Mh.nord[j];
+    T.jchi[j] = Mh.jchi[j]; T.jpar[j] = Mh.jpar[j];
+    T.jrc[j][0] = Mh.jrc[j][0]; T.jrc[j][1] = Mh.jrc[j][1];
+    T.jrp[j][0] = Mh.jrp[j][0]; T.jrp[j][1] = Mh.jrp[j][1];
+  }
+  for (int i = 0; i <= 2 * Mh.nj; ++i) {
+    if (i < 2 * Mh.nj) T.nf[i] = Mh.nf[i];
+    T.noff[i] = Mh.noff[i];
+  }
+  T.delta = P.delta;
+  for (int i = 0; i < Mh.nc; ++i) T.e[i] = P.e[i];
+  k_node<<<(unsigned)blocks, threads, smem, st>>>(T, n, Xp, Xm, Phi, Gam, g, Gvm, Gth, Gphi, theta,
+                                                  dtheta, status);
   return cudaGetLastError();
 }
 
