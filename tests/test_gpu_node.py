@@ -153,3 +153,31 @@ def test_node_linearize_errors(env):
     with pytest.raises(api.CiscvxError) as ex:
         api.node_linearize(mc, Xc, Xc, None, None, 1e-3, [])
     assert ex.value.status == api.EUNSUPPORTED
+
+
+def test_sweep_nodes_full_size_sampled(env):
+    """Every node of the 4096 x 400 sweep (1 642 496 nodes) in one launch, as
+    the bench times it; sampled nodes (first, last and 94 random) checked
+    against the oracle block by block."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    b = synth.cheetah_sweep(seed=0)
+    R = b.robots[0].as_dict()
+    m = api.Model(b.robots[0])
+    Xm = np.concatenate([b.instance(i).X for i in range(len(b))])
+    n = Xm.shape[0]
+    assert n == 4096 * 401
+    rng = np.random.default_rng(77)
+    Xp = Xm + 0.1 * rng.standard_normal(Xm.shape)
+    Phi = rng.standard_normal((n, 2 * m.ny))
+    Gam = rng.uniform(0, 1.5, (n, m.ny))
+    e = np.full(m.ny, 0.3)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    out = api.node_linearize(m, t(Xp), t(Xm), t(Phi), t(Gam), 1e-3, e)
+    api.sync_status(m)
+    sample = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 94, replace=False)]))
+    idx = torch.tensor(sample, device=dev)
+    got = {k: v[idx].cpu().numpy() for k, v in out.items()}
+    ref = oracle.node(R, Xp[sample], Xm[sample], Phi[sample], Gam[sample], 1e-3, e)
+    for k, v in _node_errors(got, ref, R).items():
+        assert v <= TOL_FP64, (k, v)
