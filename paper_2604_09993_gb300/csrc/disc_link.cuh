@@ -152,6 +152,21 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   sincos(th, &sth, &cth);
   InputPenalty<TP> ip0;  // input penalty at the substep start
   if (foot) ip0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+  // Penalty quadrature: the input-only terms H(tau) enter every substep as
+  // Simpson's rule (h/6 H(t_i) + 2h/3 H(t_i + h/2) + h/6 H(t_i + h)); they are
+  // accumulated as 2h/3 H(mid) + h/3 H(end) per substep, with h/6 H(0) added
+  // first and h/6 H(1) taken off at the end.
+  const double h3 = h * (1.0 / 3.0), h23 = 2.0 * h3, h6 = 0.5 * h3;
+  if (foot) Yom = h6 * ip0.H;
+  // FP32-Phi mode: the FP64 state needs only the s-scaled stage slopes
+  // k_theta = s omega_stage and k_omega = s (cos P - sin Q + T), so the input
+  // sums are pre-scaled by s (one FMA per slope instead of an FMA and a
+  // multiply) and s P, s Q, s T at the substep end carry over to the next start.
+  const double sPL = sd * PL, sdPs = sd * dP, sQL = sd * QL, sdQs = sd * dQ;
+  const double sTL = sd * TL, sdTs = sd * dT;
+  const double sAyg = sd * (AyL - g), sdAys = sd * dAy;
+  const double sc2 = sd * h2, sc3 = sd * h;
+  double sPi = sPL, sQi = sQL, sTi = sTL;
 
   for (int i = 0; i < nsub; ++i) {
     // ---- state stages (FP64) ----
@@ -168,6 +183,9 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     const TP thA = TP(th), omA = TP(om), pyA = TP(py), vyA = TP(vy);
     TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0);
     double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
+    const double som = sd * om, svy = foot ? sd * vy : 0.0;
+    double sPm = 0, sQm = 0, sTm = 0;
+    double ws = 0, P = 0, Q = 0, T = 0;  // FP64 stage data (FP64 mode only)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const double wj = rk_w(j);
@@ -175,28 +193,45 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       const double tj = (j == 0) ? ti : (j == 3 ? te : tm);
       const double dth = cjh * kth;
       const double ths = th + dth;
-      const double ws = (j == 0) ? om : fma(cjh, kom, om);
       double sn, cs;
       if (j == 0) { sn = sth; cs = cth; }
       else sincos_step(ths, sth, cth, dth, amask, sn, cs);
-      const double P = fma(tj, dP, PL), Q = fma(tj, dQ, QL), T = fma(tj, dT, TL);
-      const double wdot = fma(cs, P, fma(-sn, Q, T));
-      kth = sd * ws;
-      kom = sd * wdot;
+      if constexpr (F32) {
+        double sP, sQ, sT;
+        if (j == 0) { sP = sPi; sQ = sQi; sT = sTi; }
+        else if (j == 3) {
+          sPi = fma(te, sdPs, sPL); sQi = fma(te, sdQs, sQL); sTi = fma(te, sdTs, sTL);
+          sP = sPi; sQ = sQi; sT = sTi;
+        } else {
+          if (j == 1) { sPm = fma(tm, sdPs, sPL); sQm = fma(tm, sdQs, sQL); sTm = fma(tm, sdTs, sTL); }
+          sP = sPm; sQ = sQm; sT = sTm;
+        }
+        kth = (j == 0) ? som : fma(j == 3 ? sc3 : sc2, kom, som);
+        kom = fma(cs, sP, fma(-sn, sQ, sT));
+      } else {
+        ws = (j == 0) ? om : fma(cjh, kom, om);
+        P = fma(tj, dP, PL); Q = fma(tj, dQ, QL); T = fma(tj, dT, TL);
+        kth = sd * ws;
+        kom = sd * fma(cs, P, fma(-sn, Q, T));
+      }
       ath_ = fma(wj, kth, ath_);
       aom_ = fma(wj, kom, aom_);
       double pys = 0.0, vs = 0.0;
       if (foot) {
         pys = (j == 0) ? py : fma(cjh, kpy, py);
-        vs = (j == 0) ? vy : fma(cjh, kvy, vy);
-        const double ay = fma(tj, dAy, AyL) - g;
-        kpy = sd * vs;
-        kvy = sd * ay;
+        if constexpr (F32) {
+          kpy = (j == 0) ? svy : fma(j == 3 ? sc3 : sc2, kvy, svy);
+          kvy = fma(tj, sdAys, sAyg);
+        } else {
+          vs = (j == 0) ? vy : fma(cjh, kvy, vy);
+          kpy = sd * vs;
+          kvy = sd * (fma(tj, dAy, AyL) - g);
+        }
         apy = fma(wj, kpy, apy);
         avy = fma(wj, kvy, avy);
-        const double ry = fma(sn, crx, cs * cry);
+        // ground term h(-phi), phi = p_y + (R rho)_y at the stage
+        Yom = fma(h * wj, huber_value(-fma(sn, crx, fma(cs, cry, pys))), Yom);
         const InputPenalty<TP>& ipj = (j == 0) ? ip0 : (j == 3 ? ip1 : ipm);
-        Yom = fma(h * wj, ipj.H + huber_value(-(pys + ry)), Yom);
         dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
       }
       // stage data for the tangent recursion
@@ -245,7 +280,12 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     }
     th += Dth;
     om = fma(h, aom_, om);
-    if (foot) { py = fma(h, apy, py); vy = fma(h, avy, vy); ip0 = ip1; }
+    if (foot) {
+      py = fma(h, apy, py);
+      vy = fma(h, avy, vy);
+      Yom = fma(h3, ip1.H, fma(h23, ipm.H, Yom));
+      ip0 = ip1;
+    }
     ti = te;
     tiP = teP;
 
@@ -318,6 +358,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       }
     }
   }
+
+  if (foot) Yom = fma(-h6, ip0.H, Yom);  // the end point was counted with h/3
 
   // ------------------------------------------------------------ outputs ---
   const TP one = TP(1);

@@ -86,7 +86,20 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   constexpr bool PEN_FWD = FOOT && F32;
   double Yom = 0.0;
   InputPenalty<TP> fp0, fpm, fp1;
-  if (PEN_FWD) fp0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+  // input-only penalty terms as Simpson per substep (see disc_link.cuh)
+  const double h3 = h * (1.0 / 3.0), h23 = 2.0 * h3, h6 = 0.5 * h3;
+  if (PEN_FWD) {
+    fp0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+    Yom = h6 * fp0.H;
+  }
+  // The forward sweep needs only the state: slopes from s-scaled input sums
+  // (k_theta = s omega_stage, k_omega = s (cos P - sin Q + T)), s P, s Q, s T
+  // carried from each substep end to the next start.
+  const double sPL = sd * PL, sdPs = sd * dP, sQL = sd * QL, sdQs = sd * dQ;
+  const double sTL = sd * TL, sdTs = sd * dT;
+  const double sAyg = sd * (AyL - g), sdAys = sd * dAy;
+  const double sc2 = sd * h2, sc3 = sd * h;
+  double sPi = sPL, sQi = sQL, sTi = sTL;
   double ti = 0.0;  // tau at the substep start (running sum)
   TP tiP = TP(0);
   for (int i = 0; i < nsub; ++i) {
@@ -98,31 +111,43 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
       fp1 = input_penalty<TP>(te, tiP + hP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
     double kth = 0, kom = 0, ath = 0, aom = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
+    const double som = sd * om, svy = FOOT ? sd * vy : 0.0;
+    double sPm = 0, sQm = 0, sTm = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const double wj = rk_w(j);
       const double cjh = (j == 0) ? 0.0 : (j == 3 ? h : h2);
       const double tj = (j == 0) ? ti : (j == 3 ? te : tm);
       const double dth = cjh * kth;
-      const double ws = (j == 0) ? om : fma(cjh, kom, om);
       double sn, cs;
       if (j == 0) { sn = sth; cs = cth; }
       else sincos_step(th + dth, sth, cth, dth, amask, sn, cs);
-      const double wdot = fma(cs, fma(tj, dP, PL), fma(-sn, fma(tj, dQ, QL), fma(tj, dT, TL)));
-      kth = sd * ws; kom = sd * wdot;
+      double sP, sQ, sT;
+      if (j == 0) { sP = sPi; sQ = sQi; sT = sTi; }
+      else if (j == 3) {
+        sPi = fma(te, sdPs, sPL); sQi = fma(te, sdQs, sQL); sTi = fma(te, sdTs, sTL);
+        sP = sPi; sQ = sQi; sT = sTi;
+      } else {
+        if (j == 1) { sPm = fma(tm, sdPs, sPL); sQm = fma(tm, sdQs, sQL); sTm = fma(tm, sdTs, sTL); }
+        sP = sPm; sQ = sQm; sT = sTm;
+      }
+      kth = (j == 0) ? som : fma(j == 3 ? sc3 : sc2, kom, som);
+      kom = fma(cs, sP, fma(-sn, sQ, sT));
       ath = fma(wj, kth, ath); aom = fma(wj, kom, aom);
       if (FOOT) {
-        const double vs = (j == 0) ? vy : fma(cjh, kvy, vy);
         if (PEN_FWD) {
           const double pys = (j == 0) ? py : fma(cjh, kpy, py);
-          const InputPenalty<TP>& ipj = (j == 0) ? fp0 : (j == 3 ? fp1 : fpm);
-          Yom = fma(h * wj, ipj.H + huber_value(-(pys + fma(sn, crx, cs * cry))), Yom);
+          Yom = fma(h * wj, huber_value(-fma(sn, crx, fma(cs, cry, pys))), Yom);
         }
-        kpy = sd * vs; kvy = sd * (fma(tj, dAy, AyL) - g);
+        kpy = (j == 0) ? svy : fma(j == 3 ? sc3 : sc2, kvy, svy);
+        kvy = fma(tj, sdAys, sAyg);
         apy = fma(wj, kpy, apy); avy = fma(wj, kvy, avy);
       }
     }
-    if (PEN_FWD) fp0 = fp1;
+    if (PEN_FWD) {
+      Yom = fma(h3, fp1.H, fma(h23, fpm.H, Yom));
+      fp0 = fp1;
+    }
     const double Dth = h * ath;
     double s1, c1;
     sincos_step(th + Dth, sth, cth, Dth, amask, s1, c1);
@@ -133,6 +158,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
     ti = te;
     tiP = tiP + hP;
   }
+  if (PEN_FWD) Yom = fma(-h6, fp0.H, Yom);  // the end point was counted with h/3
 
   // cotangents of x~(1): w_k (+ rho on the penalty state)
   const double wpx = wk[rpx], wpy = wk[rpy], wth = wk[rth], wvx = wk[rvx], wvy = wk[rvy], wom = wk[rom];
