@@ -9,8 +9,10 @@ value = intervals linearized (STM + VJP) per second.
 
 Default workload: 4096 instances of the 7-link chain, N = 400 intervals,
 20 RK4 substeps, s ~ U[0.01, 0.05], FP32 Phi with FP64 state (batched plan,
-persistent launch in a CUDA graph).  The plain FP64 GPU path runs the same
-workload as the comparator (`fp64_path`).
+persistent launch).  A batch step is one ciscvx_batch_discretize_and_vjp
+call: both outputs from one pass, the interval's FP64 trajectory shared; the
+two paths are also timed as separate calls (roofline.separate_*_ms).  The
+plain FP64 GPU path runs the same workload as the comparator (`fp64_path`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -60,18 +62,20 @@ DEFAULT_WORKLOAD = "cheetah7-sweep-4096x400x20"
 # 2*DFMA + DADD + DMUL of one launch / intervals of that launch), recorded in
 # profiles/; keyed by (robot, n_sub, kernel, precision).
 FLOPS_PER_INTERVAL = {
-    ("cheetah7", 20, "discretize", "fp32_phi"): 30_521,
-    ("cheetah7", 20, "vjp", "fp32_phi"): 31_566,
+    ("cheetah7", 20, "discretize", "fp32_phi"): 28_608,
+    ("cheetah7", 20, "vjp", "fp32_phi"): 29_457,
     ("cheetah7", 20, "discretize", "fp64"): 126_397,
-    ("cheetah7", 20, "vjp", "fp64"): 87_665,
+    ("cheetah7", 20, "vjp", "fp64"): 82_621,
+    ("cheetah7", 20, "fused", "fp32_phi"): 31_045,
 }
 # DRAM bytes (read + write) per interval of each kernel from the same captures
 # (256 instances x 400 intervals; traffic scales with the intervals processed).
 DRAM_BYTES_PER_INTERVAL = {
-    ("cheetah7", 20, "discretize", "fp32_phi"): (312.6e6 + 1894.5e6) / 102400,
-    ("cheetah7", 20, "vjp", "fp32_phi"): (99.0e6 + 116.4e6) / 102400,
+    ("cheetah7", 20, "discretize", "fp32_phi"): (310.1e6 + 1898.7e6) / 102400,
+    ("cheetah7", 20, "vjp", "fp32_phi"): (249.1e6 + 155.8e6) / 102400,
     ("cheetah7", 20, "discretize", "fp64"): (376.0e6 + 3644.2e6) / 102400,
-    ("cheetah7", 20, "vjp", "fp64"): (581.0e6 + 750.8e6) / 102400,
+    ("cheetah7", 20, "vjp", "fp64"): (258.3e6 + 227.4e6) / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi"): (749.8e6 + 2639.7e6) / 102400,
 }
 
 
@@ -172,12 +176,14 @@ class BatchWorkload:
 
     def prepare(self, prec, fmt="dense"):
         pl = self.plan(prec, fmt)
-        if (prec, fmt) not in self.out:
-            self.out[(prec, fmt)] = pl.alloc_outputs(self.dev)
-            pl.autotune(self.X, self.U, self.s, out=self.out[(prec, fmt)])
         need = pl.vjp_workspace_size()
         if self.ws is None or self.ws.numel() < need:
             self.ws = self.torch.empty(need, dtype=self.torch.uint8, device=self.dev)
+        if (prec, fmt) not in self.out:
+            self.out[(prec, fmt)] = pl.alloc_outputs(self.dev)
+            pl.autotune(self.X, self.U, self.s, out=self.out[(prec, fmt)])
+            pl.autotune_fused(self.X, self.U, self.s, self.w, self.rho, workspace=self.ws,
+                              out=self.out[(prec, fmt)])
 
     def free(self, prec, fmt="dense"):
         self.out.pop((prec, fmt), None)
@@ -193,15 +199,20 @@ class BatchWorkload:
                                                    workspace=self.ws, out=self.gout.get((prec, fmt)))
 
     def step(self, prec, fmt="dense"):
-        self.disc(prec, fmt)
-        self.vjp(prec, fmt)
+        """One pass of the hot path: linearization and adjoint VJP of every interval
+        (ciscvx_batch_discretize_and_vjp: one shared FP64 trajectory per interval)."""
+        key = (prec, fmt)
+        _, self.gout[key] = self.plan(prec, fmt).discretize_and_vjp(
+            self.X, self.U, self.s, self.w, self.rho, workspace=self.ws, out=self.out[key],
+            gout=self.gout.get(key))
 
     def check_status(self):
         for pl in self.plans.values():
             pl.sync_status()
 
     def tune(self, prec, fmt="dense"):
-        return self.plan(prec, fmt).tune()
+        pl = self.plan(prec, fmt)
+        return {"discretize": pl.tune(), "fused": pl.tune_fused()}
 
     # end to end through the public API with host buffers: ciscvx_batch_run_host
     # (chunked, H2D / compute / D2H overlapped on three streams)
@@ -455,21 +466,28 @@ def run_ours(args):
         t = time_steps(torch, lambda: wl.step(prec), args.steps, args.warmup, stream)
         barrier()
     clocks = cs.summary()
+    # the linearization and the VJP as separate calls (each path on its own)
     kd = kernel_time(torch, lambda: wl.disc(prec), 5, stream)
     kv = kernel_time(torch, lambda: wl.vjp(prec), 5, stream)
+    # batch step: one fused launch (+ the per-instance finish) does both
+    kf = kernel_time(torch, lambda: wl.step(prec), 5, stream) if spec["kind"] == "batch" else None
     wl.check_status()
     t, kd, kv = max_over_ranks([t, kd, kv])
+    if kf is not None:
+        kf, = max_over_ranks([kf])
     units = wl.intervals * world
     value = units * args.steps / t
 
-    dom, kt = ("discretize", kd) if kd >= kv else ("vjp", kv)
-    kname = {"discretize": "k_batch_disc" if spec["kind"] == "batch" else "k_discretize",
-             "vjp": "k_batch_vjp" if spec["kind"] == "batch" else "k_vjp"}[dom]
+    if kf is not None:
+        dom, kt, kname = "fused", kf, "k_batch_disc_vjp"
+    else:
+        dom, kt = ("discretize", kd) if kd >= kv else ("vjp", kv)
+        kname = {"discretize": "k_discretize", "vjp": "k_vjp"}[dom]
     fpi = FLOPS_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec))
     bpi = DRAM_BYTES_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec))
     roof = {"bound": "alu", "kernel": f"{kname}<{'float' if prec == 'fp32_phi' else 'double'}>",
             "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4), "peak_source": "derived FP64 pipe",
-            "launch_ms": kt * 1e3, "discretize_ms": kd * 1e3, "vjp_ms": kv * 1e3,
+            "launch_ms": kt * 1e3, "separate_discretize_ms": kd * 1e3, "separate_vjp_ms": kv * 1e3,
             "traffic": None if bpi is None else bpi * wl.intervals,
             "traffic_source": None if bpi is None else "ncu dram bytes of a 102400-interval launch, scaled"}
     if fpi:
@@ -544,9 +562,9 @@ def run_ours(args):
         "fp64_path": None if t64 is None else {
             "value": units * args.steps / t64, "ms_per_step": t64 / args.steps * 1e3,
             "discretize_ms": kd64 * 1e3, "headline_speedup": t64 / t},
-        # launches of this library per timed step: batch = graph (memset + disc) + vjp + finish;
+        # launches of this library per timed step: batch = fused discretize+VJP + finish;
         # single = disc + vjp + gU + gs + L
-        "gpu_launches": args.steps * (4 if spec["kind"] == "batch" else 5),
+        "gpu_launches": args.steps * (2 if spec["kind"] == "batch" else 5),
         "roofline": roof,
         "e2e": e2e,
         "compact_outputs": compact,

@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 3
+#define CISCVX_VERSION_MINOR 4
 
 typedef enum {
   CISCVX_OK = 0,
@@ -353,6 +353,19 @@ ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* plan, siz
 ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_vjp_io* io,
                                           void* workspace, size_t ws_bytes, void* stream);
 
+/* ciscvx_batch_discretize and ciscvx_batch_discretize_vjp of the same inputs
+ * in one pass.  The adjoint's backward sweep needs the FP64 state at every
+ * substep start, which the linearization computes anyway: here the
+ * linearization records it and the backward sweep starts from it, so each
+ * interval's trajectory is integrated once instead of twice.  Outputs are
+ * those of the two calls (io's A..penalty; vjp's gX, gU, gs, L), equal to
+ * them to rounding.  vjp->X, U, s are ignored (io's inputs are used).
+ * workspace as for ciscvx_batch_discretize_vjp.  Launched directly (no graph).
+ * Errors: as the two calls. */
+ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
+                                              const ciscvx_batch_vjp_io* vjp, void* workspace,
+                                              size_t ws_bytes, void* stream);
+
 /* Times candidate launch shapes of ciscvx_batch_discretize on the given
  * buffers (their outputs are overwritten), keeps the fastest in the plan and
  * returns it in *chosen (may be NULL).  Results are cached per process by
@@ -364,8 +377,9 @@ ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* plan, const ciscvx_batch_
 
 /* End-to-end run on HOST buffers, pipelined: the instances are split into
  * n_chunks consecutive chunks of balanced cost; for each chunk the inputs are
- * copied host -> device, the chunk is linearized (and its VJP taken if
- * host_vjp is not NULL), and its outputs are copied device -> host, on three
+ * copied host -> device, the chunk is linearized (with its VJP in the same
+ * pass, as ciscvx_batch_discretize_and_vjp, if host_vjp is not NULL), and its
+ * outputs are copied device -> host, on three
  * plan-owned streams so that one chunk's copies overlap its neighbours'
  * compute.  The call is asynchronous: `stream` waits for the last copy.
  *   host: packed host arrays in the layout of ciscvx_batch_io (inputs X, U, s;
@@ -385,6 +399,17 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
                                     const ciscvx_batch_vjp_io* host_vjp,
                                     const ciscvx_batch_vjp_io* dev_vjp, void* workspace,
                                     size_t ws_bytes, void* stream);
+
+/* As ciscvx_batch_autotune, for the fused pass of ciscvx_batch_discretize_and_vjp
+ * (its launch shape is kept apart from the discretization's: the fused kernel
+ * holds more state per thread).  Overwrites the outputs; workspace as for
+ * ciscvx_batch_discretize_vjp.  Errors: as ciscvx_batch_discretize_and_vjp. */
+ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
+                                          const ciscvx_batch_vjp_io* vjp, void* workspace,
+                                          size_t ws_bytes, void* stream, ciscvx_tune* chosen);
+
+/* Current launch shape of the plan's fused pass. */
+ciscvx_status ciscvx_batch_get_tune_fused(const ciscvx_batch_plan* plan, ciscvx_tune* out);
 
 /* As ciscvx_sync_status, for the plan's status word. */
 ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* plan, void* stream);

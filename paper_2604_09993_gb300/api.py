@@ -30,7 +30,8 @@ EXPORTS = (
     "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp", "ciscvx_batch_autotune",
     "ciscvx_batch_sync_status", "ciscvx_batch_run_host",
     "ciscvx_model_pattern", "ciscvx_model_nnz", "ciscvx_discretize_compact",
-    "ciscvx_node_linearize",
+    "ciscvx_node_linearize", "ciscvx_batch_discretize_and_vjp", "ciscvx_batch_autotune_fused",
+    "ciscvx_batch_get_tune_fused",
 )
 FORMAT = {"dense": 0, "compact": 1}
 
@@ -140,6 +141,11 @@ def load(path: str | None = None):
     lib.ciscvx_batch_vjp_workspace_size.argtypes = [_vp, P(ctypes.c_size_t)]
     lib.ciscvx_batch_discretize_vjp.argtypes = [_vp, P(_BatchVjpIO), _vp, ctypes.c_size_t, _vp]
     lib.ciscvx_batch_autotune.argtypes = [_vp, P(_BatchIO), _vp, P(Tune)]
+    lib.ciscvx_batch_discretize_and_vjp.argtypes = [_vp, P(_BatchIO), P(_BatchVjpIO), _vp,
+                                                    ctypes.c_size_t, _vp]
+    lib.ciscvx_batch_autotune_fused.argtypes = [_vp, P(_BatchIO), P(_BatchVjpIO), _vp,
+                                                ctypes.c_size_t, _vp, P(Tune)]
+    lib.ciscvx_batch_get_tune_fused.argtypes = [_vp, P(Tune)]
     lib.ciscvx_batch_sync_status.argtypes = [_vp, _vp]
     lib.ciscvx_batch_run_host.argtypes = [_vp, ctypes.c_int, P(_BatchIO), P(_BatchIO), P(_BatchVjpIO),
                                           P(_BatchVjpIO), _vp, ctypes.c_size_t, _vp]
@@ -150,7 +156,9 @@ def load(path: str | None = None):
               "ciscvx_batch_offsets", "ciscvx_batch_get_tune", "ciscvx_batch_discretize",
               "ciscvx_batch_vjp_workspace_size", "ciscvx_batch_discretize_vjp",
               "ciscvx_batch_autotune", "ciscvx_batch_sync_status", "ciscvx_model_pattern",
-              "ciscvx_model_nnz", "ciscvx_discretize_compact", "ciscvx_node_linearize"):
+              "ciscvx_model_nnz", "ciscvx_discretize_compact", "ciscvx_node_linearize",
+              "ciscvx_batch_discretize_and_vjp", "ciscvx_batch_autotune_fused",
+              "ciscvx_batch_get_tune_fused"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -547,6 +555,45 @@ class BatchPlan:
                                                   workspace.numel() * workspace.element_size(),
                                                   _stream()))
         return out
+
+    def _fused_args(self, X, U, s, w, rho, workspace, out, gout, want_L):
+        import torch
+        need = self.vjp_workspace_size()
+        if workspace is None or workspace.numel() * workspace.element_size() < need:
+            workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
+        if out is None:
+            out = self.alloc_outputs(X.device)
+        if gout is None:
+            gout = {"gX": torch.empty_like(X), "gU": torch.empty_like(U), "gs": torch.empty_like(s),
+                    "L": torch.empty(self.n_inst, dtype=torch.float64, device=X.device) if want_L else None}
+        io = self._io(X, U, s, out)
+        vio = _BatchVjpIO(*[None if t is None else t.data_ptr()
+                            for t in (None, None, None, w, rho, gout["gX"], gout["gU"], gout["gs"], gout["L"])])
+        return workspace, out, gout, io, vio
+
+    def discretize_and_vjp(self, X, U, s, w, rho, workspace=None, out=None, gout=None, want_L=True):
+        """ciscvx_batch_discretize_and_vjp: both outputs from one pass.  Returns (out, gout)."""
+        workspace, out, gout, io, vio = self._fused_args(X, U, s, w, rho, workspace, out, gout, want_L)
+        _check(load().ciscvx_batch_discretize_and_vjp(self._h, ctypes.byref(io), ctypes.byref(vio),
+                                                      _ptr(workspace),
+                                                      workspace.numel() * workspace.element_size(),
+                                                      _stream()))
+        return out, gout
+
+    def autotune_fused(self, X, U, s, w, rho, workspace=None, out=None, gout=None):
+        """ciscvx_batch_autotune_fused; returns the chosen launch shape."""
+        workspace, out, gout, io, vio = self._fused_args(X, U, s, w, rho, workspace, out, gout, True)
+        t = Tune()
+        _check(load().ciscvx_batch_autotune_fused(self._h, ctypes.byref(io), ctypes.byref(vio),
+                                                  _ptr(workspace),
+                                                  workspace.numel() * workspace.element_size(),
+                                                  _stream(), ctypes.byref(t)))
+        return t.as_dict()
+
+    def tune_fused(self):
+        t = Tune()
+        _check(load().ciscvx_batch_get_tune_fused(self._h, ctypes.byref(t)))
+        return t.as_dict()
 
     def run_host(self, host_in, host_out, dev_in, dev_out, n_chunks=8, host_vjp=None, dev_vjp=None,
                  workspace=None):

@@ -21,45 +21,9 @@
 #include <string>
 #include <vector>
 
-#include "disc_link.cuh"
-#include "vjp_link.cuh"
+#include "batch_common.cuh"
 
 namespace ciscvx {
-
-struct DevInst {
-  int model, N, nsub, pad_;
-  long long x, u, s, a, b, v, p;  // element offsets: X/gX, U/gU, s/gs, A, Bm/Bp, S/defect/w, penalty/rho
-  long long part, pb;             // VJP workspace offsets: per-input partials, per-(interval, link) partials
-};
-
-struct BatchCommon {
-  const DevModel* const* models;
-  const DevInst* inst;
-  const int2* entries;   // (instance, k)
-  const int4* groups;    // (model, nsub, first entry, count)
-  const int2* items;     // (group, link)
-  int n_items;
-  int persistent;
-  int* queue;
-  unsigned* status;
-  int layout;
-};
-
-__device__ __forceinline__ int next_item(const BatchCommon& c, int& local_iter) {
-  if (!c.persistent) {
-    const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    return local_iter++ == 0 ? w : c.n_items;
-  }
-  int it = 0;
-  if ((threadIdx.x & 31) == 0) it = atomicAdd(c.queue, 1);
-  return __shfl_sync(0xffffffffu, it, 0);
-}
-
-// Launch bounds per occupancy variant: (threads per CTA, min CTAs per SM).
-template <int OCC> struct Occ;
-template <> struct Occ<0> { static constexpr int T = 256, B = 1; };  // no register cap
-template <> struct Occ<1> { static constexpr int T = 128, B = 3; };  // <= 168 registers
-template <> struct Occ<2> { static constexpr int T = 128, B = 4; };  // <= 128 registers
 
 // CMP: compact A/Bm/Bp (structural nonzeros only; strides nnzA / nnzB).
 template <typename TP, int OCC, bool CMP>
@@ -238,6 +202,7 @@ struct ciscvx_batch_plan {
   int* d_queue = nullptr;  // [0]: discretize, [1]: vjp
   unsigned* d_status = nullptr;
   ciscvx_tune tune{4, 2, 1, 1, 0};
+  ciscvx_tune tune_fused{4, 2, 1, 0, 0};  // launch shape of the fused discretize+VJP pass
   ChunkTables chunks;  // tables of the last chunk count used by ciscvx_batch_run_host
   // graph cache
   cudaStream_t cap = nullptr;
@@ -347,15 +312,15 @@ HostDecomp decompose(const ciscvx_batch_plan* p, const std::vector<int>& inst_of
   return d;
 }
 
-BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot) {
+BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot, const ciscvx_tune& t) {
   BatchCommon c;
   c.models = p->d_models;
   c.inst = p->d_inst;
   c.entries = p->d_entries;
   c.groups = p->d_groups;
-  c.items = p->tune.lpt_order ? p->d_items_lpt : p->d_items_nat;
+  c.items = t.lpt_order ? p->d_items_lpt : p->d_items_nat;
   c.n_items = p->n_items;
-  c.persistent = p->tune.ctas_per_sm > 0;
+  c.persistent = t.ctas_per_sm > 0;
   c.queue = p->d_queue + queue_slot;
   c.status = p->d_status;
   c.layout = p->layout;
@@ -363,22 +328,23 @@ BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot) {
 }
 
 // BatchCommon for chunk c of the chunked tables.
-BatchCommon common_chunk(const ciscvx_batch_plan* p, int queue_slot, int c) {
-  BatchCommon b = common_of(p, queue_slot);
+BatchCommon common_chunk(const ciscvx_batch_plan* p, int queue_slot, int c, const ciscvx_tune& tu) {
+  BatchCommon b = common_of(p, queue_slot, tu);
   const ChunkTables& t = p->chunks;
   b.entries = t.d_entries;
   b.groups = t.d_groups;
-  b.items = (p->tune.lpt_order ? t.d_items_lpt : t.d_items_nat) + t.item_off[c];
+  b.items = (tu.lpt_order ? t.d_items_lpt : t.d_items_nat) + t.item_off[c];
   b.n_items = t.item_off[c + 1] - t.item_off[c];
   return b;
 }
 
-void grid_for(const ciscvx_batch_plan* p, int n_items, unsigned& blocks, unsigned& threads) {
-  threads = 32u * (unsigned)p->tune.warps_per_cta;
-  if (p->tune.ctas_per_sm > 0) {
-    blocks = (unsigned)(p->sm_count * p->tune.ctas_per_sm);
+void grid_for(const ciscvx_batch_plan* p, const ciscvx_tune& t, int n_items, unsigned& blocks,
+              unsigned& threads) {
+  threads = 32u * (unsigned)t.warps_per_cta;
+  if (t.ctas_per_sm > 0) {
+    blocks = (unsigned)(p->sm_count * t.ctas_per_sm);
   } else {
-    blocks = (unsigned)((n_items + p->tune.warps_per_cta - 1) / p->tune.warps_per_cta);
+    blocks = (unsigned)((n_items + t.warps_per_cta - 1) / t.warps_per_cta);
   }
   if (blocks == 0) blocks = 1;
 }
@@ -390,7 +356,7 @@ cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const cisc
     if (e != cudaSuccess) return e;
   }
   unsigned blocks, threads;
-  grid_for(p, c.n_items, blocks, threads);
+  grid_for(p, p->tune, c.n_items, blocks, threads);
 #define CISCVX_DISC1(TP, OCC, CMP)                                                            \
   k_batch_disc<TP, OCC, CMP><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (TP*)io->A,   \
                                                          (TP*)io->Bm, (TP*)io->Bp, (TP*)io->S,  \
@@ -416,7 +382,7 @@ cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const cisc
 }
 
 cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStream_t st) {
-  return launch_disc_c(p, common_of(p, 0), io, st);
+  return launch_disc_c(p, common_of(p, 0, p->tune), io, st);
 }
 
 // VJP kernel over the items of `c`, then the per-instance finish over
@@ -427,7 +393,7 @@ cudaError_t launch_vjp_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscv
   if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   unsigned blocks, threads;
-  grid_for(p, c.n_items, blocks, threads);
+  grid_for(p, p->tune, c.n_items, blocks, threads);
 #define CISCVX_VJP(TP, OCC)                                                                   \
   k_batch_vjp<TP, OCC><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX, \
                                                   part, ps, pL)
@@ -448,6 +414,44 @@ cudaError_t launch_vjp_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscv
                                                 pL, io->gU, io->gs, io->L ? io->L + i0 : nullptr);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
+}
+
+// Discretize + VJP of the items of `c` in one pass, then the per-instance
+// finish over instances [i0, i1).  vio's X, U, s are not used (io's are).
+cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_io* io,
+                           const ciscvx_batch_vjp_io* vio, double* part, double* ps, double* pL,
+                           int i0, int i1, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  unsigned blocks, threads;
+  grid_for(p, p->tune_fused, c.n_items, blocks, threads);
+  e = launch_disc_vjp_fused(c, p->prec, p->tune_fused.occupancy, p->compact, blocks, threads, io->X,
+                            io->U, io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty,
+                            vio->w, vio->rho, vio->gX, part, ps, pL, s);
+  if (e == cudaSuccess && i1 > i0)
+    k_batch_vjp_finish<<<i1 - i0, FINB, 0, s>>>(p->d_models, p->d_inst + i0, p->layout, part, ps,
+                                                pL, vio->gU, vio->gs, vio->L ? vio->L + i0 : nullptr);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+// Checks of a VJP io and workspace shared by the VJP entry points.
+ciscvx_status check_vjp(const ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, bool need_x,
+                        const void* workspace, size_t ws_bytes) {
+  if (!p || !io) return set_error(CISCVX_EINVAL, "null plan or io");
+  if ((need_x && (!io->X || !io->s)) || !io->w || !io->gX || !io->gs)
+    return set_error(CISCVX_EINVAL, "null required buffer in ciscvx_batch_vjp_io");
+  if (!p->all_nu0 && ((need_x && !io->U) || !io->gU)) return set_error(CISCVX_EINVAL, "null U / gU");
+  if (!p->all_nc0 && !io->rho) return set_error(CISCVX_EINVAL, "null rho");
+  if (p->max_nsub > MAXSUB_VJP)
+    return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (plan has %d)",
+                     MAXSUB_VJP, p->max_nsub);
+  const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
+  if (!workspace || ws_bytes < need)
+    return set_error(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
+  if (((uintptr_t)workspace & 15) != 0) return set_error(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+  return CISCVX_OK;
 }
 
 bool same_io(const ciscvx_batch_io& a, const ciscvx_batch_io& b) {
@@ -513,7 +517,11 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   p->layout = layout;
   p->compact = (format == CISCVX_OUT_COMPACT);
   p->models.assign(models, models + n_models);
-  if (tune) p->tune = *tune;
+  if (tune) {
+    p->tune = *tune;
+    p->tune_fused = *tune;
+    p->tune_fused.use_graph = 0;
+  }
   cudaGetDevice(&p->device);
   cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
   if (p->sm_count < 1) p->sm_count = 1;
@@ -646,63 +654,73 @@ ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* p, size_t
 
 ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io,
                                           void* workspace, size_t ws_bytes, void* stream) {
-  if (!p || !io) return set_error(CISCVX_EINVAL, "null plan or io");
-  if (!io->X || !io->s || !io->w || !io->gX || !io->gs)
-    return set_error(CISCVX_EINVAL, "null required buffer in ciscvx_batch_vjp_io");
-  if (!p->all_nu0 && (!io->U || !io->gU)) return set_error(CISCVX_EINVAL, "null U / gU");
-  if (!p->all_nc0 && !io->rho) return set_error(CISCVX_EINVAL, "null rho");
-  if (p->max_nsub > MAXSUB_VJP)
-    return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (plan has %d)",
-                     MAXSUB_VJP, p->max_nsub);
-  const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
-  if (!workspace || ws_bytes < need)
-    return set_error(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
-  if (((uintptr_t)workspace & 15) != 0) return set_error(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+  ciscvx_status st = check_vjp(p, io, true, workspace, ws_bytes);
+  if (st != CISCVX_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   double* part = (double*)workspace;
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
-  cudaError_t e = launch_vjp_c(p, common_of(p, 1), io, part, ps, pL, 0, p->n_inst, s);
+  cudaError_t e = launch_vjp_c(p, common_of(p, 1, p->tune), io, part, ps, pL, 0, p->n_inst, s);
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch vjp launch: %s", cudaGetErrorString(e));
   return CISCVX_OK;
 }
 
-ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* p, const ciscvx_batch_io* io, void* stream,
-                                    ciscvx_tune* chosen) {
+ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* p, const ciscvx_batch_io* io,
+                                              const ciscvx_batch_vjp_io* vjp, void* workspace,
+                                              size_t ws_bytes, void* stream) {
   ciscvx_status st = check_io(p, io);
+  if (st == CISCVX_OK) st = check_vjp(p, vjp, false, workspace, ws_bytes);
   if (st != CISCVX_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  const int keep_graph = p->tune.use_graph;
+  double* part = (double*)workspace;
+  double* ps = part + p->part_total;
+  double* pL = ps + p->pb_total;
+  cudaError_t e = launch_fused_c(p, common_of(p, 0, p->tune_fused), io, vjp, part, ps, pL, 0, p->n_inst, s);
+  if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "fused launch: %s", cudaGetErrorString(e));
+  return CISCVX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+const ciscvx_tune kTuneCandidates[] = {
+    {4, 2, 1, 0, 0}, {8, 1, 1, 0, 0}, {2, 4, 1, 0, 0}, {1, 8, 1, 0, 0}, {4, 0, 1, 0, 0},
+    {4, 2, 0, 0, 0}, {4, 3, 1, 0, 1}, {2, 6, 1, 0, 1}, {4, 4, 1, 0, 2}, {2, 8, 1, 0, 2},
+    {4, 0, 1, 0, 1}, {4, 0, 1, 0, 2},
+};
+
+// Times launch() under every candidate written into *slot (warm-up + 2 timed
+// calls each), keeps the fastest there, caches it under `key`.
+template <class Launch>
+ciscvx_status autotune_slot(ciscvx_batch_plan* p, ciscvx_tune* slot, const std::string& tag,
+                            cudaStream_t s, const Launch& launch, ciscvx_tune* chosen) {
+  const int keep_graph = slot->use_graph;
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, p->device);
-  const std::string key = std::string(prop.name) + "|" + p->key;
+  const std::string key = std::string(prop.name) + "|" + p->key + tag;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      p->tune = it->second;
-      p->tune.use_graph = keep_graph;
-      if (chosen) *chosen = p->tune;
+      *slot = it->second;
+      slot->use_graph = keep_graph;
+      if (chosen) *chosen = *slot;
       return CISCVX_OK;
     }
   }
-  static const ciscvx_tune cands[] = {
-      {4, 2, 1, 0, 0}, {8, 1, 1, 0, 0}, {2, 4, 1, 0, 0}, {1, 8, 1, 0, 0}, {4, 0, 1, 0, 0},
-      {4, 2, 0, 0, 0}, {4, 3, 1, 0, 1}, {2, 6, 1, 0, 1}, {4, 4, 1, 0, 2}, {2, 8, 1, 0, 2},
-      {4, 0, 1, 0, 1}, {4, 0, 1, 0, 2},
-  };
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return set_error(CISCVX_ECUDA, "event creation failed");
   float best = 1e30f;
-  ciscvx_tune bt = p->tune;
+  ciscvx_tune bt = *slot;
   cudaError_t e = cudaSuccess;
-  for (const ciscvx_tune& c : cands) {
-    p->tune = c;
-    e = launch_disc(p, io, s);  // warm-up
+  for (const ciscvx_tune& c : kTuneCandidates) {
+    *slot = c;
+    e = launch();  // warm-up
     if (e != cudaSuccess) break;
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_disc(p, io, s);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch();
     cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) break;
@@ -713,13 +731,46 @@ ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* p, const ciscvx_batch_io*
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   bt.use_graph = keep_graph;
-  p->tune = bt;
+  *slot = bt;
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "autotune: %s", cudaGetErrorString(e));
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = bt;
   }
   if (chosen) *chosen = bt;
+  return CISCVX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* p, const ciscvx_batch_io* io, void* stream,
+                                    ciscvx_tune* chosen) {
+  ciscvx_status st = check_io(p, io);
+  if (st != CISCVX_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return autotune_slot(p, &p->tune, "", s, [&]() { return launch_disc(p, io, s); }, chosen);
+}
+
+ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* p, const ciscvx_batch_io* io,
+                                          const ciscvx_batch_vjp_io* vjp, void* workspace,
+                                          size_t ws_bytes, void* stream, ciscvx_tune* chosen) {
+  ciscvx_status st = check_io(p, io);
+  if (st == CISCVX_OK) st = check_vjp(p, vjp, false, workspace, ws_bytes);
+  if (st != CISCVX_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* part = (double*)workspace;
+  double* ps = part + p->part_total;
+  double* pL = ps + p->pb_total;
+  return autotune_slot(p, &p->tune_fused, "|fused", s, [&]() {
+    return launch_fused_c(p, common_of(p, 0, p->tune_fused), io, vjp, part, ps, pL, 0, p->n_inst, s);
+  }, chosen);
+}
+
+ciscvx_status ciscvx_batch_get_tune_fused(const ciscvx_batch_plan* p, ciscvx_tune* out) {
+  if (!p || !out) return set_error(CISCVX_EINVAL, "null argument");
+  *out = p->tune_fused;
   return CISCVX_OK;
 }
 
@@ -843,8 +894,10 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
     if (e == cudaSuccess) e = cudaEventRecord(ev_in, t.s_in);
     // compute
     if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_comp, ev_in, 0);
-    if (e == cudaSuccess) e = launch_disc_c(p, common_chunk(p, 0, c), dev, t.s_comp);
-    if (vjp && e == cudaSuccess) e = launch_vjp_c(p, common_chunk(p, 1, c), &dv, part, ps, pL, i0, i1, t.s_comp);
+    if (e == cudaSuccess) {
+      if (vjp) e = launch_fused_c(p, common_chunk(p, 0, c, p->tune_fused), dev, &dv, part, ps, pL, i0, i1, t.s_comp);
+      else e = launch_disc_c(p, common_chunk(p, 0, c, p->tune), dev, t.s_comp);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev_comp, t.s_comp);
     // device -> host: this chunk's outputs
     if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_out, ev_comp, 0);

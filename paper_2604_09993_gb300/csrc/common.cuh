@@ -177,13 +177,14 @@ __device__ __forceinline__ bool rotate_small(double s0, double c0, double d, boo
   return true;
 }
 
-// (sin, cos) of th = theta0 + d given those of theta0; `active` is the mask of
-// lanes executing this call (they vote on the tier); falls back to sincos(th).
-__device__ __forceinline__ void sincos_step(double th, double s0, double c0, double d,
+// (sin, cos) of theta0 + d given those of theta0; `active` is the mask of
+// lanes executing this call (they vote on the tier); falls back to
+// sincos(theta0 + d), the sum formed only on that path.
+__device__ __forceinline__ void sincos_step(double th0, double s0, double c0, double d,
                                             unsigned active, double& s, double& c) {
   const bool short_tier =
       __all_sync(active, abs_bits(d) <= (unsigned long long)__double_as_longlong(ROT_SHORT));
-  if (!rotate_small(s0, c0, d, short_tier, s, c)) sincos(th, &s, &c);
+  if (!rotate_small(s0, c0, d, short_tier, s, c)) sincos(th0 + d, &s, &c);
 }
 
 // Zero `count` elements starting at each active lane's own pointer `base`,
@@ -211,6 +212,15 @@ __device__ __forceinline__ void warp_zero_chunks(T* base, int count, unsigned ac
     }
   }
 }
+
+// FP64 state at every substep start of one link of one interval (what the
+// adjoint's backward sweep needs), plus the end state and the penalty
+// integrand's quadrature.  Filled by the discretization when the two are fused.
+struct Checkpoints {
+  double th[MAXSUB_VJP], om[MAXSUB_VJP], s[MAXSUB_VJP], c[MAXSUB_VJP];
+  double py[MAXSUB_VJP], vy[MAXSUB_VJP];
+  double th_end, om_end, Yom;
+};
 
 __device__ __forceinline__ double rk_c(int j) { return j == 0 ? 0.0 : (j == 3 ? 1.0 : 0.5); }
 __device__ __forceinline__ double rk_w(int j) {

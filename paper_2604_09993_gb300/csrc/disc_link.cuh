@@ -70,8 +70,9 @@ __device__ __forceinline__ InputPenalty<TP> input_penalty(double t, TP tP, doubl
 // controls; A/Bm/Bp/S/defect/pen/z: this interval's output blocks.
 // CMP: A, Bm, Bp point at this interval's compact values (structural
 // nonzeros only, at the link's offsets; see common.cuh) instead of its dense
-// blocks.
-template <typename TP, bool FOOT, bool CMP = false>
+// blocks.  CK: also record the FP64 state at every substep start (and the end
+// state and penalty quadrature) in *ck, for the adjoint's backward sweep.
+template <typename TP, bool FOOT, bool CMP = false, bool CK = false>
 __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, double sd,
                                           const double* __restrict__ xk,
                                           const double* __restrict__ xk1,
@@ -80,7 +81,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
                                           TP* __restrict__ Bm, TP* __restrict__ Bp,
                                           TP* __restrict__ S, double* __restrict__ defect,
                                           double* __restrict__ pen, double* __restrict__ z,
-                                          unsigned* status) {
+                                          unsigned* status, Checkpoints* ck = nullptr) {
   constexpr bool F32 = std::is_same<TP, float>::value;
   const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
@@ -169,6 +170,10 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   double sPi = sPL, sQi = sQL, sTi = sTL;
 
   for (int i = 0; i < nsub; ++i) {
+    if constexpr (CK) {
+      ck->th[i] = th; ck->om[i] = om; ck->s[i] = sth; ck->c[i] = cth;
+      if (foot) { ck->py[i] = py; ck->vy[i] = vy; }
+    }
     // ---- state stages (FP64) ----
     TP cw[4], sw[4], sath[4], oms[4], wdt[4], tau[4];
     TP gr[4], gp[4], vys[4], ays[4], dl0[4], dl1[4], dl2[4];
@@ -192,10 +197,9 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       const double cjh = (j == 0) ? 0.0 : (j == 3 ? h : h2);
       const double tj = (j == 0) ? ti : (j == 3 ? te : tm);
       const double dth = cjh * kth;
-      const double ths = th + dth;
       double sn, cs;
       if (j == 0) { sn = sth; cs = cth; }
-      else sincos_step(ths, sth, cth, dth, amask, sn, cs);
+      else sincos_step(th, sth, cth, dth, amask, sn, cs);
       if constexpr (F32) {
         double sP, sQ, sT;
         if (j == 0) { sP = sPi; sQ = sQi; sT = sTi; }
@@ -274,7 +278,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     const double Dth = h * ath_;
     {
       double s1, c1;
-      sincos_step(th + Dth, sth, cth, Dth, amask, s1, c1);
+      sincos_step(th, sth, cth, Dth, amask, s1, c1);
       sth = s1;
       cth = c1;
     }
@@ -360,6 +364,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   }
 
   if (foot) Yom = fma(-h6, ip0.H, Yom);  // the end point was counted with h/3
+  if constexpr (CK) { ck->th_end = th; ck->om_end = om; ck->Yom = Yom; }
 
   // ------------------------------------------------------------ outputs ---
   const TP one = TP(1);

@@ -19,7 +19,9 @@
 
 namespace ciscvx {
 
-template <typename TP, bool FOOT>
+// FUSED: the forward sweep was run by the discretization (disc_link with CK);
+// its checkpoints, end state and penalty quadrature come in through *ckin.
+template <typename TP, bool FOOT, bool FUSED = false>
 __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, double sd,
                                          const double* __restrict__ xk,
                                          const double* __restrict__ xk1,
@@ -29,7 +31,8 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
                                          const double* __restrict__ wkm1, double rho_c,
                                          double* __restrict__ gXk, double* __restrict__ gXN,
                                          double* __restrict__ part, double* __restrict__ ps,
-                                         double* __restrict__ pL, unsigned* status) {
+                                         double* __restrict__ pL, unsigned* status,
+                                         const Checkpoints* ckin = nullptr) {
   constexpr bool F32 = std::is_same<TP, float>::value;
   const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
@@ -76,15 +79,20 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   const TP cjhP[4] = {TP(0), h2P, h2P, hP};
 
   // ---- forward sweep: FP64 state and checkpoints ----
-  double ck_th[MAXSUB_VJP], ck_om[MAXSUB_VJP], ck_s[MAXSUB_VJP], ck_c[MAXSUB_VJP];
-  double ck_py[FOOT ? MAXSUB_VJP : 1], ck_vy[FOOT ? MAXSUB_VJP : 1];
+  Checkpoints ckl;  // own forward sweep (unused when FUSED)
+  const Checkpoints& ck = FUSED ? *ckin : ckl;
   double th = th0, om = om0, py = py0, vy = vy0;
-  double sth, cth;
-  sincos(th, &sth, &cth);
   // FP32 adjoint: the penalty quadrature is taken here, on the FP64 forward
   // stages, so that the backward sweep needs no FP64 work at all.
   constexpr bool PEN_FWD = FOOT && F32;
   double Yom = 0.0;
+  if constexpr (FUSED) {
+    th = ck.th_end;
+    om = ck.om_end;
+    Yom = ck.Yom;
+  } else {
+  double sth, cth;
+  sincos(th, &sth, &cth);
   InputPenalty<TP> fp0, fpm, fp1;
   // input-only penalty terms as Simpson per substep (see disc_link.cuh)
   const double h3 = h * (1.0 / 3.0), h23 = 2.0 * h3, h6 = 0.5 * h3;
@@ -103,8 +111,8 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   double ti = 0.0;  // tau at the substep start (running sum)
   TP tiP = TP(0);
   for (int i = 0; i < nsub; ++i) {
-    ck_th[i] = th; ck_om[i] = om; ck_s[i] = sth; ck_c[i] = cth;
-    if (FOOT) { ck_py[i] = py; ck_vy[i] = vy; }
+    ckl.th[i] = th; ckl.om[i] = om; ckl.s[i] = sth; ckl.c[i] = cth;
+    if (FOOT) { ckl.py[i] = py; ckl.vy[i] = vy; }
     const double tm = ti + h2, te = ti + h;
     if (PEN_FWD) {
       fpm = input_penalty<TP>(tm, tiP + h2P, sd, sdP, mu, muP, cL, cD, cLP, cDP);
@@ -121,7 +129,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
       const double dth = cjh * kth;
       double sn, cs;
       if (j == 0) { sn = sth; cs = cth; }
-      else sincos_step(th + dth, sth, cth, dth, amask, sn, cs);
+      else sincos_step(th, sth, cth, dth, amask, sn, cs);
       double sP, sQ, sT;
       if (j == 0) { sP = sPi; sQ = sQi; sT = sTi; }
       else if (j == 3) {
@@ -150,7 +158,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
     }
     const double Dth = h * ath;
     double s1, c1;
-    sincos_step(th + Dth, sth, cth, Dth, amask, s1, c1);
+    sincos_step(th, sth, cth, Dth, amask, s1, c1);
     sth = s1; cth = c1;
     th += Dth;
     om = fma(h, aom, om);
@@ -159,6 +167,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
     tiP = tiP + hP;
   }
   if (PEN_FWD) Yom = fma(-h6, fp0.H, Yom);  // the end point was counted with h/3
+  }  // own forward sweep
 
   // cotangents of x~(1): w_k (+ rho on the penalty state)
   const double wpx = wk[rpx], wpy = wk[rpy], wth = wk[rth], wvx = wk[rvx], wvy = wk[rvy], wom = wk[rom];
@@ -187,9 +196,9 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
       ipS = input_penalty<TP, !F32>(tsb, tsP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
     {
-      const double thc = ck_th[i], omc = ck_om[i], stc = ck_s[i], ctc = ck_c[i];
+      const double thc = ck.th[i], omc = ck.om[i], stc = ck.s[i], ctc = ck.c[i];
       double pyc = 0, vyc = 0;
-      if (FOOT) { pyc = ck_py[i]; vyc = ck_vy[i]; }
+      if (FOOT) { pyc = ck.py[i]; vyc = ck.vy[i]; }
       const TP thA = TP(thc), omA = TP(omc), pyA = TP(pyc), vyA = TP(vyc);
       TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0);
       double kth = 0, kom = 0, kpy = 0, kvy = 0;
@@ -204,7 +213,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
         if (!F32) {
           const double dth = cjd * kth;
           ws = (j == 0) ? omc : fma(cjd, kom, omc);
-          if (j > 0) sincos_step(thc + dth, stc, ctc, dth, amask, sn, cs);
+          if (j > 0) sincos_step(thc, stc, ctc, dth, amask, sn, cs);
           P = fma(tj, dP, PL); Q = fma(tj, dQ, QL); T = fma(tj, dT, TL);
           wdot = fma(cs, P, fma(-sn, Q, T));
           kth = sd * ws; kom = sd * wdot;
@@ -215,7 +224,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
             const double ry = fma(sn, crx, cs * cry);
             const InputPenalty<TP>& ipj = (j == 0) ? ipS : (j == 3 ? ipE : ipM);
             const double Om = ipj.H + huber_value(-(pys + ry));
-            Yom = fma(h * wj, Om, Yom);
+            if constexpr (!FUSED) Yom = fma(h * wj, Om, Yom);  // fused: taken by the discretization
             om_pen[j] = TP(Om);
             dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
           }

@@ -249,9 +249,8 @@ def test_run_host_pipelined_matches_device_path(env, n_chunks, precision):
     plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
                          precision=precision)
     X, U, s, w, rho = _packed(plan, probs, dev, torch)
-    ref = plan.discretize(X, U, s)
     ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=dev)
-    gref = plan.discretize_vjp(X, U, s, w, rho, workspace=ws)
+    ref, gref = plan.discretize_and_vjp(X, U, s, w, rho, workspace=ws)  # the pass run_host runs per chunk
     torch.cuda.synchronize()
     pin = lambda t: t.cpu().pin_memory()  # noqa: E731
     host_in = {"X": pin(X), "U": pin(U), "s": pin(s)}
@@ -322,3 +321,72 @@ def test_sweep_precision_report_16_instances(env, capsys):
         assert bw <= TOL_FP64, (k, bw)
     for k, (bw, _) in report["fp32_phi"].items():
         assert bw <= (TOL_FP32_PHI if k in ("A", "Bm", "Bp", "S") else TOL_FP64), (k, bw)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("out_format", ["dense", "compact"])
+@pytest.mark.parametrize("layout", ["node", "interval"])
+def test_fused_pass_matches_separate_calls_and_oracle(env, precision, out_format, layout):
+    """ciscvx_batch_discretize_and_vjp: the linearization and the VJP from one
+    pass equal the separate calls to rounding, and the oracle to the usual
+    tolerances."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    robots, probs, midx = _small_mixed(seed=13, n=18)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
+                         precision=precision, layout=layout, out_format=out_format)
+    X, U, s, w, rho = _packed(plan, probs, dev, torch, layout)
+    out, g = plan.discretize_and_vjp(X, U, s, w, rho)
+    sep = plan.discretize(X, U, s)
+    gsep = plan.discretize_vjp(X, U, s, w, rho)
+    plan.sync_status()
+    f32 = precision == "fp32_phi"
+    for k in ("A", "Bm", "Bp", "S"):
+        e = block_err(out[k].double().cpu().numpy(), sep[k].double().cpu().numpy())
+        assert e <= (1e-5 if f32 else 1e-13), (k, e)
+    for k in ("defect", "penalty"):
+        assert block_err(out[k].cpu().numpy(), sep[k].cpu().numpy()) <= 1e-13, k
+    for k in ("gX", "gU", "gs", "L"):
+        e = block_err(g[k].cpu().numpy(), gsep[k].cpu().numpy())
+        assert e <= (1e-5 if f32 else 1e-12), (k, e)
+    tol = 1e-4 if f32 else 1e-10
+    gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
+    for i, p in enumerate(probs):
+        Ui = p.U if layout == "node" else p.U_interval()
+        rX, rU, rs, rL = oracle.vjp(p.robot.as_dict(), p.X, Ui, p.s, p.w, p.rho, p.n_sub, layout=layout)
+        assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= tol, i
+        assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= tol, i
+        assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= tol, i
+        assert abs(L[i] - rL) <= tol * max(1.0, abs(rL)), i
+    if out_format == "dense":
+        host = {k: v.double().cpu().numpy() for k, v in out.items()}
+        for i, p in enumerate(probs):
+            Ui = p.U if layout == "node" else p.U_interval()
+            ref = oracle.discretize(p.robot.as_dict(), p.X, Ui, p.s, p.n_sub, layout=layout)
+            _check_instance(plan, host, i, p, ref, precision)
+
+
+def test_autotune_fused_keeps_results(env):
+    """The fused pass's autotuner picks a valid launch shape and the results
+    under it match the oracle."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    robots, probs, midx = _small_mixed(seed=21, n=16)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
+                         precision="fp32_phi")
+    X, U, s, w, rho = _packed(plan, probs, dev, torch)
+    t = plan.autotune_fused(X, U, s, w, rho)
+    assert t == plan.tune_fused() and t["warps_per_cta"] in (1, 2, 4, 8)
+    out, g = plan.discretize_and_vjp(X, U, s, w, rho)
+    plan.sync_status()
+    host = {k: v.double().cpu().numpy() for k, v in out.items()}
+    gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
+    for i, p in enumerate(probs):
+        ref = oracle.discretize(p.robot.as_dict(), p.X, p.U, p.s, p.n_sub)
+        _check_instance(plan, host, i, p, ref, "fp32_phi")
+        rX, rU, rs, rL = oracle.vjp(p.robot.as_dict(), p.X, p.U, p.s, p.w, p.rho, p.n_sub)
+        assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= 1e-4
+        assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
+        assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
