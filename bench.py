@@ -64,7 +64,7 @@ DEFAULT_WORKLOAD = "cheetah7-sweep-4096x400x20"
 FLOPS_PER_INTERVAL = {
     ("cheetah7", 20, "discretize", "fp32_phi"): 28_608,
     ("cheetah7", 20, "vjp", "fp32_phi"): 29_457,
-    ("cheetah7", 20, "discretize", "fp64"): 126_397,
+    ("cheetah7", 20, "discretize", "fp64"): 126_146,
     ("cheetah7", 20, "vjp", "fp64"): 82_621,
     ("cheetah7", 20, "fused", "fp32_phi"): 31_045,
 }
@@ -73,7 +73,7 @@ FLOPS_PER_INTERVAL = {
 DRAM_BYTES_PER_INTERVAL = {
     ("cheetah7", 20, "discretize", "fp32_phi"): (310.1e6 + 1898.7e6) / 102400,
     ("cheetah7", 20, "vjp", "fp32_phi"): (249.1e6 + 155.8e6) / 102400,
-    ("cheetah7", 20, "discretize", "fp64"): (376.0e6 + 3644.2e6) / 102400,
+    ("cheetah7", 20, "discretize", "fp64"): (407.3e6 + 3762.1e6) / 102400,
     ("cheetah7", 20, "vjp", "fp64"): (258.3e6 + 227.4e6) / 102400,
     ("cheetah7", 20, "fused", "fp32_phi"): (749.8e6 + 2639.7e6) / 102400,
 }
