@@ -13,7 +13,10 @@
 //               link in maximal coordinates, Sec. II-A Eq. (1); contact frame
 //               on flat ground y = 0 (normal (0,1), tangent (1,0)), Sec. II;
 //               integral path-constraint penalty Omega = M^g sabs+(g), Sec. IV-A
-//               Eq. (12), with one auxiliary state per contact.
+//               Eq. (12), with one auxiliary state per contact — or, for the
+//               aux model 1, the full Eq. (12): four cross-complementarity
+//               states per contact (phi_n, lambda^c, gamma, rho^c) before the
+//               path-penalty states, with contact inputs (phi_t, phi_n, gamma).
 //   rk4_foh()   the time-dilated augmented system d x~/d tau = s (f, Omega) on
 //               tau in [0,1], Sec. IV-B Eq. (14), integrated in integral form
 //               Eq. (15) with a first-order-hold control u(tau) =
@@ -143,6 +146,12 @@ template <class T> T sabs_plus(const T& z) {
   return (p * p) / (1.0 + sqrt(1.0 + p * p));
 }
 
+// Pseudo-Huber absolute value / norm with unit steepness (Sec. II notation):
+// sqrt(1 + x^2) - 1 (in the plane the tangential force or impulse is a
+// scalar, so the smooth norm and the smooth absolute value are the same
+// function).
+template <class T> T smooth_abs(const T& x) { return sqrt(1.0 + x * x) - 1.0; }
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -161,13 +170,18 @@ typedef struct {
   const double* crho;     // [nc][2] contact point in the body frame
   const double* cmu;      // [nc] friction coefficient
   double g;               // gravity magnitude, acting along -y
+  int aux;                // 0: one path-penalty state per contact, forces (lambda_n, lambda_t+, lambda_t-);
+                          // 1: Eq. (12): four cross-complementarity states + one path-penalty
+                          //    state per contact, forces (phi_t, phi_n) and multiplier gamma
 } OracleModel;
 }
 
 namespace {
 
 int nx_of(const OracleModel& M) { return 6 * M.nb; }
-int nxt_of(const OracleModel& M) { return 6 * M.nb + M.nc; }
+int nxt_of(const OracleModel& M) { return 6 * M.nb + (M.aux ? 5 : 1) * M.nc; }
+// first path-penalty state (the states Eq. (13) bounds)
+int pen_of(const OracleModel& M) { return 6 * M.nb + (M.aux ? 4 * M.nc : 0); }
 int nu_of(const OracleModel& M) { return 3 * M.nj + 3 * M.nc; }
 
 // World-frame lever arm r = R(theta) rho, R = [[cos, -sin], [sin, cos]].
@@ -219,19 +233,43 @@ void rhs(const OracleModel& M, const T* xt, const T* u, T* out) {
   }
   for (int i = 0; i < nc; ++i) {
     const int b = M.cbody[i];
-    const T& ln = u[3 * nj + 3 * i];
-    const T& ltp = u[3 * nj + 3 * i + 1];
-    const T& ltm = u[3 * nj + 3 * i + 2];
     T rx, ry;
     lever_arm(xt[3 * b + 2], M.crho + 2 * i, rx, ry);
-    const T fx = ltp - ltm;  // tangent (1, 0)
-    const T fy = ln;         // normal (0, 1)
-    Fx[b] = Fx[b] + fx;
-    Fy[b] = Fy[b] + fy;
-    Tq[b] = Tq[b] + cross2(rx, ry, fx, fy);
     const T phi = xt[3 * b + 1] + ry;  // signed distance of the contact point to y = 0
-    out[6 * nb + i] = sabs_plus(-ln) + sabs_plus(-ltp) + sabs_plus(-ltm) + sabs_plus(-phi) +
-                      sabs_plus(ltp + ltm - M.cmu[i] * ln);
+    if (M.aux == 0) {
+      const T& ln = u[3 * nj + 3 * i];
+      const T& ltp = u[3 * nj + 3 * i + 1];
+      const T& ltm = u[3 * nj + 3 * i + 2];
+      const T fx = ltp - ltm;  // tangent (1, 0)
+      const T fy = ln;         // normal (0, 1)
+      Fx[b] = Fx[b] + fx;
+      Fy[b] = Fy[b] + fy;
+      Tq[b] = Tq[b] + cross2(rx, ry, fx, fy);
+      out[6 * nb + i] = sabs_plus(-ln) + sabs_plus(-ltp) + sabs_plus(-ltm) + sabs_plus(-phi) +
+                        sabs_plus(ltp + ltm - M.cmu[i] * ln);
+    } else {
+      // Eq. (12): contact-frame force (phi_t, phi_n) (the world force on flat
+      // ground) and multiplier gamma; the auxiliary states integrate phi_n,
+      // lambda^c = t^T J_c v + gamma d||phi_t||~/dphi_t (Sec. II-A), gamma and
+      // rho^c = |mu phi_n|~ - ||phi_t||~, then the path penalty of the
+      // contact's nonnegativity constraints (phi_n, phi, gamma, rho^c >= 0).
+      const T& ft = u[3 * nj + 3 * i];
+      const T& fn = u[3 * nj + 3 * i + 1];
+      const T& gam = u[3 * nj + 3 * i + 2];
+      Fx[b] = Fx[b] + ft;
+      Fy[b] = Fy[b] + fn;
+      Tq[b] = Tq[b] + cross2(rx, ry, ft, fn);
+      // tangential velocity of the contact point: x-component of p' + omega x r
+      const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;
+      const T lam_c = vt + gam * (ft / sqrt(1.0 + ft * ft));
+      const T rho_c = smooth_abs(M.cmu[i] * fn) - smooth_abs(ft);
+      out[6 * nb + 4 * i] = fn;
+      out[6 * nb + 4 * i + 1] = lam_c;
+      out[6 * nb + 4 * i + 2] = gam;
+      out[6 * nb + 4 * i + 3] = rho_c;
+      out[6 * nb + 4 * nc + i] = sabs_plus(-fn) + sabs_plus(-phi) + sabs_plus(-gam) +
+                                 sabs_plus(-rho_c);
+    }
   }
   for (int b = 0; b < nb; ++b) {
     for (int k = 0; k < 3; ++k) out[3 * b + k] = xt[3 * nb + 3 * b + k];
@@ -293,7 +331,7 @@ int ind_interval(const RHSD& F, int nxt, int nu, int nsub, const double* x0, con
 }
 
 int model_ok(const OracleModel* M) {
-  if (!M || M->nb < 1 || M->nj < 0 || M->nc < 0) return 0;
+  if (!M || M->nb < 1 || M->nj < 0 || M->nc < 0 || (M->aux != 0 && M->aux != 1)) return 0;
   for (int j = 0; j < M->nj; ++j)
     if (M->jparent[j] < 0 || M->jparent[j] >= M->nb || M->jchild[j] < 0 || M->jchild[j] >= M->nb)
       return 0;
@@ -367,7 +405,7 @@ int oracle_discretize(const OracleModel* M, int N, int nsub, int layout, const d
                       const double* U, const double* s, double* A, double* Bm, double* Bp,
                       double* S, double* defect, double* penalty, int nthreads) {
   if (!model_ok(M) || N < 1 || nsub < 1 || (layout != 0 && layout != 1)) return 1;
-  const int nxt = nxt_of(*M), nu = nu_of(*M), nx = nx_of(*M), nc = M->nc;
+  const int nxt = nxt_of(*M), nu = nu_of(*M), nx = pen_of(*M), nc = M->nc;
   if (nxt + 2 * nu + 1 > MAXC) return 1;
   int err = 0;
   parallel_for(N, nthreads, [&](long k) {
@@ -398,7 +436,7 @@ int oracle_vjp(const OracleModel* M, int N, int nsub, int layout, const double* 
                const double* U, const double* s, const double* w, const double* rho, double* gX,
                double* gU, double* gs, double* L, int nthreads) {
   if (!model_ok(M) || N < 1 || nsub < 1 || (layout != 0 && layout != 1)) return 1;
-  const int nxt = nxt_of(*M), nu = nu_of(*M), nx = nx_of(*M), nc = M->nc;
+  const int nxt = nxt_of(*M), nu = nu_of(*M), nx = pen_of(*M), nc = M->nc;
   std::vector<double> A((size_t)N * nxt * nxt), Bm((size_t)N * nxt * nu), Bp((size_t)N * nxt * nu),
       S((size_t)N * nxt), D((size_t)N * nxt), P((size_t)N * (nc > 0 ? nc : 1));
   if (oracle_discretize(M, N, nsub, layout, X, U, s, A.data(), Bm.data(), Bp.data(), S.data(),
@@ -466,11 +504,6 @@ int oracle_linear_interval(int n, int m, const double* Ac, const double* Bc, int
 // their Jacobians by the same forward-mode dual numbers.
 // ---------------------------------------------------------------------------
 namespace {
-
-// Pseudo-Huber absolute value / norm with unit steepness (Sec. II notation):
-// sqrt(1 + x^2) - 1 (in the plane the tangential impulse is a scalar, so the
-// smooth norm and the smooth absolute value are the same function).
-template <class T> T smooth_abs(const T& x) { return sqrt(1.0 + x * x) - 1.0; }
 
 // Fischer-Burmeister relaxation, Eq. (16): FB^delta(a, b) = a + b - sqrt(a^2 + b^2 + delta).
 template <class T> T fischer_burmeister(const T& a, const T& b, double delta) {
@@ -587,7 +620,7 @@ void node_eval(const OracleModel& M, const T* xp, const T* xm, const T* Phi, con
     for (int r = 0; r < 2 * nj; ++r) acc = acc - G[r * nq + a] * lam[r];
     g[nq + a] = acc;
   }
-  for (int i = 0; i < nc; ++i) g[2 * nq + i] = xp[2 * nq + i] - xm[2 * nq + i];
+  for (int a = 2 * nq; a < nxt_of(M); ++a) g[a] = xp[a] - xm[a];
   // Theta
   for (int i = 0; i < nc; ++i) {
     const int b = M.cbody[i];

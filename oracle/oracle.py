@@ -26,6 +26,7 @@ class _CModel(ctypes.Structure):
         ("jrho_p", _dp), ("jrho_c", _dp),
         ("cbody", _ip), ("crho", _dp), ("cmu", _dp),
         ("g", ctypes.c_double),
+        ("aux", ctypes.c_int),
     ]
 
 
@@ -98,7 +99,9 @@ class OracleModel:
     ``robot`` is a mapping (or object with attributes) giving ``mass`` [nb],
     ``inertia`` [nb], ``joint_parent`` / ``joint_child`` [nj],
     ``joint_rho_parent`` / ``joint_rho_child`` [nj, 2], ``contact_body`` [nc],
-    ``contact_rho`` [nc, 2], ``contact_mu`` [nc] and ``gravity``.
+    ``contact_rho`` [nc, 2], ``contact_mu`` [nc], ``gravity`` and optionally
+    ``aux_model`` (0: one path-penalty state per contact; 1: the full Eq. (12)
+    auxiliary state with contact inputs (phi_t, phi_n, gamma)).
     """
 
     def __init__(self, robot):
@@ -120,10 +123,15 @@ class OracleModel:
         for key in list(k):
             if k[key].size == 0:
                 k[key] = np.zeros(2, dtype=k[key].dtype)
+        try:
+            aux = int(get("aux_model"))
+        except (KeyError, AttributeError):
+            aux = 0
         self._c = _CModel(nb, nj, nc, _d(k["mass"]), _d(k["inertia"]),
                           k["jparent"].ctypes.data_as(_ip), k["jchild"].ctypes.data_as(_ip),
                           _d(k["jrho_p"]), _d(k["jrho_c"]), k["cbody"].ctypes.data_as(_ip),
-                          _d(k["crho"]), _d(k["cmu"]), float(get("gravity")))
+                          _d(k["crho"]), _d(k["cmu"]), float(get("gravity")), aux)
+        self.aux = aux
         self.nb, self.nj, self.nc = nb, nj, nc
         self.nxt, self.nu = dims(self)
         self.nx = 6 * nb

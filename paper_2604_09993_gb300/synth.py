@@ -22,7 +22,7 @@ stream, so any subset of instances can be regenerated alone.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -46,6 +46,7 @@ class Robot:
     gravity: float = GRAVITY
     legs: list = field(default_factory=list)  # per leg: list of joint indices (for gait poses)
     torso_horizontal: bool = True
+    aux_model: int = 0  # 0: one path-penalty state per contact; 1: Eq. (12) (4 + 1 states per contact)
 
     @property
     def nb(self):
@@ -64,8 +65,12 @@ class Robot:
         return 6 * self.nb
 
     @property
+    def ny(self):
+        return (5 if self.aux_model else 1) * self.nc
+
+    @property
     def nxt(self):
-        return 6 * self.nb + self.nc
+        return 6 * self.nb + self.ny
 
     @property
     def nu(self):
@@ -77,7 +82,7 @@ class Robot:
             "joint_parent": self.joint_parent, "joint_child": self.joint_child,
             "joint_rho_parent": self.joint_rho_parent, "joint_rho_child": self.joint_rho_child,
             "contact_body": self.contact_body, "contact_rho": self.contact_rho,
-            "contact_mu": self.contact_mu, "gravity": self.gravity,
+            "contact_mu": self.contact_mu, "gravity": self.gravity, "aux_model": self.aux_model,
         }
 
 
@@ -142,6 +147,13 @@ def cheetah7(rng):
 
 
 ROBOTS = {"hopper": hopper, "biped": biped, "cheetah7": cheetah7}
+
+
+def with_cross_states(robot: Robot) -> Robot:
+    """The same robot with the full Eq. (12) auxiliary state: four
+    cross-complementarity states + one path-penalty state per contact, and
+    contact inputs (phi_t, phi_n, gamma) in place of (lambda_n, lambda_t+, lambda_t-)."""
+    return replace(robot, aux_model=1)
 
 
 # ---------------------------------------------------------------------------

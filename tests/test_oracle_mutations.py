@@ -16,7 +16,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
 PINS = ["tests/test_oracle_integrator.py", "tests/test_oracle_physics.py", "tests/test_oracle_vjp.py",
-        "tests/test_oracle_node.py"]
+        "tests/test_oracle_node.py", "tests/test_oracle_cross.py"]
 
 MUTATIONS = [
     ("parent joint torque sign", "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) - tau;",
@@ -79,6 +79,17 @@ MUTATIONS = [
     ("friction cone without mu", "const T rho = smooth_abs(M.cmu[i] * pn) - smooth_abs(pt);",
      "const T rho = smooth_abs(pn) - smooth_abs(pt);"),
     ("Gamma seed column", "gm[i].d[2 * nxt + 2 * nc + i] = 1.0;", "gm[i].d[2 * nxt + i] = 1.0;"),
+    # full auxiliary state of Eq. (12)
+    ("lambda_c without the rotation term", "const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;",
+     "const T vt = xt[3 * nb + 3 * b];"),
+    ("lambda_c lever arm", "const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;",
+     "const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * rx;"),
+    ("phi_n state integrates phi_t", "out[6 * nb + 4 * i] = fn;", "out[6 * nb + 4 * i] = ft;"),
+    ("rho_c without mu", "const T rho_c = smooth_abs(M.cmu[i] * fn) - smooth_abs(ft);",
+     "const T rho_c = smooth_abs(fn) - smooth_abs(ft);"),
+    ("cross penalty drops gamma", "sabs_plus(-fn) + sabs_plus(-phi) + sabs_plus(-gam) +",
+     "sabs_plus(-fn) + sabs_plus(-phi) + sabs_plus(gam) +"),
+    ("cross tangential force sign", "Fx[b] = Fx[b] + ft;", "Fx[b] = Fx[b] - ft;"),
 ]
 
 
