@@ -265,9 +265,9 @@ class BatchWorkload:
             n = len(idx) // m.nxt
             Xm = self.X[torch.from_numpy(idx).to(self.dev)].view(n, m.nxt).contiguous()
             Xp = (Xm + 0.1 * torch.randn(Xm.shape, generator=gen, device=self.dev, dtype=torch.float64)).contiguous()
-            Phi = torch.randn((n, 2 * m.ny), generator=gen, device=self.dev, dtype=torch.float64)
-            Gam = torch.rand((n, m.ny), generator=gen, device=self.dev, dtype=torch.float64)
-            e = np.full(m.ny, 0.3)
+            Phi = torch.randn((n, 2 * m.nc), generator=gen, device=self.dev, dtype=torch.float64)
+            Gam = torch.rand((n, m.nc), generator=gen, device=self.dev, dtype=torch.float64)
+            e = np.full(m.nc, 0.3)
             out = self.api.node_linearize(m, Xp, Xm, Phi, Gam, self.NODE_DELTA, e)
             self.node_jobs.append((m, Xp, Xm, Phi, Gam, e, out))
         return sum(j[1].shape[0] for j in self.node_jobs)

@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 4
+#define CISCVX_VERSION_MINOR 5
 
 typedef enum {
   CISCVX_OK = 0,
@@ -125,12 +125,30 @@ typedef struct {
   double mu;                /* friction coefficient, >= 0 */
 } ciscvx_contact_desc;
 
+/* Auxiliary state and contact model.
+ *   CISCVX_AUX_PENALTY: contact inputs (lambda_n, lambda_t+, lambda_t-), world
+ *     force (lambda_t+ - lambda_t-, lambda_n); one path-penalty state per
+ *     contact (n_y = n_c), as described in the file header.
+ *   CISCVX_AUX_CROSS: the full auxiliary state of Eq. (12).  Contact inputs
+ *     (phi_t, phi_n, gamma): the contact-frame force (phi_t, phi_n) (the world
+ *     force on flat ground) and the friction multiplier gamma.  Per contact i
+ *     four cross-complementarity states integrating, in this order,
+ *       phi_n,  lambda^c = t^T J_c v + gamma phi_t / sqrt(1 + phi_t^2),
+ *       gamma,  rho^c = |mu phi_n|~ - |phi_t|~     (|x|~ = sqrt(1 + x^2) - 1),
+ *     at y index 4 i .. 4 i + 3, then one path-penalty state per contact at y
+ *     index 4 n_c + i integrating h(-phi_n) + h(-phi) + h(-gamma) + h(-rho^c)
+ *     (n_y = 5 n_c).  The penalty output is the increment of the path-penalty
+ *     states.  Provided for the dense linearization (single and batch); the
+ *     VJP, compact outputs and z return CISCVX_EUNSUPPORTED for it. */
+typedef enum { CISCVX_AUX_PENALTY = 0, CISCVX_AUX_CROSS = 1 } ciscvx_aux_model;
+
 typedef struct {
   int n_bodies, n_joints, n_contacts;
   const ciscvx_body_desc* bodies;       /* [n_bodies] host memory */
   const ciscvx_joint_desc* joints;      /* [n_joints] host memory (may be NULL if 0) */
   const ciscvx_contact_desc* contacts;  /* [n_contacts] host memory (may be NULL if 0) */
   double gravity;                       /* magnitude, acting along -y, finite */
+  int aux_model;                        /* CISCVX_AUX_PENALTY or CISCVX_AUX_CROSS */
 } ciscvx_model_desc;
 
 typedef struct ciscvx_model ciscvx_model;
@@ -148,7 +166,8 @@ ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** 
  * may be in flight. */
 void ciscvx_model_destroy(ciscvx_model* model);
 
-/* n_x = 6 n_b (x~ without the auxiliary states), n_y = n_c, n_u = 3 n_j + 3 n_c.
+/* n_x = 6 n_b (x~ without the auxiliary states), n_y = n_c (CISCVX_AUX_CROSS:
+ * 5 n_c), n_u = 3 n_j + 3 n_c.
  * Any output pointer may be NULL.  EINVAL on a null model. */
 ciscvx_status ciscvx_model_dims(const ciscvx_model* model, int* n_x, int* n_y, int* n_u);
 

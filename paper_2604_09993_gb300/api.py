@@ -83,7 +83,7 @@ class _Desc(ctypes.Structure):
     _fields_ = [("n_bodies", ctypes.c_int), ("n_joints", ctypes.c_int),
                 ("n_contacts", ctypes.c_int), ("bodies", ctypes.POINTER(_Body)),
                 ("joints", ctypes.POINTER(_Joint)), ("contacts", ctypes.POINTER(_Contact)),
-                ("gravity", ctypes.c_double)]
+                ("gravity", ctypes.c_double), ("aux_model", ctypes.c_int)]
 
 
 _lib = None
@@ -193,9 +193,13 @@ class _DescHolder:
             for j in range(nj)])
         self._contacts = (_Contact * max(nc, 1))(*[
             _Contact(int(cb[i]), (ctypes.c_double * 2)(*cr[i]), cm[i]) for i in range(nc)])
+        try:
+            aux = int(_get(robot, "aux_model"))
+        except (KeyError, AttributeError):
+            aux = 0
         self.desc = _Desc(nb, nj, nc, self._bodies, self._joints, self._contacts,
-                          float(_get(robot, "gravity")))
-        self.nb = nb
+                          float(_get(robot, "gravity")), aux)
+        self.nb, self.nc, self.aux_model = nb, nc, aux
 
 
 def model_pattern(robot):
@@ -227,6 +231,8 @@ class Model:
         self.nx, self.ny, self.nu = nx.value, ny.value, nu.value
         self.nxt = self.nx + self.ny
         self.nb = self._d.nb
+        self.nc = self._d.nc            # contacts (penalty / rho columns)
+        self.aux_model = self._d.aux_model
         na, nbb = ctypes.c_int(), ctypes.c_int()
         _check(lib.ciscvx_model_nnz(h, ctypes.byref(na), ctypes.byref(nbb)))
         self.nnz_a, self.nnz_b = na.value, nbb.value
@@ -281,7 +287,7 @@ def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layou
     f64 = torch.float64
     _need(X, "X", f64); _need(U, "U", f64); _need(s, "s", f64)
     N = s.shape[0]
-    nxt, nu, nc = model.nxt, model.nu, model.ny
+    nxt, nu, nc = model.nxt, model.nu, model.nc
     pdt = f64 if precision == "fp64" else torch.float32
     dev = X.device
     if out is None:
@@ -311,7 +317,7 @@ def discretize_compact(model: Model, X, U, s, n_sub: int, precision: str = "fp64
     f64 = torch.float64
     _need(X, "X", f64); _need(U, "U", f64); _need(s, "s", f64)
     N = s.shape[0]
-    nxt, nc = model.nxt, model.ny
+    nxt, nc = model.nxt, model.nc
     pdt = f64 if precision == "fp64" else torch.float32
     dev = X.device
     if out is None:
@@ -345,7 +351,7 @@ def node_linearize(model: Model, Xp, Xm, Phi, Gam, delta: float, restitution,
     f64 = torch.float64
     _need(Xp, "Xp", f64); _need(Xm, "Xm", f64)
     n = Xp.shape[0]
-    nq, nc, nb = 3 * model.nb, model.ny, model.nb
+    nq, nc, nb = 3 * model.nb, model.nc, model.nb
     dev = Xp.device
     if nc:
         _need(Phi, "Phi", f64); _need(Gam, "Gam", f64)
@@ -374,7 +380,7 @@ def discretize_vjp(model: Model, X, U, s, w, rho, n_sub: int, precision: str = "
     f64 = torch.float64
     for t, nm in ((X, "X"), (U, "U"), (s, "s"), (w, "w")):
         _need(t, nm, f64)
-    if model.ny:
+    if model.nc:
         _need(rho, "rho", f64)
     N = s.shape[0]
     need = workspace_size(model, OP_VJP, N, layout)
@@ -386,7 +392,7 @@ def discretize_vjp(model: Model, X, U, s, w, rho, n_sub: int, precision: str = "
     L = torch.empty((), dtype=f64, device=X.device) if want_L else None
     _check(load().ciscvx_discretize_vjp(
         model.handle, int(N), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X), _ptr(U),
-        _ptr(s), _ptr(w), _ptr(rho) if model.ny else None, _ptr(gX), _ptr(gU) if model.nu else None,
+        _ptr(s), _ptr(w), _ptr(rho) if model.nc else None, _ptr(gX), _ptr(gU) if model.nu else None,
         _ptr(gs), _ptr(L), _ptr(workspace), workspace.numel() * workspace.element_size(),
         _stream()))
     return gX, gU, gs, L
@@ -400,7 +406,7 @@ def discretize_vjp_static(model: Model, X, U, s, w, rho, n_sub: int, precision: 
     f64 = torch.float64
     for t, nm in ((X, "X"), (U, "U"), (s, "s"), (w, "w")):
         _need(t, nm, f64)
-    if model.ny:
+    if model.nc:
         _need(rho, "rho", f64)
     gX = torch.empty_like(X)
     gU = torch.empty_like(U)
@@ -408,7 +414,7 @@ def discretize_vjp_static(model: Model, X, U, s, w, rho, n_sub: int, precision: 
     L = torch.empty((), dtype=f64, device=X.device) if want_L else None
     _check(load().ciscvx_discretize_vjp_static(
         model.handle, int(s.shape[0]), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X),
-        _ptr(U), _ptr(s), _ptr(w), _ptr(rho) if model.ny else None, _ptr(gX),
+        _ptr(U), _ptr(s), _ptr(w), _ptr(rho) if model.nc else None, _ptr(gX),
         _ptr(gU) if model.nu else None, _ptr(gs), _ptr(L), _stream()))
     return gX, gU, gs, L
 
@@ -439,7 +445,7 @@ def _make_function():
             model, n_sub, precision, layout = ctx.cfg
             w = torch.zeros((s.shape[0], model.nxt), dtype=X.dtype, device=X.device) \
                 if gdef is None else gdef.contiguous()
-            rho = torch.zeros((s.shape[0], model.ny), dtype=X.dtype, device=X.device) \
+            rho = torch.zeros((s.shape[0], model.nc), dtype=X.dtype, device=X.device) \
                 if gpen is None else gpen.contiguous()
             gX, gU, gs, _ = discretize_vjp(model, X, U, s, w, rho, n_sub, precision, layout,
                                            want_L=False)

@@ -108,7 +108,9 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   std::memset(&M, 0, sizeof M);
   const int nb = d->n_bodies, nj = d->n_joints, nc = d->n_contacts;
   M.nb = nb; M.nj = nj; M.nc = nc;
-  M.nxt = 6 * nb + nc;
+  M.aux = d->aux_model;
+  M.ny = (M.aux ? 5 : 1) * nc;
+  M.nxt = 6 * nb + M.ny;
   M.nu = 3 * nj + 3 * nc;
   M.g = d->gravity;
   M.tree = 1;
@@ -179,10 +181,17 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
     const double m = d->bodies[C.body].mass, I = d->bodies[C.body].inertia;
     const double rx = C.rho[0], ry = C.rho[1];
     ciscvx_status st;
-    // lambda_n: +e_y;  lambda_t+: +e_x;  lambda_t-: -e_x
-    if ((st = add_input(M, C.body, B.cin, 0, 1.0 / m, rx / I, ry / I, 0))) return st;
-    if ((st = add_input(M, C.body, B.cin + 1, 1.0 / m, 0, -ry / I, rx / I, 0))) return st;
-    if ((st = add_input(M, C.body, B.cin + 2, -1.0 / m, 0, ry / I, -rx / I, 0))) return st;
+    if (M.aux) {
+      // Eq. (12) model: phi_t: +e_x;  phi_n: +e_y;  gamma: no force (it enters the auxiliary state only)
+      if ((st = add_input(M, C.body, B.cin, 1.0 / m, 0, -ry / I, rx / I, 0))) return st;
+      if ((st = add_input(M, C.body, B.cin + 1, 0, 1.0 / m, rx / I, ry / I, 0))) return st;
+      if ((st = add_input(M, C.body, B.cin + 2, 0, 0, 0, 0, 0))) return st;
+    } else {
+      // lambda_n: +e_y;  lambda_t+: +e_x;  lambda_t-: -e_x
+      if ((st = add_input(M, C.body, B.cin, 0, 1.0 / m, rx / I, ry / I, 0))) return st;
+      if ((st = add_input(M, C.body, B.cin + 1, 1.0 / m, 0, -ry / I, rx / I, 0))) return st;
+      if ((st = add_input(M, C.body, B.cin + 2, -1.0 / m, 0, ry / I, -rx / I, 0))) return st;
+    }
   }
   // VJP slots: link b's inputs occupy slots [slot0, slot0 + nin)
   int slot = 0;
@@ -222,6 +231,8 @@ ciscvx_status check_desc(const ciscvx_model_desc* desc) {
   if (desc->n_bodies > MAXB || desc->n_joints > MAXJ || desc->n_contacts > MAXB)
     return fail(CISCVX_EUNSUPPORTED, "at most %d links, %d joints, %d contacts", MAXB, MAXJ, MAXB);
   if (!std::isfinite(desc->gravity)) return fail(CISCVX_EINVAL, "non-finite gravity");
+  if (desc->aux_model != CISCVX_AUX_PENALTY && desc->aux_model != CISCVX_AUX_CROSS)
+    return fail(CISCVX_EINVAL, "unknown aux_model %d", desc->aux_model);
   return CISCVX_OK;
 }
 
@@ -342,6 +353,7 @@ ciscvx_status ciscvx_model_pattern(const ciscvx_model_desc* desc, int* nnz_a, in
   DevModel* M = new (std::nothrow) DevModel;
   if (!M) return fail(CISCVX_ENOMEM, "host allocation failed");
   st = build_tables(desc, *M);
+  if (st == CISCVX_OK && M->aux) st = fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
   if (st == CISCVX_OK) {
     if (nnz_a) *nnz_a = M->nnzA;
     if (nnz_b) *nnz_b = M->nnzB;
@@ -361,7 +373,7 @@ ciscvx_status ciscvx_model_nnz(const ciscvx_model* m, int* nnz_a, int* nnz_b) {
 ciscvx_status ciscvx_model_dims(const ciscvx_model* m, int* n_x, int* n_y, int* n_u) {
   if (!m) return fail(CISCVX_EINVAL, "null model");
   if (n_x) *n_x = 6 * m->host.nb;
-  if (n_y) *n_y = m->host.nc;
+  if (n_y) *n_y = m->host.ny;
   if (n_u) *n_u = m->host.nu;
   return ok();
 }
@@ -389,7 +401,8 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* m, int N, int n_sub,
   if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
   if (m->host.nu > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
-  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, false, X, U,
+  if (m->host.aux && z) return fail(CISCVX_EUNSUPPORTED, "z is not provided for the Eq. (12) model");
+  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, false, m->host.aux != 0, X, U,
                                     s, A, Bm, Bp, S, defect, penalty, z, m->status,
                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
@@ -406,7 +419,8 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* m, int N, int n_sub,
   if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
   if (m->host.nnzB > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
-  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, true, X, U,
+  if (m->host.aux) return fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
+  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, true, false, X, U,
                                     s, A, Bm, Bp, S, defect, penalty, z, m->status,
                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
@@ -423,6 +437,7 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
   if (st != CISCVX_OK) return st;
   if (n_sub > MAXSUB_VJP)
     return fail(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (got %d)", MAXSUB_VJP, n_sub);
+  if (m->host.aux) return fail(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
   if (!w || (m->host.nc > 0 && !rho)) return fail(CISCVX_EINVAL, "null cotangent array");
   if (!gX || !gs || (m->host.nu > 0 && !gU)) return fail(CISCVX_EINVAL, "null gradient array");
   const size_t need = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);

@@ -26,7 +26,10 @@
 namespace ciscvx {
 
 // CMP: compact A/Bm/Bp (structural nonzeros only; strides nnzA / nnzB).
-template <typename TP, int OCC, bool CMP>
+// AUX: some model of the batch uses the Eq. (12) auxiliary state (its foot
+// links take the CROSS path); a separate instantiation keeps that path's
+// registers out of the common kernels.
+template <typename TP, int OCC, bool CMP, bool AUX = false>
 __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCommon c, const double* __restrict__ X,
                                                     const double* __restrict__ U,
                                                     const double* __restrict__ s, TP* A, TP* Bm,
@@ -57,7 +60,11 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCo
       TP* Sk = S + I.v + (size_t)k * nxt;
       double* dk = defect + I.v + (size_t)k * nxt;
       double* pk = penalty ? penalty + I.p + (size_t)k * nc : nullptr;
-      if (M.body[b].contact >= 0)
+      if (AUX && M.aux && M.body[b].contact >= 0)  // Eq. (12) model (dense outputs)
+        disc_link<TP, true, false, false, AUX>(M, b, g.y, s[I.s + k], Xi + k * nxt,
+                                               Xi + (k + 1) * nxt, uL, uR, Ak, Bmk, Bpk, Sk, dk,
+                                               pk, nullptr, c.status);
+      else if (M.body[b].contact >= 0)
         disc_link<TP, true, CMP>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
                                  Ak, Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
       else
@@ -185,6 +192,7 @@ struct ciscvx_batch_plan {
   int n_inst = 0, n_models = 0, prec = 0, layout = 0, device = 0, sm_count = 0, max_nsub = 0;
   bool compact = false;  // CISCVX_OUT_COMPACT
   bool all_nu0 = true, all_nc0 = true;
+  bool any_aux = false;  // some model uses the Eq. (12) auxiliary state (no VJP, no compact outputs)
   std::vector<const ciscvx_model*> models;
   std::vector<DevInst> inst;
   ciscvx_batch_sizes sizes{};
@@ -367,6 +375,17 @@ cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const cisc
     else CISCVX_DISC1(TP, OCC, false);           \
   } while (0)
   const int occ = p->tune.occupancy;
+  if (p->any_aux) {  // Eq. (12) model in the batch: dense outputs, no register cap
+    if (p->prec == CISCVX_FP64)
+      k_batch_disc<double, 0, false, true><<<blocks, threads, 0, st>>>(
+          c, io->X, io->U, io->s, (double*)io->A, (double*)io->Bm, (double*)io->Bp,
+          (double*)io->S, io->defect, io->penalty);
+    else
+      k_batch_disc<float, 0, false, true><<<blocks, threads, 0, st>>>(
+          c, io->X, io->U, io->s, (float*)io->A, (float*)io->Bm, (float*)io->Bp, (float*)io->S,
+          io->defect, io->penalty);
+    return cudaGetLastError();
+  }
   if (p->prec == CISCVX_FP64) {
     if (occ == 1) CISCVX_DISC(double, 1);
     else if (occ == 2) CISCVX_DISC(double, 2);
@@ -447,6 +466,7 @@ ciscvx_status check_vjp(const ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* i
   if (p->max_nsub > MAXSUB_VJP)
     return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (plan has %d)",
                      MAXSUB_VJP, p->max_nsub);
+  if (p->any_aux) return set_error(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
   const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
   if (!workspace || ws_bytes < need)
     return set_error(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
@@ -554,8 +574,13 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     p->max_nsub = std::max(p->max_nsub, n_sub[i]);
     if (nu) p->all_nu0 = false;
     if (nc) p->all_nc0 = false;
+    if (M.aux) p->any_aux = true;
   }
   z.L = (size_t)n_inst;
+  if (p->any_aux && p->compact) {
+    free_plan(p);
+    return set_error(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
+  }
 
   // work decomposition of the whole batch (one chunk)
   HostDecomp dec = decompose(p, {0, n_inst});
@@ -857,6 +882,7 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
     if (!p->all_nc0 && (!host_vjp->rho || !dev_vjp->rho)) return set_error(CISCVX_EINVAL, "null rho");
     if (p->max_nsub > MAXSUB_VJP)
       return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps", MAXSUB_VJP);
+    if (p->any_aux) return set_error(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
     const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 15) != 0)
       return set_error(CISCVX_EINVAL, "16-byte aligned workspace of %zu bytes needed", need);

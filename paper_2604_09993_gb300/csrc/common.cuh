@@ -75,6 +75,8 @@ struct DevModel {
   int nb, nj, nc, nxt, nu, nslot;   // nslot = sum of nin over links
   int nnzA, nnzB;                    // structural nonzeros of A and of B-/B+ (compact outputs)
   int tree;                          // every link is the child of at most one joint
+  int aux;                           // 0: one path-penalty state per contact; 1: Eq. (12) (4 + 1)
+  int ny;                            // auxiliary states: nc or 5 nc
   double g;
   // joints and link inertia (node constraints: impact map)
   int jpar[MAXJ], jchi[MAXJ];
@@ -256,7 +258,7 @@ struct ciscvx_model {
 // Launchers (defined in disc.cu / vjp.cu), called by the host API in api.cu.
 namespace ciscvx {
 cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int prec, int layout,
-                              bool compact, const double* X, const double* U, const double* s, void* A,
+                              bool compact, bool aux, const double* X, const double* U, const double* s, void* A,
                               void* Bm, void* Bp, void* S, double* defect, double* penalty,
                               double* z, unsigned* status, cudaStream_t st);
 cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, int N, int nsub,

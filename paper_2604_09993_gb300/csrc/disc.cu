@@ -13,7 +13,8 @@
 namespace ciscvx {
 
 // CMP: compact A/Bm/Bp (structural nonzeros only; strides nnzA / nnzB).
-template <typename TP, bool CMP>
+// AUX: the model uses the Eq. (12) auxiliary state (foot links take the CROSS path).
+template <typename TP, bool CMP, bool AUX = false>
 __global__ void __launch_bounds__(128) k_discretize(const DevModel* __restrict__ Mp, int N,
                                                     int nsub, int layout,
                                                     const double* __restrict__ X,
@@ -42,6 +43,13 @@ __global__ void __launch_bounds__(128) k_discretize(const DevModel* __restrict__
   double* dk = defect + (size_t)k * nxt;
   double* pk = penalty ? penalty + (size_t)k * nc : nullptr;
   double* zk = z ? z + (size_t)k * nxt : nullptr;
+  if constexpr (AUX) {
+    if (M.body[b].contact >= 0) {  // Eq. (12) model (no z, dense outputs)
+      disc_link<TP, true, false, false, true>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL,
+                                              uR, Ak, Bmk, Bpk, Sk, dk, pk, nullptr, status);
+      return;
+    }
+  }
   if (M.body[b].contact >= 0)
     disc_link<TP, true, CMP>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL, uR, Ak, Bmk,
                              Bpk, Sk, dk, pk, zk, status);
@@ -51,16 +59,26 @@ __global__ void __launch_bounds__(128) k_discretize(const DevModel* __restrict__
 }
 
 cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int prec, int layout,
-                              bool compact, const double* X, const double* U, const double* s,
-                              void* A, void* Bm, void* Bp, void* S, double* defect,
-                              double* penalty, double* z, unsigned* status, cudaStream_t st) {
+                              bool compact, bool aux, const double* X, const double* U,
+                              const double* s, void* A, void* Bm, void* Bp, void* S,
+                              double* defect, double* penalty, double* z, unsigned* status,
+                              cudaStream_t st) {
   const long warps = (long)((N + 31) / 32) * nb;
   const int threads = single_cta_threads(warps);
   const long blocks = (warps * 32 + threads - 1) / threads;
 #define CISCVX_K(TP, CMP)                                                                    \
   k_discretize<TP, CMP><<<(unsigned)blocks, threads, 0, st>>>(                                \
       dM, N, nsub, layout, X, U, s, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, defect, penalty, z, status)
-  if (prec == CISCVX_FP64) {
+  if (aux) {  // Eq. (12) model: dense outputs, no z (checked by the caller)
+    if (prec == CISCVX_FP64)
+      k_discretize<double, false, true><<<(unsigned)blocks, threads, 0, st>>>(
+          dM, N, nsub, layout, X, U, s, (double*)A, (double*)Bm, (double*)Bp, (double*)S, defect,
+          penalty, nullptr, status);
+    else
+      k_discretize<float, false, true><<<(unsigned)blocks, threads, 0, st>>>(
+          dM, N, nsub, layout, X, U, s, (float*)A, (float*)Bm, (float*)Bp, (float*)S, defect,
+          penalty, nullptr, status);
+  } else if (prec == CISCVX_FP64) {
     if (compact) CISCVX_K(double, true); else CISCVX_K(double, false);
   } else {
     if (compact) CISCVX_K(float, true); else CISCVX_K(float, false);

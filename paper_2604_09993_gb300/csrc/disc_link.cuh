@@ -27,6 +27,11 @@ struct Tangents {
   TP Pt[9], Pw[9];         // rotation tangents: theta row, omega row
   TP Qp[5], Qv[5];         // foot p_y/v_y tangents: columns py0, vy0, s, L, R
   TP Yr[9], Yp[5], Yd[6];  // foot penalty row: rotation columns, p_y columns, direct contact inputs
+  // Eq. (12) model (CROSS) only:
+  TP Yl[9];                // lambda^c row: rotation columns
+  TP Ylv[3];               // lambda^c row: v_x channel columns u_L forcing, u_R forcing, s
+  TP Vxs;                  // tangent of v_x with respect to s (substep start)
+  TP Yld[4], Yrd[4];       // direct terms: lambda^c row (phi_t L/R, gamma L/R), rho^c row (phi_t L/R, phi_n L/R)
 };
 
 // Penalty terms that depend on the inputs alone, at one stage time.
@@ -66,13 +71,60 @@ __device__ __forceinline__ InputPenalty<TP> input_penalty(double t, TP tP, doubl
   return r;
 }
 
+// The input-only terms of the Eq. (12) auxiliary state at one stage time, for
+// contact inputs (phi_t, phi_n, gamma) = L + t D:
+//   H   = h(-phi_n) + h(-gamma) + h(-rho^c)   (path penalty, input-only part)
+//   R   = rho^c = |mu phi_n|~ - |phi_t|~      (rho^c state)
+//   G   = gamma phi_t / sqrt(1 + phi_t^2)      (input part of lambda^c)
+// FP64 values and s-scaled slopes in the tangent precision.
+template <typename TP>
+struct InputCross {
+  double H, R, G;
+  TP d0, d1, d2;  // s dH/d(phi_t, phi_n, gamma)
+  TP r0, r1;      // s dR/d(phi_t, phi_n)
+  TP q0, q2;      // s dG/d(phi_t, gamma)
+};
+
+// pseudo-Huber absolute value sqrt(1 + x^2) - 1 (as a rsqrt(a) - 1, a = 1 + x^2)
+__device__ __forceinline__ double sabs_value(double x) {
+  const double a = fma(x, x, 1.0);
+  return fma(a, rsqrt(a), -1.0);
+}
+
+template <typename TP>
+__device__ __forceinline__ InputCross<TP> input_cross(double t, TP tP, TP sdP, double mu, TP muP,
+                                                      const double* L, const double* D,
+                                                      const TP* LP, const TP* DP) {
+  InputCross<TP> r;
+  const double ft = fma(t, D[0], L[0]), fn = fma(t, D[1], L[1]), ga = fma(t, D[2], L[2]);
+  const double at = fma(ft, ft, 1.0), rt = rsqrt(at);
+  r.R = sabs_value(mu * fn) - fma(at, rt, -1.0);
+  r.H = huber_value(-fn) + huber_value(-ga) + huber_value(-r.R);
+  r.G = ga * (ft * rt);
+  const TP ftP = LP[0] + tP * DP[0], fnP = LP[1] + tP * DP[1], gaP = LP[2] + tP * DP[2];
+  const TP rtP = TP(1) / sqrt(TP(1) + ftP * ftP);
+  const TP mfn = muP * fnP;
+  const TP dmn = mfn / sqrt(TP(1) + mfn * mfn);  // d|x|~/dx at mu phi_n
+  const TP dft = ftP * rtP;                      // d|x|~/dx at phi_t (= phi_t / sqrt(1 + phi_t^2))
+  const TP RP = (sqrt(TP(1) + mfn * mfn) - TP(1)) - (sqrt(TP(1) + ftP * ftP) - TP(1));
+  const TP hR = huber_slope(-RP);
+  r.r0 = -sdP * dft;
+  r.r1 = sdP * muP * dmn;
+  r.d0 = -hR * r.r0;
+  r.d1 = -sdP * huber_slope(-fnP) - hR * r.r1;
+  r.d2 = -sdP * huber_slope(-gaP);
+  r.q0 = sdP * gaP * rtP * rtP * rtP;
+  r.q2 = sdP * dft;
+  return r;
+}
+
 // One link of one interval.  xk/xk1: node states k and k+1; uL/uR: FOH
 // controls; A/Bm/Bp/S/defect/pen/z: this interval's output blocks.
 // CMP: A, Bm, Bp point at this interval's compact values (structural
 // nonzeros only, at the link's offsets; see common.cuh) instead of its dense
 // blocks.  CK: also record the FP64 state at every substep start (and the end
 // state and penalty quadrature) in *ck, for the adjoint's backward sweep.
-template <typename TP, bool FOOT, bool CMP = false, bool CK = false>
+template <typename TP, bool FOOT, bool CMP = false, bool CK = false, bool CROSS = false>
 __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, double sd,
                                           const double* __restrict__ xk,
                                           const double* __restrict__ xk1,
@@ -83,6 +135,10 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
                                           double* __restrict__ pen, double* __restrict__ z,
                                           unsigned* status, Checkpoints* ck = nullptr) {
   constexpr bool F32 = std::is_same<TP, float>::value;
+  // CROSS: the link carries a contact of the Eq. (12) model (see the header
+  // comment of input_cross); compact outputs and z are not provided for it.
+  static_assert(!(CROSS && (CMP || CK)), "Eq. (12) model: dense outputs only");
+  constexpr bool cross = FOOT && CROSS;
   const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
   const int nb = M.nb, nxt = M.nxt, nu = M.nu;
@@ -142,6 +198,18 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   for (int c = 0; c < 6; ++c) tg.Yd[c] = TP(0);
   tg.Pt[0] = TP(1); tg.Pw[1] = TP(1);
   tg.Qp[0] = TP(1); tg.Qv[1] = TP(1);
+  if constexpr (cross) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) tg.Yl[c] = TP(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { tg.Yld[c] = TP(0); tg.Yrd[c] = TP(0); }
+    tg.Ylv[0] = tg.Ylv[1] = tg.Ylv[2] = TP(0);
+    tg.Vxs = TP(0);
+  }
+  // Eq. (12) model: x-velocity stages for lambda^c (s-scaled slopes, as for v_y)
+  const double dAx = AxR - AxL, sAxL = sd * AxL, sdAxs = sd * dAx;
+  const TP AxLP = TP(AxL), dAxP = TP(dAx);
+  double vx = vx0, Il = 0.0, Ir = 0.0, Ig = 0.0;  // lambda^c state part, rho^c, gamma g integrals
 
   const double h = 1.0 / nsub, h2 = 0.5 * h;
   const TP hP = TP(h), sdP = TP(sd), h2P = TP(h2);
@@ -152,13 +220,21 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   double sth, cth;  // sin/cos of th at the substep start (chained)
   sincos(th, &sth, &cth);
   InputPenalty<TP> ip0;  // input penalty at the substep start
-  if (foot) ip0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+  InputCross<TP> ic0;    // Eq. (12) model: input-only terms at the substep start
+  if constexpr (cross) ic0 = input_cross<TP>(0.0, TP(0), sdP, mu, muP, cL, cD, cLP, cDP);
+  else if (foot) ip0 = input_penalty<TP>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
   // Penalty quadrature: the input-only terms H(tau) enter every substep as
   // Simpson's rule (h/6 H(t_i) + 2h/3 H(t_i + h/2) + h/6 H(t_i + h)); they are
   // accumulated as 2h/3 H(mid) + h/3 H(end) per substep, with h/6 H(0) added
   // first and h/6 H(1) taken off at the end.
   const double h3 = h * (1.0 / 3.0), h23 = 2.0 * h3, h6 = 0.5 * h3;
-  if (foot) Yom = h6 * ip0.H;
+  if constexpr (cross) {
+    Yom = h6 * ic0.H;
+    Ir = h6 * ic0.R;
+    Ig = h6 * ic0.G;
+  } else if (foot) {
+    Yom = h6 * ip0.H;
+  }
   // FP32-Phi mode: the FP64 state needs only the s-scaled stage slopes
   // k_theta = s omega_stage and k_omega = s (cos P - sin Q + T), so the input
   // sums are pre-scaled by s (one FMA per slope instead of an FMA and a
@@ -177,17 +253,24 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     // ---- state stages (FP64) ----
     TP cw[4], sw[4], sath[4], oms[4], wdt[4], tau[4];
     TP gr[4], gp[4], vys[4], ays[4], dl0[4], dl1[4], dl2[4];
+    TP lry[4], lrx[4], axs[4], vxP[4], cq0[4], cq2[4], cr0[4], cr1[4];  // Eq. (12) model
     const double tm = ti + h2, te = ti + h;
     const TP tmP = tiP + h2P, teP = tiP + hP;
     InputPenalty<TP> ipm, ip1;
-    if (foot) {
+    InputCross<TP> icm, ic1;
+    if constexpr (cross) {
+      icm = input_cross<TP>(tm, tmP, sdP, mu, muP, cL, cD, cLP, cDP);
+      ic1 = input_cross<TP>(te, teP, sdP, mu, muP, cL, cD, cLP, cDP);
+    } else if (foot) {
       ipm = input_penalty<TP>(tm, tmP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
       ip1 = input_penalty<TP>(te, teP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
     // FP32 copy of the stage recursion, anchored on the FP64 state (FP32-Phi mode)
     const TP thA = TP(th), omA = TP(om), pyA = TP(py), vyA = TP(vy);
-    TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0);
+    const TP vxA = cross ? TP(vx) : TP(0);
+    TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0), kvxA = TP(0);
     double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
+    double kvx = 0, avx = 0;  // Eq. (12) model: s a_x at the stage, its RK4 sum
     const double som = sd * om, svy = foot ? sd * vy : 0.0;
     double sPm = 0, sQm = 0, sTm = 0;
     double ws = 0, P = 0, Q = 0, T = 0;  // FP64 stage data (FP64 mode only)
@@ -200,6 +283,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       double sn, cs;
       if (j == 0) { sn = sth; cs = cth; }
       else sincos_step(th, sth, cth, dth, amask, sn, cs);
+      // Eq. (12) model: omega at the stage (kom is still the previous stage's slope)
+      const double wst = cross ? ((j == 0) ? om : fma(cjh, kom, om)) : 0.0;
       if constexpr (F32) {
         double sP, sQ, sT;
         if (j == 0) { sP = sPi; sQ = sQi; sT = sTi; }
@@ -233,10 +318,24 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         }
         apy = fma(wj, kpy, apy);
         avy = fma(wj, kvy, avy);
-        // ground term h(-phi), phi = p_y + (R rho)_y at the stage
-        Yom = fma(h * wj, huber_value(-fma(sn, crx, fma(cs, cry, pys))), Yom);
-        const InputPenalty<TP>& ipj = (j == 0) ? ip0 : (j == 3 ? ip1 : ipm);
-        dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
+        if constexpr (cross) {
+          // ground term h(-phi); lambda^c's state part v_x - omega (R rho)_y
+          const double ry = fma(sn, crx, cs * cry);
+          Yom = fma(h * wj, huber_value(-(pys + ry)), Yom);
+          const double vxs = (j == 0) ? vx : fma(cjh, kvx, vx);
+          kvx = fma(tj, sdAxs, sAxL);
+          avx = fma(wj, kvx, avx);
+          Il = fma(h * wj, fma(-wst, ry, vxs), Il);
+          vxP[j] = F32 ? ((j == 0) ? vxA : vxA + cjhP[j] * kvxA) : TP(vxs);
+          const InputCross<TP>& icj = (j == 0) ? ic0 : (j == 3 ? ic1 : icm);
+          dl0[j] = icj.d0; dl1[j] = icj.d1; dl2[j] = icj.d2;
+          cq0[j] = icj.q0; cq2[j] = icj.q2; cr0[j] = icj.r0; cr1[j] = icj.r1;
+        } else {
+          // ground term h(-phi), phi = p_y + (R rho)_y at the stage
+          Yom = fma(h * wj, huber_value(-fma(sn, crx, fma(cs, cry, pys))), Yom);
+          const InputPenalty<TP>& ipj = (j == 0) ? ip0 : (j == 3 ? ip1 : ipm);
+          dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
+        }
       }
       // stage data for the tangent recursion
       const TP cjhT = cjhP[j];
@@ -273,6 +372,12 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         gr[j] = -sdP * D4 * rxP;  // s dOmega/dtheta
         vys[j] = vsP;
         ays[j] = ayP;
+        if constexpr (cross) {
+          lry[j] = -sdP * ryP;        // s d(lambda^c)/d omega
+          lrx[j] = -sdP * wsP * rxP;  // s d(lambda^c)/d theta
+          axs[j] = AxLP + tau[j] * dAxP;
+          if constexpr (F32) kvxA = sdP * axs[j];
+        }
       }
     }
     const double Dth = h * ath_;
@@ -287,8 +392,16 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     if (foot) {
       py = fma(h, apy, py);
       vy = fma(h, avy, vy);
-      Yom = fma(h3, ip1.H, fma(h23, ipm.H, Yom));
-      ip0 = ip1;
+      if constexpr (cross) {
+        vx = fma(h, avx, vx);
+        Yom = fma(h3, ic1.H, fma(h23, icm.H, Yom));
+        Ir = fma(h3, ic1.R, fma(h23, icm.R, Ir));
+        Ig = fma(h3, ic1.G, fma(h23, icm.G, Ig));
+        ic0 = ic1;
+      } else {
+        Yom = fma(h3, ip1.H, fma(h23, ipm.H, Yom));
+        ip0 = ip1;
+      }
     }
     ti = te;
     tiP = teP;
@@ -297,7 +410,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const TP T0 = tg.Pt[c], W0 = tg.Pw[c];
-      TP kT = TP(0), kW = TP(0), aT = TP(0), aW = TP(0), ya = TP(0);
+      TP kT = TP(0), kW = TP(0), aT = TP(0), aW = TP(0), ya = TP(0), yl = TP(0);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const TP cjh = cjhP[j], wj = TP(rk_w(j));
@@ -317,10 +430,12 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         aT += wj * kT;
         aW += wj * kW;
         if (foot) ya += wj * gr[j] * Ts;
+        if constexpr (cross) yl += wj * (lry[j] * Ws + lrx[j] * Ts);
       }
       tg.Pt[c] = T0 + hP * aT;
       tg.Pw[c] = W0 + hP * aW;
       if (foot) tg.Yr[c] += hP * ya;
+      if constexpr (cross) tg.Yl[c] += hP * yl;
     }
 
     // ---- foot: p_y channel tangents and the penalty row ----
@@ -332,7 +447,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
 #pragma unroll
       for (int c = 1; c < 5; ++c) {
         const TP P0 = tg.Qp[c], V0 = tg.Qv[c];
-        TP kP = TP(0), kV = TP(0), aP = TP(0), aV = TP(0), ya = TP(0);
+        TP kP = TP(0), kV = TP(0), aP = TP(0), aV = TP(0), ya = TP(0), yv = TP(0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const TP cjh = cjhP[j], wj = TP(rk_w(j));
@@ -347,10 +462,30 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
           aP += wj * kP;
           aV += wj * kV;
           ya += wj * gp[j] * Ps;
+          // unit-forcing tangents of v_y equal those of v_x (same equation v' = s a)
+          if constexpr (cross) yv += wj * sdP * Vs;
         }
         tg.Qp[c] = P0 + hP * aP;
         tg.Qv[c] = V0 + hP * aV;
         tg.Yp[c] += hP * ya;
+        if constexpr (cross) {
+          if (c >= 3) tg.Ylv[c - 3] += hP * yv;
+        }
+      }
+      if constexpr (cross) {
+        // v_x tangent with respect to s (forcing a_x(tau)); lambda^c's s column
+        const TP V0 = tg.Vxs;
+        TP kV = TP(0), aV = TP(0), yv = TP(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const TP wj = TP(rk_w(j));
+          const TP Vs = (j == 0) ? V0 : V0 + cjhP[j] * kV;
+          kV = axs[j];
+          aV += wj * kV;
+          yv += wj * sdP * Vs;
+        }
+        tg.Vxs = V0 + hP * aV;
+        tg.Ylv[2] += hP * yv;
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -359,17 +494,31 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         tg.Yd[0] += hw * dl0[j] * wl; tg.Yd[3] += hw * dl0[j] * wr;
         tg.Yd[1] += hw * dl1[j] * wl; tg.Yd[4] += hw * dl1[j] * wr;
         tg.Yd[2] += hw * dl2[j] * wl; tg.Yd[5] += hw * dl2[j] * wr;
+        if constexpr (cross) {
+          tg.Yld[0] += hw * cq0[j] * wl; tg.Yld[1] += hw * cq0[j] * wr;
+          tg.Yld[2] += hw * cq2[j] * wl; tg.Yld[3] += hw * cq2[j] * wr;
+          tg.Yrd[0] += hw * cr0[j] * wl; tg.Yrd[1] += hw * cr0[j] * wr;
+          tg.Yrd[2] += hw * cr1[j] * wl; tg.Yrd[3] += hw * cr1[j] * wr;
+        }
       }
     }
   }
 
-  if (foot) Yom = fma(-h6, ip0.H, Yom);  // the end point was counted with h/3
+  // the end point was counted with h/3
+  if constexpr (cross) {
+    Yom = fma(-h6, ic0.H, Yom);
+    Ir = fma(-h6, ic0.R, Ir);
+    Ig = fma(-h6, ic0.G, Ig);
+  } else if (foot) {
+    Yom = fma(-h6, ip0.H, Yom);
+  }
   if constexpr (CK) { ck->th_end = th; ck->om_end = om; ck->Yom = Yom; }
 
   // ------------------------------------------------------------ outputs ---
   const TP one = TP(1);
   const TP sdT = TP(sd), s2_3 = TP(sd * sd / 3.0), s2_6 = TP(sd * sd / 6.0), s_2 = TP(0.5 * sd);
-  const int ry = foot ? 6 * nb + B.contact : -1;
+  // the contact's path-penalty row (after the Eq. (12) model's four cross states per contact)
+  const int ry = foot ? 6 * nb + (cross ? 4 * M.nc : 0) + B.contact : -1;
   if constexpr (!CMP) {
     // Zero this link's rows of A, B-, B+ (and the contact's row) cooperatively,
     // then write the structural entries.
@@ -386,6 +535,14 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       if (nu > 0) {
         warp_zero_chunks(Bm + (size_t)ry * nu, nu, amask);
         warp_zero_chunks(Bp + (size_t)ry * nu, nu, amask);
+      }
+    }
+    if constexpr (cross) {  // the contact's four cross-complementarity rows
+      const int yb = 6 * nb + 4 * B.contact;
+      warp_zero_chunks(A + (size_t)yb * nxt, 4 * nxt, amask);
+      if (nu > 0) {
+        warp_zero_chunks(Bm + (size_t)yb * nu, 4 * nu, amask);
+        warp_zero_chunks(Bp + (size_t)yb * nu, 4 * nu, amask);
       }
     }
     __syncwarp(amask);
@@ -505,6 +662,46 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       }
     }
     chk += y1 + double(Sy);
+  }
+  if constexpr (cross) {
+    // Eq. (12) cross-complementarity rows of the contact: phi_n, lambda^c, gamma, rho^c
+    const int yb = 6 * nb + 4 * B.contact;
+    const double fn_m = fma(0.5, cD[1], cL[1]), ga_m = fma(0.5, cD[2], cL[2]);  // tau-averages
+    const double Ilg = Il + Ig;
+    const double y1v[4] = {fma(sd, fn_m, xk[yb]), fma(sd, Ilg, xk[yb + 1]), fma(sd, ga_m, xk[yb + 2]),
+                           fma(sd, Ir, xk[yb + 3])};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      defect[yb + t] = y1v[t] - xk1[yb + t];
+      A[(size_t)(yb + t) * nxt + yb + t] = one;
+      chk += y1v[t];
+    }
+    TP* al = A + (size_t)(yb + 1) * nxt;
+    al[rvx] = sdT;
+    al[rth] = tg.Yl[0];
+    al[rom] = tg.Yl[1];
+    const TP Sl = TP(Ilg) + tg.Yl[2] + tg.Ylv[2];
+    S[yb] = TP(fn_m); S[yb + 1] = Sl; S[yb + 2] = TP(ga_m); S[yb + 3] = TP(Ir);
+    chk += double(Sl);
+    if (nu > 0) {
+      Bm[(size_t)yb * nu + cin + 1] = s_2; Bp[(size_t)yb * nu + cin + 1] = s_2;
+      Bm[(size_t)(yb + 2) * nu + cin + 2] = s_2; Bp[(size_t)(yb + 2) * nu + cin + 2] = s_2;
+      Bm[(size_t)(yb + 3) * nu + cin] = tg.Yrd[0]; Bp[(size_t)(yb + 3) * nu + cin] = tg.Yrd[1];
+      Bm[(size_t)(yb + 3) * nu + cin + 1] = tg.Yrd[2]; Bp[(size_t)(yb + 3) * nu + cin + 1] = tg.Yrd[3];
+      TP* bm = Bm + (size_t)(yb + 1) * nu;
+      TP* bp = Bp + (size_t)(yb + 1) * nu;
+      for (int i = 0; i < nin; ++i) {
+        const int q = B.idx[i];
+        const TP ax = TP(B.ax[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
+        TP vm = ax * tg.Ylv[0] + pc * tg.Yl[3] + qc * tg.Yl[4] + tc * tg.Yl[5];
+        TP vp = ax * tg.Ylv[1] + pc * tg.Yl[6] + qc * tg.Yl[7] + tc * tg.Yl[8];
+        const int d = q - cin;
+        if (d == 0) { vm += tg.Yld[0]; vp += tg.Yld[1]; }
+        else if (d == 2) { vm += tg.Yld[2]; vp += tg.Yld[3]; }
+        bm[q] = vm;
+        bp[q] = vp;
+      }
+    }
   }
   if (!finite_d(chk)) atomicOr(status, ST_NONFINITE);
 

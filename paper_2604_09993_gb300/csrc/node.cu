@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
     chk += g0 + g1 + g2;
     SM(Ly.wh + b) = fma(f2 - t2, M.iinv[b], vm[2]);
   }
-  for (int i = 0; i < nc; ++i) gk[2 * nq + i] = xp[2 * nq + i] - xm[2 * nq + i];
+  for (int a = 2 * nq; a < nxt; ++a) gk[a] = xp[a] - xm[a];  // auxiliary-state continuity
 
   // d/dv-: column c = -M e_c + C'^T K^-1 C' e_c, stored as row c (the block is symmetric)
   if (Gvm) {

@@ -155,7 +155,7 @@ def test_compact_argument_errors(env):
            "Bp": torch.empty((p.N, m.nnz_b), dtype=torch.float64, device=dev),
            "S": torch.empty((p.N, m.nxt), dtype=torch.float64, device=dev),
            "defect": torch.empty((p.N, m.nxt), dtype=torch.float64, device=dev),
-           "penalty": torch.empty((p.N, m.ny), dtype=torch.float64, device=dev)}
+           "penalty": torch.empty((p.N, m.nc), dtype=torch.float64, device=dev)}
     lib = api.load()
     ptr = lambda t: t.data_ptr()  # noqa: E731
     st = lib.ciscvx_discretize_compact(m.handle, p.N, p.n_sub, 0, 0, ptr(X), ptr(U), ptr(s),
@@ -230,7 +230,7 @@ def test_batch_compact_vs_dense_and_oracle(env, precision, tune):
         f = lambda a: np.asarray(a, dtype=np.float64)  # noqa: E731
         got = {"A": f(cA), "Bm": f(cBm), "Bp": f(cBp), "S": f(pc.unpack(hc["S"], "S", i, (N, nxt))),
                "defect": f(pc.unpack(hc["defect"], "defect", i, (N, nxt))),
-               "penalty": f(pc.unpack(hc["penalty"], "penalty", i, (N, m.ny)))}
+               "penalty": f(pc.unpack(hc["penalty"], "penalty", i, (N, m.nc)))}
         _check_vs_oracle(got, ref, pats[mi], nxt, nu, precision)
 
 

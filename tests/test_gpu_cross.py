@@ -1,0 +1,168 @@
+"""GPU parity of the full Eq. (12) auxiliary state (CISCVX_AUX_CROSS) against
+the FP64 oracle through the C ABI: single-instance and batched linearization,
+both precisions and both control layouts, mixed batches of the two auxiliary
+models, feasible inputs, and the entry points that return EUNSUPPORTED for it.
+Tolerances as for the default model (FP64 1e-10; FP32-Phi blocks 1e-4,
+defect and penalty 1e-10)."""
+import numpy as np
+import pytest
+
+from _util import TOL_FP32_PHI, TOL_FP64, block_err
+from paper_2604_09993_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PHI = ("A", "Bm", "Bp", "S")
+STATE = ("defect", "penalty")
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import oracle
+    from paper_2604_09993_gb300 import api, build
+    build.build()
+    oracle.build()
+    api.load()
+    return torch, oracle, api
+
+
+def _check(got, ref, precision):
+    tol = TOL_FP64 if precision == "fp64" else TOL_FP32_PHI
+    for k in PHI:
+        assert block_err(got[k], ref[k]) <= tol, (k, block_err(got[k], ref[k]))
+    for k in STATE:
+        assert block_err(got[k], ref[k]) <= TOL_FP64, (k, block_err(got[k], ref[k]))
+
+
+def _problem(name, seed, N, n_sub, feasible=False):
+    rng = np.random.default_rng(seed)
+    R = synth.with_cross_states(getattr(synth, name)(rng))
+    p = synth.draw_instance(R, rng, N, n_sub, q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15))
+    if feasible:
+        U = p.U.copy()
+        for i in range(R.nc):
+            c0 = 3 * R.nj + 3 * i
+            U[:, c0 + 1] = rng.uniform(1.0, 2.0, p.N + 1)
+            U[:, c0] = rng.uniform(-0.3, 0.3, p.N + 1) * R.contact_mu[i] * U[:, c0 + 1]
+            U[:, c0 + 2] = rng.uniform(0.1, 0.5, p.N + 1)
+        X = p.X.copy()
+        X[:, 1:3 * R.nb:3] += 3.0  # every link far above the ground
+        p = synth.Problem(R, p.N, p.n_sub, X, U, p.s, None, None)
+    return p
+
+
+def _single(env, p, precision, layout="node"):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    m = api.Model(p.robot)
+    assert (m.ny, m.nc) == (5 * p.robot.nc, p.robot.nc)
+    U = p.U if layout == "node" else p.U_interval()
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    out = api.discretize(m, t(p.X), t(U), t(p.s), p.n_sub, precision, layout)
+    api.sync_status(m)
+    got = {k: v.double().cpu().numpy() for k, v in out.items()}
+    ref = oracle.discretize(p.robot.as_dict(), p.X, U, p.s, p.n_sub, layout=layout)
+    return got, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("name,N,n_sub", [("hopper", 10, 4), ("biped", 45, 3), ("cheetah7", 50, 10)])
+def test_cross_single_matches_oracle(env, precision, name, N, n_sub):
+    got, ref = _single(env, _problem(name, 11, N, n_sub), precision)
+    _check(got, ref, precision)
+
+
+def test_cross_interval_layout(env):
+    p = _problem("biped", 12, 37, 5)
+    got, ref = _single(env, p, "fp64", layout="interval")
+    _check(got, ref, "fp64")
+
+
+def test_cross_feasible_inputs_leave_penalty_zero(env):
+    p = _problem("cheetah7", 13, 33, 4, feasible=True)
+    got, ref = _single(env, p, "fp64")
+    _check(got, ref, "fp64")
+    assert np.all(got["penalty"] == 0.0)
+    pen = slice(6 * p.robot.nb + 4 * p.robot.nc, p.robot.nxt)
+    assert not np.any(got["Bm"][:, pen]) and not np.any(got["S"][:, pen])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_cross_batch_mixed_models(env, precision):
+    """A batch holding both auxiliary models (and a robot without contacts)."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(14)
+    robots = [synth.hopper(rng), synth.with_cross_states(synth.biped(rng)),
+              synth.with_cross_states(synth.cheetah7(rng)), synth.cheetah7(rng)]
+    probs, midx = [], []
+    for _ in range(14):
+        mi = int(rng.integers(0, len(robots)))
+        probs.append(synth.draw_instance(robots[mi], rng, int(rng.integers(1, 50)), int(rng.choice([1, 3])),
+                                         q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15)))
+        midx.append(mi)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs], precision=precision)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X = t(plan.pack([p.X for p in probs], "X"))
+    U = t(plan.pack([p.U for p in probs], "U"))
+    s = t(plan.pack([p.s for p in probs], "s"))
+    out = plan.discretize(X, U, s)
+    plan.sync_status()
+    host = {k: v.double().cpu().numpy() for k, v in out.items()}
+    for i, p in enumerate(probs):
+        R = p.robot
+        N, nxt, nu, nc = p.N, R.nxt, R.nu, R.nc
+        got = {"A": plan.unpack(host["A"], "A", i, (N, nxt, nxt)),
+               "Bm": plan.unpack(host["Bm"], "B", i, (N, nxt, nu)),
+               "Bp": plan.unpack(host["Bp"], "B", i, (N, nxt, nu)),
+               "S": plan.unpack(host["S"], "S", i, (N, nxt)),
+               "defect": plan.unpack(host["defect"], "defect", i, (N, nxt)),
+               "penalty": plan.unpack(host["penalty"], "penalty", i, (N, nc))}
+        ref = oracle.discretize(R.as_dict(), p.X, p.U, p.s, p.n_sub)
+        _check(got, ref, precision)
+
+
+def test_cross_unsupported_entry_points(env):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("hopper", 15, 10, 4)
+    m = api.Model(p.robot)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X, U, s = t(p.X), t(p.U), t(p.s)
+    w = torch.zeros((p.N, m.nxt), dtype=torch.float64, device=dev)
+    rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
+    for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
+                 lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
+                 lambda: api.discretize_vjp(m, X, U, s, w, rho, p.n_sub, "fp64"),
+                 lambda: api.model_pattern(p.robot.as_dict()),
+                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
+        with pytest.raises(api.CiscvxError) as e:
+            call()
+        assert e.value.status == api.EUNSUPPORTED
+    plan = api.BatchPlan([m], [0], [p.N], [p.n_sub])
+    with pytest.raises(api.CiscvxError) as e:
+        plan.discretize_vjp(X, U, s, w, rho)
+    assert e.value.status == api.EUNSUPPORTED
+
+
+def test_cross_node_constraints(env):
+    """The node kernel's auxiliary-state continuity rows cover all 5 n_c states."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(16)
+    R = synth.with_cross_states(synth.cheetah7(rng)).as_dict()
+    m = api.Model(R)
+    n = 40
+    Xm = rng.uniform(-1, 1, (n, m.nxt))
+    Xp = Xm + 0.3 * rng.standard_normal((n, m.nxt))
+    Phi = rng.standard_normal((n, 2 * m.nc))
+    Gam = rng.uniform(0, 1, (n, m.nc))
+    e = np.full(m.nc, 0.4)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    out = api.node_linearize(m, t(Xp), t(Xm), t(Phi), t(Gam), 1e-3, e)
+    api.sync_status(m)
+    ref = oracle.node(R, Xp, Xm, Phi, Gam, 1e-3, e)
+    assert block_err(out["g"].cpu().numpy(), ref["g"]) <= TOL_FP64
+    assert block_err(out["theta"].cpu().numpy().reshape(n, -1), ref["theta"]) <= TOL_FP64

@@ -169,9 +169,9 @@ def test_sweep_nodes_full_size_sampled(env):
     assert n == 4096 * 401
     rng = np.random.default_rng(77)
     Xp = Xm + 0.1 * rng.standard_normal(Xm.shape)
-    Phi = rng.standard_normal((n, 2 * m.ny))
-    Gam = rng.uniform(0, 1.5, (n, m.ny))
-    e = np.full(m.ny, 0.3)
+    Phi = rng.standard_normal((n, 2 * m.nc))
+    Gam = rng.uniform(0, 1.5, (n, m.nc))
+    e = np.full(m.nc, 0.3)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     out = api.node_linearize(m, t(Xp), t(Xm), t(Phi), t(Gam), 1e-3, e)
     api.sync_status(m)
