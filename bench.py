@@ -524,6 +524,36 @@ def run_ours(args):
                  "nodes_per_gpu": n_nodes, "ms_per_call": tn / args.steps * 1e3}
         wl.node_free()
 
+    # the linearization of the same batch with the full Eq. (12) auxiliary state
+    # (four cross-complementarity states + one path-penalty state per contact)
+    cross = None
+    if spec["kind"] == "batch" and args.cross:
+        import dataclasses
+        wl.free(prec)
+        b = wl.batch
+        bx = dataclasses.replace(b, robots=[synth.with_cross_states(r) for r in b.robots])
+        mx = [api.Model(r) for r in bx.robots]
+        px = api.BatchPlan(mx, bx.model_idx, bx.Ns, bx.n_subs, precision=prec)
+        probs = (bx.instance(i) for i in range(len(bx)))
+        Xs, Us, ss = [], [], []
+        for pr in probs:
+            Xs.append(pr.X); Us.append(pr.U); ss.append(pr.s)
+        t_ = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+        Xx, Ux, sx = t_(px.pack(Xs, "X")), t_(px.pack(Us, "U")), t_(px.pack(ss, "s"))
+        del Xs, Us, ss
+        ox = px.alloc_outputs(dev)
+        px.autotune(Xx, Ux, sx, out=ox)
+        barrier()
+        tx = time_steps(torch, lambda: px.discretize(Xx, Ux, sx, out=ox), args.steps, args.warmup, stream)
+        barrier()
+        px.sync_status()
+        tx, = max_over_ranks([tx])
+        cross = {"metric": "linearized intervals/s (STM only; the VJP is not provided for this model)",
+                 "value": units * args.steps / tx, "unit": "intervals/s",
+                 "ms_per_step": tx / args.steps * 1e3, "n_y": mx[0].ny, "tune": px.tune()}
+        del ox, Xx, Ux, sx, px
+        torch.cuda.empty_cache()
+
     # the same step with compact outputs (structural nonzeros of A, B-, B+ only)
     compact = None
     if spec["kind"] == "batch" and not args.no_compact:
@@ -569,6 +599,7 @@ def run_ours(args):
         "e2e": e2e,
         "compact_outputs": compact,
         "node_constraints": nodes,
+        "aux_cross_model": cross,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -608,6 +639,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compact", action="store_true", help="skip the compact-output measurement")
     ap.add_argument("--no-nodes", action="store_true", help="skip the node-constraint measurement")
+    ap.add_argument("--cross", action="store_true",
+                    help="also time the linearization with the full Eq. (12) auxiliary state")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -15,6 +15,12 @@
 //    copy of the stage recursion that is re-anchored on the FP64 state at the
 //    start of every substep (a handful of conversions per substep instead of
 //    several per stage).
+// CROSS (a foot link of the Eq. (12) model): the contact's four
+// cross-complementarity states and its path-penalty state.  The lambda^c row
+// integrates v_x - omega (R rho)_y + gamma phi_t / sqrt(1 + phi_t^2) over the
+// stages; its tangents reuse the rotation tangents and the v_y channel's
+// unit-forcing tangents (v_x obeys the same equation), plus the tangent of
+// v_x with respect to s.
 #pragma once
 #include <type_traits>
 
