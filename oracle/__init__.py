@@ -20,5 +20,6 @@ from .oracle import (  # noqa: F401
     node,
     node_value,
     rhs,
+    tableau,
     vjp,
 )

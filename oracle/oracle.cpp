@@ -10,18 +10,22 @@
 //
 // What is computed, and where it comes from:
 //   rhs()       the augmented right-hand side (f, Omega): Newton-Euler per
-//               link in maximal coordinates, Sec. II-A Eq. (1); contact frame
-//               on flat ground y = 0 (normal (0,1), tangent (1,0)), Sec. II;
+//               link in maximal coordinates, Sec. II-A Eq. (1), with the joint
+//               reaction forces either as inputs or eliminated at the
+//               acceleration level (Eq. (3), eliminated_accel()); contact
+//               frame and signed distance on flat ground y = 0 or on the
+//               sinusoidal surface of Sec. VI-B (contact_frame());
 //               integral path-constraint penalty Omega = M^g sabs+(g), Sec. IV-A
 //               Eq. (12), with one auxiliary state per contact — or, for the
 //               aux model 1, the full Eq. (12): four cross-complementarity
 //               states per contact (phi_n, lambda^c, gamma, rho^c) before the
 //               path-penalty states, with contact inputs (phi_t, phi_n, gamma).
-//   rk4_foh()   the time-dilated augmented system d x~/d tau = s (f, Omega) on
+//   rk_foh()    the time-dilated augmented system d x~/d tau = s (f, Omega) on
 //               tau in [0,1], Sec. IV-B Eq. (14), integrated in integral form
 //               Eq. (15) with a first-order-hold control u(tau) =
-//               (1 - tau) u_L + tau u_R (Sec. VI: FOH), by n_sub classical
-//               fixed-step RK4 steps.
+//               (1 - tau) u_L + tau u_R (Sec. VI: FOH), by n_sub fixed steps
+//               of classical RK4 or of the Runge-Kutta-Fehlberg 4(5) pair
+//               (Sec. VI), given by their Butcher tableaux.
 //   interval()  Internal Numerical Differentiation (Sec. VI): the Jacobian of
 //               the discrete RK4 map is obtained by running the very same RK4
 //               arithmetic on forward-mode dual numbers seeded in
@@ -41,9 +45,11 @@
 //
 // Readings of points the paper leaves open (one auxiliary state per contact,
 // pseudo-Huber ramp h(z) = sqrt(1 + max(z,0)^2) - 1, joint reaction forces and
-// contact forces (lambda_n, lambda_t+, lambda_t-) as FOH inputs, N intervals
-// on N+1 nodes, classical RK4 instead of the paper's RKF tableau) are listed
-// in the project's design notes; this file follows them.
+// contact forces (lambda_n, lambda_t+, lambda_t-) as FOH inputs by default,
+// N intervals on N+1 nodes, classical RK4 by default, the RKF step advanced
+// with the fifth-order weights, the contact normal n = grad h^c / ||grad h^c||
+// off the surface) are listed in the project's design notes; this file
+// follows them.
 //
 // Build: g++ -O2 -std=c++17 -shared -fPIC -pthread oracle.cpp -o liboracle.so
 
@@ -173,6 +179,11 @@ typedef struct {
   int aux;                // 0: one path-penalty state per contact, forces (lambda_n, lambda_t+, lambda_t-);
                           // 1: Eq. (12): four cross-complementarity states + one path-penalty
                           //    state per contact, forces (phi_t, phi_n) and multiplier gamma
+  int jelim;              // 0: joint reaction forces are inputs; 1: eliminated at the
+                          //    acceleration level, Eq. (3) (inputs: joint torques and contact inputs)
+  int scheme;             // 0: classical RK4; 1: Runge-Kutta-Fehlberg 4(5), fifth-order weights
+  double terrain_amp;     // contact surface y = terrain_amp sin(terrain_k x) (0: flat ground y = 0)
+  double terrain_k;
 } OracleModel;
 }
 
@@ -182,7 +193,7 @@ int nx_of(const OracleModel& M) { return 6 * M.nb; }
 int nxt_of(const OracleModel& M) { return 6 * M.nb + (M.aux ? 5 : 1) * M.nc; }
 // first path-penalty state (the states Eq. (13) bounds)
 int pen_of(const OracleModel& M) { return 6 * M.nb + (M.aux ? 4 * M.nc : 0); }
-int nu_of(const OracleModel& M) { return 3 * M.nj + 3 * M.nc; }
+int nu_of(const OracleModel& M) { return (M.jelim ? 1 : 3) * M.nj + 3 * M.nc; }
 
 // World-frame lever arm r = R(theta) rho, R = [[cos, -sin], [sin, cos]].
 template <class T>
@@ -196,29 +207,146 @@ void lever_arm(const T& theta, const double* rho, T& rx, T& ry) {
 template <class T>
 T cross2(const T& rx, const T& ry, const T& fx, const T& fy) { return rx * fy - ry * fx; }
 
+// Solves the dense system K x = r (n x n, row-major, overwritten) by Gaussian
+// elimination with partial pivoting on the values.
+template <class T> void dense_solve(int n, std::vector<T>& K, std::vector<T>& r) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(value(K[i * n + c])) > std::fabs(value(K[piv * n + c]))) piv = i;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) std::swap(K[c * n + j], K[piv * n + j]);
+      std::swap(r[c], r[piv]);
+    }
+    for (int i = c + 1; i < n; ++i) {
+      const T f = K[i * n + c] / K[c * n + c];
+      for (int j = c; j < n; ++j) K[i * n + j] = K[i * n + j] - f * K[c * n + j];
+      r[i] = r[i] - f * r[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    T acc = r[c];
+    for (int j = c + 1; j < n; ++j) acc = acc - K[c * n + j] * r[j];
+    r[c] = acc / K[c * n + c];
+  }
+}
+
+// Contact surface and contact frame at a world point (p_x, p_y) (Sec. II-A;
+// the sinusoidal surface of Sec. VI-B).  The surface is the zero set of
+// h^c(p) = p_y - a sin(k p_x) (a = 0: flat ground y = 0).  The signed distance
+// is approximated by h^c / ||grad h^c|| (Sec. VI-B), the unit normal is
+// n = grad h^c / ||grad h^c|| (grad phi on the surface), and the tangent
+// t = (n_y, -n_x) completes the right-handed frame R_c = [t n].
+template <class T>
+struct Frame {
+  T phi, tx, ty, nx, ny;
+};
+
+template <class T>
+Frame<T> contact_frame(const OracleModel& M, const T& px, const T& py) {
+  Frame<T> f;
+  if (M.terrain_amp == 0.0) {
+    f.phi = py;
+    f.tx = T(1.0); f.ty = T(0.0);
+    f.nx = T(0.0); f.ny = T(1.0);
+    return f;
+  }
+  const double a = M.terrain_amp, k = M.terrain_k;
+  const T hc = py - a * sin(k * px);
+  const T gx = -(a * k) * cos(k * px);  // dh^c/dp_x; dh^c/dp_y = 1
+  const T inv = 1.0 / sqrt(1.0 + gx * gx);
+  f.phi = hc * inv;
+  f.nx = gx * inv;
+  f.ny = inv;
+  f.tx = f.ny;
+  f.ty = -f.nx;
+  return f;
+}
+
+// Generalized accelerations with the joint reaction forces eliminated at the
+// acceleration level (Sec. II-A, Eq. (3)).  F = (F_x, F_y, torque) per link
+// holds every other generalized force.  The joint constraints
+// C_j = p_c + R_c rho_c - p_p - R_p rho_p = 0 differentiated twice give
+// grad C v' + (v^T Hess C_j v)_j = 0, and with M v' = F + grad C^T lambda the
+// pair (v', lambda) solves
+//   [ M        -grad C^T ] [ v'     ]   [ F                      ]
+//   [ grad C    0        ] [ lambda ] = [ -(v^T Hess C_j v)_j    ],
+// solved here densely.  The only second derivative of C_j is
+// d^2 (R rho) / d theta^2 = -R rho, so v^T Hess C_j v = -omega_c^2 r_c + omega_p^2 r_p.
+template <class T>
+std::vector<T> eliminated_accel(const OracleModel& M, const T* xt, const std::vector<T>& Fx,
+                                const std::vector<T>& Fy, const std::vector<T>& Tq) {
+  const int nb = M.nb, nj = M.nj, nq = 3 * nb, n = nq + 2 * nj;
+  std::vector<T> K((size_t)n * n, T(0.0)), r(n, T(0.0));
+  for (int b = 0; b < nb; ++b) {
+    K[(size_t)(3 * b) * n + 3 * b] = T(M.mass[b]);
+    K[(size_t)(3 * b + 1) * n + 3 * b + 1] = T(M.mass[b]);
+    K[(size_t)(3 * b + 2) * n + 3 * b + 2] = T(M.inertia[b]);
+    r[3 * b] = Fx[b];
+    r[3 * b + 1] = Fy[b];
+    r[3 * b + 2] = Tq[b];
+  }
+  for (int j = 0; j < nj; ++j) {
+    const int c = M.jchild[j], p = M.jparent[j];
+    T rcx, rcy, rpx, rpy;
+    lever_arm(xt[3 * c + 2], M.jrho_c + 2 * j, rcx, rcy);
+    lever_arm(xt[3 * p + 2], M.jrho_p + 2 * j, rpx, rpy);
+    // grad C_j: +[I, d(R rho_c)/d theta] on the child, -[I, d(R rho_p)/d theta]
+    // on the parent, with d(R rho)/d theta = (-r_y, r_x)
+    const int row = nq + 2 * j;
+    struct E { int r, c; T v; };
+    const E ent[8] = {{row, 3 * c, T(1.0)},         {row, 3 * c + 2, -rcy},
+                      {row + 1, 3 * c + 1, T(1.0)}, {row + 1, 3 * c + 2, rcx},
+                      {row, 3 * p, T(-1.0)},        {row, 3 * p + 2, rpy},
+                      {row + 1, 3 * p + 1, T(-1.0)}, {row + 1, 3 * p + 2, -rpx}};
+    for (const E& e : ent) {
+      K[(size_t)e.r * n + e.c] = K[(size_t)e.r * n + e.c] + e.v;  // grad C
+      K[(size_t)e.c * n + e.r] = K[(size_t)e.c * n + e.r] - e.v;  // -grad C^T
+    }
+    const T& wc = xt[3 * nb + 3 * c + 2];
+    const T& wp = xt[3 * nb + 3 * p + 2];
+    r[row] = wc * wc * rcx - wp * wp * rpx;
+    r[row + 1] = wc * wc * rcy - wp * wp * rpy;
+  }
+  dense_solve(n, K, r);
+  r.resize(nq);
+  return r;
+}
+
 // Augmented right-hand side (f(x,u), Omega(x,u)) — NOT yet multiplied by s.
-// State x~ = (q_1..q_nb, v_1..v_nb, y_1..y_nc) with q_b = (p_x, p_y, theta),
-// v_b = (v_x, v_y, omega).  Input u = (tau_1..tau_nj, lambda_1x, lambda_1y,
-// ..., lambda_njx, lambda_njy, [lambda_n, lambda_t+, lambda_t-] per contact).
+// State x~ = (q_1..q_nb, v_1..v_nb, y) with q_b = (p_x, p_y, theta),
+// v_b = (v_x, v_y, omega).  Input u = (tau_1..tau_nj, then, unless the joint
+// reaction forces are eliminated, lambda_1x, lambda_1y, ..., lambda_njx,
+// lambda_njy, then three contact inputs per contact).
 //
 // Eq. (1): q' = v; M v' = W + J_c^T R_c phi_c + grad C^T lambda.  Here M is
 // diag(m, m, I) per link, W holds gravity and the joint torques, the joint
 // reaction force lambda_j acts +lambda_j on the child at its anchor and
 // -lambda_j on the parent at its anchor (grad C^T lambda for the revolute
 // constraint C = p_c + R_c rho_c - p_p - R_p rho_p), the joint torque tau_j
-// acts +tau_j on the child and -tau_j on the parent, and contact force
-// (lambda_t+ - lambda_t-, lambda_n) acts at the contact point.
+// acts +tau_j on the child and -tau_j on the parent, and the contact force
+// with contact-frame components (tangential, normal) acts at the contact
+// point as t tangential + n normal (R_c phi_c; on flat ground t = (1, 0),
+// n = (0, 1)).  With jelim the reaction forces come from Eq. (3) instead
+// (eliminated_accel).
 // Eq. (12): Omega_i = sum over the contact's path constraints g <= 0 of
 // h(g), with g = (-lambda_n, -lambda_t+, -lambda_t-, -phi_i(q),
-// lambda_t+ + lambda_t- - mu lambda_n), phi_i the signed distance to y = 0.
+// lambda_t+ + lambda_t- - mu lambda_n), phi_i the signed distance of the
+// contact point to the contact surface.
 template <class T>
 void rhs(const OracleModel& M, const T* xt, const T* u, T* out) {
   const int nb = M.nb, nj = M.nj, nc = M.nc;
+  const int ci = (M.jelim ? 1 : 3) * nj;  // first contact input
   std::vector<T> Fx(nb, T(0.0)), Fy(nb, T(0.0)), Tq(nb, T(0.0));
   for (int b = 0; b < nb; ++b) Fy[b] = T(-M.mass[b] * M.g);
   for (int j = 0; j < nj; ++j) {
     const int p = M.jparent[j], c = M.jchild[j];
     const T& tau = u[j];
+    if (M.jelim) {
+      Tq[c] = Tq[c] + tau;
+      Tq[p] = Tq[p] - tau;
+      continue;
+    }
     const T& lx = u[nj + 2 * j];
     const T& ly = u[nj + 2 * j + 1];
     T rcx, rcy, rpx, rpy;
@@ -235,32 +363,34 @@ void rhs(const OracleModel& M, const T* xt, const T* u, T* out) {
     const int b = M.cbody[i];
     T rx, ry;
     lever_arm(xt[3 * b + 2], M.crho + 2 * i, rx, ry);
-    const T phi = xt[3 * b + 1] + ry;  // signed distance of the contact point to y = 0
+    // signed distance and contact frame at the contact point p + r
+    const Frame<T> fr = contact_frame(M, xt[3 * b] + rx, xt[3 * b + 1] + ry);
+    const T& phi = fr.phi;
+    T fx, fy;
     if (M.aux == 0) {
-      const T& ln = u[3 * nj + 3 * i];
-      const T& ltp = u[3 * nj + 3 * i + 1];
-      const T& ltm = u[3 * nj + 3 * i + 2];
-      const T fx = ltp - ltm;  // tangent (1, 0)
-      const T fy = ln;         // normal (0, 1)
-      Fx[b] = Fx[b] + fx;
-      Fy[b] = Fy[b] + fy;
-      Tq[b] = Tq[b] + cross2(rx, ry, fx, fy);
+      const T& ln = u[ci + 3 * i];
+      const T& ltp = u[ci + 3 * i + 1];
+      const T& ltm = u[ci + 3 * i + 2];
+      const T ft = ltp - ltm;  // tangential component
+      fx = fr.tx * ft + fr.nx * ln;
+      fy = fr.ty * ft + fr.ny * ln;
       out[6 * nb + i] = sabs_plus(-ln) + sabs_plus(-ltp) + sabs_plus(-ltm) + sabs_plus(-phi) +
                         sabs_plus(ltp + ltm - M.cmu[i] * ln);
     } else {
-      // Eq. (12): contact-frame force (phi_t, phi_n) (the world force on flat
-      // ground) and multiplier gamma; the auxiliary states integrate phi_n,
-      // lambda^c = t^T J_c v + gamma d||phi_t||~/dphi_t (Sec. II-A), gamma and
-      // rho^c = |mu phi_n|~ - ||phi_t||~, then the path penalty of the
-      // contact's nonnegativity constraints (phi_n, phi, gamma, rho^c >= 0).
-      const T& ft = u[3 * nj + 3 * i];
-      const T& fn = u[3 * nj + 3 * i + 1];
-      const T& gam = u[3 * nj + 3 * i + 2];
-      Fx[b] = Fx[b] + ft;
-      Fy[b] = Fy[b] + fn;
-      Tq[b] = Tq[b] + cross2(rx, ry, ft, fn);
-      // tangential velocity of the contact point: x-component of p' + omega x r
-      const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;
+      // Eq. (12): contact-frame force (phi_t, phi_n) and multiplier gamma; the
+      // auxiliary states integrate phi_n, lambda^c = t^T J_c v + gamma
+      // d||phi_t||~/dphi_t (Sec. II-A), gamma and rho^c = |mu phi_n|~ -
+      // ||phi_t||~, then the path penalty of the contact's nonnegativity
+      // constraints (phi_n, phi, gamma, rho^c >= 0).
+      const T& ft = u[ci + 3 * i];
+      const T& fn = u[ci + 3 * i + 1];
+      const T& gam = u[ci + 3 * i + 2];
+      fx = fr.tx * ft + fr.nx * fn;
+      fy = fr.ty * ft + fr.ny * fn;
+      // contact-point velocity p' + omega x r = (v_x - omega r_y, v_y + omega r_x)
+      const T vcx = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;
+      const T vcy = xt[3 * nb + 3 * b + 1] + xt[3 * nb + 3 * b + 2] * rx;
+      const T vt = fr.tx * vcx + fr.ty * vcy;  // tangential velocity t^T J_c v
       const T lam_c = vt + gam * (ft / sqrt(1.0 + ft * ft));
       const T rho_c = smooth_abs(M.cmu[i] * fn) - smooth_abs(ft);
       out[6 * nb + 4 * i] = fn;
@@ -270,45 +400,91 @@ void rhs(const OracleModel& M, const T* xt, const T* u, T* out) {
       out[6 * nb + 4 * nc + i] = sabs_plus(-fn) + sabs_plus(-phi) + sabs_plus(-gam) +
                                  sabs_plus(-rho_c);
     }
+    Fx[b] = Fx[b] + fx;
+    Fy[b] = Fy[b] + fy;
+    Tq[b] = Tq[b] + cross2(rx, ry, fx, fy);
   }
+  std::vector<T> vd;
+  if (M.jelim) vd = eliminated_accel(M, xt, Fx, Fy, Tq);
   for (int b = 0; b < nb; ++b) {
     for (int k = 0; k < 3; ++k) out[3 * b + k] = xt[3 * nb + 3 * b + k];
+    if (M.jelim) {
+      for (int k = 0; k < 3; ++k) out[3 * nb + 3 * b + k] = vd[3 * b + k];
+      continue;
+    }
     out[3 * nb + 3 * b + 0] = Fx[b] / M.mass[b];
     out[3 * nb + 3 * b + 1] = Fy[b] / M.mass[b];
     out[3 * nb + 3 * b + 2] = Tq[b] / M.inertia[b];
   }
 }
 
-// n_sub classical RK4 steps of d x/d tau = s F(x, u(tau)) on tau in [0,1],
-// u(tau) = (1 - tau) u_L + tau u_R (first-order hold), Eqs. (14)-(15).
+// Butcher tableaux of the explicit fixed-step schemes.  Classical RK4 is the
+// default; the paper integrates with a Runge-Kutta-Fehlberg method (Sec. VI):
+// Fehlberg's six-stage 4(5) pair, advanced with its fifth-order weights (a
+// fixed step has no use for the embedded fourth-order error estimate).
+struct Tableau {
+  int s;           // stages
+  double c[6];     // stage times
+  double a[6][6];  // stage coupling (strictly lower triangular)
+  double b[6];     // weights
+};
+
+const Tableau kRK4 = {4,
+                      {0.0, 0.5, 0.5, 1.0},
+                      {{0.0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 1.0}},
+                      {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0}};
+
+const Tableau kRKF45 = {6,
+                        {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0},
+                        {{0.0},
+                         {1.0 / 4.0},
+                         {3.0 / 32.0, 9.0 / 32.0},
+                         {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0},
+                         {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0},
+                         {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}},
+                        {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0,
+                         2.0 / 55.0}};
+
+const Tableau& tableau_of(int scheme) { return scheme == 1 ? kRKF45 : kRK4; }
+
+// n_sub fixed steps of the explicit Runge-Kutta scheme `tb` applied to
+// d x/d tau = s F(x, u(tau)) on tau in [0,1], u(tau) = (1 - tau) u_L + tau u_R
+// (first-order hold), Eqs. (14)-(15):
+//   k_j = s F(x + h sum_{l<j} a_jl k_l, u((i + c_j) h)),  x <- x + h sum_j b_j k_j.
 template <class T, class RHS>
-void rk4_foh(const RHS& F, int nxt, int nu, const T* x0, const T* uL, const T* uR, const T& s,
-             int nsub, T* x1) {
-  static const double c[4] = {0.0, 0.5, 0.5, 1.0};
-  static const double w[4] = {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0};
+void rk_foh(const RHS& F, const Tableau& tb, int nxt, int nu, const T* x0, const T* uL,
+            const T* uR, const T& s, int nsub, T* x1) {
   const double h = 1.0 / nsub;
-  std::vector<T> x(x0, x0 + nxt), xs(nxt), k(nxt), acc(nxt), u(nu), fv(nxt);
+  std::vector<T> x(x0, x0 + nxt), xs(nxt), acc(nxt), u(nu), fv(nxt);
+  std::vector<std::vector<T>> k(tb.s, std::vector<T>(nxt));
   for (int i = 0; i < nsub; ++i) {
-    for (int r = 0; r < nxt; ++r) acc[r] = T(0.0);
-    for (int j = 0; j < 4; ++j) {
-      const double tau = (i + c[j]) * h;
-      for (int r = 0; r < nxt; ++r) xs[r] = (j == 0) ? x[r] : x[r] + (c[j] * h) * k[r];
+    for (int j = 0; j < tb.s; ++j) {
+      const double tau = (i + tb.c[j]) * h;
+      for (int r = 0; r < nxt; ++r) {
+        T v = x[r];
+        for (int l = 0; l < j; ++l)
+          if (tb.a[j][l] != 0.0) v = v + (tb.a[j][l] * h) * k[l][r];
+        xs[r] = v;
+      }
       for (int q = 0; q < nu; ++q) u[q] = (1.0 - tau) * uL[q] + tau * uR[q];
       F(xs.data(), u.data(), fv.data());
-      for (int r = 0; r < nxt; ++r) k[r] = s * fv[r];
-      for (int r = 0; r < nxt; ++r) acc[r] = acc[r] + w[j] * k[r];
+      for (int r = 0; r < nxt; ++r) k[j][r] = s * fv[r];
     }
-    for (int r = 0; r < nxt; ++r) x[r] = x[r] + h * acc[r];
+    for (int r = 0; r < nxt; ++r) {
+      acc[r] = T(0.0);
+      for (int j = 0; j < tb.s; ++j) acc[r] = acc[r] + tb.b[j] * k[j][r];
+      x[r] = x[r] + h * acc[r];
+    }
   }
   for (int r = 0; r < nxt; ++r) x1[r] = x[r];
 }
 
-// IND on one interval: seed duals in (x~_k, u_L, u_R, s), run rk4_foh, read
+// IND on one interval: seed duals in (x~_k, u_L, u_R, s), run rk_foh, read
 // the tangents.  Direction order: x~ (nxt), u_L (nu), u_R (nu), s (1).
 template <class RHSD>
-int ind_interval(const RHSD& F, int nxt, int nu, int nsub, const double* x0, const double* uL,
-                 const double* uR, double s, double* x1, double* A, double* Bm, double* Bp,
-                 double* S) {
+int ind_interval(const RHSD& F, const Tableau& tb, int nxt, int nu, int nsub, const double* x0,
+                 const double* uL, const double* uR, double s, double* x1, double* A, double* Bm,
+                 double* Bp, double* S) {
   const int C = nxt + 2 * nu + 1;
   if (C > MAXC) return 1;
   g_nd = C;
@@ -319,7 +495,7 @@ int ind_interval(const RHSD& F, int nxt, int nu, int nsub, const double* x0, con
     UR[q] = Dual(uR[q]); UR[q].d[nxt + nu + q] = 1.0;
   }
   Dual Sd(s); Sd.d[C - 1] = 1.0;
-  rk4_foh<Dual>(F, nxt, nu, X0.data(), UL.data(), UR.data(), Sd, nsub, X1.data());
+  rk_foh<Dual>(F, tb, nxt, nu, X0.data(), UL.data(), UR.data(), Sd, nsub, X1.data());
   for (int r = 0; r < nxt; ++r) {
     if (x1) x1[r] = X1[r].v;
     if (A) for (int c = 0; c < nxt; ++c) A[r * nxt + c] = X1[r].d[c];
@@ -332,6 +508,8 @@ int ind_interval(const RHSD& F, int nxt, int nu, int nsub, const double* x0, con
 
 int model_ok(const OracleModel* M) {
   if (!M || M->nb < 1 || M->nj < 0 || M->nc < 0 || (M->aux != 0 && M->aux != 1)) return 0;
+  if ((M->jelim != 0 && M->jelim != 1) || (M->scheme != 0 && M->scheme != 1)) return 0;
+  if (!std::isfinite(M->terrain_amp) || !std::isfinite(M->terrain_k)) return 0;
   for (int j = 0; j < M->nj; ++j)
     if (M->jparent[j] < 0 || M->jparent[j] >= M->nb || M->jchild[j] < 0 || M->jchild[j] >= M->nb)
       return 0;
@@ -384,7 +562,7 @@ int oracle_flow(const OracleModel* M, int nsub, const double* x0, const double* 
                 const double* uR, double s, double* x1) {
   if (!model_ok(M) || nsub < 1) return 1;
   auto F = [M](const double* x, const double* u, double* o) { rhs<double>(*M, x, u, o); };
-  rk4_foh<double>(F, nxt_of(*M), nu_of(*M), x0, uL, uR, s, nsub, x1);
+  rk_foh<double>(F, tableau_of(M->scheme), nxt_of(*M), nu_of(*M), x0, uL, uR, s, nsub, x1);
   return 0;
 }
 
@@ -394,7 +572,8 @@ int oracle_interval(const OracleModel* M, int nsub, const double* x0, const doub
                     double* S) {
   if (!model_ok(M) || nsub < 1) return 1;
   auto F = [M](const Dual* x, const Dual* u, Dual* o) { rhs<Dual>(*M, x, u, o); };
-  return ind_interval(F, nxt_of(*M), nu_of(*M), nsub, x0, uL, uR, s, x1, A, Bm, Bp, S);
+  return ind_interval(F, tableau_of(M->scheme), nxt_of(*M), nu_of(*M), nsub, x0, uL, uR, s, x1,
+                      A, Bm, Bp, S);
 }
 
 // All N intervals of a multiple-shooting grid (independently, Eq. (17b)).
@@ -478,13 +657,13 @@ int oracle_vjp(const OracleModel* M, int N, int nsub, int layout, const double* 
   return 0;
 }
 
-// The same integrator and IND on a linear right-hand side F(x,u) = Ac x + Bc u
-// (Ac [n][n], Bc [n][m], row-major).  Used only to pin rk4_foh/IND against
-// closed forms.
+// The same integrator (scheme 0: RK4, 1: RKF45) and IND on a linear
+// right-hand side F(x,u) = Ac x + Bc u (Ac [n][n], Bc [n][m], row-major).
+// Used only to pin rk_foh/IND against closed forms.
 int oracle_linear_interval(int n, int m, const double* Ac, const double* Bc, int nsub,
                            const double* x0, const double* uL, const double* uR, double s,
-                           double* x1, double* A, double* Bm, double* Bp, double* S) {
-  if (n < 1 || m < 0 || nsub < 1 || n + 2 * m + 1 > MAXC) return 1;
+                           double* x1, double* A, double* Bm, double* Bp, double* S, int scheme) {
+  if (n < 1 || m < 0 || nsub < 1 || n + 2 * m + 1 > MAXC || scheme < 0 || scheme > 1) return 1;
   auto F = [=](const Dual* x, const Dual* u, Dual* o) {
     for (int r = 0; r < n; ++r) {
       Dual acc(0.0);
@@ -493,7 +672,20 @@ int oracle_linear_interval(int n, int m, const double* Ac, const double* Bc, int
       o[r] = acc;
     }
   };
-  return ind_interval(F, n, m, nsub, x0, uL, uR, s, x1, A, Bm, Bp, S);
+  return ind_interval(F, tableau_of(scheme), n, m, nsub, x0, uL, uR, s, x1, A, Bm, Bp, S);
+}
+
+// The Butcher tableau of a scheme: stages, c [6], a [6][6] row-major, b [6].
+int oracle_tableau(int scheme, int* stages, double* c, double* a, double* b) {
+  if (scheme < 0 || scheme > 1) return 1;
+  const Tableau& tb = tableau_of(scheme);
+  *stages = tb.s;
+  for (int i = 0; i < 6; ++i) {
+    c[i] = tb.c[i];
+    b[i] = tb.b[i];
+    for (int j = 0; j < 6; ++j) a[6 * i + j] = tb.a[i][j];
+  }
+  return 0;
 }
 
 }  // extern "C"
@@ -508,30 +700,6 @@ namespace {
 // Fischer-Burmeister relaxation, Eq. (16): FB^delta(a, b) = a + b - sqrt(a^2 + b^2 + delta).
 template <class T> T fischer_burmeister(const T& a, const T& b, double delta) {
   return a + b - sqrt(a * a + b * b + delta);
-}
-
-// Solves the dense system K x = r (n x n, row-major, overwritten) by Gaussian
-// elimination with partial pivoting on the values.
-template <class T> void dense_solve(int n, std::vector<T>& K, std::vector<T>& r) {
-  for (int c = 0; c < n; ++c) {
-    int piv = c;
-    for (int i = c + 1; i < n; ++i)
-      if (std::fabs(value(K[i * n + c])) > std::fabs(value(K[piv * n + c]))) piv = i;
-    if (piv != c) {
-      for (int j = 0; j < n; ++j) std::swap(K[c * n + j], K[piv * n + j]);
-      std::swap(r[c], r[piv]);
-    }
-    for (int i = c + 1; i < n; ++i) {
-      const T f = K[i * n + c] / K[c * n + c];
-      for (int j = c; j < n; ++j) K[i * n + j] = K[i * n + j] - f * K[c * n + j];
-      r[i] = r[i] - f * r[c];
-    }
-  }
-  for (int c = n - 1; c >= 0; --c) {
-    T acc = r[c];
-    for (int j = c + 1; j < n; ++j) acc = acc - K[c * n + j] * r[j];
-    r[c] = acc / K[c * n + c];
-  }
 }
 
 // G~(x~+, x~-, Phi) and Theta^delta(x+, x-, Phi, Gamma) at one node.
@@ -586,16 +754,21 @@ void node_eval(const OracleModel& M, const T* xp, const T* xm, const T* Phi, con
     G[(2 * j) * nq + 3 * p + 2] = G[(2 * j) * nq + 3 * p + 2] + rpy;
     G[(2 * j + 1) * nq + 3 * p + 2] = G[(2 * j + 1) * nq + 3 * p + 2] - rpx;
   }
-  // J_c^T R_c Phi as a generalized impulse (nq), and the contact lever arms.
+  // J_c^T R_c Phi as a generalized impulse (nq), the contact lever arms and
+  // the contact frames (at the pre-impact contact points).
   std::vector<T> Jphi(nq, T(0.0)), crx(nc), cry(nc);
+  std::vector<Frame<T>> fr(nc);
   for (int i = 0; i < nc; ++i) {
     const int b = M.cbody[i];
     lever_arm(qm[3 * b + 2], M.crho + 2 * i, crx[i], cry[i]);
+    fr[i] = contact_frame(M, qm[3 * b] + crx[i], qm[3 * b + 1] + cry[i]);
     const T& pt = Phi[2 * i];
     const T& pn = Phi[2 * i + 1];
-    Jphi[3 * b] = Jphi[3 * b] + pt;
-    Jphi[3 * b + 1] = Jphi[3 * b + 1] + pn;
-    Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], pt, pn);
+    const T ix = fr[i].tx * pt + fr[i].nx * pn;  // world impulse R_c Phi
+    const T iy = fr[i].ty * pt + fr[i].ny * pn;
+    Jphi[3 * b] = Jphi[3 * b] + ix;
+    Jphi[3 * b + 1] = Jphi[3 * b + 1] + iy;
+    Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], ix, iy);
   }
   // Lambda = -K^-1 grad C w.
   std::vector<T> w(nq);
@@ -626,11 +799,16 @@ void node_eval(const OracleModel& M, const T* xp, const T* xm, const T* Phi, con
     const int b = M.cbody[i];
     const T& pt = Phi[2 * i];
     const T& pn = Phi[2 * i + 1];
-    const T phi = qm[3 * b + 1] + cry[i];
+    const T& phi = fr[i].phi;
     // contact-point velocity p' + omega x r = (v_x - omega r_y, v_y + omega r_x)
-    const T vtp = vp[3 * b] - vp[3 * b + 2] * cry[i];
-    const T vnp = vp[3 * b + 1] + vp[3 * b + 2] * crx[i];
-    const T vnm = vm[3 * b + 1] + vm[3 * b + 2] * crx[i];
+    // after (p) and before (m) the impact, in the contact frame
+    const T vxp = vp[3 * b] - vp[3 * b + 2] * cry[i];
+    const T vyp = vp[3 * b + 1] + vp[3 * b + 2] * crx[i];
+    const T vxm = vm[3 * b] - vm[3 * b + 2] * cry[i];
+    const T vym = vm[3 * b + 1] + vm[3 * b + 2] * crx[i];
+    const T vtp = fr[i].tx * vxp + fr[i].ty * vyp;
+    const T vnp = fr[i].nx * vxp + fr[i].ny * vyp;
+    const T vnm = fr[i].nx * vxm + fr[i].ny * vym;
     const T cn = vnp + e[i] * vnm;
     const T lc = vtp + Gam[i] * (pt / sqrt(1.0 + pt * pt));
     const T rho = smooth_abs(M.cmu[i] * pn) - smooth_abs(pt);

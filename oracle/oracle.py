@@ -27,6 +27,10 @@ class _CModel(ctypes.Structure):
         ("cbody", _ip), ("crho", _dp), ("cmu", _dp),
         ("g", ctypes.c_double),
         ("aux", ctypes.c_int),
+        ("jelim", ctypes.c_int),
+        ("scheme", ctypes.c_int),
+        ("terrain_amp", ctypes.c_double),
+        ("terrain_k", ctypes.c_double),
     ]
 
 
@@ -67,14 +71,15 @@ def _load():
                                        ctypes.c_int]
             lib.oracle_linear_interval.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp,
                                                    ctypes.c_int, _dp, _dp, _dp, ctypes.c_double,
-                                                   _dp, _dp, _dp, _dp, _dp]
+                                                   _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+            lib.oracle_tableau.argtypes = [ctypes.c_int, _ip, _dp, _dp, _dp]
             lib.oracle_node.argtypes = [ctypes.POINTER(_CModel), ctypes.c_int, _dp, _dp, _dp, _dp,
                                         ctypes.c_double, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
             lib.oracle_node_value.argtypes = [ctypes.POINTER(_CModel), _dp, _dp, _dp, _dp,
                                               ctypes.c_double, _dp, _dp, _dp]
             for f in ("oracle_dims", "oracle_rhs", "oracle_flow", "oracle_interval",
                       "oracle_discretize", "oracle_vjp", "oracle_linear_interval", "oracle_node",
-                      "oracle_node_value"):
+                      "oracle_node_value", "oracle_tableau"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -101,7 +106,10 @@ class OracleModel:
     ``joint_rho_parent`` / ``joint_rho_child`` [nj, 2], ``contact_body`` [nc],
     ``contact_rho`` [nc, 2], ``contact_mu`` [nc], ``gravity`` and optionally
     ``aux_model`` (0: one path-penalty state per contact; 1: the full Eq. (12)
-    auxiliary state with contact inputs (phi_t, phi_n, gamma)).
+    auxiliary state with contact inputs (phi_t, phi_n, gamma)),
+    ``joint_forces`` (0: joint reaction forces are inputs; 1: eliminated by
+    Eq. (3)), ``scheme`` (0: RK4; 1: RKF45) and ``terrain`` = (amplitude,
+    wavenumber) of the contact surface y = a sin(k x) (default flat).
     """
 
     def __init__(self, robot):
@@ -123,15 +131,21 @@ class OracleModel:
         for key in list(k):
             if k[key].size == 0:
                 k[key] = np.zeros(2, dtype=k[key].dtype)
-        try:
-            aux = int(get("aux_model"))
-        except (KeyError, AttributeError):
-            aux = 0
+        def opt(key, default):
+            try:
+                return get(key)
+            except (KeyError, AttributeError):
+                return default
+        aux = int(opt("aux_model", 0))
+        jelim = int(opt("joint_forces", 0))
+        scheme = int(opt("scheme", 0))
+        ta, tk = (float(v) for v in opt("terrain", (0.0, 0.0)))
         self._c = _CModel(nb, nj, nc, _d(k["mass"]), _d(k["inertia"]),
                           k["jparent"].ctypes.data_as(_ip), k["jchild"].ctypes.data_as(_ip),
                           _d(k["jrho_p"]), _d(k["jrho_c"]), k["cbody"].ctypes.data_as(_ip),
-                          _d(k["crho"]), _d(k["cmu"]), float(get("gravity")), aux)
-        self.aux = aux
+                          _d(k["crho"]), _d(k["cmu"]), float(get("gravity")), aux, jelim, scheme,
+                          ta, tk)
+        self.aux, self.jelim, self.scheme, self.terrain = aux, jelim, scheme, (ta, tk)
         self.nb, self.nj, self.nc = nb, nj, nc
         self.nxt, self.nu = dims(self)
         self.nx = 6 * nb
@@ -222,8 +236,8 @@ def vjp(model, X, U, s, w, rho, n_sub, layout="node", threads=0):
     return gX, gU, gs, L.value
 
 
-def linear_interval(Ac, Bc, n_sub, x0, uL, uR, s):
-    """Integrator + IND on F = Ac x + Bc u; returns (x1, A, Bm, Bp, S)."""
+def linear_interval(Ac, Bc, n_sub, x0, uL, uR, s, scheme=0):
+    """Integrator (scheme 0: RK4, 1: RKF45) + IND on F = Ac x + Bc u; returns (x1, A, Bm, Bp, S)."""
     Ac, Bc = _f64(Ac), _f64(Bc)
     n, mm = Ac.shape[0], Bc.shape[1]
     x0, uL, uR = _f64(x0), _f64(uL), _f64(uR)
@@ -234,8 +248,16 @@ def linear_interval(Ac, Bc, n_sub, x0, uL, uR, s):
     S = np.empty(n)
     _check(_load().oracle_linear_interval(n, mm, _d(Ac), _d(Bc), int(n_sub), _d(x0), _d(uL),
                                           _d(uR), float(s), _d(x1), _d(A), _d(Bm), _d(Bp),
-                                          _d(S)), "linear_interval")
+                                          _d(S), int(scheme)), "linear_interval")
     return x1, A, Bm, Bp, S
+
+
+def tableau(scheme):
+    """Butcher tableau of a scheme: (stages, c [6], a [6, 6], b [6])."""
+    st = ctypes.c_int()
+    c, a, b = np.empty(6), np.empty((6, 6)), np.empty(6)
+    _check(_load().oracle_tableau(int(scheme), ctypes.byref(st), _d(c), _d(a), _d(b)), "tableau")
+    return st.value, c, a, b
 
 
 def _nonempty(a):

@@ -47,6 +47,9 @@ class Robot:
     legs: list = field(default_factory=list)  # per leg: list of joint indices (for gait poses)
     torso_horizontal: bool = True
     aux_model: int = 0  # 0: one path-penalty state per contact; 1: Eq. (12) (4 + 1 states per contact)
+    joint_forces: int = 0  # 0: joint reaction forces are inputs; 1: eliminated by Eq. (3)
+    scheme: int = 0        # integrator: 0 classical RK4, 1 Runge-Kutta-Fehlberg 4(5)
+    terrain: tuple = (0.0, 0.0)  # contact surface y = a sin(k x) as (a, k); (0, 0) is flat ground
 
     @property
     def nb(self):
@@ -74,7 +77,7 @@ class Robot:
 
     @property
     def nu(self):
-        return 3 * self.nj + 3 * self.nc
+        return (1 if self.joint_forces else 3) * self.nj + 3 * self.nc
 
     def as_dict(self):
         return {
@@ -83,6 +86,8 @@ class Robot:
             "joint_rho_parent": self.joint_rho_parent, "joint_rho_child": self.joint_rho_child,
             "contact_body": self.contact_body, "contact_rho": self.contact_rho,
             "contact_mu": self.contact_mu, "gravity": self.gravity, "aux_model": self.aux_model,
+            "joint_forces": self.joint_forces, "scheme": self.scheme,
+            "terrain": tuple(float(v) for v in self.terrain),
         }
 
 
@@ -154,6 +159,20 @@ def with_cross_states(robot: Robot) -> Robot:
     cross-complementarity states + one path-penalty state per contact, and
     contact inputs (phi_t, phi_n, gamma) in place of (lambda_n, lambda_t+, lambda_t-)."""
     return replace(robot, aux_model=1)
+
+
+def with_paper_dynamics(robot: Robot, joint_forces=1, scheme=1, terrain=None) -> Robot:
+    """The same robot with the paper's own modelling choices: joint reaction
+    forces eliminated at the acceleration level (inputs: joint torques and
+    contact inputs), the Runge-Kutta-Fehlberg 4(5) integrator and, if given,
+    the sinusoidal contact surface y = a sin(k x) as (a, k)."""
+    t = robot.terrain if terrain is None else (float(terrain[0]), float(terrain[1]))
+    return replace(robot, joint_forces=int(joint_forces), scheme=int(scheme), terrain=t)
+
+
+# Sinusoidal surface of the biped scenario (Sec. VI-B), synthetic dimensions:
+# 5 cm amplitude, 1 m wavelength.
+TERRAIN_SINE = (0.05, 2.0 * np.pi)
 
 
 # ---------------------------------------------------------------------------

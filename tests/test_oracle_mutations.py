@@ -16,33 +16,40 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
 PINS = ["tests/test_oracle_integrator.py", "tests/test_oracle_physics.py", "tests/test_oracle_vjp.py",
-        "tests/test_oracle_node.py", "tests/test_oracle_cross.py"]
+        "tests/test_oracle_node.py", "tests/test_oracle_cross.py", "tests/test_oracle_paper_dynamics.py"]
 
 MUTATIONS = [
     ("parent joint torque sign", "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) - tau;",
      "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) + tau;"),
     ("parent joint force sign", "Fx[p] = Fx[p] - lx;", "Fx[p] = Fx[p] + lx;"),
-    ("child anchor taken from parent", "lever_arm(xt[3 * c + 2], M.jrho_c + 2 * j, rcx, rcy);",
-     "lever_arm(xt[3 * c + 2], M.jrho_p + 2 * j, rcx, rcy);"),
+    ("child anchor taken from parent",
+     "const T& ly = u[nj + 2 * j + 1];\n    T rcx, rcy, rpx, rpy;\n    lever_arm(xt[3 * c + 2], M.jrho_c + 2 * j, rcx, rcy);",
+     "const T& ly = u[nj + 2 * j + 1];\n    T rcx, rcy, rpx, rpy;\n    lever_arm(xt[3 * c + 2], M.jrho_p + 2 * j, rcx, rcy);"),
+    ("Eq. (3) child anchor taken from parent",
+     "lever_arm(xt[3 * c + 2], M.jrho_c + 2 * j, rcx, rcy);\n    lever_arm(xt[3 * p + 2], M.jrho_p + 2 * j, rpx, rpy);\n    // grad C_j",
+     "lever_arm(xt[3 * c + 2], M.jrho_p + 2 * j, rcx, rcy);\n    lever_arm(xt[3 * p + 2], M.jrho_p + 2 * j, rpx, rpy);\n    // grad C_j"),
     ("cross product sign", "T cross2(const T& rx, const T& ry, const T& fx, const T& fy) { return rx * fy - ry * fx; }",
      "T cross2(const T& rx, const T& ry, const T& fx, const T& fy) { return ry * fx - rx * fy; }"),
     ("rotation transposed", "rx = c * rho[0] - s * rho[1];\n  ry = s * rho[0] + c * rho[1];",
      "rx = c * rho[0] + s * rho[1];\n  ry = -s * rho[0] + c * rho[1];"),
     ("gravity dropped", "Fy[b] = T(-M.mass[b] * M.g);", "Fy[b] = T(0.0);"),
     ("gravity sign", "Fy[b] = T(-M.mass[b] * M.g);", "Fy[b] = T(M.mass[b] * M.g);"),
-    ("contact tangent sign", "const T fx = ltp - ltm;", "const T fx = ltm - ltp;"),
+    ("contact tangent sign", "const T ft = ltp - ltm;", "const T ft = ltm - ltp;"),
     ("inertia replaced by mass", "Tq[b] / M.inertia[b];", "Tq[b] / M.mass[b];"),
     ("q' = v index", "out[3 * b + k] = xt[3 * nb + 3 * b + k];", "out[3 * b + k] = xt[3 * nb + 3 * b];"),
-    ("signed distance uses r_x", "const T phi = xt[3 * b + 1] + ry;", "const T phi = xt[3 * b + 1] + rx;"),
+    ("signed distance uses r_x", "contact_frame(M, xt[3 * b] + rx, xt[3 * b + 1] + ry);",
+     "contact_frame(M, xt[3 * b] + rx, xt[3 * b + 1] + rx);"),
     ("friction cone sign", "sabs_plus(ltp + ltm - M.cmu[i] * ln)", "sabs_plus(ltp + ltm + M.cmu[i] * ln)"),
     ("penalty without ramp", "const T p = ramp(z);", "const T p = z;"),
     ("pseudo-Huber constant", "(p * p) / (1.0 + sqrt(1.0 + p * p))", "(p * p) / (2.0 + sqrt(1.0 + p * p))"),
     ("FOH weights swapped", "u[q] = (1.0 - tau) * uL[q] + tau * uR[q];",
      "u[q] = tau * uL[q] + (1.0 - tau) * uR[q];"),
-    ("RK4 weights", "w[4] = {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0}",
-     "w[4] = {1.0 / 8.0, 3.0 / 8.0, 3.0 / 8.0, 1.0 / 8.0}"),
-    ("RK4 stage node", "c[4] = {0.0, 0.5, 0.5, 1.0}", "c[4] = {0.0, 0.5, 0.5, 0.5}"),
-    ("dilation dropped", "k[r] = s * fv[r];", "k[r] = fv[r];"),
+    ("RK4 weights", "{1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0}",
+     "{1.0 / 8.0, 3.0 / 8.0, 3.0 / 8.0, 1.0 / 8.0}"),
+    ("RK4 stage node", "{0.0, 0.5, 0.5, 1.0},", "{0.0, 0.5, 0.5, 0.5},"),
+    ("RK4 stage coupling", "{{0.0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 1.0}}",
+     "{{0.0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 0.5}}"),
+    ("dilation dropped", "k[j][r] = s * fv[r];", "k[j][r] = fv[r];"),
     ("dual product rule term", "r.d[i] = a.v * b.d[i] + b.v * a.d[i];", "r.d[i] = a.v * b.d[i];"),
     ("dual sin derivative", "const double c = std::cos(a.v);", "const double c = -std::cos(a.v);"),
     ("dual sqrt derivative", "const double k = 0.5 / r.v;", "const double k = 1.0 / r.v;"),
@@ -64,15 +71,15 @@ MUTATIONS = [
     ("K without M^-1", "acc = acc + G[r * nq + a] * minv[a] * G[c2 * nq + a];",
      "acc = acc + G[r * nq + a] * G[c2 * nq + a];"),
     ("impulse left out of w", "w[a] = vm[a] + minv[a] * Jphi[a];", "w[a] = vm[a];"),
-    ("contact impulse moment", "Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], pt, pn);",
-     "Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], pn, pt);"),
+    ("contact impulse moment", "Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], ix, iy);",
+     "Jphi[3 * b + 2] = Jphi[3 * b + 2] + cross2(crx[i], cry[i], iy, ix);"),
     ("pose continuity sign", "for (int a = 0; a < nq; ++a) g[a] = xp[a] - xm[a];",
      "for (int a = 0; a < nq; ++a) g[a] = xp[a] + xm[a];"),
     ("restitution dropped", "const T cn = vnp + e[i] * vnm;", "const T cn = vnp;"),
-    ("tangential velocity from v-", "const T vtp = vp[3 * b] - vp[3 * b + 2] * cry[i];",
-     "const T vtp = vm[3 * b] - vm[3 * b + 2] * cry[i];"),
-    ("normal velocity lever arm", "const T vnp = vp[3 * b + 1] + vp[3 * b + 2] * crx[i];",
-     "const T vnp = vp[3 * b + 1] + vp[3 * b + 2] * cry[i];"),
+    ("tangential velocity from v-", "const T vtp = fr[i].tx * vxp + fr[i].ty * vyp;",
+     "const T vtp = fr[i].tx * vxm + fr[i].ty * vym;"),
+    ("normal velocity lever arm", "const T vyp = vp[3 * b + 1] + vp[3 * b + 2] * crx[i];",
+     "const T vyp = vp[3 * b + 1] + vp[3 * b + 2] * cry[i];"),
     ("smooth-norm gradient", "(pt / sqrt(1.0 + pt * pt))", "(pt)"),
     ("Fischer-Burmeister sign", "return a + b - sqrt(a * a + b * b + delta);",
      "return a + b + sqrt(a * a + b * b + delta) - 2.0 * sqrt(delta);"),
@@ -80,16 +87,40 @@ MUTATIONS = [
      "const T rho = smooth_abs(pn) - smooth_abs(pt);"),
     ("Gamma seed column", "gm[i].d[2 * nxt + 2 * nc + i] = 1.0;", "gm[i].d[2 * nxt + i] = 1.0;"),
     # full auxiliary state of Eq. (12)
-    ("lambda_c without the rotation term", "const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;",
-     "const T vt = xt[3 * nb + 3 * b];"),
-    ("lambda_c lever arm", "const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;",
-     "const T vt = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * rx;"),
+    ("lambda_c without the rotation term", "const T vcx = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;",
+     "const T vcx = xt[3 * nb + 3 * b];"),
+    ("lambda_c lever arm", "const T vcx = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * ry;",
+     "const T vcx = xt[3 * nb + 3 * b] - xt[3 * nb + 3 * b + 2] * rx;"),
     ("phi_n state integrates phi_t", "out[6 * nb + 4 * i] = fn;", "out[6 * nb + 4 * i] = ft;"),
     ("rho_c without mu", "const T rho_c = smooth_abs(M.cmu[i] * fn) - smooth_abs(ft);",
      "const T rho_c = smooth_abs(fn) - smooth_abs(ft);"),
     ("cross penalty drops gamma", "sabs_plus(-fn) + sabs_plus(-phi) + sabs_plus(-gam) +",
      "sabs_plus(-fn) + sabs_plus(-phi) + sabs_plus(gam) +"),
-    ("cross tangential force sign", "Fx[b] = Fx[b] + ft;", "Fx[b] = Fx[b] - ft;"),
+    ("cross tangential force sign", "fx = fr.tx * ft + fr.nx * fn;", "fx = -(fr.tx * ft) + fr.nx * fn;"),
+    # paper-faithful dynamics: Eq. (3) elimination, sinusoidal surface, RKF45
+    ("Eq. (3) parent centripetal sign", "r[row] = wc * wc * rcx - wp * wp * rpx;",
+     "r[row] = wc * wc * rcx + wp * wp * rpx;"),
+    ("Eq. (3) centripetal term dropped", "r[row + 1] = wc * wc * rcy - wp * wp * rpy;",
+     "r[row + 1] = T(0.0);"),
+    ("Eq. (3) grad C child angle column", "{row, 3 * c + 2, -rcy}", "{row, 3 * c + 2, rcy}"),
+    ("Eq. (3) grad C parent block", "{row + 1, 3 * p + 1, T(-1.0)}", "{row + 1, 3 * p + 1, T(1.0)}"),
+    ("eliminated model parent torque sign", "      Tq[p] = Tq[p] - tau;\n      continue;",
+     "      Tq[p] = Tq[p] + tau;\n      continue;"),
+    ("eliminated model inertia", "K[(size_t)(3 * b + 2) * n + 3 * b + 2] = T(M.inertia[b]);",
+     "K[(size_t)(3 * b + 2) * n + 3 * b + 2] = T(M.mass[b]);"),
+    ("terrain normal sign", "f.nx = gx * inv;", "f.nx = -gx * inv;"),
+    ("terrain slope uses sin", "const T gx = -(a * k) * cos(k * px);", "const T gx = -(a * k) * sin(k * px);"),
+    ("signed distance not normalized", "f.phi = hc * inv;", "f.phi = hc;"),
+    ("terrain tangent orientation", "f.ty = -f.nx;", "f.ty = f.nx;"),
+    ("terrain force drops normal x", "fx = fr.tx * ft + fr.nx * ln;", "fx = fr.tx * ft;"),
+    ("impact impulse in world axes", "const T ix = fr[i].tx * pt + fr[i].nx * pn;", "const T ix = pt;"),
+    ("RKF45 coupling coefficient", "-845.0 / 4104.0}", "845.0 / 4104.0}"),
+    ("RKF45 fourth-order weights",
+     "{16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0,\n                         2.0 / 55.0}",
+     "{25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0,\n                         0.0}"),
+    ("RKF45 stage time", "{0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0}",
+     "{0.0, 1.0 / 4.0, 3.0 / 8.0, 11.0 / 13.0, 1.0, 1.0 / 2.0}"),
+    ("RKF45 selected as RK4", "return scheme == 1 ? kRKF45 : kRK4;", "return kRK4;"),
 ]
 
 
