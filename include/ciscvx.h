@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 5
+#define CISCVX_VERSION_MINOR 6
 
 typedef enum {
   CISCVX_OK = 0,
@@ -142,6 +142,25 @@ typedef struct {
  *     VJP, compact outputs and z return CISCVX_EUNSUPPORTED for it. */
 typedef enum { CISCVX_AUX_PENALTY = 0, CISCVX_AUX_CROSS = 1 } ciscvx_aux_model;
 
+/* Joint reaction forces (Sec. II-A).
+ *   CISCVX_JOINT_FORCE_INPUT: lambda_j are FOH inputs (n_u = 3 n_j + 3 n_c,
+ *     order tau, lambda, contact inputs); the links are then decoupled.
+ *   CISCVX_JOINT_FORCE_ELIMINATED: the paper's model.  The joint constraints
+ *     C_j = p_c + R_c rho_c - p_p - R_p rho_p are imposed at the acceleration
+ *     level, Eq. (3): grad C v' + (v^T Hess C_j v)_j = 0, and with
+ *     M v' = W + J_c^T R_c phi + grad C^T lambda this fixes lambda
+ *     = K^-1 (kappa - grad C M^-1 (W + J_c^T R_c phi)), K = grad C M^-1 grad C^T,
+ *     kappa_j = omega_c^2 r_c - omega_p^2 r_p.  Inputs: n_u = n_j + 3 n_c
+ *     (tau, then contact inputs).  Needs a joint forest of at most
+ *     CISCVX_NODE_MAX_JOINTS joints with at most CISCVX_NODE_MAX_JOINTS_PER_LINK
+ *     on one link (EUNSUPPORTED otherwise). */
+typedef enum { CISCVX_JOINT_FORCE_INPUT = 0, CISCVX_JOINT_FORCE_ELIMINATED = 1 } ciscvx_joint_force_model;
+
+/* Integration scheme of the substeps (Sec. VI).  CISCVX_RK4: classical RK4.
+ * CISCVX_RKF45: Fehlberg's six-stage 4(5) pair, advanced with its fifth-order
+ * weights (fixed steps; the embedded estimate is not formed). */
+typedef enum { CISCVX_RK4 = 0, CISCVX_RKF45 = 1 } ciscvx_scheme;
+
 typedef struct {
   int n_bodies, n_joints, n_contacts;
   const ciscvx_body_desc* bodies;       /* [n_bodies] host memory */
@@ -149,13 +168,26 @@ typedef struct {
   const ciscvx_contact_desc* contacts;  /* [n_contacts] host memory (may be NULL if 0) */
   double gravity;                       /* magnitude, acting along -y, finite */
   int aux_model;                        /* CISCVX_AUX_PENALTY or CISCVX_AUX_CROSS */
+  int joint_forces;                     /* ciscvx_joint_force_model (0: inputs) */
+  int scheme;                           /* ciscvx_scheme (0: RK4) */
+  /* Contact surface y = terrain_amp sin(terrain_wavenumber x) (Sec. VI-B);
+   * terrain_amp = 0 is flat ground y = 0.  Signed distance phi = h^c /
+   * ||grad h^c||, h^c = y - terrain_amp sin(terrain_wavenumber x); contact
+   * frame: normal n = grad h^c / ||grad h^c||, tangent t = (n_y, -n_x); the
+   * contact-frame force (tangential, normal) acts as t tangential + n normal. */
+  double terrain_amp, terrain_wavenumber;
 } ciscvx_model_desc;
 
 typedef struct ciscvx_model ciscvx_model;
 
 /* Model of Sec. II-A / Sec. IV-A (see the file header).  Copies the host
  * description, builds the per-link device tables on the current CUDA device
- * and allocates the model's device status word.  *out receives an opaque
+ * and allocates the model's device status word.  A model with eliminated
+ * joint forces, a sinusoidal surface or the RKF45 scheme has coupled links:
+ * it is linearized by ciscvx_discretize alone (dense outputs, z not provided,
+ * a workspace from ciscvx_discretize_workspace_size); its VJP, compact
+ * outputs and batch plans return CISCVX_EUNSUPPORTED, and so do its node
+ * constraints on a sinusoidal surface.  *out receives an opaque
  * handle owned by the caller (free with ciscvx_model_destroy).  Errors:
  * EINVAL (null, counts < 0, n_bodies < 1, bad indices, non-positive mass or
  * inertia, parent == child, non-finite values), EUNSUPPORTED (limits above,
@@ -167,7 +199,7 @@ ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** 
 void ciscvx_model_destroy(ciscvx_model* model);
 
 /* n_x = 6 n_b (x~ without the auxiliary states), n_y = n_c (CISCVX_AUX_CROSS:
- * 5 n_c), n_u = 3 n_j + 3 n_c.
+ * 5 n_c), n_u = 3 n_j + 3 n_c (eliminated joint forces: n_j + 3 n_c).
  * Any output pointer may be NULL.  EINVAL on a null model. */
 ciscvx_status ciscvx_model_dims(const ciscvx_model* model, int* n_x, int* n_y, int* n_u);
 
@@ -207,9 +239,24 @@ ciscvx_status ciscvx_model_nnz(const ciscvx_model* model, int* nnz_a, int* nnz_b
 typedef enum { CISCVX_OP_DISCRETIZE = 0, CISCVX_OP_VJP = 1 } ciscvx_op;
 
 /* Bytes of device scratch memory that `op` needs for N intervals (0 if none).
- * EINVAL on null pointers, N < 1 or an unknown op/layout. */
+ * EINVAL on null pointers, N < 1 or an unknown op/layout.  For a model with
+ * coupled links the discretization's scratch depends on n_sub and the
+ * precision: CISCVX_OP_DISCRETIZE returns EUNSUPPORTED for it (use
+ * ciscvx_discretize_workspace_size). */
 ciscvx_status ciscvx_workspace_size(const ciscvx_model* model, ciscvx_op op, int N,
                                     ciscvx_u_layout layout, size_t* bytes);
+
+/* Scratch of ciscvx_discretize for N intervals of n_sub substeps: *min_bytes
+ * (the least it accepts: one chunk of 32 intervals, or N if fewer) and
+ * *full_bytes (all N intervals in one chunk).  A workspace between the two
+ * is used in chunks of as many intervals as fit (stage data of the nominal
+ * trajectory: n_sub x stages x (4 n_j + n_b + n_x~ + skyline(K) + contact
+ * fields) values per interval in the precision's dtype).  Both are 0 for
+ * models without coupled links.  Either pointer may be NULL.  EINVAL on a
+ * null model, N < 1, n_sub < 1 or an unknown precision. */
+ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* model, int N, int n_sub,
+                                               ciscvx_precision precision, size_t* min_bytes,
+                                               size_t* full_bytes);
 
 /* ----------------------------------------------------------- discretize --- */
 
@@ -222,9 +269,17 @@ ciscvx_status ciscvx_workspace_size(const ciscvx_model* model, ciscvx_op op, int
  *     NULL when n_c == 0.
  *   z: optional FP64 affine term z_k = x~(1) - A x~_k - B- u_L - B+ u_R - S s_k
  *     (NULL to skip).
- *   workspace/ws_bytes: ignored (the operation needs none); pass NULL, 0.
+ *   workspace/ws_bytes: ignored (pass NULL, 0) unless the model has coupled
+ *     links; then device scratch of at least the minimum of
+ *     ciscvx_discretize_workspace_size, 16-byte aligned (contents overwritten).
+ *     Such models run two kernels per chunk of intervals: the nominal
+ *     trajectory in FP64 (one lane per interval, with the per-stage L D L^T
+ *     solve of Eq. (3)), then one tangent column per thread in the
+ *     precision's dtype.
  * Errors: EINVAL (nulls, N < 1, n_sub < 1, unknown layout/precision),
- * EUNSUPPORTED (tensor-core precisions), ECUDA (launch failure). */
+ * EUNSUPPORTED (tensor-core precisions; z for a model with coupled links),
+ * EINVAL also for a missing or short workspace of such a model, ECUDA
+ * (launch failure). */
 ciscvx_status ciscvx_discretize(const ciscvx_model* model, int N, int n_sub,
                                 ciscvx_precision precision, ciscvx_u_layout layout,
                                 const double* X, const double* U, const double* s, void* A,

@@ -31,7 +31,7 @@ EXPORTS = (
     "ciscvx_batch_sync_status", "ciscvx_batch_run_host",
     "ciscvx_model_pattern", "ciscvx_model_nnz", "ciscvx_discretize_compact",
     "ciscvx_node_linearize", "ciscvx_batch_discretize_and_vjp", "ciscvx_batch_autotune_fused",
-    "ciscvx_batch_get_tune_fused",
+    "ciscvx_batch_get_tune_fused", "ciscvx_discretize_workspace_size",
 )
 FORMAT = {"dense": 0, "compact": 1}
 
@@ -83,7 +83,9 @@ class _Desc(ctypes.Structure):
     _fields_ = [("n_bodies", ctypes.c_int), ("n_joints", ctypes.c_int),
                 ("n_contacts", ctypes.c_int), ("bodies", ctypes.POINTER(_Body)),
                 ("joints", ctypes.POINTER(_Joint)), ("contacts", ctypes.POINTER(_Contact)),
-                ("gravity", ctypes.c_double), ("aux_model", ctypes.c_int)]
+                ("gravity", ctypes.c_double), ("aux_model", ctypes.c_int),
+                ("joint_forces", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("terrain_amp", ctypes.c_double), ("terrain_wavenumber", ctypes.c_double)]
 
 
 _lib = None
@@ -108,6 +110,9 @@ def load(path: str | None = None):
                                       ctypes.POINTER(ctypes.c_int)]
     lib.ciscvx_workspace_size.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_size_t)]
+    lib.ciscvx_discretize_workspace_size.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.POINTER(ctypes.c_size_t),
+                                                     ctypes.POINTER(ctypes.c_size_t)]
     lib.ciscvx_discretize.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                       ctypes.c_size_t, _vp]
@@ -158,7 +163,7 @@ def load(path: str | None = None):
               "ciscvx_batch_autotune", "ciscvx_batch_sync_status", "ciscvx_model_pattern",
               "ciscvx_model_nnz", "ciscvx_discretize_compact", "ciscvx_node_linearize",
               "ciscvx_batch_discretize_and_vjp", "ciscvx_batch_autotune_fused",
-              "ciscvx_batch_get_tune_fused"):
+              "ciscvx_batch_get_tune_fused", "ciscvx_discretize_workspace_size"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -193,13 +198,19 @@ class _DescHolder:
             for j in range(nj)])
         self._contacts = (_Contact * max(nc, 1))(*[
             _Contact(int(cb[i]), (ctypes.c_double * 2)(*cr[i]), cm[i]) for i in range(nc)])
-        try:
-            aux = int(_get(robot, "aux_model"))
-        except (KeyError, AttributeError):
-            aux = 0
+        def opt(key, default):
+            try:
+                return _get(robot, key)
+            except (KeyError, AttributeError):
+                return default
+        aux = int(opt("aux_model", 0))
+        jf = int(opt("joint_forces", 0))
+        scheme = int(opt("scheme", 0))
+        ta, tk = (float(v) for v in opt("terrain", (0.0, 0.0)))
         self.desc = _Desc(nb, nj, nc, self._bodies, self._joints, self._contacts,
-                          float(_get(robot, "gravity")), aux)
+                          float(_get(robot, "gravity")), aux, jf, scheme, ta, tk)
         self.nb, self.nc, self.aux_model = nb, nc, aux
+        self.coupled = bool(jf or scheme or ta != 0.0)
 
 
 def model_pattern(robot):
@@ -233,6 +244,8 @@ class Model:
         self.nb = self._d.nb
         self.nc = self._d.nc            # contacts (penalty / rho columns)
         self.aux_model = self._d.aux_model
+        # eliminated joint forces, a sinusoidal surface or RKF45: the coupled path
+        self.coupled = self._d.coupled
         na, nbb = ctypes.c_int(), ctypes.c_int()
         _check(lib.ciscvx_model_nnz(h, ctypes.byref(na), ctypes.byref(nbb)))
         self.nnz_a, self.nnz_b = na.value, nbb.value
@@ -280,9 +293,24 @@ def workspace_size(model: Model, op: int, N: int, layout: str = "node") -> int:
     return n.value
 
 
+def discretize_workspace_size(model: Model, N: int, n_sub: int, precision: str = "fp64"):
+    """ciscvx_discretize_workspace_size: (min_bytes, full_bytes) of scratch (0, 0 unless coupled)."""
+    lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().ciscvx_discretize_workspace_size(model.handle, int(N), int(n_sub),
+                                                   PRECISION[precision], ctypes.byref(lo),
+                                                   ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+# default cap on the scratch a discretize call allocates for a coupled model
+DISCRETIZE_WS_CAP = 2 << 30
+
+
 def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layout: str = "node",
-               want_z: bool = False, out: dict | None = None):
-    """ciscvx_discretize on device tensors.  Returns dict A, Bm, Bp, S, defect, penalty (, z)."""
+               want_z: bool = False, out: dict | None = None, workspace=None):
+    """ciscvx_discretize on device tensors.  Returns dict A, Bm, Bp, S, defect, penalty (, z).
+    A model with coupled links needs scratch: `workspace` (a CUDA uint8 tensor),
+    else one of min(full size, 2 GiB) (at least the minimum) is allocated."""
     import torch
     f64 = torch.float64
     _need(X, "X", f64); _need(U, "U", f64); _need(s, "s", f64)
@@ -301,11 +329,17 @@ def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layou
         }
         if want_z:
             out["z"] = torch.empty((N, nxt), dtype=f64, device=dev)
+    ws_bytes = 0
+    if model.coupled:
+        lo, hi = discretize_workspace_size(model, N, n_sub, precision)
+        if workspace is None:
+            workspace = torch.empty(max(lo, min(hi, DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+        ws_bytes = workspace.numel() * workspace.element_size()
     _check(load().ciscvx_discretize(
         model.handle, int(N), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X), _ptr(U),
         _ptr(s), _ptr(out["A"]), _ptr(out["Bm"]) if nu else None, _ptr(out["Bp"]) if nu else None,
         _ptr(out["S"]), _ptr(out["defect"]), _ptr(out["penalty"]) if nc else None,
-        _ptr(out.get("z")), None, 0, _stream()))
+        _ptr(out.get("z")), _ptr(workspace) if model.coupled else None, ws_bytes, _stream()))
     return out
 
 

@@ -11,7 +11,7 @@
 #include <new>
 #include <string>
 
-#include "common.cuh"
+#include "coupled.cuh"
 
 using namespace ciscvx;
 
@@ -109,9 +109,14 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   const int nb = d->n_bodies, nj = d->n_joints, nc = d->n_contacts;
   M.nb = nb; M.nj = nj; M.nc = nc;
   M.aux = d->aux_model;
+  M.jelim = d->joint_forces;
+  M.scheme = d->scheme;
+  M.ta = d->terrain_amp;
+  M.tk = d->terrain_wavenumber;
+  if (M.ta == 0.0) M.tk = 0.0;
   M.ny = (M.aux ? 5 : 1) * nc;
   M.nxt = 6 * nb + M.ny;
-  M.nu = 3 * nj + 3 * nc;
+  M.nu = (M.jelim ? 1 : 3) * nj + 3 * nc;
   M.g = d->gravity;
   M.tree = 1;
   for (int b = 0; b < nb; ++b) {
@@ -158,6 +163,7 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
     // torque: +tau on the child, -tau on the parent
     if ((st = add_input(M, c, j, 0, 0, 0, 0, 1.0 / Ic))) return st;
     if ((st = add_input(M, p, j, 0, 0, 0, 0, -1.0 / Ip))) return st;
+    if (M.jelim) continue;  // reaction forces are not inputs (coupled path)
     // lambda_x: +e_x on the child at rho_c, -e_x on the parent at rho_p
     //   rho x e_x = -rho_y, rho . e_x = rho_x
     if ((st = add_input(M, c, nj + 2 * j, 1.0 / mc, 0, -cy / Ic, cx / Ic, 0))) return st;
@@ -175,7 +181,7 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
     if (B.contact >= 0)
       return fail(CISCVX_EUNSUPPORTED, "link %d carries more than one contact", C.body);
     B.contact = i;
-    B.cin = 3 * nj + 3 * i;
+    B.cin = (M.jelim ? 1 : 3) * nj + 3 * i;
     B.crho[0] = C.rho[0]; B.crho[1] = C.rho[1];
     B.mu = C.mu;
     const double m = d->bodies[C.body].mass, I = d->bodies[C.body].inertia;
@@ -233,6 +239,12 @@ ciscvx_status check_desc(const ciscvx_model_desc* desc) {
   if (!std::isfinite(desc->gravity)) return fail(CISCVX_EINVAL, "non-finite gravity");
   if (desc->aux_model != CISCVX_AUX_PENALTY && desc->aux_model != CISCVX_AUX_CROSS)
     return fail(CISCVX_EINVAL, "unknown aux_model %d", desc->aux_model);
+  if (desc->joint_forces != CISCVX_JOINT_FORCE_INPUT && desc->joint_forces != CISCVX_JOINT_FORCE_ELIMINATED)
+    return fail(CISCVX_EINVAL, "unknown joint_forces %d", desc->joint_forces);
+  if (desc->scheme != CISCVX_RK4 && desc->scheme != CISCVX_RKF45)
+    return fail(CISCVX_EINVAL, "unknown scheme %d", desc->scheme);
+  if (!std::isfinite(desc->terrain_amp) || !std::isfinite(desc->terrain_wavenumber))
+    return fail(CISCVX_EINVAL, "non-finite terrain parameters");
   return CISCVX_OK;
 }
 
@@ -319,6 +331,17 @@ ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** 
   if (!m) return fail(CISCVX_ENOMEM, "host allocation failed");
   st = build_tables(desc, m->host);
   if (st != CISCVX_OK) { delete m; return st; }
+  m->cpl = nullptr;
+  if (cpl_needed(m->host)) {
+    m->cpl = new (std::nothrow) CplTab;
+    if (!m->cpl) { delete m; return fail(CISCVX_ENOMEM, "host allocation failed"); }
+    const char* why = cpl_build(m->host, *m->cpl);
+    if (why) {
+      delete m->cpl;
+      delete m;
+      return fail(CISCVX_EUNSUPPORTED, "%s", why);
+    }
+  }
   m->dev = nullptr;
   m->status = nullptr;
   cudaGetDevice(&m->device);
@@ -329,6 +352,7 @@ ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** 
   if (e != cudaSuccess) {
     if (m->dev) cudaFree(m->dev);
     if (m->status) cudaFree(m->status);
+    delete m->cpl;
     delete m;
     return e == cudaErrorMemoryAllocation ? fail(CISCVX_ENOMEM, "device allocation failed")
                                           : cuda_fail(e, "model upload");
@@ -341,6 +365,7 @@ void ciscvx_model_destroy(ciscvx_model* m) {
   if (!m) return;
   if (m->dev) cudaFree(m->dev);
   if (m->status) cudaFree(m->status);
+  delete m->cpl;
   delete m;
 }
 
@@ -354,6 +379,8 @@ ciscvx_status ciscvx_model_pattern(const ciscvx_model_desc* desc, int* nnz_a, in
   if (!M) return fail(CISCVX_ENOMEM, "host allocation failed");
   st = build_tables(desc, *M);
   if (st == CISCVX_OK && M->aux) st = fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
+  if (st == CISCVX_OK && cpl_needed(*M))
+    st = fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for models with coupled links");
   if (st == CISCVX_OK) {
     if (nnz_a) *nnz_a = M->nnzA;
     if (nnz_b) *nnz_b = M->nnzB;
@@ -383,10 +410,34 @@ ciscvx_status ciscvx_workspace_size(const ciscvx_model* m, ciscvx_op op, int N,
   if (!m || !bytes) return fail(CISCVX_EINVAL, "null argument");
   if (N < 1) return fail(CISCVX_EINVAL, "N must be >= 1");
   if (!layout_ok(layout)) return fail(CISCVX_EINVAL, "unknown control layout %d", (int)layout);
-  if (op == CISCVX_OP_DISCRETIZE) *bytes = 0;
+  if (op == CISCVX_OP_DISCRETIZE) {
+    if (m->cpl)
+      return fail(CISCVX_EUNSUPPORTED, "the scratch of a model with coupled links depends on n_sub and "
+                                       "the precision: use ciscvx_discretize_workspace_size");
+    *bytes = 0;
+  }
   else if (op == CISCVX_OP_VJP)
     *bytes = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
   else return fail(CISCVX_EINVAL, "unknown op %d", (int)op);
+  return ok();
+}
+
+ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* m, int N, int n_sub,
+                                               ciscvx_precision precision, size_t* min_bytes,
+                                               size_t* full_bytes) {
+  if (!m) return fail(CISCVX_EINVAL, "null model");
+  if (N < 1 || n_sub < 1) return fail(CISCVX_EINVAL, "need N >= 1 and n_sub >= 1");
+  if (precision != CISCVX_FP64 && precision != CISCVX_FP32_PHI && precision != CISCVX_TF32_TC &&
+      precision != CISCVX_BF16_TC)
+    return fail(CISCVX_EINVAL, "unknown precision %d", (int)precision);
+  size_t lo = 0, hi = 0;
+  if (m->cpl) {
+    const size_t per = cpl_interval_bytes(*m->cpl, n_sub, precision);
+    lo = per * (size_t)std::min(N, 32);
+    hi = per * (size_t)N;
+  }
+  if (min_bytes) *min_bytes = lo;
+  if (full_bytes) *full_bytes = hi;
   return ok();
 }
 
@@ -395,12 +446,24 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* m, int N, int n_sub,
                                 const double* X, const double* U, const double* s, void* A,
                                 void* Bm, void* Bp, void* S, double* defect, double* penalty,
                                 double* z, void* workspace, size_t ws_bytes, void* stream) {
-  (void)workspace; (void)ws_bytes;
   ciscvx_status st = check_common(m, N, n_sub, precision, layout, X, U, s);
   if (st != CISCVX_OK) return st;
   if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
   if (m->host.nu > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
+  if (m->cpl) {
+    if (z) return fail(CISCVX_EUNSUPPORTED, "z is not provided for models with coupled links");
+    const size_t per = cpl_interval_bytes(*m->cpl, n_sub, precision);
+    const size_t need = per * (size_t)std::min(N, 32);
+    if (!workspace || ws_bytes < need)
+      return fail(CISCVX_EINVAL, "workspace of at least %zu bytes needed (got %zu)", need, ws_bytes);
+    if (((uintptr_t)workspace & 15) != 0) return fail(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+    const long chunk = (long)std::min<size_t>(ws_bytes / per, (size_t)N);
+    cudaError_t e = launch_coupled(*m->cpl, N, n_sub, precision, layout, X, U, s, A, Bm, Bp, S,
+                                   defect, penalty, workspace, chunk, m->status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "coupled discretize launch");
+    return ok();
+  }
   if (m->host.aux && z) return fail(CISCVX_EUNSUPPORTED, "z is not provided for the Eq. (12) model");
   cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, false, m->host.aux != 0, X, U,
                                     s, A, Bm, Bp, S, defect, penalty, z, m->status,
@@ -420,6 +483,7 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* m, int N, int n_sub,
   if (m->host.nnzB > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
   if (m->host.aux) return fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
+  if (m->cpl) return fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for models with coupled links");
   cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, true, false, X, U,
                                     s, A, Bm, Bp, S, defect, penalty, z, m->status,
                                     (cudaStream_t)stream);
@@ -438,6 +502,7 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
   if (n_sub > MAXSUB_VJP)
     return fail(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (got %d)", MAXSUB_VJP, n_sub);
   if (m->host.aux) return fail(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
+  if (m->cpl) return fail(CISCVX_EUNSUPPORTED, "the VJP is not provided for models with coupled links");
   if (!w || (m->host.nc > 0 && !rho)) return fail(CISCVX_EINVAL, "null cotangent array");
   if (!gX || !gs || (m->host.nu > 0 && !gU)) return fail(CISCVX_EINVAL, "null gradient array");
   const size_t need = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
@@ -459,6 +524,8 @@ ciscvx_status ciscvx_node_linearize(const ciscvx_model* m, int n, const double* 
   if (!m || !params) return fail(CISCVX_EINVAL, "null model or params");
   if (n < 1) return fail(CISCVX_EINVAL, "n_nodes must be >= 1 (got %d)", n);
   const DevModel& M = m->host;
+  if (M.ta != 0.0)
+    return fail(CISCVX_EUNSUPPORTED, "node constraints are not provided on a sinusoidal contact surface");
   if (!M.tree)
     return fail(CISCVX_EUNSUPPORTED, "node constraints need every link to be the child of at most one joint");
   if (M.nj > NODE_MAXJ)

@@ -523,6 +523,11 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (tune && !tune_ok(*tune)) return set_error(CISCVX_EINVAL, "invalid ciscvx_tune");
   for (int m = 0; m < n_models; ++m)
     if (!models[m]) return set_error(CISCVX_EINVAL, "null model %d", m);
+  for (int m = 0; m < n_models; ++m)
+    if (models[m]->cpl)
+      return set_error(CISCVX_EUNSUPPORTED,
+                       "model %d has coupled links (eliminated joint forces, terrain or RKF45): "
+                       "batch plans are not provided for it (use ciscvx_discretize)", m);
   for (int i = 0; i < n_inst; ++i) {
     if (model_idx[i] < 0 || model_idx[i] >= n_models)
       return set_error(CISCVX_EINVAL, "instance %d: model index %d out of range", i, model_idx[i]);

@@ -77,6 +77,9 @@ struct DevModel {
   int tree;                          // every link is the child of at most one joint
   int aux;                           // 0: one path-penalty state per contact; 1: Eq. (12) (4 + 1)
   int ny;                            // auxiliary states: nc or 5 nc
+  int jelim;                         // joint reaction forces eliminated (Eq. (3)); coupled path only
+  int scheme;                        // 0: RK4; 1: Runge-Kutta-Fehlberg 4(5) (coupled path only)
+  double ta, tk;                     // contact surface y = ta sin(tk x) (ta = 0: flat; coupled path if not)
   double g;
   // joints and link inertia (node constraints: impact map)
   int jpar[MAXJ], jchi[MAXJ];
@@ -247,10 +250,15 @@ inline int single_cta_threads(long warps) {
 
 }  // namespace ciscvx
 
+namespace ciscvx {
+struct CplTab;
+}
+
 // The opaque model handle of the C ABI.
 struct ciscvx_model {
   ciscvx::DevModel host;  // host copy of the device tables
   ciscvx::DevModel* dev;  // device copy
+  ciscvx::CplTab* cpl;    // coupled-path tables (host), or null for per-link models
   unsigned* status;       // device status word
   int device;             // CUDA device the tables live on
 };

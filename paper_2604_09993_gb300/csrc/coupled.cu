@@ -1,0 +1,765 @@
+// coupled.cu — linearized discretization (Eqs. (14)-(15), (17b); IND with a
+// first-order hold, Sec. VI) for models whose links are coupled within an
+// interval: joint reaction forces eliminated by Eq. (3), the sinusoidal
+// contact surface of Sec. VI-B, the Runge-Kutta-Fehlberg tableau (see
+// coupled.cuh for the row classes).
+//
+// Two kernels per chunk of intervals, joined by a stage-data buffer:
+//  * k_cpl_nominal — lane = interval, FP64.  Integrates the state with the
+//    scheme's stages.  At every stage it evaluates the right-hand side: lever
+//    arms, contact frames and forces, the generalized forces, and with
+//    elimination the L D L^T factor of K = grad C M^-1 grad C^T and the
+//    reaction forces lambda = K^-1 (kappa - grad C M^-1 F), kappa_j =
+//    omega_c^2 r_c - omega_p^2 r_p.  It records, per stage, what the
+//    tangents need (the right-hand side, lever arms, the factor, contact
+//    frames and penalty slopes) and writes defects and penalty increments.
+//  * k_cpl_tangent — thread = (interval, tangent column).  Integrates one
+//    column of [A | B- | B+ | S] with the same stages from the recorded data.
+//    Per stage, the derivative of the right-hand side along the column's
+//    stage tangent: with e = dF + dgrad C^T lambda (the generalized-force
+//    tangent), the reaction-force tangent solves
+//      K dlambda = sum over joint ends s (2 omega r domega + (omega^2 r_perp +
+//                  omega' r) dtheta - e_lin / m - r_perp e_ang / I)
+//    with the recorded factor, and dv' = M^-1 (e + grad C^T dlambda).
+// The FP64 state work runs one interval per lane, so every FP64 instruction
+// has 32 useful lanes; the tangent work (n_x~ + 2 n_u + 1 columns per
+// interval) runs one column per thread in the tangent precision.  Per-lane /
+// per-thread arrays live in shared memory, element major, so a warp's access
+// to one element is one contiguous row.
+#include <algorithm>
+#include <cstring>
+
+#include "coupled.cuh"
+
+namespace ciscvx {
+
+namespace {
+
+template <int SCH>
+struct Scheme {
+  static constexpr int S = SCH ? 6 : 4;    // stages
+  static constexpr int NKS = SCH ? 5 : 1;  // stored slopes per row (RK4 only reads the previous one)
+  __device__ static constexpr int slot(int l) { return NKS == 1 ? 0 : l; }
+};
+
+// Contact surface y = ta sin(tk x) at the world point (xc, yc): approximate
+// signed distance phi = h^c / ||grad h^c||, h^c = y - ta sin(tk x) (Sec. VI-B),
+// unit normal n = grad h^c / ||grad h^c||, tangent t = (n_y, -n_x), and
+// their derivatives along x (nothing depends on y but phi).
+struct Surf {
+  double phi, tx, ty, nx, ny, phix, phiy, dtx, dty, dnx, dny;
+};
+
+__device__ __forceinline__ Surf surface(double ta, double tk, double xc, double yc) {
+  Surf f;
+  if (ta == 0.0) {
+    f.phi = yc;
+    f.tx = 1.0; f.ty = 0.0; f.nx = 0.0; f.ny = 1.0;
+    f.phix = 0.0; f.phiy = 1.0;
+    f.dtx = f.dty = f.dnx = f.dny = 0.0;
+    return f;
+  }
+  double sk, ck;
+  sincos(tk * xc, &sk, &ck);
+  const double hc = fma(-ta, sk, yc);
+  const double gx = -(ta * tk) * ck;       // dh^c/dx
+  const double gp = (ta * tk * tk) * sk;   // d gx / dx
+  const double w = 1.0 / sqrt(fma(gx, gx, 1.0));
+  const double w3g = gp * w * w * w;
+  f.phi = hc * w;
+  f.nx = gx * w; f.ny = w;
+  f.tx = w; f.ty = -f.nx;
+  f.phix = f.nx * fma(-hc * w * w, gp, 1.0);  // gx w (1 - h^c w^2 gp)
+  f.phiy = w;
+  f.dnx = w3g; f.dny = -gx * w3g;             // dn/dx = gp w^3 (1, -gx)
+  f.dtx = -gx * w3g; f.dty = -w3g;            // dt/dx = gp w^3 (-gx, -1)
+  return f;
+}
+
+// pseudo-Huber absolute value sqrt(1 + x^2) - 1 and its slope
+__device__ __forceinline__ double sabs_d(double x, double& d) {
+  const double r = sqrt(fma(x, x, 1.0));
+  d = x / r;
+  return r - 1.0;
+}
+
+// pseudo-Huber ramp h(z) and slope h'(z)
+__device__ __forceinline__ double ramp_d(double z, double& d) {
+  double H;
+  huber(z, H, d);
+  return H;
+}
+
+#define EL(o) sm[(o) * 32]
+#define LK(i, kk) EL(M.n_K + M.noff[i] + (kk) - M.nf[i])
+
+template <typename TP, int SCH>
+__global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplTab M, long i0,
+                                                    long n, int nsub, int layout,
+                                                    const double* __restrict__ X,
+                                                    const double* __restrict__ U,
+                                                    const double* __restrict__ s,
+                                                    TP* __restrict__ sd, double* __restrict__ defect,
+                                                    double* __restrict__ penalty, unsigned* status) {
+  using Sc = Scheme<SCH>;
+  constexpr int NS = Sc::S;
+  extern __shared__ double smem1[];
+  const long t = (long)blockIdx.x * 32 + threadIdx.x;
+  if (t >= n) return;
+  const long k = i0 + t;
+  double* sm = smem1 + threadIdx.x;
+  const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
+  const double* uL = layout == 0 ? U + k * nu : U + 2 * k * nu;
+  const double* uR = layout == 0 ? U + (k + 1) * nu : U + (2 * k + 1) * nu;
+  const double sk = s[k];
+  const double h = 1.0 / nsub;
+  for (int r = 0; r < nxt; ++r) EL(M.n_x + r) = X[k * nxt + r];
+  TP* sdk = sd + (size_t)t * nsub * NS * M.sd_size;
+
+  for (int i = 0; i < nsub; ++i) {
+    for (int j = 0; j < NS; ++j) {
+      const double tau = (i + M.c[j]) * h;
+      const double bj = M.b[j];
+      TP* D = sdk + (size_t)(i * NS + j) * M.sd_size;
+      // stage state and inputs
+      for (int r = 0; r < nxt; ++r) {
+        double v = EL(M.n_x + r);
+        for (int l = 0; l < j; ++l)
+          if (M.a[j][l] != 0.0) v = fma(M.a[j][l] * h, EL(M.n_k + Sc::slot(l) * nxt + r), v);
+        EL(M.n_xs + r) = v;
+      }
+      for (int q = 0; q < nu; ++q) EL(M.n_u + q) = (1.0 - tau) * uL[q] + tau * uR[q];
+      // records F_r and the slope k_r = s F_r of row r
+      auto emit = [&](int r, double F) {
+        D[M.sd_F + r] = TP(F);
+        const double kv = sk * F;
+        if (j < NS - 1) EL(M.n_k + Sc::slot(j) * nxt + r) = kv;
+        EL(M.n_acc + r) = (j == 0) ? bj * kv : fma(bj, kv, EL(M.n_acc + r));
+      };
+      // sin/cos of the link angles; joint lever arms r = R(theta) rho
+      for (int b = 0; b < nb; ++b) {
+        double sn, cs;
+        sincos(EL(M.n_xs + 3 * b + 2), &sn, &cs);
+        EL(M.n_sc + 2 * b) = sn;
+        EL(M.n_sc + 2 * b + 1) = cs;
+      }
+      for (int jj = 0; jj < nj; ++jj) {
+        for (int role = 0; role < 2; ++role) {
+          const int b = role ? M.jpar[jj] : M.jchi[jj];
+          const double* rho = role ? M.jrp[jj] : M.jrc[jj];
+          const double sn = EL(M.n_sc + 2 * b), cs = EL(M.n_sc + 2 * b + 1);
+          const double rx = fma(cs, rho[0], -sn * rho[1]), ry = fma(sn, rho[0], cs * rho[1]);
+          EL(M.n_arm + 4 * jj + 2 * role) = rx;
+          EL(M.n_arm + 4 * jj + 2 * role + 1) = ry;
+          D[M.sd_arm + 4 * jj + 2 * role] = TP(rx);
+          D[M.sd_arm + 4 * jj + 2 * role + 1] = TP(ry);
+        }
+      }
+      // generalized forces (F_x, F_y, torque) per link; QW_b = sum r . F over
+      // the forces applied at points of the link (the -dtheta coefficient of
+      // the torque's derivative)
+      for (int b = 0; b < nb; ++b) {
+        EL(M.n_f + 3 * b) = 0.0;
+        EL(M.n_f + 3 * b + 1) = -M.mass[b] * M.g;
+        EL(M.n_f + 3 * b + 2) = 0.0;
+        EL(M.n_qw + b) = 0.0;
+      }
+      for (int jj = 0; jj < nj; ++jj) {
+        const int c = M.jchi[jj], p = M.jpar[jj];
+        const double tq = EL(M.n_u + jj);
+        EL(M.n_f + 3 * c + 2) += tq;
+        EL(M.n_f + 3 * p + 2) -= tq;
+        if (!M.jelim) {  // reaction force as an input: +lambda on the child, -lambda on the parent
+          const double lx = EL(M.n_u + nj + 2 * jj), ly = EL(M.n_u + nj + 2 * jj + 1);
+          const double rcx = EL(M.n_arm + 4 * jj), rcy = EL(M.n_arm + 4 * jj + 1);
+          const double rpx = EL(M.n_arm + 4 * jj + 2), rpy = EL(M.n_arm + 4 * jj + 3);
+          EL(M.n_f + 3 * c) += lx;
+          EL(M.n_f + 3 * c + 1) += ly;
+          EL(M.n_f + 3 * c + 2) += fma(rcx, ly, -rcy * lx);
+          EL(M.n_f + 3 * p) -= lx;
+          EL(M.n_f + 3 * p + 1) -= ly;
+          EL(M.n_f + 3 * p + 2) -= fma(rpx, ly, -rpy * lx);
+          EL(M.n_qw + c) += fma(rcx, lx, rcy * ly);
+          EL(M.n_qw + p) -= fma(rpx, lx, rpy * ly);
+        }
+      }
+      // contacts: frame, force, auxiliary right-hand sides and their slopes
+      for (int ic = 0; ic < nc; ++ic) {
+        const int b = M.cbody[ic];
+        const double sn = EL(M.n_sc + 2 * b), cs = EL(M.n_sc + 2 * b + 1);
+        const double rx = fma(cs, M.crho[ic][0], -sn * M.crho[ic][1]);
+        const double ry = fma(sn, M.crho[ic][0], cs * M.crho[ic][1]);
+        const Surf f = surface(M.ta, M.tk, EL(M.n_xs + 3 * b) + rx, EL(M.n_xs + 3 * b + 1) + ry);
+        const double u0 = EL(M.n_u + M.ci0 + 3 * ic), u1 = EL(M.n_u + M.ci0 + 3 * ic + 1),
+                     u2 = EL(M.n_u + M.ci0 + 3 * ic + 2);
+        // contact-frame components (tangential, normal)
+        const double ft = M.aux ? u0 : u1 - u2, fn = M.aux ? u1 : u0;
+        const double fx = fma(f.tx, ft, f.nx * fn), fy = fma(f.ty, ft, f.ny * fn);
+        EL(M.n_f + 3 * b) += fx;
+        EL(M.n_f + 3 * b + 1) += fy;
+        EL(M.n_f + 3 * b + 2) += fma(rx, fy, -ry * fx);
+        EL(M.n_qw + b) += fma(rx, fx, ry * fy);
+        TP* Dc = D + M.sd_con + M.cf * ic;
+        Dc[0] = TP(rx); Dc[1] = TP(ry);
+        Dc[2] = TP(f.tx); Dc[3] = TP(f.ty); Dc[4] = TP(f.nx); Dc[5] = TP(f.ny);
+        Dc[6] = TP(fma(f.dtx, ft, f.dnx * fn));  // dF/dx_c at fixed inputs
+        Dc[7] = TP(fma(f.dty, ft, f.dny * fn));
+        Dc[8] = TP(f.phix); Dc[9] = TP(f.phiy);
+        const double mu = M.mu[ic];
+        if (!M.aux) {
+          // Omega = h(-lambda_n) + h(-lambda_t+) + h(-lambda_t-) + h(-phi) + h(lambda_t+ + lambda_t- - mu lambda_n)
+          double d1, d2, d3, dp, d5;
+          const double H = ramp_d(-u0, d1) + ramp_d(-u1, d2) + ramp_d(-u2, d3) + ramp_d(-f.phi, dp) +
+                           ramp_d(u1 + u2 - mu * u0, d5);
+          Dc[10] = TP(-dp);
+          Dc[11] = TP(-d1 - mu * d5);
+          Dc[12] = TP(-d2 + d5);
+          Dc[13] = TP(-d3 + d5);
+          emit(6 * nb + ic, H);
+        } else {
+          // Eq. (12): phi_n, lambda^c, gamma, rho^c, then the path penalty
+          const double gam = u2;
+          const double om = EL(M.n_xs + nq + 3 * b + 2);
+          const double vcx = fma(-om, ry, EL(M.n_xs + nq + 3 * b));
+          const double vcy = fma(om, rx, EL(M.n_xs + nq + 3 * b + 1));
+          const double rt = 1.0 / sqrt(fma(ft, ft, 1.0));
+          double dmn, dft;
+          const double rho_c = sabs_d(mu * fn, dmn) - sabs_d(ft, dft);
+          const double lam = fma(f.tx, vcx, f.ty * vcy) + gam * (ft * rt);
+          double dfn_, dph, dga, drh;
+          const double H = ramp_d(-fn, dfn_) + ramp_d(-f.phi, dph) + ramp_d(-gam, dga) +
+                           ramp_d(-rho_c, drh);
+          const double rho_ft = -dft, rho_fn = mu * dmn;
+          Dc[10] = TP(-dph);
+          Dc[11] = TP(drh * dft);            // dH/dphi_t = -h'(-rho) drho/dphi_t
+          Dc[12] = TP(-dfn_ - drh * rho_fn);  // dH/dphi_n
+          Dc[13] = TP(-dga);                 // dH/dgamma
+          Dc[14] = TP(vcx); Dc[15] = TP(vcy);
+          Dc[16] = TP(fma(f.dtx, vcx, f.dty * vcy));  // (dt/dx_c) . v_c
+          Dc[17] = TP(gam * rt * rt * rt);            // dlambda^c/dphi_t
+          Dc[18] = TP(ft * rt);                       // dlambda^c/dgamma
+          Dc[19] = TP(rho_ft);
+          Dc[20] = TP(rho_fn);
+          emit(6 * nb + 4 * ic, fn);
+          emit(6 * nb + 4 * ic + 1, lam);
+          emit(6 * nb + 4 * ic + 2, gam);
+          emit(6 * nb + 4 * ic + 3, rho_c);
+          emit(6 * nb + 4 * nc + ic, H);
+        }
+      }
+      // Eq. (3): K lambda = kappa - grad C M^-1 F, then F += grad C^T lambda
+      if (M.jelim && nk > 0) {
+        for (int r1 = 0; r1 < nk; ++r1) {
+          const int j1 = M.nord[r1 >> 1], a1 = r1 & 1;
+          for (int r2 = M.nf[r1]; r2 <= r1; ++r2) {
+            const int j2 = M.nord[r2 >> 1], a2 = r2 & 1;
+            double acc = 0.0;
+            for (int u = 0; u < 2; ++u) {
+              const int b1 = u ? M.jpar[j1] : M.jchi[j1];
+              // perp(r) = (-r_y, r_x), component a1
+              const double p1 = a1 ? EL(M.n_arm + 4 * j1 + 2 * u) : -EL(M.n_arm + 4 * j1 + 2 * u + 1);
+              for (int v = 0; v < 2; ++v) {
+                const int b2 = v ? M.jpar[j2] : M.jchi[j2];
+                if (b1 != b2) continue;
+                const double p2 =
+                    a2 ? EL(M.n_arm + 4 * j2 + 2 * v) : -EL(M.n_arm + 4 * j2 + 2 * v + 1);
+                const double e = fma(p1 * p2, M.iinv[b1], (a1 == a2) ? M.minv[b1] : 0.0);
+                acc = (u == v) ? acc + e : acc - e;
+              }
+            }
+            LK(r1, r2) = acc;
+          }
+        }
+        // Cholesky within the envelopes (diagonal slot: 1 / L_ii), then unit
+        // L = L_c diag(1 / L_c,kk) and 1/D = (1 / L_c,ii)^2
+        for (int ii = 0; ii < nk; ++ii) {
+          const int fi = M.nf[ii];
+          for (int kk = fi; kk < ii; ++kk) {
+            double acc = LK(ii, kk);
+            const int m0 = fi > M.nf[kk] ? fi : M.nf[kk];
+            for (int m = m0; m < kk; ++m) acc = fma(-LK(ii, m), LK(kk, m), acc);
+            LK(ii, kk) = acc * LK(kk, kk);
+          }
+          double d = LK(ii, ii);
+          for (int m = fi; m < ii; ++m) d = fma(-LK(ii, m), LK(ii, m), d);
+          LK(ii, ii) = 1.0 / sqrt(d);
+        }
+        for (int ii = 0; ii < nk; ++ii)
+          for (int kk = M.nf[ii]; kk < ii; ++kk) LK(ii, kk) *= LK(kk, kk);
+        for (int ii = 0; ii < nk; ++ii) LK(ii, ii) = LK(ii, ii) * LK(ii, ii);
+        for (int e = 0; e < M.nsky; ++e) D[M.sd_K + e] = TP(EL(M.n_K + e));
+        // right-hand side, joints in factor order
+        for (int jj = 0; jj < nj; ++jj) {
+          double a0 = 0.0, a1 = 0.0;
+          for (int role = 0; role < 2; ++role) {
+            const int b = role ? M.jpar[jj] : M.jchi[jj];
+            const double rx = EL(M.n_arm + 4 * jj + 2 * role), ry = EL(M.n_arm + 4 * jj + 2 * role + 1);
+            const double om = EL(M.n_xs + nq + 3 * b + 2);
+            const double aa = EL(M.n_f + 3 * b + 2) * M.iinv[b];
+            const double c0 = fma(om * om, rx, fma(ry, aa, -EL(M.n_f + 3 * b) * M.minv[b]));
+            const double c1 = fma(om * om, ry, fma(-rx, aa, -EL(M.n_f + 3 * b + 1) * M.minv[b]));
+            if (role) { a0 -= c0; a1 -= c1; } else { a0 += c0; a1 += c1; }
+          }
+          EL(M.n_lam + 2 * M.npos[jj]) = a0;
+          EL(M.n_lam + 2 * M.npos[jj] + 1) = a1;
+        }
+        for (int ii = 1; ii < nk; ++ii) {
+          double acc = EL(M.n_lam + ii);
+          for (int kk = M.nf[ii]; kk < ii; ++kk) acc = fma(-LK(ii, kk), EL(M.n_lam + kk), acc);
+          EL(M.n_lam + ii) = acc;
+        }
+        for (int ii = nk - 1; ii >= 0; --ii) {
+          double acc = EL(M.n_lam + ii) * LK(ii, ii);
+          for (int kk = ii + 1; kk < nk; ++kk)
+            if (M.nf[kk] <= ii) acc = fma(-LK(kk, ii), EL(M.n_lam + kk), acc);
+          EL(M.n_lam + ii) = acc;
+        }
+        for (int jj = 0; jj < nj; ++jj) {
+          const double lx = EL(M.n_lam + 2 * M.npos[jj]), ly = EL(M.n_lam + 2 * M.npos[jj] + 1);
+          const int c = M.jchi[jj], p = M.jpar[jj];
+          const double rcx = EL(M.n_arm + 4 * jj), rcy = EL(M.n_arm + 4 * jj + 1);
+          const double rpx = EL(M.n_arm + 4 * jj + 2), rpy = EL(M.n_arm + 4 * jj + 3);
+          EL(M.n_f + 3 * c) += lx;
+          EL(M.n_f + 3 * c + 1) += ly;
+          EL(M.n_f + 3 * c + 2) += fma(rcx, ly, -rcy * lx);
+          EL(M.n_f + 3 * p) -= lx;
+          EL(M.n_f + 3 * p + 1) -= ly;
+          EL(M.n_f + 3 * p + 2) -= fma(rpx, ly, -rpy * lx);
+          EL(M.n_qw + c) += fma(rcx, lx, rcy * ly);
+          EL(M.n_qw + p) -= fma(rpx, lx, rpy * ly);
+        }
+      }
+      for (int b = 0; b < nb; ++b) D[M.sd_qw + b] = TP(EL(M.n_qw + b));
+      // q' = v, v' = M^-1 F
+      for (int r = 0; r < nq; ++r) emit(r, EL(M.n_xs + nq + r));
+      for (int b = 0; b < nb; ++b) {
+        emit(nq + 3 * b, EL(M.n_f + 3 * b) * M.minv[b]);
+        emit(nq + 3 * b + 1, EL(M.n_f + 3 * b + 1) * M.minv[b]);
+        emit(nq + 3 * b + 2, EL(M.n_f + 3 * b + 2) * M.iinv[b]);
+      }
+    }
+    for (int r = 0; r < nxt; ++r) EL(M.n_x + r) = fma(h, EL(M.n_acc + r), EL(M.n_x + r));
+  }
+  double chk = 0.0;
+  for (int r = 0; r < nxt; ++r) {
+    const double d = EL(M.n_x + r) - X[(k + 1) * nxt + r];
+    defect[k * nxt + r] = d;
+    chk += d;
+  }
+  for (int ic = 0; ic < nc; ++ic)
+    penalty[k * nc + ic] = EL(M.n_x + M.pen0 + ic) - X[k * nxt + M.pen0 + ic];
+  if (!isfinite(chk)) atomicOr(status, ST_NONFINITE);
+}
+
+#undef LK
+
+#define ET(o) tm[(o) * bs]
+
+template <typename TP, int SCH>
+__global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n, int nsub,
+                              const double* __restrict__ s, const TP* __restrict__ sd,
+                              TP* __restrict__ A, TP* __restrict__ Bm, TP* __restrict__ Bp,
+                              TP* __restrict__ S, unsigned* status) {
+  using Sc = Scheme<SCH>;
+  constexpr int NS = Sc::S;
+  extern __shared__ __align__(16) unsigned char smem2[];
+  const int bs = blockDim.x;
+  TP* tm = reinterpret_cast<TP*>(smem2) + threadIdx.x;
+  const int C = M.C;
+  const long g = (long)blockIdx.x * bs + threadIdx.x;
+  const long t = g / C;
+  if (t >= n) return;
+  const int col = (int)(g - t * C);
+  const long k = i0 + t;
+  const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
+  const int nl = M.nlive, nqd = M.nquad;
+  int qin = -1;
+  bool right = false, scol = false;
+  if (col >= nxt) {
+    if (col < nxt + nu) qin = col - nxt;
+    else if (col < nxt + 2 * nu) { qin = col - nxt - nu; right = true; }
+    else scol = true;
+  }
+  for (int l = 0; l < nl; ++l) ET(M.t_pl + l) = TP(0);
+  for (int q = 0; q < nqd; ++q) ET(M.t_pq + q) = TP(0);
+  if (col < nxt) {
+    if (M.lrow[col] >= 0) ET(M.t_pl + M.lrow[col]) = TP(1);
+    else ET(M.t_pq + M.qrow[col]) = TP(1);
+  }
+  const TP sk = TP(s[k]);
+  const TP h = TP(1.0 / nsub);
+  const TP hsk = h * sk;
+  const TP* sdk = sd + (size_t)t * nsub * NS * M.sd_size;
+  // the column's input: a torque, a reaction force (inputs only without
+  // elimination) or a contact input
+  const int ci0 = M.ci0;
+  const bool q_torque = qin >= 0 && qin < nj;
+  const bool q_force = qin >= nj && qin < ci0;
+  const int q_con = qin >= ci0 ? (qin - ci0) / 3 : -1;
+  const int q_comp = qin >= ci0 ? (qin - ci0) % 3 : 0;
+
+  for (int i = 0; i < nsub; ++i) {
+    // quadrature rows: p += h s v at the substep start
+    for (int b = 0; b < nb; ++b) {
+      if (M.contact[b] >= 0) continue;
+      for (int c2 = 0; c2 < 2; ++c2)
+        ET(M.t_pq + M.qrow[3 * b + c2]) += hsk * ET(M.t_pq + M.qrow[nq + 3 * b + c2]);
+    }
+    for (int j = 0; j < NS; ++j) {
+      const TP* D = sdk + (size_t)(i * NS + j) * M.sd_size;
+      const TP* F = D + M.sd_F;
+      const TP bj = TP(M.b[j]), hbj = h * bj, h2b = h * h * sk * TP(M.beta[j]);
+      // stage tangent of the live rows
+      for (int l = 0; l < nl; ++l) {
+        TP v = ET(M.t_pl + l);
+        for (int m = 0; m < j; ++m)
+          if (M.a[j][m] != 0.0) v += TP(M.a[j][m]) * h * ET(M.t_k + Sc::slot(m) * nl + l);
+        ET(M.t_xs + l) = v;
+      }
+      const TP tau = (TP(i) + TP(M.c[j])) * h;
+      const TP w = qin < 0 ? TP(0) : (right ? tau : TP(1) - tau);
+      // generalized-force tangent e: -dtheta QW (moving application points) + direct inputs
+      for (int b = 0; b < nb; ++b) {
+        ET(M.t_e + 3 * b) = TP(0);
+        ET(M.t_e + 3 * b + 1) = TP(0);
+        ET(M.t_e + 3 * b + 2) = -ET(M.t_xs + M.lrow[3 * b + 2]) * D[M.sd_qw + b];
+      }
+      if (q_torque) {
+        ET(M.t_e + 3 * M.jchi[qin] + 2) += w;
+        ET(M.t_e + 3 * M.jpar[qin] + 2) -= w;
+      } else if (q_force) {
+        const int jj = (qin - nj) >> 1, cp = (qin - nj) & 1;
+        for (int role = 0; role < 2; ++role) {
+          const int b = role ? M.jpar[jj] : M.jchi[jj];
+          const TP rx = D[M.sd_arm + 4 * jj + 2 * role], ry = D[M.sd_arm + 4 * jj + 2 * role + 1];
+          const TP sw = role ? -w : w;
+          ET(M.t_e + 3 * b + cp) += sw;
+          ET(M.t_e + 3 * b + 2) += sw * (cp ? rx : -ry);
+        }
+      }
+      // contacts: force tangent and the auxiliary rows
+      for (int ic = 0; ic < nc; ++ic) {
+        const int b = M.cbody[ic];
+        const TP* Dc = D + M.sd_con + M.cf * ic;
+        const TP rx = Dc[0], ry = Dc[1];
+        const TP dth = ET(M.t_xs + M.lrow[3 * b + 2]);
+        const TP dxc = ET(M.t_xs + M.lrow[3 * b]) - ry * dth;
+        const TP dyc = ET(M.t_xs + M.lrow[3 * b + 1]) + rx * dth;
+        TP dft = TP(0), dfn = TP(0), dga = TP(0);
+        if (q_con == ic) {
+          if (M.aux) {
+            if (q_comp == 0) dft = w; else if (q_comp == 1) dfn = w; else dga = w;
+          } else {
+            if (q_comp == 0) dfn = w; else if (q_comp == 1) dft = w; else dft = -w;
+          }
+        }
+        const TP dfx = Dc[2] * dft + Dc[4] * dfn + Dc[6] * dxc;
+        const TP dfy = Dc[3] * dft + Dc[5] * dfn + Dc[7] * dxc;
+        ET(M.t_e + 3 * b) += dfx;
+        ET(M.t_e + 3 * b + 1) += dfy;
+        ET(M.t_e + 3 * b + 2) += rx * dfy - ry * dfx;
+        const TP dphi = Dc[8] * dxc + Dc[9] * dyc;
+        auto quad = [&](int row, TP dy) {
+          TP kv = sk * dy;
+          if (scol) kv += F[row];
+          ET(M.t_pq + M.qrow[row]) += hbj * kv;
+        };
+        if (!M.aux) {
+          TP dy = Dc[10] * dphi;
+          if (q_con == ic) dy += Dc[11 + q_comp] * w;
+          quad(6 * nb + ic, dy);
+        } else {
+          // lambda^c = t . v_c + gamma phi_t / sqrt(1 + phi_t^2), v_c = (v_x - omega r_y, v_y + omega r_x)
+          const TP om = F[3 * b + 2];
+          const TP dom = ET(M.t_xs + M.lrow[nq + 3 * b + 2]);
+          const TP dvcx = ET(M.t_xs + M.lrow[nq + 3 * b]) - dom * ry - om * rx * dth;
+          const TP dvcy = ET(M.t_xs + M.lrow[nq + 3 * b + 1]) + dom * rx - om * ry * dth;
+          const TP dlam = Dc[16] * dxc + Dc[2] * dvcx + Dc[3] * dvcy + Dc[17] * dft + Dc[18] * dga;
+          quad(6 * nb + 4 * ic, dfn);
+          quad(6 * nb + 4 * ic + 1, dlam);
+          quad(6 * nb + 4 * ic + 2, dga);
+          quad(6 * nb + 4 * ic + 3, Dc[19] * dft + Dc[20] * dfn);
+          quad(6 * nb + 4 * nc + ic, Dc[10] * dphi + Dc[11] * dft + Dc[12] * dfn + Dc[13] * dga);
+        }
+      }
+      // Eq. (3): K dlambda = sum over joint ends s (alpha domega + beta dtheta - e_lin / m - perp(r) e_ang / I)
+      if (M.jelim && nk > 0) {
+        for (int jj = 0; jj < nj; ++jj) {
+          TP a0 = TP(0), a1 = TP(0);
+          for (int role = 0; role < 2; ++role) {
+            const int b = role ? M.jpar[jj] : M.jchi[jj];
+            const TP rx = D[M.sd_arm + 4 * jj + 2 * role], ry = D[M.sd_arm + 4 * jj + 2 * role + 1];
+            const TP om = F[3 * b + 2], omd = F[nq + 3 * b + 2];
+            const TP dth = ET(M.t_xs + M.lrow[3 * b + 2]), dom = ET(M.t_xs + M.lrow[nq + 3 * b + 2]);
+            const TP mi = TP(M.minv[b]), ii = TP(M.iinv[b]);
+            const TP ea = ET(M.t_e + 3 * b + 2) * ii;
+            // alpha = 2 omega r, beta = omega^2 perp(r) + omega' r, perp(r) = (-r_y, r_x)
+            const TP c0 = TP(2) * om * rx * dom + (-om * om * ry + omd * rx) * dth -
+                          ET(M.t_e + 3 * b) * mi + ry * ea;
+            const TP c1 = TP(2) * om * ry * dom + (om * om * rx + omd * ry) * dth -
+                          ET(M.t_e + 3 * b + 1) * mi - rx * ea;
+            if (role) { a0 -= c0; a1 -= c1; } else { a0 += c0; a1 += c1; }
+          }
+          ET(M.t_x + 2 * M.npos[jj]) = a0;
+          ET(M.t_x + 2 * M.npos[jj] + 1) = a1;
+        }
+        const TP* Kf = D + M.sd_K;
+        for (int ii = 1; ii < nk; ++ii) {
+          TP acc = ET(M.t_x + ii);
+          const TP* row = Kf + M.noff[ii] - M.nf[ii];
+          for (int kk = M.nf[ii]; kk < ii; ++kk) acc -= row[kk] * ET(M.t_x + kk);
+          ET(M.t_x + ii) = acc;
+        }
+        for (int ii = nk - 1; ii >= 0; --ii) {
+          TP acc = ET(M.t_x + ii) * Kf[M.noff[ii] + ii - M.nf[ii]];
+          for (int kk = ii + 1; kk < nk; ++kk)
+            if (M.nf[kk] <= ii) acc -= Kf[M.noff[kk] + ii - M.nf[kk]] * ET(M.t_x + kk);
+          ET(M.t_x + ii) = acc;
+        }
+        for (int jj = 0; jj < nj; ++jj) {
+          const TP lx = ET(M.t_x + 2 * M.npos[jj]), ly = ET(M.t_x + 2 * M.npos[jj] + 1);
+          for (int role = 0; role < 2; ++role) {
+            const int b = role ? M.jpar[jj] : M.jchi[jj];
+            const TP rx = D[M.sd_arm + 4 * jj + 2 * role], ry = D[M.sd_arm + 4 * jj + 2 * role + 1];
+            const TP sx = role ? -lx : lx, sy = role ? -ly : ly;
+            ET(M.t_e + 3 * b) += sx;
+            ET(M.t_e + 3 * b + 1) += sy;
+            ET(M.t_e + 3 * b + 2) += rx * sy - ry * sx;
+          }
+        }
+      }
+      // slopes: live rows (RK stages) and quadrature rows
+      auto live = [&](int row, TP dy) {
+        TP kv = sk * dy;
+        if (scol) kv += F[row];
+        const int l = M.lrow[row];
+        if (j < NS - 1) ET(M.t_k + Sc::slot(j) * nl + l) = kv;
+        ET(M.t_acc + l) = (j == 0) ? bj * kv : ET(M.t_acc + l) + bj * kv;
+      };
+      for (int b = 0; b < nb; ++b) {
+        const TP mi = TP(M.minv[b]);
+        const TP dv0 = ET(M.t_e + 3 * b) * mi, dv1 = ET(M.t_e + 3 * b + 1) * mi;
+        const TP dw = ET(M.t_e + 3 * b + 2) * TP(M.iinv[b]);
+        live(3 * b + 2, ET(M.t_xs + M.lrow[nq + 3 * b + 2]));
+        live(nq + 3 * b + 2, dw);
+        if (M.contact[b] >= 0) {
+          live(3 * b, ET(M.t_xs + M.lrow[nq + 3 * b]));
+          live(3 * b + 1, ET(M.t_xs + M.lrow[nq + 3 * b + 1]));
+          live(nq + 3 * b, dv0);
+          live(nq + 3 * b + 1, dv1);
+        } else {
+          const TP dv[2] = {dv0, dv1};
+          for (int c2 = 0; c2 < 2; ++c2) {
+            TP kv = sk * dv[c2];
+            if (scol) kv += F[nq + 3 * b + c2];
+            TP& pq = ET(M.t_pq + M.qrow[3 * b + c2]);
+            pq += h2b * kv;
+            if (scol) pq += hbj * F[3 * b + c2];
+            ET(M.t_pq + M.qrow[nq + 3 * b + c2]) += hbj * kv;
+          }
+        }
+      }
+    }
+    for (int l = 0; l < nl; ++l) ET(M.t_pl + l) += h * ET(M.t_acc + l);
+  }
+  // column `col` of [A | B- | B+ | S]
+  TP* out;
+  size_t stride;
+  if (col < nxt) { out = A + (size_t)k * nxt * nxt + col; stride = nxt; }
+  else if (!scol) { out = (right ? Bp : Bm) + (size_t)k * nxt * nu + qin; stride = nu; }
+  else { out = S + (size_t)k * nxt; stride = 1; }
+  float chk = 0.0f;
+  for (int r = 0; r < nxt; ++r) {
+    const TP v = M.lrow[r] >= 0 ? ET(M.t_pl + M.lrow[r]) : ET(M.t_pq + M.qrow[r]);
+    out[(size_t)r * stride] = v;
+    chk += float(v);
+  }
+  if (!isfinite(chk)) atomicOr(status, ST_NONFINITE);
+}
+
+#undef ET
+#undef EL
+
+// Tangent-kernel block size: the largest of 128 / 64 / 32 threads whose
+// scratch fits in 76 KB (two or more blocks per SM).
+template <typename TP>
+int tangent_block(const CplTab& T) {
+  for (int bs = 128; bs > 32; bs /= 2)
+    if ((size_t)bs * T.t_size * sizeof(TP) <= 76u * 1024u) return bs;
+  return 32;
+}
+
+template <typename TP, int SCH>
+cudaError_t run(const CplTab& T, int N, int nsub, int layout, const double* X, const double* U,
+                const double* s, void* A, void* Bm, void* Bp, void* S, double* defect,
+                double* penalty, void* ws, long chunk, unsigned* status, cudaStream_t st) {
+  const size_t sm1 = (size_t)T.n_size * sizeof(double) * 32;
+  const int bs = tangent_block<TP>(T);
+  const size_t sm2 = (size_t)bs * T.t_size * sizeof(TP);
+  cudaError_t e = cudaFuncSetAttribute(k_cpl_nominal<TP, SCH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cpl_tangent<TP, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm2);
+  if (e != cudaSuccess) return e;
+  for (long i0 = 0; i0 < N; i0 += chunk) {
+    const long n = std::min<long>(chunk, N - i0);
+    k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
+        T, i0, n, nsub, layout, X, U, s, (TP*)ws, defect, penalty, status);
+    const long threads = n * T.C;
+    k_cpl_tangent<TP, SCH><<<(unsigned)((threads + bs - 1) / bs), bs, sm2, st>>>(
+        T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Butcher tableaux: classical RK4 and Fehlberg's 4(5) pair advanced with its
+// fifth-order weights (the published coefficients).
+void set_tableau(int scheme, CplTab& T) {
+  std::memset(T.c, 0, sizeof T.c);
+  std::memset(T.a, 0, sizeof T.a);
+  std::memset(T.b, 0, sizeof T.b);
+  if (scheme == 0) {
+    T.stages = 4;
+    T.nks = 1;
+    const double c[4] = {0.0, 0.5, 0.5, 1.0}, b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    for (int i = 0; i < 4; ++i) { T.c[i] = c[i]; T.b[i] = b[i]; }
+    T.a[1][0] = 0.5; T.a[2][1] = 0.5; T.a[3][2] = 1.0;
+  } else {
+    T.stages = 6;
+    T.nks = 5;
+    const double c[6] = {0.0, 0.25, 0.375, 12.0 / 13.0, 1.0, 0.5};
+    const double b[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+    for (int i = 0; i < 6; ++i) { T.c[i] = c[i]; T.b[i] = b[i]; }
+    T.a[1][0] = 0.25;
+    T.a[2][0] = 3.0 / 32.0; T.a[2][1] = 9.0 / 32.0;
+    T.a[3][0] = 1932.0 / 2197.0; T.a[3][1] = -7200.0 / 2197.0; T.a[3][2] = 7296.0 / 2197.0;
+    T.a[4][0] = 439.0 / 216.0; T.a[4][1] = -8.0; T.a[4][2] = 3680.0 / 513.0; T.a[4][3] = -845.0 / 4104.0;
+    T.a[5][0] = -8.0 / 27.0; T.a[5][1] = 2.0; T.a[5][2] = -3544.0 / 2565.0; T.a[5][3] = 1859.0 / 4104.0;
+    T.a[5][4] = -11.0 / 40.0;
+  }
+  for (int l = 0; l < CPL_MAXSTAGE; ++l) {
+    double bl = 0.0;
+    for (int j = 0; j < CPL_MAXSTAGE; ++j) bl += T.b[j] * T.a[j][l];
+    T.beta[l] = bl;
+  }
+}
+
+}  // namespace
+
+const char* cpl_build(const DevModel& M, CplTab& T) {
+  std::memset(&T, 0, sizeof T);
+  const int nb = M.nb, nj = M.nj, nc = M.nc;
+  T.nb = nb; T.nj = nj; T.nc = nc; T.nxt = M.nxt; T.nu = M.nu; T.ny = M.ny;
+  T.aux = M.aux; T.jelim = M.jelim; T.scheme = M.scheme;
+  T.C = M.nxt + 2 * M.nu + 1;
+  T.ci0 = (M.jelim ? 1 : 3) * nj;
+  T.pen0 = 6 * nb + (M.aux ? 4 * nc : 0);
+  T.g = M.g; T.ta = M.ta; T.tk = M.tk;
+  if (M.jelim && nj > 0) {
+    if (!M.tree) return "eliminated joint forces need every link to be the child of at most one joint";
+    if (nj > CPL_MAXJ) return "eliminated joint forces support at most 12 joints";
+    for (int b = 0; b < nb; ++b)
+      if (M.nadj[b] > NODE_MAXADJ) return "eliminated joint forces support at most 8 joints on one link";
+    T.nk = 2 * nj;
+    T.nsky = M.noff[2 * nj];
+    for (int j = 0; j < nj; ++j) { T.npos[j] = M.npos[j]; T.nord[j] = M.nord[j]; }
+    for (int i = 0; i < 2 * nj; ++i) T.nf[i] = M.nf[i];
+    for (int i = 0; i <= 2 * nj; ++i) T.noff[i] = M.noff[i];
+  }
+  set_tableau(M.scheme, T);
+  for (int b = 0; b < nb; ++b) {
+    T.mass[b] = M.mass[b]; T.inertia[b] = M.inertia[b];
+    T.minv[b] = M.minv[b]; T.iinv[b] = M.iinv[b];
+    T.contact[b] = M.body[b].contact;
+    T.nadj[b] = std::min(M.nadj[b], NODE_MAXADJ);
+    for (int t = 0; t < T.nadj[b]; ++t) T.adj[b][t] = (unsigned char)M.adj[b][t];
+    if (M.body[b].contact >= 0) {
+      const int i = M.body[b].contact;
+      T.cbody[i] = b;
+      T.crho[i][0] = M.body[b].crho[0];
+      T.crho[i][1] = M.body[b].crho[1];
+      T.mu[i] = M.body[b].mu;
+    }
+  }
+  for (int j = 0; j < nj; ++j) {
+    T.jpar[j] = M.jpar[j]; T.jchi[j] = M.jchi[j];
+    T.jrp[j][0] = M.jrp[j][0]; T.jrp[j][1] = M.jrp[j][1];
+    T.jrc[j][0] = M.jrc[j][0]; T.jrc[j][1] = M.jrc[j][1];
+  }
+  // row classes
+  const int nq = 3 * nb;
+  for (int r = 0; r < M.nxt; ++r) { T.lrow[r] = -1; T.qrow[r] = -1; }
+  int nl = 0, nqd = 0;
+  for (int b = 0; b < nb; ++b) {
+    T.lrow[3 * b + 2] = (short)nl++;
+    T.lrow[nq + 3 * b + 2] = (short)nl++;
+    const bool foot = M.body[b].contact >= 0;
+    for (int c2 = 0; c2 < 2; ++c2) {
+      if (foot) {
+        T.lrow[3 * b + c2] = (short)nl++;
+        T.lrow[nq + 3 * b + c2] = (short)nl++;
+      } else {
+        T.qrow[3 * b + c2] = (short)nqd++;
+        T.qrow[nq + 3 * b + c2] = (short)nqd++;
+      }
+    }
+  }
+  for (int r = 6 * nb; r < M.nxt; ++r) T.qrow[r] = (short)nqd++;
+  T.nlive = nl;
+  T.nquad = nqd;
+  // stage data
+  T.cf = M.aux ? CPL_CF1 : CPL_CF0;
+  T.sd_arm = 0;
+  T.sd_qw = T.sd_arm + 4 * nj;
+  T.sd_F = T.sd_qw + nb;
+  T.sd_K = T.sd_F + M.nxt;
+  T.sd_con = T.sd_K + T.nsky;
+  T.sd_size = T.sd_con + T.cf * nc;
+  // nominal kernel scratch (doubles per lane)
+  const int nxt = M.nxt;
+  T.n_x = 0;
+  T.n_xs = T.n_x + nxt;
+  T.n_acc = T.n_xs + nxt;
+  T.n_k = T.n_acc + nxt;
+  T.n_u = T.n_k + T.nks * nxt;
+  T.n_f = T.n_u + M.nu;
+  T.n_arm = T.n_f + 3 * nb;
+  T.n_sc = T.n_arm + 4 * nj;
+  T.n_K = T.n_sc + 2 * nb;
+  T.n_lam = T.n_K + T.nsky;
+  T.n_qw = T.n_lam + T.nk;
+  T.n_size = T.n_qw + nb;
+  // tangent kernel scratch (elements per thread)
+  T.t_pl = 0;
+  T.t_acc = T.t_pl + nl;
+  T.t_k = T.t_acc + nl;
+  T.t_xs = T.t_k + T.nks * nl;
+  T.t_pq = T.t_xs + nl;
+  T.t_e = T.t_pq + nqd;
+  T.t_x = T.t_e + 3 * nb;
+  T.t_size = T.t_x + T.nk;
+  if ((size_t)T.n_size * sizeof(double) * 32 > 220u * 1024u)
+    return "model too large for the coupled path's shared memory";
+  return nullptr;
+}
+
+size_t cpl_interval_bytes(const CplTab& T, int nsub, int prec) {
+  const size_t el = prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+  return (size_t)nsub * T.stages * T.sd_size * el;
+}
+
+cudaError_t launch_coupled(const CplTab& T, int N, int nsub, int prec, int layout, const double* X,
+                           const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
+                           double* defect, double* penalty, void* ws, long chunk,
+                           unsigned* status, cudaStream_t st) {
+  if (prec == CISCVX_FP64)
+    return T.scheme ? run<double, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st)
+                    : run<double, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st);
+  return T.scheme ? run<float, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st)
+                  : run<float, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st);
+}
+
+}  // namespace ciscvx

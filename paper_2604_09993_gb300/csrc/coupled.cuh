@@ -1,0 +1,81 @@
+// coupled.cuh — tables of the coupled-dynamics path (coupled.cu): models
+// whose links are coupled within an interval, which the per-link kernels
+// cannot treat.  That is the case when
+//  * the joint reaction forces are eliminated at the acceleration level
+//    (Sec. II-A, Eq. (3)): every link's acceleration then depends on every
+//    link's angle and rate through the solve of K lambda = ..., K = grad C
+//    M^-1 grad C^T, so the Jacobian blocks are dense in those rows;
+//  * the contact surface is the sinusoid of Sec. VI-B: the contact force's
+//    direction and the signed distance depend on the foot's x position;
+//  * the integrator is the Runge-Kutta-Fehlberg 4(5) tableau (Sec. VI).
+//
+// Rows of the state fall into two classes.  "Live" rows feed back into the
+// right-hand side or into the stage values another row needs: theta and
+// omega of every link and (p_x, p_y, v_x, v_y) of every link that carries a
+// contact.  They are integrated with the full Runge-Kutta stage recursion.
+// The other rows — (p_x, p_y, v_x, v_y) of links without a contact and the
+// auxiliary states — never feed back, so their tangents are quadratures of
+// the stage slopes: v += h sum_j b_j k_j, and, since p' = s v, p += h s v +
+// h^2 s sum_l beta_l kv_l with beta_l = sum_j b_j a_jl (exact for any explicit
+// tableau), which needs no stage storage.
+#pragma once
+
+#include "common.cuh"
+
+namespace ciscvx {
+
+constexpr int CPL_MAXJ = NODE_MAXJ;                 // joints (the KKT system has 2 n_j rows)
+constexpr int CPL_MAXROW = 6 * MAXB + 5 * MAXB;     // state rows n_x~
+constexpr int CPL_MAXSKY = NODE_MAXJ * (2 * NODE_MAXJ + 1);  // skyline entries of K (<= n_k (n_k+1) / 2)
+constexpr int CPL_MAXSTAGE = 6;
+// per-contact stage fields: aux model 0 / aux model 1 (see coupled.cu)
+constexpr int CPL_CF0 = 14, CPL_CF1 = 21;
+
+struct CplTab {
+  int nb, nj, nc, nxt, nu, ny, aux, jelim, scheme;
+  int C;       // tangent columns n_x~ + 2 n_u + 1
+  int nk;      // KKT rows 2 n_j (0 without elimination)
+  int nsky;    // skyline entries of K
+  int nlive, nquad;
+  int ci0;     // first contact input (n_j with elimination, 3 n_j without)
+  int pen0;    // first path-penalty state row (the penalty output's rows)
+  int stages;  // tableau stages
+  int nks;     // stored stage slopes per row (1 for RK4: only the previous one is used)
+  // stage data (per interval, per substep, per stage; in the tangent precision)
+  int sd_arm, sd_qw, sd_F, sd_K, sd_con, sd_size, cf;
+  // per-lane scratch of the nominal kernel (doubles, element major)
+  int n_x, n_xs, n_acc, n_k, n_u, n_f, n_arm, n_sc, n_K, n_lam, n_qw, n_size;
+  // per-thread scratch of the tangent kernel (tangent precision, element major)
+  int t_pl, t_acc, t_k, t_xs, t_pq, t_e, t_x, t_size;
+  double g, ta, tk;  // gravity; contact surface y = ta sin(tk x)
+  double c[CPL_MAXSTAGE], a[CPL_MAXSTAGE][CPL_MAXSTAGE], b[CPL_MAXSTAGE], beta[CPL_MAXSTAGE];
+  double mass[MAXB], inertia[MAXB], minv[MAXB], iinv[MAXB];
+  int nadj[MAXB];
+  unsigned char adj[MAXB][NODE_MAXADJ];  // (joint << 1) | (1 if the link is the joint's parent)
+  int contact[MAXB];                     // contact on the link, or -1
+  int jpar[MAXJ], jchi[MAXJ];
+  double jrp[MAXJ][2], jrc[MAXJ][2];
+  // K in skyline form, joints in children-first order (see node_symbolic)
+  int npos[CPL_MAXJ], nord[CPL_MAXJ], nf[2 * CPL_MAXJ], noff[2 * CPL_MAXJ + 1];
+  int cbody[MAXB];
+  double crho[MAXB][2], mu[MAXB];
+  short lrow[CPL_MAXROW], qrow[CPL_MAXROW];  // live / quadrature slot of each state row, or -1
+};
+
+// True when the model needs the coupled path.
+inline bool cpl_needed(const DevModel& M) { return M.jelim || M.scheme != 0 || M.ta != 0.0; }
+
+// Builds the tables; returns an error text or nullptr.
+const char* cpl_build(const DevModel& M, CplTab& T);
+
+// Bytes of stage data per interval.
+size_t cpl_interval_bytes(const CplTab& T, int nsub, int prec);
+
+// Linearized discretization of intervals [0, N) in chunks of at most
+// `chunk` intervals through the workspace (stage data of one chunk).
+cudaError_t launch_coupled(const CplTab& T, int N, int nsub, int prec, int layout, const double* X,
+                           const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
+                           double* defect, double* penalty, void* ws, long chunk,
+                           unsigned* status, cudaStream_t st);
+
+}  // namespace ciscvx

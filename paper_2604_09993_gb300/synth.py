@@ -369,3 +369,11 @@ def cheetah_sweep(seed=0, n_inst=4096, N=400, n_sub=20):
                  np.full(n_inst, n_sub, dtype=np.int32), seed, (0.01, 0.05),
                  [_ROBOT_STYLE["cheetah7"]])
 
+
+def cheetah_paper_sweep(seed=0, N=65536, n_sub=10):
+    """The paper's own model on the 7-link chain: joint reaction forces
+    eliminated (Eq. (3)), RKF45 substeps, the sinusoidal surface; one instance
+    of N intervals, gait +- 0.1, u ~ N(0,1), s ~ U[0.01, 0.05]."""
+    rng = np.random.default_rng(seed)
+    robot = with_paper_dynamics(cheetah7(rng), terrain=TERRAIN_SINE)
+    return draw_instance(robot, rng, N, n_sub, s_range=(0.01, 0.05), **_ROBOT_STYLE["cheetah7"])

@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert lib.ciscvx_version() == 5
+    assert lib.ciscvx_version() == 6
 
 
 def test_null_arguments_rejected(lib):
@@ -55,6 +55,9 @@ def test_null_arguments_rejected(lib):
                                      None, None, None, None, None, None) == api.EINVAL
     assert lib.ciscvx_discretize_compact(None, 10, 4, 0, 0, None, None, None, None, None, None,
                                          None, None, None, None, None) == api.EINVAL
+    lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.ciscvx_discretize_workspace_size(None, 10, 4, 0, ctypes.byref(lo),
+                                                ctypes.byref(hi)) == api.EINVAL
 
 
 def _desc(api, nb=2, joints=((0, 1),), contacts=((1,),), mass=1.0):
@@ -69,7 +72,9 @@ def _desc(api, nb=2, joints=((0, 1),), contacts=((1,),), mass=1.0):
 
 
 @pytest.mark.parametrize("case", ["bad_parent", "self_joint", "bad_contact", "neg_mass",
-                                  "two_contacts", "too_many_links", "zero_links"])
+                                  "two_contacts", "too_many_links", "zero_links",
+                                  "bad_joint_force_model", "bad_scheme", "nan_terrain",
+                                  "eliminated_closed_loop"])
 def test_invalid_models_rejected_before_cuda(lib, case):
     from paper_2604_09993_gb300 import api
     kw = {}
@@ -90,7 +95,18 @@ def test_invalid_models_rejected_before_cuda(lib, case):
         want = api.EUNSUPPORTED
     elif case == "zero_links":
         kw = dict(nb=0, joints=(), contacts=())
+    elif case == "eliminated_closed_loop":  # link 2 hangs from two joints: not a forest
+        kw = dict(nb=3, joints=((0, 2), (1, 2)), contacts=((2,),))
+        want = api.EUNSUPPORTED
     d, keep = _desc(api, **kw)
+    if case == "bad_joint_force_model":
+        d.joint_forces = 2
+    elif case == "bad_scheme":
+        d.scheme = 7
+    elif case == "nan_terrain":
+        d.terrain_amp = float("nan")
+    elif case == "eliminated_closed_loop":
+        d.joint_forces = 1
     h = ctypes.c_void_p()
     assert lib.ciscvx_model_create(ctypes.byref(d), ctypes.byref(h)) == want
     assert h.value is None

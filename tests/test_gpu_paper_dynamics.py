@@ -1,0 +1,199 @@
+"""GPU parity of the coupled-links path (joint reaction forces eliminated by
+Eq. (3), the sinusoidal contact surface of Sec. VI-B, the RKF45 scheme)
+against the FP64 oracle, through the C ABI.
+
+Tolerances as for the per-link path: FP64 rel <= 1e-10 on every block
+(block-normwise); FP32-Phi rel <= 1e-4 on A, B-, B+, S and rel <= 1e-10 on
+defect and penalty.  Sizes span several warps of intervals, thread blocks of
+tangent columns and a ragged tail; a short workspace forces several chunks.
+"""
+import numpy as np
+import pytest
+
+from _util import TOL_FP32_PHI, TOL_FP64, block_err
+from paper_2604_09993_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PHI = ("A", "Bm", "Bp", "S")
+STATE = ("defect", "penalty")
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import oracle
+    from paper_2604_09993_gb300 import api, build
+    build.build()
+    oracle.build()
+    api.load()
+    return torch, oracle, api
+
+
+def _problem(name, seed, N, n_sub, cross=False, **kw):
+    rng = np.random.default_rng(seed)
+    R = synth.with_paper_dynamics(getattr(synth, name)(rng), **kw)
+    if cross:
+        R = synth.with_cross_states(R)
+    return synth.draw_instance(R, rng, N, n_sub, q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15))
+
+
+def _run(env, p, precision, layout="node", workspace=None):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    m = api.Model(p.robot)
+    assert m.coupled
+    U = p.U if layout == "node" else p.U_interval()
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    out = api.discretize(m, t(p.X), t(U), t(p.s), p.n_sub, precision, layout, workspace=workspace)
+    api.sync_status(m)
+    got = {k: v.double().cpu().numpy() for k, v in out.items()}
+    ref = oracle.discretize(p.robot.as_dict(), p.X, U, p.s, p.n_sub, layout=layout)
+    return got, ref
+
+
+def _check(got, ref, precision):
+    tol = TOL_FP64 if precision == "fp64" else TOL_FP32_PHI
+    for k in PHI:
+        assert block_err(got[k], ref[k]) <= tol, (k, block_err(got[k], ref[k]))
+    for k in STATE:
+        assert block_err(got[k], ref[k]) <= TOL_FP64, (k, block_err(got[k], ref[k]))
+
+
+PAPER = dict(joint_forces=1, scheme=1, terrain=synth.TERRAIN_SINE)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("name,N,n_sub", [("hopper", 10, 4), ("biped", 45, 3), ("cheetah7", 70, 5)])
+def test_paper_dynamics_matches_oracle(env, precision, name, N, n_sub):
+    got, ref = _run(env, _problem(name, 21, N, n_sub, **PAPER), precision)
+    _check(got, ref, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("feature", [
+    dict(joint_forces=1, scheme=0),                                  # Eq. (3) alone
+    dict(joint_forces=0, scheme=0, terrain=synth.TERRAIN_SINE),      # surface alone
+    dict(joint_forces=0, scheme=1),                                  # RKF45 alone
+    dict(joint_forces=1, scheme=0, terrain=synth.TERRAIN_SINE),
+], ids=["eliminated", "terrain", "rkf45", "eliminated+terrain"])
+def test_each_feature_matches_oracle(env, precision, feature):
+    got, ref = _run(env, _problem("cheetah7", 22, 37, 4, **feature), precision)
+    _check(got, ref, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_full_eq12_state_with_paper_dynamics(env, precision):
+    got, ref = _run(env, _problem("biped", 23, 40, 3, cross=True, **PAPER), precision)
+    _check(got, ref, precision)
+
+
+def test_interval_layout(env):
+    got, ref = _run(env, _problem("biped", 24, 33, 3, **PAPER), "fp64", layout="interval")
+    _check(got, ref, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_chunked_workspace_is_bitwise_equal(env, precision):
+    """A workspace of the minimum size (32 intervals per chunk) gives the very
+    same numbers as one chunk for all intervals."""
+    torch, oracle, api = env
+    p = _problem("cheetah7", 25, 101, 3, **PAPER)
+    m = api.Model(p.robot)
+    lo, hi = api.discretize_workspace_size(m, p.N, p.n_sub, precision)
+    assert 0 < lo < hi
+    dev = torch.device("cuda:0")
+    small = torch.empty(lo, dtype=torch.uint8, device=dev)
+    full = torch.empty(hi, dtype=torch.uint8, device=dev)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    a = api.discretize(m, t(p.X), t(p.U), t(p.s), p.n_sub, precision, workspace=small)
+    b = api.discretize(m, t(p.X), t(p.U), t(p.s), p.n_sub, precision, workspace=full)
+    api.sync_status(m)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_single_interval_and_no_contacts(env):
+    """Degenerate sizes: N = 1, n_sub = 1; a robot without contacts (no y rows)."""
+    p = _problem("hopper", 26, 1, 1, **PAPER)
+    got, ref = _run(env, p, "fp64")
+    _check(got, ref, "fp64")
+    rng = np.random.default_rng(27)
+    R = synth.with_paper_dynamics(synth.biped(rng), **PAPER)
+    R = synth.Robot(**{**R.__dict__, "contact_body": np.zeros(0, np.int32),
+                       "contact_rho": np.zeros((0, 2)), "contact_mu": np.zeros(0)})
+    q = synth.draw_instance(R, rng, 5, 2, q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15))
+    got, ref = _run(env, q, "fp64")
+    for k in ("A", "Bm", "Bp", "S", "defect"):
+        assert block_err(got[k], ref[k]) <= TOL_FP64, k
+
+
+def test_unsupported_entry_points(env):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("hopper", 28, 10, 4, **PAPER)
+    m = api.Model(p.robot)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X, U, s = t(p.X), t(p.U), t(p.s)
+    w = torch.zeros((p.N, m.nxt), dtype=torch.float64, device=dev)
+    rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
+    e = np.full(m.nc, 0.0)
+    Phi = torch.zeros((3, 2 * m.nc), dtype=torch.float64, device=dev)
+    Gam = torch.zeros((3, m.nc), dtype=torch.float64, device=dev)
+    Xn = torch.zeros((3, m.nxt), dtype=torch.float64, device=dev)
+    for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
+                 lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
+                 lambda: api.discretize_vjp(m, X, U, s, w, rho, p.n_sub, "fp64"),
+                 lambda: api.model_pattern(p.robot.as_dict()),
+                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub]),
+                 lambda: api.node_linearize(m, Xn, Xn, Phi, Gam, 1e-3, e)):
+        with pytest.raises(api.CiscvxError) as err:
+            call()
+        assert err.value.status == api.EUNSUPPORTED
+    # a workspace below the minimum is an argument error
+    tiny = torch.empty(16, dtype=torch.uint8, device=dev)
+    with pytest.raises(api.CiscvxError) as err:
+        api.discretize(m, X, U, s, p.n_sub, "fp64", workspace=tiny)
+    assert err.value.status == api.EINVAL
+
+
+def test_node_constraints_with_eliminated_joint_forces(env):
+    """The impulse model does not depend on how the continuous-time reaction
+    forces are treated: on flat ground the node kernel serves these models."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(29)
+    R = synth.with_paper_dynamics(synth.cheetah7(rng), joint_forces=1, scheme=1).as_dict()
+    m = api.Model(R)
+    n = 40
+    Xm = rng.uniform(-1, 1, (n, m.nxt))
+    Xp = Xm + 0.3 * rng.standard_normal((n, m.nxt))
+    Phi = rng.standard_normal((n, 2 * m.nc))
+    Gam = rng.uniform(0, 1, (n, m.nc))
+    e = np.full(m.nc, 0.4)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    out = api.node_linearize(m, t(Xp), t(Xm), t(Phi), t(Gam), 1e-3, e)
+    api.sync_status(m)
+    ref = oracle.node(R, Xp, Xm, Phi, Gam, 1e-3, e)
+    assert block_err(out["g"].cpu().numpy(), ref["g"]) <= TOL_FP64
+    assert block_err(out["theta"].cpu().numpy().reshape(n, -1), ref["theta"]) <= TOL_FP64
+
+
+def test_sweep_size_sampled(env):
+    """At the benchmark's size and launch configuration (7-link chain, paper
+    dynamics, 65 536 intervals x 10 substeps in 2 GiB chunks, FP32-Phi): sampled
+    intervals against the oracle, and every defect finite."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = synth.cheetah_paper_sweep(seed=0)
+    m = api.Model(p.robot)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    out = api.discretize(m, t(p.X), t(p.U), t(p.s), p.n_sub, "fp32_phi")
+    api.sync_status(m)
+    assert torch.isfinite(out["defect"]).all()
+    rng = np.random.default_rng(1)
+    ks = np.unique(np.concatenate([[0, p.N - 1], rng.integers(0, p.N, 14)]))
+    for k in ks:
+        ref = oracle.discretize(p.robot.as_dict(), p.X[k:k + 2], p.U[k:k + 2], p.s[k:k + 1], p.n_sub)
+        got = {kk: v[k:k + 1].double().cpu().numpy() for kk, v in out.items()}
+        _check(got, ref, "fp32_phi")
