@@ -40,6 +40,8 @@ struct Scheme {
   static constexpr int S = SCH ? 6 : 4;    // stages
   static constexpr int NKS = SCH ? 5 : 1;  // stored slopes per row (RK4 only reads the previous one)
   __device__ static constexpr int slot(int l) { return NKS == 1 ? 0 : l; }
+  // nonzero weights (Fehlberg's fifth-order weights skip the second stage)
+  __device__ static constexpr bool bnz(int m) { return SCH ? m != 1 : true; }
 };
 
 // Contact surface y = ta sin(tk x) at the world point (xc, yc): approximate
@@ -90,6 +92,27 @@ __device__ __forceinline__ double ramp_d(double z, double& d) {
   return H;
 }
 
+// Tableau constants and link inverses in the precision of the arithmetic
+// that uses them (FP32 copies keep conversions out of the FP32 loops).
+template <typename TP>
+struct Cst {
+  __device__ static double a(const CplTab& M, int j, int l) { return M.a[j][l]; }
+  __device__ static double b(const CplTab& M, int j) { return M.b[j]; }
+  __device__ static double c(const CplTab& M, int j) { return M.c[j]; }
+  __device__ static double beta(const CplTab& M, int j) { return M.beta[j]; }
+  __device__ static double minv(const CplTab& M, int b) { return M.minv[b]; }
+  __device__ static double iinv(const CplTab& M, int b) { return M.iinv[b]; }
+};
+template <>
+struct Cst<float> {
+  __device__ static float a(const CplTab& M, int j, int l) { return M.af[j][l]; }
+  __device__ static float b(const CplTab& M, int j) { return M.bf[j]; }
+  __device__ static float c(const CplTab& M, int j) { return M.cf[j]; }
+  __device__ static float beta(const CplTab& M, int j) { return M.betaf[j]; }
+  __device__ static float minv(const CplTab& M, int b) { return M.minvf[b]; }
+  __device__ static float iinv(const CplTab& M, int b) { return M.iinvf[b]; }
+};
+
 #define EL(o) sm[(o) * 32]
 #define LK(i, kk) EL(M.n_K + M.noff[i] + (kk) - M.nf[i])
 
@@ -99,7 +122,8 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
                                                     const double* __restrict__ X,
                                                     const double* __restrict__ U,
                                                     const double* __restrict__ s,
-                                                    TP* __restrict__ sd, double* __restrict__ defect,
+                                                    TP* __restrict__ sd, TP* __restrict__ A,
+                                                    double* __restrict__ defect,
                                                     double* __restrict__ penalty, unsigned* status) {
   using Sc = Scheme<SCH>;
   constexpr int NS = Sc::S;
@@ -109,50 +133,87 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
   const long k = i0 + t;
   double* sm = smem1 + threadIdx.x;
   const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
+  const int nl = M.nlive;
   const double* uL = layout == 0 ? U + k * nu : U + 2 * k * nu;
   const double* uR = layout == 0 ? U + (k + 1) * nu : U + (2 * k + 1) * nu;
   const double sk = s[k];
   const double h = 1.0 / nsub;
-  for (int r = 0; r < nxt; ++r) EL(M.n_x + r) = X[k * nxt + r];
+  for (int r = 0; r < nxt; ++r) {
+    const double v = X[k * nxt + r];
+    if (M.lrow[r] >= 0) EL(M.n_xl + M.lrow[r]) = v;
+    else EL(M.n_xq + M.qrow[r]) = v;
+  }
   TP* sdk = sd + (size_t)t * nsub * NS * M.sd_size;
+  // stage value of state row r (live rows only)
+#define XS(r) EL(M.n_xs + M.lrow[r])
 
   for (int i = 0; i < nsub; ++i) {
+    // quadrature rows: p += h s v at the substep start (the rest below)
+    for (int b = 0; b < nb; ++b) {
+      if (M.contact[b] >= 0) continue;
+      for (int c2 = 0; c2 < 2; ++c2)
+        EL(M.n_xq + M.qrow[3 * b + c2]) = fma(h * sk, EL(M.n_xq + M.qrow[nq + 3 * b + c2]),
+                                              EL(M.n_xq + M.qrow[3 * b + c2]));
+    }
     for (int j = 0; j < NS; ++j) {
       const double tau = (i + M.c[j]) * h;
       const double bj = M.b[j];
+      const double h2b = h * h * sk * M.beta[j];
       TP* D = sdk + (size_t)(i * NS + j) * M.sd_size;
-      // stage state and inputs
-      for (int r = 0; r < nxt; ++r) {
-        double v = EL(M.n_x + r);
-        for (int l = 0; l < j; ++l)
-          if (M.a[j][l] != 0.0) v = fma(M.a[j][l] * h, EL(M.n_k + Sc::slot(l) * nxt + r), v);
-        EL(M.n_xs + r) = v;
+      for (int l = 0; l < nl; ++l) EL(M.n_xs + l) = EL(M.n_xl + l);
+      for (int m = 0; m < j; ++m) {
+        const double ah = M.a[j][m] * h;
+        if (ah == 0.0) continue;
+        for (int l = 0; l < nl; ++l)
+          EL(M.n_xs + l) = fma(ah, EL(M.n_k + Sc::slot(m) * nl + l), EL(M.n_xs + l));
       }
-      for (int q = 0; q < nu; ++q) EL(M.n_u + q) = (1.0 - tau) * uL[q] + tau * uR[q];
-      // records F_r and the slope k_r = s F_r of row r
+      auto u_at = [&](int q) { return (1.0 - tau) * uL[q] + tau * uR[q]; };
+      // records F_r and integrates row r with the slope s F_r
       auto emit = [&](int r, double F) {
+        const int l = M.lrow[r];
         D[M.sd_F + r] = TP(F);
         const double kv = sk * F;
-        if (j < NS - 1) EL(M.n_k + Sc::slot(j) * nxt + r) = kv;
-        EL(M.n_acc + r) = (j == 0) ? bj * kv : fma(bj, kv, EL(M.n_acc + r));
+        if (l >= 0) {
+          if (Sc::NKS == 1) {
+            if (j < NS - 1) EL(M.n_k + l) = kv;
+            EL(M.n_acc + l) = (j == 0) ? bj * kv : fma(bj, kv, EL(M.n_acc + l));
+            if (j == NS - 1) EL(M.n_xl + l) = fma(h, EL(M.n_acc + l), EL(M.n_xl + l));
+          } else if (j < NS - 1) {
+            EL(M.n_k + Sc::slot(j) * nl + l) = kv;
+          } else {  // last stage: x += h sum_m b_m k_m from the stored slopes
+            double acc = bj * kv;
+            for (int m = NS - 2; m >= 0; --m)
+              if (Sc::bnz(m)) acc = fma(M.b[m], EL(M.n_k + Sc::slot(m) * nl + l), acc);
+            EL(M.n_xl + l) = fma(h, acc, EL(M.n_xl + l));
+          }
+        } else {
+          const int q = M.qrow[r];
+          EL(M.n_xq + q) = fma(h * bj, kv, EL(M.n_xq + q));
+          // a velocity row of a link without a contact also moves its position:
+          // p += h^2 s beta_j k_v (p += h s v was added at the substep start)
+          if (r >= nq && r < 2 * nq && (r - nq) % 3 != 2) {
+            const int qp = M.qrow[r - nq];
+            EL(M.n_xq + qp) = fma(h2b, kv, EL(M.n_xq + qp));
+          }
+        }
       };
-      // sin/cos of the link angles; joint lever arms r = R(theta) rho
+      // lever arms r = R(theta) rho of every joint end and contact point
       for (int b = 0; b < nb; ++b) {
         double sn, cs;
-        sincos(EL(M.n_xs + 3 * b + 2), &sn, &cs);
-        EL(M.n_sc + 2 * b) = sn;
-        EL(M.n_sc + 2 * b + 1) = cs;
-      }
-      for (int jj = 0; jj < nj; ++jj) {
-        for (int role = 0; role < 2; ++role) {
-          const int b = role ? M.jpar[jj] : M.jchi[jj];
+        sincos(XS(3 * b + 2), &sn, &cs);
+        for (int tt = 0; tt < M.nadj[b]; ++tt) {
+          const int code = M.adj[b][tt], jj = code >> 1, role = code & 1;
           const double* rho = role ? M.jrp[jj] : M.jrc[jj];
-          const double sn = EL(M.n_sc + 2 * b), cs = EL(M.n_sc + 2 * b + 1);
           const double rx = fma(cs, rho[0], -sn * rho[1]), ry = fma(sn, rho[0], cs * rho[1]);
           EL(M.n_arm + 4 * jj + 2 * role) = rx;
           EL(M.n_arm + 4 * jj + 2 * role + 1) = ry;
           D[M.sd_arm + 4 * jj + 2 * role] = TP(rx);
           D[M.sd_arm + 4 * jj + 2 * role + 1] = TP(ry);
+        }
+        const int ic = M.contact[b];
+        if (ic >= 0) {
+          EL(M.n_carm + 2 * ic) = fma(cs, M.crho[ic][0], -sn * M.crho[ic][1]);
+          EL(M.n_carm + 2 * ic + 1) = fma(sn, M.crho[ic][0], cs * M.crho[ic][1]);
         }
       }
       // generalized forces (F_x, F_y, torque) per link; QW_b = sum r . F over
@@ -166,11 +227,11 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
       }
       for (int jj = 0; jj < nj; ++jj) {
         const int c = M.jchi[jj], p = M.jpar[jj];
-        const double tq = EL(M.n_u + jj);
+        const double tq = u_at(jj);
         EL(M.n_f + 3 * c + 2) += tq;
         EL(M.n_f + 3 * p + 2) -= tq;
         if (!M.jelim) {  // reaction force as an input: +lambda on the child, -lambda on the parent
-          const double lx = EL(M.n_u + nj + 2 * jj), ly = EL(M.n_u + nj + 2 * jj + 1);
+          const double lx = u_at(nj + 2 * jj), ly = u_at(nj + 2 * jj + 1);
           const double rcx = EL(M.n_arm + 4 * jj), rcy = EL(M.n_arm + 4 * jj + 1);
           const double rpx = EL(M.n_arm + 4 * jj + 2), rpy = EL(M.n_arm + 4 * jj + 3);
           EL(M.n_f + 3 * c) += lx;
@@ -186,12 +247,10 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
       // contacts: frame, force, auxiliary right-hand sides and their slopes
       for (int ic = 0; ic < nc; ++ic) {
         const int b = M.cbody[ic];
-        const double sn = EL(M.n_sc + 2 * b), cs = EL(M.n_sc + 2 * b + 1);
-        const double rx = fma(cs, M.crho[ic][0], -sn * M.crho[ic][1]);
-        const double ry = fma(sn, M.crho[ic][0], cs * M.crho[ic][1]);
-        const Surf f = surface(M.ta, M.tk, EL(M.n_xs + 3 * b) + rx, EL(M.n_xs + 3 * b + 1) + ry);
-        const double u0 = EL(M.n_u + M.ci0 + 3 * ic), u1 = EL(M.n_u + M.ci0 + 3 * ic + 1),
-                     u2 = EL(M.n_u + M.ci0 + 3 * ic + 2);
+        const double rx = EL(M.n_carm + 2 * ic), ry = EL(M.n_carm + 2 * ic + 1);
+        const Surf f = surface(M.ta, M.tk, XS(3 * b) + rx, XS(3 * b + 1) + ry);
+        const double u0 = u_at(M.ci0 + 3 * ic), u1 = u_at(M.ci0 + 3 * ic + 1),
+                     u2 = u_at(M.ci0 + 3 * ic + 2);
         // contact-frame components (tangential, normal)
         const double ft = M.aux ? u0 : u1 - u2, fn = M.aux ? u1 : u0;
         const double fx = fma(f.tx, ft, f.nx * fn), fy = fma(f.ty, ft, f.ny * fn);
@@ -199,7 +258,7 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
         EL(M.n_f + 3 * b + 1) += fy;
         EL(M.n_f + 3 * b + 2) += fma(rx, fy, -ry * fx);
         EL(M.n_qw + b) += fma(rx, fx, ry * fy);
-        TP* Dc = D + M.sd_con + M.cf * ic;
+        TP* Dc = D + M.sd_con + M.ncf * ic;
         Dc[0] = TP(rx); Dc[1] = TP(ry);
         Dc[2] = TP(f.tx); Dc[3] = TP(f.ty); Dc[4] = TP(f.nx); Dc[5] = TP(f.ny);
         Dc[6] = TP(fma(f.dtx, ft, f.dnx * fn));  // dF/dx_c at fixed inputs
@@ -219,9 +278,9 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
         } else {
           // Eq. (12): phi_n, lambda^c, gamma, rho^c, then the path penalty
           const double gam = u2;
-          const double om = EL(M.n_xs + nq + 3 * b + 2);
-          const double vcx = fma(-om, ry, EL(M.n_xs + nq + 3 * b));
-          const double vcy = fma(om, rx, EL(M.n_xs + nq + 3 * b + 1));
+          const double om = XS(nq + 3 * b + 2);
+          const double vcx = fma(-om, ry, XS(nq + 3 * b));
+          const double vcy = fma(om, rx, XS(nq + 3 * b + 1));
           const double rt = 1.0 / sqrt(fma(ft, ft, 1.0));
           double dmn, dft;
           const double rho_c = sabs_d(mu * fn, dmn) - sabs_d(ft, dft);
@@ -231,9 +290,9 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
                            ramp_d(-rho_c, drh);
           const double rho_ft = -dft, rho_fn = mu * dmn;
           Dc[10] = TP(-dph);
-          Dc[11] = TP(drh * dft);            // dH/dphi_t = -h'(-rho) drho/dphi_t
+          Dc[11] = TP(drh * dft);             // dH/dphi_t = -h'(-rho) drho/dphi_t
           Dc[12] = TP(-dfn_ - drh * rho_fn);  // dH/dphi_n
-          Dc[13] = TP(-dga);                 // dH/dgamma
+          Dc[13] = TP(-dga);                  // dH/dgamma
           Dc[14] = TP(vcx); Dc[15] = TP(vcy);
           Dc[16] = TP(fma(f.dtx, vcx, f.dty * vcy));  // (dt/dx_c) . v_c
           Dc[17] = TP(gam * rt * rt * rt);            // dlambda^c/dphi_t
@@ -294,7 +353,7 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
           for (int role = 0; role < 2; ++role) {
             const int b = role ? M.jpar[jj] : M.jchi[jj];
             const double rx = EL(M.n_arm + 4 * jj + 2 * role), ry = EL(M.n_arm + 4 * jj + 2 * role + 1);
-            const double om = EL(M.n_xs + nq + 3 * b + 2);
+            const double om = XS(nq + 3 * b + 2);
             const double aa = EL(M.n_f + 3 * b + 2) * M.iinv[b];
             const double c0 = fma(om * om, rx, fma(ry, aa, -EL(M.n_f + 3 * b) * M.minv[b]));
             const double c1 = fma(om * om, ry, fma(-rx, aa, -EL(M.n_f + 3 * b + 1) * M.minv[b]));
@@ -330,25 +389,54 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
         }
       }
       for (int b = 0; b < nb; ++b) D[M.sd_qw + b] = TP(EL(M.n_qw + b));
-      // q' = v, v' = M^-1 F
-      for (int r = 0; r < nq; ++r) emit(r, EL(M.n_xs + nq + r));
+      // q' = v: live position rows take the stage velocity; a link without a
+      // contact records its velocity at the substep start only (the tangent
+      // kernel needs no more of it)
+      for (int b = 0; b < nb; ++b) {
+        emit(3 * b + 2, XS(nq + 3 * b + 2));
+        if (M.contact[b] >= 0) {
+          emit(3 * b, XS(nq + 3 * b));
+          emit(3 * b + 1, XS(nq + 3 * b + 1));
+        } else if (j == 0) {
+          D[M.sd_F + 3 * b] = TP(EL(M.n_xq + M.qrow[nq + 3 * b]));
+          D[M.sd_F + 3 * b + 1] = TP(EL(M.n_xq + M.qrow[nq + 3 * b + 1]));
+        }
+      }
+      // v' = M^-1 F
       for (int b = 0; b < nb; ++b) {
         emit(nq + 3 * b, EL(M.n_f + 3 * b) * M.minv[b]);
         emit(nq + 3 * b + 1, EL(M.n_f + 3 * b + 1) * M.minv[b]);
         emit(nq + 3 * b + 2, EL(M.n_f + 3 * b + 2) * M.iinv[b]);
       }
     }
-    for (int r = 0; r < nxt; ++r) EL(M.n_x + r) = fma(h, EL(M.n_acc + r), EL(M.n_x + r));
   }
+#undef XS
   double chk = 0.0;
   for (int r = 0; r < nxt; ++r) {
-    const double d = EL(M.n_x + r) - X[(k + 1) * nxt + r];
+    const double x = M.lrow[r] >= 0 ? EL(M.n_xl + M.lrow[r]) : EL(M.n_xq + M.qrow[r]);
+    const double d = x - X[(k + 1) * nxt + r];
     defect[k * nxt + r] = d;
     chk += d;
   }
-  for (int ic = 0; ic < nc; ++ic)
-    penalty[k * nc + ic] = EL(M.n_x + M.pen0 + ic) - X[k * nxt + M.pen0 + ic];
+  for (int ic = 0; ic < nc; ++ic) {
+    const int r = M.pen0 + ic;
+    const double x = M.lrow[r] >= 0 ? EL(M.n_xl + M.lrow[r]) : EL(M.n_xq + M.qrow[r]);
+    penalty[k * nc + ic] = x - X[k * nxt + r];
+  }
   if (!isfinite(chk)) atomicOr(status, ST_NONFINITE);
+  // closed-form columns of A: e_p, e_v + s e_p (links without a contact), e_y
+  TP* Ak = A + (size_t)k * nxt * nxt;
+  auto unit_col = [&](int c, int r2, TP v2) {
+    for (int r = 0; r < nxt; ++r) Ak[(size_t)r * nxt + c] = (r == c) ? TP(1) : (r == r2 ? v2 : TP(0));
+  };
+  for (int b = 0; b < nb; ++b) {
+    if (M.contact[b] >= 0) continue;
+    for (int c2 = 0; c2 < 2; ++c2) {
+      unit_col(3 * b + c2, -1, TP(0));
+      unit_col(nq + 3 * b + c2, 3 * b + c2, TP(sk));
+    }
+  }
+  for (int r = 6 * nb; r < nxt; ++r) unit_col(r, -1, TP(0));
 }
 
 #undef LK
@@ -361,15 +449,16 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
                               TP* __restrict__ A, TP* __restrict__ Bm, TP* __restrict__ Bp,
                               TP* __restrict__ S, unsigned* status) {
   using Sc = Scheme<SCH>;
+  using K = Cst<TP>;
   constexpr int NS = Sc::S;
   extern __shared__ __align__(16) unsigned char smem2[];
   const int bs = blockDim.x;
   TP* tm = reinterpret_cast<TP*>(smem2) + threadIdx.x;
-  const int C = M.C;
+  const int C = M.cnt;
   const long g = (long)blockIdx.x * bs + threadIdx.x;
   const long t = g / C;
   if (t >= n) return;
-  const int col = (int)(g - t * C);
+  const int col = M.cperm[g - t * C];
   const long k = i0 + t;
   const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
   const int nl = M.nlive, nqd = M.nquad;
@@ -387,7 +476,7 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
     else ET(M.t_pq + M.qrow[col]) = TP(1);
   }
   const TP sk = TP(s[k]);
-  const TP h = TP(1.0 / nsub);
+  const TP h = TP(1) / TP(nsub);
   const TP hsk = h * sk;
   const TP* sdk = sd + (size_t)t * nsub * NS * M.sd_size;
   // the column's input: a torque, a reaction force (inputs only without
@@ -397,6 +486,7 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
   const bool q_force = qin >= nj && qin < ci0;
   const int q_con = qin >= ci0 ? (qin - ci0) / 3 : -1;
   const int q_comp = qin >= ci0 ? (qin - ci0) % 3 : 0;
+#define TXS(r) ET(M.t_xs + M.lrow[r])
 
   for (int i = 0; i < nsub; ++i) {
     // quadrature rows: p += h s v at the substep start
@@ -408,21 +498,21 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
     for (int j = 0; j < NS; ++j) {
       const TP* D = sdk + (size_t)(i * NS + j) * M.sd_size;
       const TP* F = D + M.sd_F;
-      const TP bj = TP(M.b[j]), hbj = h * bj, h2b = h * h * sk * TP(M.beta[j]);
+      const TP bj = K::b(M, j), hbj = h * bj, h2b = h * h * sk * K::beta(M, j);
       // stage tangent of the live rows
-      for (int l = 0; l < nl; ++l) {
-        TP v = ET(M.t_pl + l);
-        for (int m = 0; m < j; ++m)
-          if (M.a[j][m] != 0.0) v += TP(M.a[j][m]) * h * ET(M.t_k + Sc::slot(m) * nl + l);
-        ET(M.t_xs + l) = v;
+      for (int l = 0; l < nl; ++l) ET(M.t_xs + l) = ET(M.t_pl + l);
+      for (int m = 0; m < j; ++m) {
+        const TP ah = K::a(M, j, m) * h;
+        if (ah == TP(0)) continue;
+        for (int l = 0; l < nl; ++l) ET(M.t_xs + l) += ah * ET(M.t_k + Sc::slot(m) * nl + l);
       }
-      const TP tau = (TP(i) + TP(M.c[j])) * h;
+      const TP tau = (TP(i) + K::c(M, j)) * h;
       const TP w = qin < 0 ? TP(0) : (right ? tau : TP(1) - tau);
       // generalized-force tangent e: -dtheta QW (moving application points) + direct inputs
       for (int b = 0; b < nb; ++b) {
         ET(M.t_e + 3 * b) = TP(0);
         ET(M.t_e + 3 * b + 1) = TP(0);
-        ET(M.t_e + 3 * b + 2) = -ET(M.t_xs + M.lrow[3 * b + 2]) * D[M.sd_qw + b];
+        ET(M.t_e + 3 * b + 2) = -TXS(3 * b + 2) * D[M.sd_qw + b];
       }
       if (q_torque) {
         ET(M.t_e + 3 * M.jchi[qin] + 2) += w;
@@ -440,11 +530,11 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
       // contacts: force tangent and the auxiliary rows
       for (int ic = 0; ic < nc; ++ic) {
         const int b = M.cbody[ic];
-        const TP* Dc = D + M.sd_con + M.cf * ic;
+        const TP* Dc = D + M.sd_con + M.ncf * ic;
         const TP rx = Dc[0], ry = Dc[1];
-        const TP dth = ET(M.t_xs + M.lrow[3 * b + 2]);
-        const TP dxc = ET(M.t_xs + M.lrow[3 * b]) - ry * dth;
-        const TP dyc = ET(M.t_xs + M.lrow[3 * b + 1]) + rx * dth;
+        const TP dth = TXS(3 * b + 2);
+        const TP dxc = TXS(3 * b) - ry * dth;
+        const TP dyc = TXS(3 * b + 1) + rx * dth;
         TP dft = TP(0), dfn = TP(0), dga = TP(0);
         if (q_con == ic) {
           if (M.aux) {
@@ -471,9 +561,9 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
         } else {
           // lambda^c = t . v_c + gamma phi_t / sqrt(1 + phi_t^2), v_c = (v_x - omega r_y, v_y + omega r_x)
           const TP om = F[3 * b + 2];
-          const TP dom = ET(M.t_xs + M.lrow[nq + 3 * b + 2]);
-          const TP dvcx = ET(M.t_xs + M.lrow[nq + 3 * b]) - dom * ry - om * rx * dth;
-          const TP dvcy = ET(M.t_xs + M.lrow[nq + 3 * b + 1]) + dom * rx - om * ry * dth;
+          const TP dom = TXS(nq + 3 * b + 2);
+          const TP dvcx = TXS(nq + 3 * b) - dom * ry - om * rx * dth;
+          const TP dvcy = TXS(nq + 3 * b + 1) + dom * rx - om * ry * dth;
           const TP dlam = Dc[16] * dxc + Dc[2] * dvcx + Dc[3] * dvcy + Dc[17] * dft + Dc[18] * dga;
           quad(6 * nb + 4 * ic, dfn);
           quad(6 * nb + 4 * ic + 1, dlam);
@@ -490,8 +580,8 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
             const int b = role ? M.jpar[jj] : M.jchi[jj];
             const TP rx = D[M.sd_arm + 4 * jj + 2 * role], ry = D[M.sd_arm + 4 * jj + 2 * role + 1];
             const TP om = F[3 * b + 2], omd = F[nq + 3 * b + 2];
-            const TP dth = ET(M.t_xs + M.lrow[3 * b + 2]), dom = ET(M.t_xs + M.lrow[nq + 3 * b + 2]);
-            const TP mi = TP(M.minv[b]), ii = TP(M.iinv[b]);
+            const TP dth = TXS(3 * b + 2), dom = TXS(nq + 3 * b + 2);
+            const TP mi = K::minv(M, b), ii = K::iinv(M, b);
             const TP ea = ET(M.t_e + 3 * b + 2) * ii;
             // alpha = 2 omega r, beta = omega^2 perp(r) + omega' r, perp(r) = (-r_y, r_x)
             const TP c0 = TP(2) * om * rx * dom + (-om * om * ry + omd * rx) * dth -
@@ -533,35 +623,51 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
         TP kv = sk * dy;
         if (scol) kv += F[row];
         const int l = M.lrow[row];
-        if (j < NS - 1) ET(M.t_k + Sc::slot(j) * nl + l) = kv;
-        ET(M.t_acc + l) = (j == 0) ? bj * kv : ET(M.t_acc + l) + bj * kv;
+        if (Sc::NKS == 1) {
+          if (j < NS - 1) ET(M.t_k + l) = kv;
+          ET(M.t_acc + l) = (j == 0) ? bj * kv : ET(M.t_acc + l) + bj * kv;
+          if (j == NS - 1) ET(M.t_pl + l) += h * ET(M.t_acc + l);
+        } else if (j < NS - 1) {
+          ET(M.t_k + Sc::slot(j) * nl + l) = kv;
+        } else {  // last stage: x += h sum_m b_m k_m from the stored slopes
+          TP acc = bj * kv;
+          for (int m = NS - 2; m >= 0; --m)
+            if (Sc::bnz(m)) acc += K::b(M, m) * ET(M.t_k + Sc::slot(m) * nl + l);
+          ET(M.t_pl + l) += h * acc;
+        }
       };
       for (int b = 0; b < nb; ++b) {
-        const TP mi = TP(M.minv[b]);
+        const TP mi = K::minv(M, b);
         const TP dv0 = ET(M.t_e + 3 * b) * mi, dv1 = ET(M.t_e + 3 * b + 1) * mi;
-        const TP dw = ET(M.t_e + 3 * b + 2) * TP(M.iinv[b]);
-        live(3 * b + 2, ET(M.t_xs + M.lrow[nq + 3 * b + 2]));
+        const TP dw = ET(M.t_e + 3 * b + 2) * K::iinv(M, b);
+        live(3 * b + 2, TXS(nq + 3 * b + 2));
         live(nq + 3 * b + 2, dw);
         if (M.contact[b] >= 0) {
-          live(3 * b, ET(M.t_xs + M.lrow[nq + 3 * b]));
-          live(3 * b + 1, ET(M.t_xs + M.lrow[nq + 3 * b + 1]));
+          live(3 * b, TXS(nq + 3 * b));
+          live(3 * b + 1, TXS(nq + 3 * b + 1));
           live(nq + 3 * b, dv0);
           live(nq + 3 * b + 1, dv1);
         } else {
+          // p' = s v with v a quadrature row: p gains h^2 s beta_j k_v here
+          // (h s v at the substep start); for the s column also the nominal
+          // velocity's own contribution h sum_j b_j v_j = h (v_0 + h s sum_j beta_j F_v,j)
           const TP dv[2] = {dv0, dv1};
           for (int c2 = 0; c2 < 2; ++c2) {
             TP kv = sk * dv[c2];
-            if (scol) kv += F[nq + 3 * b + c2];
-            TP& pq = ET(M.t_pq + M.qrow[3 * b + c2]);
-            pq += h2b * kv;
-            if (scol) pq += hbj * F[3 * b + c2];
+            TP pinc = TP(0);
+            if (scol) {
+              kv += F[nq + 3 * b + c2];
+              pinc = h2b * F[nq + 3 * b + c2];
+              if (j == 0) pinc += h * F[3 * b + c2];
+            }
+            ET(M.t_pq + M.qrow[3 * b + c2]) += h2b * kv + pinc;
             ET(M.t_pq + M.qrow[nq + 3 * b + c2]) += hbj * kv;
           }
         }
       }
     }
-    for (int l = 0; l < nl; ++l) ET(M.t_pl + l) += h * ET(M.t_acc + l);
   }
+#undef TXS
   // column `col` of [A | B- | B+ | S]
   TP* out;
   size_t stride;
@@ -605,8 +711,8 @@ cudaError_t run(const CplTab& T, int N, int nsub, int layout, const double* X, c
   for (long i0 = 0; i0 < N; i0 += chunk) {
     const long n = std::min<long>(chunk, N - i0);
     k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
-        T, i0, n, nsub, layout, X, U, s, (TP*)ws, defect, penalty, status);
-    const long threads = n * T.C;
+        T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status);
+    const long threads = n * T.cnt;
     k_cpl_tangent<TP, SCH><<<(unsigned)((threads + bs - 1) / bs), bs, sm2, st>>>(
         T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status);
     e = cudaGetLastError();
@@ -710,37 +816,54 @@ const char* cpl_build(const DevModel& M, CplTab& T) {
   for (int r = 6 * nb; r < M.nxt; ++r) T.qrow[r] = (short)nqd++;
   T.nlive = nl;
   T.nquad = nqd;
+  // integrated columns: every column but the closed-form ones
+  int cnt = 0;
+  for (int c = 0; c < T.C; ++c) {
+    const bool trivial = c < M.nxt && (c >= 6 * nb || (M.body[(c % nq) / 3].contact < 0 && (c % 3) != 2));
+    if (!trivial) T.cperm[cnt++] = (short)c;
+  }
+  T.cnt = cnt;
   // stage data
-  T.cf = M.aux ? CPL_CF1 : CPL_CF0;
+  T.ncf = M.aux ? CPL_CF1 : CPL_CF0;
   T.sd_arm = 0;
   T.sd_qw = T.sd_arm + 4 * nj;
   T.sd_F = T.sd_qw + nb;
   T.sd_K = T.sd_F + M.nxt;
   T.sd_con = T.sd_K + T.nsky;
-  T.sd_size = T.sd_con + T.cf * nc;
+  T.sd_size = T.sd_con + T.ncf * nc;
   // nominal kernel scratch (doubles per lane)
-  const int nxt = M.nxt;
-  T.n_x = 0;
-  T.n_xs = T.n_x + nxt;
-  T.n_acc = T.n_xs + nxt;
-  T.n_k = T.n_acc + nxt;
-  T.n_u = T.n_k + T.nks * nxt;
-  T.n_f = T.n_u + M.nu;
+  const bool acc = T.nks == 1;  // RK4 keeps an accumulator; RKF45 sums its stored slopes
+  T.n_xl = 0;
+  T.n_xs = T.n_xl + nl;
+  T.n_acc = T.n_xs + nl;
+  T.n_k = T.n_acc + (acc ? nl : 0);
+  T.n_xq = T.n_k + T.nks * nl;
+  T.n_f = T.n_xq + nqd;
   T.n_arm = T.n_f + 3 * nb;
-  T.n_sc = T.n_arm + 4 * nj;
-  T.n_K = T.n_sc + 2 * nb;
+  T.n_carm = T.n_arm + 4 * nj;
+  T.n_K = T.n_carm + 2 * nc;
   T.n_lam = T.n_K + T.nsky;
   T.n_qw = T.n_lam + T.nk;
   T.n_size = T.n_qw + nb;
   // tangent kernel scratch (elements per thread)
   T.t_pl = 0;
   T.t_acc = T.t_pl + nl;
-  T.t_k = T.t_acc + nl;
+  T.t_k = T.t_acc + (acc ? nl : 0);
   T.t_xs = T.t_k + T.nks * nl;
   T.t_pq = T.t_xs + nl;
   T.t_e = T.t_pq + nqd;
   T.t_x = T.t_e + 3 * nb;
   T.t_size = T.t_x + T.nk;
+  for (int i = 0; i < CPL_MAXSTAGE; ++i) {
+    T.cf[i] = (float)T.c[i];
+    T.bf[i] = (float)T.b[i];
+    T.betaf[i] = (float)T.beta[i];
+    for (int j = 0; j < CPL_MAXSTAGE; ++j) T.af[i][j] = (float)T.a[i][j];
+  }
+  for (int b = 0; b < nb; ++b) {
+    T.minvf[b] = (float)T.minv[b];
+    T.iinvf[b] = (float)T.iinv[b];
+  }
   if ((size_t)T.n_size * sizeof(double) * 32 > 220u * 1024u)
     return "model too large for the coupled path's shared memory";
   return nullptr;

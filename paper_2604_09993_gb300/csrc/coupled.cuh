@@ -42,14 +42,19 @@ struct CplTab {
   int stages;  // tableau stages
   int nks;     // stored stage slopes per row (1 for RK4: only the previous one is used)
   // stage data (per interval, per substep, per stage; in the tangent precision)
-  int sd_arm, sd_qw, sd_F, sd_K, sd_con, sd_size, cf;
-  // per-lane scratch of the nominal kernel (doubles, element major)
-  int n_x, n_xs, n_acc, n_k, n_u, n_f, n_arm, n_sc, n_K, n_lam, n_qw, n_size;
+  int sd_arm, sd_qw, sd_F, sd_K, sd_con, sd_size, ncf;
+  // per-lane scratch of the nominal kernel (doubles, element major): live
+  // rows x, stage values, accumulator (RK4 only), stored slopes; quadrature
+  // rows; generalized forces, lever arms, factor of K, reaction forces
+  int n_xl, n_xs, n_acc, n_k, n_xq, n_f, n_arm, n_carm, n_K, n_lam, n_qw, n_size;
   // per-thread scratch of the tangent kernel (tangent precision, element major)
   int t_pl, t_acc, t_k, t_xs, t_pq, t_e, t_x, t_size;
   double g, ta, tk;  // gravity; contact surface y = ta sin(tk x)
   double c[CPL_MAXSTAGE], a[CPL_MAXSTAGE][CPL_MAXSTAGE], b[CPL_MAXSTAGE], beta[CPL_MAXSTAGE];
   double mass[MAXB], inertia[MAXB], minv[MAXB], iinv[MAXB];
+  // FP32 copies for the FP32 tangent kernel (no conversions in its loops)
+  float cf[CPL_MAXSTAGE], af[CPL_MAXSTAGE][CPL_MAXSTAGE], bf[CPL_MAXSTAGE], betaf[CPL_MAXSTAGE];
+  float minvf[MAXB], iinvf[MAXB];
   int nadj[MAXB];
   unsigned char adj[MAXB][NODE_MAXADJ];  // (joint << 1) | (1 if the link is the joint's parent)
   int contact[MAXB];                     // contact on the link, or -1
@@ -60,6 +65,13 @@ struct CplTab {
   int cbody[MAXB];
   double crho[MAXB][2], mu[MAXB];
   short lrow[CPL_MAXROW], qrow[CPL_MAXROW];  // live / quadrature slot of each state row, or -1
+  // Tangent columns the tangent kernel integrates.  The columns of A for the
+  // positions and linear velocities of links without a contact and for the
+  // auxiliary states are closed-form (those states never enter the
+  // right-hand side: A e_p = e_p, A e_v = e_v + s e_p, A e_y = e_y); the
+  // nominal kernel writes them.
+  int cnt;                                   // columns integrated
+  short cperm[CPL_MAXROW + 2 * (3 * MAXJ + 3 * MAXB) + 1];  // integrated column index -> column
 };
 
 // True when the model needs the coupled path.
