@@ -415,6 +415,24 @@ def cpu_baseline(name, budget_s=12.0):
                       f"IND linearization + Phi-contracted VJP, FP64, {cores} threads"}
 
 
+def paper_cpu_baseline(p, budget_s=4.0):
+    """The oracle on a bounded sample of the paper-dynamics workload (all host cores)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    R = p.robot.as_dict()
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < budget_s and n + 4 * cores <= p.N:
+        k = n + 4 * cores
+        oracle.discretize(R, p.X[n:k + 1], p.U[n:k + 1], p.s[n:k], p.n_sub, threads=cores)
+        n = k
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "intervals/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {n} intervals of the workload: dual-number IND with the dense "
+                      f"KKT solve of Eq. (3), FP64, {cores} threads"}
+
+
 def run_ours(args):
     import torch
     rank, world, lrank = dist_env()
@@ -575,6 +593,57 @@ def run_ours(args):
                    "e2e": None if args.no_e2e else measure_e2e("compact")}
         wl.free(prec, "compact")
 
+    # the paper's own model on the 7-link chain (joint reaction forces
+    # eliminated by Eq. (3), RKF45 substeps, sinusoidal surface): the
+    # coupled-links path, one instance of 65 536 intervals x 10 substeps per GPU
+    paper = None
+    if not args.no_paper:
+        if spec["kind"] == "batch":
+            wl.free(prec)
+        torch.cuda.empty_cache()
+        pp = synth.cheetah_paper_sweep(seed=rank)
+        mp = api.Model(pp.robot)
+        t_ = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+        Xp, Up, sp = t_(pp.X), t_(pp.U), t_(pp.s)
+        paper = {"metric": "linearized intervals/s (STM), and of the linearize-and-contract VJP",
+                 "unit": "intervals/s",
+                 "workload": f"7-link chain, eliminated joint forces, RKF45, sinusoidal surface "
+                             f"{synth.TERRAIN_SINE[0]} sin({synth.TERRAIN_SINE[1]:.4f} x), "
+                             f"1 x {pp.N} intervals x {pp.n_sub} substeps per GPU",
+                 }
+        for pr in ("fp32_phi", "fp64"):
+            lo, hi = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr)
+            ws = torch.empty(max(lo, min(hi, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+            out = api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, workspace=ws)
+            fn = lambda: api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, out=out, workspace=ws)  # noqa: E731
+            barrier()
+            tp = time_steps(torch, fn, args.steps, args.warmup, stream)
+            barrier()
+            api.sync_status(mp)
+            tp, = max_over_ranks([tp])
+            paper[pr] = {"value": pp.N * world * args.steps / tp, "ms_per_call": tp / args.steps * 1e3,
+                         "chunks": -(-hi // ws.numel()), "workspace_bytes": ws.numel()}
+            del out, ws
+            torch.cuda.empty_cache()
+            # the VJP of the same workload (dense blocks per chunk, then A^T lambda, B^T lambda, S . lambda)
+            wv = torch.randn((pp.N, mp.nxt), dtype=torch.float64, device=dev)
+            rv = torch.full((pp.N, mp.nc), 10.0, dtype=torch.float64, device=dev)
+            lo, hi = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr, api.OP_VJP)
+            ws = torch.empty(max(lo, min(hi, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+            fv = lambda: api.discretize_vjp(mp, Xp, Up, sp, wv, rv, pp.n_sub, pr, workspace=ws)  # noqa: E731
+            barrier()
+            tv = time_steps(torch, fv, max(1, args.steps // 2), args.warmup, stream)
+            barrier()
+            api.sync_status(mp)
+            tv, = max_over_ranks([tv])
+            paper[pr]["vjp"] = {"value": pp.N * world * max(1, args.steps // 2) / tv,
+                                "ms_per_call": tv / max(1, args.steps // 2) * 1e3}
+            del ws, wv, rv
+            torch.cuda.empty_cache()
+        del Xp, Up, sp, mp
+        if world == 1 and not args.no_cpu_baseline:
+            paper["cpu_baseline"] = paper_cpu_baseline(pp)
+
     if rank != 0:
         return
     line = {
@@ -600,6 +669,7 @@ def run_ours(args):
         "compact_outputs": compact,
         "node_constraints": nodes,
         "aux_cross_model": cross,
+        "paper_dynamics": paper,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -639,6 +709,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compact", action="store_true", help="skip the compact-output measurement")
     ap.add_argument("--no-nodes", action="store_true", help="skip the node-constraint measurement")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the paper-dynamics (coupled links) measurement")
     ap.add_argument("--cross", action="store_true",
                     help="also time the linearization with the full Eq. (12) auxiliary state")
     args = ap.parse_args()

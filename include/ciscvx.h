@@ -184,10 +184,11 @@ typedef struct ciscvx_model ciscvx_model;
  * description, builds the per-link device tables on the current CUDA device
  * and allocates the model's device status word.  A model with eliminated
  * joint forces, a sinusoidal surface or the RKF45 scheme has coupled links:
- * it is linearized by ciscvx_discretize alone (dense outputs, z not provided,
- * a workspace from ciscvx_discretize_workspace_size); its VJP, compact
- * outputs and batch plans return CISCVX_EUNSUPPORTED, and so do its node
- * constraints on a sinusoidal surface.  *out receives an opaque
+ * it is linearized by ciscvx_discretize (dense outputs, z not provided, a
+ * workspace from ciscvx_discretize_workspace_size) and its VJP by
+ * linearize-and-contract; its compact outputs and batch plans return
+ * CISCVX_EUNSUPPORTED, and so do its node constraints on a sinusoidal
+ * surface.  *out receives an opaque
  * handle owned by the caller (free with ciscvx_model_destroy).  Errors:
  * EINVAL (null, counts < 0, n_bodies < 1, bad indices, non-positive mass or
  * inertia, parent == child, non-finite values), EUNSUPPORTED (limits above,
@@ -239,23 +240,31 @@ ciscvx_status ciscvx_model_nnz(const ciscvx_model* model, int* nnz_a, int* nnz_b
 typedef enum { CISCVX_OP_DISCRETIZE = 0, CISCVX_OP_VJP = 1 } ciscvx_op;
 
 /* Bytes of device scratch memory that `op` needs for N intervals (0 if none).
- * EINVAL on null pointers, N < 1 or an unknown op/layout.  For a model with
- * coupled links the discretization's scratch depends on n_sub and the
- * precision: CISCVX_OP_DISCRETIZE returns EUNSUPPORTED for it (use
- * ciscvx_discretize_workspace_size). */
+ * EINVAL on null pointers, N < 1 or an unknown op/layout.  Where the scratch
+ * depends on n_sub and the precision (CISCVX_OP_DISCRETIZE for a model with
+ * coupled links; CISCVX_OP_VJP for one with coupled links or the Eq. (12)
+ * state) it returns EUNSUPPORTED: use ciscvx_discretize_workspace_size. */
 ciscvx_status ciscvx_workspace_size(const ciscvx_model* model, ciscvx_op op, int N,
                                     ciscvx_u_layout layout, size_t* bytes);
 
-/* Scratch of ciscvx_discretize for N intervals of n_sub substeps: *min_bytes
- * (the least it accepts: one chunk of 32 intervals, or N if fewer) and
- * *full_bytes (all N intervals in one chunk).  A workspace between the two
- * is used in chunks of as many intervals as fit (stage data of the nominal
- * trajectory: n_sub x stages x (4 n_j + n_b + n_x~ + skyline(K) + contact
- * fields) values per interval in the precision's dtype).  Both are 0 for
- * models without coupled links.  Either pointer may be NULL.  EINVAL on a
- * null model, N < 1, n_sub < 1 or an unknown precision. */
-ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* model, int N, int n_sub,
-                                               ciscvx_precision precision, size_t* min_bytes,
+/* Scratch of `op` for N intervals of n_sub substeps in `precision` and
+ * `layout`: *min_bytes (the least the call accepts) and *full_bytes (enough
+ * to treat all N intervals at once); a workspace between the two is used in
+ * chunks of as many intervals as fit.
+ *   CISCVX_OP_DISCRETIZE: 0 and 0 for models without coupled links; for a
+ *     model with coupled links the stage data of the nominal trajectory
+ *     (n_sub x stages x (4 n_j + n_b + n_x~ + skyline(K) + contact fields)
+ *     values per interval in the precision's dtype), minimum 32 intervals.
+ *   CISCVX_OP_VJP: for the default model (no coupled links, aux model
+ *     CISCVX_AUX_PENALTY) min = full = ciscvx_workspace_size(CISCVX_OP_VJP);
+ *     otherwise the linearize-and-contract VJP's dense blocks (A, B-, B+, S in
+ *     the precision's dtype, defect and penalty in FP64) plus the stage data,
+ *     per interval, minimum 32 intervals.
+ * Either pointer may be NULL.  EINVAL on a null model, N < 1, n_sub < 1 or an
+ * unknown op, precision or layout. */
+ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* model, ciscvx_op op, int N,
+                                               int n_sub, ciscvx_precision precision,
+                                               ciscvx_u_layout layout, size_t* min_bytes,
                                                size_t* full_bytes);
 
 /* ----------------------------------------------------------- discretize --- */
@@ -300,7 +309,15 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* model, int N, int n_
 /* Vector-Jacobian product of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k
  * (defect and penalty as above) with respect to X, U and s, by the discrete
  * adjoint of the RK4 substeps with the state checkpointed at every substep
- * start and the stages recomputed.
+ * start and the stages recomputed.  For a model with the Eq. (12) auxiliary
+ * state (CISCVX_AUX_CROSS) or with coupled links, by linearize-and-contract
+ * instead: per chunk of intervals the dense blocks are formed in the
+ * workspace (as ciscvx_discretize computes them) and contracted,
+ * dL/dx~_k = A_k^T lambda_k - rho_k (path-penalty rows) - w_{k-1},
+ * dL/du = B-_k^T lambda_k / B+_k^T lambda_k (summed per node in the node
+ * layout), dL/ds_k = S_k . lambda_k, lambda_k = w_k + rho_k on the
+ * path-penalty rows; its workspace comes from
+ * ciscvx_discretize_workspace_size(CISCVX_OP_VJP) (no substep limit).
  *   w [N][n_x~], rho [N][n_c] (FP64, device; rho may be NULL when n_c == 0).
  *   gX [N+1][n_x~], gU like U, gs [N]: FP64 outputs (device), overwritten.
  *   L: optional FP64 scalar on the device (NULL to skip).

@@ -111,6 +111,7 @@ def load(path: str | None = None):
     lib.ciscvx_workspace_size.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_size_t)]
     lib.ciscvx_discretize_workspace_size.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_int,
                                                      ctypes.POINTER(ctypes.c_size_t),
                                                      ctypes.POINTER(ctypes.c_size_t)]
     lib.ciscvx_discretize.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -293,12 +294,13 @@ def workspace_size(model: Model, op: int, N: int, layout: str = "node") -> int:
     return n.value
 
 
-def discretize_workspace_size(model: Model, N: int, n_sub: int, precision: str = "fp64"):
-    """ciscvx_discretize_workspace_size: (min_bytes, full_bytes) of scratch (0, 0 unless coupled)."""
+def discretize_workspace_size(model: Model, N: int, n_sub: int, precision: str = "fp64",
+                              op: int = OP_DISCRETIZE, layout: str = "node"):
+    """ciscvx_discretize_workspace_size: (min_bytes, full_bytes) of scratch for `op`."""
     lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
-    _check(load().ciscvx_discretize_workspace_size(model.handle, int(N), int(n_sub),
-                                                   PRECISION[precision], ctypes.byref(lo),
-                                                   ctypes.byref(hi)))
+    _check(load().ciscvx_discretize_workspace_size(model.handle, int(op), int(N), int(n_sub),
+                                                   PRECISION[precision], LAYOUT[layout],
+                                                   ctypes.byref(lo), ctypes.byref(hi)))
     return lo.value, hi.value
 
 
@@ -331,7 +333,7 @@ def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layou
             out["z"] = torch.empty((N, nxt), dtype=f64, device=dev)
     ws_bytes = 0
     if model.coupled:
-        lo, hi = discretize_workspace_size(model, N, n_sub, precision)
+        lo, hi = discretize_workspace_size(model, N, n_sub, precision, OP_DISCRETIZE, layout)
         if workspace is None:
             workspace = torch.empty(max(lo, min(hi, DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
         ws_bytes = workspace.numel() * workspace.element_size()
@@ -417,9 +419,10 @@ def discretize_vjp(model: Model, X, U, s, w, rho, n_sub: int, precision: str = "
     if model.nc:
         _need(rho, "rho", f64)
     N = s.shape[0]
-    need = workspace_size(model, OP_VJP, N, layout)
-    if workspace is None or workspace.numel() * workspace.element_size() < need:
-        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
+    lo, hi = discretize_workspace_size(model, N, n_sub, precision, OP_VJP, layout)
+    if workspace is None or workspace.numel() * workspace.element_size() < lo:
+        workspace = torch.empty(max(lo, min(hi, DISCRETIZE_WS_CAP), 16), dtype=torch.uint8,
+                                device=X.device)
     gX = torch.empty_like(X)
     gU = torch.empty_like(U)
     gs = torch.empty_like(s)

@@ -416,25 +416,39 @@ ciscvx_status ciscvx_workspace_size(const ciscvx_model* m, ciscvx_op op, int N,
                                        "the precision: use ciscvx_discretize_workspace_size");
     *bytes = 0;
   }
-  else if (op == CISCVX_OP_VJP)
+  else if (op == CISCVX_OP_VJP) {
+    if (m->cpl || m->host.aux)
+      return fail(CISCVX_EUNSUPPORTED, "this model's VJP is linearize-and-contract, whose scratch depends on "
+                                       "n_sub and the precision: use ciscvx_discretize_workspace_size");
     *bytes = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
+  }
   else return fail(CISCVX_EINVAL, "unknown op %d", (int)op);
   return ok();
 }
 
-ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* m, int N, int n_sub,
-                                               ciscvx_precision precision, size_t* min_bytes,
+ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* m, ciscvx_op op, int N,
+                                               int n_sub, ciscvx_precision precision,
+                                               ciscvx_u_layout layout, size_t* min_bytes,
                                                size_t* full_bytes) {
   if (!m) return fail(CISCVX_EINVAL, "null model");
   if (N < 1 || n_sub < 1) return fail(CISCVX_EINVAL, "need N >= 1 and n_sub >= 1");
   if (precision != CISCVX_FP64 && precision != CISCVX_FP32_PHI && precision != CISCVX_TF32_TC &&
       precision != CISCVX_BF16_TC)
     return fail(CISCVX_EINVAL, "unknown precision %d", (int)precision);
+  if (!layout_ok(layout)) return fail(CISCVX_EINVAL, "unknown control layout %d", (int)layout);
+  if (op != CISCVX_OP_DISCRETIZE && op != CISCVX_OP_VJP) return fail(CISCVX_EINVAL, "unknown op %d", (int)op);
   size_t lo = 0, hi = 0;
-  if (m->cpl) {
-    const size_t per = cpl_interval_bytes(*m->cpl, n_sub, precision);
-    lo = per * (size_t)std::min(N, 32);
-    hi = per * (size_t)N;
+  if (op == CISCVX_OP_DISCRETIZE) {
+    if (m->cpl) {
+      const size_t per = cpl_interval_bytes(*m->cpl, n_sub, precision);
+      lo = per * (size_t)std::min(N, 32);
+      hi = per * (size_t)N;
+    }
+  } else if (m->cpl || m->host.aux) {
+    lo = contract_bytes(m->host, m->cpl, std::min(N, 32), n_sub, precision);
+    hi = contract_bytes(m->host, m->cpl, N, n_sub, precision);
+  } else {
+    lo = hi = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
   }
   if (min_bytes) *min_bytes = lo;
   if (full_bytes) *full_bytes = hi;
@@ -499,12 +513,21 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
                                     void* stream) {
   ciscvx_status st = check_common(m, N, n_sub, precision, layout, X, U, s);
   if (st != CISCVX_OK) return st;
-  if (n_sub > MAXSUB_VJP)
-    return fail(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (got %d)", MAXSUB_VJP, n_sub);
-  if (m->host.aux) return fail(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
-  if (m->cpl) return fail(CISCVX_EUNSUPPORTED, "the VJP is not provided for models with coupled links");
   if (!w || (m->host.nc > 0 && !rho)) return fail(CISCVX_EINVAL, "null cotangent array");
   if (!gX || !gs || (m->host.nu > 0 && !gU)) return fail(CISCVX_EINVAL, "null gradient array");
+  if (m->host.aux || m->cpl) {  // linearize-and-contract
+    const size_t need = contract_bytes(m->host, m->cpl, std::min(N, 32), n_sub, precision);
+    if (!workspace || ws_bytes < need)
+      return fail(CISCVX_EINVAL, "workspace of at least %zu bytes needed (got %zu)", need, ws_bytes);
+    if (((uintptr_t)workspace & 15) != 0) return fail(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+    cudaError_t e = launch_contract_vjp(m->host, m->dev, m->cpl, N, n_sub, precision, layout, X, U, s,
+                                        w, rho, gX, gU, gs, L, workspace, ws_bytes, m->status,
+                                        (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "contract vjp launch");
+    return ok();
+  }
+  if (n_sub > MAXSUB_VJP)
+    return fail(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (got %d)", MAXSUB_VJP, n_sub);
   const size_t need = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
   if (!workspace || ws_bytes < need)
     return fail(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);

@@ -1,0 +1,186 @@
+// contract.cu — the VJP by linearize-and-contract, for the models without a
+// reverse-mode adjoint kernel (the full Eq. (12) auxiliary state, coupled
+// links).  Per chunk of intervals the dense IND blocks are formed in the
+// workspace by the discretization kernels, then contracted with the cotangent
+// of the scalar L = sum_k w_k . defect_k + sum_k rho_k . penalty_k:
+//   lambda_k = w_k + rho_k on the path-penalty rows       (cotangent of x~(1) of interval k)
+//   dL/dx~_k = A_k^T lambda_k - (rho_k on the path-penalty rows) - w_{k-1}
+//   dL/du    = B-_k^T lambda_k at u_L, B+_k^T lambda_k at u_R (node layout:
+//              node k collects B-_k^T lambda_k + B+_{k-1}^T lambda_{k-1})
+//   dL/ds_k  = S_k . lambda_k
+// (defect_k = x~(1) - x~_{k+1}, penalty_k = y(1) - y_k, Eq. (17b)).  The
+// contraction runs one thread per (interval, output column), each a dot
+// product down one column of a block, so a warp's loads of one row are
+// contiguous; node-shared sums carry across chunk boundaries through the
+// output itself (chunks run in stream order), so no atomics are needed and
+// the result does not depend on the chunking.  L is reduced per chunk by one
+// block in a fixed order.
+#include "coupled.cuh"
+
+namespace ciscvx {
+
+namespace {
+
+template <typename TP>
+__global__ void k_contract(int nxt, int nu, int nc, int pen0, long i0, long n, long N, int layout,
+                           const TP* __restrict__ A, const TP* __restrict__ Bm,
+                           const TP* __restrict__ Bp, const TP* __restrict__ S,
+                           const double* __restrict__ w, const double* __restrict__ rho,
+                           double* __restrict__ gX, double* __restrict__ gU,
+                           double* __restrict__ gs) {
+  const int ncol = nxt + nu + 1;
+  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long t = g / ncol;
+  if (t >= n) return;
+  const int c = (int)(g - t * ncol);
+  const long k = i0 + t;
+  const double* wk = w + k * nxt;
+  auto lam = [&](const double* wv, long kk, int r) {
+    double v = wv[r];
+    if (r >= pen0 && r < pen0 + nc) v += rho[kk * nc + (r - pen0)];
+    return v;
+  };
+  if (c < nxt) {
+    const TP* a = A + (size_t)t * nxt * nxt + c;
+    double acc = 0.0;
+    for (int r = 0; r < nxt; ++r) acc = fma((double)a[(size_t)r * nxt], lam(wk, k, r), acc);
+    if (c >= pen0 && c < pen0 + nc) acc -= rho[k * nc + (c - pen0)];
+    if (k >= 1) acc -= w[(k - 1) * nxt + c];
+    gX[k * nxt + c] = acc;
+    if (k == N - 1) gX[N * nxt + c] = -wk[c];
+  } else if (c < nxt + nu) {
+    const int q = c - nxt;
+    const TP* bm = Bm + (size_t)t * nxt * nu + q;
+    const TP* bp = Bp + (size_t)t * nxt * nu + q;
+    double am = 0.0, ap = 0.0;
+    for (int r = 0; r < nxt; ++r) {
+      const double l = lam(wk, k, r);
+      am = fma((double)bm[(size_t)r * nu], l, am);
+      ap = fma((double)bp[(size_t)r * nu], l, ap);
+    }
+    if (layout == CISCVX_FOH_INTERVAL) {
+      gU[(2 * k) * nu + q] = am;
+      gU[(2 * k + 1) * nu + q] = ap;
+    } else {
+      // node k: B-_k^T lambda_k + B+_{k-1}^T lambda_{k-1}; the second term
+      // comes from this chunk's previous interval or, at the chunk's first
+      // interval, from the previous chunk (already stored in gU)
+      double prev = 0.0;
+      if (t > 0) {
+        const TP* bq = Bp + (size_t)(t - 1) * nxt * nu + q;
+        const double* wq = w + (k - 1) * nxt;
+        for (int r = 0; r < nxt; ++r) prev = fma((double)bq[(size_t)r * nu], lam(wq, k - 1, r), prev);
+      } else if (k > 0) {
+        prev = gU[k * nu + q];
+      }
+      gU[k * nu + q] = am + prev;
+      if (t == n - 1) gU[(k + 1) * nu + q] = ap;  // carried into node k + 1
+    }
+  } else {
+    const TP* sv = S + (size_t)t * nxt;
+    double acc = 0.0;
+    for (int r = 0; r < nxt; ++r) acc = fma((double)sv[r], lam(wk, k, r), acc);
+    gs[k] = acc;
+  }
+}
+
+// L += sum over the chunk of w . defect + rho . penalty (one block, fixed order).
+__global__ void __launch_bounds__(256) k_contract_L(int nxt, int nc, long i0, long n,
+                                                    const double* __restrict__ defect,
+                                                    const double* __restrict__ penalty,
+                                                    const double* __restrict__ w,
+                                                    const double* __restrict__ rho, double* L) {
+  __shared__ double part[256];
+  double acc = 0.0;
+  const long nd = n * nxt, np = n * nc;
+  for (long e = threadIdx.x; e < nd; e += 256) acc = fma(w[i0 * nxt + e], defect[e], acc);
+  for (long e = threadIdx.x; e < np; e += 256) acc = fma(rho[i0 * nc + e], penalty[e], acc);
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *L += part[0];
+}
+
+size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Workspace layout of one chunk of n intervals.
+struct ChunkLayout {
+  size_t A, Bm, Bp, S, defect, penalty, stage, total;
+};
+
+ChunkLayout chunk_layout(const DevModel& M, const CplTab* T, long n, int nsub, int prec) {
+  const size_t el = prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+  const size_t nxt = M.nxt, nu = M.nu, nc = M.nc;
+  ChunkLayout L;
+  size_t o = 0;
+  L.A = o; o = align16(o + n * nxt * nxt * el);
+  L.Bm = o; o = align16(o + n * nxt * nu * el);
+  L.Bp = o; o = align16(o + n * nxt * nu * el);
+  L.S = o; o = align16(o + n * nxt * el);
+  L.defect = o; o = align16(o + n * nxt * sizeof(double));
+  L.penalty = o; o = align16(o + n * nc * sizeof(double));
+  L.stage = o; o = align16(o + (T ? n * cpl_interval_bytes(*T, nsub, prec) : 0));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+size_t contract_bytes(const DevModel& M, const CplTab* T, long n, int nsub, int prec) {
+  return chunk_layout(M, T, n, nsub, prec).total;
+}
+
+cudaError_t launch_contract_vjp(const DevModel& Mh, const DevModel* dM, const CplTab* T, int N,
+                                int nsub, int prec, int layout, const double* X, const double* U,
+                                const double* s, const double* w, const double* rho, double* gX,
+                                double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
+                                unsigned* status, cudaStream_t st) {
+  const int nxt = Mh.nxt, nu = Mh.nu, nc = Mh.nc;
+  const int pen0 = 6 * Mh.nb + (Mh.aux ? 4 * nc : 0);
+  // largest chunk that fits (the caller checked that min(N, 32) intervals do)
+  long lo = 1, hi = N;
+  while (lo < hi) {
+    const long mid = (lo + hi + 1) / 2;
+    if (contract_bytes(Mh, T, mid, nsub, prec) <= ws_bytes) lo = mid; else hi = mid - 1;
+  }
+  const long chunk = lo;
+  cudaError_t e = cudaSuccess;
+  if (L) e = cudaMemsetAsync(L, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  char* base = (char*)ws;
+  for (long i0 = 0; i0 < N; i0 += chunk) {
+    const long n = std::min<long>(chunk, N - i0);
+    const ChunkLayout Ly = chunk_layout(Mh, T, n, nsub, prec);
+    void *A = base + Ly.A, *Bm = base + Ly.Bm, *Bp = base + Ly.Bp, *S = base + Ly.S;
+    double* defect = (double*)(base + Ly.defect);
+    double* penalty = (double*)(base + Ly.penalty);
+    const double* Xc = X + i0 * nxt;
+    const double* Uc = U ? (layout == CISCVX_FOH_NODE ? U + i0 * nu : U + 2 * i0 * nu) : nullptr;
+    if (T)
+      e = launch_coupled(*T, (int)n, nsub, prec, layout, Xc, Uc, s + i0, A, Bm, Bp, S, defect, penalty,
+                         base + Ly.stage, n, status, st);
+    else
+      e = launch_discretize(dM, Mh.nb, (int)n, nsub, prec, layout, false, Mh.aux != 0, Xc, Uc, s + i0,
+                            A, Bm, Bp, S, defect, penalty, nullptr, status, st);
+    if (e != cudaSuccess) return e;
+    const long threads = n * (nxt + nu + 1);
+    const int bs = 128;
+    if (prec == CISCVX_FP64)
+      k_contract<double><<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(
+          nxt, nu, nc, pen0, i0, n, N, layout, (const double*)A, (const double*)Bm,
+          (const double*)Bp, (const double*)S, w, rho, gX, gU, gs);
+    else
+      k_contract<float><<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(
+          nxt, nu, nc, pen0, i0, n, N, layout, (const float*)A, (const float*)Bm,
+          (const float*)Bp, (const float*)S, w, rho, gX, gU, gs);
+    if (L) k_contract_L<<<1, 256, 0, st>>>(nxt, nc, i0, n, defect, penalty, w, rho, L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace ciscvx

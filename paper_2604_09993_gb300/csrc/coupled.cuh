@@ -90,4 +90,13 @@ cudaError_t launch_coupled(const CplTab& T, int N, int nsub, int prec, int layou
                            double* defect, double* penalty, void* ws, long chunk,
                            unsigned* status, cudaStream_t st);
 
+// VJP by linearize-and-contract (contract.cu): workspace bytes for a chunk of
+// n intervals, and the chunked launch (T null for per-link models).
+size_t contract_bytes(const DevModel& M, const CplTab* T, long n, int nsub, int prec);
+cudaError_t launch_contract_vjp(const DevModel& Mh, const DevModel* dM, const CplTab* T, int N,
+                                int nsub, int prec, int layout, const double* X, const double* U,
+                                const double* s, const double* w, const double* rho, double* gX,
+                                double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
+                                unsigned* status, cudaStream_t st);
+
 }  // namespace ciscvx

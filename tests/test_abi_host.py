@@ -56,7 +56,7 @@ def test_null_arguments_rejected(lib):
     assert lib.ciscvx_discretize_compact(None, 10, 4, 0, 0, None, None, None, None, None, None,
                                          None, None, None, None, None) == api.EINVAL
     lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
-    assert lib.ciscvx_discretize_workspace_size(None, 10, 4, 0, ctypes.byref(lo),
+    assert lib.ciscvx_discretize_workspace_size(None, 0, 10, 4, 0, 0, ctypes.byref(lo),
                                                 ctypes.byref(hi)) == api.EINVAL
 
 

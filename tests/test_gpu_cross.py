@@ -1,7 +1,8 @@
 """GPU parity of the full Eq. (12) auxiliary state (CISCVX_AUX_CROSS) against
 the FP64 oracle through the C ABI: single-instance and batched linearization,
 both precisions and both control layouts, mixed batches of the two auxiliary
-models, feasible inputs, and the entry points that return EUNSUPPORTED for it.
+models, feasible inputs, the linearize-and-contract VJP, and the entry points
+that return EUNSUPPORTED for it.
 Tolerances as for the default model (FP64 1e-10; FP32-Phi blocks 1e-4,
 defect and penalty 1e-10)."""
 import numpy as np
@@ -135,7 +136,6 @@ def test_cross_unsupported_entry_points(env):
     rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
     for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
                  lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
-                 lambda: api.discretize_vjp(m, X, U, s, w, rho, p.n_sub, "fp64"),
                  lambda: api.model_pattern(p.robot.as_dict()),
                  lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
         with pytest.raises(api.CiscvxError) as e:
@@ -166,3 +166,29 @@ def test_cross_node_constraints(env):
     ref = oracle.node(R, Xp, Xm, Phi, Gam, 1e-3, e)
     assert block_err(out["g"].cpu().numpy(), ref["g"]) <= TOL_FP64
     assert block_err(out["theta"].cpu().numpy().reshape(n, -1), ref["theta"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("layout", ["node", "interval"])
+def test_cross_vjp_matches_oracle(env, precision, tol, layout):
+    """The VJP of this model is linearize-and-contract: against the oracle's
+    Phi-contracted gradient, with a workspace of the minimum size (chunks of 32)."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("biped", 17, 75, 3)
+    rng = np.random.default_rng(18)
+    m = api.Model(p.robot)
+    w = rng.standard_normal((p.N, m.nxt))
+    rho = np.full((p.N, m.nc), 10.0)
+    U = p.U if layout == "node" else p.U_interval()
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    lo, hi = api.discretize_workspace_size(m, p.N, p.n_sub, precision, api.OP_VJP, layout)
+    assert lo < hi
+    ws = torch.empty(lo, dtype=torch.uint8, device=dev)
+    gX, gU, gs, L = api.discretize_vjp(m, t(p.X), t(U), t(p.s), t(w), t(rho), p.n_sub, precision,
+                                       layout, workspace=ws)
+    api.sync_status(m)
+    rX, rU, rs, rL = oracle.vjp(p.robot.as_dict(), p.X, U, p.s, w, rho, p.n_sub, layout=layout)
+    for g, r, nm in ((gX, rX, "gX"), (gU, rU, "gU"), (gs, rs, "gs")):
+        assert block_err(g.cpu().numpy(), r) <= tol, (nm, block_err(g.cpu().numpy(), r))
+    assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))

@@ -4,8 +4,10 @@ against the FP64 oracle, through the C ABI.
 
 Tolerances as for the per-link path: FP64 rel <= 1e-10 on every block
 (block-normwise); FP32-Phi rel <= 1e-4 on A, B-, B+, S and rel <= 1e-10 on
-defect and penalty.  Sizes span several warps of intervals, thread blocks of
-tangent columns and a ragged tail; a short workspace forces several chunks.
+defect and penalty; the linearize-and-contract VJP against the oracle's
+Phi-contracted gradient at the same tolerances.  Sizes span several warps of
+intervals, thread blocks of tangent columns and a ragged tail; a short
+workspace forces several chunks.
 """
 import numpy as np
 import pytest
@@ -135,15 +137,12 @@ def test_unsupported_entry_points(env):
     m = api.Model(p.robot)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     X, U, s = t(p.X), t(p.U), t(p.s)
-    w = torch.zeros((p.N, m.nxt), dtype=torch.float64, device=dev)
-    rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
     e = np.full(m.nc, 0.0)
     Phi = torch.zeros((3, 2 * m.nc), dtype=torch.float64, device=dev)
     Gam = torch.zeros((3, m.nc), dtype=torch.float64, device=dev)
     Xn = torch.zeros((3, m.nxt), dtype=torch.float64, device=dev)
     for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
                  lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
-                 lambda: api.discretize_vjp(m, X, U, s, w, rho, p.n_sub, "fp64"),
                  lambda: api.model_pattern(p.robot.as_dict()),
                  lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub]),
                  lambda: api.node_linearize(m, Xn, Xn, Phi, Gam, 1e-3, e)):
@@ -197,3 +196,63 @@ def test_sweep_size_sampled(env):
         ref = oracle.discretize(p.robot.as_dict(), p.X[k:k + 2], p.U[k:k + 2], p.s[k:k + 1], p.n_sub)
         got = {kk: v[k:k + 1].double().cpu().numpy() for kk, v in out.items()}
         _check(got, ref, "fp32_phi")
+
+
+def _vjp(env, p, precision, layout="node", workspace=None):
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(30)
+    m = api.Model(p.robot)
+    w = rng.standard_normal((p.N, m.nxt))
+    rho = np.full((p.N, m.nc), 10.0)
+    U = p.U if layout == "node" else p.U_interval()
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    got = api.discretize_vjp(m, t(p.X), t(U), t(p.s), t(w), t(rho), p.n_sub, precision, layout,
+                             workspace=workspace)
+    api.sync_status(m)
+    ref = oracle.vjp(p.robot.as_dict(), p.X, U, p.s, w, rho, p.n_sub, layout=layout)
+    return got, ref
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("layout", ["node", "interval"])
+def test_vjp_matches_oracle(env, precision, tol, layout):
+    p = _problem("cheetah7", 31, 45, 3, **PAPER)
+    (gX, gU, gs, L), (rX, rU, rs, rL) = _vjp(env, p, precision, layout)
+    for g, r, nm in ((gX, rX, "gX"), (gU, rU, "gU"), (gs, rs, "gs")):
+        assert block_err(g.cpu().numpy(), r) <= tol, (nm, block_err(g.cpu().numpy(), r))
+    assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))
+
+
+def test_vjp_chunking_is_bitwise_equal(env):
+    """A minimum workspace (chunks of 32 intervals, node-shared sums carried
+    across chunk boundaries) gives the same gradient as one chunk."""
+    torch, oracle, api = env
+    p = _problem("biped", 32, 77, 2, **PAPER)
+    m = api.Model(p.robot)
+    lo, hi = api.discretize_workspace_size(m, p.N, p.n_sub, "fp64", api.OP_VJP)
+    dev = torch.device("cuda:0")
+    a = _vjp(env, p, "fp64", workspace=torch.empty(lo, dtype=torch.uint8, device=dev))[0]
+    b = _vjp(env, p, "fp64", workspace=torch.empty(hi, dtype=torch.uint8, device=dev))[0]
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+    assert a[3].item() != 0.0
+
+
+def test_autograd_through_the_coupled_path(env):
+    """torch.autograd through discretize_fn: backward is the contracted VJP."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("hopper", 33, 12, 3, **PAPER)
+    m = api.Model(p.robot)
+    X = torch.tensor(p.X, device=dev, requires_grad=True)
+    U = torch.tensor(p.U, device=dev, requires_grad=True)
+    s = torch.tensor(p.s, device=dev, requires_grad=True)
+    d, pen = api.discretize_fn(m, X, U, s, p.n_sub, "fp64")
+    w = torch.randn_like(d)
+    (d * w).sum().add((pen * 10.0).sum()).backward()
+    rho = np.full((p.N, m.nc), 10.0)
+    rX, rU, rs, _ = oracle.vjp(p.robot.as_dict(), p.X, p.U, p.s, w.cpu().numpy(), rho, p.n_sub)
+    assert block_err(X.grad.cpu().numpy(), rX) <= TOL_FP64
+    assert block_err(U.grad.cpu().numpy(), rU) <= TOL_FP64
+    assert block_err(s.grad.cpu().numpy(), rs) <= TOL_FP64
