@@ -445,15 +445,8 @@ def run_ours(args):
     from paper_2604_09993_gb300 import api, build
     build.build()
     api.load()
-    spec = WORKLOADS[args.workload]
-    n_inst = args.instances or spec["instances"]
-    wl = (BatchWorkload if spec["kind"] == "batch" else SingleWorkload)(spec, n_inst, dev, seed=rank)
     stream = torch.cuda.current_stream()
-    prec = args.precision
     global L2_FLUSH
-    in_bytes = sum(getattr(wl, k).numel() * 8 for k in ("X", "U", "s", "w", "rho"))
-    if in_bytes <= L2_BYTES:
-        L2_FLUSH = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
         if world > 1:
@@ -464,6 +457,84 @@ def run_ours(args):
     def max_over_ranks(vals):
         from paper_2604_09993_gb300 import dist as pdist
         return pdist.max_over_ranks(vals, device=dev)
+
+    def measure_paper():
+        """The paper's own model on the 7-link chain (joint reaction forces
+        eliminated by Eq. (3), RKF45 substeps, sinusoidal surface): the
+        coupled-links path, one instance of args.paper_intervals intervals x
+        10 substeps per GPU; linearization and its VJP, FP32-Phi and FP64."""
+        global L2_FLUSH
+        saved = L2_FLUSH
+        if L2_FLUSH is None:  # its inputs fit in L2: flush it before every timed call
+            L2_FLUSH = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+        torch.cuda.empty_cache()
+        pp = synth.cheetah_paper_sweep(seed=rank, N=args.paper_intervals)
+        mp = api.Model(pp.robot)
+        t_ = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+        Xp, Up, sp = t_(pp.X), t_(pp.U), t_(pp.s)
+        paper = {"metric": "linearized intervals/s (STM), and of the linearize-and-contract VJP",
+                 "unit": "intervals/s",
+                 "workload": f"7-link chain, eliminated joint forces, RKF45, sinusoidal surface "
+                             f"{synth.TERRAIN_SINE[0]} sin({synth.TERRAIN_SINE[1]:.4f} x), "
+                             f"1 x {pp.N} intervals x {pp.n_sub} substeps per GPU",
+                 }
+        precs = ("fp32_phi", "fp64") if args.paper_precision == "both" else (args.paper_precision,)
+        for pr in precs:
+            lo, hi = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr)
+            ws = torch.empty(max(lo, min(hi, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+            out = api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, workspace=ws)
+            fn = lambda: api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, out=out, workspace=ws)  # noqa: E731
+            barrier()
+            tp = time_steps(torch, fn, args.steps, args.warmup, stream)
+            barrier()
+            api.sync_status(mp)
+            tp, = max_over_ranks([tp])
+            paper[pr] = {"value": pp.N * world * args.steps / tp, "ms_per_call": tp / args.steps * 1e3,
+                         "chunks": -(-hi // ws.numel()), "workspace_bytes": ws.numel()}
+            del out, ws
+            torch.cuda.empty_cache()
+            # the VJP of the same workload (dense blocks per chunk, then A^T lambda, B^T lambda, S . lambda)
+            wv = torch.randn((pp.N, mp.nxt), dtype=torch.float64, device=dev)
+            rv = torch.full((pp.N, mp.nc), 10.0, dtype=torch.float64, device=dev)
+            lo, hi = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr, api.OP_VJP)
+            ws = torch.empty(max(lo, min(hi, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+            fv = lambda: api.discretize_vjp(mp, Xp, Up, sp, wv, rv, pp.n_sub, pr, workspace=ws)  # noqa: E731
+            barrier()
+            tv = time_steps(torch, fv, max(1, args.steps // 2), args.warmup, stream)
+            barrier()
+            api.sync_status(mp)
+            tv, = max_over_ranks([tv])
+            paper[pr]["vjp"] = {"value": pp.N * world * max(1, args.steps // 2) / tv,
+                                "ms_per_call": tv / max(1, args.steps // 2) * 1e3}
+            del ws, wv, rv
+            torch.cuda.empty_cache()
+        del Xp, Up, sp, mp
+        if world == 1 and not args.no_cpu_baseline:
+            paper["cpu_baseline"] = paper_cpu_baseline(pp)
+
+        L2_FLUSH = saved
+        return paper
+
+    if args.paper_only:
+        paper = measure_paper()
+        if rank == 0:
+            f32 = paper.get("fp32_phi") or paper["fp64"]
+            print(json.dumps({
+                "metric": paper["metric"], "value": f32["value"], "unit": "intervals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": f32["ms_per_call"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 state + f32 Phi", "data": "synthetic (seeded robot)",
+                "config": {"workload": paper["workload"], "l2": "L2 flushed before every timed call"},
+                "paper_dynamics": paper}))
+        return
+
+    spec = WORKLOADS[args.workload]
+    n_inst = args.instances or spec["instances"]
+    wl = (BatchWorkload if spec["kind"] == "batch" else SingleWorkload)(spec, n_inst, dev, seed=rank)
+    prec = args.precision
+    in_bytes = sum(getattr(wl, k).numel() * 8 for k in ("X", "U", "s", "w", "rho"))
+    if in_bytes <= L2_BYTES:
+        L2_FLUSH = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
     # plain FP64 GPU path (comparator)
     t64 = kd64 = None
@@ -594,55 +665,12 @@ def run_ours(args):
         wl.free(prec, "compact")
 
     # the paper's own model on the 7-link chain (joint reaction forces
-    # eliminated by Eq. (3), RKF45 substeps, sinusoidal surface): the
-    # coupled-links path, one instance of 65 536 intervals x 10 substeps per GPU
+    # eliminated by Eq. (3), RKF45, sinusoidal surface): the coupled-links path
     paper = None
     if not args.no_paper:
         if spec["kind"] == "batch":
             wl.free(prec)
-        torch.cuda.empty_cache()
-        pp = synth.cheetah_paper_sweep(seed=rank)
-        mp = api.Model(pp.robot)
-        t_ = lambda a: torch.tensor(a, device=dev)  # noqa: E731
-        Xp, Up, sp = t_(pp.X), t_(pp.U), t_(pp.s)
-        paper = {"metric": "linearized intervals/s (STM), and of the linearize-and-contract VJP",
-                 "unit": "intervals/s",
-                 "workload": f"7-link chain, eliminated joint forces, RKF45, sinusoidal surface "
-                             f"{synth.TERRAIN_SINE[0]} sin({synth.TERRAIN_SINE[1]:.4f} x), "
-                             f"1 x {pp.N} intervals x {pp.n_sub} substeps per GPU",
-                 }
-        for pr in ("fp32_phi", "fp64"):
-            lo, hi = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr)
-            ws = torch.empty(max(lo, min(hi, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
-            out = api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, workspace=ws)
-            fn = lambda: api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, out=out, workspace=ws)  # noqa: E731
-            barrier()
-            tp = time_steps(torch, fn, args.steps, args.warmup, stream)
-            barrier()
-            api.sync_status(mp)
-            tp, = max_over_ranks([tp])
-            paper[pr] = {"value": pp.N * world * args.steps / tp, "ms_per_call": tp / args.steps * 1e3,
-                         "chunks": -(-hi // ws.numel()), "workspace_bytes": ws.numel()}
-            del out, ws
-            torch.cuda.empty_cache()
-            # the VJP of the same workload (dense blocks per chunk, then A^T lambda, B^T lambda, S . lambda)
-            wv = torch.randn((pp.N, mp.nxt), dtype=torch.float64, device=dev)
-            rv = torch.full((pp.N, mp.nc), 10.0, dtype=torch.float64, device=dev)
-            lo, hi = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr, api.OP_VJP)
-            ws = torch.empty(max(lo, min(hi, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
-            fv = lambda: api.discretize_vjp(mp, Xp, Up, sp, wv, rv, pp.n_sub, pr, workspace=ws)  # noqa: E731
-            barrier()
-            tv = time_steps(torch, fv, max(1, args.steps // 2), args.warmup, stream)
-            barrier()
-            api.sync_status(mp)
-            tv, = max_over_ranks([tv])
-            paper[pr]["vjp"] = {"value": pp.N * world * max(1, args.steps // 2) / tv,
-                                "ms_per_call": tv / max(1, args.steps // 2) * 1e3}
-            del ws, wv, rv
-            torch.cuda.empty_cache()
-        del Xp, Up, sp, mp
-        if world == 1 and not args.no_cpu_baseline:
-            paper["cpu_baseline"] = paper_cpu_baseline(pp)
+        paper = measure_paper()
 
     if rank != 0:
         return
@@ -711,6 +739,11 @@ def main():
     ap.add_argument("--no-nodes", action="store_true", help="skip the node-constraint measurement")
     ap.add_argument("--no-paper", action="store_true",
                     help="skip the paper-dynamics (coupled links) measurement")
+    ap.add_argument("--paper-only", action="store_true",
+                    help="run only the paper-dynamics measurement (its own JSON line)")
+    ap.add_argument("--paper-intervals", type=int, default=65536,
+                    help="intervals of the paper-dynamics instance")
+    ap.add_argument("--paper-precision", default="both", choices=["both", "fp32_phi", "fp64"])
     ap.add_argument("--cross", action="store_true",
                     help="also time the linearization with the full Eq. (12) auxiliary state")
     args = ap.parse_args()
