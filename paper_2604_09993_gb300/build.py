@@ -55,11 +55,27 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return _build_locked(verbose, ptxas_info)
 
 
+JIT_SRC = os.path.join(CSRC, "cpl_tangent_jit.cuh")
+
+
+def _embed_jit_source(objdir):
+    """Writes the run-time compiled device source into a C++ raw string literal."""
+    text = open(JIT_SRC).read()
+    assert ")CPLJIT" not in text
+    out = os.path.join(objdir, "cpl_tangent_jit_src.inc")
+    body = 'static const char kCplTangentJitSrc[] = R"CPLJIT(' + text + ')CPLJIT";\n'
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
+
+
 def _build_locked(verbose, ptxas_info):
     nvcc = nvcc_path()
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
+    _embed_jit_source(objdir)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra += ["-I", objdir]
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")

@@ -27,6 +27,7 @@
 // per-thread arrays live in shared memory, element major, so a warp's access
 // to one element is one contiguous row.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 
 #include "coupled.cuh"
@@ -700,6 +701,7 @@ cudaError_t run(const CplTab& T, int N, int nsub, int layout, const double* X, c
                 const double* s, void* A, void* Bm, void* Bp, void* S, double* defect,
                 double* penalty, void* ws, long chunk, unsigned* status, cudaStream_t st) {
   const size_t sm1 = (size_t)T.n_size * sizeof(double) * 32;
+  const CplJit* jit = cpl_jit_tangent(T, std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI);
   const int bs = tangent_block<TP>(T);
   const size_t sm2 = (size_t)bs * T.t_size * sizeof(TP);
   cudaError_t e = cudaFuncSetAttribute(k_cpl_nominal<TP, SCH>,
@@ -713,9 +715,16 @@ cudaError_t run(const CplTab& T, int N, int nsub, int layout, const double* X, c
     k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
         T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status);
     const long threads = n * T.cnt;
-    k_cpl_tangent<TP, SCH><<<(unsigned)((threads + bs - 1) / bs), bs, sm2, st>>>(
-        T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status);
-    e = cudaGetLastError();
+    if (jit) {
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = cpl_jit_launch(*jit, T, std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI, i0, n,
+                           nsub, s, ws, A, Bm, Bp, S, status, st);
+    } else {
+      k_cpl_tangent<TP, SCH><<<(unsigned)((threads + bs - 1) / bs), bs, sm2, st>>>(
+          T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

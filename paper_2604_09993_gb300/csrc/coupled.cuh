@@ -90,6 +90,18 @@ cudaError_t launch_coupled(const CplTab& T, int N, int nsub, int prec, int layou
                            double* defect, double* penalty, void* ws, long chunk,
                            unsigned* status, cudaStream_t st);
 
+// Run-time specialized tangent kernel (jit.cu): null when unavailable (no
+// NVRTC, a failed compile, or CISCVX_COUPLED_JIT=0); then the generic kernel runs.
+struct CplJit {
+  void* fn = nullptr;  // CUfunction
+  int bs = 0;
+  size_t smem = 0;
+};
+const CplJit* cpl_jit_tangent(const CplTab& T, int prec);
+cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,
+                           const double* s, const void* sd, void* A, void* Bm, void* Bp, void* S,
+                           unsigned* status, cudaStream_t st);
+
 // VJP by linearize-and-contract (contract.cu): workspace bytes for a chunk of
 // n intervals, and the chunked launch (T null for per-link models).
 size_t contract_bytes(const DevModel& M, const CplTab* T, long n, int nsub, int prec);

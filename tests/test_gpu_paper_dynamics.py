@@ -256,3 +256,22 @@ def test_autograd_through_the_coupled_path(env):
     assert block_err(X.grad.cpu().numpy(), rX) <= TOL_FP64
     assert block_err(U.grad.cpu().numpy(), rU) <= TOL_FP64
     assert block_err(s.grad.cpu().numpy(), rs) <= TOL_FP64
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_phi", 1e-5)])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_specialized_and_generic_tangent_kernels_agree(env, precision, tol, scheme, monkeypatch):
+    """The run-time specialized tangent kernel (default) and the generic one
+    (CISCVX_COUPLED_JIT=0) compute the same blocks; both meet the oracle."""
+    torch, oracle, api = env
+    p = _problem("cheetah7", 34, 41, 3, joint_forces=1, scheme=scheme, terrain=synth.TERRAIN_SINE)
+    got_jit, ref = _run(env, p, precision)
+    monkeypatch.setenv("CISCVX_COUPLED_JIT", "0")
+    got_gen, _ = _run(env, p, precision)
+    monkeypatch.delenv("CISCVX_COUPLED_JIT")
+    _check(got_jit, ref, precision)
+    _check(got_gen, ref, precision)
+    for k in PHI:
+        assert block_err(got_jit[k], got_gen[k]) <= tol, k
+    for k in STATE:
+        assert np.array_equal(got_jit[k], got_gen[k]), k
