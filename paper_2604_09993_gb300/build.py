@@ -55,15 +55,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return _build_locked(verbose, ptxas_info)
 
 
-JIT_SRC = os.path.join(CSRC, "cpl_tangent_jit.cuh")
-
-
 def _embed_jit_source(objdir):
-    """Writes the run-time compiled device source into a C++ raw string literal."""
-    text = open(JIT_SRC).read()
-    assert ")CPLJIT" not in text
-    out = os.path.join(objdir, "cpl_tangent_jit_src.inc")
-    body = 'static const char kCplTangentJitSrc[] = R"CPLJIT(' + text + ')CPLJIT";\n'
+    """Writes the device sources the library compiles at run time (NVRTC) into
+    C++ raw string literals: the shared scalar math followed by each kernel."""
+    math = open(os.path.join(CSRC, "dev_math.cuh")).read()
+    body = ""
+    for var, fname in (("kCplTangentJitSrc", "cpl_tangent_jit.cuh"), ("kCplNominalJitSrc", "cpl_nominal_jit.cuh")):
+        text = math + open(os.path.join(CSRC, fname)).read()
+        assert ")CPLJIT" not in text
+        body += f'static const char {var}[] = R"CPLJIT(' + text + ')CPLJIT";\n'
+    out = os.path.join(objdir, "cpl_jit_src.inc")
     if not os.path.exists(out) or open(out).read() != body:
         with open(out, "w") as f:
             f.write(body)

@@ -701,7 +701,9 @@ cudaError_t run(const CplTab& T, int N, int nsub, int layout, const double* X, c
                 const double* s, void* A, void* Bm, void* Bp, void* S, double* defect,
                 double* penalty, void* ws, long chunk, unsigned* status, cudaStream_t st) {
   const size_t sm1 = (size_t)T.n_size * sizeof(double) * 32;
-  const CplJit* jit = cpl_jit_tangent(T, std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI);
+  const int prec = std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI;
+  const CplJit* jit = cpl_jit_tangent(T, prec);
+  const CplJit* jnom = cpl_jit_nominal(T, prec);
   const int bs = tangent_block<TP>(T);
   const size_t sm2 = (size_t)bs * T.t_size * sizeof(TP);
   cudaError_t e = cudaFuncSetAttribute(k_cpl_nominal<TP, SCH>,
@@ -712,14 +714,17 @@ cudaError_t run(const CplTab& T, int N, int nsub, int layout, const double* X, c
   if (e != cudaSuccess) return e;
   for (long i0 = 0; i0 < N; i0 += chunk) {
     const long n = std::min<long>(chunk, N - i0);
-    k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
-        T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status);
+    if (jnom)
+      e = cpl_jit_launch_nominal(*jnom, T, i0, n, nsub, layout, X, U, s, ws, A, defect, penalty, status, st);
+    else
+      k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
+          T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status);
+    if (e != cudaSuccess) return e;
     const long threads = n * T.cnt;
     if (jit) {
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        e = cpl_jit_launch(*jit, T, std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI, i0, n,
-                           nsub, s, ws, A, Bm, Bp, S, status, st);
+        e = cpl_jit_launch(*jit, T, prec, i0, n, nsub, s, ws, A, Bm, Bp, S, status, st);
     } else {
       k_cpl_tangent<TP, SCH><<<(unsigned)((threads + bs - 1) / bs), bs, sm2, st>>>(
           T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status);

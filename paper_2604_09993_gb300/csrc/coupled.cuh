@@ -98,6 +98,11 @@ struct CplJit {
   size_t smem = 0;
 };
 const CplJit* cpl_jit_tangent(const CplTab& T, int prec);
+const CplJit* cpl_jit_nominal(const CplTab& T, int prec);
+cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, long n, int nsub,
+                                   int layout, const double* X, const double* U, const double* s,
+                                   void* sd, void* A, double* defect, double* penalty,
+                                   unsigned* status, cudaStream_t st);
 cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,
                            const double* s, const void* sd, void* A, void* Bm, void* Bp, void* S,
                            unsigned* status, cudaStream_t st);

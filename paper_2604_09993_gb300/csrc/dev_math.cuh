@@ -1,0 +1,98 @@
+// dev_math.cuh — scalar device math shared by the library's kernels and by
+// the sources the library compiles at run time (NVRTC): no host headers, only
+// CUDA built-ins.
+#pragma once
+
+namespace ciscvx {
+
+// Pseudo-Huber ramp h(z) = sqrt(1 + p^2) - 1 = p^2 / (1 + sqrt(1 + p^2)),
+// p = max(z, 0), and its derivative h'(z) = p / sqrt(1 + p^2).
+__device__ __forceinline__ void huber(double z, double& H, double& D) {
+  const double p = fmax(z, 0.0);
+  const double r = sqrt(fma(p, p, 1.0));
+  H = (p * p) / (1.0 + r);
+  D = p / r;
+}
+
+// Value only: h(z) in FP64 for the penalty state, as a rsqrt(a) - 1 with
+// a = 1 + z^2 (about 7 FP64 issue slots on this GPU against about 18 for
+// z^2 / (1 + sqrt(a))).  Its absolute error is a few ulp of a, i.e. ~1e-15
+// for |z| <= 10; the cancellation for small z only affects the relative error
+// of values far below the penalty's magnitude.  Lanes with z <= 0 skip it.
+__device__ __forceinline__ double huber_value(double z) {
+  double H = 0.0;
+  if (__double_as_longlong(z) > 0) {  // z > 0, tested on the bit pattern
+    const double a = fma(z, z, 1.0);
+    H = fma(a, rsqrt(a), -1.0);
+  }
+  return H;
+}
+
+// Value in FP32 (adjoint weights only; the penalty state itself uses the FP64 value).
+__device__ __forceinline__ float huber_value(float z) {
+  const float p = fmaxf(z, 0.0f);
+  return (p * p) / (1.0f + sqrtf(fmaf(p, p, 1.0f)));
+}
+
+// Derivative only, in the tangent precision: h'(z) = p / sqrt(1 + p^2).
+__device__ __forceinline__ float huber_slope(float z) {
+  const float p = fmaxf(z, 0.0f);
+  return p * rsqrtf(fmaf(p, p, 1.0f));
+}
+__device__ __forceinline__ double huber_slope(double z) {
+  const double p = fmax(z, 0.0);
+  return p * rsqrt(fma(p, p, 1.0));
+}
+
+// (sin, cos) of theta + d from (s0, c0) = (sin theta, cos theta) by angle
+// addition, with sin d and cos d from their Taylor series.  Two tiers, chosen
+// per warp so that no FP64 instruction runs partly masked:
+//  * short, used when every active lane has |d| <= 0.02:
+//    sin d through d^5, cos d through d^6 (truncation <= 2.6e-16 absolute);
+//  * long, |d| <= 0.2: sin d through d^9, cos d through d^10 (<= 5e-16).
+// Lanes with |d| > 0.2 (or a NaN) return false; the caller uses sincos.
+constexpr double ROT_SHORT = 0.02;
+constexpr double ROT_DMAX = 0.2;
+
+__device__ __forceinline__ unsigned long long abs_bits(double d) {
+  return (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ bool rotate_small(double s0, double c0, double d, bool short_tier,
+                                             double& s, double& c) {
+  if (abs_bits(d) > (unsigned long long)__double_as_longlong(ROT_DMAX)) return false;
+  const double x = d * d;
+  double ps, pc;
+  if (short_tier) {
+    ps = fma(x, 1.0 / 120.0, -1.0 / 6.0);
+    ps = fma(ps, x, 1.0);
+    pc = fma(x, -1.0 / 720.0, 1.0 / 24.0);
+    pc = fma(pc, x, -0.5);
+  } else {
+    ps = fma(x, 1.0 / 362880.0, -1.0 / 5040.0);
+    ps = fma(ps, x, 1.0 / 120.0);
+    ps = fma(ps, x, -1.0 / 6.0);
+    ps = fma(ps, x, 1.0);
+    pc = fma(x, -1.0 / 3628800.0, 1.0 / 40320.0);
+    pc = fma(pc, x, -1.0 / 720.0);
+    pc = fma(pc, x, 1.0 / 24.0);
+    pc = fma(pc, x, -0.5);
+  }
+  const double sd = d * ps;
+  const double cd = fma(pc, x, 1.0);
+  s = fma(s0, cd, c0 * sd);
+  c = fma(c0, cd, -(s0 * sd));
+  return true;
+}
+
+// (sin, cos) of theta0 + d given those of theta0; `active` is the mask of
+// lanes executing this call (they vote on the tier); falls back to
+// sincos(theta0 + d), the sum formed only on that path.
+__device__ __forceinline__ void sincos_step(double th0, double s0, double c0, double d,
+                                            unsigned active, double& s, double& c) {
+  const bool short_tier =
+      __all_sync(active, abs_bits(d) <= (unsigned long long)__double_as_longlong(ROT_SHORT));
+  if (!rotate_small(s0, c0, d, short_tier, s, c)) sincos(th0 + d, &s, &c);
+}
+
+}  // namespace ciscvx

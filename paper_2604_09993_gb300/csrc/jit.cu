@@ -25,7 +25,7 @@
 #include <vector>
 
 #include "coupled.cuh"
-#include "cpl_tangent_jit_src.inc"  // kCplTangentJitSrc (generated from cpl_tangent_jit.cuh)
+#include "cpl_jit_src.inc"  // kCplTangentJitSrc, kCplNominalJitSrc (generated from the .cuh sources)
 
 namespace ciscvx {
 
@@ -99,11 +99,11 @@ void arr(std::ostringstream& o, const char* name, const T* v, int n) {
   o << "};\n";
 }
 
-void tab(std::ostringstream& o, const char* name, const double* v, int n) {
+void tab(std::ostringstream& o, const char* type, const char* name, const double* v, int n) {
   char buf[64];
-  o << "__constant__ TP " << name << "[" << n << "] = {";
+  o << "__constant__ " << type << " " << name << "[" << n << "] = {";
   for (int i = 0; i < n; ++i) {
-    std::snprintf(buf, sizeof buf, "%s(TP)%.17g", i ? "," : "", v[i]);
+    std::snprintf(buf, sizeof buf, "%s(%s)%.17g", i ? "," : "", type, v[i]);
     o << buf;
   }
   o << "};\n";
@@ -120,9 +120,12 @@ std::string prelude(const CplTab& T, int prec, int bs) {
     << ", NCF = " << T.ncf << ";\n";
   o << "constexpr int SD_ARM = " << T.sd_arm << ", SD_QW = " << T.sd_qw << ", SD_F = " << T.sd_F
     << ", SD_K = " << T.sd_K << ", SD_CON = " << T.sd_con << ", SD_SIZE = " << T.sd_size << ";\n";
+  o << "constexpr int NSKY = " << T.nsky << ", PEN0 = " << T.pen0 << ";\n";
+  o << "constexpr bool TERRAIN = " << (T.ta != 0.0 ? "true" : "false") << ";\n";
   arr(o, "JPAR", T.jpar, T.nj);
   arr(o, "JCHI", T.jchi, T.nj);
   arr(o, "NPOS", T.npos, T.nk ? T.nj : 0);
+  arr(o, "NORD", T.nord, T.nk ? T.nj : 0);
   arr(o, "NF", T.nf, T.nk);
   arr(o, "NOFF", T.noff, T.nk ? T.nk + 1 : 0);
   arr(o, "CBODY", T.cbody, T.nc);
@@ -140,13 +143,21 @@ std::string prelude(const CplTab& T, int prec, int bs) {
   double a[36];
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) a[6 * i + j] = T.a[i][j];
-  tab(o, "TAB_A6", a, 36);
-  tab(o, "TAB_B", T.b, 6);
-  tab(o, "TAB_C", T.c, 6);
-  tab(o, "TAB_BETA", T.beta, 6);
+  tab(o, "TP", "TAB_A6", a, 36);
+  tab(o, "TP", "TAB_B", T.b, 6);
+  tab(o, "TP", "TAB_C", T.c, 6);
+  tab(o, "TP", "TAB_BETA", T.beta, 6);
+  tab(o, "double", "TABD_A6", a, 36);
+  tab(o, "double", "TABD_B", T.b, 6);
+  tab(o, "double", "TABD_C", T.c, 6);
+  tab(o, "double", "TABD_BETA", T.beta, 6);
   o << "#define TAB_A(j, m) TAB_A6[6 * (j) + (m)]\n";
+  o << "#define TABD_A(j, m) TABD_A6[6 * (j) + (m)]\n";
   return o.str();
 }
+
+// Compiles `src` (cached) and returns its kernel `name`, or null.
+const CplJit* compile(const std::string& src, const char* name, int bs, size_t smem);
 
 }  // namespace
 
@@ -154,7 +165,27 @@ const CplJit* cpl_jit_tangent(const CplTab& T, int prec) {
   const char* env = std::getenv("CISCVX_COUPLED_JIT");
   if (env && env[0] == '0') return nullptr;
   const int bs = prec == CISCVX_FP64 ? 64 : 128;
-  const std::string src = prelude(T, prec, bs) + kCplTangentJitSrc;
+  const size_t el = prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+  const size_t smem = T.scheme ? (size_t)5 * T.nlive * bs * el : 0;
+  return compile(prelude(T, prec, bs) + kCplTangentJitSrc, "cpl_tangent", bs, smem);
+}
+
+const CplJit* cpl_jit_nominal(const CplTab& T, int prec) {
+  const char* env = std::getenv("CISCVX_COUPLED_JIT");
+  if (env && env[0] == '0') return nullptr;
+  // per lane: K's skyline, the stored slopes (plus the RK4 accumulator), the
+  // quadrature rows and the lever arms, in doubles; one warp per block
+  const int nks = T.scheme ? 5 : 1;
+  const size_t elems = (size_t)T.nsky + nks * T.nlive + (nks == 1 ? T.nlive : 0) + T.nquad + 4 * T.nj;
+  const size_t smem = elems * sizeof(double) * 32;
+  if (smem > 200u * 1024u) return nullptr;
+  std::string src = prelude(T, prec, 32) + "#define CPL_NW 1\n" + kCplNominalJitSrc;
+  return compile(src, "cpl_nominal", 32, smem);
+}
+
+namespace {
+
+const CplJit* compile(const std::string& src, const char* name, int bs, size_t smem) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(src);
   if (it != g_cache.end()) return it->second.fn ? &it->second : nullptr;
@@ -189,9 +220,7 @@ const CplJit* cpl_jit_tangent(const CplTab& T, int prec) {
   CUmodule mod = nullptr;
   CUfunction fn = nullptr;
   if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS) return nullptr;
-  if (g_drv.get_fn(&fn, mod, "cpl_tangent") != CUDA_SUCCESS) return nullptr;
-  const size_t el = prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
-  const size_t smem = T.scheme ? (size_t)5 * T.nlive * bs * el : 0;
+  if (g_drv.get_fn(&fn, mod, name) != CUDA_SUCCESS) return nullptr;
   if (smem > 48u * 1024u &&
       g_drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
     return nullptr;
@@ -199,6 +228,31 @@ const CplJit* cpl_jit_tangent(const CplTab& T, int prec) {
   J.bs = bs;
   J.smem = smem;
   return &J;
+}
+
+}  // namespace
+
+cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, long n, int nsub,
+                                   int layout, const double* X, const double* U, const double* s,
+                                   void* sd, void* A, double* defect, double* penalty,
+                                   unsigned* status, cudaStream_t st) {
+  // NumN {mass, minv, iinv [NB]; jrp, jrc [max(NJ,1)][2]; crho [max(NC,1)][2]; mu [max(NC,1)]; g, ta, tk}
+  std::vector<double> num;
+  const int nj1 = T.nj > 0 ? T.nj : 1, nc1 = T.nc > 0 ? T.nc : 1;
+  for (int b = 0; b < T.nb; ++b) num.push_back(T.mass[b]);
+  for (int b = 0; b < T.nb; ++b) num.push_back(T.minv[b]);
+  for (int b = 0; b < T.nb; ++b) num.push_back(T.iinv[b]);
+  for (int j = 0; j < nj1; ++j) { num.push_back(j < T.nj ? T.jrp[j][0] : 0.0); num.push_back(j < T.nj ? T.jrp[j][1] : 0.0); }
+  for (int j = 0; j < nj1; ++j) { num.push_back(j < T.nj ? T.jrc[j][0] : 0.0); num.push_back(j < T.nj ? T.jrc[j][1] : 0.0); }
+  for (int i = 0; i < nc1; ++i) { num.push_back(i < T.nc ? T.crho[i][0] : 0.0); num.push_back(i < T.nc ? T.crho[i][1] : 0.0); }
+  for (int i = 0; i < nc1; ++i) num.push_back(i < T.nc ? T.mu[i] : 0.0);
+  num.push_back(T.g);
+  num.push_back(T.ta);
+  num.push_back(T.tk);
+  void* args[] = {num.data(), &i0, &n, &nsub, &layout, &X, &U, &s, &sd, &A, &defect, &penalty, &status};
+  const unsigned grid = (unsigned)((n + J.bs - 1) / J.bs);
+  const CUresult r = g_drv.launch((CUfunction)J.fn, grid, 1, 1, J.bs, 1, 1, (unsigned)J.smem, (CUstream)st, args, nullptr);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 
 cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,

@@ -261,8 +261,10 @@ def test_autograd_through_the_coupled_path(env):
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_phi", 1e-5)])
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_specialized_and_generic_tangent_kernels_agree(env, precision, tol, scheme, monkeypatch):
-    """The run-time specialized tangent kernel (default) and the generic one
-    (CISCVX_COUPLED_JIT=0) compute the same blocks; both meet the oracle."""
+    """The run-time specialized kernels (default) and the generic ones
+    (CISCVX_COUPLED_JIT=0) compute the same blocks; both meet the oracle.
+    The specialized nominal kernel chains sin/cos by angle addition and uses
+    other roundings, so the FP64 state agrees to 1e-12, not bitwise."""
     torch, oracle, api = env
     p = _problem("cheetah7", 34, 41, 3, joint_forces=1, scheme=scheme, terrain=synth.TERRAIN_SINE)
     got_jit, ref = _run(env, p, precision)
@@ -274,4 +276,4 @@ def test_specialized_and_generic_tangent_kernels_agree(env, precision, tol, sche
     for k in PHI:
         assert block_err(got_jit[k], got_gen[k]) <= tol, k
     for k in STATE:
-        assert np.array_equal(got_jit[k], got_gen[k]), k
+        assert block_err(got_jit[k], got_gen[k]) <= 1e-12, k
