@@ -84,31 +84,52 @@ __global__ void k_contract(int nxt, int nu, int nc, int pen0, long i0, long n, l
   }
 }
 
-// L += sum over the chunk of w . defect + rho . penalty (one block, fixed order).
+// L over a chunk, in two fixed-order passes (deterministic): block b sums a
+// fixed contiguous range of w . defect + rho . penalty into part[b], then one
+// block adds the partial sums in order to *L.
+constexpr int LRED_BLOCKS = 512;
+
 __global__ void __launch_bounds__(256) k_contract_L(int nxt, int nc, long i0, long n,
                                                     const double* __restrict__ defect,
                                                     const double* __restrict__ penalty,
                                                     const double* __restrict__ w,
-                                                    const double* __restrict__ rho, double* L) {
-  __shared__ double part[256];
+                                                    const double* __restrict__ rho,
+                                                    double* __restrict__ part) {
+  __shared__ double red[256];
+  const long nd = n * nxt, np = n * nc, tot = nd + np;
+  const long per = (tot + gridDim.x - 1) / gridDim.x;
+  const long lo = blockIdx.x * per, hi = lo + per < tot ? lo + per : tot;
   double acc = 0.0;
-  const long nd = n * nxt, np = n * nc;
-  for (long e = threadIdx.x; e < nd; e += 256) acc = fma(w[i0 * nxt + e], defect[e], acc);
-  for (long e = threadIdx.x; e < np; e += 256) acc = fma(rho[i0 * nc + e], penalty[e], acc);
-  part[threadIdx.x] = acc;
+  for (long e = lo + threadIdx.x; e < hi; e += 256)
+    acc = e < nd ? fma(w[i0 * nxt + e], defect[e], acc) : fma(rho[i0 * nc + (e - nd)], penalty[e - nd], acc);
+  red[threadIdx.x] = acc;
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *L += part[0];
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_contract_L_sum(const double* __restrict__ part, int nparts,
+                                                        double* L) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < nparts; e += 256) acc += part[e];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *L += red[0];
 }
 
 size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // Workspace layout of one chunk of n intervals.
 struct ChunkLayout {
-  size_t A, Bm, Bp, S, defect, penalty, stage, total;
+  size_t A, Bm, Bp, S, defect, penalty, part, stage, total;
 };
 
 ChunkLayout chunk_layout(const DevModel& M, const CplTab* T, long n, int nsub, int prec) {
@@ -122,6 +143,7 @@ ChunkLayout chunk_layout(const DevModel& M, const CplTab* T, long n, int nsub, i
   L.S = o; o = align16(o + n * nxt * el);
   L.defect = o; o = align16(o + n * nxt * sizeof(double));
   L.penalty = o; o = align16(o + n * nc * sizeof(double));
+  L.part = o; o = align16(o + LRED_BLOCKS * sizeof(double));
   L.stage = o; o = align16(o + (T ? n * cpl_interval_bytes(*T, nsub, prec) : 0));
   L.total = o;
   return L;
@@ -176,7 +198,13 @@ cudaError_t launch_contract_vjp(const DevModel& Mh, const DevModel* dM, const Cp
       k_contract<float><<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(
           nxt, nu, nc, pen0, i0, n, N, layout, (const float*)A, (const float*)Bm,
           (const float*)Bp, (const float*)S, w, rho, gX, gU, gs);
-    if (L) k_contract_L<<<1, 256, 0, st>>>(nxt, nc, i0, n, defect, penalty, w, rho, L);
+    if (L) {
+      double* part = (double*)(base + Ly.part);
+      const long tot = n * (nxt + nc);
+      const int nblk = (int)std::min<long>(LRED_BLOCKS, (tot + 2047) / 2048);
+      k_contract_L<<<nblk, 256, 0, st>>>(nxt, nc, i0, n, defect, penalty, w, rho, part);
+      k_contract_L_sum<<<1, 256, 0, st>>>(part, nblk, L);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
