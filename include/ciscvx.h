@@ -185,10 +185,12 @@ typedef struct ciscvx_model ciscvx_model;
  * and allocates the model's device status word.  A model with eliminated
  * joint forces, a sinusoidal surface or the RKF45 scheme has coupled links:
  * it is linearized by ciscvx_discretize (dense outputs, z not provided, a
- * workspace from ciscvx_discretize_workspace_size) and its VJP by
- * linearize-and-contract; its compact outputs and batch plans return
- * CISCVX_EUNSUPPORTED, and so do its node constraints on a sinusoidal
- * surface.  *out receives an opaque
+ * workspace from ciscvx_discretize_workspace_size) or in a batch plan
+ * (ciscvx_batch_discretize, dense outputs; the plan groups its instances by
+ * n_sub and owns their stage-data workspace), and its VJP by
+ * linearize-and-contract (single instance).  Its compact outputs, batched
+ * VJPs, the fused pass and the host executor return CISCVX_EUNSUPPORTED, and
+ * so do its node constraints on a sinusoidal surface.  *out receives an opaque
  * handle owned by the caller (free with ciscvx_model_destroy).  Errors:
  * EINVAL (null, counts < 0, n_bodies < 1, bad indices, non-positive mass or
  * inertia, parent == child, non-finite values), EUNSUPPORTED (limits above,

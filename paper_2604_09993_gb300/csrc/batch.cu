@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "batch_common.cuh"
+#include "coupled.cuh"
 
 namespace ciscvx {
 
@@ -193,6 +194,16 @@ struct ciscvx_batch_plan {
   bool compact = false;  // CISCVX_OUT_COMPACT
   bool all_nu0 = true, all_nc0 = true;
   bool any_aux = false;  // some model uses the Eq. (12) auxiliary state (no VJP, no compact outputs)
+  bool any_cpl = false;  // some model has coupled links (coupled path; no VJP, no compact outputs)
+  // coupled-path groups: instances of one coupled model with one n_sub, as
+  // (instance, k) entries; one stage-data workspace shared in stream order
+  struct CplGroup {
+    int model, nsub, first, count;
+  };
+  std::vector<CplGroup> cpl_groups;
+  int2* d_cpl_entries = nullptr;
+  void* d_cpl_ws = nullptr;
+  size_t cpl_ws_bytes = 0;
   std::vector<const ciscvx_model*> models;
   std::vector<DevInst> inst;
   ciscvx_batch_sizes sizes{};
@@ -256,6 +267,8 @@ void free_plan(ciscvx_batch_plan* p) {
   cudaFree(p->d_items_nat);
   cudaFree(p->d_queue);
   cudaFree(p->d_status);
+  cudaFree(p->d_cpl_entries);
+  cudaFree(p->d_cpl_ws);
   delete p;
 }
 
@@ -288,7 +301,8 @@ HostDecomp decompose(const ciscvx_batch_plan* p, const std::vector<int>& inst_of
   for (int c = 0; c < K; ++c) {
     std::map<std::pair<int, int>, std::vector<int>> buckets;
     for (int i = inst_off[c]; i < inst_off[c + 1]; ++i)
-      buckets[{p->inst[i].model, p->inst[i].nsub}].push_back(i);
+      if (!p->models[p->inst[i].model]->cpl)  // coupled models take the coupled path
+        buckets[{p->inst[i].model, p->inst[i].nsub}].push_back(i);
     std::vector<std::pair<long long, int2>> costed;
     for (auto& kv : buckets) {
       const int m = kv.first.first, ns = kv.first.second;
@@ -400,8 +414,25 @@ cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const cisc
   return cudaGetLastError();
 }
 
+// Coupled-path groups of the plan (after the per-link items).
+cudaError_t launch_cpl_groups(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStream_t st) {
+  for (const auto& g : p->cpl_groups) {
+    const CplTab& T = *p->models[g.model]->cpl;
+    const size_t per = cpl_interval_bytes(T, g.nsub, p->prec);
+    const long chunk = (long)std::min<size_t>((size_t)g.count, p->cpl_ws_bytes / per);
+    cudaError_t e = launch_coupled(T, g.count, g.nsub, p->prec, p->layout, io->X, io->U, io->s, io->A,
+                                   io->Bm, io->Bp, io->S, io->defect, io->penalty, p->d_cpl_ws, chunk,
+                                   p->d_status, st, p->d_cpl_entries + g.first, p->d_inst);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStream_t st) {
-  return launch_disc_c(p, common_of(p, 0, p->tune), io, st);
+  cudaError_t e = cudaSuccess;
+  if (p->n_items > 0) e = launch_disc_c(p, common_of(p, 0, p->tune), io, st);
+  if (e == cudaSuccess && !p->cpl_groups.empty()) e = launch_cpl_groups(p, io, st);
+  return e;
 }
 
 // VJP kernel over the items of `c`, then the per-instance finish over
@@ -467,6 +498,9 @@ ciscvx_status check_vjp(const ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* i
     return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (plan has %d)",
                      MAXSUB_VJP, p->max_nsub);
   if (p->any_aux) return set_error(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
+  if (p->any_cpl)
+    return set_error(CISCVX_EUNSUPPORTED, "batched VJPs are not provided for models with coupled links "
+                                          "(use ciscvx_discretize_vjp per instance)");
   const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
   if (!workspace || ws_bytes < need)
     return set_error(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
@@ -524,10 +558,10 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   for (int m = 0; m < n_models; ++m)
     if (!models[m]) return set_error(CISCVX_EINVAL, "null model %d", m);
   for (int m = 0; m < n_models; ++m)
-    if (models[m]->cpl)
+    if (models[m]->cpl && format == CISCVX_OUT_COMPACT)
       return set_error(CISCVX_EUNSUPPORTED,
                        "model %d has coupled links (eliminated joint forces, terrain or RKF45): "
-                       "batch plans are not provided for it (use ciscvx_discretize)", m);
+                       "compact outputs are not provided for it", m);
   for (int i = 0; i < n_inst; ++i) {
     if (model_idx[i] < 0 || model_idx[i] >= n_models)
       return set_error(CISCVX_EINVAL, "instance %d: model index %d out of range", i, model_idx[i]);
@@ -579,7 +613,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     p->max_nsub = std::max(p->max_nsub, n_sub[i]);
     if (nu) p->all_nu0 = false;
     if (nc) p->all_nc0 = false;
-    if (M.aux) p->any_aux = true;
+    if (M.aux && !models[model_idx[i]]->cpl) p->any_aux = true;
+    if (models[model_idx[i]]->cpl) p->any_cpl = true;
   }
   z.L = (size_t)n_inst;
   if (p->any_aux && p->compact) {
@@ -597,9 +632,36 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   const std::vector<int2>& entries = dec.entries;
   const std::vector<int4>& groups = dec.groups;
 
+  // coupled-path groups: (model, n_sub) -> (instance, k) entries; the stage-data
+  // workspace holds one chunk of the largest group
+  std::vector<int2> cpl_entries;
+  {
+    std::map<std::pair<int, int>, std::vector<int>> buckets;
+    for (int i = 0; i < n_inst; ++i)
+      if (models[p->inst[i].model]->cpl) buckets[{p->inst[i].model, p->inst[i].nsub}].push_back(i);
+    size_t ws = 0;
+    for (auto& kv : buckets) {
+      ciscvx_batch_plan::CplGroup g{kv.first.first, kv.first.second, (int)cpl_entries.size(), 0};
+      for (int i : kv.second)
+        for (int k = 0; k < p->inst[i].N; ++k) cpl_entries.push_back(make_int2(i, k));
+      g.count = (int)cpl_entries.size() - g.first;
+      const CplTab& T = *models[g.model]->cpl;
+      ws = std::max(ws, cpl_interval_bytes(T, g.nsub, precision) * (size_t)std::min(g.count, 32768));
+      p->cpl_groups.push_back(g);
+      cudaError_t pe = cpl_prepare(T, precision);  // compile the specialized kernels before any capture
+      if (pe != cudaSuccess) {
+        free_plan(p);
+        return set_error(CISCVX_ECUDA, "coupled kernels: %s", cudaGetErrorString(pe));
+      }
+    }
+    p->cpl_ws_bytes = ws;
+  }
+
   std::vector<const DevModel*> dm(n_models);
   for (int m = 0; m < n_models; ++m) dm[m] = models[m]->dev;
   cudaError_t e = upload(&p->d_models, dm);
+  if (e == cudaSuccess && !cpl_entries.empty()) e = upload(&p->d_cpl_entries, cpl_entries);
+  if (e == cudaSuccess && p->cpl_ws_bytes) e = cudaMalloc(&p->d_cpl_ws, p->cpl_ws_bytes);
   if (e == cudaSuccess) e = upload(&p->d_inst, p->inst);
   if (e == cudaSuccess) e = upload(&p->d_entries, entries);
   if (e == cudaSuccess) e = upload(&p->d_groups, groups);
@@ -871,6 +933,9 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
                                     size_t ws_bytes, void* stream) {
   ciscvx_status st = check_io(p, dev);
   if (st != CISCVX_OK) return st;
+  if (p->any_cpl)
+    return set_error(CISCVX_EUNSUPPORTED, "the host executor is not provided for plans with coupled-link "
+                                          "models (use ciscvx_batch_discretize)");
   if (!host || !host->X || !host->s || !host->A || !host->S || !host->defect)
     return set_error(CISCVX_EINVAL, "null required host buffer");
   if (!p->all_nu0 && (!host->U || !host->Bm || !host->Bp)) return set_error(CISCVX_EINVAL, "null host U / Bm / Bp");

@@ -7,12 +7,6 @@
 
 namespace ciscvx {
 
-struct DevInst {
-  int model, N, nsub, pad_;
-  long long x, u, s, a, b, v, p;  // element offsets: X/gX, U/gU, s/gs, A, Bm/Bp, S/defect/w, penalty/rho
-  long long part, pb;             // VJP workspace offsets: per-input partials, per-(interval, link) partials
-};
-
 struct BatchCommon {
   const DevModel* const* models;
   const DevInst* inst;

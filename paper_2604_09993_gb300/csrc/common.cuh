@@ -72,6 +72,16 @@ struct DevBody {
 // y, (om,q), then (y,q) for a foot link.  B- and B+ share the pattern.
 constexpr int A_PER_LINK = 10, A_PER_FOOT = 5;
 
+// One instance of a batch: model, horizon, substeps and its element offsets
+// into the packed arrays.
+struct DevInst {
+  int model, N, nsub, pad_;
+  long long x, u, s, a, b, v, p;  // element offsets: X/gX, U/gU, s/gs, A, Bm/Bp, S/defect/w, penalty/rho
+  long long part, pb;             // VJP workspace offsets: per-input partials, per-(interval, link) partials
+};
+// the run-time compiled kernels read the same table as InstRec (dev_math.cuh)
+static_assert(sizeof(DevInst) == sizeof(InstRec), "instance table layouts differ");
+
 struct DevModel {
   int nb, nj, nc, nxt, nu, nslot;   // nslot = sum of nin over links
   int nnzA, nnzB;                    // structural nonzeros of A and of B-/B+ (compact outputs)

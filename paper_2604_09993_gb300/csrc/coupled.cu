@@ -114,6 +114,45 @@ struct Cst<float> {
   __device__ static float iinv(const CplTab& M, int b) { return M.iinvf[b]; }
 };
 
+// Where interval e's data live: for a single instance (entries null) interval
+// e itself; in a batch, entry e = (instance, k) of the batch's instance table.
+struct IvAddr {
+  const double *x0, *x1, *uL, *uR;
+  long long s, a, b, v, p;  // element offsets: s, A, Bm/Bp, S/defect, penalty
+};
+
+__device__ __forceinline__ IvAddr iv_addr(long e, int nxt, int nu, int nc, int layout,
+                                          const double* X, const double* U, const int2* entries,
+                                          const DevInst* inst) {
+  long long k = e, xo, uo;
+  IvAddr r;
+  if (entries) {
+    const int2 en = entries[e];
+    const DevInst& I = inst[en.x];
+    k = en.y;
+    xo = I.x + k * nxt;
+    uo = I.u + (layout == 0 ? k : 2 * k) * nu;
+    r.s = I.s + k;
+    r.a = I.a + k * nxt * nxt;
+    r.b = I.b + k * nxt * nu;
+    r.v = I.v + k * nxt;
+    r.p = I.p + k * nc;
+  } else {
+    xo = k * nxt;
+    uo = (layout == 0 ? k : 2 * k) * nu;
+    r.s = k;
+    r.a = k * nxt * nxt;
+    r.b = k * nxt * nu;
+    r.v = k * nxt;
+    r.p = k * nc;
+  }
+  r.x0 = X + xo;
+  r.x1 = r.x0 + nxt;
+  r.uL = U ? U + uo : nullptr;
+  r.uR = U ? U + uo + nu : nullptr;
+  return r;
+}
+
 #define EL(o) sm[(o) * 32]
 #define LK(i, kk) EL(M.n_K + M.noff[i] + (kk) - M.nf[i])
 
@@ -125,22 +164,24 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
                                                     const double* __restrict__ s,
                                                     TP* __restrict__ sd, TP* __restrict__ A,
                                                     double* __restrict__ defect,
-                                                    double* __restrict__ penalty, unsigned* status) {
+                                                    double* __restrict__ penalty, unsigned* status,
+                                                    const int2* __restrict__ entries,
+                                                    const DevInst* __restrict__ inst) {
   using Sc = Scheme<SCH>;
   constexpr int NS = Sc::S;
   extern __shared__ double smem1[];
   const long t = (long)blockIdx.x * 32 + threadIdx.x;
   if (t >= n) return;
-  const long k = i0 + t;
   double* sm = smem1 + threadIdx.x;
   const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
   const int nl = M.nlive;
-  const double* uL = layout == 0 ? U + k * nu : U + 2 * k * nu;
-  const double* uR = layout == 0 ? U + (k + 1) * nu : U + (2 * k + 1) * nu;
-  const double sk = s[k];
+  const IvAddr ad = iv_addr(i0 + t, nxt, nu, nc, layout, X, U, entries, inst);
+  const double* uL = ad.uL;
+  const double* uR = ad.uR;
+  const double sk = s[ad.s];
   const double h = 1.0 / nsub;
   for (int r = 0; r < nxt; ++r) {
-    const double v = X[k * nxt + r];
+    const double v = ad.x0[r];
     if (M.lrow[r] >= 0) EL(M.n_xl + M.lrow[r]) = v;
     else EL(M.n_xq + M.qrow[r]) = v;
   }
@@ -415,18 +456,18 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
   double chk = 0.0;
   for (int r = 0; r < nxt; ++r) {
     const double x = M.lrow[r] >= 0 ? EL(M.n_xl + M.lrow[r]) : EL(M.n_xq + M.qrow[r]);
-    const double d = x - X[(k + 1) * nxt + r];
-    defect[k * nxt + r] = d;
+    const double d = x - ad.x1[r];
+    defect[ad.v + r] = d;
     chk += d;
   }
   for (int ic = 0; ic < nc; ++ic) {
     const int r = M.pen0 + ic;
     const double x = M.lrow[r] >= 0 ? EL(M.n_xl + M.lrow[r]) : EL(M.n_xq + M.qrow[r]);
-    penalty[k * nc + ic] = x - X[k * nxt + r];
+    penalty[ad.p + ic] = x - ad.x0[r];
   }
   if (!isfinite(chk)) atomicOr(status, ST_NONFINITE);
   // closed-form columns of A: e_p, e_v + s e_p (links without a contact), e_y
-  TP* Ak = A + (size_t)k * nxt * nxt;
+  TP* Ak = A + ad.a;
   auto unit_col = [&](int c, int r2, TP v2) {
     for (int r = 0; r < nxt; ++r) Ak[(size_t)r * nxt + c] = (r == c) ? TP(1) : (r == r2 ? v2 : TP(0));
   };
@@ -448,7 +489,8 @@ template <typename TP, int SCH>
 __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n, int nsub,
                               const double* __restrict__ s, const TP* __restrict__ sd,
                               TP* __restrict__ A, TP* __restrict__ Bm, TP* __restrict__ Bp,
-                              TP* __restrict__ S, unsigned* status) {
+                              TP* __restrict__ S, unsigned* status, int layout,
+                              const int2* __restrict__ entries, const DevInst* __restrict__ inst) {
   using Sc = Scheme<SCH>;
   using K = Cst<TP>;
   constexpr int NS = Sc::S;
@@ -460,8 +502,8 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
   const long t = g / C;
   if (t >= n) return;
   const int col = M.cperm[g - t * C];
-  const long k = i0 + t;
   const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
+  const IvAddr ad = iv_addr(i0 + t, nxt, nu, nc, layout, nullptr, nullptr, entries, inst);
   const int nl = M.nlive, nqd = M.nquad;
   int qin = -1;
   bool right = false, scol = false;
@@ -476,7 +518,7 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
     if (M.lrow[col] >= 0) ET(M.t_pl + M.lrow[col]) = TP(1);
     else ET(M.t_pq + M.qrow[col]) = TP(1);
   }
-  const TP sk = TP(s[k]);
+  const TP sk = TP(s[ad.s]);
   const TP h = TP(1) / TP(nsub);
   const TP hsk = h * sk;
   const TP* sdk = sd + (size_t)t * nsub * NS * M.sd_size;
@@ -672,9 +714,9 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
   // column `col` of [A | B- | B+ | S]
   TP* out;
   size_t stride;
-  if (col < nxt) { out = A + (size_t)k * nxt * nxt + col; stride = nxt; }
-  else if (!scol) { out = (right ? Bp : Bm) + (size_t)k * nxt * nu + qin; stride = nu; }
-  else { out = S + (size_t)k * nxt; stride = 1; }
+  if (col < nxt) { out = A + ad.a + col; stride = nxt; }
+  else if (!scol) { out = (right ? Bp : Bm) + ad.b + qin; stride = nu; }
+  else { out = S + ad.v; stride = 1; }
   float chk = 0.0f;
   for (int r = 0; r < nxt; ++r) {
     const TP v = M.lrow[r] >= 0 ? ET(M.t_pl + M.lrow[r]) : ET(M.t_pq + M.qrow[r]);
@@ -697,37 +739,51 @@ int tangent_block(const CplTab& T) {
 }
 
 template <typename TP, int SCH>
-cudaError_t run(const CplTab& T, int N, int nsub, int layout, const double* X, const double* U,
+cudaError_t prepare(const CplTab& T) {
+  static bool done = false;  // generic kernels' shared-memory limit (raised once, before any capture)
+  if (done) return cudaSuccess;
+  const int bs = tangent_block<TP>(T);
+  cudaError_t e = cudaFuncSetAttribute(k_cpl_nominal<TP, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       220 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cpl_tangent<TP, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  (void)bs;
+  done = e == cudaSuccess;
+  return e;
+}
+
+template <typename TP, int SCH>
+cudaError_t run(const CplTab& T, long N, int nsub, int layout, const double* X, const double* U,
                 const double* s, void* A, void* Bm, void* Bp, void* S, double* defect,
-                double* penalty, void* ws, long chunk, unsigned* status, cudaStream_t st) {
+                double* penalty, void* ws, long chunk, unsigned* status, cudaStream_t st,
+                const int2* entries, const DevInst* inst) {
   const size_t sm1 = (size_t)T.n_size * sizeof(double) * 32;
   const int prec = std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI;
   const CplJit* jit = cpl_jit_tangent(T, prec);
   const CplJit* jnom = cpl_jit_nominal(T, prec);
   const int bs = tangent_block<TP>(T);
   const size_t sm2 = (size_t)bs * T.t_size * sizeof(TP);
-  cudaError_t e = cudaFuncSetAttribute(k_cpl_nominal<TP, SCH>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cpl_tangent<TP, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm2);
+  cudaError_t e = prepare<TP, SCH>(T);
   if (e != cudaSuccess) return e;
   for (long i0 = 0; i0 < N; i0 += chunk) {
     const long n = std::min<long>(chunk, N - i0);
     if (jnom)
-      e = cpl_jit_launch_nominal(*jnom, T, i0, n, nsub, layout, X, U, s, ws, A, defect, penalty, status, st);
+      e = cpl_jit_launch_nominal(*jnom, T, i0, n, nsub, layout, X, U, s, ws, A, defect, penalty, status, st,
+                                 entries, inst);
     else
       k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
-          T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status);
+          T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status, entries, inst);
     if (e != cudaSuccess) return e;
     const long threads = n * T.cnt;
     if (jit) {
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        e = cpl_jit_launch(*jit, T, prec, i0, n, nsub, s, ws, A, Bm, Bp, S, status, st);
+        e = cpl_jit_launch(*jit, T, prec, i0, n, nsub, s, ws, A, Bm, Bp, S, status, st, layout, entries,
+                           inst);
     } else {
       k_cpl_tangent<TP, SCH><<<(unsigned)((threads + bs - 1) / bs), bs, sm2, st>>>(
-          T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status);
+          T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status, layout, entries,
+          inst);
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
@@ -888,15 +944,23 @@ size_t cpl_interval_bytes(const CplTab& T, int nsub, int prec) {
   return (size_t)nsub * T.stages * T.sd_size * el;
 }
 
-cudaError_t launch_coupled(const CplTab& T, int N, int nsub, int prec, int layout, const double* X,
+cudaError_t launch_coupled(const CplTab& T, long N, int nsub, int prec, int layout, const double* X,
                            const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
                            double* defect, double* penalty, void* ws, long chunk,
-                           unsigned* status, cudaStream_t st) {
+                           unsigned* status, cudaStream_t st, const int2* entries,
+                           const DevInst* inst) {
   if (prec == CISCVX_FP64)
-    return T.scheme ? run<double, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st)
-                    : run<double, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st);
-  return T.scheme ? run<float, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st)
-                  : run<float, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st);
+    return T.scheme ? run<double, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst)
+                    : run<double, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst);
+  return T.scheme ? run<float, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst)
+                  : run<float, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst);
+}
+
+cudaError_t cpl_prepare(const CplTab& T, int prec) {
+  cpl_jit_tangent(T, prec);
+  cpl_jit_nominal(T, prec);
+  if (prec == CISCVX_FP64) return T.scheme ? prepare<double, 1>(T) : prepare<double, 0>(T);
+  return T.scheme ? prepare<float, 1>(T) : prepare<float, 0>(T);
 }
 
 }  // namespace ciscvx

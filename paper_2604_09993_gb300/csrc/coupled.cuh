@@ -84,11 +84,17 @@ const char* cpl_build(const DevModel& M, CplTab& T);
 size_t cpl_interval_bytes(const CplTab& T, int nsub, int prec);
 
 // Linearized discretization of intervals [0, N) in chunks of at most
-// `chunk` intervals through the workspace (stage data of one chunk).
-cudaError_t launch_coupled(const CplTab& T, int N, int nsub, int prec, int layout, const double* X,
+// `chunk` intervals through the workspace (stage data of one chunk).  With
+// `entries`, interval e is entry e = (instance, k) of the batch instance
+// table `inst` (element offsets into the packed arrays); else interval e.
+cudaError_t launch_coupled(const CplTab& T, long N, int nsub, int prec, int layout, const double* X,
                            const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
                            double* defect, double* penalty, void* ws, long chunk,
-                           unsigned* status, cudaStream_t st);
+                           unsigned* status, cudaStream_t st, const int2* entries = nullptr,
+                           const DevInst* inst = nullptr);
+// Compiles the specialized kernels and sets the generic kernels' limits
+// (before a launch is captured in a graph).
+cudaError_t cpl_prepare(const CplTab& T, int prec);
 
 // Run-time specialized tangent kernel (jit.cu): null when unavailable (no
 // NVRTC, a failed compile, or CISCVX_COUPLED_JIT=0); then the generic kernel runs.
@@ -102,10 +108,12 @@ const CplJit* cpl_jit_nominal(const CplTab& T, int prec);
 cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, long n, int nsub,
                                    int layout, const double* X, const double* U, const double* s,
                                    void* sd, void* A, double* defect, double* penalty,
-                                   unsigned* status, cudaStream_t st);
+                                   unsigned* status, cudaStream_t st, const int2* entries,
+                                   const DevInst* inst);
 cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,
                            const double* s, const void* sd, void* A, void* Bm, void* Bp, void* S,
-                           unsigned* status, cudaStream_t st);
+                           unsigned* status, cudaStream_t st, int layout, const int2* entries,
+                           const DevInst* inst);
 
 // VJP by linearize-and-contract (contract.cu): workspace bytes for a chunk of
 // n intervals, and the chunked launch (T null for per-link models).

@@ -79,22 +79,29 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
                                                              TP* __restrict__ sd, TP* __restrict__ A,
                                                              double* __restrict__ defect,
                                                              double* __restrict__ penalty,
-                                                             unsigned* status) {
+                                                             unsigned* status,
+                                                             const int2* __restrict__ entries,
+                                                             const InstRec* __restrict__ inst) {
   extern __shared__ double jit_sm1[];
   double* sm = jit_sm1 + threadIdx.x;
 #define SE(o) sm[(o) * BLK]
   const long t = (long)blockIdx.x * BLK + threadIdx.x;
   if (t >= n) return;
   const unsigned active = __activemask();
-  const long k = i0 + t;
-  const double* uL = layout == 0 ? U + k * NU : U + 2 * k * NU;
-  const double* uR = layout == 0 ? U + (k + 1) * NU : U + (2 * k + 1) * NU;
-  const double sk = s[k];
+  const double *uL, *uR, *x0;
+  double sk;
+  {
+    const IvRef ad = iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst);
+    uL = U + ad.u;
+    uR = U + ad.u + NU;
+    x0 = X + ad.x;
+    sk = s[ad.s];
+  }
   const double h = 1.0 / nsub;
   double xl[NL], f[3 * NB], qw[NB], sn0[NB], cs0[NB];
 #pragma unroll
   for (int r = 0; r < NXT; ++r) {
-    const double v = X[k * NXT + r];
+    const double v = x0[r];
     if (LROW[r] >= 0) xl[LROW[r]] = v;
     else SE(E_XQ + QROW[r]) = v;
   }
@@ -411,22 +418,24 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
     }
   }
   double chk = 0.0;
+  const IvRef ad = iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst);
+  const double* x1 = x0 + NXT;
 #pragma unroll
   for (int r = 0; r < NXT; ++r) {
     const double x = LROW[r] >= 0 ? xl[LROW[r]] : SE(E_XQ + QROW[r]);
-    const double dv = x - X[(k + 1) * NXT + r];
-    defect[k * NXT + r] = dv;
+    const double dv = x - x1[r];
+    defect[ad.v + r] = dv;
     chk += dv;
   }
 #pragma unroll
   for (int ic = 0; ic < NC; ++ic) {
     const int r = PEN0 + ic;
     const double x = LROW[r] >= 0 ? xl[LROW[r]] : SE(E_XQ + QROW[r]);
-    penalty[k * NC + ic] = x - X[k * NXT + r];
+    penalty[ad.p + ic] = x - x0[r];
   }
   if (!isfinite(chk)) atomicOr(status, 1u);
   // closed-form columns of A: e_p, e_v + s e_p (links without a contact), e_y
-  TP* Ak = A + (size_t)k * NXT * NXT;
+  TP* Ak = A + ad.a;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (CONTACT[b] >= 0) continue;

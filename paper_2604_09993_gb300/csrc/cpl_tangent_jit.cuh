@@ -32,14 +32,16 @@ extern "C" __global__ void __launch_bounds__(BS) cpl_tangent(const __grid_consta
                                                             const TP* __restrict__ sd,
                                                             TP* __restrict__ A, TP* __restrict__ Bm,
                                                             TP* __restrict__ Bp, TP* __restrict__ S,
-                                                            unsigned* status) {
+                                                            unsigned* status, int layout,
+                                                            const int2* __restrict__ entries,
+                                                            const ciscvx::InstRec* __restrict__ inst) {
   extern __shared__ __align__(16) unsigned char jit_smem[];
   TP* ksh = reinterpret_cast<TP*>(jit_smem) + threadIdx.x;  // stored slopes (RKF45), element major
   const long g = (long)blockIdx.x * BS + threadIdx.x;
   const long t = g / CNT;
   if (t >= n) return;
   const int col = CPERM[g - t * CNT];
-  const long k = i0 + t;
+
   constexpr int NQ = 3 * NB;
   int qin = -1;
   bool right = false, scol = false;
@@ -53,7 +55,7 @@ extern "C" __global__ void __launch_bounds__(BS) cpl_tangent(const __grid_consta
   for (int l = 0; l < NL; ++l) PL[l] = (LINV[l] == col) ? TP(1) : TP(0);
 #pragma unroll
   for (int q = 0; q < NQD; ++q) PQ[q] = (QINV[q] == col) ? TP(1) : TP(0);
-  const TP sk = TP(s[k]);
+  const TP sk = TP(s[ciscvx::iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst).s]);
   const TP h = TP(1) / TP(nsub);
   const TP hsk = h * sk;
   const TP* sdk = sd + (size_t)t * nsub * NSTG * SD_SIZE;
@@ -270,9 +272,10 @@ extern "C" __global__ void __launch_bounds__(BS) cpl_tangent(const __grid_consta
   // column `col` of [A | B- | B+ | S]
   TP* out;
   size_t stride;
-  if (col < NXT) { out = A + (size_t)k * NXT * NXT + col; stride = NXT; }
-  else if (!scol) { out = (right ? Bp : Bm) + (size_t)k * NXT * NU + qin; stride = NU; }
-  else { out = S + (size_t)k * NXT; stride = 1; }
+  const ciscvx::IvRef ad = ciscvx::iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst);
+  if (col < NXT) { out = A + ad.a + col; stride = NXT; }
+  else if (!scol) { out = (right ? Bp : Bm) + ad.b + qin; stride = NU; }
+  else { out = S + ad.v; stride = 1; }
   float chk = 0.0f;
 #pragma unroll
   for (int r = 0; r < NXT; ++r) {

@@ -95,4 +95,38 @@ __device__ __forceinline__ void sincos_step(double th0, double s0, double c0, do
   if (!rotate_small(s0, c0, d, short_tier, s, c)) sincos(th0 + d, &s, &c);
 }
 
+// Where interval e's data live (the library's batch instance table has this
+// layout): for a single instance (entries null) interval e itself; in a batch,
+// entry e = (instance, k).
+struct InstRec {
+  int model, N, nsub, pad_;
+  long long x, u, s, a, b, v, p;  // element offsets: X, U, s, A, Bm/Bp, S/defect, penalty
+  long long part, pb;
+};
+
+struct IvRef {
+  long long x, u, s, a, b, v, p;
+};
+
+__device__ __forceinline__ IvRef iv_ref(long long e, int nxt, int nu, int nc, int layout,
+                                        const int2* entries, const InstRec* inst) {
+  IvRef r;
+  long long k = e;
+  long long x = 0, u = 0, sv = 0, a = 0, b = 0, v = 0, p = 0;
+  if (entries) {
+    const int2 en = entries[e];
+    const InstRec& I = inst[en.x];
+    k = en.y;
+    x = I.x; u = I.u; sv = I.s; a = I.a; b = I.b; v = I.v; p = I.p;
+  }
+  r.x = x + k * nxt;
+  r.u = u + (layout == 0 ? k : 2 * k) * nu;
+  r.s = sv + k;
+  r.a = a + k * nxt * nxt;
+  r.b = b + k * nxt * nu;
+  r.v = v + k * nxt;
+  r.p = p + k * nc;
+  return r;
+}
+
 }  // namespace ciscvx

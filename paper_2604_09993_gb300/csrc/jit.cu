@@ -185,7 +185,11 @@ const CplJit* cpl_jit_nominal(const CplTab& T, int prec) {
 
 namespace {
 
-const CplJit* compile(const std::string& src, const char* name, int bs, size_t smem) {
+const CplJit* compile(const std::string& src0, const char* name, int bs, size_t smem) {
+  // a loaded module belongs to the current device's context: key by device too
+  int cur = 0;
+  cudaGetDevice(&cur);
+  const std::string src = "// device " + std::to_string(cur) + "\n" + src0;
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(src);
   if (it != g_cache.end()) return it->second.fn ? &it->second : nullptr;
@@ -235,7 +239,8 @@ const CplJit* compile(const std::string& src, const char* name, int bs, size_t s
 cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, long n, int nsub,
                                    int layout, const double* X, const double* U, const double* s,
                                    void* sd, void* A, double* defect, double* penalty,
-                                   unsigned* status, cudaStream_t st) {
+                                   unsigned* status, cudaStream_t st, const int2* entries,
+                                   const DevInst* inst) {
   // NumN {mass, minv, iinv [NB]; jrp, jrc [max(NJ,1)][2]; crho [max(NC,1)][2]; mu [max(NC,1)]; g, ta, tk}
   std::vector<double> num;
   const int nj1 = T.nj > 0 ? T.nj : 1, nc1 = T.nc > 0 ? T.nc : 1;
@@ -249,7 +254,8 @@ cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, lo
   num.push_back(T.g);
   num.push_back(T.ta);
   num.push_back(T.tk);
-  void* args[] = {num.data(), &i0, &n, &nsub, &layout, &X, &U, &s, &sd, &A, &defect, &penalty, &status};
+  void* args[] = {num.data(), &i0, &n, &nsub, &layout, &X, &U, &s, &sd, &A, &defect, &penalty, &status,
+                  &entries, &inst};
   const unsigned grid = (unsigned)((n + J.bs - 1) / J.bs);
   const CUresult r = g_drv.launch((CUfunction)J.fn, grid, 1, 1, J.bs, 1, 1, (unsigned)J.smem, (CUstream)st, args, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
@@ -257,7 +263,8 @@ cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, lo
 
 cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,
                            const double* s, const void* sd, void* A, void* Bm, void* Bp, void* S,
-                           unsigned* status, cudaStream_t st) {
+                           unsigned* status, cudaStream_t st, int layout, const int2* entries,
+                           const DevInst* inst) {
   // Num {TP minv[NB]; TP iinv[NB];}
   unsigned char num[2 * MAXB * sizeof(double)];
   if (prec == CISCVX_FP64) {
@@ -267,7 +274,7 @@ cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, 
     float* f = (float*)num;
     for (int b = 0; b < T.nb; ++b) { f[b] = T.minvf[b]; f[T.nb + b] = T.iinvf[b]; }
   }
-  void* args[] = {num, &i0, &n, &nsub, &s, &sd, &A, &Bm, &Bp, &S, &status};
+  void* args[] = {num, &i0, &n, &nsub, &s, &sd, &A, &Bm, &Bp, &S, &status, &layout, &entries, &inst};
   const long threads = n * T.cnt;
   const unsigned grid = (unsigned)((threads + J.bs - 1) / J.bs);
   const CUresult r = g_drv.launch((CUfunction)J.fn, grid, 1, 1, J.bs, 1, 1, (unsigned)J.smem, (CUstream)st, args, nullptr);

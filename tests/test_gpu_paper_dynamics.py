@@ -144,11 +144,17 @@ def test_unsupported_entry_points(env):
     for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
                  lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
                  lambda: api.model_pattern(p.robot.as_dict()),
-                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub]),
+                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact"),
                  lambda: api.node_linearize(m, Xn, Xn, Phi, Gam, 1e-3, e)):
         with pytest.raises(api.CiscvxError) as err:
             call()
         assert err.value.status == api.EUNSUPPORTED
+    plan = api.BatchPlan([m], [0], [p.N], [p.n_sub], precision="fp64")
+    w = torch.zeros((p.N, m.nxt), dtype=torch.float64, device=dev)
+    rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
+    with pytest.raises(api.CiscvxError) as err:
+        plan.discretize_vjp(X, U, s, w, rho)
+    assert err.value.status == api.EUNSUPPORTED
     # a workspace below the minimum is an argument error
     tiny = torch.empty(16, dtype=torch.uint8, device=dev)
     with pytest.raises(api.CiscvxError) as err:
@@ -277,3 +283,50 @@ def test_specialized_and_generic_tangent_kernels_agree(env, precision, tol, sche
         assert block_err(got_jit[k], got_gen[k]) <= tol, k
     for k in STATE:
         assert block_err(got_jit[k], got_gen[k]) <= 1e-12, k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_batch_plan_with_coupled_models(env, precision):
+    """A batch plan mixing per-link models (default, Eq. (12)) with coupled ones
+    (paper dynamics with RKF45, eliminated joints with RK4) and several n_sub:
+    the per-link instances take the persistent kernel, the coupled ones are
+    grouped by (model, n_sub) and take the coupled path; every instance meets
+    the oracle."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(35)
+    robots = [synth.hopper(rng),
+              synth.with_paper_dynamics(synth.biped(rng), **PAPER),
+              synth.with_paper_dynamics(synth.cheetah7(rng), joint_forces=1, scheme=0),
+              synth.with_cross_states(synth.biped(rng))]
+    probs, midx = [], []
+    for _ in range(13):
+        mi = int(rng.integers(0, len(robots)))
+        probs.append(synth.draw_instance(robots[mi], rng, int(rng.integers(1, 60)), int(rng.choice([1, 3])),
+                                         q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15)))
+        midx.append(mi)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [q.N for q in probs], [q.n_sub for q in probs], precision=precision)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X = t(plan.pack([q.X for q in probs], "X"))
+    U = t(plan.pack([q.U for q in probs], "U"))
+    sv = t(plan.pack([q.s for q in probs], "s"))
+    out = plan.discretize(X, U, sv)
+    plan.sync_status()
+    host = {k: v.double().cpu().numpy() for k, v in out.items()}
+    for i, q in enumerate(probs):
+        R = q.robot
+        N, nxt, nu, nc = q.N, R.nxt, R.nu, R.nc
+        got = {"A": plan.unpack(host["A"], "A", i, (N, nxt, nxt)),
+               "Bm": plan.unpack(host["Bm"], "B", i, (N, nxt, nu)),
+               "Bp": plan.unpack(host["Bp"], "B", i, (N, nxt, nu)),
+               "S": plan.unpack(host["S"], "S", i, (N, nxt)),
+               "defect": plan.unpack(host["defect"], "defect", i, (N, nxt)),
+               "penalty": plan.unpack(host["penalty"], "penalty", i, (N, nc))}
+        ref = oracle.discretize(R.as_dict(), q.X, q.U, q.s, q.n_sub)
+        _check(got, ref, precision)
+    # graph replay gives the same numbers
+    out2 = plan.discretize(X, U, sv)
+    plan.sync_status()
+    for k in out:
+        assert torch.equal(out[k], out2[k]), k
