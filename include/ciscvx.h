@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 6
+#define CISCVX_VERSION_MINOR 7
 
 typedef enum {
   CISCVX_OK = 0,
@@ -189,8 +189,7 @@ typedef struct ciscvx_model ciscvx_model;
  * (ciscvx_batch_discretize, dense outputs; the plan groups its instances by
  * n_sub and owns their stage-data workspace), and its VJP by
  * linearize-and-contract (single instance).  Its compact outputs, batched
- * VJPs, the fused pass and the host executor return CISCVX_EUNSUPPORTED, and
- * so do its node constraints on a sinusoidal surface.  *out receives an opaque
+ * VJPs, the fused pass and the host executor return CISCVX_EUNSUPPORTED.  *out receives an opaque
  * handle owned by the caller (free with ciscvx_model_destroy).  Errors:
  * EINVAL (null, counts < 0, n_bodies < 1, bad indices, non-positive mass or
  * inertia, parent == child, non-finite values), EUNSUPPORTED (limits above,
@@ -543,7 +542,7 @@ ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* plan, void* stre
 
 /* Theta rows per contact, and the local variables its Jacobian is taken in. */
 #define CISCVX_NODE_THETA_ROWS 8
-#define CISCVX_NODE_THETA_COLS 10
+#define CISCVX_NODE_THETA_COLS 12
 /* Joints per model, and joints attached to one link, the node kernel supports. */
 #define CISCVX_NODE_MAX_JOINTS 12
 #define CISCVX_NODE_MAX_JOINTS_PER_LINK 8
@@ -563,14 +562,23 @@ typedef struct {
  *     Gth  [n][3 n_b][n_b]  : d(v rows)/d theta-_b (the other pose
  *                             coordinates do not enter the v rows)
  *     Gphi [n][3 n_b][2 n_c]: d(v rows)/d Phi
+ *     Gpx  [n][3 n_b][n_c]  : d(v rows)/d p_x- of the link carrying each
+ *                             contact (the contact frame moves with the
+ *                             contact point on a sinusoidal surface; 0 on
+ *                             flat ground)
+ *   On a sinusoidal surface the impulse acts as t Phi_t + n Phi_n with the
+ *   contact frame at the pre-impact contact point, and phi, c and lambda^c
+ *   below use that frame (phi = h^c / ||grad h^c||; velocities projected on
+ *   n and t).
  *   The remaining blocks are constant and not stored: d(q rows)/dq+ = I,
  *   d(q rows)/dq- = -I, d(v rows)/dv+ = M, d(y rows)/dy+ = I,
  *   d(y rows)/dy- = -I, all others 0 (G~ does not depend on Gamma).
  *   theta [n][n_c][8]: Theta^delta (device; required when n_c > 0).
- *   dtheta [n][n_c][8][10] (device, may be NULL): each contact's rows
+ *   dtheta [n][n_c][8][12] (device, may be NULL): each contact's rows
  *     differentiated in the local variables of the link carrying it, in the
- *     order (p_y-, theta-, v_x+, v_y+, omega+, v_y-, omega-, Phi_t, Phi_n,
- *     Gamma); Theta's derivatives in every other variable are 0.
+ *     order (p_x-, p_y-, theta-, v_x+, v_y+, omega+, v_x-, v_y-, omega-,
+ *     Phi_t, Phi_n, Gamma); Theta's derivatives in every other variable are 0
+ *     (on flat ground the p_x- and v_x- columns are 0 too).
  * Errors: EINVAL (nulls, n_nodes < 1, delta or restitution invalid),
  * EUNSUPPORTED (more than CISCVX_NODE_MAX_JOINTS joints or more than
  * CISCVX_NODE_MAX_JOINTS_PER_LINK on one link, or a link that is the child of
@@ -578,8 +586,8 @@ typedef struct {
 ciscvx_status ciscvx_node_linearize(const ciscvx_model* model, int n_nodes, const double* Xp,
                                     const double* Xm, const double* Phi, const double* Gam,
                                     const ciscvx_node_params* params, double* g, double* Gvm,
-                                    double* Gth, double* Gphi, double* theta, double* dtheta,
-                                    void* stream);
+                                    double* Gth, double* Gphi, double* Gpx, double* theta,
+                                    double* dtheta, void* stream);
 
 /* ------------------------------------------------ allocation-free VJP --- */
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libciscvx.so")
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(7)
 PRECISION = {"fp64": 0, "fp32_phi": 1, "tf32_tc": 2, "bf16_tc": 3}
 LAYOUT = {"node": 0, "interval": 1}
+NODE_THETA_COLS = 12  # CISCVX_NODE_THETA_COLS
 OP_DISCRETIZE, OP_VJP = 0, 1
 
 # Every symbol include/ciscvx.h declares.
@@ -127,7 +128,7 @@ def load(path: str | None = None):
     lib.ciscvx_model_nnz.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.ciscvx_node_linearize.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(_NodeParams), _vp, _vp, _vp, _vp, _vp,
-                                          _vp, _vp]
+                                          _vp, _vp, _vp]
     lib.ciscvx_discretize_compact.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _vp, _vp]
@@ -382,7 +383,7 @@ def node_linearize(model: Model, Xp, Xm, Phi, Gam, delta: float, restitution,
 
     Xp, Xm [n, nxt], Phi [n, 2 nc], Gam [n, nc]: device float64 tensors;
     restitution: nc host floats.  Returns dict g, theta and, with jacobians,
-    Gvm, Gth, Gphi, dtheta (layouts in include/ciscvx.h)."""
+    Gvm, Gth, Gphi, Gpx, dtheta (layouts in include/ciscvx.h)."""
     import torch
     f64 = torch.float64
     _need(Xp, "Xp", f64); _need(Xm, "Xm", f64)
@@ -398,14 +399,15 @@ def node_linearize(model: Model, Xp, Xm, Phi, Gam, delta: float, restitution,
             out.update(Gvm=torch.empty((n, nq, nq), dtype=f64, device=dev),
                        Gth=torch.empty((n, nq, nb), dtype=f64, device=dev),
                        Gphi=torch.empty((n, nq, 2 * nc), dtype=f64, device=dev),
-                       dtheta=torch.empty((n, nc, 8, 10), dtype=f64, device=dev))
+                       Gpx=torch.empty((n, nq, nc), dtype=f64, device=dev),
+                       dtheta=torch.empty((n, nc, 8, NODE_THETA_COLS), dtype=f64, device=dev))
     e = (ctypes.c_double * max(nc, 1))(*[float(v) for v in np.asarray(restitution, dtype=np.float64).reshape(-1)])
     prm = _NodeParams(float(delta), e)
-    has = lambda k: _ptr(out[k]) if out.get(k) is not None and (nc or k not in ("theta", "Gphi", "dtheta")) else None  # noqa: E731
+    has = lambda k: _ptr(out[k]) if out.get(k) is not None and (nc or k not in ("theta", "Gphi", "Gpx", "dtheta")) else None  # noqa: E731
     _check(load().ciscvx_node_linearize(
         model.handle, int(n), _ptr(Xp), _ptr(Xm), _ptr(Phi) if nc else None, _ptr(Gam) if nc else None,
-        ctypes.byref(prm), _ptr(out["g"]), has("Gvm"), has("Gth"), has("Gphi"), has("theta"),
-        has("dtheta"), _stream()))
+        ctypes.byref(prm), _ptr(out["g"]), has("Gvm"), has("Gth"), has("Gphi"), has("Gpx"),
+        has("theta"), has("dtheta"), _stream()))
     return out
 
 

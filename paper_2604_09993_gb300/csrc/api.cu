@@ -542,13 +542,11 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
 ciscvx_status ciscvx_node_linearize(const ciscvx_model* m, int n, const double* Xp,
                                     const double* Xm, const double* Phi, const double* Gam,
                                     const ciscvx_node_params* params, double* g, double* Gvm,
-                                    double* Gth, double* Gphi, double* theta, double* dtheta,
-                                    void* stream) {
+                                    double* Gth, double* Gphi, double* Gpx, double* theta,
+                                    double* dtheta, void* stream) {
   if (!m || !params) return fail(CISCVX_EINVAL, "null model or params");
   if (n < 1) return fail(CISCVX_EINVAL, "n_nodes must be >= 1 (got %d)", n);
   const DevModel& M = m->host;
-  if (M.ta != 0.0)
-    return fail(CISCVX_EUNSUPPORTED, "node constraints are not provided on a sinusoidal contact surface");
   if (!M.tree)
     return fail(CISCVX_EUNSUPPORTED, "node constraints need every link to be the child of at most one joint");
   if (M.nj > NODE_MAXJ)
@@ -571,8 +569,8 @@ ciscvx_status ciscvx_node_linearize(const ciscvx_model* m, int n, const double* 
   }
   if (node_smem_per_warp(M) > 220u * 1024u)
     return fail(CISCVX_EUNSUPPORTED, "model too large for the node kernel's shared memory");
-  cudaError_t e = launch_node(M, m->dev, n, Xp, Xm, Phi, Gam, P, g, Gvm, Gth, Gphi, theta, dtheta,
-                              m->status, (cudaStream_t)stream);
+  cudaError_t e = launch_node(M, m->dev, n, Xp, Xm, Phi, Gam, P, g, Gvm, Gth, Gphi, Gpx, theta,
+                              dtheta, m->status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "node launch");
   return ok();
 }

@@ -204,7 +204,8 @@ size_t node_smem_per_warp(const DevModel& M);
 cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const double* Xp,
                         const double* Xm, const double* Phi, const double* Gam,
                         const NodeParams& P, double* g, double* Gvm, double* Gth, double* Gphi,
-                        double* theta, double* dtheta, unsigned* status, cudaStream_t st);
+                        double* Gpx, double* theta, double* dtheta, unsigned* status,
+                        cudaStream_t st);
 // Records a formatted last-error message (thread-local) and returns st.
 ciscvx_status set_error(ciscvx_status st, const char* fmt, ...);
 }  // namespace ciscvx

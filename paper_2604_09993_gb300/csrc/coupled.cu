@@ -45,40 +45,6 @@ struct Scheme {
   __device__ static constexpr bool bnz(int m) { return SCH ? m != 1 : true; }
 };
 
-// Contact surface y = ta sin(tk x) at the world point (xc, yc): approximate
-// signed distance phi = h^c / ||grad h^c||, h^c = y - ta sin(tk x) (Sec. VI-B),
-// unit normal n = grad h^c / ||grad h^c||, tangent t = (n_y, -n_x), and
-// their derivatives along x (nothing depends on y but phi).
-struct Surf {
-  double phi, tx, ty, nx, ny, phix, phiy, dtx, dty, dnx, dny;
-};
-
-__device__ __forceinline__ Surf surface(double ta, double tk, double xc, double yc) {
-  Surf f;
-  if (ta == 0.0) {
-    f.phi = yc;
-    f.tx = 1.0; f.ty = 0.0; f.nx = 0.0; f.ny = 1.0;
-    f.phix = 0.0; f.phiy = 1.0;
-    f.dtx = f.dty = f.dnx = f.dny = 0.0;
-    return f;
-  }
-  double sk, ck;
-  sincos(tk * xc, &sk, &ck);
-  const double hc = fma(-ta, sk, yc);
-  const double gx = -(ta * tk) * ck;       // dh^c/dx
-  const double gp = (ta * tk * tk) * sk;   // d gx / dx
-  const double w = 1.0 / sqrt(fma(gx, gx, 1.0));
-  const double w3g = gp * w * w * w;
-  f.phi = hc * w;
-  f.nx = gx * w; f.ny = w;
-  f.tx = w; f.ty = -f.nx;
-  f.phix = f.nx * fma(-hc * w * w, gp, 1.0);  // gx w (1 - h^c w^2 gp)
-  f.phiy = w;
-  f.dnx = w3g; f.dny = -gx * w3g;             // dn/dx = gp w^3 (1, -gx)
-  f.dtx = -gx * w3g; f.dty = -w3g;            // dt/dx = gp w^3 (-gx, -1)
-  return f;
-}
-
 // pseudo-Huber absolute value sqrt(1 + x^2) - 1 and its slope
 __device__ __forceinline__ double sabs_d(double x, double& d) {
   const double r = sqrt(fma(x, x, 1.0));
@@ -290,7 +256,7 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
       for (int ic = 0; ic < nc; ++ic) {
         const int b = M.cbody[ic];
         const double rx = EL(M.n_carm + 2 * ic), ry = EL(M.n_carm + 2 * ic + 1);
-        const Surf f = surface(M.ta, M.tk, XS(3 * b) + rx, XS(3 * b + 1) + ry);
+        const SurfFrame f = contact_surface(M.ta, M.tk, XS(3 * b) + rx, XS(3 * b + 1) + ry);
         const double u0 = u_at(M.ci0 + 3 * ic), u1 = u_at(M.ci0 + 3 * ic + 1),
                      u2 = u_at(M.ci0 + 3 * ic + 2);
         // contact-frame components (tangential, normal)

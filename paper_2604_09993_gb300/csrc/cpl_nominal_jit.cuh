@@ -34,36 +34,6 @@ struct NumN {
 
 using namespace ciscvx;
 
-// contact surface y = ta sin(tk x): phi = h^c / ||grad h^c||, n, t, and x-derivatives
-struct SurfJ {
-  double phi, tx, ty, nx, ny, phix, phiy, dtx, dty, dnx, dny;
-};
-__device__ __forceinline__ SurfJ surface_j(double ta, double tk, double xc, double yc) {
-  SurfJ f;
-  if (!TERRAIN) {
-    f.phi = yc;
-    f.tx = 1.0; f.ty = 0.0; f.nx = 0.0; f.ny = 1.0;
-    f.phix = 0.0; f.phiy = 1.0;
-    f.dtx = f.dty = f.dnx = f.dny = 0.0;
-    return f;
-  }
-  double sk, ck;
-  sincos(tk * xc, &sk, &ck);
-  const double hc = fma(-ta, sk, yc);
-  const double gx = -(ta * tk) * ck;
-  const double gp = (ta * tk * tk) * sk;
-  const double w = 1.0 / sqrt(fma(gx, gx, 1.0));
-  const double w3g = gp * w * w * w;
-  f.phi = hc * w;
-  f.nx = gx * w; f.ny = w;
-  f.tx = w; f.ty = -f.nx;
-  f.phix = f.nx * fma(-hc * w * w, gp, 1.0);
-  f.phiy = w;
-  f.dnx = w3g; f.dny = -gx * w3g;
-  f.dtx = -gx * w3g; f.dty = -w3g;
-  return f;
-}
-
 __device__ __forceinline__ TP ramp_slope(double z) { return huber_slope(TP(z)); }
 // pseudo-Huber absolute value sqrt(1 + x^2) - 1 (FP64) as a rsqrt(a) - 1
 __device__ __forceinline__ double sabs_v(double x) {
@@ -228,7 +198,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
         const int b = CBODY[ic];
         const double rx = fma(cs[b], P.crho[ic][0], -sn[b] * P.crho[ic][1]);
         const double ry = fma(sn[b], P.crho[ic][0], cs[b] * P.crho[ic][1]);
-        const SurfJ fr = surface_j(P.ta, P.tk, xs[LROW[3 * b]] + rx, xs[LROW[3 * b + 1]] + ry);
+        const SurfFrame fr = contact_surface(TERRAIN ? P.ta : 0.0, P.tk, xs[LROW[3 * b]] + rx, xs[LROW[3 * b + 1]] + ry);
         const double u0 = u_at(CI0 + 3 * ic), u1 = u_at(CI0 + 3 * ic + 1), u2 = u_at(CI0 + 3 * ic + 2);
         const double ft = AUX ? u0 : u1 - u2, fn = AUX ? u1 : u0;
         const double fx = fma(fr.tx, ft, fr.nx * fn), fy = fma(fr.ty, ft, fr.ny * fn);

@@ -95,6 +95,41 @@ __device__ __forceinline__ void sincos_step(double th0, double s0, double c0, do
   if (!rotate_small(s0, c0, d, short_tier, s, c)) sincos(th0 + d, &s, &c);
 }
 
+// Contact surface y = ta sin(tk x) at the world point (xc, yc) (Sec. VI-B;
+// ta = 0: flat ground y = 0): approximate signed distance phi = h^c /
+// ||grad h^c||, h^c = y - ta sin(tk x); unit normal n = grad h^c / ||grad h^c||
+// (grad phi on the surface); tangent t = (n_y, -n_x); their derivatives along
+// x (nothing depends on y but phi).
+struct SurfFrame {
+  double phi, tx, ty, nx, ny, phix, phiy, dtx, dty, dnx, dny;
+};
+
+__device__ __forceinline__ SurfFrame contact_surface(double ta, double tk, double xc, double yc) {
+  SurfFrame f;
+  if (ta == 0.0) {
+    f.phi = yc;
+    f.tx = 1.0; f.ty = 0.0; f.nx = 0.0; f.ny = 1.0;
+    f.phix = 0.0; f.phiy = 1.0;
+    f.dtx = f.dty = f.dnx = f.dny = 0.0;
+    return f;
+  }
+  double sk, ck;
+  sincos(tk * xc, &sk, &ck);
+  const double hc = fma(-ta, sk, yc);
+  const double gx = -(ta * tk) * ck;       // dh^c/dx
+  const double gp = (ta * tk * tk) * sk;   // d gx / dx
+  const double w = 1.0 / sqrt(fma(gx, gx, 1.0));
+  const double w3g = gp * w * w * w;
+  f.phi = hc * w;
+  f.nx = gx * w; f.ny = w;
+  f.tx = w; f.ty = -f.nx;
+  f.phix = f.nx * fma(-hc * w * w, gp, 1.0);  // gx w (1 - h^c w^2 gp)
+  f.phiy = w;
+  f.dnx = w3g; f.dny = -gx * w3g;             // dn/dx = gp w^3 (1, -gx)
+  f.dtx = -gx * w3g; f.dty = -w3g;            // dt/dx = gp w^3 (-gx, -1)
+  return f;
+}
+
 // Where interval e's data live (the library's batch instance table has this
 // layout): for a single instance (entries null) interval e itself; in a batch,
 // entry e = (instance, k).

@@ -15,6 +15,18 @@
 //     t_j = s_jb (-r_jb omega^_b + perp(r_jb) a_b / I_b) for the joints j on link b,
 //   where r are world lever arms, perp(r) = (-r_y, r_x) = d(R rho)/dtheta and
 //   s_jb = +1 (child) / -1 (parent).
+// On the sinusoidal surface (Sec. VI-B) the contact frame [t n] is taken at
+// the pre-impact contact point x_c = p_x- + r_x, so the world impulse
+// I = t Phi_t + n Phi_n moves with p_x- and theta- of the contact's link:
+// dI/dx_c = (dt/dx) Phi_t + (dn/dx) Phi_n =: D.  With h = F' - C''^T mu for a
+// coordinate the generalized impulse F = J_c^T R_c Phi depends on, the v rows'
+// column is -h + C'^T K^-1 (C'' v^ + C' M^-1 h):
+//   d/dtheta_b: h = a_b e_theta + g, g = (dI, r x dI), dI = -r_y D;
+//   d/dp_x-   : h = (D, r x D) (C' does not depend on positions);
+//   d/dPhi    : h = (t or n, r x (t or n)).
+// Theta's pairs read the contact point's distance phi and its velocity in the
+// contact frame: c = n . (v_c+ + e v_c-), lambda^c = t . v_c+ + Gamma
+// dPhi_t/..., with v_c = (v_x - omega r_y, v_y + omega r_x).
 //
 // Mapping: lane = node.  The joint impulse couples every link of a node, so
 // one thread owns one node; a warp's 32 lanes run the same program on 32
@@ -47,19 +59,25 @@ struct NodeTab {
   double mass[MAXB], inertia[MAXB], minv[MAXB], iinv[MAXB];
   double crho[MAXB][2], mu[MAXB];
   double delta, e[MAXB];
+  double ta, tk;  // contact surface y = ta sin(tk x)
 };
 
 // Per-lane scratch layout (in doubles; each element is a row of 32 lanes).
 struct NodeLayout {
-  int arm, carm, K, wh, mu, x, total;
+  int arm, carm, fr, K, wh, mu, x, total;
 };
 
-__host__ __device__ inline NodeLayout node_layout(int nb, int nj, int nc, int nsky) {
+// per-contact contact-frame slots (at the pre-impact contact point)
+constexpr int FR_TX = 0, FR_TY = 1, FR_NX = 2, FR_NY = 3, FR_DTX = 4, FR_DTY = 5, FR_DNX = 6,
+              FR_DNY = 7, FR_PHI = 8, FR_PHIX = 9, FR_PHIY = 10, FR_N = 11;
+
+__host__ __device__ inline NodeLayout node_layout(int nb, int nj, int nc, int nsky, bool terrain) {
   const int nk = 2 * nj;
   NodeLayout L;
   L.arm = 0;                       // perp lever arms per joint: child x, y; parent x, y (4 nj)
   L.carm = L.arm + 4 * nj;         // world lever arm r of each contact point          (2 nc)
-  L.K = L.carm + 2 * nc;           // K = L D L^T in skyline rows: unit L left of the diagonal, 1/D on it (nsky)
+  L.fr = L.carm + 2 * nc;          // contact frame, its x-derivatives, phi (FR_N nc; sinusoidal surface only)
+  L.K = L.fr + (terrain ? FR_N * nc : 0);  // K = L D L^T in skyline rows: unit L left of the diagonal, 1/D on it (nsky)
   L.wh = L.K + nsky;               // omega^ of every link (post-impact velocity the map implies) (nb)
   L.mu = L.wh + nb;                // mu = K^-1 C' w                                    (nk)
   L.x = L.mu + nk;                 // right-hand side / solution of one solve          (nk)
@@ -144,14 +162,15 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
                                               const double* __restrict__ Xm,
                                               const double* __restrict__ Phi,
                                               const double* __restrict__ Gam, double* g,
-                                              double* Gvm, double* Gth, double* Gphi,
+                                              double* Gvm, double* Gth, double* Gphi, double* Gpx,
                                               double* theta, double* dtheta, unsigned* status) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nq = 3 * nb, nk = 2 * nj;
-  const NodeLayout Ly = node_layout(nb, nj, nc, M.noff[2 * nj]);
+  const bool terrain = M.ta != 0.0;
+  const NodeLayout Ly = node_layout(nb, nj, nc, M.noff[2 * nj], terrain);
   double* sm = smem + (size_t)warp * Ly.total * 32 + lane;
   const double* xp = Xp + k * nxt;
   const double* xm = Xm + k * nxt;
@@ -172,10 +191,23 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
     }
     const int ci = M.contact[b];
     if (ci >= 0) {
-      SM(Ly.carm + 2 * ci) = c * M.crho[b][0] - s * M.crho[b][1];
-      SM(Ly.carm + 2 * ci + 1) = s * M.crho[b][0] + c * M.crho[b][1];
+      const double rx = c * M.crho[b][0] - s * M.crho[b][1], ry = s * M.crho[b][0] + c * M.crho[b][1];
+      SM(Ly.carm + 2 * ci) = rx;
+      SM(Ly.carm + 2 * ci + 1) = ry;
+      if (terrain) {
+        const SurfFrame f = contact_surface(M.ta, M.tk, xm[3 * b] + rx, xm[3 * b + 1] + ry);
+        double* F = &SM(Ly.fr + FR_N * ci);
+        F[FR_TX * 32] = f.tx; F[FR_TY * 32] = f.ty; F[FR_NX * 32] = f.nx; F[FR_NY * 32] = f.ny;
+        F[FR_DTX * 32] = f.dtx; F[FR_DTY * 32] = f.dty; F[FR_DNX * 32] = f.dnx; F[FR_DNY * 32] = f.dny;
+        F[FR_PHI * 32] = f.phi; F[FR_PHIX * 32] = f.phix; F[FR_PHIY * 32] = f.phiy;
+      }
     }
   }
+  // contact-frame value `slot` of contact ci: stored on the sinusoid; on flat
+  // ground t = (1, 0), n = (0, 1) and nothing depends on x (phi is formed at its use)
+#define FRV(ci, slot) \
+  (terrain ? SM(Ly.fr + FR_N * (ci) + (slot)) \
+           : ((slot) == FR_TX || (slot) == FR_NY || (slot) == FR_PHIY ? 1.0 : 0.0))
 
   // K = C' M^-1 C'^T (skyline rows, joints in the children-first order), then K = L D L^T
   for (int r1 = 0; r1 < nk; ++r1) {
@@ -215,14 +247,16 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
     for (int kk = M.nf[i]; kk < i; ++kk) LK(i, kk) *= LK(kk, kk);
   for (int i = 0; i < nk; ++i) LK(i, i) = LK(i, i) * LK(i, i);
 
-  // w = v- + M^-1 J_c^T Phi on link b (generalized impulse of its contact)
+  // w = v- + M^-1 J_c^T R_c Phi on link b (generalized impulse of its contact:
+  // world impulse t Phi_t + n Phi_n at the contact point)
   auto impulse = [&](int b, double& f0, double& f1, double& f2) {
     f0 = f1 = f2 = 0.0;
     const int ci = M.contact[b];
     if (ci >= 0) {
       const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
-      f0 = ph[2 * ci];
-      f1 = ph[2 * ci + 1];
+      const double pt = ph[2 * ci], pn = ph[2 * ci + 1];
+      f0 = fma(FRV(ci, FR_TX), pt, FRV(ci, FR_NX) * pn);
+      f1 = fma(FRV(ci, FR_TY), pt, FRV(ci, FR_NY) * pn);
       f2 = rx * f1 - ry * f0;
     }
   };
@@ -295,10 +329,19 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
   if (Gth) {
     double* out = Gth + (size_t)k * nq * nb;
     for (int b = 0; b < nb; ++b) {
-      double ab = 0.0;
+      double ab = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
       const int ci = M.contact[b];
-      if (ci >= 0)
-        ab = -fma(SM(Ly.carm + 2 * ci), ph[2 * ci], SM(Ly.carm + 2 * ci + 1) * ph[2 * ci + 1]);
+      if (ci >= 0) {
+        double i0, i1, i2;
+        impulse(b, i0, i1, i2);
+        const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
+        ab = -fma(rx, i0, ry * i1);
+        // the frame turns with x_c: dI = -r_y (dt/dx Phi_t + dn/dx Phi_n)
+        const double pt = ph[2 * ci], pn = ph[2 * ci + 1];
+        g0 = -ry * fma(FRV(ci, FR_DTX), pt, FRV(ci, FR_DNX) * pn);
+        g1 = -ry * fma(FRV(ci, FR_DTY), pt, FRV(ci, FR_DNY) * pn);
+        g2 = rx * g1 - ry * g0;
+      }
       for (int t = 0; t < M.nadj[b]; ++t) {
         const int code = M.adj[b][t], j = code >> 1, role = code & 1;
         const double px = SM(Ly.arm + 4 * j + 2 * role), py = SM(Ly.arm + 4 * j + 2 * role + 1);
@@ -306,12 +349,13 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
         const double rm = fma(py, SM(Ly.mu + 2 * M.npos[j]), -px * SM(Ly.mu + 2 * M.npos[j] + 1));
         ab = role ? ab - rm : ab + rm;
       }
-      const double wb = SM(Ly.wh + b), ai = ab * M.iinv[b];
+      const double wb = SM(Ly.wh + b), ai = (ab + g2) * M.iinv[b];
+      const double l0 = g0 * M.minv[b], l1 = g1 * M.minv[b];
       for (int r = 0; r < nk; ++r) SM(Ly.x + r) = 0.0;
       for (int t = 0; t < M.nadj[b]; ++t) {
         const int code = M.adj[b][t], j = code >> 1, role = code & 1, r = 2 * M.npos[j];
         const double px = SM(Ly.arm + 4 * j + 2 * role), py = SM(Ly.arm + 4 * j + 2 * role + 1);
-        const double t0 = fma(px, ai, -py * wb), t1 = fma(py, ai, px * wb);
+        const double t0 = fma(px, ai, fma(-py, wb, l0)), t1 = fma(py, ai, fma(px, wb, l1));
         SM(Ly.x + r) = role ? -t0 : t0;
         SM(Ly.x + r + 1) = role ? -t1 : t1;
       }
@@ -319,7 +363,7 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
       for (int bb = 0; bb < nb; ++bb) {
         double t0, t1, t2;
         ct_link(M, sm, Ly, Ly.x, bb, t0, t1, t2);
-        if (bb == b) t2 -= ab;
+        if (bb == b) { t0 -= g0; t1 -= g1; t2 -= ab + g2; }
         out[(size_t)(3 * bb) * nb + b] = t0;
         out[(size_t)(3 * bb + 1) * nb + b] = t1;
         out[(size_t)(3 * bb + 2) * nb + b] = t2;
@@ -336,8 +380,10 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
       if (ci < 0) continue;
       const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
       for (int comp = 0; comp < 2; ++comp) {
-        const double f0 = (comp == 0) ? 1.0 : 0.0, f1 = (comp == 1) ? 1.0 : 0.0;
-        const double f2 = (comp == 0) ? -ry : rx;
+        // world direction of the impulse component: t (Phi_t) or n (Phi_n)
+        const double f0 = comp == 0 ? FRV(ci, FR_TX) : FRV(ci, FR_NX);
+        const double f1 = comp == 0 ? FRV(ci, FR_TY) : FRV(ci, FR_NY);
+        const double f2 = rx * f1 - ry * f0;
         c_link(M, sm, Ly, nk, b, f0 * M.minv[b], f1 * M.minv[b], f2 * M.iinv[b]);
         ldl_solve(M, sm, Ly, nk, M.lmin[b]);
         const int col = 2 * ci + comp;
@@ -354,20 +400,53 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
     }
   }
 
+  // d/dp_x- of each contact's link: column = -f + C'^T K^-1 C' M^-1 f, f = (D, r x D),
+  // D = (dt/dx) Phi_t + (dn/dx) Phi_n (zero on flat ground)
+  if (Gpx && nc > 0 && !terrain) {  // on flat ground the frame does not move: the block is 0
+    double* out = Gpx + (size_t)k * nq * nc;
+    for (int q = 0; q < nq * nc; ++q) out[q] = 0.0;
+  } else if (Gpx && nc > 0) {
+    double* out = Gpx + (size_t)k * nq * nc;
+    for (int b = 0; b < nb; ++b) {
+      const int ci = M.contact[b];
+      if (ci < 0) continue;
+      const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
+      const double pt = ph[2 * ci], pn = ph[2 * ci + 1];
+      const double f0 = fma(FRV(ci, FR_DTX), pt, FRV(ci, FR_DNX) * pn);
+      const double f1 = fma(FRV(ci, FR_DTY), pt, FRV(ci, FR_DNY) * pn);
+      const double f2 = rx * f1 - ry * f0;
+      c_link(M, sm, Ly, nk, b, f0 * M.minv[b], f1 * M.minv[b], f2 * M.iinv[b]);
+      ldl_solve(M, sm, Ly, nk, M.lmin[b]);
+      for (int bb = 0; bb < nb; ++bb) {
+        double t0, t1, t2;
+        ct_link(M, sm, Ly, Ly.x, bb, t0, t1, t2);
+        if (bb == b) { t0 -= f0; t1 -= f1; t2 -= f2; }
+        out[(size_t)(3 * bb) * nc + ci] = t0;
+        out[(size_t)(3 * bb + 1) * nc + ci] = t1;
+        out[(size_t)(3 * bb + 2) * nc + ci] = t2;
+        chk += t0 + t1 + t2;
+      }
+    }
+  }
+
   // Theta^delta per contact, and its Jacobian in the contact's local variables
-  // (p_y-, theta-, v_x+, v_y+, omega+, v_y-, omega-, Phi_t, Phi_n, Gamma) of its link.
+  // (p_x-, p_y-, theta-, v_x+, v_y+, omega+, v_x-, v_y-, omega-, Phi_t, Phi_n, Gamma)
+  // of its link.
   for (int b = 0; b < nb; ++b) {
     const int ci = M.contact[b];
     if (ci < 0) continue;
     const double rx = SM(Ly.carm + 2 * ci), ry = SM(Ly.carm + 2 * ci + 1);
     const double pt = ph[2 * ci], pn = ph[2 * ci + 1], ga = gm[ci], e = M.e[ci];
     const double mu = M.mu[b];
+    const double tx = FRV(ci, FR_TX), ty = FRV(ci, FR_TY), nx = FRV(ci, FR_NX), ny = FRV(ci, FR_NY);
     const double wp = xp[nq + 3 * b + 2], wm = xm[nq + 3 * b + 2];
-    const double phi = xm[3 * b + 1] + ry;
-    const double vtp = fma(-wp, ry, xp[nq + 3 * b]);
-    const double vnp = fma(wp, rx, xp[nq + 3 * b + 1]);
-    const double vnm = fma(wm, rx, xm[nq + 3 * b + 1]);
-    const double cn = fma(e, vnm, vnp);
+    const double phi = terrain ? FRV(ci, FR_PHI) : xm[3 * b + 1] + ry;  // flat: p_y- + r_y
+    // contact-point velocities after (p) and before (m) the impact
+    const double vxp = fma(-wp, ry, xp[nq + 3 * b]), vyp = fma(wp, rx, xp[nq + 3 * b + 1]);
+    const double vxm = fma(-wm, ry, xm[nq + 3 * b]), vym = fma(wm, rx, xm[nq + 3 * b + 1]);
+    const double Vx = fma(e, vxm, vxp), Vy = fma(e, vym, vyp);  // v_c+ + e v_c-
+    const double cn = fma(nx, Vx, ny * Vy);
+    const double vtp = fma(tx, vxp, ty * vyp);
     const double sq = sqrt(fma(pt, pt, 1.0));
     const double gn = pt / sq;
     const double lc = fma(ga, gn, vtp);
@@ -387,46 +466,66 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ NodeTab M,
     th[7] = -rho;
     chk += th[0] + th[1] + th[2] + th[3] + rho + phi;
     if (dtheta) {
-      // derivatives of the pair arguments in the local variables:
-      //   phi: p_y 1, theta r_x
-      //   cn:  theta -(w+ + e w-) r_y, v_y+ 1, w+ r_x, v_y- e, w- e r_x
-      //   lc:  theta -w+ r_x, v_x+ 1, w+ -r_y, Phi_t Gamma / sq^3, Gamma gn
-      //   rho: Phi_t -dpt, Phi_n mu dmn
-      double* D = dtheta + ((size_t)k * nc + ci) * 80;
-      for (int q = 0; q < 80; ++q) D[q] = 0.0;
-      const double dcn_th = -(wp + e * wm) * ry, dlc_th = -wp * rx;
+      // derivatives of the pair arguments in the local variables
+      // (0 p_x, 1 p_y, 2 theta, 3 v_x+, 4 v_y+, 5 w+, 6 v_x-, 7 v_y-, 8 w-, 9 Phi_t, 10 Phi_n, 11 Gamma),
+      // with dx_c = dp_x - r_y dtheta, dy_c = dp_y + r_x dtheta:
+      //   phi: phi_x dx_c + phi_y dy_c
+      //   cn = n . V: (dn/dx) . V dx_c + n . dV,  V = v_c+ + e v_c-
+      //   lc = t . v_c+ + Gamma gn: (dt/dx) . v_c+ dx_c + t . dv_c+ + ...
+      //   dv_c/dtheta = (-w r_x, -w r_y), dv_c/dw = (-r_y, r_x)
+      constexpr int NT = CISCVX_NODE_THETA_COLS;
+      double* D = dtheta + ((size_t)k * nc + ci) * 8 * NT;
+      for (int q = 0; q < 8 * NT; ++q) D[q] = 0.0;
+      const double phx = FRV(ci, FR_PHIX), phy = FRV(ci, FR_PHIY);
+      const double dndx_V = fma(FRV(ci, FR_DNX), Vx, FRV(ci, FR_DNY) * Vy);
+      const double dtdx_v = fma(FRV(ci, FR_DTX), vxp, FRV(ci, FR_DTY) * vyp);
+      // argument derivatives: [px, py, theta]
+      const double dphi[3] = {phx, phy, fma(-phx, ry, phy * rx)};
+      const double dcn_x = dndx_V, dlc_x = dtdx_v;
+      // theta: through x_c and through the lever arms of both velocities
+      const double dcn_th = fma(-ry, dcn_x, -(wp + e * wm) * fma(nx, rx, ny * ry));
+      const double dlc_th = fma(-ry, dlc_x, -wp * fma(tx, rx, ty * ry));
       const double dlc_pt = ga / (sq * sq * sq);
       const double c1 = f1b * dcn, c2 = f2b * dlc;
-      D[0 * 10 + 8] = f0a; D[0 * 10 + 0] = f0b; D[0 * 10 + 1] = f0b * rx;
-      D[1 * 10 + 8] = f1a;
-      D[1 * 10 + 1] = c1 * dcn_th; D[1 * 10 + 3] = c1; D[1 * 10 + 4] = c1 * rx;
-      D[1 * 10 + 5] = c1 * e; D[1 * 10 + 6] = c1 * e * rx;
-      D[2 * 10 + 8] = f2a;
-      D[2 * 10 + 1] = c2 * dlc_th; D[2 * 10 + 2] = c2; D[2 * 10 + 4] = -c2 * ry;
-      D[2 * 10 + 7] = c2 * dlc_pt; D[2 * 10 + 9] = c2 * gn;
-      D[3 * 10 + 9] = f3a; D[3 * 10 + 7] = -f3b * dpt; D[3 * 10 + 8] = f3b * mu * dmn;
-      D[4 * 10 + 8] = -1.0;
-      D[5 * 10 + 0] = -1.0; D[5 * 10 + 1] = -rx;
-      D[6 * 10 + 9] = -1.0;
-      D[7 * 10 + 7] = dpt; D[7 * 10 + 8] = -mu * dmn;
+      // row 0: FB(Phi_n, phi)
+      D[0 * NT + 10] = f0a;
+      D[0 * NT + 0] = f0b * dphi[0]; D[0 * NT + 1] = f0b * dphi[1]; D[0 * NT + 2] = f0b * dphi[2];
+      // row 1: FB(Phi_n, |cn|~)
+      D[1 * NT + 10] = f1a;
+      D[1 * NT + 0] = c1 * dcn_x; D[1 * NT + 2] = c1 * dcn_th;
+      D[1 * NT + 3] = c1 * nx; D[1 * NT + 4] = c1 * ny; D[1 * NT + 5] = c1 * fma(-nx, ry, ny * rx);
+      D[1 * NT + 6] = c1 * e * nx; D[1 * NT + 7] = c1 * e * ny; D[1 * NT + 8] = c1 * e * fma(-nx, ry, ny * rx);
+      // row 2: FB(Phi_n, |lc|~)
+      D[2 * NT + 10] = f2a;
+      D[2 * NT + 0] = c2 * dlc_x; D[2 * NT + 2] = c2 * dlc_th;
+      D[2 * NT + 3] = c2 * tx; D[2 * NT + 4] = c2 * ty; D[2 * NT + 5] = c2 * fma(-tx, ry, ty * rx);
+      D[2 * NT + 9] = c2 * dlc_pt; D[2 * NT + 11] = c2 * gn;
+      // row 3: FB(Gamma, rho)
+      D[3 * NT + 11] = f3a; D[3 * NT + 9] = -f3b * dpt; D[3 * NT + 10] = f3b * mu * dmn;
+      D[4 * NT + 10] = -1.0;
+      D[5 * NT + 0] = -dphi[0]; D[5 * NT + 1] = -dphi[1]; D[5 * NT + 2] = -dphi[2];
+      D[6 * NT + 11] = -1.0;
+      D[7 * NT + 9] = dpt; D[7 * NT + 10] = -mu * dmn;
     }
   }
   if (!isfinite(chk)) atomicOr(status, ST_NONFINITE);
 }
 
+#undef FRV
 #undef LK
 #undef SM
 
 }  // namespace
 
 size_t node_smem_per_warp(const DevModel& M) {
-  return (size_t)node_layout(M.nb, M.nj, M.nc, M.noff[2 * M.nj]).total * 32 * sizeof(double);
+  return (size_t)node_layout(M.nb, M.nj, M.nc, M.noff[2 * M.nj], M.ta != 0.0).total * 32 * sizeof(double);
 }
 
 cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const double* Xp,
                         const double* Xm, const double* Phi, const double* Gam,
                         const NodeParams& P, double* g, double* Gvm, double* Gth, double* Gphi,
-                        double* theta, double* dtheta, unsigned* status, cudaStream_t st) {
+                        double* Gpx, double* theta, double* dtheta, unsigned* status,
+                        cudaStream_t st) {
   const size_t per_warp = node_smem_per_warp(Mh);
   const size_t budget = 220u * 1024u;  // one CTA per SM, as many warps as fit (<= 8)
   int wpc = (int)std::min<size_t>(8, std::max<size_t>(1, budget / per_warp));
@@ -463,9 +562,11 @@ cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const dou
     T.noff[i] = Mh.noff[i];
   }
   T.delta = P.delta;
+  T.ta = Mh.ta;
+  T.tk = Mh.tk;
   for (int i = 0; i < Mh.nc; ++i) T.e[i] = P.e[i];
-  k_node<<<(unsigned)blocks, threads, smem, st>>>(T, n, Xp, Xm, Phi, Gam, g, Gvm, Gth, Gphi, theta,
-                                                  dtheta, status);
+  k_node<<<(unsigned)blocks, threads, smem, st>>>(T, n, Xp, Xm, Phi, Gam, g, Gvm, Gth, Gphi, Gpx,
+                                                  theta, dtheta, status);
   return cudaGetLastError();
 }
 

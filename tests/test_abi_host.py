@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert lib.ciscvx_version() == 6
+    assert lib.ciscvx_version() == 7
 
 
 def test_null_arguments_rejected(lib):
@@ -52,7 +52,7 @@ def test_null_arguments_rejected(lib):
     assert lib.ciscvx_model_dims(None, None, None, None) == api.EINVAL
     prm = api._NodeParams(1e-3, None)
     assert lib.ciscvx_node_linearize(None, 4, None, None, None, None, ctypes.byref(prm), None,
-                                     None, None, None, None, None, None) == api.EINVAL
+                                     None, None, None, None, None, None, None) == api.EINVAL
     assert lib.ciscvx_discretize_compact(None, 10, 4, 0, 0, None, None, None, None, None, None,
                                          None, None, None, None, None) == api.EINVAL
     lo, hi = ctypes.c_size_t(), ctypes.c_size_t()

@@ -2,8 +2,9 @@
 
 Every output block is compared node by node with the oracle's dual-number
 Jacobians at the FP64 tolerance (block-normwise relative 1e-10): the residual
-G~, d(v rows)/dv-, d(v rows)/dtheta-, d(v rows)/dPhi, Theta^delta and each
-contact's local Theta Jacobian.  Node counts span several warps with a ragged
+G~, d(v rows)/dv-, d(v rows)/dtheta-, d(v rows)/dPhi, d(v rows)/dp_x-,
+Theta^delta and each contact's local Theta Jacobian, on flat ground and on
+the sinusoidal surface of Sec. VI-B.  Node counts span several warps with a ragged
 tail.
 """
 import numpy as np
@@ -30,6 +31,9 @@ def _robot(name):
     rng = np.random.default_rng(31)
     if name in ("hopper", "biped", "cheetah7"):
         return getattr(synth, name)(rng).as_dict()
+    if name.endswith("_sine"):  # the sinusoidal contact surface of Sec. VI-B
+        R = getattr(synth, name[:-5])(rng)
+        return synth.with_paper_dynamics(R, joint_forces=0, scheme=0, terrain=synth.TERRAIN_SINE).as_dict()
     from test_gpu_discretize import _edge_robots
     return _edge_robots()[name]
 
@@ -47,13 +51,14 @@ def _inputs(R, n, seed):
 
 
 def _local_cols(R, nxt):
+    """Oracle columns of (p_x-, p_y-, theta-, v_x+, v_y+, omega+, v_x-, v_y-, omega-, Phi_t, Phi_n, Gamma)."""
     nb, nc = len(R["mass"]), len(R["contact_body"])
     nq = 3 * nb
     out = []
     for i, b in enumerate(R["contact_body"]):
-        out.append([nxt + 3 * b + 1, nxt + 3 * b + 2, nq + 3 * b, nq + 3 * b + 1, nq + 3 * b + 2,
-                    nxt + nq + 3 * b + 1, nxt + nq + 3 * b + 2, 2 * nxt + 2 * i, 2 * nxt + 2 * i + 1,
-                    2 * nxt + 2 * nc + i])
+        out.append([nxt + 3 * b, nxt + 3 * b + 1, nxt + 3 * b + 2, nq + 3 * b, nq + 3 * b + 1,
+                    nq + 3 * b + 2, nxt + nq + 3 * b, nxt + nq + 3 * b + 1, nxt + nq + 3 * b + 2,
+                    2 * nxt + 2 * i, 2 * nxt + 2 * i + 1, 2 * nxt + 2 * nc + i])
     return out
 
 
@@ -69,6 +74,8 @@ def _node_errors(got, ref, R):
     }
     if nc:
         blocks["Gphi"] = (got["Gphi"], J[:, V, 2 * nxt:2 * nxt + 2 * nc])
+        px = [nxt + 3 * b for b in R["contact_body"]]
+        blocks["Gpx"] = (got["Gpx"], J[:, V][:, :, px])
         blocks["theta"] = (got["theta"], ref["theta"].reshape(-1, nc, 8))
         cols = _local_cols(R, nxt)
         dref = np.stack([ref["Jth"][:, 8 * i:8 * i + 8][:, :, cols[i]] for i in range(nc)], axis=1)
@@ -93,7 +100,8 @@ def _run(env, R, n, seed, delta=1e-3, jacobians=True):
 
 
 @pytest.mark.parametrize("name,n", [("hopper", 45), ("biped", 70), ("cheetah7", 101),
-                                    ("no_contact", 33), ("lone_link", 5)])
+                                    ("no_contact", 33), ("lone_link", 5), ("hopper_sine", 40),
+                                    ("biped_sine", 66), ("cheetah7_sine", 99)])
 def test_node_linearize_matches_oracle(env, name, n):
     R = _robot(name)
     got, ref = _run(env, R, n, seed=n)

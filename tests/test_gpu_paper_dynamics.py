@@ -137,15 +137,10 @@ def test_unsupported_entry_points(env):
     m = api.Model(p.robot)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     X, U, s = t(p.X), t(p.U), t(p.s)
-    e = np.full(m.nc, 0.0)
-    Phi = torch.zeros((3, 2 * m.nc), dtype=torch.float64, device=dev)
-    Gam = torch.zeros((3, m.nc), dtype=torch.float64, device=dev)
-    Xn = torch.zeros((3, m.nxt), dtype=torch.float64, device=dev)
     for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
                  lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
                  lambda: api.model_pattern(p.robot.as_dict()),
-                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact"),
-                 lambda: api.node_linearize(m, Xn, Xn, Phi, Gam, 1e-3, e)):
+                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
         with pytest.raises(api.CiscvxError) as err:
             call()
         assert err.value.status == api.EUNSUPPORTED
