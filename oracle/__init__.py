@@ -19,6 +19,7 @@ from .oracle import (  # noqa: F401
     linear_interval,
     node,
     node_value,
+    psi,
     rhs,
     tableau,
     vjp,

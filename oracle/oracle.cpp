@@ -42,6 +42,11 @@
 //               (Eq. (6a) with the joint impulse eliminated, Sec. II-B) and the
 //               Fischer-Burmeister-relaxed impulse conditions Theta^delta
 //               (Eqs. (6b)-(6e), (16)), with Jacobians by dual numbers.
+//   psi()       Psi^{delta,eps}(y-_{k+1}, y+_k) <= 0 of Eq. (17c) on every
+//               interval: Fischer-Burmeister-relaxed (Eq. (16)) integral
+//               cross-complementarity of the auxiliary-state increments
+//               (Eq. (11) applied to the pairs of Eq. (12)) and the relaxed
+//               path-constraint rows of Eq. (13), with Jacobians by dual numbers.
 //
 // Readings of points the paper leaves open (one auxiliary state per contact,
 // pseudo-Huber ramp h(z) = sqrt(1 + max(z,0)^2) - 1, joint reaction forces and
@@ -857,6 +862,50 @@ int oracle_node(const OracleModel* M, int n, const double* Xp, const double* Xm,
     for (int r = 0; r < 8 * nc; ++r) {
       if (theta) theta[k * 8 * nc + r] = tv[r].v;
       if (Jth) for (int c = 0; c < ncol; ++c) Jth[((size_t)k * 8 * nc + r) * ncol + c] = tv[r].d[c];
+    }
+  });
+  return 0;
+}
+
+// Psi^{delta,eps}(y-_{k+1}, y+_k) at N intervals, from the node states
+// Xp, Xm [N+1][nxt] (post-/pre-impact).  With d = y-_{k+1} - y+_k the
+// auxiliary-state increment over interval k:
+//   aux model 1 (Eq. (12) states phi_n, lambda^c, gamma, rho^c at y index
+//     4i..4i+3, path penalty at 4 nc + i): per contact i the integral
+//     cross-complementarity pairs (phi_n, lambda^c) and (gamma, rho^c)
+//     relaxed by Eq. (16), FB(d[4i], d[4i+1]) and FB(d[4i+2], d[4i+3]), at
+//     rows 2i and 2i+1; then per contact the relaxed path-constraint row of
+//     Eq. (13), d[4 nc + i] - eps, at row 2 nc + i (3 nc rows);
+//   aux model 0 (one path-penalty state per contact): d[i] - eps (nc rows).
+// Outputs (any may be NULL): psi [N][npsi], J [N][npsi][2 ny] with columns
+// (y+_k, y-_{k+1}).
+int oracle_psi(const OracleModel* M, int N, const double* Xp, const double* Xm, double delta,
+               double eps, double* psi, double* J, int nthreads) {
+  if (!model_ok(M) || N < 1 || !(delta > 0.0)) return 1;
+  const int nxt = nxt_of(*M), nc = M->nc, ny = nxt - 6 * M->nb;
+  const int npsi = M->aux ? 3 * nc : nc, ncol = 2 * ny;
+  if (ncol > MAXC) return 1;
+  parallel_for(N, nthreads, [&](long k) {
+    g_nd = ncol;
+    std::vector<Dual> d(ny), out(npsi);
+    for (int j = 0; j < ny; ++j) {
+      Dual yp(Xp[k * nxt + 6 * M->nb + j]), ym(Xm[(k + 1) * nxt + 6 * M->nb + j]);
+      yp.d[j] = 1.0;
+      ym.d[ny + j] = 1.0;
+      d[j] = ym - yp;
+    }
+    if (M->aux) {
+      for (int i = 0; i < nc; ++i) {
+        out[2 * i] = fischer_burmeister(d[4 * i], d[4 * i + 1], delta);
+        out[2 * i + 1] = fischer_burmeister(d[4 * i + 2], d[4 * i + 3], delta);
+        out[2 * nc + i] = d[4 * nc + i] - eps;
+      }
+    } else {
+      for (int i = 0; i < nc; ++i) out[i] = d[i] - eps;
+    }
+    for (int r = 0; r < npsi; ++r) {
+      if (psi) psi[k * npsi + r] = out[r].v;
+      if (J) for (int c = 0; c < ncol; ++c) J[((size_t)k * npsi + r) * ncol + c] = out[r].d[c];
     }
   });
   return 0;

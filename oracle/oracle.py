@@ -77,9 +77,11 @@ def _load():
                                         ctypes.c_double, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
             lib.oracle_node_value.argtypes = [ctypes.POINTER(_CModel), _dp, _dp, _dp, _dp,
                                               ctypes.c_double, _dp, _dp, _dp]
+            lib.oracle_psi.argtypes = [ctypes.POINTER(_CModel), ctypes.c_int, _dp, _dp,
+                                       ctypes.c_double, ctypes.c_double, _dp, _dp, ctypes.c_int]
             for f in ("oracle_dims", "oracle_rhs", "oracle_flow", "oracle_interval",
                       "oracle_discretize", "oracle_vjp", "oracle_linear_interval", "oracle_node",
-                      "oracle_node_value", "oracle_tableau"):
+                      "oracle_node_value", "oracle_tableau", "oracle_psi"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -298,3 +300,21 @@ def node_value(model, xp, xm, Phi, Gam, delta, e):
                                      _d(_nonempty(Gam)), float(delta), _d(_nonempty(e)), _d(g),
                                      _d(th)), "node_value")
     return g, th[:8 * nc]
+
+
+def psi(model, Xp, Xm, delta, eps, threads=0):
+    """Psi^{delta,eps}(y-_{k+1}, y+_k) on the N intervals between N+1 nodes.
+
+    Returns dict psi [N, npsi] and J [N, npsi, 2 ny], columns (y+_k, y-_{k+1});
+    npsi = 3 nc for the Eq. (12) auxiliary state, nc for one penalty state per
+    contact (rows as in oracle.cpp's oracle_psi)."""
+    m = _model(model)
+    Xp, Xm = _f64(Xp), _f64(Xm)
+    N = Xp.shape[0] - 1
+    ny = m.nxt - 6 * m.nb
+    npsi = 3 * m.nc if m.aux else m.nc
+    out = {"psi": np.empty((N, npsi)), "J": np.empty((N, npsi, 2 * ny))}
+    _check(_load().oracle_psi(m.ptr, N, _d(Xp), _d(Xm), float(delta), float(eps),
+                              _d(_nonempty(out["psi"])), _d(_nonempty(out["J"])), int(threads)),
+           "psi")
+    return out

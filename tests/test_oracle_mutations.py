@@ -16,9 +16,18 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
 PINS = ["tests/test_oracle_integrator.py", "tests/test_oracle_physics.py", "tests/test_oracle_vjp.py",
-        "tests/test_oracle_node.py", "tests/test_oracle_cross.py", "tests/test_oracle_paper_dynamics.py"]
+        "tests/test_oracle_node.py", "tests/test_oracle_cross.py", "tests/test_oracle_paper_dynamics.py",
+        "tests/test_oracle_psi.py"]
 
 MUTATIONS = [
+    ("Psi pair (phi_n, lambda^c) takes gamma", "out[2 * i] = fischer_burmeister(d[4 * i], d[4 * i + 1], delta);",
+     "out[2 * i] = fischer_burmeister(d[4 * i], d[4 * i + 2], delta);"),
+    ("Psi pair (gamma, rho^c) takes lambda^c", "out[2 * i + 1] = fischer_burmeister(d[4 * i + 2], d[4 * i + 3], delta);",
+     "out[2 * i + 1] = fischer_burmeister(d[4 * i + 1], d[4 * i + 3], delta);"),
+    ("Psi increment reversed", "d[j] = ym - yp;", "d[j] = yp - ym;"),
+    ("Psi epsilon sign", "out[2 * nc + i] = d[4 * nc + i] - eps;", "out[2 * nc + i] = d[4 * nc + i] + eps;"),
+    ("Psi path row index", "out[2 * nc + i] = d[4 * nc + i] - eps;", "out[2 * nc + i] = d[4 * i + 3] - eps;"),
+    ("Psi y- taken at node k", "ym(Xm[(k + 1) * nxt + 6 * M->nb + j]);", "ym(Xm[k * nxt + 6 * M->nb + j]);"),
     ("parent joint torque sign", "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) - tau;",
      "Tq[p] = Tq[p] - cross2(rpx, rpy, lx, ly) + tau;"),
     ("parent joint force sign", "Fx[p] = Fx[p] - lx;", "Fx[p] = Fx[p] + lx;"),
