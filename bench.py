@@ -43,6 +43,17 @@ from paper_2604_09993_gb300 import synth  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 126 * 2 ** 20
 
+
+def _measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+HBM_GBS = _measured_hbm_gbs()
+
 # make(n_inst, seed): rank r of a multi-GPU run uses seed r (its own independent batch)
 WORKLOADS = {
     "cheetah7-sweep-4096x400x20": dict(kind="batch", instances=4096,
@@ -613,6 +624,36 @@ def run_ours(args):
                  "nodes_per_gpu": n_nodes, "ms_per_call": tn / args.steps * 1e3}
         wl.node_free()
 
+    # Psi^{delta,eps} (Eq. (17c)) with the Eq. (12) auxiliary state on as many
+    # intervals as the batch holds, as one trajectory of seeded node states
+    psi = None
+    if spec["kind"] == "batch" and not args.no_nodes:
+        wl.free(prec)
+        rx = synth.with_cross_states(wl.batch.robots[0])
+        mp = api.Model(rx)
+        npsi, ny = api.psi_rows(mp), mp.ny
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(4321)
+        Xp = torch.rand((wl.intervals + 1, mp.nxt), generator=gen, device=dev, dtype=torch.float64)
+        Xm = torch.rand((wl.intervals + 1, mp.nxt), generator=gen, device=dev, dtype=torch.float64)
+        po = api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4)
+        barrier()
+        tp = time_steps(torch, lambda: api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4, out=po), args.steps,
+                        args.warmup, stream)
+        barrier()
+        api.sync_status(mp)
+        tp, = max_over_ranks([tp])
+        # algorithmic bytes per interval: y+ and y- read, Psi and its Jacobian written
+        bpi = 8 * (2 * ny + npsi * (1 + ny))
+        psi = {"metric": "linearized intervals/s (Psi^{delta,eps}, Eq. (12) auxiliary state, FP64)",
+               "value": wl.intervals * world * args.steps / tp, "unit": "intervals/s",
+               "intervals_per_gpu": wl.intervals, "robot": rx.name, "n_psi": npsi, "n_y": ny,
+               "ms_per_call": tp / args.steps * 1e3, "bytes_per_interval": bpi,
+               "achieved_gbs": bpi * wl.intervals * args.steps / tp / 1e9}
+        psi["hbm_frac_of_measured"] = psi["achieved_gbs"] / HBM_GBS if HBM_GBS else None
+        del Xp, Xm, po, mp
+        torch.cuda.empty_cache()
+
     # the linearization of the same batch with the full Eq. (12) auxiliary state
     # (four cross-complementarity states + one path-penalty state per contact)
     cross = None
@@ -696,6 +737,7 @@ def run_ours(args):
         "e2e": e2e,
         "compact_outputs": compact,
         "node_constraints": nodes,
+        "psi": psi,
         "aux_cross_model": cross,
         "paper_dynamics": paper,
         "clocks": clocks,

@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 7
+#define CISCVX_VERSION_MINOR 8
 
 typedef enum {
   CISCVX_OK = 0,
@@ -138,8 +138,9 @@ typedef struct {
  *     at y index 4 i .. 4 i + 3, then one path-penalty state per contact at y
  *     index 4 n_c + i integrating h(-phi_n) + h(-phi) + h(-gamma) + h(-rho^c)
  *     (n_y = 5 n_c).  The penalty output is the increment of the path-penalty
- *     states.  Provided for the dense linearization (single and batch); the
- *     VJP, compact outputs and z return CISCVX_EUNSUPPORTED for it. */
+ *     states.  Provided for the dense linearization (single and batch) and
+ *     the single-instance VJP (linearize-and-contract); compact outputs, z
+ *     and batched VJPs return CISCVX_EUNSUPPORTED for it. */
 typedef enum { CISCVX_AUX_PENALTY = 0, CISCVX_AUX_CROSS = 1 } ciscvx_aux_model;
 
 /* Joint reaction forces (Sec. II-A).
@@ -535,9 +536,8 @@ ciscvx_status ciscvx_batch_sync_status(const ciscvx_batch_plan* plan, void* stre
  *     "Phi_n times a signed quantity = 0" (Eqs. (6c), (6d)) is relaxed as the
  *     complementarity of Phi_n with the quantity's pseudo-Huber magnitude.
  *
- * With the single penalty state per contact of this model, the remaining node
- * constraint Psi (Eq. (17c)) is the linear y-_{k+1} - y+_k <= epsilon and
- * needs no linearization.
+ * The constraint between consecutive nodes, Psi (Eq. (17c)), is
+ * ciscvx_psi_linearize below.
  */
 
 /* Theta rows per contact, and the local variables its Jacobian is taken in. */
@@ -588,6 +588,43 @@ ciscvx_status ciscvx_node_linearize(const ciscvx_model* model, int n_nodes, cons
                                     const ciscvx_node_params* params, double* g, double* Gvm,
                                     double* Gth, double* Gphi, double* Gpx, double* theta,
                                     double* dtheta, void* stream);
+
+/* ------------------------------------------ interval-node constraints --- */
+/*
+ * Psi^{delta,eps}(y-_{k+1}, y+_k) <= 0 (Sec. IV-C, Eq. (17c)) on the N grid
+ * intervals between N+1 nodes, for the auxiliary-state increment
+ * d_k = y-_{k+1} - y+_k (pre-impact state at the interval's end minus
+ * post-impact state at its start; y = the last n_y entries of x~):
+ *   CISCVX_AUX_CROSS (n_psi = 3 n_c): per contact i the integral
+ *     cross-complementarity of Eq. (11) on the Eq. (12) pairs, relaxed by
+ *     Eq. (16) with FB(a, b) = a + b - sqrt(a^2 + b^2 + delta):
+ *       row 2i       FB(d[4i], d[4i+1])      (phi_n, lambda^c)
+ *       row 2i+1     FB(d[4i+2], d[4i+3])    (gamma, rho^c)
+ *     then the relaxed path constraints of Eq. (13):
+ *       row 2 n_c + i   d[4 n_c + i] - epsilon;
+ *     the nonnegativity of the increments comes from the path penalty (the
+ *     integrands' sign constraints), as the paper prescribes, and the pair
+ *     (phi_n, signed distance) has no state to pair (no auxiliary state
+ *     integrates the signed distance).
+ *   CISCVX_AUX_PENALTY (n_psi = n_c): row i = d[i] - epsilon.
+ */
+
+/* n_psi of the model: 3 n_c (CISCVX_AUX_CROSS) or n_c. */
+ciscvx_status ciscvx_psi_rows(const ciscvx_model* model, int* n_psi);
+
+/* Psi and its Jacobian at N intervals (thread per output element; FP64).
+ *   Xp, Xm [N+1][n_x~]: post- and pre-impact node states (device; only their
+ *     y entries are read: y+ of nodes 0..N-1, y- of nodes 1..N).
+ *   psi [N][n_psi] (device, required when n_psi > 0).
+ *   dpsi [N][n_psi][n_y] (device, may be NULL): d Psi_k / d y-_{k+1}; the
+ *     Jacobian in y+_k is its negative, in every other variable 0.
+ * Asynchronous on `stream`; a non-finite Psi sets the model's status word
+ * (ciscvx_sync_status).  n_psi == 0 (no contacts) is a no-op.
+ * Errors: EINVAL (null model, N < 1, delta not finite > 0, epsilon not
+ * finite >= 0, null Xp/Xm/psi), ECUDA. */
+ciscvx_status ciscvx_psi_linearize(const ciscvx_model* model, int N, const double* Xp,
+                                   const double* Xm, double delta, double epsilon, double* psi,
+                                   double* dpsi, void* stream);
 
 /* ------------------------------------------------ allocation-free VJP --- */
 

@@ -32,7 +32,8 @@ EXPORTS = (
     "ciscvx_batch_sync_status", "ciscvx_batch_run_host",
     "ciscvx_model_pattern", "ciscvx_model_nnz", "ciscvx_discretize_compact",
     "ciscvx_node_linearize", "ciscvx_batch_discretize_and_vjp", "ciscvx_batch_autotune_fused",
-    "ciscvx_batch_get_tune_fused", "ciscvx_discretize_workspace_size",
+    "ciscvx_batch_get_tune_fused", "ciscvx_discretize_workspace_size", "ciscvx_psi_rows",
+    "ciscvx_psi_linearize",
 )
 FORMAT = {"dense": 0, "compact": 1}
 
@@ -129,6 +130,9 @@ def load(path: str | None = None):
     lib.ciscvx_node_linearize.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(_NodeParams), _vp, _vp, _vp, _vp, _vp,
                                           _vp, _vp, _vp]
+    lib.ciscvx_psi_rows.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
+    lib.ciscvx_psi_linearize.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                         _vp, _vp, _vp]
     lib.ciscvx_discretize_compact.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _vp, _vp]
@@ -408,6 +412,35 @@ def node_linearize(model: Model, Xp, Xm, Phi, Gam, delta: float, restitution,
         model.handle, int(n), _ptr(Xp), _ptr(Xm), _ptr(Phi) if nc else None, _ptr(Gam) if nc else None,
         ctypes.byref(prm), _ptr(out["g"]), has("Gvm"), has("Gth"), has("Gphi"), has("Gpx"),
         has("theta"), has("dtheta"), _stream()))
+    return out
+
+
+def psi_rows(model: Model) -> int:
+    """ciscvx_psi_rows: rows of Psi^{delta,eps} per interval (3 nc or nc)."""
+    n = ctypes.c_int()
+    _check(load().ciscvx_psi_rows(model.handle, ctypes.byref(n)))
+    return n.value
+
+
+def psi_linearize(model: Model, Xp, Xm, delta: float, epsilon: float, jacobian: bool = True,
+                  out: dict | None = None):
+    """ciscvx_psi_linearize: Psi^{delta,eps}(y-_{k+1}, y+_k) and d Psi / d y-_{k+1}.
+
+    Xp, Xm [N+1, nxt] device float64 tensors.  Returns dict psi [N, n_psi] and,
+    with jacobian, dpsi [N, n_psi, n_y] (the Jacobian in y+_k is -dpsi)."""
+    import torch
+    f64 = torch.float64
+    _need(Xp, "Xp", f64); _need(Xm, "Xm", f64)
+    N = Xp.shape[0] - 1
+    npsi, ny = psi_rows(model), model.nxt - 6 * model.nb
+    if out is None:
+        out = {"psi": torch.empty((N, npsi), dtype=f64, device=Xp.device)}
+        if jacobian:
+            out["dpsi"] = torch.empty((N, npsi, ny), dtype=f64, device=Xp.device)
+    _check(load().ciscvx_psi_linearize(
+        model.handle, int(N), _ptr(Xp), _ptr(Xm), float(delta), float(epsilon),
+        _ptr(out["psi"]) if npsi else None,
+        _ptr(out["dpsi"]) if npsi and out.get("dpsi") is not None else None, _stream()))
     return out
 
 

@@ -575,6 +575,28 @@ ciscvx_status ciscvx_node_linearize(const ciscvx_model* m, int n, const double* 
   return ok();
 }
 
+ciscvx_status ciscvx_psi_rows(const ciscvx_model* m, int* n_psi) {
+  if (!m || !n_psi) return fail(CISCVX_EINVAL, "null model or output");
+  *n_psi = psi_rows(m->host);
+  return ok();
+}
+
+ciscvx_status ciscvx_psi_linearize(const ciscvx_model* m, int N, const double* Xp, const double* Xm,
+                                   double delta, double epsilon, double* psi, double* dpsi,
+                                   void* stream) {
+  if (!m) return fail(CISCVX_EINVAL, "null model");
+  if (N < 1) return fail(CISCVX_EINVAL, "N must be >= 1 (got %d)", N);
+  if (!(std::isfinite(delta) && delta > 0.0)) return fail(CISCVX_EINVAL, "delta must be finite and > 0");
+  if (!(std::isfinite(epsilon) && epsilon >= 0.0))
+    return fail(CISCVX_EINVAL, "epsilon must be finite and >= 0");
+  const DevModel& M = m->host;
+  if (psi_rows(M) == 0) return ok();
+  if (!Xp || !Xm || !psi) return fail(CISCVX_EINVAL, "null state or psi array");
+  cudaError_t e = launch_psi(M, N, Xp, Xm, delta, epsilon, psi, dpsi, m->status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "psi launch");
+  return ok();
+}
+
 ciscvx_status ciscvx_sync_status(const ciscvx_model* m, void* stream) {
   if (!m) return fail(CISCVX_EINVAL, "null model");
   cudaStream_t st = (cudaStream_t)stream;

@@ -206,6 +206,10 @@ cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const dou
                         const NodeParams& P, double* g, double* Gvm, double* Gth, double* Gphi,
                         double* Gpx, double* theta, double* dtheta, unsigned* status,
                         cudaStream_t st);
+// Psi^{delta,eps} rows per interval, and its launcher (psi.cu).
+int psi_rows(const DevModel& M);
+cudaError_t launch_psi(const DevModel& M, int N, const double* Xp, const double* Xm, double delta,
+                       double eps, double* psi, double* dpsi, unsigned* status, cudaStream_t st);
 // Records a formatted last-error message (thread-local) and returns st.
 ciscvx_status set_error(ciscvx_status st, const char* fmt, ...);
 }  // namespace ciscvx

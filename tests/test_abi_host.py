@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert lib.ciscvx_version() == 7
+    assert lib.ciscvx_version() == 8
 
 
 def test_null_arguments_rejected(lib):
@@ -58,6 +58,8 @@ def test_null_arguments_rejected(lib):
     lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
     assert lib.ciscvx_discretize_workspace_size(None, 0, 10, 4, 0, 0, ctypes.byref(lo),
                                                 ctypes.byref(hi)) == api.EINVAL
+    assert lib.ciscvx_psi_rows(None, None) == api.EINVAL
+    assert lib.ciscvx_psi_linearize(None, 4, None, None, 0.1, 1e-4, None, None, None) == api.EINVAL
 
 
 def _desc(api, nb=2, joints=((0, 1),), contacts=((1,),), mass=1.0):
