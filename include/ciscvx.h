@@ -626,6 +626,148 @@ ciscvx_status ciscvx_psi_linearize(const ciscvx_model* model, int N, const doubl
                                    const double* Xm, double delta, double epsilon, double* psi,
                                    double* dpsi, void* stream);
 
+/* ---------------------------------------------- SOCP canonicalization --- */
+/*
+ * The convex subproblem of one prox-linear SCP iteration (Sec. V: linearized
+ * nonconvex constraints under an exact l1 penalty, convex constraints kept,
+ * quadratic proximal term) assembled on the GPU in the canonical SOCP form
+ * of a conic interior-point solver (Sec. VI: CSC matrices, row-wise
+ * normalization, affine variable scaling):
+ *
+ *   minimize 1/2 z^T P z + c^T z   s.t.   A z = b,   h - G z in R+^l x Q^2 x ... x Q^2
+ *
+ * (Q^2 = {(s0, s1): s0 >= |s1|}), for the CITO problem of Eq. (17) at an
+ * iterate zbar, on N intervals between N+1 nodes.
+ *
+ * Variables, period k = 0..N (node part, then, for k < N, interval part):
+ *   x~-_k [n_x~], x~+_k [n_x~], Phi_k [2 n_c], Gamma_k [n_c],
+ *   u_k [n_u] (CISCVX_FOH_NODE only), nuG+_k, nuG-_k [n_x~ each], tTheta_k [8 n_c];
+ *   u_L,k, u_R,k [n_u each] (CISCVX_FOH_INTERVAL only), s_k [1],
+ *   nuF+_k, nuF-_k [n_x~ each], tPsi_k [n_psi].
+ * nu and t are the penalty slacks ("slack" columns); the rest are the
+ * problem's variables.
+ *
+ * Equality rows, period k: G~ rows of node k [n_x~]
+ *     J_G (z - zbar) + G~(zbar) - nuG+ + nuG- = 0;
+ *   dynamics rows of interval k [n_x~] (k < N), Eq. (17b) linearized
+ *     A_k x~+_k + B-_k u_L + B+_k u_R + S_k s_k - x~-_{k+1} - nuF+ + nuF- = b,
+ *     b = A_k x~+bar_k + B-_k u_Lbar + B+_k u_Rbar + S_k sbar_k - F~bar_k,
+ *     F~bar_k = defect_k + x~+bar_{k+1} (the linearization evaluated with
+ *     X = the post-impact states x~+bar), u_L, u_R = u_k, u_{k+1} (node
+ *     layout) or u_L,k, u_R,k;
+ *   then x-_0 = x_init [n_x] and x+_N = x_final [n_x] (Eq. (17g)).
+ * Inequality rows (G z <= h), nonnegative orthant first, period k:
+ *   Theta rows of node k [8 n_c]: J_Theta (z - zbar) + Theta(zbar) - tTheta <= 0;
+ *   -tTheta <= 0 [8 n_c]; -nuG+ <= 0, -nuG- <= 0 [2 n_x~];
+ *   the input rows of u_k (node layout);
+ *   for k < N: Psi rows [n_psi]: J_Psi (z - zbar) + Psi(zbar) - tPsi <= 0;
+ *   -tPsi <= 0 [n_psi]; -nuF+ <= 0, -nuF- <= 0 [2 n_x~];
+ *   s_k <= s_max, -s_k <= -s_min; the input rows of u_L,k then u_R,k
+ *   (interval layout);
+ *   input rows of one control vector (the set U of Eq. (17d)): per joint
+ *   tau_j <= tau_max_j, -tau_j <= tau_max_j [2 n_j]; per contact,
+ *   CISCVX_AUX_PENALTY: -lambda_n, -lambda_t+, -lambda_t- <= 0 and
+ *   lambda_t+ + lambda_t- - mu lambda_n <= 0 [4]; CISCVX_AUX_CROSS:
+ *   -gamma <= 0 [1].
+ * Then, CISCVX_AUX_CROSS only, one Q^2 block per control vector (in the
+ * order above) and contact: (mu phi_n, phi_t), i.e. G rows -mu e_phi_n and
+ * -e_phi_t, h = 0: the friction cone |phi_t| <= mu phi_n.
+ *
+ * Objective: P = w_px on the diagonal of every problem variable plus the
+ * torque cost w_torque * sum_k integral_0^1 |tau(t)|^2 dt of the FOH
+ * torques ((|a|^2 + a.b + |b|^2) / 3 per interval, a, b its end values);
+ * c = -w_px zbar on problem variables, w_ep on slack columns.
+ *
+ * Scaling: problem variables z = D zhat + o with per-component scale and
+ * offset (x~ for x~- and x~+, u, s, Phi, Gamma; identity by default);
+ * slacks unscaled.  A <- A D, b <- b - A o, G <- G D, h <- h - G o,
+ * P <- D P D, c <- D (P o + c).  Then every equality and nonnegative row is
+ * multiplied by rho = 1 / (max |entry| over its problem-variable columns)
+ * (rho = 1 when there is none or it is 0), and each Q^2 block by the
+ * smallest rho of its two rows; rho is returned per row.
+ */
+
+typedef struct ciscvx_socp ciscvx_socp;
+
+typedef struct {
+  double w_px;                 /* proximal weight, finite > 0 */
+  double w_ep;                 /* exact-penalty weight, finite > 0 */
+  double w_torque;             /* torque-cost weight, finite >= 0 */
+  double s_min, s_max;         /* 0 <= s_min <= s_max, finite */
+  const double* torque_max;    /* [n_j] host, finite > 0 (NULL if n_j == 0) */
+  const double* x_init;        /* [n_x] host */
+  const double* x_final;       /* [n_x] host */
+  /* affine scaling z = D zhat + o; each pair may be NULL (scale 1, offset 0);
+   * scales finite > 0, offsets finite */
+  const double* scale_x; const double* offset_x;      /* [n_x~] */
+  const double* scale_u; const double* offset_u;      /* [n_u] */
+  double scale_s, offset_s;                           /* scale_s 0 means 1 */
+  const double* scale_phi; const double* offset_phi;  /* [2 n_c] */
+  const double* scale_gam; const double* offset_gam;  /* [n_c] */
+} ciscvx_socp_params;
+
+typedef struct {
+  int n_var, n_eq, n_ineq;     /* columns; rows of A; rows of G */
+  int n_nonneg;                /* l: the first l rows of G */
+  int n_soc;                   /* Q^2 blocks after them (each 2 rows) */
+  long long nnz_A, nnz_G, nnz_P;
+} ciscvx_socp_dims;
+
+/* Builds the structure (host; the CSC patterns and the source map of every
+ * entry, uploaded to the device) for model, N intervals and the control
+ * layout.  The node blocks are taken dense (d(v rows)/dp_x- only on a
+ * sinusoidal surface; Theta's p_x- and v_x- columns too), the interval blocks
+ * at the model's structural pattern where the model has one (joint reaction
+ * forces as inputs, one penalty state per contact: ciscvx_model_pattern),
+ * dense otherwise.
+ * Errors: EINVAL (nulls, N < 1, params invalid), EUNSUPPORTED (more than
+ * 2^31 - 1 entries in a matrix), ENOMEM, ECUDA. */
+ciscvx_status ciscvx_socp_create(const ciscvx_model* model, int N, int layout,
+                                 const ciscvx_socp_params* params, ciscvx_socp** out);
+void ciscvx_socp_destroy(ciscvx_socp* socp);
+ciscvx_status ciscvx_socp_get_dims(const ciscvx_socp* socp, ciscvx_socp_dims* dims);
+
+/* The CSC index arrays and P's values (host buffers, any may be NULL):
+ * *_colptr [n_var + 1], *_rowind [nnz]; rows sorted within a column; P holds
+ * its upper triangle. */
+ciscvx_status ciscvx_socp_structure(const ciscvx_socp* socp, int* A_colptr, int* A_rowind,
+                                    int* G_colptr, int* G_rowind, int* P_colptr, int* P_rowind,
+                                    double* P_values);
+
+/* Device inputs of n_inst instances of the socp's shape, each array the
+ * concatenation over instances of the per-instance layout (the outputs of
+ * ciscvx_discretize at X = Xp, ciscvx_node_linearize at (Xp, Xm, Phi, Gam)
+ * and ciscvx_psi_linearize at (Xp, Xm), in FP64 except the Phi blocks). */
+typedef struct {
+  const double* Xp;     /* [N+1][n_x~] iterate: post-impact node states */
+  const double* Xm;     /* [N+1][n_x~] pre-impact node states */
+  const double* U;      /* [N+1][n_u] or [N][2][n_u] per the layout */
+  const double* s;      /* [N] */
+  const double* Phi;    /* [N+1][2 n_c] (NULL if n_c == 0) */
+  const double* Gam;    /* [N+1][n_c]   (NULL if n_c == 0) */
+  int phi_precision;    /* CISCVX_FP64 or CISCVX_FP32_PHI: type of A, Bm, Bp, S */
+  const void* A; const void* Bm; const void* Bp; const void* S;  /* dense, as ciscvx_discretize */
+  const double* defect; /* [N][n_x~] */
+  const double* g;      /* [N+1][n_x~] and the Jacobian blocks of ciscvx_node_linearize */
+  const double* Gvm; const double* Gth; const double* Gphi;
+  const double* Gpx;    /* read only on a sinusoidal surface */
+  const double* theta; const double* dtheta;  /* NULL if n_c == 0 */
+  const double* psi; const double* dpsi;      /* NULL if n_c == 0 */
+} ciscvx_socp_inputs;
+
+/* Device outputs, [n_inst][...] each: A_values [nnz_A], b [n_eq],
+ * G_values [nnz_G], h [n_ineq], c [n_var]; row scales rho_A [n_eq], rho_G
+ * [n_ineq] (may be NULL). */
+typedef struct {
+  double* A_values; double* b; double* G_values; double* h; double* c;
+  double* rho_A; double* rho_G;
+} ciscvx_socp_outputs;
+
+/* Numeric phase for n_inst instances (asynchronous on stream).  Errors:
+ * EINVAL (nulls, n_inst < 1, phi_precision), ECUDA. */
+ciscvx_status ciscvx_socp_fill(const ciscvx_socp* socp, int n_inst, const ciscvx_socp_inputs* in,
+                               const ciscvx_socp_outputs* out, void* stream);
+
 /* ------------------------------------------------ allocation-free VJP --- */
 
 /* Bytes of device scratch the library keeps for ciscvx_discretize_vjp_static. */

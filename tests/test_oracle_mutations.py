@@ -7,6 +7,7 @@ against that build through ``CISCVX_ORACLE_LIB``.  The pins must fail for
 every planted error; the real oracle must pass (the other test files).
 """
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -147,3 +148,50 @@ def test_pins_reject_planted_error(name, old, new):
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
+# Planted errors in the dense SOCP assembly (oracle/socp.py), caught by its pins.
+SOCP_SRC = os.path.join(ROOT, "oracle", "socp.py")
+SOCP_PINS = ["tests/test_oracle_socp.py"]
+SOCP_MUTATIONS = [
+    ("dynamics right-hand side takes the pre-impact state",
+     "b_rows.append(jz - (lin[\"defect\"][k, r_] + Xp[k + 1, r_]))",
+     "b_rows.append(jz - (lin[\"defect\"][k, r_] + Xm[k + 1, r_]))"),
+    ("B+ placed on u_L", "r[uR] += lin[\"Bp\"][k, r_]", "r[uL] += lin[\"Bp\"][k, r_]"),
+    ("impact slack sign", "r[L.col[\"nuGp\", k][r_]] -= 1.0", "r[L.col[\"nuGp\", k][r_]] += 1.0"),
+    ("dynamics slack sign", "r[L.col[\"nuFm\", k][r_]] += 1.0", "r[L.col[\"nuFm\", k][r_]] -= 1.0"),
+    ("Theta slack sign", "r[L.col[\"tth\", k][r_]] = -1.0\n            G_rows.append(r)\n            h_rows.append(hz)",
+     "r[L.col[\"tth\", k][r_]] = 1.0\n            G_rows.append(r)\n            h_rows.append(hz)"),
+    ("Psi sides swapped", "r[yp] += ps[\"J\"][k, r_, :ny]", "r[yp] += ps[\"J\"][k, r_, ny:]"),
+    ("torque cost coupling", "P0[a, b_] += w / 3", "P0[a, b_] += w / 6"),
+    ("proximal linear term sign", "c0[L.is_problem] = -prm[\"w_px\"] * zbar[L.is_problem]",
+     "c0[L.is_problem] = prm[\"w_px\"] * zbar[L.is_problem]"),
+    ("offset dropped from c", "c1 = D * (P0 @ o + c0)", "c1 = D * c0"),
+    ("offset sign in b", "A1, b1 = A0 * D[None, :], b0 - A0 @ o", "A1, b1 = A0 * D[None, :], b0 + A0 @ o"),
+    ("cone block scaled by the larger rho", "rG[r0:r0 + 2] = rG[r0:r0 + 2].min()",
+     "rG[r0:r0 + 2] = rG[r0:r0 + 2].max()"),
+    ("friction cone coefficient sign", "r[a] = -L.mu[i]", "r[a] = L.mu[i]"),
+    ("second-order cone on the wrong input", "r1[pt] = -1.0", "r1[pn] = -1.0"),
+    ("final boundary on the pre-impact state", "(L.col[\"xp\", N][:nx], prm[\"x_final\"])",
+     "(L.col[\"xm\", N][:nx], prm[\"x_final\"])"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", SOCP_MUTATIONS, ids=[m[0] for m in SOCP_MUTATIONS])
+def test_socp_pins_reject_planted_error(name, old, new, oracle_mod):
+    src = open(SOCP_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
+    with tempfile.TemporaryDirectory() as tmp:
+        # a tree whose oracle package carries the planted error; the built
+        # oracle library and the product package are the real ones
+        shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(tmp, "tests"),
+                        ignore=shutil.ignore_patterns("__pycache__"))
+        shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(tmp, "oracle"),
+                        ignore=shutil.ignore_patterns("__pycache__", "*.so", "*.lock"))
+        os.symlink(os.path.join(ROOT, "paper_2604_09993_gb300"), os.path.join(tmp, "paper_2604_09993_gb300"))
+        open(os.path.join(tmp, "oracle", "socp.py"), "w").write(src.replace(old, new))
+        env = dict(os.environ, CISCVX_ORACLE_LIB=oracle_mod.build())
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            *SOCP_PINS], cwd=tmp, env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+        assert "passed" in r.stdout or "failed" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
