@@ -755,16 +755,18 @@ typedef struct {
   const double* psi; const double* dpsi;      /* NULL if n_c == 0 */
 } ciscvx_socp_inputs;
 
-/* Device outputs, [n_inst][...] each: A_values [nnz_A], b [n_eq],
- * G_values [nnz_G], h [n_ineq], c [n_var]; row scales rho_A [n_eq], rho_G
- * [n_ineq] (may be NULL). */
+/* Device outputs, [n_inst][...] each, all required: A_values [nnz_A],
+ * b [n_eq], G_values [nnz_G], h [n_ineq], c [n_var], and the row scales
+ * rho_A [n_eq], rho_G [n_ineq] (to map the solver's duals back). */
 typedef struct {
   double* A_values; double* b; double* G_values; double* h; double* c;
   double* rho_A; double* rho_G;
 } ciscvx_socp_outputs;
 
-/* Numeric phase for n_inst instances (asynchronous on stream).  Errors:
- * EINVAL (nulls, n_inst < 1, phi_precision), ECUDA. */
+/* Numeric phase for n_inst instances (asynchronous on stream): a row pass
+ * (row scales, b and h), a CSC pass (the values of A and G) and a column
+ * pass (c).  The inputs may not alias the outputs.  Errors: EINVAL (nulls,
+ * n_inst < 1, phi_precision), ECUDA. */
 ciscvx_status ciscvx_socp_fill(const ciscvx_socp* socp, int n_inst, const ciscvx_socp_inputs* in,
                                const ciscvx_socp_outputs* out, void* stream);
 

@@ -33,7 +33,8 @@ EXPORTS = (
     "ciscvx_model_pattern", "ciscvx_model_nnz", "ciscvx_discretize_compact",
     "ciscvx_node_linearize", "ciscvx_batch_discretize_and_vjp", "ciscvx_batch_autotune_fused",
     "ciscvx_batch_get_tune_fused", "ciscvx_discretize_workspace_size", "ciscvx_psi_rows",
-    "ciscvx_psi_linearize",
+    "ciscvx_psi_linearize", "ciscvx_socp_create", "ciscvx_socp_destroy", "ciscvx_socp_get_dims",
+    "ciscvx_socp_structure", "ciscvx_socp_fill",
 )
 FORMAT = {"dense": 0, "compact": 1}
 
@@ -56,6 +57,41 @@ class _BatchIO(ctypes.Structure):
 
 class _BatchVjpIO(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("X", "U", "s", "w", "rho", "gX", "gU", "gs", "L")]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class _SocpParams(ctypes.Structure):
+    _fields_ = [("w_px", ctypes.c_double), ("w_ep", ctypes.c_double), ("w_torque", ctypes.c_double),
+                ("s_min", ctypes.c_double), ("s_max", ctypes.c_double), ("torque_max", _dp),
+                ("x_init", _dp), ("x_final", _dp), ("scale_x", _dp), ("offset_x", _dp),
+                ("scale_u", _dp), ("offset_u", _dp), ("scale_s", ctypes.c_double),
+                ("offset_s", ctypes.c_double), ("scale_phi", _dp), ("offset_phi", _dp),
+                ("scale_gam", _dp), ("offset_gam", _dp)]
+
+
+class _SocpDims(ctypes.Structure):
+    _fields_ = [("n_var", ctypes.c_int), ("n_eq", ctypes.c_int), ("n_ineq", ctypes.c_int),
+                ("n_nonneg", ctypes.c_int), ("n_soc", ctypes.c_int), ("nnz_A", ctypes.c_longlong),
+                ("nnz_G", ctypes.c_longlong), ("nnz_P", ctypes.c_longlong)]
+
+
+_SOCP_IN = ("Xp", "Xm", "U", "s", "Phi", "Gam")
+_SOCP_IN2 = ("A", "Bm", "Bp", "S", "defect", "g", "Gvm", "Gth", "Gphi", "Gpx", "theta", "dtheta",
+             "psi", "dpsi")
+
+
+class _SocpInputs(ctypes.Structure):
+    _fields_ = ([(k, ctypes.c_void_p) for k in _SOCP_IN] + [("phi_precision", ctypes.c_int)] +
+                [(k, ctypes.c_void_p) for k in _SOCP_IN2])
+
+
+_SOCP_OUT = ("A_values", "b", "G_values", "h", "c", "rho_A", "rho_G")
+
+
+class _SocpOutputs(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in _SOCP_OUT]
 
 
 class _NodeParams(ctypes.Structure):
@@ -133,6 +169,15 @@ def load(path: str | None = None):
     lib.ciscvx_psi_rows.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
     lib.ciscvx_psi_linearize.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                          _vp, _vp, _vp]
+    lib.ciscvx_socp_create.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_SocpParams),
+                                       ctypes.POINTER(_vp)]
+    lib.ciscvx_socp_destroy.argtypes = [_vp]
+    lib.ciscvx_socp_destroy.restype = None
+    lib.ciscvx_socp_get_dims.argtypes = [_vp, ctypes.POINTER(_SocpDims)]
+    _ip32 = ctypes.POINTER(ctypes.c_int)
+    lib.ciscvx_socp_structure.argtypes = [_vp, _ip32, _ip32, _ip32, _ip32, _ip32, _ip32, _dp]
+    lib.ciscvx_socp_fill.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(_SocpInputs),
+                                     ctypes.POINTER(_SocpOutputs), _vp]
     lib.ciscvx_discretize_compact.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _vp, _vp]
@@ -215,7 +260,7 @@ class _DescHolder:
         ta, tk = (float(v) for v in opt("terrain", (0.0, 0.0)))
         self.desc = _Desc(nb, nj, nc, self._bodies, self._joints, self._contacts,
                           float(_get(robot, "gravity")), aux, jf, scheme, ta, tk)
-        self.nb, self.nc, self.aux_model = nb, nc, aux
+        self.nb, self.nj, self.nc, self.aux_model = nb, nj, nc, aux
         self.coupled = bool(jf or scheme or ta != 0.0)
 
 
@@ -248,6 +293,7 @@ class Model:
         self.nx, self.ny, self.nu = nx.value, ny.value, nu.value
         self.nxt = self.nx + self.ny
         self.nb = self._d.nb
+        self.nj = self._d.nj
         self.nc = self._d.nc            # contacts (penalty / rho columns)
         self.aux_model = self._d.aux_model
         # eliminated joint forces, a sinusoidal surface or RKF45: the coupled path
@@ -535,6 +581,101 @@ def discretize_fn(model: Model, X, U, s, n_sub: int, precision: str = "fp64", la
     if _Discretize is None:
         _Discretize = _make_function()
     return _Discretize.apply(X, U, s, model, n_sub, precision, layout)
+
+
+def _host_vec(v, n, name):
+    if v is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1))
+    if a.size != n:
+        raise ValueError(f"{name} must hold {n} values")
+    return a, a.ctypes.data_as(_dp)
+
+
+class Socp:
+    """ciscvx_socp: the SCP subproblem of one (model, N, layout) shape as a
+    canonical SOCP (CSC structure on the host, values filled on the GPU for
+    any number of instances).  Keyword parameters as ciscvx_socp_params; the
+    scale/offset pairs are dicts {"x": (scale, offset), "u": ..., "s": ...,
+    "phi": ..., "gam": ...} (each entry optional)."""
+
+    def __init__(self, model: Model, N: int, layout: str = "node", *, w_px, w_ep, w_torque, s_min, s_max,
+                 torque_max, x_init, x_final, scaling=None):
+        lib = load()
+        self.model, self.N, self.layout = model, int(N), layout
+        sc = scaling or {}
+        nx = 6 * model.nb
+        keep = []
+
+        def vec(v, n, name):
+            a, p = _host_vec(v, n, name)
+            keep.append(a)
+            return p
+
+        def pair(key, n):
+            s_, o_ = sc.get(key, (None, None))
+            return vec(s_, n, f"scale_{key}"), vec(o_, n, f"offset_{key}")
+
+        sx, ox = pair("x", model.nxt)
+        su, ou = pair("u", model.nu)
+        sp, op = pair("phi", 2 * model.nc)
+        sg, og = pair("gam", model.nc)
+        ss, os_ = sc.get("s", (0.0, 0.0))
+        prm = _SocpParams(float(w_px), float(w_ep), float(w_torque), float(s_min), float(s_max),
+                          vec(torque_max, model.nj, "torque_max") if model.nj else None,
+                          vec(x_init, nx, "x_init"), vec(x_final, nx, "x_final"), sx, ox, su, ou,
+                          float(ss or 0.0), float(os_ or 0.0), sp, op, sg, og)
+        h = _vp()
+        _check(lib.ciscvx_socp_create(model.handle, self.N, LAYOUT[layout], ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h
+        d = _SocpDims()
+        _check(lib.ciscvx_socp_get_dims(h, ctypes.byref(d)))
+        self.dims = {f: getattr(d, f) for f, _ in d._fields_}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().ciscvx_socp_destroy(h)
+            self._h = None
+
+    def structure(self):
+        """Host CSC index arrays of A, G and P, and P's values (numpy)."""
+        d = self.dims
+        i32 = lambda n: np.zeros(max(int(n), 1), dtype=np.int32)  # noqa: E731
+        out = {"A_colptr": i32(d["n_var"] + 1), "A_rowind": i32(d["nnz_A"]),
+               "G_colptr": i32(d["n_var"] + 1), "G_rowind": i32(d["nnz_G"]),
+               "P_colptr": i32(d["n_var"] + 1), "P_rowind": i32(d["nnz_P"]),
+               "P_values": np.zeros(max(int(d["nnz_P"]), 1))}
+        ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))  # noqa: E731
+        _check(load().ciscvx_socp_structure(self._h, ip(out["A_colptr"]), ip(out["A_rowind"]),
+                                            ip(out["G_colptr"]), ip(out["G_rowind"]), ip(out["P_colptr"]),
+                                            ip(out["P_rowind"]), out["P_values"].ctypes.data_as(_dp)))
+        for k, n in (("A_rowind", d["nnz_A"]), ("G_rowind", d["nnz_G"]), ("P_rowind", d["nnz_P"]),
+                     ("P_values", d["nnz_P"])):
+            out[k] = out[k][:int(n)]
+        return out
+
+    def alloc_outputs(self, n_inst: int, device):
+        import torch
+        d = self.dims
+        f = lambda n: torch.empty((n_inst, int(n)), dtype=torch.float64, device=device)  # noqa: E731
+        return {"A_values": f(d["nnz_A"]), "b": f(d["n_eq"]), "G_values": f(d["nnz_G"]),
+                "h": f(d["n_ineq"]), "c": f(d["n_var"]), "rho_A": f(d["n_eq"]), "rho_G": f(d["n_ineq"])}
+
+    def fill(self, n_inst: int, inputs: dict, out: dict | None = None, precision: str = "fp64"):
+        """ciscvx_socp_fill: inputs maps Xp, Xm, U, s, Phi, Gam, A, Bm, Bp, S, defect, g, Gvm, Gth,
+        Gphi, Gpx, theta, dtheta, psi, dpsi to contiguous device tensors (instances concatenated)."""
+        import torch
+        if out is None:
+            out = self.alloc_outputs(n_inst, inputs["Xp"].device)
+        ptr = lambda k: _ptr(inputs.get(k))  # noqa: E731
+        for k, t in inputs.items():
+            if t is not None and not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                raise ValueError(f"{k} must be a contiguous CUDA tensor")
+        ins = _SocpInputs(*[ptr(k) for k in _SOCP_IN], PRECISION[precision], *[ptr(k) for k in _SOCP_IN2])
+        outs = _SocpOutputs(*[_ptr(out[k]) for k in _SOCP_OUT])
+        _check(load().ciscvx_socp_fill(self._h, int(n_inst), ctypes.byref(ins), ctypes.byref(outs), _stream()))
+        return out
 
 
 class BatchPlan:

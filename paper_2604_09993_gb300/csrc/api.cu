@@ -305,6 +305,11 @@ ciscvx_status cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
+// The compact pattern for the other translation units (SOCP canonicalization).
+void ciscvx::model_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int32_t* bc) {
+  fill_pattern(M, ar, ac, br, bc);
+}
+
 // Sets this thread's last-error message for entry points defined in other files.
 ciscvx_status ciscvx::set_error(ciscvx_status st, const char* fmt, ...) {
   char buf[512];

@@ -206,6 +206,9 @@ cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const dou
                         const NodeParams& P, double* g, double* Gvm, double* Gth, double* Gphi,
                         double* Gpx, double* theta, double* dtheta, unsigned* status,
                         cudaStream_t st);
+// Structural nonzeros of A and B-/B+ in compact order (api.cu); for models
+// without coupled links and without the Eq. (12) state.
+void model_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int32_t* bc);
 // Psi^{delta,eps} rows per interval, and its launcher (psi.cu).
 int psi_rows(const DevModel& M);
 cudaError_t launch_psi(const DevModel& M, int N, const double* Xp, const double* Xm, double delta,

@@ -1,0 +1,197 @@
+"""GPU parity of the SOCP canonicalization (ciscvx_socp_*) against the oracle's
+dense assembly of the same subproblem.
+
+The GPU path linearizes on the GPU (ciscvx_discretize at X = Xp,
+ciscvx_node_linearize, ciscvx_psi_linearize) and canonicalizes; the oracle
+linearizes with its dual numbers and assembles densely from the definition.
+A, b, G, h, P, c and the row scales are compared entry by entry
+(block-normwise relative 1e-10 for FP64 inputs), for both auxiliary models,
+both control layouts, the sinusoidal surface and the paper's dynamics, and
+for several instances filled in one call.  The CSC structure is checked to be
+well formed.
+"""
+import numpy as np
+import pytest
+
+from _util import TOL_FP64, TOL_FP32_PHI, block_err
+from paper_2604_09993_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+NSUB, DELTA, EPS = 4, 0.05, 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import oracle
+    from oracle import socp as osocp
+    from paper_2604_09993_gb300 import api, build
+    build.build()
+    oracle.build()
+    api.load()
+    return torch, oracle, osocp, api
+
+
+def _robot(name, variant):
+    rng = np.random.default_rng(17)
+    R = getattr(synth, name)(rng)
+    if variant == "cross":
+        R = synth.with_cross_states(R)
+    elif variant == "sine":
+        R = synth.with_paper_dynamics(R, joint_forces=0, scheme=0, terrain=synth.TERRAIN_SINE)
+    elif variant == "paper":
+        R = synth.with_cross_states(synth.with_paper_dynamics(R, terrain=synth.TERRAIN_SINE))
+    return R.as_dict()
+
+
+def _iterate(m, N, layout, rng):
+    nxt, nu, nb, nc = m.nxt, m.nu, m.nb, m.nc
+    Xp = np.zeros((N + 1, nxt))
+    Xp[:, : 6 * nb] = rng.uniform(-0.3, 0.3, (N + 1, 6 * nb))
+    Xp[:, 6 * nb:] = rng.uniform(-0.5, 0.5, (N + 1, nxt - 6 * nb))
+    Xm = Xp + 0.05 * rng.standard_normal(Xp.shape)
+    U = rng.standard_normal((N + 1, nu) if layout == "node" else (N, 2, nu))
+    s = rng.uniform(0.05, 0.15, N)
+    Phi = rng.standard_normal((N + 1, 2 * nc))
+    Gam = rng.uniform(0.1, 1.0, (N + 1, nc))
+    return Xp, Xm, U, s, Phi, Gam
+
+
+def _params(m, rng, scaled=True):
+    nb, nj, nc, nxt, nu = m.nb, m.nj, m.nc, m.nxt, m.nu
+    prm = {"w_px": 3.0, "w_ep": 50.0, "w_torque": 0.7, "s_min": 0.02, "s_max": 0.3,
+           "torque_max": rng.uniform(2, 4, nj), "x_init": rng.uniform(-0.2, 0.2, 6 * nb),
+           "x_final": rng.uniform(-0.2, 0.2, 6 * nb)}
+    if scaled:
+        prm.update(scale_x=rng.uniform(0.5, 2, nxt), offset_x=rng.uniform(-0.1, 0.1, nxt),
+                   scale_u=rng.uniform(0.5, 2, nu), offset_u=rng.uniform(-0.1, 0.1, nu),
+                   scale_s=0.1, offset_s=0.05, scale_phi=rng.uniform(0.5, 2, 2 * nc),
+                   offset_phi=rng.uniform(-0.1, 0.1, 2 * nc), scale_gam=rng.uniform(0.5, 2, nc),
+                   offset_gam=rng.uniform(-0.1, 0.1, nc))
+    return prm
+
+
+def _socp(api, m, N, layout, prm):
+    scaling = {k: (prm.get(f"scale_{k}"), prm.get(f"offset_{k}")) for k in ("x", "u", "phi", "gam")}
+    scaling["s"] = (prm.get("scale_s", 0.0), prm.get("offset_s", 0.0))
+    return api.Socp(m, N, layout, w_px=prm["w_px"], w_ep=prm["w_ep"], w_torque=prm["w_torque"],
+                    s_min=prm["s_min"], s_max=prm["s_max"], torque_max=prm["torque_max"],
+                    x_init=prm["x_init"], x_final=prm["x_final"], scaling=scaling)
+
+
+def _linearize(torch, api, m, layout, its, precision):
+    """GPU linearization of several iterates, concatenated per instance."""
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)  # noqa: E731
+    cat = {}
+    for Xp, Xm, U, s, Phi, Gam in its:
+        d = api.discretize(m, t(Xp), t(U), t(s), NSUB, precision, layout)
+        e = np.full(m.nc, 0.4)
+        nd = api.node_linearize(m, t(Xp), t(Xm), t(Phi.reshape(-1, 2 * m.nc)), t(Gam.reshape(-1, m.nc)), DELTA, e)
+        ps = api.psi_linearize(m, t(Xp), t(Xm), DELTA, EPS)
+        parts = {"Xp": t(Xp), "Xm": t(Xm), "U": t(U), "s": t(s), "Phi": t(Phi), "Gam": t(Gam),
+                 "A": d["A"], "Bm": d["Bm"], "Bp": d["Bp"], "S": d["S"], "defect": d["defect"],
+                 "g": nd["g"], "Gvm": nd["Gvm"], "Gth": nd["Gth"], "Gphi": nd["Gphi"], "Gpx": nd["Gpx"],
+                 "theta": nd["theta"], "dtheta": nd["dtheta"], "psi": ps["psi"], "dpsi": ps["dpsi"]}
+        for k, v in parts.items():
+            cat.setdefault(k, []).append(v.reshape(-1))
+    return {k: torch.cat(v).contiguous() for k, v in cat.items()}
+
+
+def _dense(colptr, rowind, vals, nrow, ncol):
+    M = np.zeros((nrow, ncol))
+    for c in range(ncol):
+        for e in range(colptr[c], colptr[c + 1]):
+            M[rowind[e], c] = vals[e]
+    return M
+
+
+def _check_structure(st, dims):
+    for key, nnz, nrow in (("A", dims["nnz_A"], dims["n_eq"]), ("G", dims["nnz_G"], dims["n_ineq"]),
+                           ("P", dims["nnz_P"], dims["n_var"])):
+        cp, ri = st[f"{key}_colptr"], st[f"{key}_rowind"]
+        assert cp[0] == 0 and cp[-1] == nnz and np.all(np.diff(cp) >= 0)
+        for c in range(dims["n_var"]):
+            rows = ri[cp[c]:cp[c + 1]]
+            assert np.all(np.diff(rows) > 0) and (len(rows) == 0 or (rows[0] >= 0 and rows[-1] < nrow))
+            if key == "P":
+                assert len(rows) == 0 or rows[-1] <= c
+
+
+CASES = [("hopper", "default", "node"), ("hopper", "cross", "interval"), ("biped", "default", "interval"),
+         ("biped", "cross", "node"), ("cheetah7", "default", "node"), ("hopper", "sine", "node"),
+         ("hopper", "paper", "interval")]
+
+
+@pytest.mark.parametrize("name,variant,layout", CASES)
+def test_socp_parity(env, name, variant, layout):
+    torch, oracle, osocp, api = env
+    R = _robot(name, variant)
+    m = api.Model(R)
+    rng = np.random.default_rng(5)
+    N, n_inst = 3, 2
+    prm = _params(m, rng)
+    its = [_iterate(m, N, layout, rng) for _ in range(n_inst)]
+    sp = _socp(api, m, N, layout, prm)
+    dims = sp.dims
+    st = sp.structure()
+    _check_structure(st, dims)
+    out = sp.fill(n_inst, _linearize(torch, api, m, layout, its, "fp64"))
+    api.sync_status(m)
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    for i, (Xp, Xm, U, s, Phi, Gam) in enumerate(its):
+        ref = osocp.assemble(R, N, layout, prm, Xp, Xm, U, s, Phi, Gam, NSUB, DELTA, EPS, np.full(m.nc, 0.4))
+        assert (dims["n_var"], dims["n_eq"], dims["n_ineq"]) == (len(ref["c"]), len(ref["b"]), len(ref["h"]))
+        assert (dims["n_nonneg"], dims["n_soc"]) == (ref["n_nonneg"], ref["n_soc"])
+        nv = dims["n_var"]
+        A = _dense(st["A_colptr"], st["A_rowind"], out["A_values"][i], dims["n_eq"], nv)
+        G = _dense(st["G_colptr"], st["G_rowind"], out["G_values"][i], dims["n_ineq"], nv)
+        P = _dense(st["P_colptr"], st["P_rowind"], st["P_values"], nv, nv)
+        P = P + np.triu(P, 1).T
+        for got, want in ((A, ref["A"]), (out["b"][i], ref["b"]), (G, ref["G"]), (out["h"][i], ref["h"]),
+                          (P, ref["P"]), (out["c"][i], ref["c"]), (out["rho_A"][i], ref["rho_A"]),
+                          (out["rho_G"][i], ref["rho_G"])):
+            assert block_err(got, want) <= TOL_FP64
+
+
+def test_socp_fp32_phi_inputs(env):
+    torch, oracle, osocp, api = env
+    R = _robot("cheetah7", "default")
+    m = api.Model(R)
+    rng = np.random.default_rng(6)
+    N = 4
+    prm = _params(m, rng, scaled=False)
+    it = _iterate(m, N, "node", rng)
+    sp = _socp(api, m, N, "node", prm)
+    st = sp.structure()
+    out = sp.fill(1, _linearize(torch, api, m, "node", [it], "fp32_phi"), precision="fp32_phi")
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = osocp.assemble(R, N, "node", prm, *it, NSUB, DELTA, EPS, np.full(m.nc, 0.4))
+    d = sp.dims
+    A = _dense(st["A_colptr"], st["A_rowind"], out["A_values"][0], d["n_eq"], d["n_var"])
+    assert block_err(A, ref["A"]) <= TOL_FP32_PHI
+    assert block_err(out["b"][0], ref["b"]) <= TOL_FP32_PHI
+    G = _dense(st["G_colptr"], st["G_rowind"], out["G_values"][0], d["n_ineq"], d["n_var"])
+    assert block_err(G, ref["G"]) <= TOL_FP64   # G takes no Phi block
+
+
+def test_socp_arguments(env):
+    torch, oracle, osocp, api = env
+    R = _robot("hopper", "default")
+    m = api.Model(R)
+    rng = np.random.default_rng(1)
+    prm = _params(m, rng)
+    lib = api.load()
+    for bad in ({"w_px": 0.0}, {"w_ep": -1.0}, {"s_min": 0.5, "s_max": 0.1},
+                {"torque_max": np.zeros(m.nj)}, {"x_init": np.full(6 * m.nb, np.nan)}):
+        with pytest.raises(Exception):
+            _socp(api, m, 3, "node", dict(prm, **bad))
+    with pytest.raises(Exception):
+        _socp(api, m, 0, "node", prm)
+    sp = _socp(api, m, 3, "node", prm)
+    ins = api._SocpInputs()
+    outs = api._SocpOutputs()
+    import ctypes
+    assert lib.ciscvx_socp_fill(sp._h, 1, ctypes.byref(ins), ctypes.byref(outs), None) == api.EINVAL
+    assert lib.ciscvx_socp_fill(sp._h, 0, ctypes.byref(ins), ctypes.byref(outs), None) == api.EINVAL
