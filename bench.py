@@ -283,6 +283,66 @@ class BatchWorkload:
             self.node_jobs.append((m, Xp, Xm, Phi, Gam, e, out))
         return sum(j[1].shape[0] for j in self.node_jobs)
 
+    # SOCP canonicalization (ciscvx_socp_fill) of every instance of the first
+    # model that shares its horizon, from the plan's dense linearization, the
+    # node constraints and Psi (all built untimed in setup)
+    def socp_setup(self, prec):
+        torch, b, api = self.torch, self.batch, self.api
+        m = self.models[0]
+        N = int(b.Ns[0])
+        inst = np.nonzero((b.model_idx == 0) & (b.Ns == N))[0]
+        p = self.plan(prec)
+        per = {"X": (N + 1) * m.nxt, "U": (N + 1) * m.nu, "s": N, "A": N * m.nxt * m.nxt,
+               "B": N * m.nxt * m.nu, "S": N * m.nxt, "defect": N * m.nxt}
+        n = len(inst)
+        if not np.array_equal(inst, np.arange(n)) or any(
+                p.offsets[i][k] != i * v for i in inst for k, v in per.items()):
+            return None  # the instances are not a plain concatenation in the plan
+        self.prepare(prec)
+        self.disc(prec)
+        out = self.out[(prec, "dense")]
+        gen = torch.Generator(device=self.dev)
+        gen.manual_seed(99)
+        nn = n * (N + 1)
+        Xp = self.X[: nn * m.nxt].view(nn, m.nxt)
+        Xm = (Xp + 0.05 * torch.randn(Xp.shape, generator=gen, device=self.dev, dtype=torch.float64)).contiguous()
+        Phi = torch.randn((nn, 2 * m.nc), generator=gen, device=self.dev, dtype=torch.float64)
+        Gam = torch.rand((nn, m.nc), generator=gen, device=self.dev, dtype=torch.float64)
+        nd = api.node_linearize(m, Xp, Xm, Phi, Gam, self.NODE_DELTA, np.full(m.nc, 0.3))
+        ps = api.psi_linearize(m, Xp, Xm, self.NODE_DELTA, 1e-4)
+        # Psi per instance: drop the rows that straddle two instances
+        pad = lambda t: torch.cat([t, t[:1]]).view(n, N + 1, *t.shape[1:])[:, :N].contiguous()  # noqa: E731
+        psi, dpsi = pad(ps["psi"]), pad(ps["dpsi"])
+        del ps
+        self.socp = api.Socp(m, N, "node", w_px=2000.0, w_ep=50000.0, w_torque=1.0, s_min=0.005,
+                             s_max=0.1, torque_max=np.full(m.nj, 50.0), x_init=np.zeros(6 * m.nb),
+                             x_final=np.zeros(6 * m.nb))
+        self.socp_in = {"Xp": Xp, "Xm": Xm, "U": self.U[: n * per["U"]], "s": self.s[: n * N], "Phi": Phi,
+                        "Gam": Gam, "A": out["A"], "Bm": out["Bm"], "Bp": out["Bp"], "S": out["S"],
+                        "defect": out["defect"], "g": nd["g"], "Gvm": nd["Gvm"], "Gth": nd["Gth"],
+                        "Gphi": nd["Gphi"], "Gpx": nd["Gpx"], "theta": nd["theta"], "dtheta": nd["dtheta"],
+                        "psi": psi, "dpsi": dpsi}
+        self.socp_n, self.socp_prec = n, prec
+        self.socp_out = self.socp.fill(n, self.socp_in, precision=prec)
+        d = self.socp.dims
+        # algorithmic bytes per instance: every output once, every input element the
+        # assembly references once (A and B-/B+ at their structural pattern)
+        el = 4 if prec == "fp32_phi" else 8
+        nq, nc, nxt = 3 * m.nb, m.nc, m.nxt
+        out_b = 8 * (d["nnz_A"] + d["nnz_G"] + 2 * d["n_eq"] + 2 * d["n_ineq"] + d["n_var"])
+        in_b = (el * N * (m.nnz_a + 2 * m.nnz_b + nxt) + 8 * N * nxt
+                + 8 * (N + 1) * (2 * nxt + m.nu + 3 * nc + nxt + nq * nq + nq * m.nb + nq * 2 * nc
+                                 + 8 * nc + 8 * nc * 10)
+                + 8 * N * (psi.shape[-1] * 3))
+        return {"instances": n, "N": N, "dims": d, "bytes_per_instance": out_b + in_b}
+
+    def socp_step(self):
+        self.socp.fill(self.socp_n, self.socp_in, out=self.socp_out, precision=self.socp_prec)
+
+    def socp_free(self):
+        self.socp = self.socp_in = self.socp_out = None
+        self.torch.cuda.empty_cache()
+
     def node_step(self):
         for m, Xp, Xm, Phi, Gam, e, out in self.node_jobs:
             self.api.node_linearize(m, Xp, Xm, Phi, Gam, self.NODE_DELTA, e, out=out)
@@ -654,6 +714,28 @@ def run_ours(args):
         del Xp, Xm, po, mp
         torch.cuda.empty_cache()
 
+    # the SOCP canonicalization of the batch's instances (one shape)
+    socp = None
+    if spec["kind"] == "batch" and not args.no_socp:
+        wl.free(prec)
+        info = wl.socp_setup(prec)
+        if info is not None:
+            barrier()
+            tq = time_steps(torch, wl.socp_step, args.steps, args.warmup, stream)
+            barrier()
+            wl.check_status()
+            tq, = max_over_ranks([tq])
+            n_iv = info["instances"] * info["N"]
+            gbs = info["bytes_per_instance"] * info["instances"] * args.steps / tq / 1e9
+            socp = {"metric": "canonicalized intervals/s (SCP subproblem as a CSC SOCP, FP64 values)",
+                    "value": n_iv * world * args.steps / tq, "unit": "intervals/s",
+                    "instances_per_gpu": info["instances"], "N": info["N"],
+                    "ms_per_call": tq / args.steps * 1e3, "dims": info["dims"],
+                    "bytes_per_instance": info["bytes_per_instance"], "achieved_gbs": gbs,
+                    "hbm_frac_of_measured": gbs / HBM_GBS if HBM_GBS else None, "phi_inputs": prec}
+        wl.socp_free()
+        wl.free(prec)
+
     # the linearization of the same batch with the full Eq. (12) auxiliary state
     # (four cross-complementarity states + one path-penalty state per contact)
     cross = None
@@ -738,6 +820,7 @@ def run_ours(args):
         "compact_outputs": compact,
         "node_constraints": nodes,
         "psi": psi,
+        "socp": socp,
         "aux_cross_model": cross,
         "paper_dynamics": paper,
         "clocks": clocks,
@@ -779,6 +862,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compact", action="store_true", help="skip the compact-output measurement")
     ap.add_argument("--no-nodes", action="store_true", help="skip the node-constraint measurement")
+    ap.add_argument("--no-socp", action="store_true", help="skip the SOCP canonicalization measurement")
     ap.add_argument("--no-paper", action="store_true",
                     help="skip the paper-dynamics (coupled links) measurement")
     ap.add_argument("--paper-only", action="store_true",

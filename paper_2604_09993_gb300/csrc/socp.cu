@@ -11,8 +11,9 @@
 // sorted into CSC order (for the value pass), and precomputes everything that
 // does not depend on the iterate: the column scales and offsets, P and P o.
 // The numeric phase (device, per call, any number of instances of that shape):
-//   rows:   thread per (instance, row): the row's scaled max-norm over the
-//           problem columns -> rho, and b (or h) = rho (J zbar - residual - J o)
+//   rows:   block per (instance, chunk of whole rows): entry terms into shared
+//           memory, then per row its scaled max-norm over the problem columns
+//           -> rho, and b (or h) = rho (J zbar - residual - J o)
 //   values: thread per (instance, CSC entry): source * D[col] * rho[row]
 //   c:      thread per (instance, column): D (P o - w_px zbar), or w_ep
 // The descriptors are shared by all instances and stay in L2; every output is
@@ -30,46 +31,64 @@ using namespace ciscvx;
 namespace {
 
 // ---------------------------------------------------------------- sources ---
-// bits 58..63 kind, bit 57 negate, bits 32..56 interval/node index, 0..31 offset
+// A 64-bit descriptor: bits 60..63 the array (kind), bit 59 negate, bits
+// 0..58 the element offset within one instance's part of that array (or the
+// index of a constant).  Three kind spaces: entry sources (SRC_*), column
+// iterates (Z_*), row residuals (R_*).
 enum : unsigned {
-  SRC_CONST = 1, SRC_A, SRC_BM, SRC_BP, SRC_S, SRC_GVM, SRC_GTH, SRC_GPHI, SRC_GPX, SRC_DTH, SRC_DPSI
+  SRC_CONST = 0, SRC_A, SRC_BM, SRC_BP, SRC_S, SRC_GVM, SRC_GTH, SRC_GPHI, SRC_GPX, SRC_DTH, SRC_DPSI, SRC_N
 };
-// column iterate sources (kind bits as above, offset = component)
-enum : unsigned { Z_SLACK = 0, Z_XP, Z_XM, Z_PHI, Z_GAM, Z_U, Z_UL, Z_UR, Z_S };
-// row residual sources
-enum : unsigned { R_CONST = 1, R_G, R_DYN, R_TH, R_PSI };
+enum : unsigned { Z_SLACK = 0, Z_XP, Z_XM, Z_PHI, Z_GAM, Z_U, Z_S, Z_N };
+enum : unsigned { R_CONST = 0, R_G, R_DYN, R_TH, R_PSI };
 
 constexpr int SOCP_MAXK = (1 << 25) - 1;
+constexpr uint64_t OFF_MASK = (1ull << 59) - 1;
 
-inline uint64_t desc(unsigned kind, long k, unsigned off, bool neg = false) {
-  return ((uint64_t)kind << 58) | ((uint64_t)(neg ? 1 : 0) << 57) | ((uint64_t)k << 32) | off;
+inline uint64_t enc(unsigned kind, uint64_t off, bool neg = false) {
+  return ((uint64_t)kind << 60) | ((uint64_t)(neg ? 1 : 0) << 59) | (off & OFF_MASK);
 }
-__host__ __device__ inline unsigned d_kind(uint64_t d) { return (unsigned)(d >> 58); }
-__host__ __device__ inline bool d_neg(uint64_t d) { return (d >> 57) & 1u; }
-__host__ __device__ inline long d_k(uint64_t d) { return (long)((d >> 32) & 0x1FFFFFFull); }
-__host__ __device__ inline unsigned d_off(uint64_t d) { return (unsigned)(d & 0xFFFFFFFFull); }
+__host__ __device__ inline unsigned d_kind(uint64_t d) { return (unsigned)(d >> 60); }
+__host__ __device__ inline bool d_neg(uint64_t d) { return (d >> 59) & 1u; }
+__host__ __device__ inline long long d_off(uint64_t d) { return (long long)(d & OFF_MASK); }
 
 // Device copy of one matrix's tables.
 struct MatDev {
   int nrow;
   long long nnz;
-  const int* rowptr;         // [nrow + 1] row view
-  const int* rcol;           // [nnz] column of each row-view entry
-  const uint64_t* rsrc;      // [nnz] source of each row-view entry
-  const uint64_t* res;       // [nrow] residual source (R_*)
+  // the rows that depend on the iterate (linearized constraints), problem-
+  // variable entries only, in SELL-32 order: groups of 32 rows (one warp),
+  // entry j of the group's row `lane` at gptr[group] + 32 j + lane, padded to
+  // the group's longest row with zero entries; rows sorted by length within
+  // windows of SELL_WINDOW rows so that a group's rows are of similar length
+  int n_lin;                 // such rows (padded to a multiple of 32)
+  const int* lrow;           // [n_lin] their row indices (-1: padding)
+  const long long* gptr;     // [n_lin / 32 + 1] first slot of each group
+  const uint64_t* lsrc;      // source of each slot
+  const int* lcol;           // its column
+  const double* lD;          // its column scale (0 in padding)
+  const uint64_t* lres;      // [n_lin] residual source (R_*) of each row
+  // rows of constants only: rho and rho (h - G o) do not depend on the iterate
+  int n_fix;
+  const int* frow;           // [n_fix]
+  const double* frho;        // [n_fix]
+  const double* frhs;        // [n_fix]
   const int* crow;           // [nnz] row of each CSC entry
-  const int* ccol;           // [nnz] column of each CSC entry
   const uint64_t* csrc;      // [nnz] source of each CSC entry
+  const double* cscale;      // [nnz] D[col] (constants: the signed value times D[col])
   int soc0;                  // first row of the Q^2 blocks (rows pair up from here), or nrow
 };
 
-// Per-call pointers and per-instance strides (elements).
+
+// Per-call pointers and per-instance strides (elements), indexed by kind.
 struct SocpIO {
-  int N, nxt, nu, nb, nc, npsi, ny, nq, n_var, node_layout, phi64;
-  long long sX, sU, sS, sPhi, sGam, sA, sB, sSv, sDef, sG, sGvm, sGth, sGphi, sGpx, sTh, sDth, sPsi, sDpsi;
-  const double *Xp, *Xm, *U, *s, *Phi, *Gam, *defect, *g, *Gvm, *Gth, *Gphi, *Gpx, *theta, *dtheta,
-      *psi, *dpsi;
-  const void *A, *Bm, *Bp, *S;
+  const void* sp[SRC_N];     // entry-source arrays
+  long long ss[SRC_N];       // their per-instance strides
+  unsigned f32;              // bit k: array k holds FP32
+  const double* zp[Z_N];     // iterate arrays
+  long long zs[Z_N];
+  const double *g, *defect, *Xp, *Xm, *theta, *psi;
+  long long sG, sDef, sX, sTh, sPsi;
+  int nxt, n_var;
   const double* consts;
   const uint64_t* colz;  // [n_var] iterate source of each column
   const double* D;       // [n_var]
@@ -78,116 +97,175 @@ struct SocpIO {
   double w_px, w_ep;
 };
 
-__device__ __forceinline__ double phi_at(const SocpIO& I, const void* p, long long idx) {
-  return I.phi64 ? ((const double*)p)[idx] : (double)((const float*)p)[idx];
+// The per-kind pointer tables, copied to shared memory by each block: lanes
+// of one warp index them with different kinds, which the kernel-parameter
+// (constant) bank would serve one address at a time.
+struct KindTab {
+  const void* sp[SRC_N];
+  long long ss[SRC_N];
+  const double* zp[Z_N];
+  long long zs[Z_N];
+  unsigned f32;
+};
+
+__device__ __forceinline__ void load_tab(const SocpIO& I, KindTab& K) {
+  const int t = threadIdx.x;
+  if (t < SRC_N) {
+    K.sp[t] = I.sp[t];
+    K.ss[t] = I.ss[t];
+  }
+  if (t < Z_N) {
+    K.zp[t] = I.zp[t];
+    K.zs[t] = I.zs[t];
+  }
+  if (t == 0) K.f32 = I.f32;
+  __syncthreads();
 }
 
-__device__ double fetch(const SocpIO& I, long inst, uint64_t d) {
-  const unsigned kind = d_kind(d), off = d_off(d);
-  const long k = d_k(d);
+__device__ __forceinline__ double fetch(const SocpIO& I, const KindTab& K, long inst, uint64_t d) {
+  const unsigned kind = d_kind(d);
+  const long long off = d_off(d);
   double v;
-  switch (kind) {
-    case SRC_CONST: v = I.consts[off]; break;
-    case SRC_A: v = phi_at(I, I.A, inst * I.sA + k * (long long)I.nxt * I.nxt + off); break;
-    case SRC_BM: v = phi_at(I, I.Bm, inst * I.sB + k * (long long)I.nxt * I.nu + off); break;
-    case SRC_BP: v = phi_at(I, I.Bp, inst * I.sB + k * (long long)I.nxt * I.nu + off); break;
-    case SRC_S: v = phi_at(I, I.S, inst * I.sSv + k * (long long)I.nxt + off); break;
-    case SRC_GVM: v = I.Gvm[inst * I.sGvm + k * (long long)I.nq * I.nq + off]; break;
-    case SRC_GTH: v = I.Gth[inst * I.sGth + k * (long long)I.nq * I.nb + off]; break;
-    case SRC_GPHI: v = I.Gphi[inst * I.sGphi + k * (long long)I.nq * 2 * I.nc + off]; break;
-    case SRC_GPX: v = I.Gpx[inst * I.sGpx + k * (long long)I.nq * I.nc + off]; break;
-    case SRC_DTH: v = I.dtheta[inst * I.sDth + k * (long long)I.nc * 8 * CISCVX_NODE_THETA_COLS + off]; break;
-    case SRC_DPSI: v = I.dpsi[inst * I.sDpsi + k * (long long)I.npsi * I.ny + off]; break;
-    default: v = 0.0;
+  if (kind == SRC_CONST) {
+    v = I.consts[off];
+  } else {
+    const long long idx = inst * K.ss[kind] + off;
+    v = ((K.f32 >> kind) & 1u) ? (double)((const float*)K.sp[kind])[idx] : ((const double*)K.sp[kind])[idx];
   }
   return d_neg(d) ? -v : v;
 }
 
-__device__ double zbar_at(const SocpIO& I, long inst, uint64_t d) {
-  const unsigned off = d_off(d);
-  const long k = d_k(d);
-  switch (d_kind(d)) {
-    case Z_XP: return I.Xp[inst * I.sX + k * I.nxt + off];
-    case Z_XM: return I.Xm[inst * I.sX + k * I.nxt + off];
-    case Z_PHI: return I.Phi[inst * I.sPhi + k * 2 * I.nc + off];
-    case Z_GAM: return I.Gam[inst * I.sGam + k * I.nc + off];
-    case Z_U: return I.U[inst * I.sU + k * I.nu + off];
-    case Z_UL: return I.U[inst * I.sU + (2 * k) * I.nu + off];
-    case Z_UR: return I.U[inst * I.sU + (2 * k + 1) * I.nu + off];
-    case Z_S: return I.s[inst * I.sS + k];
-    default: return 0.0;
-  }
+__device__ __forceinline__ double zbar_at(const KindTab& K, long inst, uint64_t d) {
+  return K.zp[d_kind(d)][inst * K.zs[d_kind(d)] + d_off(d)];
 }
 
 __device__ double residual_at(const SocpIO& I, long inst, uint64_t d) {
-  const unsigned off = d_off(d);
-  const long k = d_k(d);
+  const long long off = d_off(d);
   switch (d_kind(d)) {
-    case R_G: return I.g[inst * I.sG + k * I.nxt + off];
-    case R_DYN:  // F~(x~+_k, U_k, s_k) - x~-_{k+1}, with F~ = defect + x~+_{k+1}
-      return I.defect[inst * I.sDef + k * I.nxt + off] + I.Xp[inst * I.sX + (k + 1) * I.nxt + off] -
-             I.Xm[inst * I.sX + (k + 1) * I.nxt + off];
-    case R_TH: return I.theta[inst * I.sTh + k * 8 * I.nc + off];
-    case R_PSI: return I.psi[inst * I.sPsi + k * I.npsi + off];
-    default: return 0.0;
+    case R_G: return I.g[inst * I.sG + off];
+    case R_DYN:  // F~(x~+_k, U_k, s_k) - x~-_{k+1}, with F~ = defect + x~+_{k+1}; off = k n_x~ + r
+      return I.defect[inst * I.sDef + off] + I.Xp[inst * I.sX + off + I.nxt] - I.Xm[inst * I.sX + off + I.nxt];
+    case R_TH: return I.theta[inst * I.sTh + off];
+    case R_PSI: return I.psi[inst * I.sPsi + off];
+    default: return I.consts[off];
   }
 }
 
-// Scaled max-norm of row r over the problem columns.
-__device__ double row_norm(const SocpIO& I, const MatDev& T, long inst, int r) {
-  double nrm = 0.0;
-  for (int e = T.rowptr[r]; e < T.rowptr[r + 1]; ++e) {
-    const int c = T.rcol[e];
-    if (d_kind(I.colz[c]) == Z_SLACK) continue;
-    nrm = fmax(nrm, fabs(fetch(I, inst, T.rsrc[e]) * I.D[c]));
-  }
-  return nrm;
+constexpr int SELL_WINDOW = 256;
+constexpr int IPB = 4;  // instances per thread: the tables are read once for all of
+                        // them, and each thread has IPB independent gathers in flight
+
+// Scaled iterate zhat = (zbar - o) / D per (instance, column), 0 on slacks,
+// written into the caller's c (the column pass overwrites it at the end).
+__global__ void __launch_bounds__(256) k_socp_zhat(const __grid_constant__ SocpIO I, int n_inst, double* zhat) {
+  __shared__ KindTab K;
+  load_tab(I, K);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= I.n_var) return;
+  const uint64_t zc = I.colz[j];
+  const double idj = 1.0 / I.D[j], oj = I.o[j];
+  for (long base = (long)blockIdx.y * IPB; base < n_inst; base += (long)gridDim.y * IPB)
+#pragma unroll
+    for (int i = 0; i < IPB; ++i)
+      if (base + i < n_inst)
+        zhat[(base + i) * I.n_var + j] = d_kind(zc) == Z_SLACK ? 0.0 : (zbar_at(K, base + i, zc) - oj) * idj;
 }
 
-__global__ void __launch_bounds__(256) k_socp_rows(SocpIO I, MatDev T, int n_inst, double* rho_out,
-                                                    double* rhs_out) {
-  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long)n_inst * T.nrow) return;
-  const long inst = g / T.nrow;
-  const int r = (int)(g - inst * T.nrow);
-  double nrm = 0.0, jz = 0.0, jo = 0.0;
-  for (int e = T.rowptr[r]; e < T.rowptr[r + 1]; ++e) {
-    const int c = T.rcol[e];
-    const uint64_t zc = I.colz[c];
-    const double v = fetch(I, inst, T.rsrc[e]);
-    if (d_kind(zc) != Z_SLACK) {
-      nrm = fmax(nrm, fabs(v * I.D[c]));
-      jz = fma(v, zbar_at(I, inst, zc), jz);
-      jo = fma(v, I.o[c], jo);
+// Row pass over the linearized rows: thread per (row, IPB instances).  With
+// m = value x D: rho = 1 / max |m| (the max taken on the bit patterns of
+// the magnitudes, which order like the values), and
+// rhs = rho (sum m zhat - residual) = rho (J zbar - residual - J o).
+__global__ void __launch_bounds__(256) k_socp_rows(const __grid_constant__ SocpIO I, MatDev T, int n_inst,
+                                                   const double* zhat, double* rho_out, double* rhs_out) {
+  __shared__ KindTab K;
+  load_tab(I, K);
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= T.n_lin) return;
+  const int r = T.lrow[w];
+  const long long g0 = T.gptr[w >> 5], g1 = T.gptr[(w >> 5) + 1];
+  const uint64_t rd = T.lres[w];
+  for (long base = (long)blockIdx.y * IPB; base < n_inst; base += (long)gridDim.y * IPB) {
+    unsigned long long mx[IPB];
+    double acc[IPB];
+#pragma unroll
+    for (int i = 0; i < IPB; ++i) {
+      mx[i] = 0ull;
+      acc[i] = 0.0;
+    }
+    for (long long e = g0 + (w & 31); e < g1; e += 32) {
+      const uint64_t d = T.lsrc[e];
+      const int c = T.lcol[e];
+      const double dc = T.lD[e];
+#pragma unroll
+      for (int i = 0; i < IPB; ++i) {
+        if (base + i >= n_inst) break;
+        const double m = fetch(I, K, base + i, d) * dc;
+        mx[i] = ullmax(mx[i], (unsigned long long)__double_as_longlong(m) & 0x7FFFFFFFFFFFFFFFull);
+        acc[i] = fma(m, zhat[(base + i) * I.n_var + c], acc[i]);
+      }
+    }
+    if (r < 0) continue;  // padding row
+#pragma unroll
+    for (int i = 0; i < IPB; ++i) {
+      if (base + i >= n_inst) break;
+      const long inst = base + i;
+      const double nrm = __longlong_as_double((long long)mx[i]);
+      const double rho = nrm > 0.0 ? 1.0 / nrm : 1.0;
+      rho_out[inst * T.nrow + r] = rho;
+      rhs_out[inst * T.nrow + r] = rho * (acc[i] - residual_at(I, inst, rd));
     }
   }
-  if (r >= T.soc0) {  // a Q^2 block takes the larger norm of its two rows
-    const int partner = T.soc0 + ((r - T.soc0) ^ 1);
-    nrm = fmax(nrm, row_norm(I, T, inst, partner));
+}
+
+// Rows of constants: their precomputed rho and right-hand side, per instance.
+__global__ void __launch_bounds__(256) k_socp_fixed(MatDev T, int n_inst, double* rho_out, double* rhs_out) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= T.n_fix) return;
+  const int r = T.frow[w];
+  const double rho = T.frho[w], rhs = T.frhs[w];
+  for (long inst = blockIdx.y; inst < n_inst; inst += gridDim.y) {
+    rho_out[inst * T.nrow + r] = rho;
+    rhs_out[inst * T.nrow + r] = rhs;
   }
-  const uint64_t rd = T.res[r];
-  const double rhs = (d_kind(rd) == R_CONST ? I.consts[d_off(rd)] : jz - residual_at(I, inst, rd)) - jo;
-  const double rho = nrm > 0.0 ? 1.0 / nrm : 1.0;
-  rho_out[inst * T.nrow + r] = rho;
-  rhs_out[inst * T.nrow + r] = rho * rhs;
 }
 
-__global__ void __launch_bounds__(256) k_socp_values(SocpIO I, MatDev T, int n_inst, const double* rho,
-                                                      double* val) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)n_inst * T.nnz) return;
-  const long inst = (long)(g / T.nnz);
-  const long long e = g - (long long)inst * T.nnz;
-  val[g] = fetch(I, inst, T.csrc[e]) * I.D[T.ccol[e]] * rho[inst * T.nrow + T.crow[e]];
+// Value pass: thread per (CSC entry, IPB instances).
+__global__ void __launch_bounds__(256) k_socp_values(const __grid_constant__ SocpIO I, MatDev T, int n_inst,
+                                                      const double* rho, double* val) {
+  __shared__ KindTab K;
+  load_tab(I, K);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= T.nnz) return;
+  const uint64_t d = T.csrc[e];
+  const double sc = T.cscale[e];
+  const int row = T.crow[e];
+  const bool cst = d_kind(d) == SRC_CONST;
+  for (long base = (long)blockIdx.y * IPB; base < n_inst; base += (long)gridDim.y * IPB) {
+    double v[IPB];
+#pragma unroll
+    for (int i = 0; i < IPB; ++i) {
+      v[i] = 0.0;
+      if (base + i < n_inst) v[i] = (cst ? sc : fetch(I, K, base + i, d) * sc) * rho[(base + i) * T.nrow + row];
+    }
+#pragma unroll
+    for (int i = 0; i < IPB; ++i)
+      if (base + i < n_inst) val[(base + i) * T.nnz + e] = v[i];
+  }
 }
 
-__global__ void __launch_bounds__(256) k_socp_c(SocpIO I, int n_inst, double* c) {
-  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long)n_inst * I.n_var) return;
-  const long inst = g / I.n_var;
-  const int j = (int)(g - inst * I.n_var);
+// Column pass: c, thread per (column, IPB instances).
+__global__ void __launch_bounds__(256) k_socp_c(const __grid_constant__ SocpIO I, int n_inst, double* c) {
+  __shared__ KindTab K;
+  load_tab(I, K);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= I.n_var) return;
   const uint64_t zc = I.colz[j];
-  c[g] = d_kind(zc) == Z_SLACK ? I.w_ep : I.D[j] * (I.Po[j] - I.w_px * zbar_at(I, inst, zc));
+  const double dj = I.D[j], poj = I.Po[j];
+  for (long base = (long)blockIdx.y * IPB; base < n_inst; base += (long)gridDim.y * IPB)
+#pragma unroll
+    for (int i = 0; i < IPB; ++i)
+      if (base + i < n_inst)
+        c[(base + i) * I.n_var + j] = d_kind(zc) == Z_SLACK ? I.w_ep : dj * (poj - I.w_px * zbar_at(K, base + i, zc));
 }
 
 // ---------------------------------------------------------- host builder ---
@@ -245,9 +323,46 @@ struct Builder {
     const_idx[v] = i;
     return i;
   }
-  uint64_t one(bool neg = false) { return desc(SRC_CONST, 0, cst(1.0), neg); }
-  uint64_t value(double v) { return desc(SRC_CONST, 0, cst(v)); }
-  uint64_t rconst(double v) { return desc(R_CONST, 0, cst(v)); }
+  uint64_t one(bool neg = false) { return enc(SRC_CONST, cst(1.0), neg); }
+  uint64_t value(double v) { return enc(SRC_CONST, cst(v)); }
+  uint64_t rconst(double v) { return enc(R_CONST, cst(v)); }
+
+  // entry source: element (k, off) of an output block, as a per-instance offset
+  uint64_t desc(unsigned kind, long k, unsigned off, bool neg = false) const {
+    long long blk = 0;
+    switch (kind) {
+      case SRC_A: blk = (long long)nxt * nxt; break;
+      case SRC_BM: case SRC_BP: blk = (long long)nxt * nu; break;
+      case SRC_S: blk = nxt; break;
+      case SRC_GVM: blk = (long long)nq * nq; break;
+      case SRC_GTH: blk = (long long)nq * nb; break;
+      case SRC_GPHI: blk = (long long)nq * 2 * nc; break;
+      case SRC_GPX: blk = (long long)nq * nc; break;
+      case SRC_DTH: blk = (long long)nc * 8 * CISCVX_NODE_THETA_COLS; break;
+      case SRC_DPSI: blk = (long long)npsi * ny; break;
+    }
+    return enc(kind, (uint64_t)(k * blk + off), neg);
+  }
+  // row residual: element (k, off) of g, defect, theta or psi
+  uint64_t rdesc(unsigned kind, long k, unsigned off) const {
+    const long long blk = kind == R_TH ? 8LL * nc : kind == R_PSI ? (long long)npsi : (long long)nxt;
+    return enc(kind, (uint64_t)(k * blk + off));
+  }
+  // column iterate: component i of node / interval k (ZB_UL, ZB_UR: the
+  // per-interval control layout's u_L, u_R)
+  enum : unsigned { ZB_UL = 100, ZB_UR = 101 };
+  uint64_t zdesc(unsigned zk, long k, int i) const {
+    switch (zk) {
+      case Z_XP: case Z_XM: return enc(zk, (uint64_t)(k * nxt + i));
+      case Z_PHI: return enc(zk, (uint64_t)(k * 2 * nc + i));
+      case Z_GAM: return enc(zk, (uint64_t)(k * nc + i));
+      case Z_U: return enc(Z_U, (uint64_t)(k * nu + i));
+      case ZB_UL: return enc(Z_U, (uint64_t)(2 * k * nu + i));
+      case ZB_UR: return enc(Z_U, (uint64_t)((2 * k + 1) * nu + i));
+      case Z_S: return enc(Z_S, (uint64_t)k);
+    }
+    return 0;
+  }
 
   // columns: n of them, iterate source kind zk at index k (components 0..n-1),
   // scale/offset vectors sc/of of length n (null = identity) or slack
@@ -255,7 +370,7 @@ struct Builder {
     const int c0 = (int)colz.size();
     v.push_back(c0);
     for (int i = 0; i < n; ++i) {
-      colz.push_back(zk == Z_SLACK ? 0 : desc(zk, k, (unsigned)i));
+      colz.push_back(zk == Z_SLACK ? 0 : zdesc(zk, k, i));
       D.push_back(zk != Z_SLACK && sc ? sc[i] : 1.0);
       o.push_back(zk != Z_SLACK && of ? of[i] : 0.0);
     }
@@ -275,8 +390,8 @@ struct Builder {
       take(c_tth, 8 * nc, Z_SLACK, 0, nullptr, nullptr);
       if (k < N) {
         if (!node) {
-          take(c_uL, nu, Z_UL, k, P.scale_u, P.offset_u);
-          take(c_uR, nu, Z_UR, k, P.scale_u, P.offset_u);
+          take(c_uL, nu, ZB_UL, k, P.scale_u, P.offset_u);
+          take(c_uR, nu, ZB_UR, k, P.scale_u, P.offset_u);
         }
         take(c_s, 1, Z_S, k, ss, os);
         take(c_nuFp, nxt, Z_SLACK, 0, nullptr, nullptr);
@@ -309,10 +424,11 @@ struct Builder {
   }
 
   void rows(const ciscvx_socp_params& P) {
+    cst(0.0);  // the padding entries of the SELL layout point at it
     for (int k = 0; k <= N; ++k) {
       // G~ rows of node k
       for (int r = 0; r < nxt; ++r) {
-        const int row = A.begin_row(desc(R_G, k, (unsigned)r));
+        const int row = A.begin_row(rdesc(R_G, k, (unsigned)r));
         if (r < nq) {
           A.add(row, c_xm[k] + r, one(true));
           A.add(row, c_xp[k] + r, one());
@@ -336,7 +452,7 @@ struct Builder {
       // dynamics rows of interval k
       if (k < N) {
         for (int r = 0; r < nxt; ++r) {
-          const int row = A.begin_row(desc(R_DYN, k, (unsigned)r));
+          const int row = A.begin_row(rdesc(R_DYN, k, (unsigned)r));
           if (has_pattern) {
             for (size_t e = 0; e < par.size(); ++e)
               if (par[e] == r) A.add(row, c_xp[k] + pac[e], desc(SRC_A, k, (unsigned)(r * nxt + pac[e])));
@@ -369,7 +485,7 @@ struct Builder {
             c_xm[k] + nq + 3 * b, c_xm[k] + nq + 3 * b + 1, c_xm[k] + nq + 3 * b + 2,
             c_phi[k] + 2 * i, c_phi[k] + 2 * i + 1, c_gam[k] + i};
         for (int j = 0; j < 8; ++j) {
-          const int row = G.begin_row(desc(R_TH, k, (unsigned)(8 * i + j)));
+          const int row = G.begin_row(rdesc(R_TH, k, (unsigned)(8 * i + j)));
           for (int v = 0; v < CISCVX_NODE_THETA_COLS; ++v) {
             if (!terrain && (v == 0 || v == 6)) continue;  // zero on flat ground
             G.add(row, cols[v], desc(SRC_DTH, k, (unsigned)((8 * i + j) * CISCVX_NODE_THETA_COLS + v)));
@@ -383,7 +499,7 @@ struct Builder {
       if (node) input_rows(c_u[k], P);
       if (k < N) {
         for (int r = 0; r < npsi; ++r) {
-          const int row = G.begin_row(desc(R_PSI, k, (unsigned)r));
+          const int row = G.begin_row(rdesc(R_PSI, k, (unsigned)r));
           int ja, jb = -1;
           if (aux && r < 2 * nc) {
             ja = 4 * (r >> 1) + 2 * (r & 1);
@@ -461,17 +577,83 @@ namespace {
 
 // Sorts a matrix's entries into CSC order and fills its host index arrays and
 // device tables.
-bool finish(const HostMat& H, int n_var, std::vector<int>& colptr, std::vector<int>& rowind,
+bool finish(const HostMat& H, const Builder& B, std::vector<int>& colptr, std::vector<int>& rowind,
             MatDev& T, ciscvx_socp* so, int soc0, cudaError_t& e) {
+  const int n_var = (int)B.colz.size();
   const long long nnz = (long long)H.e.size();
-  std::vector<int> rowptr(H.nrow + 1, 0), rcol(nnz), crow(nnz), ccol(nnz);
-  std::vector<uint64_t> rsrc(nnz), csrc(nnz);
-  for (long long i = 0; i < nnz; ++i) {
-    ++rowptr[H.e[i].row + 1];
-    rcol[i] = H.e[i].col;
-    rsrc[i] = H.e[i].src;
-  }
+  std::vector<int> rowptr(H.nrow + 1, 0), crow(nnz);
+  std::vector<uint64_t> csrc(nnz);
+  std::vector<double> cscale(nnz);
+  for (long long i = 0; i < nnz; ++i) ++rowptr[H.e[i].row + 1];
   for (int r = 0; r < H.nrow; ++r) rowptr[r + 1] += rowptr[r];
+  auto is_problem = [&](int col) { return d_kind(B.colz[col]) != Z_SLACK; };
+  auto cval = [&](uint64_t d) { return (d_neg(d) ? -1.0 : 1.0) * B.consts[d_off(d)]; };
+  // rows that depend on the iterate, and rows of constants (rho and h precomputed)
+  std::vector<int> lin, lrow, lcol, frow;
+  std::vector<long long> gptr{0};
+  std::vector<uint64_t> lsrc, lres;
+  std::vector<double> lD, frho, frhs, fnrm(H.nrow, 0.0);
+  auto nprob = [&](int r) {
+    int n = 0;
+    for (int i = rowptr[r]; i < rowptr[r + 1]; ++i) n += is_problem(H.e[i].col);
+    return n;
+  };
+  for (int r = 0; r < H.nrow; ++r) {
+    if (d_kind(H.res[r]) != R_CONST) {
+      lin.push_back(r);
+    } else {
+      for (int i = rowptr[r]; i < rowptr[r + 1]; ++i) {
+        const Entry& x = H.e[i];
+        if (d_kind(x.src) != SRC_CONST) return false;  // constant rows hold constants only
+        if (is_problem(x.col)) fnrm[r] = std::max(fnrm[r], std::fabs(cval(x.src) * B.D[x.col]));
+      }
+    }
+  }
+  // SELL-32 layout of the linearized rows
+  for (size_t w0 = 0; w0 < lin.size(); w0 += SELL_WINDOW) {
+    const size_t w1 = std::min(lin.size(), w0 + SELL_WINDOW);
+    std::stable_sort(lin.begin() + w0, lin.begin() + w1, [&](int a, int b) { return nprob(a) > nprob(b); });
+  }
+  while (lin.size() % 32) lin.push_back(-1);
+  const uint64_t zero = enc(SRC_CONST, (uint64_t)std::distance(
+      B.consts.begin(), std::find(B.consts.begin(), B.consts.end(), 0.0)));
+  for (size_t g = 0; g < lin.size(); g += 32) {
+    int width = 0;
+    for (int l = 0; l < 32; ++l) width = std::max(width, lin[g + l] < 0 ? 0 : nprob(lin[g + l]));
+    const size_t base = lsrc.size();
+    lsrc.resize(base + 32 * (size_t)width, zero);
+    lcol.resize(base + 32 * (size_t)width, 0);
+    lD.resize(base + 32 * (size_t)width, 0.0);
+    for (int l = 0; l < 32; ++l) {
+      const int r = lin[g + l];
+      lrow.push_back(r);
+      lres.push_back(r < 0 ? 0 : H.res[r]);
+      if (r < 0) continue;
+      int j = 0;
+      for (int i = rowptr[r]; i < rowptr[r + 1]; ++i) {
+        const Entry& x = H.e[i];
+        if (!is_problem(x.col)) continue;
+        const size_t slot = base + 32 * (size_t)j + l;
+        lsrc[slot] = x.src;
+        lcol[slot] = x.col;
+        lD[slot] = B.D[x.col];
+        ++j;
+      }
+    }
+    gptr.push_back((long long)lsrc.size());
+  }
+  for (int r = 0; r < H.nrow; ++r) {
+    if (d_kind(H.res[r]) != R_CONST) continue;
+    double nrm = fnrm[r];
+    if (r >= soc0) nrm = std::max(nrm, fnrm[soc0 + ((r - soc0) ^ 1)]);  // a Q^2 block shares its scale
+    double go = 0.0;
+    for (int i = rowptr[r]; i < rowptr[r + 1]; ++i)
+      if (is_problem(H.e[i].col)) go += cval(H.e[i].src) * B.o[H.e[i].col];
+    const double rho = nrm > 0.0 ? 1.0 / nrm : 1.0;
+    frow.push_back(r);
+    frho.push_back(rho);
+    frhs.push_back(rho * (B.consts[d_off(H.res[r])] - go));
+  }
   std::vector<long long> perm(nnz);
   for (long long i = 0; i < nnz; ++i) perm[i] = i;
   std::sort(perm.begin(), perm.end(), [&](long long a, long long b) {
@@ -483,8 +665,9 @@ bool finish(const HostMat& H, int n_var, std::vector<int>& colptr, std::vector<i
     const Entry& x = H.e[perm[i]];
     if (i > 0 && x.col == H.e[perm[i - 1]].col && x.row == H.e[perm[i - 1]].row) return false;
     crow[i] = x.row;
-    ccol[i] = x.col;
     csrc[i] = x.src;
+    // the column scale, with a constant's signed value folded in
+    cscale[i] = B.D[x.col] * (d_kind(x.src) == SRC_CONST ? cval(x.src) : 1.0);
     rowind[i] = x.row;
     ++colptr[x.col + 1];
   }
@@ -492,18 +675,25 @@ bool finish(const HostMat& H, int n_var, std::vector<int>& colptr, std::vector<i
   T.nrow = H.nrow;
   T.nnz = nnz;
   T.soc0 = soc0;
+  T.n_lin = (int)lrow.size();
+  T.n_fix = (int)frow.size();
   auto up = [&](auto& v) {
     auto* p = upload(v, e);
     if (p) so->allocs.push_back((void*)p);
     return p;
   };
-  T.rowptr = up(rowptr);
-  T.rcol = up(rcol);
-  T.rsrc = up(rsrc);
-  T.res = up(H.res);
+  T.lrow = up(lrow);
+  T.gptr = up(gptr);
+  T.lsrc = up(lsrc);
+  T.lcol = up(lcol);
+  T.lD = up(lD);
+  T.lres = up(lres);
+  T.frow = up(frow);
+  T.frho = up(frho);
+  T.frhs = up(frhs);
   T.crow = up(crow);
-  T.ccol = up(ccol);
   T.csrc = up(csrc);
+  T.cscale = up(cscale);
   return true;
 }
 
@@ -595,8 +785,8 @@ ciscvx_status ciscvx_socp_create(const ciscvx_model* m, int N, int layout, const
   for (int c = 0; c < n_var; ++c) so->P_colptr[c + 1] += so->P_colptr[c];
 
   cudaError_t e = cudaSuccess;
-  bool uniq = finish(B.A, n_var, so->A_colptr, so->A_rowind, so->dA, so, B.A.nrow, e) &&
-              finish(B.G, n_var, so->G_colptr, so->G_rowind, so->dG, so, B.n_nonneg, e);
+  bool uniq = finish(B.A, B, so->A_colptr, so->A_rowind, so->dA, so, B.A.nrow, e) &&
+              finish(B.G, B, so->G_colptr, so->G_rowind, so->dG, so, B.n_nonneg, e);
   auto up = [&](auto& v) {
     auto* p = upload(v, e);
     if (p) so->allocs.push_back((void*)p);
@@ -609,7 +799,7 @@ ciscvx_status ciscvx_socp_create(const ciscvx_model* m, int N, int layout, const
   so->colz = up(B.colz);
   if (!uniq) {
     free_socp(so);
-    return set_error(CISCVX_EINVAL, "internal: duplicate SOCP entry");
+    return set_error(CISCVX_EINVAL, "internal: duplicate SOCP entry or a non-constant fixed row");
   }
   if (e != cudaSuccess) {
     free_socp(so);
@@ -667,44 +857,63 @@ ciscvx_status ciscvx_socp_fill(const ciscvx_socp* so, int n_inst, const ciscvx_s
     return set_error(CISCVX_EINVAL, "null output");
   SocpIO I;
   std::memset(&I, 0, sizeof I);
-  const int N = so->N, nxt = so->nxt, nu = so->nu, nq = so->nq;
-  I.N = N; I.nxt = nxt; I.nu = nu; I.nb = so->nb; I.nc = nc; I.npsi = so->npsi; I.ny = so->ny; I.nq = nq;
-  I.n_var = so->dims.n_var; I.node_layout = so->layout == CISCVX_FOH_NODE;
-  I.phi64 = in->phi_precision == CISCVX_FP64;
-  I.sX = (long long)(N + 1) * nxt;
-  I.sU = so->layout == CISCVX_FOH_NODE ? (long long)(N + 1) * nu : (long long)N * 2 * nu;
-  I.sS = N;
-  I.sPhi = (long long)(N + 1) * 2 * nc;
-  I.sGam = (long long)(N + 1) * nc;
-  I.sA = (long long)N * nxt * nxt;
-  I.sB = (long long)N * nxt * nu;
-  I.sSv = (long long)N * nxt;
-  I.sDef = (long long)N * nxt;
-  I.sG = (long long)(N + 1) * nxt;
-  I.sGvm = (long long)(N + 1) * nq * nq;
-  I.sGth = (long long)(N + 1) * nq * so->nb;
-  I.sGphi = (long long)(N + 1) * nq * 2 * nc;
-  I.sGpx = (long long)(N + 1) * nq * nc;
-  I.sTh = (long long)(N + 1) * 8 * nc;
-  I.sDth = (long long)(N + 1) * nc * 8 * CISCVX_NODE_THETA_COLS;
-  I.sPsi = (long long)N * so->npsi;
-  I.sDpsi = (long long)N * so->npsi * so->ny;
-  I.Xp = in->Xp; I.Xm = in->Xm; I.U = in->U; I.s = in->s; I.Phi = in->Phi; I.Gam = in->Gam;
-  I.defect = in->defect; I.g = in->g; I.Gvm = in->Gvm; I.Gth = in->Gth; I.Gphi = in->Gphi; I.Gpx = in->Gpx;
-  I.theta = in->theta; I.dtheta = in->dtheta; I.psi = in->psi; I.dpsi = in->dpsi;
-  I.A = in->A; I.Bm = in->Bm; I.Bp = in->Bp; I.S = in->S;
+  const long long N = so->N, nxt = so->nxt, nu = so->nu, nq = so->nq, nb = so->nb, npsi = so->npsi, ny = so->ny;
+  const bool f32 = in->phi_precision == CISCVX_FP32_PHI;
+  auto src = [&](unsigned k, const void* p, long long stride) {
+    I.sp[k] = p;
+    I.ss[k] = stride;
+  };
+  src(SRC_A, in->A, N * nxt * nxt);
+  src(SRC_BM, in->Bm, N * nxt * nu);
+  src(SRC_BP, in->Bp, N * nxt * nu);
+  src(SRC_S, in->S, N * nxt);
+  src(SRC_GVM, in->Gvm, (N + 1) * nq * nq);
+  src(SRC_GTH, in->Gth, (N + 1) * nq * nb);
+  src(SRC_GPHI, in->Gphi, (N + 1) * nq * 2 * nc);
+  src(SRC_GPX, in->Gpx, (N + 1) * nq * nc);
+  src(SRC_DTH, in->dtheta, (N + 1) * nc * 8 * CISCVX_NODE_THETA_COLS);
+  src(SRC_DPSI, in->dpsi, N * npsi * ny);
+  I.f32 = f32 ? (1u << SRC_A) | (1u << SRC_BM) | (1u << SRC_BP) | (1u << SRC_S) : 0u;
+  auto zsrc = [&](unsigned k, const double* p, long long stride) {
+    I.zp[k] = p;
+    I.zs[k] = stride;
+  };
+  zsrc(Z_XP, in->Xp, (N + 1) * nxt);
+  zsrc(Z_XM, in->Xm, (N + 1) * nxt);
+  zsrc(Z_PHI, in->Phi, (N + 1) * 2 * nc);
+  zsrc(Z_GAM, in->Gam, (N + 1) * nc);
+  zsrc(Z_U, in->U, so->layout == CISCVX_FOH_NODE ? (N + 1) * nu : N * 2 * nu);
+  zsrc(Z_S, in->s, N);
+  I.g = in->g; I.sG = (N + 1) * nxt;
+  I.defect = in->defect; I.sDef = N * nxt;
+  I.Xp = in->Xp; I.Xm = in->Xm; I.sX = (N + 1) * nxt;
+  I.theta = in->theta; I.sTh = (N + 1) * 8 * nc;
+  I.psi = in->psi; I.sPsi = N * npsi;
+  I.nxt = (int)nxt; I.n_var = so->dims.n_var;
   I.consts = so->consts; I.colz = so->colz; I.D = so->D; I.o = so->o; I.Po = so->Po;
   I.w_px = so->w_px; I.w_ep = so->w_ep;
   cudaStream_t st = (cudaStream_t)stream;
   const int bs = 256;
-  auto grid = [&](long long n) { return (unsigned)((n + bs - 1) / bs); };
-  const long long nA = (long long)n_inst * so->dA.nrow, nG = (long long)n_inst * so->dG.nrow;
-  if (nA) k_socp_rows<<<grid(nA), bs, 0, st>>>(I, so->dA, n_inst, out->rho_A, out->b);
-  if (nG) k_socp_rows<<<grid(nG), bs, 0, st>>>(I, so->dG, n_inst, out->rho_G, out->h);
-  const long long vA = (long long)n_inst * so->dA.nnz, vG = (long long)n_inst * so->dG.nnz;
-  if (vA) k_socp_values<<<grid(vA), bs, 0, st>>>(I, so->dA, n_inst, out->rho_A, out->A_values);
-  if (vG) k_socp_values<<<grid(vG), bs, 0, st>>>(I, so->dG, n_inst, out->rho_G, out->G_values);
-  k_socp_c<<<grid((long long)n_inst * I.n_var), bs, 0, st>>>(I, n_inst, out->c);
+  const unsigned gy = (unsigned)std::min((n_inst + IPB - 1) / IPB, 65535);
+  auto grid = [&](long long n, int per) { return dim3((unsigned)((n + per - 1) / per), gy); };
+  // zhat into c, the row passes read it, the column pass overwrites it with c
+  k_socp_zhat<<<grid(I.n_var, bs), bs, 0, st>>>(I, n_inst, out->c);
+  for (int w = 0; w < 2; ++w) {
+    const MatDev& T = w == 0 ? so->dA : so->dG;
+    double* rho = w == 0 ? out->rho_A : out->rho_G;
+    double* rhs = w == 0 ? out->b : out->h;
+    if (T.n_lin) k_socp_rows<<<grid(T.n_lin, bs), bs, 0, st>>>(I, T, n_inst, out->c, rho, rhs);
+    if (T.n_fix)
+      k_socp_fixed<<<dim3((unsigned)((T.n_fix + bs - 1) / bs), (unsigned)std::min(n_inst, 65535)), bs, 0, st>>>(
+          T, n_inst, rho, rhs);
+  }
+  for (int w = 0; w < 2; ++w) {
+    const MatDev& T = w == 0 ? so->dA : so->dG;
+    if (T.nnz)
+      k_socp_values<<<grid(T.nnz, bs), bs, 0, st>>>(I, T, n_inst, w == 0 ? out->rho_A : out->rho_G,
+                                                     w == 0 ? out->A_values : out->G_values);
+  }
+  k_socp_c<<<grid(I.n_var, bs), bs, 0, st>>>(I, n_inst, out->c);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "socp launch: %s", cudaGetErrorString(e));
   return set_error(CISCVX_OK, "");

@@ -60,6 +60,12 @@ def test_null_arguments_rejected(lib):
                                                 ctypes.byref(hi)) == api.EINVAL
     assert lib.ciscvx_psi_rows(None, None) == api.EINVAL
     assert lib.ciscvx_psi_linearize(None, 4, None, None, 0.1, 1e-4, None, None, None) == api.EINVAL
+    h = ctypes.c_void_p()
+    assert lib.ciscvx_socp_create(None, 4, 0, None, ctypes.byref(h)) == api.EINVAL
+    assert lib.ciscvx_socp_get_dims(None, None) == api.EINVAL
+    assert lib.ciscvx_socp_structure(None, None, None, None, None, None, None, None) == api.EINVAL
+    assert lib.ciscvx_socp_fill(None, 1, None, None, None) == api.EINVAL
+    lib.ciscvx_socp_destroy(None)
 
 
 def _desc(api, nb=2, joints=((0, 1),), contacts=((1,),), mass=1.0):
