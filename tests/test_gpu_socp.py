@@ -195,3 +195,80 @@ def test_socp_arguments(env):
     import ctypes
     assert lib.ciscvx_socp_fill(sp._h, 1, ctypes.byref(ins), ctypes.byref(outs), None) == api.EINVAL
     assert lib.ciscvx_socp_fill(sp._h, 0, ctypes.byref(ins), ctypes.byref(outs), None) == api.EINVAL
+
+
+def test_socp_sweep_size_sampled_periods(env):
+    """N = 400 intervals of the 7-link chain, 64 instances in one call (the
+    bench's per-instance size).  The rows of period k touch periods k and k+1
+    only, so the oracle's assembly of the 2-interval slice starting at node k
+    gives them exactly (columns shifted by the periods before k); sampled
+    periods of sampled instances are compared row by row, with their scales
+    and right-hand sides."""
+    import scipy.sparse as sps
+    torch, oracle, osocp, api = env
+    R = _robot("cheetah7", "default")
+    m = api.Model(R)
+    rng = np.random.default_rng(8)
+    N, n_inst, layout = 400, 64, "node"
+    prm = _params(m, rng)
+    its = [_iterate(m, N, layout, rng) for _ in range(n_inst)]
+    sp = _socp(api, m, N, layout, prm)
+    st, d = sp.structure(), sp.dims
+    out = sp.fill(n_inst, _linearize(torch, api, m, layout, its, "fp64"))
+    api.sync_status(m)
+    Lf = osocp.Layout(R, N, layout)
+    Ls = osocp.Layout(R, 2, layout)
+    per_col = Ls.col["xm", 1][0] - Ls.col["xm", 0][0]
+    nA_per = 2 * m.nxt
+    nG_node = 16 * m.nc + 2 * m.nxt + 2 * m.nj + 4 * m.nc
+    nG_int = 2 * api.psi_rows(m) + 2 * m.nxt + 2
+    for inst in (0, 37, 63):
+        Xp, Xm, U, s, Phi, Gam = its[inst]
+        A = sps.csc_matrix((out["A_values"][inst].cpu().numpy(), st["A_rowind"], st["A_colptr"]),
+                           shape=(d["n_eq"], d["n_var"])).tocsr()
+        G = sps.csc_matrix((out["G_values"][inst].cpu().numpy(), st["G_rowind"], st["G_colptr"]),
+                           shape=(d["n_ineq"], d["n_var"])).tocsr()
+        b, h = out["b"][inst].cpu().numpy(), out["h"][inst].cpu().numpy()
+        rA, rG = out["rho_A"][inst].cpu().numpy(), out["rho_G"][inst].cpu().numpy()
+        for k in (0, 1, 199, N - 2):
+            sl = slice(k, k + 3)
+            ref = osocp.assemble(R, 2, layout, prm, Xp[sl], Xm[sl], U[sl], s[k:k + 2], Phi[sl], Gam[sl],
+                                 NSUB, DELTA, EPS, np.full(m.nc, 0.4))
+            shift = Lf.col["xm", k][0] - Ls.col["xm", 0][0]
+            ncols = 2 * per_col
+            for M, vec, rho, rows_f, rows_s, Mr, vr, rr in (
+                    (A, b, rA, slice(k * nA_per, (k + 1) * nA_per), slice(0, nA_per), ref["A"], ref["b"], ref["rho_A"]),
+                    (G, h, rG, slice(k * (nG_node + nG_int), (k + 1) * (nG_node + nG_int)), slice(0, nG_node + nG_int),
+                     ref["G"], ref["h"], ref["rho_G"])):
+                got = M[rows_f].toarray()
+                assert np.abs(got[:, :shift]).max(initial=0) == 0
+                assert np.abs(got[:, shift + ncols:]).max(initial=0) == 0
+                assert block_err(got[:, shift:shift + ncols], Mr[rows_s, :ncols]) <= TOL_FP64
+                assert block_err(vec[rows_f], vr[rows_s]) <= TOL_FP64
+                assert block_err(rho[rows_f], rr[rows_s]) <= TOL_FP64
+
+
+def test_socp_fp32_inputs_widen_exactly(env):
+    """FP32 Phi blocks are widened exactly: the fill from FP32 blocks equals,
+    bit for bit, the fill from the same blocks converted to FP64 by torch
+    (zeros, negative values and values of every magnitude included)."""
+    torch, oracle, osocp, api = env
+    R = _robot("biped", "cross")
+    m = api.Model(R)
+    rng = np.random.default_rng(12)
+    N = 5
+    prm = _params(m, rng)
+    it = _iterate(m, N, "interval", rng)
+    sp = _socp(api, m, N, "interval", prm)
+    ins = _linearize(torch, api, m, "interval", [it], "fp32_phi")
+    gen = torch.Generator(device=ins["A"].device).manual_seed(3)
+    for k in ("A", "Bm", "Bp", "S"):  # spread the magnitudes and plant exact zeros
+        t = ins[k]
+        scale = torch.pow(2.0, torch.randint(-60, 60, t.shape, generator=gen, device=t.device).float())
+        ins[k] = torch.where(torch.rand(t.shape, generator=gen, device=t.device) < 0.1,
+                             torch.zeros_like(t), t * scale).contiguous()
+    o32 = sp.fill(1, ins, precision="fp32_phi")
+    ins64 = dict(ins, **{k: ins[k].double() for k in ("A", "Bm", "Bp", "S")})
+    o64 = sp.fill(1, ins64, precision="fp64")
+    for k in o32:
+        assert torch.equal(o32[k], o64[k]), k
