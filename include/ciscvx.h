@@ -138,9 +138,10 @@ typedef struct {
  *     at y index 4 i .. 4 i + 3, then one path-penalty state per contact at y
  *     index 4 n_c + i integrating h(-phi_n) + h(-phi) + h(-gamma) + h(-rho^c)
  *     (n_y = 5 n_c).  The penalty output is the increment of the path-penalty
- *     states.  Provided for the dense linearization (single and batch) and
- *     the single-instance VJP (linearize-and-contract); compact outputs, z
- *     and batched VJPs return CISCVX_EUNSUPPORTED for it. */
+ *     states.  Provided for the dense linearization (single and batch, z
+ *     formed from the dense outputs) and the single-instance VJP
+ *     (linearize-and-contract); compact outputs and batched VJPs return
+ *     CISCVX_EUNSUPPORTED for it. */
 typedef enum { CISCVX_AUX_PENALTY = 0, CISCVX_AUX_CROSS = 1 } ciscvx_aux_model;
 
 /* Joint reaction forces (Sec. II-A).
@@ -185,7 +186,7 @@ typedef struct ciscvx_model ciscvx_model;
  * description, builds the per-link device tables on the current CUDA device
  * and allocates the model's device status word.  A model with eliminated
  * joint forces, a sinusoidal surface or the RKF45 scheme has coupled links:
- * it is linearized by ciscvx_discretize (dense outputs, z not provided, a
+ * it is linearized by ciscvx_discretize (dense outputs, z formed from them, a
  * workspace from ciscvx_discretize_workspace_size) or in a batch plan
  * (ciscvx_batch_discretize, dense outputs; the plan groups its instances by
  * n_sub and owns their stage-data workspace), and its VJP by

@@ -471,7 +471,6 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* m, int N, int n_sub,
   if (m->host.nu > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
   if (m->cpl) {
-    if (z) return fail(CISCVX_EUNSUPPORTED, "z is not provided for models with coupled links");
     const size_t per = cpl_interval_bytes(*m->cpl, n_sub, precision);
     const size_t need = per * (size_t)std::min(N, 32);
     if (!workspace || ws_bytes < need)
@@ -480,13 +479,18 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* m, int N, int n_sub,
     const long chunk = (long)std::min<size_t>(ws_bytes / per, (size_t)N);
     cudaError_t e = launch_coupled(*m->cpl, N, n_sub, precision, layout, X, U, s, A, Bm, Bp, S,
                                    defect, penalty, workspace, chunk, m->status, (cudaStream_t)stream);
+    if (e == cudaSuccess && z)
+      e = launch_affine_z(m->host, N, precision, layout, X, U, s, A, Bm, Bp, S, defect, z, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "coupled discretize launch");
     return ok();
   }
-  if (m->host.aux && z) return fail(CISCVX_EUNSUPPORTED, "z is not provided for the Eq. (12) model");
+  // the Eq. (12) model's kernels do not form z; it comes from the outputs
+  const bool post_z = m->host.aux && z;
   cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, false, m->host.aux != 0, X, U,
-                                    s, A, Bm, Bp, S, defect, penalty, z, m->status,
+                                    s, A, Bm, Bp, S, defect, penalty, post_z ? nullptr : z, m->status,
                                     (cudaStream_t)stream);
+  if (e == cudaSuccess && post_z)
+    e = launch_affine_z(m->host, N, precision, layout, X, U, s, A, Bm, Bp, S, defect, z, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
   return ok();
 }

@@ -209,6 +209,11 @@ cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const dou
 // Structural nonzeros of A and B-/B+ in compact order (api.cu); for models
 // without coupled links and without the Eq. (12) state.
 void model_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int32_t* bc);
+// The affine term z_k = x~(1) - A x~_k - B- u_L - B+ u_R - S s_k from the
+// dense outputs (contract.cu), for the models whose kernels do not form it.
+cudaError_t launch_affine_z(const DevModel& M, int N, int prec, int layout, const double* X, const double* U,
+                            const double* s, const void* A, const void* Bm, const void* Bp, const void* S,
+                            const double* defect, double* z, cudaStream_t st);
 // Psi^{delta,eps} rows per interval, and its launcher (psi.cu).
 int psi_rows(const DevModel& M);
 cudaError_t launch_psi(const DevModel& M, int N, const double* Xp, const double* Xm, double delta,

@@ -149,7 +149,50 @@ ChunkLayout chunk_layout(const DevModel& M, const CplTab* T, long n, int nsub, i
   return L;
 }
 
+// z_k = x~(1) - A_k x~_k - B-_k u_L - B+_k u_R - S_k s_k with x~(1) =
+// defect_k + x~_{k+1}: thread per (interval, row), FP64 accumulation over the
+// row of each block (a thread's row is contiguous, so its loads reuse L1 lines).
+template <typename TP>
+__global__ void __launch_bounds__(256) k_affine_z(int nxt, int nu, long N, int node_layout,
+                                                  const double* __restrict__ X, const double* __restrict__ U,
+                                                  const double* __restrict__ s, const TP* __restrict__ A,
+                                                  const TP* __restrict__ Bm, const TP* __restrict__ Bp,
+                                                  const TP* __restrict__ S, const double* __restrict__ defect,
+                                                  double* __restrict__ z) {
+  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N * nxt) return;
+  const long k = g / nxt;
+  const double* xk = X + k * nxt;
+  double acc = defect[g] + X[g + nxt];
+  const TP* a = A + g * nxt;
+  for (int c = 0; c < nxt; ++c) acc = fma(-(double)a[c], xk[c], acc);
+  if (nu > 0) {
+    const double* uL = U + (node_layout ? k : 2 * k) * nu;
+    const double* uR = U + (node_layout ? k + 1 : 2 * k + 1) * nu;
+    const TP* bm = Bm + g * nu;
+    const TP* bp = Bp + g * nu;
+    for (int q = 0; q < nu; ++q) acc = fma(-(double)bm[q], uL[q], fma(-(double)bp[q], uR[q], acc));
+  }
+  z[g] = fma(-(double)S[g], s[k], acc);
+}
+
 }  // namespace
+
+cudaError_t launch_affine_z(const DevModel& M, int N, int prec, int layout, const double* X, const double* U,
+                            const double* s, const void* A, const void* Bm, const void* Bp, const void* S,
+                            const double* defect, double* z, cudaStream_t st) {
+  const long n = (long)N * M.nxt;
+  const int bs = 256;
+  const unsigned grid = (unsigned)((n + bs - 1) / bs);
+  const int node = layout == CISCVX_FOH_NODE;
+  if (prec == CISCVX_FP64)
+    k_affine_z<double><<<grid, bs, 0, st>>>(M.nxt, M.nu, N, node, X, U, s, (const double*)A, (const double*)Bm,
+                                           (const double*)Bp, (const double*)S, defect, z);
+  else
+    k_affine_z<float><<<grid, bs, 0, st>>>(M.nxt, M.nu, N, node, X, U, s, (const float*)A, (const float*)Bm,
+                                          (const float*)Bp, (const float*)S, defect, z);
+  return cudaGetLastError();
+}
 
 size_t contract_bytes(const DevModel& M, const CplTab* T, long n, int nsub, int prec) {
   return chunk_layout(M, T, n, nsub, prec).total;

@@ -2,7 +2,7 @@
 the FP64 oracle through the C ABI: single-instance and batched linearization,
 both precisions and both control layouts, mixed batches of the two auxiliary
 models, feasible inputs, the linearize-and-contract VJP, and the entry points
-that return EUNSUPPORTED for it.
+that return EUNSUPPORTED for it, and the affine term z formed from the outputs.
 Tolerances as for the default model (FP64 1e-10; FP32-Phi blocks 1e-4,
 defect and penalty 1e-10)."""
 import numpy as np
@@ -134,8 +134,7 @@ def test_cross_unsupported_entry_points(env):
     X, U, s = t(p.X), t(p.U), t(p.s)
     w = torch.zeros((p.N, m.nxt), dtype=torch.float64, device=dev)
     rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
-    for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
-                 lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
+    for call in (lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
                  lambda: api.model_pattern(p.robot.as_dict()),
                  lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
         with pytest.raises(api.CiscvxError) as e:
@@ -192,3 +191,21 @@ def test_cross_vjp_matches_oracle(env, precision, tol, layout):
     for g, r, nm in ((gX, rX, "gX"), (gU, rU, "gU"), (gs, rs, "gs")):
         assert block_err(g.cpu().numpy(), r) <= tol, (nm, block_err(g.cpu().numpy(), r))
     assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+def test_cross_affine_term(env, precision, tol):
+    """z_k = x~(1) - A x~_k - B- u_L - B+ u_R - S s_k, from the oracle's blocks."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("biped", 16, 37, 4)
+    m = api.Model(p.robot)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    got = api.discretize(m, t(p.X), t(p.U), t(p.s), p.n_sub, precision, want_z=True)
+    ref = oracle.discretize(p.robot.as_dict(), p.X, p.U, p.s, p.n_sub)
+    z = ref["defect"] + p.X[1:] - np.einsum("kij,kj->ki", ref["A"], p.X[:-1]) \
+        - np.einsum("kij,kj->ki", ref["Bm"], p.U[:-1]) - np.einsum("kij,kj->ki", ref["Bp"], p.U[1:]) \
+        - ref["S"] * p.s[:, None]
+    zg = got["z"].cpu().numpy()
+    for k in range(p.N):
+        assert block_err(zg[k], z[k]) <= tol

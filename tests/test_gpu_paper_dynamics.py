@@ -137,8 +137,7 @@ def test_unsupported_entry_points(env):
     m = api.Model(p.robot)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     X, U, s = t(p.X), t(p.U), t(p.s)
-    for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", want_z=True),
-                 lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
+    for call in (lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
                  lambda: api.model_pattern(p.robot.as_dict()),
                  lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
         with pytest.raises(api.CiscvxError) as err:
@@ -325,3 +324,27 @@ def test_batch_plan_with_coupled_models(env, precision):
     plan.sync_status()
     for k in out:
         assert torch.equal(out[k], out2[k]), k
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("layout", ["node", "interval"])
+def test_affine_term(env, precision, tol, layout):
+    """z_k = x~(1) - A x~_k - B- u_L - B+ u_R - S s_k, from the oracle's blocks
+    (coupled links: formed from the dense outputs after the coupled kernels)."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("hopper", 29, 45, 4, **PAPER)
+    U = p.U
+    if layout == "interval":
+        U = np.stack([p.U[:-1], p.U[1:]], axis=1) + 0.1
+    m = api.Model(p.robot)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)  # noqa: E731
+    got = api.discretize(m, t(p.X), t(U), t(p.s), p.n_sub, precision, layout, want_z=True)
+    ref = oracle.discretize(p.robot.as_dict(), p.X, U, p.s, p.n_sub, layout)
+    uL, uR = (p.U[:-1], p.U[1:]) if layout == "node" else (U[:, 0], U[:, 1])
+    z = ref["defect"] + p.X[1:] - np.einsum("kij,kj->ki", ref["A"], p.X[:-1]) \
+        - np.einsum("kij,kj->ki", ref["Bm"], uL) - np.einsum("kij,kj->ki", ref["Bp"], uR) \
+        - ref["S"] * p.s[:, None]
+    zg = got["z"].cpu().numpy()
+    for k in range(p.N):
+        assert block_err(zg[k], z[k]) <= tol
