@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(FINB) k_batch_vjp_finish(const DevModel* const
                                                            double* gU, double* gs, double* L) {
   __shared__ double red[FINB];
   const DevInst I = inst[blockIdx.x];
+  if (I.contract) return;  // written by the linearize-and-contract pass
   const DevModel& M = *models[I.model];
   const int nu = M.nu, nslot = M.nslot, nb = M.nb, N = I.N;
   const double* P = part + I.part;
@@ -210,6 +211,13 @@ struct ciscvx_batch_plan {
   size_t part_total = 0, pb_total = 0;
   int n_items = 0;
   std::vector<int2> items_lpt, items_nat;
+  // the adjoint kernel's items: those of the instances that are not contract instances
+  int n_vitems = 0;
+  int2* d_vitems_lpt = nullptr;
+  int2* d_vitems_nat = nullptr;
+  bool any_contract = false;   // Eq. (12) or coupled-link instances: VJP by linearize-and-contract
+  int max_nsub_adj = 0;        // largest n_sub among the other instances
+  size_t contract_ws = 0;      // bytes of VJP workspace the contract pass needs (after the adjoint's)
   std::string key;
   // device tables
   const DevModel** d_models = nullptr;
@@ -265,6 +273,8 @@ void free_plan(ciscvx_batch_plan* p) {
   cudaFree(p->d_groups);
   cudaFree(p->d_items_lpt);
   cudaFree(p->d_items_nat);
+  cudaFree(p->d_vitems_lpt);
+  cudaFree(p->d_vitems_nat);
   cudaFree(p->d_queue);
   cudaFree(p->d_status);
   cudaFree(p->d_cpl_entries);
@@ -342,6 +352,10 @@ BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot, const ciscvx_t
   c.groups = p->d_groups;
   c.items = t.lpt_order ? p->d_items_lpt : p->d_items_nat;
   c.n_items = p->n_items;
+  if (queue_slot == 1) {  // the adjoint pass skips the contract instances
+    c.items = t.lpt_order ? p->d_vitems_lpt : p->d_vitems_nat;
+    c.n_items = p->n_vitems;
+  }
   c.persistent = t.ctas_per_sm > 0;
   c.queue = p->d_queue + queue_slot;
   c.status = p->d_status;
@@ -466,6 +480,31 @@ cudaError_t launch_vjp_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscv
   return e;
 }
 
+// Offset of the contract pass's part of the VJP workspace (after the
+// adjoint's partial sums, 16-byte aligned).
+size_t contract_ws_offset(const ciscvx_batch_plan* p) {
+  return (sizeof(double) * (p->part_total + 2 * p->pb_total) + 15) & ~(size_t)15;
+}
+
+// The VJP of every contract instance (Eq. (12) state or coupled links) by
+// linearize-and-contract, one instance after another in stream order, each
+// in chunks of what fits in the workspace.
+cudaError_t launch_contract_instances(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, void* ws,
+                                      size_t ws_bytes, cudaStream_t s) {
+  for (int i = 0; i < p->n_inst; ++i) {
+    const DevInst& I = p->inst[i];
+    if (!I.contract) continue;
+    const ciscvx_model* m = p->models[I.model];
+    const bool nu = m->host.nu > 0, nc = m->host.nc > 0;
+    cudaError_t e = launch_contract_vjp(
+        m->host, m->dev, m->cpl, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
+        io->s + I.s, io->w + I.v, nc ? io->rho + I.p : nullptr, io->gX + I.x, nu ? io->gU + I.u : nullptr,
+        io->gs + I.s, io->L ? io->L + i : nullptr, ws, ws_bytes, p->d_status, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Discretize + VJP of the items of `c` in one pass, then the per-instance
 // finish over instances [i0, i1).  vio's X, U, s are not used (io's are).
 cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_io* io,
@@ -494,14 +533,10 @@ ciscvx_status check_vjp(const ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* i
     return set_error(CISCVX_EINVAL, "null required buffer in ciscvx_batch_vjp_io");
   if (!p->all_nu0 && ((need_x && !io->U) || !io->gU)) return set_error(CISCVX_EINVAL, "null U / gU");
   if (!p->all_nc0 && !io->rho) return set_error(CISCVX_EINVAL, "null rho");
-  if (p->max_nsub > MAXSUB_VJP)
+  if (p->max_nsub_adj > MAXSUB_VJP)
     return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (plan has %d)",
-                     MAXSUB_VJP, p->max_nsub);
-  if (p->any_aux) return set_error(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
-  if (p->any_cpl)
-    return set_error(CISCVX_EUNSUPPORTED, "batched VJPs are not provided for models with coupled links "
-                                          "(use ciscvx_discretize_vjp per instance)");
-  const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
+                     MAXSUB_VJP, p->max_nsub_adj);
+  const size_t need = contract_ws_offset(p) + p->contract_ws;
   if (!workspace || ws_bytes < need)
     return set_error(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
   if (((uintptr_t)workspace & 15) != 0) return set_error(CISCVX_EINVAL, "workspace must be 16-byte aligned");
@@ -615,6 +650,14 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     if (nc) p->all_nc0 = false;
     if (M.aux && !models[model_idx[i]]->cpl) p->any_aux = true;
     if (models[model_idx[i]]->cpl) p->any_cpl = true;
+    I.contract = (M.aux || models[model_idx[i]]->cpl) ? 1 : 0;
+    if (I.contract) {
+      p->any_contract = true;
+      p->contract_ws = std::max(p->contract_ws, contract_bytes(M, models[model_idx[i]]->cpl,
+                                                               std::min<long>(N[i], 4096), n_sub[i], precision));
+    } else {
+      p->max_nsub_adj = std::max(p->max_nsub_adj, n_sub[i]);
+    }
   }
   z.L = (size_t)n_inst;
   if (p->any_aux && p->compact) {
@@ -629,6 +672,12 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   p->n_items = (int)dec.items_lpt.size();
   p->items_lpt = dec.items_lpt;
   p->items_nat = dec.items_nat;
+  std::vector<int2> vitems_lpt, vitems_nat;
+  for (const int2& it : dec.items_lpt)
+    if (!models[dec.groups[it.x].x]->host.aux) vitems_lpt.push_back(it);
+  for (const int2& it : dec.items_nat)
+    if (!models[dec.groups[it.x].x]->host.aux) vitems_nat.push_back(it);
+  p->n_vitems = (int)vitems_lpt.size();
   const std::vector<int2>& entries = dec.entries;
   const std::vector<int4>& groups = dec.groups;
 
@@ -667,6 +716,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (e == cudaSuccess) e = upload(&p->d_groups, groups);
   if (e == cudaSuccess) e = upload(&p->d_items_lpt, p->items_lpt);
   if (e == cudaSuccess) e = upload(&p->d_items_nat, p->items_nat);
+  if (e == cudaSuccess && !vitems_lpt.empty()) e = upload(&p->d_vitems_lpt, vitems_lpt);
+  if (e == cudaSuccess && !vitems_nat.empty()) e = upload(&p->d_vitems_nat, vitems_nat);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_queue, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned));
@@ -740,7 +791,7 @@ ciscvx_status ciscvx_batch_discretize(ciscvx_batch_plan* p, const ciscvx_batch_i
 
 ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* p, size_t* bytes) {
   if (!p || !bytes) return set_error(CISCVX_EINVAL, "null argument");
-  *bytes = sizeof(double) * (p->part_total + 2 * p->pb_total);
+  *bytes = contract_ws_offset(p) + p->contract_ws;
   return CISCVX_OK;
 }
 
@@ -753,6 +804,8 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_bat
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
   cudaError_t e = launch_vjp_c(p, common_of(p, 1, p->tune), io, part, ps, pL, 0, p->n_inst, s);
+  if (e == cudaSuccess && p->any_contract)
+    e = launch_contract_instances(p, io, (char*)workspace + contract_ws_offset(p), p->contract_ws, s);
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch vjp launch: %s", cudaGetErrorString(e));
   return CISCVX_OK;
 }
@@ -763,6 +816,15 @@ ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* p, const ciscvx
   ciscvx_status st = check_io(p, io);
   if (st == CISCVX_OK) st = check_vjp(p, vjp, false, workspace, ws_bytes);
   if (st != CISCVX_OK) return st;
+  if (p->any_contract) {  // the two calls in sequence, on io's inputs
+    st = ciscvx_batch_discretize(p, io, stream);
+    if (st != CISCVX_OK) return st;
+    ciscvx_batch_vjp_io v = *vjp;
+    v.X = io->X;
+    v.U = io->U;
+    v.s = io->s;
+    return ciscvx_batch_discretize_vjp(p, &v, workspace, ws_bytes, stream);
+  }
   cudaStream_t s = (cudaStream_t)stream;
   double* part = (double*)workspace;
   double* ps = part + p->part_total;

@@ -75,7 +75,8 @@ constexpr int A_PER_LINK = 10, A_PER_FOOT = 5;
 // One instance of a batch: model, horizon, substeps and its element offsets
 // into the packed arrays.
 struct DevInst {
-  int model, N, nsub, pad_;
+  int model, N, nsub;
+  int contract;                   // 1: the VJP is linearize-and-contract (Eq. (12) state or coupled links)
   long long x, u, s, a, b, v, p;  // element offsets: X/gX, U/gU, s/gs, A, Bm/Bp, S/defect/w, penalty/rho
   long long part, pb;             // VJP workspace offsets: per-input partials, per-(interval, link) partials
 };

@@ -132,18 +132,12 @@ def test_cross_unsupported_entry_points(env):
     m = api.Model(p.robot)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     X, U, s = t(p.X), t(p.U), t(p.s)
-    w = torch.zeros((p.N, m.nxt), dtype=torch.float64, device=dev)
-    rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
     for call in (lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
                  lambda: api.model_pattern(p.robot.as_dict()),
                  lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
         with pytest.raises(api.CiscvxError) as e:
             call()
         assert e.value.status == api.EUNSUPPORTED
-    plan = api.BatchPlan([m], [0], [p.N], [p.n_sub])
-    with pytest.raises(api.CiscvxError) as e:
-        plan.discretize_vjp(X, U, s, w, rho)
-    assert e.value.status == api.EUNSUPPORTED
 
 
 def test_cross_node_constraints(env):

@@ -143,12 +143,6 @@ def test_unsupported_entry_points(env):
         with pytest.raises(api.CiscvxError) as err:
             call()
         assert err.value.status == api.EUNSUPPORTED
-    plan = api.BatchPlan([m], [0], [p.N], [p.n_sub], precision="fp64")
-    w = torch.zeros((p.N, m.nxt), dtype=torch.float64, device=dev)
-    rho = torch.zeros((p.N, m.nc), dtype=torch.float64, device=dev)
-    with pytest.raises(api.CiscvxError) as err:
-        plan.discretize_vjp(X, U, s, w, rho)
-    assert err.value.status == api.EUNSUPPORTED
     # a workspace below the minimum is an argument error
     tiny = torch.empty(16, dtype=torch.uint8, device=dev)
     with pytest.raises(api.CiscvxError) as err:
