@@ -140,8 +140,8 @@ typedef struct {
  *     (n_y = 5 n_c).  The penalty output is the increment of the path-penalty
  *     states.  Provided for the dense linearization (single and batch, z
  *     formed from the dense outputs) and the single-instance VJP
- *     (linearize-and-contract); compact outputs and batched VJPs return
- *     CISCVX_EUNSUPPORTED for it. */
+ *     (linearize-and-contract, also inside batch plans); compact outputs
+ *     return CISCVX_EUNSUPPORTED for it. */
 typedef enum { CISCVX_AUX_PENALTY = 0, CISCVX_AUX_CROSS = 1 } ciscvx_aux_model;
 
 /* Joint reaction forces (Sec. II-A).
@@ -190,8 +190,9 @@ typedef struct ciscvx_model ciscvx_model;
  * workspace from ciscvx_discretize_workspace_size) or in a batch plan
  * (ciscvx_batch_discretize, dense outputs; the plan groups its instances by
  * n_sub and owns their stage-data workspace), and its VJP by
- * linearize-and-contract (single instance).  Its compact outputs, batched
- * VJPs, the fused pass and the host executor return CISCVX_EUNSUPPORTED.  *out receives an opaque
+ * linearize-and-contract (single instance, and in batch plans, where the
+ * fused pass runs the linearization and the VJP as two calls).  Its compact
+ * outputs and the host executor return CISCVX_EUNSUPPORTED.  *out receives an opaque
  * handle owned by the caller (free with ciscvx_model_destroy).  Errors:
  * EINVAL (null, counts < 0, n_bodies < 1, bad indices, non-positive mass or
  * inertia, parent == child, non-finite values), EUNSUPPORTED (limits above,
@@ -441,9 +442,12 @@ ciscvx_status ciscvx_batch_discretize(ciscvx_batch_plan* plan, const ciscvx_batc
 ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* plan, size_t* bytes);
 
 /* VJP (as ciscvx_discretize_vjp) of every instance; L receives one value per
- * instance.  workspace: device, >= ciscvx_batch_vjp_workspace_size bytes,
- * 16-byte aligned.  Errors: EINVAL, EUNSUPPORTED (n_sub > CISCVX_MAX_VJP_SUBSTEPS
- * in some instance), ECUDA. */
+ * instance.  Default-model instances take the batched adjoint kernel;
+ * instances of the Eq. (12) model or with coupled links are linearized and
+ * contracted one after another in stream order (chunked in the last part of
+ * the workspace).  workspace: device, >= ciscvx_batch_vjp_workspace_size
+ * bytes, 16-byte aligned.  Errors: EINVAL, EUNSUPPORTED (n_sub >
+ * CISCVX_MAX_VJP_SUBSTEPS in some default-model instance), ECUDA. */
 ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_vjp_io* io,
                                           void* workspace, size_t ws_bytes, void* stream);
 
