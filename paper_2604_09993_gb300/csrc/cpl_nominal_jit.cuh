@@ -14,7 +14,11 @@
 //    tangents need are taken in the tangent precision.
 // The stored stage slopes, K, the quadrature rows and the lever arms sit in
 // shared memory (element major); the live rows, stage values, generalized
-// forces and sin/cos stay in registers.
+// forces and sin/cos stay in registers.  Under RKF45 only the slopes of the
+// live rows that are not kinematic are stored: theta and the contact links'
+// p have the slope s v, so their stage values are
+// x0 + h s c_j v0 + h^2 s sum_m (A^2)_jm k_m(v) and their substep update is
+// h s v0 + h^2 s sum_m beta_m k_m(v), beta = b^T A.
 constexpr int SCH = CPL_SCH;
 constexpr int NW = CPL_NW;
 constexpr int BLK = 32 * NW;
@@ -22,7 +26,8 @@ constexpr int NSTG = SCH ? 6 : 4;
 constexpr int NKS = SCH ? 5 : 1;
 constexpr int NQ = 3 * NB;
 // shared-memory elements per lane
-constexpr int E_K = 0, E_KST = E_K + NSKY, E_ACC = E_KST + NKS * NL,
+constexpr int NKR = SCH ? NLD : NL;  // rows whose slopes are stored
+constexpr int E_K = 0, E_KST = E_K + NSKY, E_ACC = E_KST + NKS * NKR,
               E_XQ = E_ACC + (NKS == 1 ? NL : 0), E_ARM = E_XQ + NQD, E_SIZE = E_ARM + 4 * NJ;
 
 struct NumN {
@@ -103,11 +108,19 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
       for (int l = 0; l < NL; ++l) xs[l] = 0.0;
       if (SCH) {
         for (int m = 0; m < j; ++m) {
-          const double ah = TABD_A(j, m) * h;
-          if (ah == 0.0) continue;
+          const double ah = TABD_A(j, m) * h, a2h = TABD_A2(j, m) * (h * h * sk);
 #pragma unroll
-          for (int l = 0; l < NL; ++l) xs[l] = fma(ah, SE(E_KST + m * NL + l), xs[l]);
+          for (int l = 0; l < NL; ++l) {
+            if (LVEL[l] < 0) {
+              if (ah != 0.0) xs[l] = fma(ah, SE(E_KST + m * NKR + LDYN[l]), xs[l]);
+            } else if (a2h != 0.0) {
+              xs[l] = fma(a2h, SE(E_KST + m * NKR + LDYN[LVEL[l]]), xs[l]);
+            }
+          }
         }
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+          if (LVEL[l] >= 0) xs[l] = fma(h * sk * TABD_C[j], xl[LVEL[l]], xs[l]);
       } else if (j > 0) {
         const double ah = TABD_A(j, j - 1) * h;
 #pragma unroll
@@ -134,13 +147,23 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
             const double acc = (j == 0) ? bj * kv : fma(bj, kv, SE(E_ACC + l));
             if (j < NSTG - 1) SE(E_ACC + l) = acc;
             else xl[l] = fma(h, acc, xl[l]);
+          } else if (LVEL[l] >= 0) {
+            // kinematic: from the velocity's stored slopes; the velocity's own
+            // update comes later in this stage (its rows are emitted after)
+            if (j == NSTG - 1) {
+              double acc = 0.0;
+#pragma unroll
+              for (int m = NSTG - 2; m >= 0; --m)
+                if (TABD_BETA[m] != 0.0) acc = fma(TABD_BETA[m], SE(E_KST + m * NKR + LDYN[LVEL[l]]), acc);
+              xl[l] = fma(h * sk, fma(h, acc, xl[LVEL[l]]), xl[l]);
+            }
           } else if (j < NSTG - 1) {
-            SE(E_KST + j * NL + l) = kv;
+            SE(E_KST + j * NKR + LDYN[l]) = kv;
           } else {
             double acc = bj * kv;
 #pragma unroll
             for (int m = NSTG - 2; m >= 0; --m)
-              if (m != 1) acc = fma(TABD_B[m], SE(E_KST + m * NL + l), acc);
+              if (m != 1) acc = fma(TABD_B[m], SE(E_KST + m * NKR + LDYN[l]), acc);
             xl[l] = fma(h, acc, xl[l]);
           }
         } else {

@@ -139,6 +139,18 @@ std::string prelude(const CplTab& T, int prec, int bs) {
   }
   arr(o, "LINV", linv.data(), T.nlive);
   arr(o, "QINV", qinv.data(), T.nquad);
+  // live rows whose derivative is a live velocity (theta, and p of contact
+  // links): LVEL = the velocity's live index; the others are numbered by LDYN
+  std::vector<int> ldyn(T.nlive, -1), lvel(T.nlive, -1);
+  int nld = 0;
+  for (int l = 0; l < T.nlive; ++l) {
+    const int r = linv[l];
+    if (r < 3 * T.nb && T.lrow[r + 3 * T.nb] >= 0) lvel[l] = T.lrow[r + 3 * T.nb];
+    else ldyn[l] = nld++;
+  }
+  o << "constexpr int NLD = " << nld << ";\n";
+  arr(o, "LDYN", ldyn.data(), T.nlive);
+  arr(o, "LVEL", lvel.data(), T.nlive);
   arr(o, "CPERM", T.cperm, T.cnt);
   double a[36];
   for (int i = 0; i < 6; ++i)
@@ -151,8 +163,17 @@ std::string prelude(const CplTab& T, int prec, int bs) {
   tab(o, "double", "TABD_B", T.b, 6);
   tab(o, "double", "TABD_C", T.c, 6);
   tab(o, "double", "TABD_BETA", T.beta, 6);
+  double a2[36];  // the tableau squared: a kinematic row's stage value from its velocity's slopes
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double v = 0.0;
+      for (int l = 0; l < 6; ++l) v += T.a[i][l] * T.a[l][j];
+      a2[6 * i + j] = v;
+    }
+  tab(o, "double", "TABD_A26", a2, 36);
   o << "#define TAB_A(j, m) TAB_A6[6 * (j) + (m)]\n";
   o << "#define TABD_A(j, m) TABD_A6[6 * (j) + (m)]\n";
+  o << "#define TABD_A2(j, m) TABD_A26[6 * (j) + (m)]\n";
   return o.str();
 }
 
@@ -175,8 +196,13 @@ const CplJit* cpl_jit_nominal(const CplTab& T, int prec) {
   if (env && env[0] == '0') return nullptr;
   // per lane: K's skyline, the stored slopes (plus the RK4 accumulator), the
   // quadrature rows and the lever arms, in doubles; one warp per block
+  // (RKF45 stores the slopes of the live rows that are not kinematic: theta
+  // and the contact links' p follow from their velocities' slopes)
   const int nks = T.scheme ? 5 : 1;
-  const size_t elems = (size_t)T.nsky + nks * T.nlive + (nks == 1 ? T.nlive : 0) + T.nquad + 4 * T.nj;
+  int nkin = 0;
+  for (int r = 0; r < 3 * T.nb; ++r) nkin += T.lrow[r] >= 0 && T.lrow[r + 3 * T.nb] >= 0;
+  const int nkr = T.scheme ? T.nlive - nkin : T.nlive;
+  const size_t elems = (size_t)T.nsky + nks * nkr + (nks == 1 ? T.nlive : 0) + T.nquad + 4 * T.nj;
   const size_t smem = elems * sizeof(double) * 32;
   if (smem > 200u * 1024u) return nullptr;
   std::string src = prelude(T, prec, 32) + "#define CPL_NW 1\n" + kCplNominalJitSrc;
