@@ -77,7 +77,7 @@ FLOPS_PER_INTERVAL = {
     ("cheetah7", 20, "vjp", "fp32_phi"): 29_457,
     ("cheetah7", 20, "discretize", "fp64"): 126_146,
     ("cheetah7", 20, "vjp", "fp64"): 82_621,
-    ("cheetah7", 20, "fused", "fp32_phi"): 31_045,
+    ("cheetah7", 20, "fused", "fp32_phi"): 31_046,
 }
 # DRAM bytes (read + write) per interval of each kernel from the same captures
 # (256 instances x 400 intervals; traffic scales with the intervals processed).
@@ -86,7 +86,7 @@ DRAM_BYTES_PER_INTERVAL = {
     ("cheetah7", 20, "vjp", "fp32_phi"): (249.1e6 + 155.8e6) / 102400,
     ("cheetah7", 20, "discretize", "fp64"): (407.3e6 + 3762.1e6) / 102400,
     ("cheetah7", 20, "vjp", "fp64"): (258.3e6 + 227.4e6) / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi"): (749.8e6 + 2639.7e6) / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi"): (756.6e6 + 2646.6e6) / 102400,
 }
 
 
