@@ -69,7 +69,7 @@ extern "C" {
 #endif
 
 #define CISCVX_VERSION_MAJOR 0
-#define CISCVX_VERSION_MINOR 8
+#define CISCVX_VERSION_MINOR 9
 
 typedef enum {
   CISCVX_OK = 0,
@@ -709,6 +709,11 @@ typedef struct {
   double scale_s, offset_s;                           /* scale_s 0 means 1 */
   const double* scale_phi; const double* offset_phi;  /* [2 n_c] */
   const double* scale_gam; const double* offset_gam;  /* [n_c] */
+  /* layout of the A, Bm, Bp inputs of ciscvx_socp_fill: CISCVX_OUT_DENSE, or
+   * CISCVX_OUT_COMPACT (their structural nonzeros in ciscvx_model_pattern
+   * order, as ciscvx_discretize_compact writes them; models with a pattern
+   * only) */
+  int phi_format;
 } ciscvx_socp_params;
 
 typedef struct {
@@ -726,7 +731,8 @@ typedef struct {
  * forces as inputs, one penalty state per contact: ciscvx_model_pattern),
  * dense otherwise.
  * Errors: EINVAL (nulls, N < 1, params invalid), EUNSUPPORTED (more than
- * 2^31 - 1 entries in a matrix), ENOMEM, ECUDA. */
+ * 2^31 - 1 entries in a matrix; compact inputs for a model without a
+ * pattern), ENOMEM, ECUDA. */
 ciscvx_status ciscvx_socp_create(const ciscvx_model* model, int N, int layout,
                                  const ciscvx_socp_params* params, ciscvx_socp** out);
 void ciscvx_socp_destroy(ciscvx_socp* socp);
@@ -751,7 +757,8 @@ typedef struct {
   const double* Phi;    /* [N+1][2 n_c] (NULL if n_c == 0) */
   const double* Gam;    /* [N+1][n_c]   (NULL if n_c == 0) */
   int phi_precision;    /* CISCVX_FP64 or CISCVX_FP32_PHI: type of A, Bm, Bp, S */
-  const void* A; const void* Bm; const void* Bp; const void* S;  /* dense, as ciscvx_discretize */
+  const void* A; const void* Bm; const void* Bp;  /* per the socp's phi_format */
+  const void* S;                                  /* [N][n_x~] */
   const double* defect; /* [N][n_x~] */
   const double* g;      /* [N+1][n_x~] and the Jacobian blocks of ciscvx_node_linearize */
   const double* Gvm; const double* Gth; const double* Gphi;

@@ -68,7 +68,7 @@ class _SocpParams(ctypes.Structure):
                 ("x_init", _dp), ("x_final", _dp), ("scale_x", _dp), ("offset_x", _dp),
                 ("scale_u", _dp), ("offset_u", _dp), ("scale_s", ctypes.c_double),
                 ("offset_s", ctypes.c_double), ("scale_phi", _dp), ("offset_phi", _dp),
-                ("scale_gam", _dp), ("offset_gam", _dp)]
+                ("scale_gam", _dp), ("offset_gam", _dp), ("phi_format", ctypes.c_int)]
 
 
 class _SocpDims(ctypes.Structure):
@@ -600,7 +600,7 @@ class Socp:
     "phi": ..., "gam": ...} (each entry optional)."""
 
     def __init__(self, model: Model, N: int, layout: str = "node", *, w_px, w_ep, w_torque, s_min, s_max,
-                 torque_max, x_init, x_final, scaling=None):
+                 torque_max, x_init, x_final, scaling=None, phi_format: str = "dense"):
         lib = load()
         self.model, self.N, self.layout = model, int(N), layout
         sc = scaling or {}
@@ -624,7 +624,7 @@ class Socp:
         prm = _SocpParams(float(w_px), float(w_ep), float(w_torque), float(s_min), float(s_max),
                           vec(torque_max, model.nj, "torque_max") if model.nj else None,
                           vec(x_init, nx, "x_init"), vec(x_final, nx, "x_final"), sx, ox, su, ou,
-                          float(ss or 0.0), float(os_ or 0.0), sp, op, sg, og)
+                          float(ss or 0.0), float(os_ or 0.0), sp, op, sg, og, FORMAT[phi_format])
         h = _vp()
         _check(lib.ciscvx_socp_create(model.handle, self.N, LAYOUT[layout], ctypes.byref(prm), ctypes.byref(h)))
         self._h = h

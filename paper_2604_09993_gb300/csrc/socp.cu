@@ -311,6 +311,8 @@ struct Builder {
   std::vector<int32_t> par, pac, pbr, pbc;
   std::vector<int> contact_body;
 
+  bool compact = false;  // A, Bm, Bp inputs hold the pattern's nonzeros only
+
   Builder(const DevModel& m, int N_, int layout) : M(m), N(N_) {
     nxt = M.nxt; nu = M.nu; nb = M.nb; nj = M.nj; nc = M.nc;
     nq = 3 * nb; nx = 6 * nb; ny = nxt - nx;
@@ -343,8 +345,8 @@ struct Builder {
   uint64_t desc(unsigned kind, long k, unsigned off, bool neg = false) const {
     long long blk = 0;
     switch (kind) {
-      case SRC_A: blk = (long long)nxt * nxt; break;
-      case SRC_BM: case SRC_BP: blk = (long long)nxt * nu; break;
+      case SRC_A: blk = compact ? (long long)M.nnzA : (long long)nxt * nxt; break;
+      case SRC_BM: case SRC_BP: blk = compact ? (long long)M.nnzB : (long long)nxt * nu; break;
       case SRC_S: blk = nxt; break;
       case SRC_GVM: blk = (long long)nq * nq; break;
       case SRC_GTH: blk = (long long)nq * nb; break;
@@ -467,20 +469,21 @@ struct Builder {
           const int row = A.begin_row(rdesc(R_DYN, k, (unsigned)r));
           if (has_pattern) {
             for (size_t e = 0; e < par.size(); ++e)
-              if (par[e] == r) A.add(row, c_xp[k] + pac[e], desc(SRC_A, k, (unsigned)(r * nxt + pac[e])));
+              if (par[e] == r)
+                A.add(row, c_xp[k] + pac[e], desc(SRC_A, k, (unsigned)(compact ? e : r * nxt + pac[e])));
           } else {
             for (int c = 0; c < nxt; ++c) A.add(row, c_xp[k] + c, desc(SRC_A, k, (unsigned)(r * nxt + c)));
           }
           A.add(row, c_xm[k + 1] + r, one(true));
-          auto badd = [&](int q) {
-            A.add(row, uL(k) + q, desc(SRC_BM, k, (unsigned)(r * nu + q)));
-            A.add(row, uR(k) + q, desc(SRC_BP, k, (unsigned)(r * nu + q)));
+          auto badd = [&](int q, unsigned off) {
+            A.add(row, uL(k) + q, desc(SRC_BM, k, off));
+            A.add(row, uR(k) + q, desc(SRC_BP, k, off));
           };
           if (has_pattern) {
             for (size_t e = 0; e < pbr.size(); ++e)
-              if (pbr[e] == r) badd(pbc[e]);
+              if (pbr[e] == r) badd(pbc[e], (unsigned)(compact ? e : r * nu + pbc[e]));
           } else {
-            for (int q = 0; q < nu; ++q) badd(q);
+            for (int q = 0; q < nu; ++q) badd(q, (unsigned)(r * nu + q));
           }
           A.add(row, c_s[k], desc(SRC_S, k, (unsigned)r));
           A.add(row, c_nuFp[k] + r, one(true));
@@ -574,6 +577,7 @@ T* upload(const std::vector<T>& v, cudaError_t& e) {
 
 struct ciscvx_socp {
   int N, layout, device;
+  int nnzA, nnzB;  // per-interval sizes of compact A and B- / B+ (0: dense)
   ciscvx_socp_dims dims;
   int nxt, nu, nb, nc, npsi, ny, nq;
   double w_px, w_ep;
@@ -755,7 +759,12 @@ ciscvx_status ciscvx_socp_create(const ciscvx_model* m, int N, int layout, const
       !finite_all(P->offset_gam, M.nc) || !std::isfinite(P->offset_s))
     return set_error(CISCVX_EINVAL, "scales must be finite > 0 and offsets finite");
 
+  if (P->phi_format != CISCVX_OUT_DENSE && P->phi_format != CISCVX_OUT_COMPACT)
+    return set_error(CISCVX_EINVAL, "unknown phi_format %d", P->phi_format);
   Builder B(M, N, layout);
+  B.compact = P->phi_format == CISCVX_OUT_COMPACT;
+  if (B.compact && !B.has_pattern)
+    return set_error(CISCVX_EUNSUPPORTED, "compact inputs need a model with a structural pattern");
   B.columns(*P);
   B.rows(*P);
   const int n_var = (int)B.colz.size();
@@ -766,6 +775,8 @@ ciscvx_status ciscvx_socp_create(const ciscvx_model* m, int N, int layout, const
   so->N = N; so->layout = layout; so->device = m->device;
   so->nxt = M.nxt; so->nu = M.nu; so->nb = M.nb; so->nc = M.nc; so->npsi = B.npsi; so->ny = B.ny;
   so->nq = B.nq; so->w_px = P->w_px; so->w_ep = P->w_ep;
+  so->nnzA = B.compact ? M.nnzA : 0;
+  so->nnzB = B.compact ? M.nnzB : 0;
 
   // objective: P = w_px on problem columns + the FOH torque cost, then D P D; P o
   std::map<std::pair<int, int>, double> Pm;  // (row, col), row <= col
@@ -875,9 +886,9 @@ ciscvx_status ciscvx_socp_fill(const ciscvx_socp* so, int n_inst, const ciscvx_s
     I.sp[k] = p;
     I.ss[k] = stride;
   };
-  src(SRC_A, in->A, N * nxt * nxt);
-  src(SRC_BM, in->Bm, N * nxt * nu);
-  src(SRC_BP, in->Bp, N * nxt * nu);
+  src(SRC_A, in->A, so->nnzA ? N * so->nnzA : N * nxt * nxt);
+  src(SRC_BM, in->Bm, so->nnzB ? N * so->nnzB : N * nxt * nu);
+  src(SRC_BP, in->Bp, so->nnzB ? N * so->nnzB : N * nxt * nu);
   src(SRC_S, in->S, N * nxt);
   src(SRC_GVM, in->Gvm, (N + 1) * nq * nq);
   src(SRC_GTH, in->Gth, (N + 1) * nq * nb);

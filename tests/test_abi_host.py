@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert lib.ciscvx_version() == 8
+    assert lib.ciscvx_version() == 9
 
 
 def test_null_arguments_rejected(lib):

@@ -272,3 +272,47 @@ def test_socp_fp32_inputs_widen_exactly(env):
     o64 = sp.fill(1, ins64, precision="fp64")
     for k in o32:
         assert torch.equal(o32[k], o64[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("layout", ["node", "interval"])
+def test_socp_from_compact_outputs(env, precision, layout):
+    """The fill from compact A / B- / B+ (ciscvx_discretize_compact) equals the
+    fill from the dense blocks bit for bit: the same values feed the same
+    arithmetic, only their addresses differ."""
+    torch, oracle, osocp, api = env
+    R = _robot("biped", "default")
+    m = api.Model(R)
+    rng = np.random.default_rng(21)
+    N, n_inst = 7, 3
+    prm = _params(m, rng)
+    its = [_iterate(m, N, layout, rng) for _ in range(n_inst)]
+    dense = _linearize(torch, api, m, layout, its, precision)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)  # noqa: E731
+    comp = dict(dense)
+    parts = {"A": [], "Bm": [], "Bp": []}
+    for Xp, Xm, U, s, Phi, Gam in its:
+        c = api.discretize_compact(m, t(Xp), t(U), t(s), NSUB, precision, layout)
+        for k in parts:
+            parts[k].append(c[k].reshape(-1))
+    for k in parts:
+        comp[k] = torch.cat(parts[k]).contiguous()
+    sd = _socp(api, m, N, layout, prm)
+    scaling = {k: (prm.get(f"scale_{k}"), prm.get(f"offset_{k}")) for k in ("x", "u", "phi", "gam")}
+    scaling["s"] = (prm.get("scale_s", 0.0), prm.get("offset_s", 0.0))
+    sc = api.Socp(m, N, layout, w_px=prm["w_px"], w_ep=prm["w_ep"], w_torque=prm["w_torque"],
+                  s_min=prm["s_min"], s_max=prm["s_max"], torque_max=prm["torque_max"],
+                  x_init=prm["x_init"], x_final=prm["x_final"], scaling=scaling, phi_format="compact")
+    assert sc.dims == sd.dims
+    o_d = sd.fill(n_inst, dense, precision=precision)
+    o_c = sc.fill(n_inst, comp, precision=precision)
+    for k in o_d:
+        assert torch.equal(o_d[k], o_c[k]), k
+    # a model without a structural pattern cannot take compact inputs
+    mc = api.Model(_robot("hopper", "cross"))
+    with pytest.raises(api.CiscvxError) as e:
+        api.Socp(mc, N, layout, w_px=1.0, w_ep=1.0, w_torque=0.0, s_min=0.0, s_max=1.0,
+                 torque_max=np.ones(mc.nj), x_init=np.zeros(6 * mc.nb), x_final=np.zeros(6 * mc.nb),
+                 phi_format="compact")
+    assert e.value.status == api.EUNSUPPORTED
