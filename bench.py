@@ -424,10 +424,19 @@ class SingleWorkload:
 L2_FLUSH = None
 
 
-def time_steps(torch, fn, steps, warmup, stream):
+def time_steps(torch, fn, steps, warmup, stream, name="timed"):
     """Seconds for `steps` calls of fn after `warmup` calls, CUDA events on the
     launching stream.  With L2_FLUSH set, L2 is flushed before every step,
-    outside the timed spans, and the spans are summed."""
+    outside the timed spans, and the spans are summed.  The whole measurement
+    is an NVTX range `name` (host-side marker; profilers can filter on it)."""
+    torch.cuda.nvtx.range_push(name)
+    try:
+        return _time_steps(torch, fn, steps, warmup, stream)
+    finally:
+        torch.cuda.nvtx.range_pop()
+
+
+def _time_steps(torch, fn, steps, warmup, stream):
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
@@ -557,7 +566,7 @@ def run_ours(args):
             out = api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, workspace=ws)
             fn = lambda: api.discretize(mp, Xp, Up, sp, pp.n_sub, pr, out=out, workspace=ws)  # noqa: E731
             barrier()
-            tp = time_steps(torch, fn, args.steps, args.warmup, stream)
+            tp = time_steps(torch, fn, args.steps, args.warmup, stream, name="paper dynamics: linearization")
             barrier()
             api.sync_status(mp)
             tp, = max_over_ranks([tp])
@@ -572,7 +581,7 @@ def run_ours(args):
             ws = torch.empty(max(lo, min(hi, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
             fv = lambda: api.discretize_vjp(mp, Xp, Up, sp, wv, rv, pp.n_sub, pr, workspace=ws)  # noqa: E731
             barrier()
-            tv = time_steps(torch, fv, max(1, args.steps // 2), args.warmup, stream)
+            tv = time_steps(torch, fv, max(1, args.steps // 2), args.warmup, stream, name="paper dynamics: VJP")
             barrier()
             api.sync_status(mp)
             tv, = max_over_ranks([tv])
@@ -613,7 +622,7 @@ def run_ours(args):
     if not args.no_fp64 and prec != "fp64":
         wl.prepare("fp64")
         barrier()
-        t64 = time_steps(torch, lambda: wl.step("fp64"), args.steps, args.warmup, stream)
+        t64 = time_steps(torch, lambda: wl.step("fp64"), args.steps, args.warmup, stream, name="FP64 comparator step")
         barrier()
         kd64 = kernel_time(torch, lambda: wl.disc("fp64"), 3, stream)
         t64, kd64 = max_over_ranks([t64, kd64])
@@ -624,7 +633,7 @@ def run_ours(args):
     barrier()
     with ClockSampler(lrank) as cs:
         barrier()
-        t = time_steps(torch, lambda: wl.step(prec), args.steps, args.warmup, stream)
+        t = time_steps(torch, lambda: wl.step(prec), args.steps, args.warmup, stream, name="headline step")
         barrier()
     clocks = cs.summary()
     # the linearization and the VJP as separate calls (each path on its own)
@@ -662,7 +671,7 @@ def run_ours(args):
         h2d, d2h = wl.e2e_setup(prec, fmt) if fmt != "dense" else wl.e2e_setup(prec)
         ke = max(1, args.steps // 2)
         step = (lambda: wl.e2e_step(prec, fmt)) if fmt != "dense" else (lambda: wl.e2e_step(prec))
-        te = time_steps(torch, step, ke, 1, stream)
+        te = time_steps(torch, step, ke, 1, stream, name="end to end")
         te, = max_over_ranks([te])
         wl.e2e_free()
         return {"value": units * ke / te, "unit": "intervals/s", "h2d_bytes_per_step": h2d,
@@ -676,7 +685,7 @@ def run_ours(args):
         wl.free(prec)
         n_nodes = wl.node_setup()
         barrier()
-        tn = time_steps(torch, wl.node_step, args.steps, args.warmup, stream)
+        tn = time_steps(torch, wl.node_step, args.steps, args.warmup, stream, name="node constraints")
         barrier()
         wl.check_status()
         tn, = max_over_ranks([tn])
@@ -700,7 +709,7 @@ def run_ours(args):
         po = api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4)
         barrier()
         tp = time_steps(torch, lambda: api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4, out=po), args.steps,
-                        args.warmup, stream)
+                        args.warmup, stream, name="Psi")
         barrier()
         api.sync_status(mp)
         tp, = max_over_ranks([tp])
@@ -722,7 +731,7 @@ def run_ours(args):
         info = wl.socp_setup(prec)
         if info is not None:
             barrier()
-            tq = time_steps(torch, wl.socp_step, args.steps, args.warmup, stream)
+            tq = time_steps(torch, wl.socp_step, args.steps, args.warmup, stream, name="SOCP canonicalization")
             barrier()
             wl.check_status()
             tq, = max_over_ranks([tq])
@@ -758,7 +767,7 @@ def run_ours(args):
         ox = px.alloc_outputs(dev)
         px.autotune(Xx, Ux, sx, out=ox)
         barrier()
-        tx = time_steps(torch, lambda: px.discretize(Xx, Ux, sx, out=ox), args.steps, args.warmup, stream)
+        tx = time_steps(torch, lambda: px.discretize(Xx, Ux, sx, out=ox), args.steps, args.warmup, stream, name="Eq. (12) model")
         barrier()
         px.sync_status()
         tx, = max_over_ranks([tx])
@@ -775,7 +784,7 @@ def run_ours(args):
         wl.prepare(prec, "compact")
         wl.step(prec, "compact")
         barrier()
-        tc = time_steps(torch, lambda: wl.step(prec, "compact"), args.steps, args.warmup, stream)
+        tc = time_steps(torch, lambda: wl.step(prec, "compact"), args.steps, args.warmup, stream, name="compact outputs")
         barrier()
         kdc = kernel_time(torch, lambda: wl.disc(prec, "compact"), 5, stream)
         wl.check_status()

@@ -14,6 +14,7 @@
 // once per set of buffers and replayed.  An autotuner times launch shapes.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -844,8 +845,51 @@ const ciscvx_tune kTuneCandidates[] = {
     {4, 0, 1, 0, 1}, {4, 0, 1, 0, 2},
 };
 
+// The tuner's choices can persist across processes in a text file named by
+// CISCVX_TUNE_CACHE: one line per key, "key<TAB>warps ctas lpt graph occupancy".
+// It is read once, at the first autotune of the process; every new choice is
+// appended.  Lines that do not parse into a valid tune are ignored.
+bool g_tune_file_read = false;
+
+const char* tune_file() {
+  const char* f = std::getenv("CISCVX_TUNE_CACHE");
+  return (f && f[0]) ? f : nullptr;
+}
+
+void read_tune_file() {  // g_tune_mu held
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = tune_file();
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[4096];
+  while (std::fgets(line, sizeof line, f)) {
+    char* tab = std::strchr(line, '\t');
+    if (!tab) continue;
+    *tab = '\0';
+    ciscvx_tune t{};
+    if (std::sscanf(tab + 1, "%d %d %d %d %d", &t.warps_per_cta, &t.ctas_per_sm, &t.lpt_order, &t.use_graph,
+                    &t.occupancy) == 5 &&
+        tune_ok(t))
+      g_tune_cache[line] = t;
+  }
+  std::fclose(f);
+}
+
+void append_tune_file(const std::string& key, const ciscvx_tune& t) {  // g_tune_mu held
+  const char* path = tune_file();
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s\t%d %d %d %d %d\n", key.c_str(), t.warps_per_cta, t.ctas_per_sm, t.lpt_order, t.use_graph,
+               t.occupancy);
+  std::fclose(f);
+}
+
 // Times launch() under every candidate written into *slot (warm-up + 2 timed
-// calls each), keeps the fastest there, caches it under `key`.
+// calls each), keeps the fastest there, caches it under `key` (and in the
+// CISCVX_TUNE_CACHE file, if set).
 template <class Launch>
 ciscvx_status autotune_slot(ciscvx_batch_plan* p, ciscvx_tune* slot, const std::string& tag,
                             cudaStream_t s, const Launch& launch, ciscvx_tune* chosen) {
@@ -855,6 +899,7 @@ ciscvx_status autotune_slot(ciscvx_batch_plan* p, ciscvx_tune* slot, const std::
   const std::string key = std::string(prop.name) + "|" + p->key + tag;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
+    read_tune_file();
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       *slot = it->second;
@@ -890,6 +935,7 @@ ciscvx_status autotune_slot(ciscvx_batch_plan* p, ciscvx_tune* slot, const std::
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = bt;
+    append_tune_file(key, bt);
   }
   if (chosen) *chosen = bt;
   return CISCVX_OK;

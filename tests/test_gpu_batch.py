@@ -390,3 +390,45 @@ def test_autotune_fused_keeps_results(env):
         assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= 1e-4
         assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
         assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
+
+
+_TUNE_SCRIPT = r"""
+import json, sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+from paper_2604_09993_gb300 import api, synth
+rng = np.random.default_rng(3)
+R = synth.hopper(rng)
+probs = [synth.draw_instance(R, rng, 20, 4, q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15)) for _ in range(5)]
+m = api.Model(R)
+plan = api.BatchPlan([m], [0] * 5, [q.N for q in probs], [q.n_sub for q in probs], precision="fp32_phi")
+t = lambda a: torch.tensor(a, device="cuda:0")
+X, U, s = t(plan.pack([q.X for q in probs], "X")), t(plan.pack([q.U for q in probs], "U")), t(plan.pack([q.s for q in probs], "s"))
+print(json.dumps(plan.autotune(X, U, s)))
+"""
+
+
+def test_tune_cache_file(env, tmp_path):
+    """CISCVX_TUNE_CACHE: a process's autotune choice is written to the file,
+    and the next process takes it from there instead of timing again (shown by
+    planting a different valid choice in the file)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    envv = dict(os.environ, CISCVX_TUNE_CACHE=str(cache))
+    script = _TUNE_SCRIPT.format(root=root)
+    r1 = subprocess.run([sys.executable, "-c", script], env=envv, capture_output=True, text=True, timeout=300)
+    assert r1.returncode == 0, r1.stderr[-2000:]
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and "\t" in lines[0]
+    key = lines[0].split("\t")[0]
+    cache.write_text(f"{key}\t2 6 1 0 1\nnot a tune line\n")
+    r2 = subprocess.run([sys.executable, "-c", script], env=envv, capture_output=True, text=True, timeout=300)
+    assert r2.returncode == 0, r2.stderr[-2000:]
+    t2 = json.loads(r2.stdout.strip().splitlines()[-1])
+    assert (t2["warps_per_cta"], t2["ctas_per_sm"], t2["lpt_order"], t2["occupancy"]) == (2, 6, 1, 1)
+    assert len(cache.read_text().splitlines()) == 2   # nothing re-timed, nothing appended
