@@ -6,18 +6,24 @@
 //
 // Two phases.  The symbolic phase (host, once per (model, N, layout)) lays out
 // the columns and rows and lists every structural entry with a 64-bit source
-// descriptor: which output block of which interval or node holds its value,
-// or a constant.  It keeps the entries both row by row (for the row pass) and
-// sorted into CSC order (for the value pass), and precomputes everything that
-// does not depend on the iterate: the column scales and offsets, P and P o.
-// The numeric phase (device, per call, any number of instances of that shape):
-//   rows:   block per (instance, chunk of whole rows): entry terms into shared
-//           memory, then per row its scaled max-norm over the problem columns
-//           -> rho, and b (or h) = rho (J zbar - residual - J o)
-//   values: thread per (instance, CSC entry): source * D[col] * rho[row]
-//   c:      thread per (instance, column): D (P o - w_px zbar), or w_ep
+// descriptor: which output array holds its value, at which offset within one
+// instance's part, or a constant.  It keeps the rows that depend on the
+// iterate in a SELL-32 view (for the row pass) and all entries sorted into CSC
+// order (for the value pass), and precomputes everything that does not depend
+// on the iterate: the column scales and offsets, P, P o, and the scales and
+// right-hand sides of the rows made of constants.
+// The numeric phase (device, per call, any number of instances of that shape,
+// IPB instances per thread):
+//   zhat:   thread per column: the scaled iterate (zbar - o) / D, into c
+//   rows:   thread per linearized row: rho = 1 / max |value D| over its
+//           problem-variable entries, and rho (sum value D zhat - residual)
+//   fixed:  the precomputed rho and right-hand side of the constant rows
+//   values: thread per CSC entry: value * D[col] * rho[row]
+//   c:      thread per column: D (P o - w_px zbar), or w_ep
 // The descriptors are shared by all instances and stay in L2; every output is
-// written once, coalesced.
+// written once, coalesced.  FP64 throughout; the FP64 pipe bounds the row and
+// value passes, so FP32 sources are widened and signs flipped on the integer
+// pipe.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -75,7 +81,6 @@ struct MatDev {
   const int* crow;           // [nnz] row of each CSC entry
   const uint64_t* csrc;      // [nnz] source of each CSC entry
   const double* cscale;      // [nnz] D[col] (constants: the signed value times D[col])
-  int soc0;                  // first row of the Q^2 blocks (rows pair up from here), or nrow
 };
 
 
@@ -690,7 +695,6 @@ bool finish(const HostMat& H, const Builder& B, std::vector<int>& colptr, std::v
   for (int c = 0; c < n_var; ++c) colptr[c + 1] += colptr[c];
   T.nrow = H.nrow;
   T.nnz = nnz;
-  T.soc0 = soc0;
   T.n_lin = (int)lrow.size();
   T.n_fix = (int)frow.size();
   auto up = [&](auto& v) {
