@@ -138,10 +138,9 @@ typedef struct {
  *     at y index 4 i .. 4 i + 3, then one path-penalty state per contact at y
  *     index 4 n_c + i integrating h(-phi_n) + h(-phi) + h(-gamma) + h(-rho^c)
  *     (n_y = 5 n_c).  The penalty output is the increment of the path-penalty
- *     states.  Provided for the dense linearization (single and batch, z
- *     formed from the dense outputs) and the single-instance VJP
- *     (linearize-and-contract, also inside batch plans); compact outputs
- *     return CISCVX_EUNSUPPORTED for it. */
+ *     states.  Provided for the dense and compact linearization (single
+ *     and batch; z formed from the dense outputs, not provided with compact
+ *     ones) and the VJP (linearize-and-contract, also inside batch plans). */
 typedef enum { CISCVX_AUX_PENALTY = 0, CISCVX_AUX_CROSS = 1 } ciscvx_aux_model;
 
 /* Joint reaction forces (Sec. II-A).
@@ -221,13 +220,22 @@ ciscvx_status ciscvx_model_dims(const ciscvx_model* model, int* n_x, int* n_y, i
  *   A: for each link b in order: (px,px) (px,vx) (py,py) (py,vy) (th,th)
  *      (th,om) (vx,vx) (vy,vy) (om,th) (om,om), then, if a contact sits on
  *      b, (y,py) (y,th) (y,vy) (y,om) (y,y); px/py/th = rows 3b, 3b+1, 3b+2,
- *      vx/vy/om = rows 3n_b + 3b + (0, 1, 2), y = row 6n_b + (contact index);
+ *      vx/vy/om = rows 3n_b + 3b + (0, 1, 2), y = the contact's path-penalty
+ *      row (6n_b + contact index; CISCVX_AUX_CROSS: 6n_b + 4n_c + contact
+ *      index); CISCVX_AUX_CROSS then adds, for the contact's rows
+ *      c0..c3 = 6n_b + 4 (contact index) + (0..3) (phi_n, lambda^c, gamma,
+ *      rho^c): (c0,c0) (c1,c1) (c2,c2) (c3,c3) (c1,vx) (c1,th) (c1,om);
  *   B: for each link b in order, for each input q acting on b (for each
  *      joint j in increasing index that has b as parent or child: tau_j,
- *      lambda_jx, lambda_jy; then, if a contact sits on b, its lambda_n,
- *      lambda_t+, lambda_t-): (px,q) if q has an x force component,
- *      (py,q) if a y component, (th,q), (vx,q) if x, (vy,q) if y, (om,q),
- *      then (y,q) if a contact sits on b.
+ *      lambda_jx, lambda_jy; then, if a contact sits on b, its contact
+ *      inputs in order): (px,q) if q has an x force component, (py,q) if a
+ *      y component, (th,q) if q exerts a torque on b, (vx,q) if x, (vy,q) if
+ *      y, (om,q) if a torque, then (y,q) if a contact sits on b;
+ *      CISCVX_AUX_CROSS then adds, after the groups of a foot link, (c1,q)
+ *      for each of its inputs in the same order that has an x component or
+ *      a torque or is phi_t or gamma, then (c0,phi_n) (c2,gamma) (c3,phi_t)
+ *      (c3,phi_n).  (gamma exerts no force: it has only the (y,gamma),
+ *      (c1,gamma) and (c2,gamma) entries.)
  * Call with NULL arrays to get the counts; then a_row/a_col receive nnz_A
  * and b_row/b_col nnz_B int32 indices (host memory, caller-owned).  Any of
  * nnz_a, nnz_b may be NULL.  Errors: as ciscvx_model_create for the

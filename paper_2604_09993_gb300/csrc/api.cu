@@ -36,6 +36,17 @@ ciscvx_status ok() {
 
 bool finite2(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]); }
 
+// Input i of link B exerts a torque on it (the Eq. (12) model's gamma exerts
+// no force at all).
+bool input_torque(const DevBody& B, int i) { return B.p[i] != 0.0 || B.q[i] != 0.0 || B.t[i] != 0.0; }
+
+// Input i of a foot link enters its contact's lambda^c row (Eq. (12) model):
+// through v_x or the rotation, or directly (phi_t, gamma).
+bool input_lambda(const DevBody& B, int i) {
+  const int d = B.idx[i] - B.cin;
+  return B.ax[i] != 0.0 || input_torque(B, i) || d == 0 || d == 2;
+}
+
 // Adds input `q` acting on link `b` with the given coefficients.
 ciscvx_status add_input(DevModel& M, int b, int q, double ax, double ay, double p, double qq,
                         double t) {
@@ -215,11 +226,17 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   int aoff = 0, boff = 0;
   for (int b = 0; b < nb; ++b) {
     DevBody& B = M.body[b];
+    const bool cross = M.aux && B.contact >= 0;
     B.a_off = aoff;
     B.b_off = boff;
-    aoff += A_PER_LINK + (B.contact >= 0 ? A_PER_FOOT : 0);
+    aoff += A_PER_LINK + (B.contact >= 0 ? A_PER_FOOT : 0) + (cross ? A_PER_CROSS : 0);
     for (int i = 0; i < B.nin; ++i)
-      boff += 2 + (B.ax[i] != 0.0 ? 2 : 0) + (B.ay[i] != 0.0 ? 2 : 0) + (B.contact >= 0 ? 1 : 0);
+      boff += (input_torque(B, i) ? 2 : 0) + (B.ax[i] != 0.0 ? 2 : 0) + (B.ay[i] != 0.0 ? 2 : 0) +
+              (B.contact >= 0 ? 1 : 0);
+    if (cross) {
+      for (int i = 0; i < B.nin; ++i) boff += input_lambda(B, i) ? 1 : 0;
+      boff += B_CROSS_FIXED;
+    }
   }
   M.nnzA = aoff;
   M.nnzB = boff;
@@ -254,31 +271,44 @@ void fill_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int3
   const int nb = M.nb;
   for (int b = 0; b < nb; ++b) {
     const DevBody& B = M.body[b];
+    const bool cross = M.aux && B.contact >= 0;
     const int px = 3 * b, py = px + 1, th = px + 2;
     const int vx = 3 * nb + 3 * b, vy = vx + 1, om = vx + 2;
-    const int y = B.contact >= 0 ? 6 * nb + B.contact : -1;
-    const int arow[15] = {px, px, py, py, th, th, vx, vy, om, om, y, y, y, y, y};
-    const int acol[15] = {px, vx, py, vy, th, om, vx, vy, th, om, py, th, vy, om, y};
-    const int na = A_PER_LINK + (y >= 0 ? A_PER_FOOT : 0);
+    // the contact's path-penalty row, and (Eq. (12) model) its first cross row
+    const int y = B.contact >= 0 ? 6 * nb + (M.aux ? 4 * M.nc : 0) + B.contact : -1;
+    const int c0 = cross ? 6 * nb + 4 * B.contact : -1;
+    const int arow[22] = {px, px, py, py, th, th, vx, vy, om, om, y, y, y, y, y,
+                          c0, c0 + 1, c0 + 2, c0 + 3, c0 + 1, c0 + 1, c0 + 1};
+    const int acol[22] = {px, vx, py, vy, th, om, vx, vy, th, om, py, th, vy, om, y,
+                          c0, c0 + 1, c0 + 2, c0 + 3, vx, th, om};
+    const int na = A_PER_LINK + (y >= 0 ? A_PER_FOOT : 0) + (cross ? A_PER_CROSS : 0);
     for (int j = 0; j < na; ++j) {
       if (ar) ar[B.a_off + j] = arow[j];
       if (ac) ac[B.a_off + j] = acol[j];
     }
     int o = B.b_off;
+    auto put = [&](int r, int q) {
+      if (br) br[o] = r;
+      if (bc) bc[o] = q;
+      ++o;
+    };
     for (int i = 0; i < B.nin; ++i) {
-      const bool nx = B.ax[i] != 0.0, ny = B.ay[i] != 0.0;
-      int rows[7], n = 0;
-      if (nx) rows[n++] = px;
-      if (ny) rows[n++] = py;
-      rows[n++] = th;
-      if (nx) rows[n++] = vx;
-      if (ny) rows[n++] = vy;
-      rows[n++] = om;
-      if (y >= 0) rows[n++] = y;
-      for (int t = 0; t < n; ++t, ++o) {
-        if (br) br[o] = rows[t];
-        if (bc) bc[o] = B.idx[i];
-      }
+      const bool nx = B.ax[i] != 0.0, ny = B.ay[i] != 0.0, tq = input_torque(B, i);
+      if (nx) put(px, B.idx[i]);
+      if (ny) put(py, B.idx[i]);
+      if (tq) put(th, B.idx[i]);
+      if (nx) put(vx, B.idx[i]);
+      if (ny) put(vy, B.idx[i]);
+      if (tq) put(om, B.idx[i]);
+      if (y >= 0) put(y, B.idx[i]);
+    }
+    if (cross) {
+      for (int i = 0; i < B.nin; ++i)
+        if (input_lambda(B, i)) put(c0 + 1, B.idx[i]);
+      put(c0, B.cin + 1);
+      put(c0 + 2, B.cin + 2);
+      put(c0 + 3, B.cin);
+      put(c0 + 3, B.cin + 1);
     }
   }
 }
@@ -383,7 +413,6 @@ ciscvx_status ciscvx_model_pattern(const ciscvx_model_desc* desc, int* nnz_a, in
   DevModel* M = new (std::nothrow) DevModel;
   if (!M) return fail(CISCVX_ENOMEM, "host allocation failed");
   st = build_tables(desc, *M);
-  if (st == CISCVX_OK && M->aux) st = fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
   if (st == CISCVX_OK && cpl_needed(*M))
     st = fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for models with coupled links");
   if (st == CISCVX_OK) {
@@ -505,10 +534,11 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* m, int N, int n_sub,
   if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
   if (m->host.nnzB > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
-  if (m->host.aux) return fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
   if (m->cpl) return fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for models with coupled links");
-  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, true, false, X, U,
-                                    s, A, Bm, Bp, S, defect, penalty, z, m->status,
+  if (m->host.aux && z)
+    return fail(CISCVX_EUNSUPPORTED, "z with compact outputs is not provided for the Eq. (12) model");
+  cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, true, m->host.aux != 0, X,
+                                    U, s, A, Bm, Bp, S, defect, penalty, z, m->status,
                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
   return ok();

@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCo
       TP* Sk = S + I.v + (size_t)k * nxt;
       double* dk = defect + I.v + (size_t)k * nxt;
       double* pk = penalty ? penalty + I.p + (size_t)k * nc : nullptr;
-      if (AUX && M.aux && M.body[b].contact >= 0)  // Eq. (12) model (dense outputs)
-        disc_link<TP, true, false, false, AUX>(M, b, g.y, s[I.s + k], Xi + k * nxt,
+      if (AUX && M.aux && M.body[b].contact >= 0)  // Eq. (12) model
+        disc_link<TP, true, CMP, false, AUX>(M, b, g.y, s[I.s + k], Xi + k * nxt,
                                                Xi + (k + 1) * nxt, uL, uR, Ak, Bmk, Bpk, Sk, dk,
                                                pk, nullptr, c.status);
       else if (M.body[b].contact >= 0)
@@ -404,15 +404,17 @@ cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const cisc
     else CISCVX_DISC1(TP, OCC, false);           \
   } while (0)
   const int occ = p->tune.occupancy;
-  if (p->any_aux) {  // Eq. (12) model in the batch: dense outputs, no register cap
-    if (p->prec == CISCVX_FP64)
-      k_batch_disc<double, 0, false, true><<<blocks, threads, 0, st>>>(
-          c, io->X, io->U, io->s, (double*)io->A, (double*)io->Bm, (double*)io->Bp,
-          (double*)io->S, io->defect, io->penalty);
-    else
-      k_batch_disc<float, 0, false, true><<<blocks, threads, 0, st>>>(
-          c, io->X, io->U, io->s, (float*)io->A, (float*)io->Bm, (float*)io->Bp, (float*)io->S,
-          io->defect, io->penalty);
+  if (p->any_aux) {  // Eq. (12) model in the batch: no register cap
+#define CISCVX_DISC_AUX(TP, CMP)                                                             \
+  k_batch_disc<TP, 0, CMP, true><<<blocks, threads, 0, st>>>(c, io->X, io->U, io->s, (TP*)io->A, \
+                                                             (TP*)io->Bm, (TP*)io->Bp, (TP*)io->S, \
+                                                             io->defect, io->penalty)
+    if (p->prec == CISCVX_FP64) {
+      if (p->compact) CISCVX_DISC_AUX(double, true); else CISCVX_DISC_AUX(double, false);
+    } else {
+      if (p->compact) CISCVX_DISC_AUX(float, true); else CISCVX_DISC_AUX(float, false);
+    }
+#undef CISCVX_DISC_AUX
     return cudaGetLastError();
   }
   if (p->prec == CISCVX_FP64) {
@@ -661,10 +663,6 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     }
   }
   z.L = (size_t)n_inst;
-  if (p->any_aux && p->compact) {
-    free_plan(p);
-    return set_error(CISCVX_EUNSUPPORTED, "compact outputs are not provided for the Eq. (12) model");
-  }
 
   // work decomposition of the whole batch (one chunk)
   HostDecomp dec = decompose(p, {0, n_inst});

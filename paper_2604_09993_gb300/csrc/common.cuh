@@ -64,13 +64,19 @@ struct DevBody {
 
 // Compact outputs keep only the structural nonzeros of A and B-/B+, per
 // interval, link by link (rows px, py, th, vx, vy, om of link b, y of its
-// contact).  Link b's A entries, at a_off: (px,px) (px,vx) (py,py) (py,vy)
-// (th,th) (th,om) (vx,vx) (vy,vy) (om,th) (om,om), then for a foot link
-// (y,py) (y,th) (y,vy) (y,om) (y,y).  Link b's B entries, at b_off, for each
-// of its inputs q in slot order: (px,q) if the input has an x force
-// component, (py,q) if it has a y component, (th,q), (vx,q) if x, (vy,q) if
-// y, (om,q), then (y,q) for a foot link.  B- and B+ share the pattern.
-constexpr int A_PER_LINK = 10, A_PER_FOOT = 5;
+// contact's path-penalty state).  Link b's A entries, at a_off: (px,px)
+// (px,vx) (py,py) (py,vy) (th,th) (th,om) (vx,vx) (vy,vy) (om,th) (om,om),
+// then for a foot link (y,py) (y,th) (y,vy) (y,om) (y,y).  Link b's B
+// entries, at b_off, for each of its inputs q in slot order: (px,q) if the
+// input has an x force component, (py,q) if it has a y component, (th,q) if
+// it exerts a torque, (vx,q) if x, (vy,q) if y, (om,q) if a torque, then
+// (y,q) for a foot link.  B- and B+ share the pattern.
+// Eq. (12) model (cross-complementarity rows c0..c3 = phi_n, lambda^c, gamma,
+// rho^c of the foot's contact): after the foot's A entries (c0,c0) (c1,c1)
+// (c2,c2) (c3,c3) (c1,vx) (c1,th) (c1,om); after the link's B groups one
+// (c1,q) per input in slot order that pushes along x, exerts a torque, or is
+// phi_t or gamma, then (c0,phi_n) (c2,gamma) (c3,phi_t) (c3,phi_n).
+constexpr int A_PER_LINK = 10, A_PER_FOOT = 5, A_PER_CROSS = 7, B_CROSS_FIXED = 4;
 
 // One instance of a batch: model, horizon, substeps and its element offsets
 // into the packed arrays.

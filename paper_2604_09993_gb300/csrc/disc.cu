@@ -44,9 +44,9 @@ __global__ void __launch_bounds__(128) k_discretize(const DevModel* __restrict__
   double* pk = penalty ? penalty + (size_t)k * nc : nullptr;
   double* zk = z ? z + (size_t)k * nxt : nullptr;
   if constexpr (AUX) {
-    if (M.body[b].contact >= 0) {  // Eq. (12) model (no z, dense outputs)
-      disc_link<TP, true, false, false, true>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL,
-                                              uR, Ak, Bmk, Bpk, Sk, dk, pk, nullptr, status);
+    if (M.body[b].contact >= 0) {  // Eq. (12) model (z from the dense outputs, by the caller)
+      disc_link<TP, true, CMP, false, true>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL,
+                                            uR, Ak, Bmk, Bpk, Sk, dk, pk, nullptr, status);
       return;
     }
   }
@@ -69,15 +69,16 @@ cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int p
 #define CISCVX_K(TP, CMP)                                                                    \
   k_discretize<TP, CMP><<<(unsigned)blocks, threads, 0, st>>>(                                \
       dM, N, nsub, layout, X, U, s, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, defect, penalty, z, status)
-  if (aux) {  // Eq. (12) model: dense outputs, no z (checked by the caller)
-    if (prec == CISCVX_FP64)
-      k_discretize<double, false, true><<<(unsigned)blocks, threads, 0, st>>>(
-          dM, N, nsub, layout, X, U, s, (double*)A, (double*)Bm, (double*)Bp, (double*)S, defect,
-          penalty, nullptr, status);
-    else
-      k_discretize<float, false, true><<<(unsigned)blocks, threads, 0, st>>>(
-          dM, N, nsub, layout, X, U, s, (float*)A, (float*)Bm, (float*)Bp, (float*)S, defect,
-          penalty, nullptr, status);
+  if (aux) {  // Eq. (12) model: the kernels form no z (the caller does, from dense outputs)
+#define CISCVX_KA(TP, CMP)                                                                    \
+  k_discretize<TP, CMP, true><<<(unsigned)blocks, threads, 0, st>>>(                          \
+      dM, N, nsub, layout, X, U, s, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, defect, penalty, nullptr, status)
+    if (prec == CISCVX_FP64) {
+      if (compact) CISCVX_KA(double, true); else CISCVX_KA(double, false);
+    } else {
+      if (compact) CISCVX_KA(float, true); else CISCVX_KA(float, false);
+    }
+#undef CISCVX_KA
   } else if (prec == CISCVX_FP64) {
     if (compact) CISCVX_K(double, true); else CISCVX_K(double, false);
   } else {

@@ -142,8 +142,10 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
                                           unsigned* status, Checkpoints* ck = nullptr) {
   constexpr bool F32 = std::is_same<TP, float>::value;
   // CROSS: the link carries a contact of the Eq. (12) model (see the header
-  // comment of input_cross); compact outputs and z are not provided for it.
-  static_assert(!(CROSS && (CMP || CK)), "Eq. (12) model: dense outputs only");
+  // comment of input_cross); the kernels form no z for it (callers form it
+  // from the dense outputs) and no checkpoints (its VJP is
+  // linearize-and-contract).
+  static_assert(!(CROSS && CK), "Eq. (12) model: no checkpoints");
   constexpr bool cross = FOOT && CROSS;
   const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
@@ -583,13 +585,15 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     zr[5] = om - double(S[rom]) * sd - double(tg.Pw[0]) * xk[rth] - double(tg.Pw[1]) * xk[rom];
   }
   // B-, B+: per input q of this link (slot order), entries in rows px (if the
-  // input pushes along x), py (along y), th, vx, vy, om, then y for a foot.
-  // nzx/nzy: the input has an x/y force component (tested on the bit pattern).
+  // input pushes along x), py (along y), th (if it exerts a torque), vx, vy,
+  // om (torque), then y for a foot.  nzx/nzy/tq: the input has an x / y force
+  // component / a torque (tested on the bit patterns).
+  auto torque = [&](int i) { return (abs_bits(B.p[i]) | abs_bits(B.q[i]) | abs_bits(B.t[i])) != 0ull; };
   if (nu > 0) {
     int o = B.b_off;
     for (int i = 0; i < nin; ++i) {
       const int q = B.idx[i];
-      const bool nzx = abs_bits(B.ax[i]) != 0ull, nzy = abs_bits(B.ay[i]) != 0ull;
+      const bool nzx = abs_bits(B.ax[i]) != 0ull, nzy = abs_bits(B.ay[i]) != 0ull, tq = torque(i);
       const TP ax = TP(B.ax[i]), ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
       const TP bmpx = ax * s2_3, bppx = ax * s2_6, bvx = ax * s_2;
       const TP bmpy = ay * s2_3, bppy = ay * s2_6, bvy = ay * s_2;
@@ -600,10 +604,10 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       if constexpr (CMP) {
         if (nzx) { Bm[o] = bmpx; Bp[o] = bppx; ++o; }
         if (nzy) { Bm[o] = bmpy; Bp[o] = bppy; ++o; }
-        Bm[o] = bmth; Bp[o] = bpth; ++o;
+        if (tq) { Bm[o] = bmth; Bp[o] = bpth; ++o; }
         if (nzx) { Bm[o] = bvx; Bp[o] = bvx; ++o; }
         if (nzy) { Bm[o] = bvy; Bp[o] = bvy; ++o; }
-        Bm[o] = bmom; Bp[o] = bpom; ++o;
+        if (tq) { Bm[o] = bmom; Bp[o] = bpom; ++o; }
         if (foot) ++o;  // the y entry, written below
       } else {
         Bm[(size_t)rpx * nu + q] = bmpx; Bp[(size_t)rpx * nu + q] = bppx;
@@ -657,7 +661,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         const int d = q - cin;
         if (d >= 0 && d < 3) { vm += tg.Yd[d]; vp += tg.Yd[3 + d]; }
         if constexpr (CMP) {
-          o += 3 + (abs_bits(B.ax[i]) != 0ull ? 2 : 0) + (abs_bits(B.ay[i]) != 0ull ? 2 : 0);
+          o += 1 + (torque(i) ? 2 : 0) + (abs_bits(B.ax[i]) != 0ull ? 2 : 0) + (abs_bits(B.ay[i]) != 0ull ? 2 : 0);
           Bm[o - 1] = vm;
           Bp[o - 1] = vp;
         } else {
@@ -676,26 +680,38 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     const double Ilg = Il + Ig;
     const double y1v[4] = {fma(sd, fn_m, xk[yb]), fma(sd, Ilg, xk[yb + 1]), fma(sd, ga_m, xk[yb + 2]),
                            fma(sd, Ir, xk[yb + 3])};
+    // compact: after the foot's 15 A entries (c_t,c_t) for t = 0..3, then
+    // (c1,vx) (c1,th) (c1,om)
+    constexpr int JA = A_PER_LINK + A_PER_FOOT;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       defect[yb + t] = y1v[t] - xk1[yb + t];
-      A[(size_t)(yb + t) * nxt + yb + t] = one;
+      a_put(yb + t, yb + t, JA + t, one);
       chk += y1v[t];
     }
-    TP* al = A + (size_t)(yb + 1) * nxt;
-    al[rvx] = sdT;
-    al[rth] = tg.Yl[0];
-    al[rom] = tg.Yl[1];
+    a_put(yb + 1, rvx, JA + 4, sdT);
+    a_put(yb + 1, rth, JA + 5, tg.Yl[0]);
+    a_put(yb + 1, rom, JA + 6, tg.Yl[1]);
     const TP Sl = TP(Ilg) + tg.Yl[2] + tg.Ylv[2];
     S[yb] = TP(fn_m); S[yb + 1] = Sl; S[yb + 2] = TP(ga_m); S[yb + 3] = TP(Ir);
     chk += double(Sl);
     if (nu > 0) {
-      Bm[(size_t)yb * nu + cin + 1] = s_2; Bp[(size_t)yb * nu + cin + 1] = s_2;
-      Bm[(size_t)(yb + 2) * nu + cin + 2] = s_2; Bp[(size_t)(yb + 2) * nu + cin + 2] = s_2;
-      Bm[(size_t)(yb + 3) * nu + cin] = tg.Yrd[0]; Bp[(size_t)(yb + 3) * nu + cin] = tg.Yrd[1];
-      Bm[(size_t)(yb + 3) * nu + cin + 1] = tg.Yrd[2]; Bp[(size_t)(yb + 3) * nu + cin + 1] = tg.Yrd[3];
-      TP* bm = Bm + (size_t)(yb + 1) * nu;
-      TP* bp = Bp + (size_t)(yb + 1) * nu;
+      // compact: after the link's input groups, (c1,q) for the inputs that
+      // enter lambda^c, then (c0,phi_n) (c2,gamma) (c3,phi_t) (c3,phi_n)
+      int o = B.b_off;
+      if constexpr (CMP)
+        for (int i = 0; i < nin; ++i)
+          o += 1 + (torque(i) ? 2 : 0) + (abs_bits(B.ax[i]) != 0ull ? 2 : 0) + (abs_bits(B.ay[i]) != 0ull ? 2 : 0);
+      auto b_put = [&](int r, int q, TP vm, TP vp) {
+        if constexpr (CMP) {
+          Bm[o] = vm;
+          Bp[o] = vp;
+          ++o;
+        } else {
+          Bm[(size_t)r * nu + q] = vm;
+          Bp[(size_t)r * nu + q] = vp;
+        }
+      };
       for (int i = 0; i < nin; ++i) {
         const int q = B.idx[i];
         const TP ax = TP(B.ax[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
@@ -704,9 +720,12 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         const int d = q - cin;
         if (d == 0) { vm += tg.Yld[0]; vp += tg.Yld[1]; }
         else if (d == 2) { vm += tg.Yld[2]; vp += tg.Yld[3]; }
-        bm[q] = vm;
-        bp[q] = vp;
+        if (!CMP || abs_bits(B.ax[i]) != 0ull || torque(i) || d == 0 || d == 2) b_put(yb + 1, q, vm, vp);
       }
+      b_put(yb, cin + 1, s_2, s_2);
+      b_put(yb + 2, cin + 2, s_2, s_2);
+      b_put(yb + 3, cin, tg.Yrd[0], tg.Yrd[1]);
+      b_put(yb + 3, cin + 1, tg.Yrd[2], tg.Yrd[3]);
     }
   }
   if (!finite_d(chk)) atomicOr(status, ST_NONFINITE);

@@ -71,7 +71,8 @@ def _single(env, p, precision, layout="node", want_z=False):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
-@pytest.mark.parametrize("case", ["hopper", "cheetah_n50", "biped_interval"])
+@pytest.mark.parametrize("case", ["hopper", "cheetah_n50", "biped_interval", "biped_cross",
+                                  "cheetah7_cross_interval"])
 def test_single_compact_vs_oracle_and_dense(env, precision, case):
     torch, oracle, api = env
     layout = "node"
@@ -79,6 +80,12 @@ def test_single_compact_vs_oracle_and_dense(env, precision, case):
         p = synth.hopper_fp64()
     elif case == "cheetah_n50":
         p = synth.cheetah_n50(seed=1)
+    elif case.endswith("_cross") or case.endswith("_cross_interval"):
+        # the Eq. (12) auxiliary state (four cross-complementarity rows per contact)
+        rng = np.random.default_rng(10)
+        robot = synth.with_cross_states(getattr(synth, case.split("_")[0])(rng))
+        p = synth.draw_instance(robot, rng, 41, 3, q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15))
+        layout = "interval" if case.endswith("_interval") else "node"
     else:
         rng = np.random.default_rng(8)
         robot = synth.biped(rng)
@@ -257,3 +264,50 @@ def test_batch_compact_run_host_one_chunk_identical(env):
     plan.sync_status()
     for k, v in ref.items():
         assert torch.equal(host_out[k], v.cpu()), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_batch_compact_both_aux_models(env, precision):
+    """A compact batch mixing both auxiliary models: against the dense plan at
+    the pattern and against the oracle."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(33)
+    robots = [synth.hopper(rng), synth.with_cross_states(synth.biped(rng)),
+              synth.with_cross_states(synth.cheetah7(rng))]
+    probs, midx = [], []
+    for i in range(10):
+        mi = i % 3
+        probs.append(synth.draw_instance(robots[mi], rng, int(rng.integers(1, 50)), int(rng.choice([2, 4])),
+                                         q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15)))
+        midx.append(mi)
+    models = [api.Model(r) for r in robots]
+    Ns, nss = [p.N for p in probs], [p.n_sub for p in probs]
+    pc = api.BatchPlan(models, midx, Ns, nss, precision=precision, out_format="compact")
+    pd = api.BatchPlan(models, midx, Ns, nss, precision=precision)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X = t(pc.pack([p.X for p in probs], "X"))
+    U = t(pc.pack([p.U for p in probs], "U"))
+    s = t(pc.pack([p.s for p in probs], "s"))
+    hc = {k: v.cpu() for k, v in pc.discretize(X, U, s).items()}
+    hd = {k: v.cpu() for k, v in pd.discretize(X, U, s).items()}
+    pc.sync_status()
+    pd.sync_status()
+    f32 = precision == "fp32_phi"
+    for i, (p, mi) in enumerate(zip(probs, midx)):
+        m = models[mi]
+        ar, ac, br, bc = m.pattern()
+        N, nxt, nu = p.N, m.nxt, m.nu
+        cA = pc.unpack(hc["A"], "A", i, (N, m.nnz_a))
+        cBm = pc.unpack(hc["Bm"], "B", i, (N, m.nnz_b))
+        cBp = pc.unpack(hc["Bp"], "B", i, (N, m.nnz_b))
+        dA = pd.unpack(hd["A"], "A", i, (N, nxt, nxt))
+        dBm = pd.unpack(hd["Bm"], "B", i, (N, nxt, nu))
+        _close(cA, dA[:, ar, ac], ("A", i), f32)
+        _close(cBm, dBm[:, br, bc], ("Bm", i), f32)
+        ref = oracle.discretize(p.robot.as_dict(), p.X, p.U, p.s, p.n_sub)
+        f = lambda a: np.asarray(a, dtype=np.float64)  # noqa: E731
+        got = {"A": f(cA), "Bm": f(cBm), "Bp": f(cBp), "S": f(pc.unpack(hc["S"], "S", i, (N, nxt))),
+               "defect": f(pc.unpack(hc["defect"], "defect", i, (N, nxt))),
+               "penalty": f(pc.unpack(hc["penalty"], "penalty", i, (N, m.nc)))}
+        _check_vs_oracle(got, ref, (ar, ac, br, bc), nxt, nu, precision)

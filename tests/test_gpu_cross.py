@@ -2,7 +2,8 @@
 the FP64 oracle through the C ABI: single-instance and batched linearization,
 both precisions and both control layouts, mixed batches of the two auxiliary
 models, feasible inputs, the linearize-and-contract VJP, and the entry points
-that return EUNSUPPORTED for it, and the affine term z formed from the outputs.
+that return EUNSUPPORTED for it (z with compact outputs), and the affine term z
+formed from the dense outputs.
 Tolerances as for the default model (FP64 1e-10; FP32-Phi blocks 1e-4,
 defect and penalty 1e-10)."""
 import numpy as np
@@ -132,12 +133,10 @@ def test_cross_unsupported_entry_points(env):
     m = api.Model(p.robot)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     X, U, s = t(p.X), t(p.U), t(p.s)
-    for call in (lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
-                 lambda: api.model_pattern(p.robot.as_dict()),
-                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
-        with pytest.raises(api.CiscvxError) as e:
-            call()
-        assert e.value.status == api.EUNSUPPORTED
+    # compact outputs are provided (tests/test_gpu_compact.py); z with them is not
+    with pytest.raises(api.CiscvxError) as e:
+        api.discretize_compact(m, X, U, s, p.n_sub, "fp64", want_z=True)
+    assert e.value.status == api.EUNSUPPORTED
 
 
 def test_cross_node_constraints(env):

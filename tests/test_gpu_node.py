@@ -31,6 +31,8 @@ def _robot(name):
     rng = np.random.default_rng(31)
     if name in ("hopper", "biped", "cheetah7"):
         return getattr(synth, name)(rng).as_dict()
+    if name.endswith("_cross"):  # the Eq. (12) auxiliary state (n_y = 5 n_c)
+        return synth.with_cross_states(getattr(synth, name[:-6])(rng)).as_dict()
     if name.endswith("_sine"):  # the sinusoidal contact surface of Sec. VI-B
         R = getattr(synth, name[:-5])(rng)
         return synth.with_paper_dynamics(R, joint_forces=0, scheme=0, terrain=synth.TERRAIN_SINE).as_dict()
@@ -38,10 +40,15 @@ def _robot(name):
     return _edge_robots()[name]
 
 
+def _nxt(R):
+    nb, nc = len(R["mass"]), len(R["contact_body"])
+    return 6 * nb + (5 if R.get("aux_model", 0) else 1) * nc
+
+
 def _inputs(R, n, seed):
     rng = np.random.default_rng(seed)
     nb, nc = len(R["mass"]), len(R["contact_body"])
-    nxt = 6 * nb + nc
+    nxt = _nxt(R)
     Xm = rng.uniform(-1, 1, (n, nxt))
     Xp = Xm + 0.5 * rng.standard_normal((n, nxt))
     Phi = rng.standard_normal((n, 2 * nc))
@@ -64,7 +71,7 @@ def _local_cols(R, nxt):
 
 def _node_errors(got, ref, R):
     nb, nc = len(R["mass"]), len(R["contact_body"])
-    nq, nxt = 3 * nb, 6 * nb + nc
+    nq, nxt = 3 * nb, _nxt(R)
     V = slice(nq, 2 * nq)
     J = ref["Jg"]
     blocks = {
@@ -101,7 +108,8 @@ def _run(env, R, n, seed, delta=1e-3, jacobians=True):
 
 @pytest.mark.parametrize("name,n", [("hopper", 45), ("biped", 70), ("cheetah7", 101),
                                     ("no_contact", 33), ("lone_link", 5), ("hopper_sine", 40),
-                                    ("biped_sine", 66), ("cheetah7_sine", 99)])
+                                    ("biped_sine", 66), ("cheetah7_sine", 99), ("hopper_cross", 37),
+                                    ("cheetah7_cross", 64)])
 def test_node_linearize_matches_oracle(env, name, n):
     R = _robot(name)
     got, ref = _run(env, R, n, seed=n)

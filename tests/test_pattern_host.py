@@ -30,6 +30,9 @@ def _robots():
     rng = np.random.default_rng(21)
     out = {"hopper": synth.hopper(rng), "biped": synth.biped(rng), "cheetah7": synth.cheetah7(rng)}
     out.update(_edge_robots())
+    # the Eq. (12) auxiliary state: four cross-complementarity rows per contact
+    for name in ("hopper", "biped", "cheetah7"):
+        out[name + "_cross"] = synth.with_cross_states(out[name])
     return out
 
 
@@ -43,30 +46,52 @@ def _documented_order(R):
     jp, jc = np.asarray(R["joint_parent"]), np.asarray(R["joint_child"])
     nj = len(jp)
     cb = list(np.asarray(R["contact_body"]))
+    nc = len(cb)
+    cross = bool(R.get("aux_model", 0))
     a, b = [], []
     for k in range(nb):
         px, py, th = 3 * k, 3 * k + 1, 3 * k + 2
         vx, vy, om = 3 * nb + 3 * k, 3 * nb + 3 * k + 1, 3 * nb + 3 * k + 2
-        y = 6 * nb + cb.index(k) if k in cb else None
+        foot = k in cb
+        # the contact's path-penalty row comes after the 4 n_c cross rows in the Eq. (12) model
+        y = 6 * nb + (4 * nc if cross else 0) + cb.index(k) if foot else None
         a += [(px, px), (px, vx), (py, py), (py, vy), (th, th), (th, om), (vx, vx), (vy, vy),
               (om, th), (om, om)]
-        if y is not None:
+        if foot:
             a += [(y, py), (y, th), (y, vy), (y, om), (y, y)]
-        inputs = []  # (column, has x force, has y force)
+        inputs = []  # (column, x force, y force, torque, enters lambda^c directly)
         for j in range(nj):
             if k in (jp[j], jc[j]):
-                inputs += [(j, False, False), (nj + 2 * j, True, False), (nj + 2 * j + 1, False, True)]
-        if y is not None:
+                inputs += [(j, False, False, True, False), (nj + 2 * j, True, False, True, False),
+                           (nj + 2 * j + 1, False, True, True, False)]
+        if foot:
             c0 = 3 * nj + 3 * cb.index(k)
-            inputs += [(c0, False, True), (c0 + 1, True, False), (c0 + 2, True, False)]
-        for q, fx, fy in inputs:
-            rows = ([px] if fx else []) + ([py] if fy else []) + [th] + ([vx] if fx else []) + \
-                   ([vy] if fy else []) + [om] + ([y] if y is not None else [])
+            if cross:   # phi_t (x force), phi_n (y force), gamma (no force)
+                inputs += [(c0, True, False, True, True), (c0 + 1, False, True, True, False),
+                           (c0 + 2, False, False, False, True)]
+            else:       # lambda_n (y), lambda_t+ (x), lambda_t- (x)
+                inputs += [(c0, False, True, True, False), (c0 + 1, True, False, True, False),
+                           (c0 + 2, True, False, True, False)]
+        for q, fx, fy, tq, _ in inputs:
+            rows = ([px] if fx else []) + ([py] if fy else []) + ([th] if tq else []) + \
+                   ([vx] if fx else []) + ([vy] if fy else []) + ([om] if tq else []) + \
+                   ([y] if foot else [])
             b += [(r, q) for r in rows]
+        if foot and cross:   # rows phi_n, lambda^c, gamma, rho^c of the contact
+            r0 = 6 * nb + 4 * cb.index(k)
+            a += [(r0, r0), (r0 + 1, r0 + 1), (r0 + 2, r0 + 2), (r0 + 3, r0 + 3),
+                  (r0 + 1, vx), (r0 + 1, th), (r0 + 1, om)]
+            b += [(r0 + 1, q) for q, fx, fy, tq, direct in inputs if fx or tq or direct]
+            c0 = 3 * nj + 3 * cb.index(k)
+            b += [(r0, c0 + 1), (r0 + 2, c0 + 2), (r0 + 3, c0), (r0 + 3, c0 + 1)]
     return a, b
 
 
-@pytest.mark.parametrize("name", ["hopper", "biped", "cheetah7", "no_contact", "lone_link"])
+NAMES = ["hopper", "biped", "cheetah7", "no_contact", "lone_link", "hopper_cross", "biped_cross",
+         "cheetah7_cross"]
+
+
+@pytest.mark.parametrize("name", NAMES)
 def test_pattern_order_and_counts(env, name):
     oracle, api = env
     R = _as_dict(_robots()[name])
@@ -76,17 +101,17 @@ def test_pattern_order_and_counts(env, name):
     assert list(zip(br.tolist(), bc.tolist())) == b
     assert len(set(a)) == len(a) and len(set(b)) == len(b)
     nb, nc = len(R["mass"]), len(R["contact_body"])
-    assert len(a) == 10 * nb + 5 * nc
+    assert len(a) == 10 * nb + (12 if R.get("aux_model", 0) else 5) * nc
 
 
-@pytest.mark.parametrize("name", ["hopper", "biped", "cheetah7", "no_contact", "lone_link"])
+@pytest.mark.parametrize("name", NAMES)
 def test_pattern_matches_oracle_nonzeros(env, name):
     """Oracle nonzeros (union over intervals) == pattern, on inputs that make
     every penalty term active somewhere (feet below ground, negative forces)."""
     oracle, api = env
     R = _as_dict(_robots()[name])
     nb, nj, nc = len(R["mass"]), len(R["joint_parent"]), len(R["contact_body"])
-    nxt, nu = 6 * nb + nc, 3 * nj + 3 * nc
+    nxt, nu = 6 * nb + (5 if R.get("aux_model", 0) else 1) * nc, 3 * nj + 3 * nc
     rng = np.random.default_rng(5)
     N, n_sub = 24, 3
     X = rng.uniform(-0.6, 0.6, (N + 1, nxt))
