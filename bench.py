@@ -771,10 +771,24 @@ def run_ours(args):
         barrier()
         px.sync_status()
         tx, = max_over_ranks([tx])
-        cross = {"metric": "linearized intervals/s (STM only; the VJP is not provided for this model)",
+        cross = {"metric": "linearized intervals/s (STM; this model's VJP is linearize-and-contract)",
                  "value": units * args.steps / tx, "unit": "intervals/s",
                  "ms_per_step": tx / args.steps * 1e3, "n_y": mx[0].ny, "tune": px.tune()}
-        del ox, Xx, Ux, sx, px
+        del ox, px
+        torch.cuda.empty_cache()
+        # the same with compact outputs (the packing of X, U, s does not depend on the format)
+        pxc = api.BatchPlan(mx, bx.model_idx, bx.Ns, bx.n_subs, precision=prec, out_format="compact")
+        oxc = pxc.alloc_outputs(dev)
+        pxc.autotune(Xx, Ux, sx, out=oxc)
+        barrier()
+        txc = time_steps(torch, lambda: pxc.discretize(Xx, Ux, sx, out=oxc), args.steps, args.warmup, stream,
+                         name="Eq. (12) model, compact")
+        barrier()
+        pxc.sync_status()
+        txc, = max_over_ranks([txc])
+        cross["compact"] = {"value": units * args.steps / txc, "unit": "intervals/s",
+                            "ms_per_step": txc / args.steps * 1e3, "tune": pxc.tune()}
+        del oxc, Xx, Ux, sx, pxc
         torch.cuda.empty_cache()
 
     # the same step with compact outputs (structural nonzeros of A, B-, B+ only)
