@@ -446,15 +446,23 @@ ciscvx_status ciscvx_batch_get_tune(const ciscvx_batch_plan* plan, ciscvx_tune* 
 ciscvx_status ciscvx_batch_discretize(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
                                       void* stream);
 
-/* Bytes of device scratch ciscvx_batch_discretize_vjp needs. */
+/* Bytes of device scratch ciscvx_batch_discretize_vjp needs (the minimum). */
 ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* plan, size_t* bytes);
+
+/* The minimum, and the size from which the instances of the Eq. (12) model
+ * and with coupled links take the batched linearize-and-contract pass (all
+ * their dense blocks in the workspace at once: one launch per kind instead
+ * of several per instance).  Equal when the plan has no such instances. */
+ciscvx_status ciscvx_batch_vjp_workspace_sizes(const ciscvx_batch_plan* plan, size_t* min_bytes,
+                                               size_t* full_bytes);
 
 /* VJP (as ciscvx_discretize_vjp) of every instance; L receives one value per
  * instance.  Default-model instances take the batched adjoint kernel;
  * instances of the Eq. (12) model or with coupled links are linearized and
- * contracted one after another in stream order (chunked in the last part of
- * the workspace).  workspace: device, >= ciscvx_batch_vjp_workspace_size
- * bytes, 16-byte aligned.  Errors: EINVAL, EUNSUPPORTED (n_sub >
+ * contracted: all at once when the workspace reaches the full size of
+ * ciscvx_batch_vjp_workspace_sizes, else one after another in stream order
+ * (chunked in the last part of the workspace).  workspace: device, >=
+ * ciscvx_batch_vjp_workspace_size bytes, 16-byte aligned.  Errors: EINVAL, EUNSUPPORTED (n_sub >
  * CISCVX_MAX_VJP_SUBSTEPS in some default-model instance), ECUDA. */
 ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_vjp_io* io,
                                           void* workspace, size_t ws_bytes, void* stream);

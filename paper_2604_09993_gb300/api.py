@@ -34,7 +34,7 @@ EXPORTS = (
     "ciscvx_node_linearize", "ciscvx_batch_discretize_and_vjp", "ciscvx_batch_autotune_fused",
     "ciscvx_batch_get_tune_fused", "ciscvx_discretize_workspace_size", "ciscvx_psi_rows",
     "ciscvx_psi_linearize", "ciscvx_socp_create", "ciscvx_socp_destroy", "ciscvx_socp_get_dims",
-    "ciscvx_socp_structure", "ciscvx_socp_fill",
+    "ciscvx_socp_structure", "ciscvx_socp_fill", "ciscvx_batch_vjp_workspace_sizes",
 )
 FORMAT = {"dense": 0, "compact": 1}
 
@@ -195,6 +195,7 @@ def load(path: str | None = None):
     lib.ciscvx_batch_get_tune.argtypes = [_vp, P(Tune)]
     lib.ciscvx_batch_discretize.argtypes = [_vp, P(_BatchIO), _vp]
     lib.ciscvx_batch_vjp_workspace_size.argtypes = [_vp, P(ctypes.c_size_t)]
+    lib.ciscvx_batch_vjp_workspace_sizes.argtypes = [_vp, P(ctypes.c_size_t), P(ctypes.c_size_t)]
     lib.ciscvx_batch_discretize_vjp.argtypes = [_vp, P(_BatchVjpIO), _vp, ctypes.c_size_t, _vp]
     lib.ciscvx_batch_autotune.argtypes = [_vp, P(_BatchIO), _vp, P(Tune)]
     lib.ciscvx_batch_discretize_and_vjp.argtypes = [_vp, P(_BatchIO), P(_BatchVjpIO), _vp,
@@ -357,6 +358,8 @@ def discretize_workspace_size(model: Model, N: int, n_sub: int, precision: str =
 
 # default cap on the scratch a discretize call allocates for a coupled model
 DISCRETIZE_WS_CAP = 2 << 30
+# default cap of the batch VJP scratch for the batched contract pass
+BATCH_VJP_WS_CAP = 16 << 30
 
 
 def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layout: str = "node",
@@ -759,10 +762,24 @@ class BatchPlan:
         _check(load().ciscvx_batch_vjp_workspace_size(self._h, ctypes.byref(n)))
         return n.value
 
+    def vjp_workspace_sizes(self):
+        """(min, full) bytes of VJP scratch: full enables the batched
+        linearize-and-contract pass of Eq. (12) / coupled-link instances."""
+        lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(load().ciscvx_batch_vjp_workspace_sizes(self._h, ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
     def discretize_vjp(self, X, U, s, w, rho, workspace=None, want_L=True, out=None):
-        """ciscvx_batch_discretize_vjp; returns dict gX, gU, gs, L (per instance)."""
+        """ciscvx_batch_discretize_vjp; returns dict gX, gU, gs, L (per instance).
+        A given workspace of at least the minimum is used as it is (the
+        library picks the contract pass by its size); without one (or with a
+        smaller one), one of the full size (batched contract pass) is
+        allocated when that is at most BATCH_VJP_WS_CAP bytes, else of the
+        minimum."""
         import torch
-        need = self.vjp_workspace_size()
+        lo, hi = self.vjp_workspace_sizes()
+        need = lo if workspace is not None and workspace.numel() * workspace.element_size() >= lo else \
+            (hi if hi <= BATCH_VJP_WS_CAP else lo)
         if workspace is None or workspace.numel() * workspace.element_size() < need:
             workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
         if out is None:
@@ -777,7 +794,9 @@ class BatchPlan:
 
     def _fused_args(self, X, U, s, w, rho, workspace, out, gout, want_L):
         import torch
-        need = self.vjp_workspace_size()
+        lo, hi = self.vjp_workspace_sizes()
+        need = lo if workspace is not None and workspace.numel() * workspace.element_size() >= lo else \
+            (hi if hi <= BATCH_VJP_WS_CAP else lo)  # as discretize_vjp
         if workspace is None or workspace.numel() * workspace.element_size() < need:
             workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
         if out is None:

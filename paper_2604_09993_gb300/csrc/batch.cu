@@ -219,6 +219,21 @@ struct ciscvx_batch_plan {
   bool any_contract = false;   // Eq. (12) or coupled-link instances: VJP by linearize-and-contract
   int max_nsub_adj = 0;        // largest n_sub among the other instances
   size_t contract_ws = 0;      // bytes of VJP workspace the contract pass needs (after the adjoint's)
+  // batched contract pass (when the workspace holds every contract instance's
+  // dense blocks): the instance table with its output offsets moved into that
+  // region, the Eq. (12) instances' items, (instance, k) entries per model,
+  // and the contract instances
+  DevInst* d_inst_ws = nullptr;
+  int n_citems = 0;
+  int2* d_citems_lpt = nullptr;
+  int2* d_citems_nat = nullptr;
+  struct CBucket { int model; long first, count; };
+  std::vector<CBucket> cbuckets;
+  int2* d_centries = nullptr;
+  std::vector<int> cinst;
+  int* d_cinst = nullptr;
+  size_t cws_A = 0, cws_B = 0, cws_V = 0, cws_P = 0;  // elements of each block region
+  size_t cws_full = 0;                                 // bytes of the region
   std::string key;
   // device tables
   const DevModel** d_models = nullptr;
@@ -276,6 +291,11 @@ void free_plan(ciscvx_batch_plan* p) {
   cudaFree(p->d_items_nat);
   cudaFree(p->d_vitems_lpt);
   cudaFree(p->d_vitems_nat);
+  cudaFree(p->d_inst_ws);
+  cudaFree(p->d_citems_lpt);
+  cudaFree(p->d_citems_nat);
+  cudaFree(p->d_centries);
+  cudaFree(p->d_cinst);
   cudaFree(p->d_queue);
   cudaFree(p->d_status);
   cudaFree(p->d_cpl_entries);
@@ -508,6 +528,61 @@ cudaError_t launch_contract_instances(ciscvx_batch_plan* p, const ciscvx_batch_v
   return cudaSuccess;
 }
 
+// The same for all contract instances at once, when the workspace holds all
+// their dense blocks: one persistent launch of the per-link kernel over the
+// Eq. (12) instances' items and the coupled groups write the blocks at the
+// instances' workspace offsets (d_inst_ws); then one contraction per model
+// and one fixed-order L per instance.
+cudaError_t launch_contract_batched(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, void* ws,
+                                    cudaStream_t st) {
+  const size_t el = p->prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  char* base = (char*)ws;
+  void* A = base;
+  void* Bm = base + al(p->cws_A * el);
+  void* Bp = (char*)Bm + al(p->cws_B * el);
+  void* S = (char*)Bp + al(p->cws_B * el);
+  double* defect = (double*)((char*)S + al(p->cws_V * el));
+  double* penalty = (double*)((char*)defect + al(p->cws_V * 8));
+  cudaError_t e = cudaSuccess;
+  if (p->n_citems > 0) {
+    BatchCommon c = common_of(p, 0, p->tune);
+    c.items = p->tune.lpt_order ? p->d_citems_lpt : p->d_citems_nat;
+    c.n_items = p->n_citems;
+    c.inst = p->d_inst_ws;
+    if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), st);
+    unsigned blocks, threads;
+    grid_for(p, p->tune, c.n_items, blocks, threads);
+    if (e == cudaSuccess) {
+      if (p->prec == CISCVX_FP64)
+        k_batch_disc<double, 0, false, true><<<blocks, threads, 0, st>>>(
+            c, io->X, io->U, io->s, (double*)A, (double*)Bm, (double*)Bp, (double*)S, defect, penalty);
+      else
+        k_batch_disc<float, 0, false, true><<<blocks, threads, 0, st>>>(
+            c, io->X, io->U, io->s, (float*)A, (float*)Bm, (float*)Bp, (float*)S, defect, penalty);
+      e = cudaGetLastError();
+    }
+  }
+  for (const auto& g : p->cpl_groups) {
+    if (e != cudaSuccess) break;
+    const CplTab& T = *p->models[g.model]->cpl;
+    const size_t per = cpl_interval_bytes(T, g.nsub, p->prec);
+    const long chunk = (long)std::min<size_t>((size_t)g.count, p->cpl_ws_bytes / per);
+    e = launch_coupled(T, g.count, g.nsub, p->prec, p->layout, io->X, io->U, io->s, A, Bm, Bp, S, defect,
+                       penalty, p->d_cpl_ws, chunk, p->d_status, st, p->d_cpl_entries + g.first, p->d_inst_ws);
+  }
+  for (const auto& bk : p->cbuckets) {
+    if (e != cudaSuccess) break;
+    e = launch_contract_batch(p->models[bk.model]->host, p->d_inst, p->d_inst_ws, p->d_centries + bk.first,
+                              bk.count, p->prec, p->layout, A, Bm, Bp, S, io->w, io->rho, io->gX, io->gU,
+                              io->gs, st);
+  }
+  if (e == cudaSuccess && io->L)
+    e = launch_contract_L_batch(p->d_models, p->d_inst, p->d_inst_ws, p->d_cinst, (int)p->cinst.size(), defect,
+                                penalty, io->w, io->rho, io->L, st);
+  return e;
+}
+
 // Discretize + VJP of the items of `c` in one pass, then the per-instance
 // finish over instances [i0, i1).  vio's X, U, s are not used (io's are).
 cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_io* io,
@@ -671,12 +746,44 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   p->n_items = (int)dec.items_lpt.size();
   p->items_lpt = dec.items_lpt;
   p->items_nat = dec.items_nat;
-  std::vector<int2> vitems_lpt, vitems_nat;
+  std::vector<int2> vitems_lpt, vitems_nat, citems_lpt, citems_nat;
   for (const int2& it : dec.items_lpt)
-    if (!models[dec.groups[it.x].x]->host.aux) vitems_lpt.push_back(it);
+    (models[dec.groups[it.x].x]->host.aux ? citems_lpt : vitems_lpt).push_back(it);
   for (const int2& it : dec.items_nat)
-    if (!models[dec.groups[it.x].x]->host.aux) vitems_nat.push_back(it);
+    (models[dec.groups[it.x].x]->host.aux ? citems_nat : vitems_nat).push_back(it);
   p->n_vitems = (int)vitems_lpt.size();
+  p->n_citems = (int)citems_lpt.size();
+  // the batched contract pass: workspace offsets of the contract instances'
+  // dense blocks, and their (instance, k) entries grouped by model
+  std::vector<DevInst> inst_ws = p->inst;
+  std::vector<int2> centries;
+  {
+    for (int i = 0; i < n_inst; ++i) {
+      if (!p->inst[i].contract) continue;
+      const DevModel& M = models[p->inst[i].model]->host;
+      const size_t n = (size_t)p->inst[i].N;
+      DevInst& W = inst_ws[i];
+      W.a = (long long)p->cws_A; W.b = (long long)p->cws_B; W.v = (long long)p->cws_V; W.p = (long long)p->cws_P;
+      p->cws_A += n * M.nxt * M.nxt;
+      p->cws_B += n * M.nxt * M.nu;
+      p->cws_V += n * M.nxt;
+      p->cws_P += n * M.nc;
+      p->cinst.push_back(i);
+    }
+    for (int m = 0; m < n_models; ++m) {
+      ciscvx_batch_plan::CBucket bk{m, (long)centries.size(), 0};
+      for (int i : p->cinst)
+        if (p->inst[i].model == m)
+          for (int k = 0; k < p->inst[i].N; ++k) centries.push_back(make_int2(i, k));
+      bk.count = (long)centries.size() - bk.first;
+      if (bk.count) p->cbuckets.push_back(bk);
+    }
+    const size_t el = precision == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    p->cws_full = p->cinst.empty() ? 0
+                  : al(p->cws_A * el) + 2 * al(p->cws_B * el) + al(p->cws_V * el) + al(p->cws_V * 8) +
+                        al(p->cws_P * 8);
+  }
   const std::vector<int2>& entries = dec.entries;
   const std::vector<int4>& groups = dec.groups;
 
@@ -717,6 +824,13 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (e == cudaSuccess) e = upload(&p->d_items_nat, p->items_nat);
   if (e == cudaSuccess && !vitems_lpt.empty()) e = upload(&p->d_vitems_lpt, vitems_lpt);
   if (e == cudaSuccess && !vitems_nat.empty()) e = upload(&p->d_vitems_nat, vitems_nat);
+  if (e == cudaSuccess && !p->cinst.empty()) {
+    e = upload(&p->d_inst_ws, inst_ws);
+    if (e == cudaSuccess && !citems_lpt.empty()) e = upload(&p->d_citems_lpt, citems_lpt);
+    if (e == cudaSuccess && !citems_nat.empty()) e = upload(&p->d_citems_nat, citems_nat);
+    if (e == cudaSuccess) e = upload(&p->d_centries, centries);
+    if (e == cudaSuccess) e = upload(&p->d_cinst, p->cinst);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->d_queue, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned));
@@ -794,6 +908,13 @@ ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* p, size_t
   return CISCVX_OK;
 }
 
+ciscvx_status ciscvx_batch_vjp_workspace_sizes(const ciscvx_batch_plan* p, size_t* min_bytes, size_t* full_bytes) {
+  if (!p || !min_bytes || !full_bytes) return set_error(CISCVX_EINVAL, "null argument");
+  *min_bytes = contract_ws_offset(p) + p->contract_ws;
+  *full_bytes = contract_ws_offset(p) + std::max(p->contract_ws, p->cws_full);
+  return CISCVX_OK;
+}
+
 ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io,
                                           void* workspace, size_t ws_bytes, void* stream) {
   ciscvx_status st = check_vjp(p, io, true, workspace, ws_bytes);
@@ -803,8 +924,12 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_bat
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
   cudaError_t e = launch_vjp_c(p, common_of(p, 1, p->tune), io, part, ps, pL, 0, p->n_inst, s);
-  if (e == cudaSuccess && p->any_contract)
-    e = launch_contract_instances(p, io, (char*)workspace + contract_ws_offset(p), p->contract_ws, s);
+  if (e == cudaSuccess && p->any_contract) {
+    char* cws = (char*)workspace + contract_ws_offset(p);
+    const size_t have = ws_bytes - contract_ws_offset(p);
+    if (have >= p->cws_full) e = launch_contract_batched(p, io, cws, s);
+    else e = launch_contract_instances(p, io, cws, p->contract_ws, s);
+  }
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch vjp launch: %s", cudaGetErrorString(e));
   return CISCVX_OK;
 }

@@ -40,47 +40,37 @@ __global__ void k_contract(int nxt, int nu, int nc, int pen0, long i0, long n, l
     if (r >= pen0 && r < pen0 + nc) v += rho[kk * nc + (r - pen0)];
     return v;
   };
-  if (c < nxt) {
-    const TP* a = A + (size_t)t * nxt * nxt + c;
+  // block values are widened on the integer pipe (the FP64 pipe bounds this)
+  auto dot = [&](const TP* col, int stride, const double* wv, long kk) {
     double acc = 0.0;
-    for (int r = 0; r < nxt; ++r) acc = fma((double)a[(size_t)r * nxt], lam(wk, k, r), acc);
+    for (int r = 0; r < nxt; ++r) acc = fma(widen(col[(size_t)r * stride]), lam(wv, kk, r), acc);
+    return acc;
+  };
+  if (c < nxt) {
+    double acc = dot(A + (size_t)t * nxt * nxt + c, nxt, wk, k);
     if (c >= pen0 && c < pen0 + nc) acc -= rho[k * nc + (c - pen0)];
     if (k >= 1) acc -= w[(k - 1) * nxt + c];
     gX[k * nxt + c] = acc;
     if (k == N - 1) gX[N * nxt + c] = -wk[c];
   } else if (c < nxt + nu) {
     const int q = c - nxt;
-    const TP* bm = Bm + (size_t)t * nxt * nu + q;
-    const TP* bp = Bp + (size_t)t * nxt * nu + q;
-    double am = 0.0, ap = 0.0;
-    for (int r = 0; r < nxt; ++r) {
-      const double l = lam(wk, k, r);
-      am = fma((double)bm[(size_t)r * nu], l, am);
-      ap = fma((double)bp[(size_t)r * nu], l, ap);
-    }
+    const double am = dot(Bm + (size_t)t * nxt * nu + q, nu, wk, k);
     if (layout == CISCVX_FOH_INTERVAL) {
       gU[(2 * k) * nu + q] = am;
-      gU[(2 * k + 1) * nu + q] = ap;
+      gU[(2 * k + 1) * nu + q] = dot(Bp + (size_t)t * nxt * nu + q, nu, wk, k);
     } else {
       // node k: B-_k^T lambda_k + B+_{k-1}^T lambda_{k-1}; the second term
       // comes from this chunk's previous interval or, at the chunk's first
       // interval, from the previous chunk (already stored in gU)
       double prev = 0.0;
-      if (t > 0) {
-        const TP* bq = Bp + (size_t)(t - 1) * nxt * nu + q;
-        const double* wq = w + (k - 1) * nxt;
-        for (int r = 0; r < nxt; ++r) prev = fma((double)bq[(size_t)r * nu], lam(wq, k - 1, r), prev);
-      } else if (k > 0) {
-        prev = gU[k * nu + q];
-      }
+      if (t > 0) prev = dot(Bp + (size_t)(t - 1) * nxt * nu + q, nu, w + (k - 1) * nxt, k - 1);
+      else if (k > 0) prev = gU[k * nu + q];
       gU[k * nu + q] = am + prev;
-      if (t == n - 1) gU[(k + 1) * nu + q] = ap;  // carried into node k + 1
+      if (t == n - 1)  // carried into node k + 1
+        gU[(k + 1) * nu + q] = dot(Bp + (size_t)t * nxt * nu + q, nu, wk, k);
     }
   } else {
-    const TP* sv = S + (size_t)t * nxt;
-    double acc = 0.0;
-    for (int r = 0; r < nxt; ++r) acc = fma((double)sv[r], lam(wk, k, r), acc);
-    gs[k] = acc;
+    gs[k] = dot(S + (size_t)t * nxt, 1, wk, k);
   }
 }
 
@@ -191,6 +181,122 @@ cudaError_t launch_affine_z(const DevModel& M, int N, int prec, int layout, cons
   else
     k_affine_z<float><<<grid, bs, 0, st>>>(M.nxt, M.nu, N, node, X, U, s, (const float*)A, (const float*)Bm,
                                           (const float*)Bp, (const float*)S, defect, z);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// The contraction of k_contract for entries (instance, k) of one model in a
+// batch: the blocks at the instance's workspace offsets (inst_ws), the
+// cotangents and gradients at its own (inst).  Chunks hold whole instances,
+// so the node sum B-_k^T lambda_k + B+_{k-1}^T lambda_{k-1} is formed here.
+template <typename TP>
+__global__ void __launch_bounds__(128) k_contract_batch(int nxt, int nu, int nc, int pen0, long n, int layout,
+                                                        const DevInst* __restrict__ inst,
+                                                        const DevInst* __restrict__ inst_ws,
+                                                        const int2* __restrict__ entries,
+                                                        const TP* __restrict__ A, const TP* __restrict__ Bm,
+                                                        const TP* __restrict__ Bp, const TP* __restrict__ S,
+                                                        const double* __restrict__ w,
+                                                        const double* __restrict__ rho, double* __restrict__ gX,
+                                                        double* __restrict__ gU, double* __restrict__ gs) {
+  const int ncol = nxt + nu + 1;
+  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long e = g / ncol;
+  if (e >= n) return;
+  const int c = (int)(g - e * ncol);
+  const int2 en = entries[e];
+  const DevInst I = inst[en.x];
+  const DevInst W = inst_ws[en.x];
+  const long k = en.y, N = I.N;
+  const double* wk = w + I.v + k * nxt;
+  const double* rk = rho + I.p + k * nc;
+  auto lam = [&](const double* wv, const double* rv, int r) {
+    double v = wv[r];
+    if (r >= pen0 && r < pen0 + nc) v += rv[r - pen0];
+    return v;
+  };
+  // block values are widened on the integer pipe (the FP64 pipe bounds this)
+  auto dot = [&](const TP* col, int stride, const double* wv, const double* rv) {
+    double acc = 0.0;
+    for (int r = 0; r < nxt; ++r) acc = fma(widen(col[(size_t)r * stride]), lam(wv, rv, r), acc);
+    return acc;
+  };
+  if (c < nxt) {
+    double acc = dot(A + W.a + k * nxt * nxt + c, nxt, wk, rk);
+    if (c >= pen0 && c < pen0 + nc) acc -= rk[c - pen0];
+    if (k >= 1) acc -= wk[c - nxt];
+    gX[I.x + k * nxt + c] = acc;
+    if (k == N - 1) gX[I.x + N * nxt + c] = -wk[c];
+  } else if (c < nxt + nu) {
+    const int q = c - nxt;
+    const double am = dot(Bm + W.b + k * nxt * nu + q, nu, wk, rk);
+    if (layout == CISCVX_FOH_INTERVAL) {
+      gU[I.u + (2 * k) * nu + q] = am;
+      gU[I.u + (2 * k + 1) * nu + q] = dot(Bp + W.b + k * nxt * nu + q, nu, wk, rk);
+    } else {
+      // node k: B-_k^T lambda_k + B+_{k-1}^T lambda_{k-1}; node N: B+_{N-1}^T lambda_{N-1}
+      const double prev = k > 0 ? dot(Bp + W.b + (k - 1) * nxt * nu + q, nu, wk - nxt, rk - nc) : 0.0;
+      gU[I.u + k * nu + q] = am + prev;
+      if (k == N - 1) gU[I.u + (k + 1) * nu + q] = dot(Bp + W.b + k * nxt * nu + q, nu, wk, rk);
+    }
+  } else {
+    gs[I.s + k] = dot(S + W.v + k * nxt, 1, wk, rk);
+  }
+}
+
+// L of one listed instance per block, in a fixed order.
+__global__ void __launch_bounds__(256) k_contract_L_batch(const DevModel* const* models, const DevInst* inst,
+                                                          const DevInst* inst_ws, const int* list,
+                                                          const double* __restrict__ defect,
+                                                          const double* __restrict__ penalty,
+                                                          const double* __restrict__ w,
+                                                          const double* __restrict__ rho, double* L) {
+  __shared__ double red[256];
+  const int i = list[blockIdx.x];
+  const DevInst I = inst[i], W = inst_ws[i];
+  const DevModel& M = *models[I.model];
+  const long nd = (long)I.N * M.nxt, np = (long)I.N * M.nc;
+  double acc = 0.0;
+  for (long e = threadIdx.x; e < nd + np; e += 256)
+    acc = e < nd ? fma(w[I.v + e], defect[W.v + e], acc) : fma(rho[I.p + e - nd], penalty[W.p + e - nd], acc);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) L[i] = red[0];
+}
+
+}  // namespace
+
+cudaError_t launch_contract_batch(const DevModel& Mh, const DevInst* inst, const DevInst* inst_ws,
+                                  const int2* entries, long n_entries, int prec, int layout, const void* A,
+                                  const void* Bm, const void* Bp, const void* S, const double* w,
+                                  const double* rho, double* gX, double* gU, double* gs, cudaStream_t st) {
+  if (n_entries == 0) return cudaSuccess;
+  const int nxt = Mh.nxt, nu = Mh.nu, nc = Mh.nc;
+  const int pen0 = 6 * Mh.nb + (Mh.aux ? 4 * nc : 0);
+  const long threads = n_entries * (nxt + nu + 1);
+  const int bs = 128;
+  const unsigned grid = (unsigned)((threads + bs - 1) / bs);
+  if (prec == CISCVX_FP64)
+    k_contract_batch<double><<<grid, bs, 0, st>>>(nxt, nu, nc, pen0, n_entries, layout, inst, inst_ws, entries,
+                                                  (const double*)A, (const double*)Bm, (const double*)Bp,
+                                                  (const double*)S, w, rho, gX, gU, gs);
+  else
+    k_contract_batch<float><<<grid, bs, 0, st>>>(nxt, nu, nc, pen0, n_entries, layout, inst, inst_ws, entries,
+                                                 (const float*)A, (const float*)Bm, (const float*)Bp,
+                                                 (const float*)S, w, rho, gX, gU, gs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_L_batch(const DevModel* const* models, const DevInst* inst, const DevInst* inst_ws,
+                                    const int* list, int n_list, const double* defect, const double* penalty,
+                                    const double* w, const double* rho, double* L, cudaStream_t st) {
+  if (n_list == 0) return cudaSuccess;
+  k_contract_L_batch<<<n_list, 256, 0, st>>>(models, inst, inst_ws, list, defect, penalty, w, rho, L);
   return cudaGetLastError();
 }
 

@@ -164,4 +164,20 @@ __device__ __forceinline__ IvRef iv_ref(long long e, int nxt, int nu, int nc, in
   return r;
 }
 
+// FP32 -> FP64 (exact) from the IEEE-754 binary32 and binary64 layouts on the
+// integer pipe: exponent rebiased by 1023 - 127, the 23 fraction bits moved
+// to the top of the 52.  Zeros keep their sign; subnormals, infinities and
+// NaNs take the conversion instruction.  On this part the conversion
+// instruction occupies the FP64 pipe, which bounds the kernels that read FP32
+// blocks into FP64 sums.
+__device__ __forceinline__ double widen(unsigned u) {
+  const unsigned e = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (e == 0u || e == 0xFFu) return (double)__uint_as_float(u);
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double widen(float f) { return widen(__float_as_uint(f)); }
+__device__ __forceinline__ double widen(double d) { return d; }
+
 }  // namespace ciscvx

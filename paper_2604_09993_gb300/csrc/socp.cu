@@ -127,20 +127,6 @@ __device__ __forceinline__ void load_tab(const SocpIO& I, KindTab& K) {
   __syncthreads();
 }
 
-// FP32 -> FP64 (exact) from the IEEE-754 binary32 and binary64 layouts on the
-// integer pipe: exponent rebiased by 1023 - 127, the 23 fraction bits moved
-// to the top of the 52.  Zeros keep their sign; subnormals, infinities and
-// NaNs take the conversion instruction.  On this part the FP64 pipe, which
-// the conversion instruction and an FP64 negation would occupy, bounds the
-// fill.
-__device__ __forceinline__ double widen(unsigned u) {
-  const unsigned e = (u >> 23) & 0xFFu;
-  if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (e == 0u || e == 0xFFu) return (double)__uint_as_float(u);
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
-  return __hiloint2double((int)hi, (int)(u << 29));
-}
-
 // The entry's value, its sign applied by flipping the sign bit.
 __device__ __forceinline__ double fetch(const SocpIO& I, const KindTab& K, long inst, uint64_t d) {
   const unsigned kind = d_kind(d);

@@ -86,3 +86,29 @@ def test_fused_entry_point_with_contract_instances(env):
         assert torch.equal(out[k], out2[k]), k
     for k in ("gX", "gU", "gs", "L"):
         assert torch.equal(gout[k], g2[k]), k
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+def test_batched_and_per_instance_contract_paths_agree(env, precision, tol):
+    """A workspace of the full size takes the batched contract pass, one of the
+    minimum size the per-instance one; both meet the oracle and agree."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    robots, probs, midx = _batch(43, 14)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [q.N for q in probs], [q.n_sub for q in probs], precision=precision)
+    lo, hi = plan.vjp_workspace_sizes()
+    assert hi > lo
+    X, U, s, w, rho = _packed(torch, plan, probs, dev)
+    g_full = plan.discretize_vjp(X, U, s, w, rho, workspace=torch.empty(hi, dtype=torch.uint8, device=dev))
+    g_min = plan.discretize_vjp(X, U, s, w, rho, workspace=torch.empty(lo, dtype=torch.uint8, device=dev))
+    plan.sync_status()
+    for k in ("gX", "gU", "gs", "L"):
+        a, b = g_full[k].cpu().numpy(), g_min[k].cpu().numpy()
+        assert block_err(a, b) <= (1e-12 if precision == "fp64" else 1e-5), (k, block_err(a, b))
+    host = {k: v.cpu().numpy() for k, v in g_full.items()}
+    for i, q in enumerate(probs):
+        rX, rU, rs, rL = oracle.vjp(q.robot.as_dict(), q.X, q.U, q.s, q.w, q.rho, q.n_sub)
+        assert block_err(plan.unpack(host["gX"], "X", i, q.X.shape), rX) <= tol, i
+        assert block_err(plan.unpack(host["gU"], "U", i, q.U.shape), rU) <= tol, i
+        assert block_err(plan.unpack(host["gs"], "s", i, q.s.shape), rs) <= tol, i
