@@ -633,7 +633,7 @@ ciscvx_status ciscvx_node_linearize(const ciscvx_model* model, int n_nodes, cons
 /* n_psi of the model: 3 n_c (CISCVX_AUX_CROSS) or n_c. */
 ciscvx_status ciscvx_psi_rows(const ciscvx_model* model, int* n_psi);
 
-/* Psi and its Jacobian at N intervals (thread per output element; FP64).
+/* Psi and its Jacobian at N intervals (one thread per interval and contact; FP64).
  *   Xp, Xm [N+1][n_x~]: post- and pre-impact node states (device; only their
  *     y entries are read: y+ of nodes 0..N-1, y- of nodes 1..N).
  *   psi [N][n_psi] (device, required when n_psi > 0).

@@ -9,12 +9,19 @@
 //   one path-penalty state per contact: row i = d[i] - eps.
 // FB(a, b) = a + b - sqrt(a^2 + b^2 + delta); dFB/da = 1 - a / sqrt(.).
 //
-// One thread per row (interval k, row r) evaluates FB once and writes its
-// value and its dense Jacobian row into shared memory; the block then copies
-// its intervals' rows, which are contiguous in psi and dpsi, to global memory
-// with consecutive threads on consecutive doubles.  8 (2 n_y + n_psi (1 + n_y))
-// bytes per interval against about 20 FP64 operations per FB row: on this
-// part's FP64 rate the two bounds are of the same order.
+// The FP64 pipe (two lanes per SM per clock on this part) and HBM bound the
+// kernel with times of the same order, so the FP64 work is laid out without
+// divergence and the writes are coalesced:
+//  * one thread per (interval, contact) evaluates that contact's rows (two FB
+//    rows and one path row, or one path row), so every lane of a warp runs
+//    the same FP64 instructions;
+//  * the block keeps only the values and the two slopes of each FB row in
+//    shared memory (a few dozen bytes per contact), and then writes its
+//    intervals' slice of psi and of the dense Jacobian, which are contiguous,
+//    with consecutive threads on consecutive 16-byte pairs; each Jacobian
+//    entry is formed from its (interval, row, column) index and that table.
+#include <cstdint>
+
 #include "common.cuh"
 
 namespace ciscvx {
@@ -22,68 +29,108 @@ namespace ciscvx {
 namespace {
 
 constexpr int PSI_THREADS = 256;
-constexpr int PSI_SMEM = 48 * 1024;  // staging per block (no opt-in needed)
 
-// Intervals one block stages: as many as fit, at most one per thread row.
-__host__ __device__ inline int psi_block_intervals(int npsi, int ny) {
-  const int per = npsi * (ny + 1) * (int)sizeof(double);
-  int ib = PSI_SMEM / per;
-  if (ib * npsi > PSI_THREADS) ib = PSI_THREADS / npsi;
+// Intervals per block: one thread per (interval, contact), rounded down to an
+// even count so that every block's slice of psi and dpsi starts on a 16-byte
+// boundary when the arrays do.
+__host__ __device__ inline int psi_block_intervals(int nc) {
+  int ib = PSI_THREADS / nc;
+  if (ib > 1) ib &= ~1;
   return ib < 1 ? 1 : ib;
 }
 
-__global__ void __launch_bounds__(PSI_THREADS) k_psi(int nx, int nxt, int nc, int aux, long N,
-                                                     const double* __restrict__ Xp,
+// floor(e / d) for 0 <= e < 2^22 and d >= 1 from the FP32 reciprocal rd = 1/d
+// (rounded): (e + 1/2)/d lies at least 1/(2d) from every integer, and the two
+// FP32 roundings move it by at most 2^-23 (e + 1/2)/d < 1/(2d).
+__device__ __forceinline__ int div_small(int e, float rd) {
+  return __float2int_rz(__fmul_rn(__int2float_rn(e) + 0.5f, rd));
+}
+
+// non-finite test on the exponent bits (integer pipe)
+__device__ __forceinline__ bool nonfinite_bits(double v) {
+  return ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
+}
+
+struct PsiShape {
+  int nx, nxt, nc, ny, npsi, aux;
+  float r_rowlen, r_ny;  // 1/(n_psi n_y), 1/n_y in FP32 (see div_small)
+};
+
+// Entry e of a block's Jacobian slice [nk][n_psi][n_y]; sj holds the slopes
+// (da, db) of the two FB rows of each (interval, contact) of the block.
+__device__ __forceinline__ double dpsi_entry(const PsiShape& p, const double* sj, int e) {
+  const int kk = div_small(e, p.r_rowlen);
+  const int rem = e - kk * p.npsi * p.ny;
+  const int r = div_small(rem, p.r_ny);
+  const int c = rem - r * p.ny;
+  if (!p.aux) return c == r ? 1.0 : 0.0;
+  if (r >= 2 * p.nc) return c == 4 * p.nc + (r - 2 * p.nc) ? 1.0 : 0.0;
+  const int ja = 2 * r;  // 4 (r >> 1) + 2 (r & 1)
+  if (c != ja && c != ja + 1) return 0.0;
+  return sj[(kk * p.nc + (r >> 1)) * 4 + 2 * (r & 1) + (c - ja)];
+}
+
+__global__ void __launch_bounds__(PSI_THREADS) k_psi(PsiShape p, long N, const double* __restrict__ Xp,
                                                      const double* __restrict__ Xm, double delta,
                                                      double eps, double* __restrict__ psi,
-                                                     double* __restrict__ dpsi, unsigned* status) {
+                                                     double* __restrict__ dpsi, int vec,
+                                                     unsigned* status) {
   extern __shared__ double sh[];
-  const int ny = nxt - nx, npsi = aux ? 3 * nc : nc;
-  const int ib = psi_block_intervals(npsi, ny);
+  const int nc = p.nc, npsi = p.npsi;
+  const int ib = psi_block_intervals(nc);
   const long k0 = (long)blockIdx.x * ib;
   const int nk = (int)(N - k0 < ib ? N - k0 : ib);
-  double* sv = sh;                      // [nk][npsi] values
-  double* sd = sh + (size_t)ib * npsi;  // [nk][npsi][ny] Jacobian rows
+  double* sv = sh;                      // [nk][n_psi] values
+  double* sj = sh + (size_t)ib * npsi;  // [nk][n_c][4] slopes (da, db) of the two FB rows
   const int t = threadIdx.x;
-  if (t < nk * npsi) {
-    const int kk = t / npsi, r = t - kk * npsi;
+  bool bad = false;
+  for (int u = t; u < nk * nc; u += PSI_THREADS) {
+    const int kk = u / nc, i = u - kk * nc;
     const long k = k0 + kk;
-    const double* yp = Xp + k * nxt + nx;
-    const double* ym = Xm + (k + 1) * nxt + nx;
-    int ja, jb = -1;
-    if (aux && r < 2 * nc) {
-      ja = 4 * (r >> 1) + 2 * (r & 1);
-      jb = ja + 1;
+    const double* yp = Xp + k * p.nxt + p.nx;
+    const double* ym = Xm + (k + 1) * p.nxt + p.nx;
+    double* v = sv + (size_t)kk * npsi;
+    if (p.aux) {
+      double* s4 = sj + (size_t)u * 4;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int ja = 4 * i + 2 * q;
+        const double a = ym[ja] - yp[ja], b = ym[ja + 1] - yp[ja + 1];
+        // one reciprocal square root gives both sqrt(x) = x / sqrt(x) and 1/sqrt(x)
+        const double x = fma(a, a, fma(b, b, delta));
+        const double iq = rsqrt(x);
+        const double val = (a + b) - x * iq;
+        s4[2 * q] = fma(-a, iq, 1.0);
+        s4[2 * q + 1] = fma(-b, iq, 1.0);
+        v[2 * i + q] = val;
+        bad |= nonfinite_bits(val);
+      }
+      const int jp = 4 * nc + i;
+      const double val = (ym[jp] - yp[jp]) - eps;
+      v[2 * nc + i] = val;
+      bad |= nonfinite_bits(val);
     } else {
-      ja = aux ? 4 * nc + (r - 2 * nc) : r;
+      const double val = (ym[i] - yp[i]) - eps;
+      v[i] = val;
+      bad |= nonfinite_bits(val);
     }
-    const double a = ym[ja] - yp[ja];
-    double val, da = 1.0, db = 0.0;
-    if (jb >= 0) {
-      const double b = ym[jb] - yp[jb];
-      // one reciprocal square root gives both q and 1/q (the FP64 pipe, two
-      // lanes per SM per clock on this part, bounds the kernel with HBM)
-      const double x = fma(a, a, fma(b, b, delta));
-      const double iq = rsqrt(x);
-      val = (a + b) - x * iq;
-      da = fma(-a, iq, 1.0);
-      db = fma(-b, iq, 1.0);
-    } else {
-      val = a - eps;
-    }
-    if (!isfinite(val)) atomicOr(status, ST_NONFINITE);
-    sv[t] = val;
-    double* row = sd + (size_t)t * ny;
-    for (int c = 0; c < ny; ++c) row[c] = c == ja ? da : (c == jb ? db : 0.0);
   }
+  if (bad) atomicOr(status, ST_NONFINITE);
   __syncthreads();
-  const long nv = (long)nk * npsi;
+  const int nv = nk * npsi;
   double* gv = psi + k0 * npsi;
-  for (long e = t; e < nv; e += PSI_THREADS) gv[e] = sv[e];
-  if (dpsi) {
-    double* gd = dpsi + k0 * npsi * ny;
-    for (long e = t; e < nv * ny; e += PSI_THREADS) gd[e] = sd[e];
+  for (int e = t; e < nv; e += PSI_THREADS) gv[e] = sv[e];
+  if (!dpsi) return;
+  double* gd = dpsi + k0 * npsi * p.ny;
+  const int nd = nv * p.ny;
+  int e0 = 0;
+  if (vec) {  // the slice starts on a 16-byte boundary: pairs of entries
+    double2* gd2 = reinterpret_cast<double2*>(gd);
+    for (int q = t; q < nd / 2; q += PSI_THREADS)
+      gd2[q] = make_double2(dpsi_entry(p, sj, 2 * q), dpsi_entry(p, sj, 2 * q + 1));
+    e0 = nd & ~1;
   }
+  for (int e = e0 + t; e < nd; e += PSI_THREADS) gd[e] = dpsi_entry(p, sj, e);
 }
 
 }  // namespace
@@ -92,13 +139,27 @@ int psi_rows(const DevModel& M) { return M.aux ? 3 * M.nc : M.nc; }
 
 cudaError_t launch_psi(const DevModel& M, int N, const double* Xp, const double* Xm, double delta,
                        double eps, double* psi, double* dpsi, unsigned* status, cudaStream_t st) {
-  const int nx = 6 * M.nb, ny = M.nxt - nx, npsi = psi_rows(M);
-  if (npsi == 0 || N == 0) return cudaSuccess;
-  const int ib = psi_block_intervals(npsi, ny);
-  const size_t smem = (size_t)ib * npsi * (ny + 1) * sizeof(double);
+  PsiShape p;
+  p.nx = 6 * M.nb;
+  p.nxt = M.nxt;
+  p.nc = M.nc;
+  p.ny = M.nxt - p.nx;
+  p.npsi = psi_rows(M);
+  p.aux = M.aux ? 1 : 0;
+  if (p.npsi == 0 || N == 0) return cudaSuccess;
+  const int ib = psi_block_intervals(p.nc);
+  // div_small's range: a block's Jacobian slice has ib n_psi n_y < 2^22
+  // entries (at most 8 * 96 * 160 for 32 contacts)
+  p.r_rowlen = 1.0f / (float)(p.npsi * p.ny);
+  p.r_ny = 1.0f / (float)p.ny;
+  const size_t smem = (size_t)ib * (p.npsi + 4 * p.nc) * sizeof(double);
   const long blocks = (N + ib - 1) / ib;
-  k_psi<<<(unsigned)blocks, PSI_THREADS, smem, st>>>(nx, M.nxt, M.nc, M.aux ? 1 : 0, N, Xp, Xm, delta,
-                                                     eps, psi, dpsi, status);
+  // every block slice starts at an even entry (ib even, or ib == 1 with an
+  // even row length); pairs are stored when dpsi itself is 16-byte aligned
+  const int vec = dpsi && ((reinterpret_cast<uintptr_t>(dpsi) & 15) == 0) &&
+                  (ib % 2 == 0 || (p.npsi * p.ny) % 2 == 0);
+  k_psi<<<(unsigned)blocks, PSI_THREADS, smem, st>>>(p, N, Xp, Xm, delta, eps, psi, dpsi, vec,
+                                                     status);
   return cudaGetLastError();
 }
 

@@ -111,3 +111,50 @@ def test_psi_edge_cases(env):
     out = api.psi_linearize(m, X, X, 0.25, 1e-3)
     np.testing.assert_array_equal(out["psi"].cpu().numpy()[:, :2 * m.nc], -0.5)
     np.testing.assert_array_equal(out["psi"].cpu().numpy()[:, 2 * m.nc:], -1e-3)
+
+
+def _every_link_in_contact(cross):
+    """7-link chain with one contact at the distal end of every link (n_c = 7)."""
+    import dataclasses
+    R = synth.cheetah7(np.random.default_rng(43))
+    nb = R.nb
+    half = 0.5 * np.asarray(R.length)
+    R = dataclasses.replace(R, contact_body=np.arange(nb, dtype=np.int32),
+                            contact_rho=np.stack([np.zeros(nb), -half], axis=1),
+                            contact_mu=np.full(nb, synth.MU))
+    return (synth.with_cross_states(R) if cross else R).as_dict()
+
+
+@pytest.mark.parametrize("cross", [False, True])
+def test_psi_many_contacts_and_unaligned_jacobian(env, cross):
+    """n_c = 7: an odd contact count, blocks of 36 intervals with a ragged last
+    block whose Jacobian slice has an odd length; then the same call with dpsi
+    one double past a 16-byte boundary (element-wise stores), bit-identical."""
+    torch, oracle, api = env
+    R = _every_link_in_contact(cross)
+    m = api.Model(R)
+    assert m.nc == 7
+    N = 101
+    Xp, Xm = _nodes(R, N, 99, m.nxt)
+    dev = torch.device("cuda:0")
+    tXp, tXm = torch.tensor(Xp, device=dev), torch.tensor(Xm, device=dev)
+    out = api.psi_linearize(m, tXp, tXm, 0.05, 1e-4)
+    api.sync_status(m)
+    ref = oracle.psi(R, Xp, Xm, 0.05, 1e-4)
+    psi, dpsi = out["psi"].cpu().numpy(), out["dpsi"].cpu().numpy()
+    ny = m.ny
+    for k in range(N):
+        assert block_err(psi[k], ref["psi"][k]) <= TOL_FP64
+        assert block_err(dpsi[k], ref["J"][k][:, ny:]) <= TOL_FP64
+    npsi = api.psi_rows(m)
+    buf = torch.full((N * npsi * ny + 1,), float("nan"), dtype=torch.float64, device=dev)
+    off = buf[1:]
+    assert off.data_ptr() % 16 == 8
+    psi2 = torch.empty_like(out["psi"])
+    lib = api.load()
+    assert lib.ciscvx_psi_linearize(m.handle, N, api._ptr(tXp), api._ptr(tXm), 0.05, 1e-4,
+                                    api._ptr(psi2), api._ptr(off), api._stream()) == 0
+    api.sync_status(m)
+    assert torch.equal(psi2, out["psi"])
+    assert torch.equal(off.view(N, npsi, ny), out["dpsi"])
+    assert torch.isnan(buf[0])
