@@ -73,25 +73,33 @@ def test_linear_system_matches_rk4_polynomial(oracle_mod, n_sub, s):
 
 
 def test_linear_system_fourth_order_convergence(oracle_mod):
-    """Errors against the exact FOH flow (Van Loan block exponential) fall ~16x per halving of h."""
+    """Errors of x, A, B-, B+ and S against the exact FOH flow (Van Loan block exponential) fall ~16x per halving of h."""
     rng = np.random.default_rng(5)
     n, m = 4, 2
     Ac = rng.standard_normal((n, n)) * 0.8
     Bc = rng.standard_normal((n, m))
     x0, uL, uR = rng.standard_normal(n), rng.standard_normal(m), rng.standard_normal(m)
     s = 0.9
-    M, _ = _aug(Ac, Bc, s)
+    M, M1 = _aug(Ac, Bc, s)
     E = sla.expm(M)
     A_ex = E[:n, :n]
     Bp_ex = E[:n, n + m:]
     Bm_ex = E[:n, n:n + m] - Bp_ex
-    x_ex = E[:n, :] @ np.concatenate([x0, uL, uR - uL])
+    z0 = np.concatenate([x0, uL, uR - uL])
+    x_ex = E[:n, :] @ z0
+    # d/ds expm(M(s)) is the top-right block of expm([[M, M1], [0, M]]), M1 = dM/ds
+    K = M.shape[0]
+    big = np.zeros((2 * K, 2 * K))
+    big[:K, :K] = M
+    big[K:, K:] = M
+    big[:K, K:] = M1
+    S_ex = (sla.expm(big)[:K, K:] @ z0)[:n]
     assert np.allclose(A_ex, sla.expm(s * Ac), rtol=1e-13, atol=1e-13)
     errs = []
     for n_sub in (2, 4, 8, 16):
-        x1, A, Bm, Bp, _ = oracle_mod.linear_interval(Ac, Bc, n_sub, x0, uL, uR, s)
+        x1, A, Bm, Bp, S = oracle_mod.linear_interval(Ac, Bc, n_sub, x0, uL, uR, s)
         errs.append(max(np.abs(A - A_ex).max(), np.abs(Bm - Bm_ex).max(),
-                        np.abs(Bp - Bp_ex).max(), np.abs(x1 - x_ex).max()))
+                        np.abs(Bp - Bp_ex).max(), np.abs(x1 - x_ex).max(), np.abs(S - S_ex).max()))
     ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
     for r in ratios:
         assert 12.0 < r < 20.0, (errs, ratios)
