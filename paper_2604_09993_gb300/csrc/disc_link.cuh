@@ -13,8 +13,11 @@
 //  * derivatives of the penalty terms are evaluated in the tangent precision;
 //  * in FP32-Phi mode the tangent recursion takes its stage data from an FP32
 //    copy of the stage recursion that is re-anchored on the FP64 state at the
-//    start of every substep (a handful of conversions per substep instead of
-//    several per stage).
+//    start of every substep; the anchors are narrowed on the integer pipe
+//    (to_f32_rz), so no conversion instruction takes an FP64-pipe slot;
+//  * with checkpoints (CK) in FP32-Phi mode those anchors are the checkpoints,
+//    so the FP32 adjoint's backward sweep issues no FP64 instruction per
+//    substep.
 // CROSS (a foot link of the Eq. (12) model): the contact's four
 // cross-complementarity states and its path-penalty state.  The lambda^c row
 // integrates v_x - omega (R rho)_y + gamma phi_t / sqrt(1 + phi_t^2) over the
@@ -254,7 +257,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   double sPi = sPL, sQi = sQL, sTi = sTL;
 
   for (int i = 0; i < nsub; ++i) {
-    if constexpr (CK) {
+    if constexpr (CK && !F32) {
       ck->th[i] = th; ck->om[i] = om; ck->s[i] = sth; ck->c[i] = cth;
       if (foot) { ck->py[i] = py; ck->vy[i] = vy; }
     }
@@ -273,9 +276,15 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       ipm = input_penalty<TP>(tm, tmP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
       ip1 = input_penalty<TP>(te, teP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
-    // FP32 copy of the stage recursion, anchored on the FP64 state (FP32-Phi mode)
-    const TP thA = TP(th), omA = TP(om), pyA = TP(py), vyA = TP(vy);
-    const TP vxA = cross ? TP(vx) : TP(0);
+    // FP32 copy of the stage recursion, anchored on the FP64 state (FP32-Phi
+    // mode; the anchors are narrowed on the integer pipe).  With CK the
+    // anchors are the checkpoints: the FP32 backward sweep starts from them.
+    const TP thA = anchor<TP>(th), omA = anchor<TP>(om), pyA = anchor<TP>(py), vyA = anchor<TP>(vy);
+    const TP vxA = cross ? anchor<TP>(vx) : TP(0);
+    if constexpr (CK && F32) {
+      ck->thf[i] = thA; ck->omf[i] = omA;
+      if (foot) { ck->pyf[i] = pyA; ck->vyf[i] = vyA; }
+    }
     TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0), kvxA = TP(0);
     double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
     double kvx = 0, avx = 0;  // Eq. (12) model: s a_x at the stage, its RK4 sum

@@ -1,16 +1,20 @@
 // vjp_link.cuh — one link of one interval of the discrete-adjoint VJP, shared
 // by the single-instance and the batched kernels (see vjp.cu).
 //
-// Forward sweep: the FP64 state, checkpointing (theta, omega, sin theta,
-// cos theta) — and (p_y, v_y) for a foot link — at every substep start.
+// Forward sweep: the FP64 state, checkpointed at every substep start.
 // Backward sweep: per substep, the four stages are recomputed from the
 // checkpoint and the transposed stage Jacobians are applied in the adjoint
 // precision TP.
-//  * FP64 adjoint: the stages are recomputed in FP64 (sin/cos chained as in
-//    the forward kernel) and the penalty quadrature (for L) is taken there.
-//  * FP32 adjoint: the penalty quadrature is taken in the forward sweep on the
-//    FP64 stages, and the backward sweep recomputes the stages in FP32 from
-//    the FP64 checkpoints, so it issues no FP64 instruction at all.
+//  * FP64 adjoint: the checkpoints are (theta, omega, sin theta, cos theta),
+//    and (p_y, v_y) for a foot link; the stages are recomputed in FP64
+//    (sin/cos chained as in the forward kernel) and the penalty quadrature
+//    (for L) is taken there.
+//  * FP32 adjoint: the checkpoints are the FP32 anchors of the stage
+//    recursion (theta, omega, and p_y, v_y for a foot link, narrowed on the
+//    integer pipe), the penalty quadrature is taken in the forward sweep on
+//    the FP64 stages, and the backward sweep recomputes the stages in FP32
+//    from the anchors with tau in FP32, so it issues no FP64 instruction per
+//    substep.
 #pragma once
 #include <type_traits>
 
@@ -111,8 +115,13 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   double ti = 0.0;  // tau at the substep start (running sum)
   TP tiP = TP(0);
   for (int i = 0; i < nsub; ++i) {
-    ckl.th[i] = th; ckl.om[i] = om; ckl.s[i] = sth; ckl.c[i] = cth;
-    if (FOOT) { ckl.py[i] = py; ckl.vy[i] = vy; }
+    if constexpr (F32) {  // the FP32 backward sweep needs only the FP32 anchors
+      ckl.thf[i] = anchor<TP>(th); ckl.omf[i] = anchor<TP>(om);
+      if (FOOT) { ckl.pyf[i] = anchor<TP>(py); ckl.vyf[i] = anchor<TP>(vy); }
+    } else {
+      ckl.th[i] = th; ckl.om[i] = om; ckl.s[i] = sth; ckl.c[i] = cth;
+      if (FOOT) { ckl.py[i] = py; ckl.vy[i] = vy; }
+    }
     const double tm = ti + h2, te = ti + h;
     if (PEN_FWD) {
       fpm = input_penalty<TP>(tm, tiP + h2P, sd, sdP, mu, muP, cL, cD, cLP, cDP);
@@ -185,21 +194,30 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   InputPenalty<TP> ipE;
   if (FOOT) ipE = input_penalty<TP, !F32>(1.0, TP(1), sd, sdP, mu, muP, cL, cD, cLP, cDP);
   double di = (double)(nsub - 1);
-  for (int i = nsub - 1; i >= 0; --i, di -= 1.0) {
+  TP fi = TP(nsub - 1);  // substep index in the tangent precision (exact)
+  for (int i = nsub - 1; i >= 0; --i, di -= 1.0, fi -= TP(1)) {
     TP cs_[4], sn_[4], sath[4], oms[4], wdt[4], tau[4];
     TP gr[4], gp[4], vys[4], ays[4], om_pen[4], dl0[4], dl1[4], dl2[4];
-    const double tsb = di * h, tmb = tsb + h2, teb = tsb + h;  // substep start / midpoint / end
-    const TP tsP = TP(tsb), tmP = tsP + h2P, teP = tsP + hP;
+    // substep start / midpoint / end: FP64 for the FP64 adjoint; the FP32
+    // adjoint takes them in FP32 and issues no FP64 instruction per substep
+    const double tsb = di * h, tmb = tsb + h2, teb = tsb + h;
+    const TP tsP = F32 ? fi * hP : TP(tsb), tmP = tsP + h2P, teP = tsP + hP;
     InputPenalty<TP> ipS, ipM;
     if (FOOT) {
       ipM = input_penalty<TP, !F32>(tmb, tmP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
       ipS = input_penalty<TP, !F32>(tsb, tsP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
     }
     {
-      const double thc = ck.th[i], omc = ck.om[i], stc = ck.s[i], ctc = ck.c[i];
-      double pyc = 0, vyc = 0;
-      if (FOOT) { pyc = ck.py[i]; vyc = ck.vy[i]; }
-      const TP thA = TP(thc), omA = TP(omc), pyA = TP(pyc), vyA = TP(vyc);
+      // FP64 adjoint: the FP64 checkpoint; FP32 adjoint: the FP32 anchors
+      double thc = 0, omc = 0, stc = 0, ctc = 1, pyc = 0, vyc = 0;
+      TP thA = TP(0), omA = TP(0), pyA = TP(0), vyA = TP(0);
+      if constexpr (F32) {
+        thA = ck.thf[i]; omA = ck.omf[i];
+        if (FOOT) { pyA = ck.pyf[i]; vyA = ck.vyf[i]; }
+      } else {
+        thc = ck.th[i]; omc = ck.om[i]; stc = ck.s[i]; ctc = ck.c[i];
+        if (FOOT) { pyc = ck.py[i]; vyc = ck.vy[i]; }
+      }
       TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0);
       double kth = 0, kom = 0, kpy = 0, kvy = 0;
 #pragma unroll
