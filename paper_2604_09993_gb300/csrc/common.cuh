@@ -159,6 +159,8 @@ struct Checkpoints {
   // FP32 adjoint: the FP32 anchors of the stage recursion at each substep start
   float thf[MAXSUB_VJP], omf[MAXSUB_VJP], pyf[MAXSUB_VJP], vyf[MAXSUB_VJP];
   double th_end, om_end, Yom;
+  // the link's FOH input sums (AxL, AxR, AyL, AyR, PL, PR, QL, QR, TL, TR) and h = 1/n_sub
+  double ins[10], h;
 };
 
 __device__ __forceinline__ double rk_c(int j) { return j == 0 ? 0.0 : (j == 3 ? 1.0 : 0.5); }

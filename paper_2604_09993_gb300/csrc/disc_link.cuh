@@ -189,16 +189,18 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     for (int m = 0; m < 3; ++m) {
       cL[m] = uL[cin + m];
       cD[m] = uR[cin + m] - cL[m];
-      cLP[m] = TP(cL[m]);
-      cDP[m] = TP(cD[m]);
+      cLP[m] = anchor<TP>(cL[m]);
+      cDP[m] = anchor<TP>(cD[m]);
     }
   }
   const double mu = B.mu, crx = B.crho[0], cry = B.crho[1];
-  const TP muP = TP(mu), crxP = TP(crx), cryP = TP(cry);
+  const TP muP = anchor<TP>(mu), crxP = anchor<TP>(crx), cryP = anchor<TP>(cry);
   const double dP = PR - PL, dQ = QR - QL, dT = TR - TL, dAy = AyR - AyL;
-  // tangent-precision copies of the input sums
-  const TP PLP = TP(PL), dPP = TP(dP), QLP = TP(QL), dQP = TP(dQ), TLP = TP(TL), dTP = TP(dT);
-  const TP AyLP = TP(AyL), dAyP = TP(dAy), gP = TP(g);
+  // tangent-precision copies of the input sums (FP32: narrowed on the integer
+  // pipe, like every FP32 copy of a per-interval constant below)
+  const TP PLP = anchor<TP>(PL), dPP = anchor<TP>(dP), QLP = anchor<TP>(QL), dQP = anchor<TP>(dQ),
+           TLP = anchor<TP>(TL), dTP = anchor<TP>(dT);
+  const TP AyLP = anchor<TP>(AyL), dAyP = anchor<TP>(dAy), gP = anchor<TP>(g);
 
   Tangents<TP> tg;
 #pragma unroll
@@ -219,11 +221,16 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   }
   // Eq. (12) model: x-velocity stages for lambda^c (s-scaled slopes, as for v_y)
   const double dAx = AxR - AxL, sAxL = sd * AxL, sdAxs = sd * dAx;
-  const TP AxLP = TP(AxL), dAxP = TP(dAx);
+  const TP AxLP = anchor<TP>(AxL), dAxP = anchor<TP>(dAx);
   double vx = vx0, Il = 0.0, Ir = 0.0, Ig = 0.0;  // lambda^c state part, rho^c, gamma g integrals
 
   const double h = 1.0 / nsub, h2 = 0.5 * h;
-  const TP hP = TP(h), sdP = TP(sd), h2P = TP(h2);
+  if constexpr (CK) {  // the backward sweep of the fused pass takes these over
+    ck->h = h;
+    ck->ins[0] = AxL; ck->ins[1] = AxR; ck->ins[2] = AyL; ck->ins[3] = AyR; ck->ins[4] = PL;
+    ck->ins[5] = PR; ck->ins[6] = QL; ck->ins[7] = QR; ck->ins[8] = TL; ck->ins[9] = TR;
+  }
+  const TP hP = anchor<TP>(h), sdP = anchor<TP>(sd), h2P = anchor<TP>(h2);
   const TP cjhP[4] = {TP(0), h2P, h2P, hP};
   double th = th0, om = om0, py = py0, vy = vy0, Yom = 0.0;
   double ti = 0.0;  // tau at the substep start (running sum; rounding ~1e-16 per step)
@@ -533,7 +540,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
 
   // ------------------------------------------------------------ outputs ---
   const TP one = TP(1);
-  const TP sdT = TP(sd), s2_3 = TP(sd * sd / 3.0), s2_6 = TP(sd * sd / 6.0), s_2 = TP(0.5 * sd);
+  const TP sdT = anchor<TP>(sd), s2_3 = anchor<TP>(sd2 * (1.0 / 3.0)), s2_6 = anchor<TP>(sd2 * (1.0 / 6.0)),
+           s_2 = anchor<TP>(0.5 * sd);
   // the contact's path-penalty row (after the Eq. (12) model's four cross states per contact)
   const int ry = foot ? 6 * nb + (cross ? 4 * M.nc : 0) + B.contact : -1;
   if constexpr (!CMP) {
@@ -603,7 +611,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     for (int i = 0; i < nin; ++i) {
       const int q = B.idx[i];
       const bool nzx = abs_bits(B.ax[i]) != 0ull, nzy = abs_bits(B.ay[i]) != 0ull, tq = torque(i);
-      const TP ax = TP(B.ax[i]), ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
+      const TP ax = anchor<TP>(B.ax[i]), ay = anchor<TP>(B.ay[i]), pc = anchor<TP>(B.p[i]),
+               qc = anchor<TP>(B.q[i]), tc = anchor<TP>(B.t[i]);
       const TP bmpx = ax * s2_3, bppx = ax * s2_6, bvx = ax * s_2;
       const TP bmpy = ay * s2_3, bppy = ay * s2_6, bvy = ay * s_2;
       const TP bmth = pc * tg.Pt[3] + qc * tg.Pt[4] + tc * tg.Pt[5];
@@ -664,7 +673,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       int o = B.b_off;
       for (int i = 0; i < nin; ++i) {
         const int q = B.idx[i];
-        const TP ay = TP(B.ay[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
+        const TP ay = anchor<TP>(B.ay[i]), pc = anchor<TP>(B.p[i]), qc = anchor<TP>(B.q[i]),
+                 tc = anchor<TP>(B.t[i]);
         TP vm = pc * tg.Yr[3] + qc * tg.Yr[4] + tc * tg.Yr[5] + ay * tg.Yp[3];
         TP vp = pc * tg.Yr[6] + qc * tg.Yr[7] + tc * tg.Yr[8] + ay * tg.Yp[4];
         const int d = q - cin;
@@ -723,7 +733,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       };
       for (int i = 0; i < nin; ++i) {
         const int q = B.idx[i];
-        const TP ax = TP(B.ax[i]), pc = TP(B.p[i]), qc = TP(B.q[i]), tc = TP(B.t[i]);
+        const TP ax = anchor<TP>(B.ax[i]), pc = anchor<TP>(B.p[i]), qc = anchor<TP>(B.q[i]),
+                 tc = anchor<TP>(B.t[i]);
         TP vm = ax * tg.Ylv[0] + pc * tg.Yl[3] + qc * tg.Yl[4] + tc * tg.Yl[5];
         TP vp = ax * tg.Ylv[1] + pc * tg.Yl[6] + qc * tg.Yl[7] + tc * tg.Yl[8];
         const int d = q - cin;

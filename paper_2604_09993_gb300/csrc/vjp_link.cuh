@@ -44,14 +44,20 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   const double g = M.g;
   const int nin = B.nin;
   double AxL = 0, AxR = 0, AyL = 0, AyR = 0, PL = 0, PR = 0, QL = 0, QR = 0, TL = 0, TR = 0;
-  for (int i = 0; i < nin; ++i) {
-    const int q = B.idx[i];
-    const double a = uL[q], c = uR[q];
-    AxL = fma(B.ax[i], a, AxL); AxR = fma(B.ax[i], c, AxR);
-    AyL = fma(B.ay[i], a, AyL); AyR = fma(B.ay[i], c, AyR);
-    PL = fma(B.p[i], a, PL); PR = fma(B.p[i], c, PR);
-    QL = fma(B.q[i], a, QL); QR = fma(B.q[i], c, QR);
-    TL = fma(B.t[i], a, TL); TR = fma(B.t[i], c, TR);
+  if constexpr (FUSED) {  // formed by the discretization's forward sweep
+    AxL = ckin->ins[0]; AxR = ckin->ins[1]; AyL = ckin->ins[2]; AyR = ckin->ins[3];
+    PL = ckin->ins[4]; PR = ckin->ins[5]; QL = ckin->ins[6]; QR = ckin->ins[7];
+    TL = ckin->ins[8]; TR = ckin->ins[9];
+  } else {
+    for (int i = 0; i < nin; ++i) {
+      const int q = B.idx[i];
+      const double a = uL[q], c = uR[q];
+      AxL = fma(B.ax[i], a, AxL); AxR = fma(B.ax[i], c, AxR);
+      AyL = fma(B.ay[i], a, AyL); AyR = fma(B.ay[i], c, AyR);
+      PL = fma(B.p[i], a, PL); PR = fma(B.p[i], c, PR);
+      QL = fma(B.q[i], a, QL); QR = fma(B.q[i], c, QR);
+      TL = fma(B.t[i], a, TL); TR = fma(B.t[i], c, TR);
+    }
   }
   const int rpx = 3 * b, rpy = rpx + 1, rth = rpx + 2;
   const int rvx = 3 * nb + 3 * b, rvy = rvx + 1, rom = rvx + 2;
@@ -70,16 +76,18 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
     for (int m = 0; m < 3; ++m) {
       cL[m] = uL[cin + m];
       cD[m] = uR[cin + m] - cL[m];
-      cLP[m] = TP(cL[m]);
-      cDP[m] = TP(cD[m]);
+      cLP[m] = anchor<TP>(cL[m]);
+      cDP[m] = anchor<TP>(cD[m]);
     }
   }
   const double mu = B.mu, crx = B.crho[0], cry = B.crho[1];
-  const TP muP = TP(mu), crxP = TP(crx), cryP = TP(cry);
-  const TP PLP = TP(PL), dPP = TP(dP), QLP = TP(QL), dQP = TP(dQ), TLP = TP(TL), dTP = TP(dT);
-  const TP AyLP = TP(AyL), dAyP = TP(dAy), gP = TP(g);
-  const double h = 1.0 / nsub, h2 = 0.5 * h;
-  const TP sdP = TP(sd), hP = TP(h), h2P = TP(h2);
+  const TP muP = anchor<TP>(mu), crxP = anchor<TP>(crx), cryP = anchor<TP>(cry);
+  // FP32 copies narrowed on the integer pipe (see to_f32_rz)
+  const TP PLP = anchor<TP>(PL), dPP = anchor<TP>(dP), QLP = anchor<TP>(QL), dQP = anchor<TP>(dQ),
+           TLP = anchor<TP>(TL), dTP = anchor<TP>(dT);
+  const TP AyLP = anchor<TP>(AyL), dAyP = anchor<TP>(dAy), gP = anchor<TP>(g);
+  const double h = FUSED ? ckin->h : 1.0 / nsub, h2 = 0.5 * h;
+  const TP sdP = anchor<TP>(sd), hP = anchor<TP>(h), h2P = anchor<TP>(h2);
   const TP cjhP[4] = {TP(0), h2P, h2P, hP};
 
   // ---- forward sweep: FP64 state and checkpoints ----
@@ -185,8 +193,8 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   if (FOOT) { ry_ = 6 * nb + B.contact; wy = wk[ry_]; lam_y = wy + rho_c; }
 
   // ---- backward sweep ----
-  TP lth = TP(wth), lom = TP(wom), lpy = TP(0), lvy = TP(0);
-  const TP ly = TP(lam_y);
+  TP lth = anchor<TP>(wth), lom = anchor<TP>(wom), lpy = TP(0), lvy = TP(0);
+  const TP ly = anchor<TP>(lam_y);
   TP gsd = TP(0), gPL = TP(0), gPR = TP(0), gQL = TP(0), gQR = TP(0), gTL = TP(0), gTR = TP(0);
   TP gAyL = TP(0), gAyR = TP(0), gd[6] = {TP(0), TP(0), TP(0), TP(0), TP(0), TP(0)};
   // input penalty at the end of the current substep (FP64 values only for the
@@ -331,7 +339,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   }
 
   // ---- translation: transposed closed forms ----
-  const double s2_3 = sd * sd / 3.0, s2_6 = sd * sd / 6.0, s_2 = 0.5 * sd;
+  const double s2_3 = sd * sd * (1.0 / 3.0), s2_6 = sd * sd * (1.0 / 6.0), s_2 = 0.5 * sd;
   const double gAxL = wpx * s2_3 + wvx * s_2, gAxR = wpx * s2_6 + wvx * s_2;
   const double gAyLt = wpy * s2_3 + wvy * s_2 + double(gAyL), gAyRt = wpy * s2_6 + wvy * s_2 + double(gAyR);
   const double gsd_t = wpx * (vx0 + 2.0 * sd * ax3) + wvx * axm + wpy * (vy0 + 2.0 * sd * ay3) +
