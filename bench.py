@@ -40,6 +40,7 @@ from paper_2604_09993_gb300 import synth  # noqa: E402
 
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
 # x 2 flop x 2.07 GHz (a microbenchmark measured 1.196 TFLOP/s at 1.99 GHz).
+METRIC = "linearized intervals/s (STM + adjoint VJP) vs plain FP64 GPU path at stated error"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 126 * 2 ** 20
 
@@ -832,8 +833,13 @@ def run_ours(args):
 
     if rank != 0:
         return
+    fp64 = None if t64 is None else {
+        "value": units * args.steps / t64, "unit": "intervals/s", "ms_per_step": t64 / args.steps * 1e3,
+        "discretize_ms": kd64 * 1e3, "headline_speedup": t64 / t,
+        "stated_error": "FP64 path: every block rel <= 1e-10; headline: Phi blocks rel <= 1e-4, "
+                        "defect/penalty/state rel <= 1e-10 (block-normwise, vs the FP64 oracle)"}
     line = {
-        "metric": "linearized intervals/s (STM + adjoint VJP)",
+        "metric": METRIC,
         "value": value, "unit": "intervals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
@@ -844,24 +850,25 @@ def run_ours(args):
                    "l2": ("inputs larger than L2" if L2_FLUSH is None
                           else "L2 flushed before every timed step (buffer of twice the L2 written)"),
                    "tune": wl.tune(prec)},
-        "fp64_path": None if t64 is None else {
-            "value": units * args.steps / t64, "ms_per_step": t64 / args.steps * 1e3,
-            "discretize_ms": kd64 * 1e3, "headline_speedup": t64 / t},
         # launches of this library per timed step: batch = fused discretize+VJP + finish;
         # single = disc + vjp + gU + gs + L
         "gpu_launches": args.steps * (2 if spec["kind"] == "batch" else 5),
         "roofline": roof,
+        "clocks": clocks,
         "e2e": e2e,
+        # secondary legs (other rows of the hot path on the same box)
         "compact_outputs": compact,
         "node_constraints": nodes,
         "psi": psi,
         "socp": socp,
         "aux_cross_model": cross,
         "paper_dynamics": paper,
-        "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
+    # last, so that it stays in any tail of this line: the metric's comparator,
+    # the plain FP64 GPU path on the same workload and GPU
+    line["fp64_path"] = fp64
     print(json.dumps(line))
 
 
@@ -874,7 +881,7 @@ def run_reference(args):
         cpu_baseline(args.workload, budget_s=1.0)
     vals = [cpu_baseline(args.workload, budget_s=3.0) for _ in range(args.steps)]
     v = statistics.mean(x["value"] for x in vals)
-    line = {"impl": "reference", "metric": "linearized intervals/s (STM + adjoint VJP)", "value": v,
+    line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "intervals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded robots; no dataset)", "config": {"workload": args.workload},

@@ -84,7 +84,11 @@ typedef enum {
 typedef enum {
   CISCVX_FP64 = 0,      /* state, penalty and Phi blocks in FP64 */
   CISCVX_FP32_PHI = 1,  /* Phi blocks (A, B-, B+, S) propagated and stored in FP32;
-                           state, defect and penalty stay FP64 */
+                           state, defect and penalty stay FP64.  Accuracy is
+                           block-normwise (error <= 1e-4 of max|block|, an
+                           absolute error on the block's scale): entries far
+                           below that scale carry no relative accuracy; use
+                           CISCVX_FP64 where small entries matter one by one */
   CISCVX_TF32_TC = 2,   /* reserved: tensor-core Phi products; returns EUNSUPPORTED */
   CISCVX_BF16_TC = 3    /* reserved: tensor-core Phi products; returns EUNSUPPORTED */
 } ciscvx_precision;
@@ -818,10 +822,24 @@ ciscvx_status ciscvx_socp_fill(const ciscvx_socp* socp, int n_inst, const ciscvx
  *   Calls share the one array: calls whose work overlaps on the GPU (other
  *   streams or host threads) race; serialize them.  Nothing in the array
  *   needs clearing (every scratch element is written before it is read).
- *   Calls no cudaMalloc, cudaFree or other allocating routine.
- * Errors: as ciscvx_discretize_vjp, and CISCVX_EUNSUPPORTED when N intervals
- * of this model need more scratch than CISCVX_STATIC_SCRATCH_BYTES
- * (ciscvx_workspace_size(CISCVX_OP_VJP) tells how much). */
+ *   The cached address is valid for the life of the device's primary
+ *   context; after cudaDeviceReset do not call this entry point on that
+ *   device again in the same process.
+ *   Calls no cudaMalloc, cudaFree or other allocating routine.  One
+ *   exception at set-up: for a model with coupled links, the first call for
+ *   a model shape and precision in the process compiles and loads the
+ *   run-time specialized kernels (the runtime takes device memory for the
+ *   loaded code); make that call, or any ciscvx_discretize /
+ *   ciscvx_discretize_vjp call of that model and precision, at set-up.
+ *   Models: all of them.  Per-link models with one penalty state per contact
+ *   run the adjoint kernel, whose scratch is ciscvx_workspace_size(
+ *   CISCVX_OP_VJP) for N intervals.  Models whose VJP is linearize-and-
+ *   contract (coupled links, Eq. (12) auxiliary state) run in chunks of the
+ *   intervals whose dense blocks fit the array; their minimum is the
+ *   min_bytes of ciscvx_discretize_workspace_size(CISCVX_OP_VJP).
+ * Errors: as ciscvx_discretize_vjp, and CISCVX_EUNSUPPORTED when the minimum
+ * scratch of this request (min_bytes of ciscvx_discretize_workspace_size with
+ * CISCVX_OP_VJP) exceeds CISCVX_STATIC_SCRATCH_BYTES. */
 ciscvx_status ciscvx_discretize_vjp_static(const ciscvx_model* model, int N, int n_sub,
                                            ciscvx_precision precision, ciscvx_u_layout layout,
                                            const double* X, const double* U, const double* s,

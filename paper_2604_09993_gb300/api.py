@@ -20,6 +20,7 @@ PRECISION = {"fp64": 0, "fp32_phi": 1, "tf32_tc": 2, "bf16_tc": 3}
 LAYOUT = {"node": 0, "interval": 1}
 NODE_THETA_COLS = 12  # CISCVX_NODE_THETA_COLS
 OP_DISCRETIZE, OP_VJP = 0, 1
+STATIC_SCRATCH_BYTES = 16 * 1024 * 1024  # CISCVX_STATIC_SCRATCH_BYTES
 
 # Every symbol include/ciscvx.h declares.
 EXPORTS = (

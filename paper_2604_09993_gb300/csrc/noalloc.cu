@@ -15,12 +15,22 @@
 // address, so on its first call on a device (with that device current) the
 // entry point asks the runtime for the array's device address with
 // cudaGetSymbolAddress, checks the result, and caches it for that device.
-// That first call should therefore come before any stream capture.  No
-// cudaMalloc, cudaFree or allocating library routine is called.  Every call
-// shares the one array: two calls whose work overlaps on the GPU (different
-// streams or host threads) race and corrupt each other's results, so callers
-// must serialize them.  The VJP writes every scratch element before reading
-// it, so nothing needs clearing between calls.
+// That first call should therefore come before any stream capture.  The
+// cached address stays valid for the life of the device's primary context: a
+// cudaDeviceReset (or any teardown of that context) invalidates it, so a
+// process that resets a device must not call this entry point on it again.
+// No cudaMalloc, cudaFree or allocating library routine is called.  Every
+// call shares the one array: two calls whose work overlaps on the GPU
+// (different streams or host threads) race and corrupt each other's results,
+// so callers must serialize them.  The VJP writes every scratch element
+// before reading it, so nothing needs clearing between calls.
+//
+// Sizing: the request is sized with ciscvx_discretize_workspace_size.  For
+// models whose VJP is the adjoint kernel (per-link models with one penalty
+// state per contact) the scratch is one fixed size for N.  For models whose
+// VJP is linearize-and-contract (coupled links, Eq. (12) auxiliary state) the
+// work runs in chunks of intervals that fit the scratch, so only the minimum
+// (a chunk of up to 32 intervals) has to fit.
 #include <mutex>
 
 #include "common.cuh"
@@ -64,12 +74,14 @@ extern "C" ciscvx_status ciscvx_discretize_vjp_static(
     const double* rho, double* gX, double* gU, double* gs, double* L, void* stream) {
   if (!model) return ciscvx::set_error(CISCVX_EINVAL, "null model");
   size_t need = 0;
-  ciscvx_status st = ciscvx_workspace_size(model, CISCVX_OP_VJP, N, layout, &need);
+  ciscvx_status st = ciscvx_discretize_workspace_size(model, CISCVX_OP_VJP, N, n_sub, precision,
+                                                      layout, &need, nullptr);
   if (st != CISCVX_OK) return st;
   if (need > kScratchBytes)
     return ciscvx::set_error(CISCVX_EUNSUPPORTED,
-                             "this VJP needs %zu bytes of scratch; the built-in static scratch holds "
-                             "%zu bytes (use ciscvx_discretize_vjp with a workspace, or fewer intervals)",
+                             "this VJP needs at least %zu bytes of scratch; the built-in static "
+                             "scratch holds %zu bytes (use ciscvx_discretize_vjp with a workspace, "
+                             "or fewer intervals)",
                              need, kScratchBytes);
   void* scratch = nullptr;
   st = scratch_address(&scratch);

@@ -24,6 +24,41 @@ TUNES = [
     {"warps_per_cta": 2, "ctas_per_sm": 0, "lpt_order": 1, "use_graph": 0, "occupancy": 2},
 ]
 
+# The fused pass's autotuner candidates (warps per CTA, CTAs per SM, item
+# order, graph, register-cap variant), as the library lists them: every
+# launch shape the tuner can pick is run by the parity tests below, and the
+# full-size test asserts that its pick is one of them.
+FUSED_CANDIDATES = [
+    (4, 2, 1, 0, 0), (8, 1, 1, 0, 0), (2, 4, 1, 0, 0), (1, 8, 1, 0, 0), (4, 0, 1, 0, 0),
+    (4, 2, 0, 0, 0), (4, 3, 1, 0, 1), (2, 6, 1, 0, 1), (4, 4, 1, 0, 2), (2, 8, 1, 0, 2),
+    (4, 0, 1, 0, 1), (4, 0, 1, 0, 2),
+]
+_TUNE_KEYS = ("warps_per_cta", "ctas_per_sm", "lpt_order", "use_graph", "occupancy")
+
+
+def _tune_dict(c):
+    return dict(zip(_TUNE_KEYS, c))
+
+
+def _tune_tuple(t):
+    return tuple(int(t[k]) for k in _TUNE_KEYS)
+
+
+# oracle results are independent of the launch shape: computed once per input set
+_ORACLE_CACHE = {}
+
+
+def _oracle_refs(oracle, key, probs, layout="node"):
+    if (key, layout) not in _ORACLE_CACHE:
+        refs = []
+        for p in probs:
+            Ui = p.U if layout == "node" else p.U_interval()
+            R = p.robot.as_dict()
+            refs.append((oracle.discretize(R, p.X, Ui, p.s, p.n_sub, layout=layout),
+                         oracle.vjp(R, p.X, Ui, p.s, p.w, p.rho, p.n_sub, layout=layout)))
+        _ORACLE_CACHE[(key, layout)] = refs
+    return _ORACLE_CACHE[(key, layout)]
+
 
 @pytest.fixture(scope="module")
 def env():
@@ -184,9 +219,11 @@ def test_mixed_1024_sampled(env):
         assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
 
 
-def test_sweep_4096x400x20_sampled(env):
-    """The 4096-instance sweep at full size (FP32 Phi): sampled intervals checked one by one,
-    four instances' VJPs checked whole; a graph replay reproduces the outputs bit for bit."""
+@pytest.fixture(scope="module")
+def sweep(env):
+    """The 4096 x 400 x 20 sweep packed on the device, with the oracle's
+    results for the sampled intervals (8 random instances plus the first and
+    the last, 8 intervals each) and three instances' whole VJPs."""
     torch, oracle, api = env
     dev = torch.device("cuda:0")
     b = synth.cheetah_sweep(seed=0)
@@ -194,26 +231,58 @@ def test_sweep_4096x400x20_sampled(env):
     plan = api.BatchPlan([model], b.model_idx, b.Ns, b.n_subs, precision="fp32_phi")
     probs = [b.instance(i) for i in range(len(b))]
     X, U, s, w, rho = _packed(plan, probs, dev, torch)
-    out = plan.discretize(X, U, s)
-    torch.cuda.synchronize()
     rng = np.random.default_rng(2)
     inst = sorted(rng.choice(len(b), 8, replace=False)) + [0, len(b) - 1]
     R = b.robots[0].as_dict()
-    nxt, nu = b.robots[0].nxt, b.robots[0].nu
+    samples = []
     for i in inst:
         p = probs[i]
-        o = plan.offsets[i]
         for k in sorted(set(rng.choice(p.N, 6, replace=False).tolist() + [0, p.N - 1])):
             x1, A, Bm, Bp, S = oracle.interval(R, p.n_sub, p.X[k], p.U[k], p.U[k + 1], p.s[k])
-            a0 = o["A"] + k * nxt * nxt
-            b0 = o["B"] + k * nxt * nu
-            v0 = o["S"] + k * nxt
-            assert block_err(out["A"][a0:a0 + nxt * nxt].double().cpu().numpy(), A.ravel()) <= TOL_FP32_PHI
-            assert block_err(out["Bm"][b0:b0 + nxt * nu].double().cpu().numpy(), Bm.ravel()) <= TOL_FP32_PHI
-            assert block_err(out["Bp"][b0:b0 + nxt * nu].double().cpu().numpy(), Bp.ravel()) <= TOL_FP32_PHI
-            assert block_err(out["S"][v0:v0 + nxt].double().cpu().numpy(), S) <= TOL_FP32_PHI
-            d = out["defect"][v0:v0 + nxt].cpu().numpy()
-            assert block_err(d, x1 - p.X[k + 1]) <= TOL_FP64
+            samples.append((i, k, A, Bm, Bp, S, x1 - p.X[k + 1]))
+    vjps = {}
+    for i in (0, 1234, 4095):
+        p = probs[i]
+        vjps[i] = oracle.vjp(R, p.X, p.U, p.s, p.w, p.rho, p.n_sub, threads=0)
+    return dict(b=b, model=model, plan=plan, inputs=(X, U, s, w, rho), samples=samples, vjps=vjps)
+
+
+def _check_sweep_samples(plan, out, sw):
+    b = sw["b"]
+    nxt, nu = b.robots[0].nxt, b.robots[0].nu
+    for i, k, A, Bm, Bp, S, dref in sw["samples"]:
+        o = plan.offsets[i]
+        a0 = o["A"] + k * nxt * nxt
+        b0 = o["B"] + k * nxt * nu
+        v0 = o["S"] + k * nxt
+        assert block_err(out["A"][a0:a0 + nxt * nxt].double().cpu().numpy(), A.ravel()) <= TOL_FP32_PHI
+        assert block_err(out["Bm"][b0:b0 + nxt * nu].double().cpu().numpy(), Bm.ravel()) <= TOL_FP32_PHI
+        assert block_err(out["Bp"][b0:b0 + nxt * nu].double().cpu().numpy(), Bp.ravel()) <= TOL_FP32_PHI
+        assert block_err(out["S"][v0:v0 + nxt].double().cpu().numpy(), S) <= TOL_FP32_PHI
+        d = out["defect"][v0:v0 + nxt].cpu().numpy()
+        assert block_err(d, dref) <= TOL_FP64
+
+
+def _check_sweep_vjps(plan, g, sw):
+    gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
+    for i, (rX, rU, rs, rL) in sw["vjps"].items():
+        assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= 1e-4
+        assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
+        assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= 1e-4
+        assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
+
+
+def test_sweep_4096x400x20_sampled(env, sweep):
+    """The 4096-instance sweep at full size (FP32 Phi), separate calls: sampled
+    intervals checked one by one, three instances' VJPs checked whole; a graph
+    replay reproduces the outputs bit for bit."""
+    torch, oracle, api = env
+    plan = sweep["plan"]
+    X, U, s, w, rho = sweep["inputs"]
+    nxt = sweep["b"].robots[0].nxt
+    out = plan.discretize(X, U, s)
+    torch.cuda.synchronize()
+    _check_sweep_samples(plan, out, sweep)
     # replay reproduces bit for bit
     d0 = out["defect"].clone()
     a0 = out["A"][: 10 * nxt * nxt].clone()
@@ -223,14 +292,41 @@ def test_sweep_4096x400x20_sampled(env):
     del out
     g = plan.discretize_vjp(X, U, s, w, rho)
     plan.sync_status()
-    gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
-    for i in (0, 1234, 4095):
-        p = probs[i]
-        rX, rU, rs, rL = oracle.vjp(R, p.X, p.U, p.s, p.w, p.rho, p.n_sub, threads=0)
-        assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= 1e-4
-        assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
-        assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= 1e-4
-        assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
+    _check_sweep_vjps(plan, g, sweep)
+    del g
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("shape", ["autotune", (4, 2, 1, 0, 0), (4, 4, 1, 0, 2), (4, 3, 1, 0, 1)],
+                         ids=["autotuned", "occ0", "occ2", "occ1"])
+def test_sweep_fused_pass_full_size_sampled(env, sweep, shape):
+    """The fused pass (ciscvx_batch_discretize_and_vjp, the bench's step) on the
+    full 4096 x 400 x 20 sweep under the autotuner's pick and under each
+    register-cap variant: the same sampled intervals and instance VJPs against
+    the oracle.  The autotuner's pick is one of the candidates the small-batch
+    test runs one by one."""
+    torch, oracle, api = env
+    b = sweep["b"]
+    X, U, s, w, rho = sweep["inputs"]
+    if shape == "autotune":
+        plan = sweep["plan"]
+        ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=X.device)
+        out = plan.alloc_outputs(X.device)
+        pick = plan.autotune_fused(X, U, s, w, rho, workspace=ws, out=out)
+        assert _tune_tuple(pick) in FUSED_CANDIDATES, pick
+        assert _tune_tuple(plan.tune_fused()) == _tune_tuple(pick)
+    else:
+        plan = api.BatchPlan([sweep["model"]], b.model_idx, b.Ns, b.n_subs, precision="fp32_phi",
+                             tune=_tune_dict(shape))
+        assert plan.tune_fused()["occupancy"] == shape[4]
+        ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=X.device)
+        out = plan.alloc_outputs(X.device)
+    out, g = plan.discretize_and_vjp(X, U, s, w, rho, workspace=ws, out=out)
+    plan.sync_status()
+    _check_sweep_samples(plan, out, sweep)
+    _check_sweep_vjps(plan, g, sweep)
+    del out, g, ws
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("n_chunks", [1, 3, 24])
@@ -323,19 +419,16 @@ def test_sweep_precision_report_16_instances(env, capsys):
         assert bw <= (TOL_FP32_PHI if k in ("A", "Bm", "Bp", "S") else TOL_FP64), (k, bw)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
-@pytest.mark.parametrize("out_format", ["dense", "compact"])
-@pytest.mark.parametrize("layout", ["node", "interval"])
-def test_fused_pass_matches_separate_calls_and_oracle(env, precision, out_format, layout):
-    """ciscvx_batch_discretize_and_vjp: the linearization and the VJP from one
-    pass equal the separate calls to rounding, and the oracle to the usual
-    tolerances."""
+def _fused_check(env, precision, out_format, layout, tune):
     torch, oracle, api = env
     dev = torch.device("cuda:0")
     robots, probs, midx = _small_mixed(seed=13, n=18)
     models = [api.Model(r) for r in robots]
     plan = api.BatchPlan(models, midx, [p.N for p in probs], [p.n_sub for p in probs],
-                         precision=precision, layout=layout, out_format=out_format)
+                         precision=precision, layout=layout, out_format=out_format, tune=tune)
+    if tune is not None:
+        assert _tune_tuple(plan.tune_fused())[:3] == _tune_tuple(tune)[:3]
+        assert plan.tune_fused()["occupancy"] == tune["occupancy"]
     X, U, s, w, rho = _packed(plan, probs, dev, torch, layout)
     out, g = plan.discretize_and_vjp(X, U, s, w, rho)
     sep = plan.discretize(X, U, s)
@@ -351,10 +444,10 @@ def test_fused_pass_matches_separate_calls_and_oracle(env, precision, out_format
         e = block_err(g[k].cpu().numpy(), gsep[k].cpu().numpy())
         assert e <= (1e-5 if f32 else 1e-12), (k, e)
     tol = 1e-4 if f32 else 1e-10
+    refs = _oracle_refs(oracle, ("small_mixed", 13, 18), probs, layout)
     gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
     for i, p in enumerate(probs):
-        Ui = p.U if layout == "node" else p.U_interval()
-        rX, rU, rs, rL = oracle.vjp(p.robot.as_dict(), p.X, Ui, p.s, p.w, p.rho, p.n_sub, layout=layout)
+        rX, rU, rs, rL = refs[i][1]
         assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= tol, i
         assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= tol, i
         assert block_err(plan.unpack(gs, "s", i, rs.shape), rs) <= tol, i
@@ -362,9 +455,28 @@ def test_fused_pass_matches_separate_calls_and_oracle(env, precision, out_format
     if out_format == "dense":
         host = {k: v.double().cpu().numpy() for k, v in out.items()}
         for i, p in enumerate(probs):
-            Ui = p.U if layout == "node" else p.U_interval()
-            ref = oracle.discretize(p.robot.as_dict(), p.X, Ui, p.s, p.n_sub, layout=layout)
-            _check_instance(plan, host, i, p, ref, precision)
+            _check_instance(plan, host, i, p, refs[i][0], precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("out_format", ["dense", "compact"])
+@pytest.mark.parametrize("layout", ["node", "interval"])
+def test_fused_pass_matches_separate_calls_and_oracle(env, precision, out_format, layout):
+    """ciscvx_batch_discretize_and_vjp: the linearization and the VJP from one
+    pass equal the separate calls to rounding, and the oracle to the usual
+    tolerances."""
+    _fused_check(env, precision, out_format, layout, None)
+
+
+@pytest.mark.parametrize("cand", FUSED_CANDIDATES, ids=lambda c: "w%d-c%d-l%d-g%d-occ%d" % c)
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("out_format", ["dense", "compact"])
+def test_fused_pass_every_tuner_candidate(env, cand, precision, out_format):
+    """The fused pass under every launch shape its autotuner can pick, in
+    particular each register-cap variant (occupancy 0: uncapped, 1: at most
+    168 registers, 2: at most 128 registers, the one the tuner picks for the
+    4096 x 400 x 20 sweep), against the separate calls and the oracle."""
+    _fused_check(env, precision, out_format, "node", _tune_dict(cand))
 
 
 def test_autotune_fused_keeps_results(env):
