@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "state_df.cuh"
 
 namespace ciscvx {
 
@@ -125,6 +126,120 @@ __device__ __forceinline__ InputCross<TP> input_cross(double t, TP tP, TP sdP, d
   r.q0 = sdP * gaP * rtP * rtP * rtP;
   r.q2 = sdP * dft;
   return r;
+}
+
+// Stage data of one substep for the tangent recursion (tangent precision).
+template <typename TP>
+struct StageT {
+  TP cw[4], sw[4], sath[4], oms[4], wdt[4], tau[4];
+  TP gr[4], gp[4], vys[4], ays[4], dl0[4], dl1[4], dl2[4];
+  TP lry[4], lrx[4], axs[4], cq0[4], cq2[4], cr0[4], cr1[4];  // Eq. (12) model
+};
+
+// One substep of the tangent recursion (IND, Sec. VI) of one link from its
+// stage data: the nine rotation columns, the foot's p_y channel and penalty
+// row, and (CROSS) the lambda^c row.
+template <typename TP, bool FOOT, bool CROSS>
+__device__ __forceinline__ void tangent_substep(Tangents<TP>& tg, const StageT<TP>& st, TP sdP, TP hP,
+                                                const TP* cjhP) {
+  constexpr bool foot = FOOT;
+  constexpr bool cross = FOOT && CROSS;
+  // ---- rotation tangents: 9 columns, 4 stages each ----
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const TP T0 = tg.Pt[c], W0 = tg.Pw[c];
+    TP kT = TP(0), kW = TP(0), aT = TP(0), aW = TP(0), ya = TP(0), yl = TP(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const TP cjh = cjhP[j], wj = TP(rk_w(j));
+      const TP Ts = (j == 0) ? T0 : T0 + cjh * kT;
+      const TP Ws = (j == 0) ? W0 : W0 + cjh * kW;
+      const TP wl = TP(1) - st.tau[j], wr = st.tau[j];
+      TP fT = TP(0), fW = TP(0);
+      if (c == 2) { fT = st.oms[j]; fW = st.wdt[j]; }
+      else if (c == 3) fW = sdP * st.cw[j] * wl;
+      else if (c == 4) fW = -sdP * st.sw[j] * wl;
+      else if (c == 5) fW = sdP * wl;
+      else if (c == 6) fW = sdP * st.cw[j] * wr;
+      else if (c == 7) fW = -sdP * st.sw[j] * wr;
+      else if (c == 8) fW = sdP * wr;
+      kT = sdP * Ws + fT;
+      kW = st.sath[j] * Ts + fW;
+      aT += wj * kT;
+      aW += wj * kW;
+      if (foot) ya += wj * st.gr[j] * Ts;
+      if constexpr (cross) yl += wj * (st.lry[j] * Ws + st.lrx[j] * Ts);
+    }
+    tg.Pt[c] = T0 + hP * aT;
+    tg.Pw[c] = W0 + hP * aW;
+    if (foot) tg.Yr[c] += hP * ya;
+    if constexpr (cross) tg.Yl[c] += hP * yl;
+  }
+
+  // ---- foot: p_y channel tangents and the penalty row ----
+  if (foot) {
+    TP y0 = TP(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y0 += TP(rk_w(j)) * st.gp[j];
+    tg.Yp[0] += hP * y0;  // p_y0 column: stage tangent of p_y is 1
+#pragma unroll
+    for (int c = 1; c < 5; ++c) {
+      const TP P0 = tg.Qp[c], V0 = tg.Qv[c];
+      TP kP = TP(0), kV = TP(0), aP = TP(0), aV = TP(0), ya = TP(0), yv = TP(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const TP cjh = cjhP[j], wj = TP(rk_w(j));
+        const TP Ps = (j == 0) ? P0 : P0 + cjh * kP;
+        const TP Vs = (j == 0) ? V0 : V0 + cjh * kV;
+        TP fP = TP(0), fV = TP(0);
+        if (c == 2) { fP = st.vys[j]; fV = st.ays[j]; }
+        else if (c == 3) fV = sdP * (TP(1) - st.tau[j]);
+        else if (c == 4) fV = sdP * st.tau[j];
+        kP = sdP * Vs + fP;
+        kV = fV;
+        aP += wj * kP;
+        aV += wj * kV;
+        ya += wj * st.gp[j] * Ps;
+        // unit-forcing tangents of v_y equal those of v_x (same equation v' = s a)
+        if constexpr (cross) yv += wj * sdP * Vs;
+      }
+      tg.Qp[c] = P0 + hP * aP;
+      tg.Qv[c] = V0 + hP * aV;
+      tg.Yp[c] += hP * ya;
+      if constexpr (cross) {
+        if (c >= 3) tg.Ylv[c - 3] += hP * yv;
+      }
+    }
+    if constexpr (cross) {
+      // v_x tangent with respect to s (forcing a_x(tau)); lambda^c's s column
+      const TP V0 = tg.Vxs;
+      TP kV = TP(0), aV = TP(0), yv = TP(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const TP wj = TP(rk_w(j));
+        const TP Vs = (j == 0) ? V0 : V0 + cjhP[j] * kV;
+        kV = st.axs[j];
+        aV += wj * kV;
+        yv += wj * sdP * Vs;
+      }
+      tg.Vxs = V0 + hP * aV;
+      tg.Ylv[2] += hP * yv;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const TP hw = hP * TP(rk_w(j));
+      const TP wl = TP(1) - st.tau[j], wr = st.tau[j];
+      tg.Yd[0] += hw * st.dl0[j] * wl; tg.Yd[3] += hw * st.dl0[j] * wr;
+      tg.Yd[1] += hw * st.dl1[j] * wl; tg.Yd[4] += hw * st.dl1[j] * wr;
+      tg.Yd[2] += hw * st.dl2[j] * wl; tg.Yd[5] += hw * st.dl2[j] * wr;
+      if constexpr (cross) {
+        tg.Yld[0] += hw * st.cq0[j] * wl; tg.Yld[1] += hw * st.cq0[j] * wr;
+        tg.Yld[2] += hw * st.cq2[j] * wl; tg.Yld[3] += hw * st.cq2[j] * wr;
+        tg.Yrd[0] += hw * st.cr0[j] * wl; tg.Yrd[1] += hw * st.cr0[j] * wr;
+        tg.Yrd[2] += hw * st.cr1[j] * wl; tg.Yrd[3] += hw * st.cr1[j] * wr;
+      }
+    }
+  }
 }
 
 // One link of one interval.  xk/xk1: node states k and k+1; uL/uR: FOH
@@ -263,278 +378,239 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   const double sc2 = sd * h2, sc3 = sd * h;
   double sPi = sPL, sQi = sQL, sTi = sTL;
 
-  for (int i = 0; i < nsub; ++i) {
-    if constexpr (CK && !F32) {
-      ck->th[i] = th; ck->om[i] = om; ck->s[i] = sth; ck->c[i] = cth;
-      if (foot) { ck->py[i] = py; ck->vy[i] = vy; }
-    }
-    // ---- state stages (FP64) ----
-    TP cw[4], sw[4], sath[4], oms[4], wdt[4], tau[4];
-    TP gr[4], gp[4], vys[4], ays[4], dl0[4], dl1[4], dl2[4];
-    TP lry[4], lrx[4], axs[4], vxP[4], cq0[4], cq2[4], cr0[4], cr1[4];  // Eq. (12) model
-    const double tm = ti + h2, te = ti + h;
-    const TP tmP = tiP + h2P, teP = tiP + hP;
-    InputPenalty<TP> ipm, ip1;
-    InputCross<TP> icm, ic1;
-    if constexpr (cross) {
-      icm = input_cross<TP>(tm, tmP, sdP, mu, muP, cL, cD, cLP, cDP);
-      ic1 = input_cross<TP>(te, teP, sdP, mu, muP, cL, cD, cLP, cDP);
-    } else if (foot) {
-      ipm = input_penalty<TP>(tm, tmP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
-      ip1 = input_penalty<TP>(te, teP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
-    }
-    // FP32 copy of the stage recursion, anchored on the FP64 state (FP32-Phi
-    // mode; the anchors are narrowed on the integer pipe).  With CK the
-    // anchors are the checkpoints: the FP32 backward sweep starts from them.
-    const TP thA = anchor<TP>(th), omA = anchor<TP>(om), pyA = anchor<TP>(py), vyA = anchor<TP>(vy);
-    const TP vxA = cross ? anchor<TP>(vx) : TP(0);
-    if constexpr (CK && F32) {
-      ck->thf[i] = thA; ck->omf[i] = omA;
-      if (foot) { ck->pyf[i] = pyA; ck->vyf[i] = vyA; }
-    }
-    TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0), kvxA = TP(0);
-    double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
-    double kvx = 0, avx = 0;  // Eq. (12) model: s a_x at the stage, its RK4 sum
-    const double som = sd * om, svy = foot ? sd * vy : 0.0;
-    double sPm = 0, sQm = 0, sTm = 0;
-    double ws = 0, P = 0, Q = 0, T = 0;  // FP64 stage data (FP64 mode only)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const double wj = rk_w(j);
-      const double cjh = (j == 0) ? 0.0 : (j == 3 ? h : h2);
-      const double tj = (j == 0) ? ti : (j == 3 ? te : tm);
-      const double dth = cjh * kth;
-      double sn, cs;
-      if (j == 0) { sn = sth; cs = cth; }
-      else sincos_step(th, sth, cth, dth, amask, sn, cs);
-      // Eq. (12) model: omega at the stage (kom is still the previous stage's slope)
-      const double wst = cross ? ((j == 0) ? om : fma(cjh, kom, om)) : 0.0;
-      if constexpr (F32) {
-        double sP, sQ, sT;
-        if (j == 0) { sP = sPi; sQ = sQi; sT = sTi; }
-        else if (j == 3) {
-          sPi = fma(te, sdPs, sPL); sQi = fma(te, sdQs, sQL); sTi = fma(te, sdTs, sTL);
-          sP = sPi; sQ = sQi; sT = sTi;
-        } else {
-          if (j == 1) { sPm = fma(tm, sdPs, sPL); sQm = fma(tm, sdQs, sQL); sTm = fma(tm, sdTs, sTL); }
-          sP = sPm; sQ = sQm; sT = sTm;
-        }
-        kth = (j == 0) ? som : fma(j == 3 ? sc3 : sc2, kom, som);
-        kom = fma(cs, sP, fma(-sn, sQ, sT));
-      } else {
-        ws = (j == 0) ? om : fma(cjh, kom, om);
-        P = fma(tj, dP, PL); Q = fma(tj, dQ, QL); T = fma(tj, dT, TL);
-        kth = sd * ws;
-        kom = sd * fma(cs, P, fma(-sn, Q, T));
+  // FP32-Phi mode of the default model: stage values in float-float on the
+  // FP32 pipe, the state accumulated in FP64 (state_df.cuh); the tangent
+  // recursion takes its FP32 stage data from the same pass.
+  constexpr bool DF = F32 && !CROSS;
+  if constexpr (DF) {
+    const DfLink C = df_link(sd, nsub, PL, dP, QL, dQ, TL, dT, AyL, dAy, g, foot, crx, cry, mu, cL, cD);
+    DfState S = df_state_init<FOOT>(C, th0, om0, py0, vy0);
+    InputPenalty<TP> ipA, ipB;  // FP32 slopes of the input-only terms at the substep start / end
+    if (foot) ipA = input_penalty<TP, false>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+    for (int i = 0; i < nsub; ++i) {
+      if constexpr (CK) {  // FP32 anchors at the substep start: the backward sweep's checkpoints
+        ck->thf[i] = anchor<TP>(S.th); ck->omf[i] = anchor<TP>(S.om);
+        if (foot) { ck->pyf[i] = anchor<TP>(S.py); ck->vyf[i] = anchor<TP>(S.vy); }
       }
-      ath_ = fma(wj, kth, ath_);
-      aom_ = fma(wj, kom, aom_);
-      double pys = 0.0, vs = 0.0;
+      StageF sf[4];
+      df_substep<FOOT, true>(C, i, amask, S, sf);
+      StageT<TP> st;
+      InputPenalty<TP> ipM;
       if (foot) {
-        pys = (j == 0) ? py : fma(cjh, kpy, py);
-        if constexpr (F32) {
-          kpy = (j == 0) ? svy : fma(j == 3 ? sc3 : sc2, kvy, svy);
-          kvy = fma(tj, sdAys, sAyg);
-        } else {
-          vs = (j == 0) ? vy : fma(cjh, kvy, vy);
-          kpy = sd * vs;
-          kvy = sd * (fma(tj, dAy, AyL) - g);
-        }
-        apy = fma(wj, kpy, apy);
-        avy = fma(wj, kvy, avy);
-        if constexpr (cross) {
-          // ground term h(-phi); lambda^c's state part v_x - omega (R rho)_y
-          const double ry = fma(sn, crx, cs * cry);
-          Yom = fma(h * wj, huber_value(-(pys + ry)), Yom);
-          const double vxs = (j == 0) ? vx : fma(cjh, kvx, vx);
-          kvx = fma(tj, sdAxs, sAxL);
-          avx = fma(wj, kvx, avx);
-          Il = fma(h * wj, fma(-wst, ry, vxs), Il);
-          vxP[j] = F32 ? ((j == 0) ? vxA : vxA + cjhP[j] * kvxA) : TP(vxs);
-          const InputCross<TP>& icj = (j == 0) ? ic0 : (j == 3 ? ic1 : icm);
-          dl0[j] = icj.d0; dl1[j] = icj.d1; dl2[j] = icj.d2;
-          cq0[j] = icj.q0; cq2[j] = icj.q2; cr0[j] = icj.r0; cr1[j] = icj.r1;
-        } else {
-          // ground term h(-phi), phi = p_y + (R rho)_y at the stage
-          Yom = fma(h * wj, huber_value(-fma(sn, crx, fma(cs, cry, pys))), Yom);
-          const InputPenalty<TP>& ipj = (j == 0) ? ip0 : (j == 3 ? ip1 : ipm);
-          dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
-        }
+        ipM = input_penalty<TP, false>(0.0, TP(sf[1].tau), sd, sdP, mu, muP, cL, cD, cLP, cDP);
+        ipB = input_penalty<TP, false>(0.0, TP(sf[3].tau), sd, sdP, mu, muP, cL, cD, cLP, cDP);
       }
-      // stage data for the tangent recursion
-      const TP cjhT = cjhP[j];
-      TP csP, snP, PP, QP, TT, wsP, pysP = TP(0), vsP = TP(0);
-      if constexpr (F32) {
-        const TP tP = (j == 0) ? tiP : (j == 3 ? teP : tmP);
-        const TP thsP = (j == 0) ? thA : thA + cjhT * kthA;
-        wsP = (j == 0) ? omA : omA + cjhT * komA;
-        sincosf(thsP, &snP, &csP);
-        PP = PLP + tP * dPP; QP = QLP + tP * dQP; TT = TLP + tP * dTP;
-        tau[j] = tP;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const TP tP = sf[j].tau, csP = sf[j].cs, snP = sf[j].sn;
+        const TP PP = PLP + tP * dPP, QP = QLP + tP * dQP, TT = TLP + tP * dTP;
+        st.cw[j] = csP;
+        st.sw[j] = snP;
+        st.sath[j] = -sdP * (snP * PP + csP * QP);  // s * d(omega')/d(theta)
+        st.oms[j] = sf[j].ws;
+        st.wdt[j] = csP * PP - snP * QP + TT;
+        st.tau[j] = tP;
         if (foot) {
-          pysP = (j == 0) ? pyA : pyA + cjhT * kpyA;
-          vsP = (j == 0) ? vyA : vyA + cjhT * kvyA;
+          const TP rxP = csP * crxP - snP * cryP, ryP = snP * crxP + csP * cryP;
+          const TP D4 = huber_slope(-(TP(sf[j].pys) + ryP));
+          st.gp[j] = -sdP * D4;        // s dOmega/dp_y
+          st.gr[j] = -sdP * D4 * rxP;  // s dOmega/dtheta
+          st.vys[j] = sf[j].vys;
+          st.ays[j] = AyLP + tP * dAyP - gP;
+          const InputPenalty<TP>& ipj = (j == 0) ? ipA : (j == 3 ? ipB : ipM);
+          st.dl0[j] = ipj.d0; st.dl1[j] = ipj.d1; st.dl2[j] = ipj.d2;
         }
-      } else {
-        csP = cs; snP = sn; PP = P; QP = Q; TT = T; wsP = ws; pysP = pys; vsP = vs;
-        tau[j] = tj;
       }
-      const TP wdP = csP * PP - snP * QP + TT;
-      cw[j] = csP;
-      sw[j] = snP;
-      sath[j] = -sdP * (snP * PP + csP * QP);  // s * d(omega')/d(theta)
-      oms[j] = wsP;
-      wdt[j] = wdP;
-      if constexpr (F32) { kthA = sdP * wsP; komA = sdP * wdP; }
+      tangent_substep<TP, FOOT, false>(tg, st, sdP, hP, cjhP);
+      if (foot) ipA = ipB;
+    }
+    df_state_finish<FOOT>(C, S);
+    th = S.th;
+    om = S.om;
+    Yom = S.Y;
+  } else {
+    for (int i = 0; i < nsub; ++i) {
+      if constexpr (CK && !F32) {
+        ck->th[i] = th; ck->om[i] = om; ck->s[i] = sth; ck->c[i] = cth;
+        if (foot) { ck->py[i] = py; ck->vy[i] = vy; }
+      }
+      // ---- state stages (FP64) ----
+      StageT<TP> st;
+      TP (&cw)[4] = st.cw, (&sw)[4] = st.sw, (&sath)[4] = st.sath, (&oms)[4] = st.oms;
+      TP (&wdt)[4] = st.wdt, (&tau)[4] = st.tau, (&gr)[4] = st.gr, (&gp)[4] = st.gp;
+      TP (&vys)[4] = st.vys, (&ays)[4] = st.ays, (&dl0)[4] = st.dl0, (&dl1)[4] = st.dl1, (&dl2)[4] = st.dl2;
+      TP (&lry)[4] = st.lry, (&lrx)[4] = st.lrx, (&axs)[4] = st.axs, (&cq0)[4] = st.cq0;
+      TP (&cq2)[4] = st.cq2, (&cr0)[4] = st.cr0, (&cr1)[4] = st.cr1;
+      TP vxP[4];  // Eq. (12) model
+      const double tm = ti + h2, te = ti + h;
+      const TP tmP = tiP + h2P, teP = tiP + hP;
+      InputPenalty<TP> ipm, ip1;
+      InputCross<TP> icm, ic1;
+      if constexpr (cross) {
+        icm = input_cross<TP>(tm, tmP, sdP, mu, muP, cL, cD, cLP, cDP);
+        ic1 = input_cross<TP>(te, teP, sdP, mu, muP, cL, cD, cLP, cDP);
+      } else if (foot) {
+        ipm = input_penalty<TP>(tm, tmP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
+        ip1 = input_penalty<TP>(te, teP, sd, sdP, mu, muP, cL, cD, cLP, cDP);
+      }
+      // FP32 copy of the stage recursion, anchored on the FP64 state (FP32-Phi
+      // mode; the anchors are narrowed on the integer pipe).  With CK the
+      // anchors are the checkpoints: the FP32 backward sweep starts from them.
+      const TP thA = anchor<TP>(th), omA = anchor<TP>(om), pyA = anchor<TP>(py), vyA = anchor<TP>(vy);
+      const TP vxA = cross ? anchor<TP>(vx) : TP(0);
+      if constexpr (CK && F32) {
+        ck->thf[i] = thA; ck->omf[i] = omA;
+        if (foot) { ck->pyf[i] = pyA; ck->vyf[i] = vyA; }
+      }
+      TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0), kvxA = TP(0);
+      double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
+      double kvx = 0, avx = 0;  // Eq. (12) model: s a_x at the stage, its RK4 sum
+      const double som = sd * om, svy = foot ? sd * vy : 0.0;
+      double sPm = 0, sQm = 0, sTm = 0;
+      double ws = 0, P = 0, Q = 0, T = 0;  // FP64 stage data (FP64 mode only)
+  #pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double wj = rk_w(j);
+        const double cjh = (j == 0) ? 0.0 : (j == 3 ? h : h2);
+        const double tj = (j == 0) ? ti : (j == 3 ? te : tm);
+        const double dth = cjh * kth;
+        double sn, cs;
+        if (j == 0) { sn = sth; cs = cth; }
+        else sincos_step(th, sth, cth, dth, amask, sn, cs);
+        // Eq. (12) model: omega at the stage (kom is still the previous stage's slope)
+        const double wst = cross ? ((j == 0) ? om : fma(cjh, kom, om)) : 0.0;
+        if constexpr (F32) {
+          double sP, sQ, sT;
+          if (j == 0) { sP = sPi; sQ = sQi; sT = sTi; }
+          else if (j == 3) {
+            sPi = fma(te, sdPs, sPL); sQi = fma(te, sdQs, sQL); sTi = fma(te, sdTs, sTL);
+            sP = sPi; sQ = sQi; sT = sTi;
+          } else {
+            if (j == 1) { sPm = fma(tm, sdPs, sPL); sQm = fma(tm, sdQs, sQL); sTm = fma(tm, sdTs, sTL); }
+            sP = sPm; sQ = sQm; sT = sTm;
+          }
+          kth = (j == 0) ? som : fma(j == 3 ? sc3 : sc2, kom, som);
+          kom = fma(cs, sP, fma(-sn, sQ, sT));
+        } else {
+          ws = (j == 0) ? om : fma(cjh, kom, om);
+          P = fma(tj, dP, PL); Q = fma(tj, dQ, QL); T = fma(tj, dT, TL);
+          kth = sd * ws;
+          kom = sd * fma(cs, P, fma(-sn, Q, T));
+        }
+        ath_ = fma(wj, kth, ath_);
+        aom_ = fma(wj, kom, aom_);
+        double pys = 0.0, vs = 0.0;
+        if (foot) {
+          pys = (j == 0) ? py : fma(cjh, kpy, py);
+          if constexpr (F32) {
+            kpy = (j == 0) ? svy : fma(j == 3 ? sc3 : sc2, kvy, svy);
+            kvy = fma(tj, sdAys, sAyg);
+          } else {
+            vs = (j == 0) ? vy : fma(cjh, kvy, vy);
+            kpy = sd * vs;
+            kvy = sd * (fma(tj, dAy, AyL) - g);
+          }
+          apy = fma(wj, kpy, apy);
+          avy = fma(wj, kvy, avy);
+          if constexpr (cross) {
+            // ground term h(-phi); lambda^c's state part v_x - omega (R rho)_y
+            const double ry = fma(sn, crx, cs * cry);
+            Yom = fma(h * wj, huber_value(-(pys + ry)), Yom);
+            const double vxs = (j == 0) ? vx : fma(cjh, kvx, vx);
+            kvx = fma(tj, sdAxs, sAxL);
+            avx = fma(wj, kvx, avx);
+            Il = fma(h * wj, fma(-wst, ry, vxs), Il);
+            vxP[j] = F32 ? ((j == 0) ? vxA : vxA + cjhP[j] * kvxA) : TP(vxs);
+            const InputCross<TP>& icj = (j == 0) ? ic0 : (j == 3 ? ic1 : icm);
+            dl0[j] = icj.d0; dl1[j] = icj.d1; dl2[j] = icj.d2;
+            cq0[j] = icj.q0; cq2[j] = icj.q2; cr0[j] = icj.r0; cr1[j] = icj.r1;
+          } else {
+            // ground term h(-phi), phi = p_y + (R rho)_y at the stage
+            Yom = fma(h * wj, huber_value(-fma(sn, crx, fma(cs, cry, pys))), Yom);
+            const InputPenalty<TP>& ipj = (j == 0) ? ip0 : (j == 3 ? ip1 : ipm);
+            dl0[j] = ipj.d0; dl1[j] = ipj.d1; dl2[j] = ipj.d2;
+          }
+        }
+        // stage data for the tangent recursion
+        const TP cjhT = cjhP[j];
+        TP csP, snP, PP, QP, TT, wsP, pysP = TP(0), vsP = TP(0);
+        if constexpr (F32) {
+          const TP tP = (j == 0) ? tiP : (j == 3 ? teP : tmP);
+          const TP thsP = (j == 0) ? thA : thA + cjhT * kthA;
+          wsP = (j == 0) ? omA : omA + cjhT * komA;
+          sincosf(thsP, &snP, &csP);
+          PP = PLP + tP * dPP; QP = QLP + tP * dQP; TT = TLP + tP * dTP;
+          tau[j] = tP;
+          if (foot) {
+            pysP = (j == 0) ? pyA : pyA + cjhT * kpyA;
+            vsP = (j == 0) ? vyA : vyA + cjhT * kvyA;
+          }
+        } else {
+          csP = cs; snP = sn; PP = P; QP = Q; TT = T; wsP = ws; pysP = pys; vsP = vs;
+          tau[j] = tj;
+        }
+        const TP wdP = csP * PP - snP * QP + TT;
+        cw[j] = csP;
+        sw[j] = snP;
+        sath[j] = -sdP * (snP * PP + csP * QP);  // s * d(omega')/d(theta)
+        oms[j] = wsP;
+        wdt[j] = wdP;
+        if constexpr (F32) { kthA = sdP * wsP; komA = sdP * wdP; }
+        if (foot) {
+          const TP ayP = AyLP + tau[j] * dAyP - gP;
+          if constexpr (F32) { kpyA = sdP * vsP; kvyA = sdP * ayP; }
+          const TP rxP = csP * crxP - snP * cryP;
+          const TP ryP = snP * crxP + csP * cryP;
+          const TP D4 = huber_slope(-(pysP + ryP));
+          gp[j] = -sdP * D4;        // s dOmega/dp_y
+          gr[j] = -sdP * D4 * rxP;  // s dOmega/dtheta
+          vys[j] = vsP;
+          ays[j] = ayP;
+          if constexpr (cross) {
+            lry[j] = -sdP * ryP;        // s d(lambda^c)/d omega
+            lrx[j] = -sdP * wsP * rxP;  // s d(lambda^c)/d theta
+            axs[j] = AxLP + tau[j] * dAxP;
+            if constexpr (F32) kvxA = sdP * axs[j];
+          }
+        }
+      }
+      const double Dth = h * ath_;
+      {
+        double s1, c1;
+        sincos_step(th, sth, cth, Dth, amask, s1, c1);
+        sth = s1;
+        cth = c1;
+      }
+      th += Dth;
+      om = fma(h, aom_, om);
       if (foot) {
-        const TP ayP = AyLP + tau[j] * dAyP - gP;
-        if constexpr (F32) { kpyA = sdP * vsP; kvyA = sdP * ayP; }
-        const TP rxP = csP * crxP - snP * cryP;
-        const TP ryP = snP * crxP + csP * cryP;
-        const TP D4 = huber_slope(-(pysP + ryP));
-        gp[j] = -sdP * D4;        // s dOmega/dp_y
-        gr[j] = -sdP * D4 * rxP;  // s dOmega/dtheta
-        vys[j] = vsP;
-        ays[j] = ayP;
+        py = fma(h, apy, py);
+        vy = fma(h, avy, vy);
         if constexpr (cross) {
-          lry[j] = -sdP * ryP;        // s d(lambda^c)/d omega
-          lrx[j] = -sdP * wsP * rxP;  // s d(lambda^c)/d theta
-          axs[j] = AxLP + tau[j] * dAxP;
-          if constexpr (F32) kvxA = sdP * axs[j];
+          vx = fma(h, avx, vx);
+          Yom = fma(h3, ic1.H, fma(h23, icm.H, Yom));
+          Ir = fma(h3, ic1.R, fma(h23, icm.R, Ir));
+          Ig = fma(h3, ic1.G, fma(h23, icm.G, Ig));
+          ic0 = ic1;
+        } else {
+          Yom = fma(h3, ip1.H, fma(h23, ipm.H, Yom));
+          ip0 = ip1;
         }
       }
-    }
-    const double Dth = h * ath_;
-    {
-      double s1, c1;
-      sincos_step(th, sth, cth, Dth, amask, s1, c1);
-      sth = s1;
-      cth = c1;
-    }
-    th += Dth;
-    om = fma(h, aom_, om);
-    if (foot) {
-      py = fma(h, apy, py);
-      vy = fma(h, avy, vy);
-      if constexpr (cross) {
-        vx = fma(h, avx, vx);
-        Yom = fma(h3, ic1.H, fma(h23, icm.H, Yom));
-        Ir = fma(h3, ic1.R, fma(h23, icm.R, Ir));
-        Ig = fma(h3, ic1.G, fma(h23, icm.G, Ig));
-        ic0 = ic1;
-      } else {
-        Yom = fma(h3, ip1.H, fma(h23, ipm.H, Yom));
-        ip0 = ip1;
-      }
-    }
-    ti = te;
-    tiP = teP;
+      ti = te;
+      tiP = teP;
 
-    // ---- rotation tangents: 9 columns, 4 stages each ----
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const TP T0 = tg.Pt[c], W0 = tg.Pw[c];
-      TP kT = TP(0), kW = TP(0), aT = TP(0), aW = TP(0), ya = TP(0), yl = TP(0);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const TP cjh = cjhP[j], wj = TP(rk_w(j));
-        const TP Ts = (j == 0) ? T0 : T0 + cjh * kT;
-        const TP Ws = (j == 0) ? W0 : W0 + cjh * kW;
-        const TP wl = TP(1) - tau[j], wr = tau[j];
-        TP fT = TP(0), fW = TP(0);
-        if (c == 2) { fT = oms[j]; fW = wdt[j]; }
-        else if (c == 3) fW = sdP * cw[j] * wl;
-        else if (c == 4) fW = -sdP * sw[j] * wl;
-        else if (c == 5) fW = sdP * wl;
-        else if (c == 6) fW = sdP * cw[j] * wr;
-        else if (c == 7) fW = -sdP * sw[j] * wr;
-        else if (c == 8) fW = sdP * wr;
-        kT = sdP * Ws + fT;
-        kW = sath[j] * Ts + fW;
-        aT += wj * kT;
-        aW += wj * kW;
-        if (foot) ya += wj * gr[j] * Ts;
-        if constexpr (cross) yl += wj * (lry[j] * Ws + lrx[j] * Ts);
-      }
-      tg.Pt[c] = T0 + hP * aT;
-      tg.Pw[c] = W0 + hP * aW;
-      if (foot) tg.Yr[c] += hP * ya;
-      if constexpr (cross) tg.Yl[c] += hP * yl;
+      tangent_substep<TP, FOOT, CROSS>(tg, st, sdP, hP, cjhP);
     }
 
-    // ---- foot: p_y channel tangents and the penalty row ----
-    if (foot) {
-      TP y0 = TP(0);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) y0 += TP(rk_w(j)) * gp[j];
-      tg.Yp[0] += hP * y0;  // p_y0 column: stage tangent of p_y is 1
-#pragma unroll
-      for (int c = 1; c < 5; ++c) {
-        const TP P0 = tg.Qp[c], V0 = tg.Qv[c];
-        TP kP = TP(0), kV = TP(0), aP = TP(0), aV = TP(0), ya = TP(0), yv = TP(0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const TP cjh = cjhP[j], wj = TP(rk_w(j));
-          const TP Ps = (j == 0) ? P0 : P0 + cjh * kP;
-          const TP Vs = (j == 0) ? V0 : V0 + cjh * kV;
-          TP fP = TP(0), fV = TP(0);
-          if (c == 2) { fP = vys[j]; fV = ays[j]; }
-          else if (c == 3) fV = sdP * (TP(1) - tau[j]);
-          else if (c == 4) fV = sdP * tau[j];
-          kP = sdP * Vs + fP;
-          kV = fV;
-          aP += wj * kP;
-          aV += wj * kV;
-          ya += wj * gp[j] * Ps;
-          // unit-forcing tangents of v_y equal those of v_x (same equation v' = s a)
-          if constexpr (cross) yv += wj * sdP * Vs;
-        }
-        tg.Qp[c] = P0 + hP * aP;
-        tg.Qv[c] = V0 + hP * aV;
-        tg.Yp[c] += hP * ya;
-        if constexpr (cross) {
-          if (c >= 3) tg.Ylv[c - 3] += hP * yv;
-        }
-      }
-      if constexpr (cross) {
-        // v_x tangent with respect to s (forcing a_x(tau)); lambda^c's s column
-        const TP V0 = tg.Vxs;
-        TP kV = TP(0), aV = TP(0), yv = TP(0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const TP wj = TP(rk_w(j));
-          const TP Vs = (j == 0) ? V0 : V0 + cjhP[j] * kV;
-          kV = axs[j];
-          aV += wj * kV;
-          yv += wj * sdP * Vs;
-        }
-        tg.Vxs = V0 + hP * aV;
-        tg.Ylv[2] += hP * yv;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const TP hw = hP * TP(rk_w(j));
-        const TP wl = TP(1) - tau[j], wr = tau[j];
-        tg.Yd[0] += hw * dl0[j] * wl; tg.Yd[3] += hw * dl0[j] * wr;
-        tg.Yd[1] += hw * dl1[j] * wl; tg.Yd[4] += hw * dl1[j] * wr;
-        tg.Yd[2] += hw * dl2[j] * wl; tg.Yd[5] += hw * dl2[j] * wr;
-        if constexpr (cross) {
-          tg.Yld[0] += hw * cq0[j] * wl; tg.Yld[1] += hw * cq0[j] * wr;
-          tg.Yld[2] += hw * cq2[j] * wl; tg.Yld[3] += hw * cq2[j] * wr;
-          tg.Yrd[0] += hw * cr0[j] * wl; tg.Yrd[1] += hw * cr0[j] * wr;
-          tg.Yrd[2] += hw * cr1[j] * wl; tg.Yrd[3] += hw * cr1[j] * wr;
-        }
-      }
+    // the end point was counted with h/3
+    if constexpr (cross) {
+      Yom = fma(-h6, ic0.H, Yom);
+      Ir = fma(-h6, ic0.R, Ir);
+      Ig = fma(-h6, ic0.G, Ig);
+    } else if (foot) {
+      Yom = fma(-h6, ip0.H, Yom);
     }
-  }
-
-  // the end point was counted with h/3
-  if constexpr (cross) {
-    Yom = fma(-h6, ic0.H, Yom);
-    Ir = fma(-h6, ic0.R, Ir);
-    Ig = fma(-h6, ic0.G, Ig);
-  } else if (foot) {
-    Yom = fma(-h6, ip0.H, Yom);
   }
   if constexpr (CK) { ck->th_end = th; ck->om_end = om; ck->Yom = Yom; }
 

@@ -102,6 +102,21 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
     th = ck.th_end;
     om = ck.om_end;
     Yom = ck.Yom;
+  } else if constexpr (F32) {
+    // FP32 adjoint: stage values in float-float, the state accumulated in FP64
+    // (state_df.cuh); the anchors at every substep start are the checkpoints,
+    // and the penalty quadrature is taken here.
+    const DfLink C = df_link(sd, nsub, PL, dP, QL, dQ, TL, dT, AyL, dAy, g, FOOT, crx, cry, mu, cL, cD);
+    DfState S = df_state_init<FOOT>(C, th0, om0, py0, vy0);
+    for (int i = 0; i < nsub; ++i) {
+      ckl.thf[i] = anchor<TP>(S.th); ckl.omf[i] = anchor<TP>(S.om);
+      if (FOOT) { ckl.pyf[i] = anchor<TP>(S.py); ckl.vyf[i] = anchor<TP>(S.vy); }
+      df_substep<FOOT, false>(C, i, amask, S, nullptr);
+    }
+    df_state_finish<FOOT>(C, S);
+    th = S.th;
+    om = S.om;
+    Yom = S.Y;
   } else {
   double sth, cth;
   sincos(th, &sth, &cth);
