@@ -28,10 +28,31 @@ __device__ __forceinline__ double huber_value(double z) {
   return H;
 }
 
-// Value in FP32 (adjoint weights only; the penalty state itself uses the FP64 value).
+// Value in FP32 (adjoint weights only; the penalty state itself uses the FP64
+// value): p^2 / (1 + sqrt(1 + p^2)) with the square root as a rsqrt(a) and
+// the fast division, a few ulp.
 __device__ __forceinline__ float huber_value(float z) {
   const float p = fmaxf(z, 0.0f);
-  return (p * p) / (1.0f + sqrtf(fmaf(p, p, 1.0f)));
+  const float a = fmaf(p, p, 1.0f);
+  return __fdividef(p * p, fmaf(a, rsqrtf(a), 1.0f));
+}
+
+// (sin, cos) of theta0 + d in FP32 from (s0, c0) = (sin, cos)(theta0):
+// Taylor series of sin d through d^7 and of cos d through d^8 (truncation
+// below 6e-9 for |d| <= 0.5, under FP32 rounding), then angle addition; for
+// |d| > 0.5 (or NaN) sincosf of theta0 + d, out of line.
+static __device__ __noinline__ void sincos_f32_far(float th, float* s, float* c) { sincosf(th, s, c); }
+
+__device__ __forceinline__ void sincos_f32_step(float th0, float s0, float c0, float d, float& s, float& c) {
+  if (fabsf(d) <= 0.5f) {
+    const float x = d * d;
+    const float sd = d * fmaf(x, fmaf(x, fmaf(x, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+    const float cm = x * fmaf(x, fmaf(x, fmaf(x, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f);
+    s = fmaf(s0, cm, fmaf(c0, sd, s0));  // s0 cos d + c0 sin d
+    c = fmaf(c0, cm, fmaf(-s0, sd, c0));  // c0 cos d - s0 sin d
+  } else {
+    sincos_f32_far(th0 + d, &s, &c);
+  }
 }
 
 // Derivative only, in the tangent precision: h'(z) = p / sqrt(1 + p^2).

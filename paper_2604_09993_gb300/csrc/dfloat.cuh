@@ -1,7 +1,7 @@
 // dfloat.cuh — float-float ("double-single") arithmetic on the FP32 pipe.
 //
-// A value is the unevaluated sum h + l of two floats with |l| <= ulp(h) / 2
-// after normalization, about 48 significand bits.  On this GPU one FP64-pipe
+// A value is the unevaluated sum h + l of two floats with |l| a few ulp(h)
+// at most, about 47 significand bits.  On this GPU one FP64-pipe
 // instruction takes the issue time of ~64 FP32 instructions, so the
 // kernels evaluate the right-hand side of their RK stages (angle chain,
 // slopes, penalty integrands) in this arithmetic and keep FP64 only for the
@@ -11,10 +11,16 @@
 //  * TwoSum (Knuth, TAOCP vol. 2, 4.2.2): s + e = a + b exactly, any order;
 //  * Fast2Sum (Dekker 1971): the same for |a| >= |b|;
 //  * TwoProd with an FMA: p + e = a b exactly (e = fma(a, b, -p));
-//  * sum and product of two float-float numbers in the accurate forms
-//    analysed by Joldes, Muller and Popescu (ACM TOMS 44(2), 2017):
-//    relative error <= 3u^2 + 13u^3 for the sum (two TwoSums, two
-//    renormalizations) and <= 4u^2 for the FMA-based product, u = 2^-24.
+//  * the sum of two float-float numbers in the "sloppy" form (TwoSum of
+//    the high parts, the low parts added in FP32, one Fast2Sum): its
+//    absolute error is <= 4u^2 (|x| + |y|), u = 2^-24, which is what these
+//    kernels need (errors on the scale of the operands), though under
+//    cancellation it has no relative bound;
+//  * the product with an FMA (TwoProd of the high parts plus the two cross
+//    terms), left unnormalized: relative error <= 12u^2 for operands whose
+//    low part is below one ulp of the high part, the result's low part a few
+//    ulp of its high part at most; every sum renormalizes.
+// (Joldes, Muller and Popescu, ACM TOMS 44(2), 2017, analyse these forms.)
 // The device versions use the _rn intrinsics so that the compiler never
 // contracts a product and a sum into one FMA, which would break the exact
 // error terms; the host versions (tests) are compiled without contraction.
@@ -88,12 +94,10 @@ DF_HD dflt df_neg(dflt x) { return dflt{-x.h, -x.l}; }
 // Exact scaling by a power of two (no overflow or underflow in this use).
 DF_HD dflt df_scale(dflt x, float p2) { return dflt{f_mul(x.h, p2), f_mul(x.l, p2)}; }
 
-// x + y (accurate form: TwoSum of the high parts and of the low parts).
+// x + y (sloppy form, renormalized).
 DF_HD dflt df_add(dflt x, dflt y) {
-  dflt s = two_sum(x.h, y.h);
-  const dflt t = two_sum(x.l, y.l);
-  s = fast_two_sum(s.h, f_add(s.l, t.h));
-  return fast_two_sum(s.h, f_add(s.l, t.l));
+  const dflt s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, f_add(s.l, f_add(x.l, y.l)));
 }
 DF_HD dflt df_sub(dflt x, dflt y) { return df_add(x, df_neg(y)); }
 // x + f, f a float.
@@ -101,24 +105,24 @@ DF_HD dflt df_add_f(dflt x, float f) {
   const dflt s = two_sum(x.h, f);
   return fast_two_sum(s.h, f_add(s.l, x.l));
 }
-// x y.
+// x y (unnormalized).
 DF_HD dflt df_mul(dflt x, dflt y) {
   dflt p = two_prod(x.h, y.h);
   p.l = f_fma(x.h, y.l, p.l);
   p.l = f_fma(x.l, y.h, p.l);
-  return fast_two_sum(p.h, p.l);
+  return p;
 }
-// x f, f a float.
+// x f, f a float (unnormalized).
 DF_HD dflt df_mul_f(dflt x, float f) {
   dflt p = two_prod(x.h, f);
   p.l = f_fma(x.l, f, p.l);
-  return fast_two_sum(p.h, p.l);
+  return p;
 }
-// x^2
+// x^2 (unnormalized)
 DF_HD dflt df_sqr(dflt x) {
   dflt p = two_prod(x.h, x.h);
   p.l = f_fma(f_add(x.h, x.h), x.l, p.l);
-  return fast_two_sum(p.h, p.l);
+  return p;
 }
 
 // Constants 1/n as float-float, formed at compile time from the double value.
@@ -130,8 +134,8 @@ DF_HD dflt df_sqr(dflt x) {
 // patterns (integer pipe): the high part keeps the sign, the rebiased
 // exponent and the top 23 fraction bits (round toward zero); the low part is
 // the remaining 29 fraction bits, normalized into a float (its last 5 bits
-// truncated), then the pair is renormalized with Fast2Sum.
-// |x - (h + l)| <= 2^-47 |x| for normal x with |x| in
+// truncated), so |l| < ulp(h).  |x - (h + l)| <= 2^-47 |x| for normal x
+// with |x| in
 // [2^-90, 2^127]; outside that range the low part is flushed to zero and the
 // high part is the FP32 value toward zero (0 below 2^-126).
 // ---------------------------------------------------------------------------
@@ -166,7 +170,7 @@ DF_DEV dflt df_split(double x) {
     const unsigned m = (p >= 23) ? (r >> (p - 23)) : (r << (23 - p));
     if (el > 0) lb = sign | ((unsigned)el << 23) | (m & 0x7fffffu);
   }
-  return fast_two_sum(bits_f(hb), bits_f(lb));  // normalized: |l| <= ulp(h) / 2
+  return dflt{bits_f(hb), bits_f(lb)};
 }
 
 // ---------------------------------------------------------------------------
@@ -176,8 +180,8 @@ DF_DEV dflt df_split(double x) {
 //    1 - cos d = x/2 - x^2/24 + x^3/720, x = d^2 (truncation <= 3e-16);
 //  * long tier, |d| <= 0.2: q through x^5 and 1 - cos d through x^5, with
 //    x/6, x^2/120, x^2/24 and x^3/720 in float-float (truncation <= 2e-16).
-// Absolute error of either result <= 2e-15 (short) / 3e-15 (long) for d
-// exact in float-float (the FP32 tail terms dominate).
+// Absolute error of either result <= 5e-15 for d exact in float-float (the
+// FP32 tail terms dominate).
 // ---------------------------------------------------------------------------
 DF_HD void sin_vers_short(dflt d, dflt& sn, dflt& vc) {
   const dflt x = df_sqr(d);
@@ -210,7 +214,7 @@ DF_HD void sin_vers_long(dflt d, dflt& sn, dflt& vc) {
 // Pseudo-Huber ramp h(z) = sqrt(1 + p^2) - 1, p = max(z, 0), in float-float:
 // a = 1 + p^2, y0 = sqrt(a_h) (FP32, correctly rounded), and one correction
 // (a - y0^2) / (2 y0) with the residual formed exactly by TwoProd; the
-// result's error is <= 2e-14 max(1, h) for |z| <= 10 (the cancellation in
+// result's error is <= 3e-14 max(1, h) for |z| <= 10 (the cancellation in
 // sqrt(a) - 1 for small p only affects values far below that bound).
 DF_HD dflt huber_df(dflt z) {
   if (!(z.h > 0.0f)) return dflt{0.0f, 0.0f};

@@ -726,8 +726,9 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   defect[rpx] = px1 - xk1[rpx]; defect[rpy] = py1 - xk1[rpy]; defect[rth] = th - xk1[rth];
   defect[rvx] = vx1 - xk1[rvx]; defect[rvy] = vy1 - xk1[rvy]; defect[rom] = om - xk1[rom];
   double chk = px1 + py1 + th + vx1 + vy1 + om + Spx + Spy;
+  TP chkP = TP(0);  // the tangent values, summed in their own precision (finite check only)
 #pragma unroll
-  for (int c = 0; c < 9; ++c) chk += double(tg.Pt[c]) + double(tg.Pw[c]);
+  for (int c = 0; c < 9; ++c) chkP += tg.Pt[c] + tg.Pw[c];
 
   double y1 = 0.0;
   if (foot) {
@@ -766,7 +767,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
         if (wz) zr[6] -= double(vm) * uL[q] + double(vp) * uR[q];
       }
     }
-    chk += y1 + double(Sy);
+    chk += y1;
+    chkP += Sy;
   }
   if constexpr (cross) {
     // Eq. (12) cross-complementarity rows of the contact: phi_n, lambda^c, gamma, rho^c
@@ -789,7 +791,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     a_put(yb + 1, rom, JA + 6, tg.Yl[1]);
     const TP Sl = TP(Ilg) + tg.Yl[2] + tg.Ylv[2];
     S[yb] = TP(fn_m); S[yb + 1] = Sl; S[yb + 2] = TP(ga_m); S[yb + 3] = TP(Ir);
-    chk += double(Sl);
+    chkP += Sl;
     if (nu > 0) {
       // compact: after the link's input groups, (c1,q) for the inputs that
       // enter lambda^c, then (c0,phi_n) (c2,gamma) (c3,phi_t) (c3,phi_n)
@@ -824,7 +826,7 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       b_put(yb + 3, cin + 1, tg.Yrd[2], tg.Yrd[3]);
     }
   }
-  if (!finite_d(chk)) atomicOr(status, ST_NONFINITE);
+  if (!finite_d(chk) || !isfinite(chkP)) atomicOr(status, ST_NONFINITE);
 
   if (wz) {
     z[rpx] = zr[0]; z[rpy] = zr[1]; z[rth] = zr[2];

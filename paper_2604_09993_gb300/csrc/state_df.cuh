@@ -37,12 +37,11 @@ namespace ciscvx {
 __device__ __forceinline__ void add_df(double& x, dflt d) { x = (x + widen(d.h)) + widen(d.l); }
 
 // sin(d) and 1 - cos(d) of a stage's angle increment: the short Taylor tier
-// when every lane of the warp has |d| <= 0.02, else the long tier per lane
-// (|d| <= 0.2), else FP64 sincos of d (rare; also taken by NaN).
-__device__ __forceinline__ void rot_inc(dflt d, unsigned amask, dflt& sn, dflt& vc) {
-  if (__all_sync(amask, fabsf(d.h) <= 0.02f)) {
-    sin_vers_short(d, sn, vc);
-  } else if (fabsf(d.h) <= 0.2f) {
+// when every lane of the warp has |d| <= 0.02, else (out of line, so that
+// the rare paths do not crowd the instruction cache) the long tier per lane
+// (|d| <= 0.2), else FP64 sincos of d (also taken by NaN).
+static __device__ __noinline__ void rot_inc_slow(dflt d, dflt& sn, dflt& vc) {
+  if (fabsf(d.h) <= 0.2f) {
     sin_vers_long(d, sn, vc);
   } else {
     double s, c;
@@ -50,6 +49,11 @@ __device__ __forceinline__ void rot_inc(dflt d, unsigned amask, dflt& sn, dflt& 
     sn = df_split(s);
     vc = df_split(1.0 - c);
   }
+}
+
+__device__ __forceinline__ void rot_inc(dflt d, unsigned amask, dflt& sn, dflt& vc) {
+  if (__all_sync(amask, fabsf(d.h) <= 0.02f)) sin_vers_short(d, sn, vc);
+  else rot_inc_slow(d, sn, vc);
 }
 
 // Per-interval constants of one link (float-float).

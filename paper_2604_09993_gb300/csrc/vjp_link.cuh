@@ -243,6 +243,9 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
       }
       TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0);
       double kth = 0, kom = 0, kpy = 0, kvy = 0;
+      // FP32 adjoint: sin/cos of the anchor once per substep, the stages by angle addition
+      float sA = 0.0f, cA = 1.0f;
+      if constexpr (F32) sincos_f32_far(thA, &sA, &cA);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const double wj = rk_w(j);
@@ -273,9 +276,9 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
         TP csP, snP, PP, QP, TT, wsP, pysP = TP(0), vsP = TP(0);
         if constexpr (F32) {
           const TP tP = (j == 0) ? tsP : (j == 3 ? teP : tmP);
-          const TP thsP = (j == 0) ? thA : thA + cjh * kthA;
           wsP = (j == 0) ? omA : omA + cjh * komA;
-          sincosf(thsP, &snP, &csP);
+          if (j == 0) { snP = sA; csP = cA; }
+          else sincos_f32_step(thA, sA, cA, cjh * kthA, snP, csP);
           PP = PLP + tP * dPP; QP = QLP + tP * dQP; TT = TLP + tP * dTP;
           tau[j] = tP;
           if (FOOT) {
@@ -356,13 +359,13 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   // ---- translation: transposed closed forms ----
   const double s2_3 = sd * sd * (1.0 / 3.0), s2_6 = sd * sd * (1.0 / 6.0), s_2 = 0.5 * sd;
   const double gAxL = wpx * s2_3 + wvx * s_2, gAxR = wpx * s2_6 + wvx * s_2;
-  const double gAyLt = wpy * s2_3 + wvy * s_2 + double(gAyL), gAyRt = wpy * s2_6 + wvy * s_2 + double(gAyR);
+  const double gAyLt = wpy * s2_3 + wvy * s_2 + widen(gAyL), gAyRt = wpy * s2_6 + wvy * s_2 + widen(gAyR);
   const double gsd_t = wpx * (vx0 + 2.0 * sd * ax3) + wvx * axm + wpy * (vy0 + 2.0 * sd * ay3) +
-                       wvy * aym + double(gsd);
+                       wvy * aym + widen(gsd);
 
   // node-state gradient of this link's rows: own part minus w_{k-1} (defect_{k-1} subtracts x~_k)
-  const double own[6] = {wpx, wpy + double(lpy), double(lth), wpx * sd + wvx,
-                         wpy * sd + wvy + double(lvy), double(lom)};
+  const double own[6] = {wpx, wpy + widen(lpy), widen(lth), wpx * sd + wvx,
+                         wpy * sd + wvy + widen(lvy), widen(lom)};
   const int rows[6] = {rpx, rpy, rth, rvx, rvy, rom};
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
@@ -377,20 +380,20 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
   // per-input partials of this link
   double* pp = part + 2 * B.slot0;
   for (int i = 0; i < nin; ++i) {
-    double gl = B.ax[i] * gAxL + B.ay[i] * gAyLt + B.p[i] * double(gPL) + B.q[i] * double(gQL) +
-                B.t[i] * double(gTL);
-    double gr_ = B.ax[i] * gAxR + B.ay[i] * gAyRt + B.p[i] * double(gPR) + B.q[i] * double(gQR) +
-                 B.t[i] * double(gTR);
+    double gl = B.ax[i] * gAxL + B.ay[i] * gAyLt + B.p[i] * widen(gPL) + B.q[i] * widen(gQL) +
+                B.t[i] * widen(gTL);
+    double gr_ = B.ax[i] * gAxR + B.ay[i] * gAyRt + B.p[i] * widen(gPR) + B.q[i] * widen(gQR) +
+                 B.t[i] * widen(gTR);
     if (FOOT) {
       const int d = B.idx[i] - cin;
-      if (d >= 0 && d < 3) { gl += double(gd[d]); gr_ += double(gd[3 + d]); }
+      if (d >= 0 && d < 3) { gl += widen(gd[d]); gr_ += widen(gd[3 + d]); }
     }
     pp[2 * i] = gl;
     pp[2 * i + 1] = gr_;
   }
   ps[b] = gsd_t;
   pL[b] = Lp;
-  if (!finite_d(Lp + gsd_t + double(lth) + double(lom))) atomicOr(status, ST_NONFINITE);
+  if (!finite_d(Lp + gsd_t + widen(lth) + widen(lom))) atomicOr(status, ST_NONFINITE);
 }
 
 }  // namespace ciscvx
