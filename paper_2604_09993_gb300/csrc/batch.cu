@@ -381,6 +381,7 @@ BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot, const ciscvx_t
   c.queue = p->d_queue + queue_slot;
   c.status = p->d_status;
   c.layout = p->layout;
+  c.ck_smem = 0;
   return c;
 }
 
@@ -593,9 +594,18 @@ cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const cis
   if (e != cudaSuccess) return e;
   unsigned blocks, threads;
   grid_for(p, p->tune_fused, c.n_items, blocks, threads);
-  e = launch_disc_vjp_fused(c, p->prec, p->tune_fused.occupancy, p->compact, blocks, threads, io->X,
+  // FP32 pass: the checkpoints (4 FP32 anchors per substep and thread) in
+  // shared memory when a block's fit in the default 48 KB
+  BatchCommon cf = c;
+  size_t smem = 0;
+  const size_t ck_bytes = (size_t)threads * 4 * sizeof(float) * (size_t)p->max_nsub_adj;
+  if (p->prec == CISCVX_FP32_PHI && p->max_nsub_adj > 0 && ck_bytes <= 48u * 1024u) {
+    cf.ck_smem = 1;
+    smem = ck_bytes;
+  }
+  e = launch_disc_vjp_fused(cf, p->prec, p->tune_fused.occupancy, p->compact, blocks, threads, io->X,
                             io->U, io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty,
-                            vio->w, vio->rho, vio->gX, part, ps, pL, s);
+                            vio->w, vio->rho, vio->gX, part, ps, pL, smem, s);
   if (e == cudaSuccess && i1 > i0)
     k_batch_vjp_finish<<<i1 - i0, FINB, 0, s>>>(p->d_models, p->d_inst + i0, p->layout, part, ps,
                                                 pL, vio->gU, vio->gs, vio->L ? vio->L + i0 : nullptr);

@@ -18,6 +18,7 @@ struct BatchCommon {
   int* queue;
   unsigned* status;
   int layout;
+  int ck_smem;  // fused pass: FP32 checkpoints in dynamic shared memory (4 n_sub floats per thread)
 };
 
 __device__ __forceinline__ int next_item(const BatchCommon& c, int& local_iter) {
@@ -44,6 +45,6 @@ cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool 
                                   const double* U, const double* s, void* A, void* Bm, void* Bp,
                                   void* S, double* defect, double* penalty, const double* w,
                                   const double* rho, double* gX, double* part, double* ps,
-                                  double* pL, cudaStream_t st);
+                                  double* pL, size_t smem, cudaStream_t st);
 
 }  // namespace ciscvx

@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B)
                      double* penalty, const double* __restrict__ w,
                      const double* __restrict__ rho, double* gX, double* part, double* ps,
                      double* pL) {
+  extern __shared__ float ck_smem[];
   const int lane = threadIdx.x & 31;
   int iter = 0;
   for (;;) {
@@ -56,6 +57,8 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B)
       const double* xk = Xi + k * nxt;
       const double* xk1 = Xi + (k + 1) * nxt;
       Checkpoints ck;
+      ck.sm = c.ck_smem ? ck_smem + threadIdx.x : nullptr;
+      ck.sst = blockDim.x;
       if (B.contact >= 0) {
         disc_link<TP, true, CMP, true>(M, b, g.y, sk, xk, xk1, uL, uR, Ak, Bmk, Bpk, Sk, dk, pk,
                                        nullptr, c.status, &ck);
@@ -78,9 +81,9 @@ cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool 
                                   const double* U, const double* s, void* A, void* Bm, void* Bp,
                                   void* S, double* defect, double* penalty, const double* w,
                                   const double* rho, double* gX, double* part, double* ps,
-                                  double* pL, cudaStream_t st) {
+                                  double* pL, size_t smem, cudaStream_t st) {
 #define CISCVX_FUSED1(TP, OCC, CMP)                                                            \
-  k_batch_disc_vjp<TP, OCC, CMP><<<blocks, threads, 0, st>>>(c, X, U, s, (TP*)A, (TP*)Bm,        \
+  k_batch_disc_vjp<TP, OCC, CMP><<<blocks, threads, smem, st>>>(c, X, U, s, (TP*)A, (TP*)Bm,     \
                                                              (TP*)Bp, (TP*)S, defect, penalty, w, \
                                                              rho, gX, part, ps, pL)
 #define CISCVX_FUSED(TP, OCC)                   \

@@ -161,6 +161,20 @@ struct Checkpoints {
   double th_end, om_end, Yom;
   // the link's FOH input sums (AxL, AxR, AyL, AyR, PL, PR, QL, QR, TL, TR) and h = 1/n_sub
   double ins[10], h;
+  // When sm is set, the FP32 anchors live in shared memory instead of
+  // thf..vyf: anchor f (0 theta, 1 omega, 2 p_y, 3 v_y) of substep i at
+  // sm[(4 i + f) sst] (element-major over the block's threads, so a warp's
+  // accesses are conflict-free).  The fused pass sets it when the block's
+  // anchors fit; local memory otherwise.
+  float* sm;
+  int sst;
+  __device__ __forceinline__ void put_f(int i, int f, float v) {
+    if (sm) sm[(4 * i + f) * sst] = v;
+    else (f == 0 ? thf : f == 1 ? omf : f == 2 ? pyf : vyf)[i] = v;
+  }
+  __device__ __forceinline__ float get_f(int i, int f) const {
+    return sm ? sm[(4 * i + f) * sst] : (f == 0 ? thf : f == 1 ? omf : f == 2 ? pyf : vyf)[i];
+  }
 };
 
 __device__ __forceinline__ double rk_c(int j) { return j == 0 ? 0.0 : (j == 3 ? 1.0 : 0.5); }

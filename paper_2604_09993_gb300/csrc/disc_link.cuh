@@ -389,8 +389,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
     if (foot) ipA = input_penalty<TP, false>(0.0, TP(0), sd, sdP, mu, muP, cL, cD, cLP, cDP);
     for (int i = 0; i < nsub; ++i) {
       if constexpr (CK) {  // FP32 anchors at the substep start: the backward sweep's checkpoints
-        ck->thf[i] = anchor<TP>(S.th); ck->omf[i] = anchor<TP>(S.om);
-        if (foot) { ck->pyf[i] = anchor<TP>(S.py); ck->vyf[i] = anchor<TP>(S.vy); }
+        ck->put_f(i, 0, anchor<TP>(S.th)); ck->put_f(i, 1, anchor<TP>(S.om));
+        if (foot) { ck->put_f(i, 2, anchor<TP>(S.py)); ck->put_f(i, 3, anchor<TP>(S.vy)); }
       }
       StageF sf[4];
       df_substep<FOOT, true>(C, i, amask, S, sf);

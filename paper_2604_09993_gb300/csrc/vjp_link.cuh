@@ -92,6 +92,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
 
   // ---- forward sweep: FP64 state and checkpoints ----
   Checkpoints ckl;  // own forward sweep (unused when FUSED)
+  ckl.sm = nullptr;
   const Checkpoints& ck = FUSED ? *ckin : ckl;
   double th = th0, om = om0, py = py0, vy = vy0;
   // FP32 adjoint: the penalty quadrature is taken here, on the FP64 forward
@@ -235,8 +236,8 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
       double thc = 0, omc = 0, stc = 0, ctc = 1, pyc = 0, vyc = 0;
       TP thA = TP(0), omA = TP(0), pyA = TP(0), vyA = TP(0);
       if constexpr (F32) {
-        thA = ck.thf[i]; omA = ck.omf[i];
-        if (FOOT) { pyA = ck.pyf[i]; vyA = ck.vyf[i]; }
+        thA = ck.get_f(i, 0); omA = ck.get_f(i, 1);
+        if (FOOT) { pyA = ck.get_f(i, 2); vyA = ck.get_f(i, 3); }
       } else {
         thc = ck.th[i]; omc = ck.om[i]; stc = ck.s[i]; ctc = ck.c[i];
         if (FOOT) { pyc = ck.py[i]; vyc = ck.vy[i]; }
