@@ -70,31 +70,41 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "cheetah7-sweep-4096x400x20"
 
-# Executed FP64 flops per interval of each kernel (ncu SASS counters
+# Executed FP64 flops per interval of the FP64 kernels (ncu SASS counters
 # 2*DFMA + DADD + DMUL of one launch / intervals of that launch), recorded in
 # profiles/; keyed by (robot, n_sub, kernel, precision).  These are the counts
-# of the uncapped variant: a register-capped build recomputes some values
-# instead of spilling them and executes more (the fused pass's 128-register
-# variant 32 712), so the uncapped count stands for the algorithmic work.
+# of the uncapped variant.  The FP32-Phi kernels are not FP64-bound any more
+# (their stage values run in float-float on the FP32 pipe): their roofline is
+# the instruction issue rate below.  FP64_STATE_FLOPS is the FP64 work per
+# interval of the FP64-state formulation of the same fused pass (an earlier
+# build of this kernel), kept as a context figure.
 FLOPS_PER_INTERVAL = {
-    ("cheetah7", 20, "discretize", "fp32_phi"): 28_353,
-    ("cheetah7", 20, "vjp", "fp32_phi"): 28_562,
     ("cheetah7", 20, "discretize", "fp64"): 126_146,
     ("cheetah7", 20, "vjp", "fp64"): 82_621,
-    ("cheetah7", 20, "fused", "fp32_phi"): 30_693,
 }
+FP64_STATE_FLOPS = {("cheetah7", 20, "fused", "fp32_phi"): 30_693}
+# Warp-instructions issued per interval (ncu smsp__inst_executed.sum / the
+# 102 400 intervals of the capture), keyed by (robot, n_sub, kernel,
+# precision, register-cap variant).  The uncapped variant's count is the
+# kernel's work; a capped variant executes a few per cent more (spills and
+# recomputation).
+WARP_INSTR_PER_INTERVAL = {
+    ("cheetah7", 20, "fused", "fp32_phi", 0): 1_272_148_413 / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 1): 1_326_959_116 / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 2): 1_354_123_638 / 102400,
+}
+# Issue peak: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz.
+ISSUE_PEAK = 152 * 4 * 2.07e9
 # DRAM bytes (read + write) per interval of each kernel from the same captures
 # (256 instances x 400 intervals; traffic scales with the intervals processed),
-# keyed by (robot, n_sub, kernel, precision, register-cap variant): spills of
-# a capped variant add local-memory traffic.  None when the variant the tuner
-# picked was not captured.
+# keyed by (robot, n_sub, kernel, precision, register-cap variant).  None when
+# the variant the tuner picked was not captured.
 DRAM_BYTES_PER_INTERVAL = {
-    ("cheetah7", 20, "discretize", "fp32_phi", 0): (311.6e6 + 1898.0e6) / 102400,
-    ("cheetah7", 20, "vjp", "fp32_phi", 0): (245.4e6 + 129.3e6) / 102400,
     ("cheetah7", 20, "discretize", "fp64", 0): (407.3e6 + 3762.1e6) / 102400,
     ("cheetah7", 20, "vjp", "fp64", 0): (258.3e6 + 227.4e6) / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi", 0): (688.6e6 + 2358.6e6) / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi", 2): (1046.4e6 + 2668.5e6) / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 0): (785.2e6 + 2709.5e6) / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 1): (1021.1e6 + 2855.4e6) / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 2): (1101.8e6 + 2875.5e6) / 102400,
 }
 
 
@@ -661,21 +671,39 @@ def run_ours(args):
     else:
         dom, kt = ("discretize", kd) if kd >= kv else ("vjp", kv)
         kname = {"discretize": "k_discretize", "vjp": "k_vjp"}[dom]
-    fpi = FLOPS_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec))
     tune = wl.tune(prec)
     occ = tune[dom]["occupancy"] if tune and dom in tune else 0
     bpi = DRAM_BYTES_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec, occ))
-    roof = {"bound": "alu", "kernel": f"{kname}<{'float' if prec == 'fp32_phi' else 'double'}>",
-            "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4), "peak_source": "derived FP64 pipe",
-            "launch_ms": kt * 1e3, "separate_discretize_ms": kd * 1e3, "separate_vjp_ms": kv * 1e3,
-            "occupancy_variant": occ,
-            "traffic": None if bpi is None else bpi * wl.intervals,
-            "traffic_source": None if bpi is None else "ncu dram bytes of a 102400-interval launch, scaled"}
-    if fpi:
+    kprec = "float" if prec == "fp32_phi" else "double"
+    wpi = WARP_INSTR_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec, 0))
+    fpi = FLOPS_PER_INTERVAL.get((wl.robot_name, wl.n_sub, dom, prec))
+    if wpi:
+        # instruction issue bound: the FP32-Phi kernels run their stage values in
+        # float-float on the FP32 pipe; FP64 pipe, FP32 pipe and DRAM all below it
+        ach = wpi * wl.intervals / kt
+        roof = {"bound": "alu", "kernel": f"{kname}<{kprec}>", "unit": "G warp-instructions/s",
+                "peak": round(ISSUE_PEAK / 1e9, 1),
+                "peak_source": "derived issue rate: 152 SMs x 4 schedulers x 1 instr/clk x 2.07 GHz",
+                "achieved": ach / 1e9, "frac": ach / ISSUE_PEAK,
+                "work_per_interval": round(wpi), "work_source": "ncu smsp__inst_executed.sum, uncapped variant"}
+        f64 = FP64_STATE_FLOPS.get((wl.robot_name, wl.n_sub, dom, prec))
+        if f64:
+            roof["fp64_equivalent"] = {
+                "flops_per_interval": f64, "tflops": f64 * wl.intervals / kt / 1e12,
+                "frac_of_fp64_peak": f64 * wl.intervals / kt / 1e12 / FP64_PEAK_TFLOPS,
+                "note": "FP64 work of the FP64-state formulation of this pass, per second of this kernel"}
+    elif fpi:
         ach = fpi * wl.intervals / kt / 1e12
-        roof.update(achieved=ach, frac=ach / FP64_PEAK_TFLOPS)
+        roof = {"bound": "alu", "kernel": f"{kname}<{kprec}>", "unit": "TFLOP/s",
+                "peak": round(FP64_PEAK_TFLOPS, 4), "peak_source": "derived FP64 pipe",
+                "achieved": ach, "frac": ach / FP64_PEAK_TFLOPS}
     else:
-        roof.update(achieved=None, frac=None)
+        roof = {"bound": "alu", "kernel": f"{kname}<{kprec}>", "unit": None, "peak": None,
+                "achieved": None, "frac": None}
+    roof.update({"launch_ms": kt * 1e3, "separate_discretize_ms": kd * 1e3, "separate_vjp_ms": kv * 1e3,
+                 "occupancy_variant": occ,
+                 "traffic": None if bpi is None else bpi * wl.intervals,
+                 "traffic_source": None if bpi is None else "ncu dram bytes of a 102400-interval launch, scaled"})
 
     # end to end through the public API with host (pinned) buffers
     def measure_e2e(fmt):
