@@ -60,7 +60,8 @@ def _embed_jit_source(objdir):
     C++ raw string literals: the shared scalar math followed by each kernel."""
     math = open(os.path.join(CSRC, "dev_math.cuh")).read()
     body = ""
-    for var, fname in (("kCplTangentJitSrc", "cpl_tangent_jit.cuh"), ("kCplNominalJitSrc", "cpl_nominal_jit.cuh")):
+    for var, fname in (("kCplTangentJitSrc", "cpl_tangent_jit.cuh"), ("kCplNominalJitSrc", "cpl_nominal_jit.cuh"),
+                       ("kCplAdjointJitSrc", "cpl_adjoint_jit.cuh")):
         text = math + open(os.path.join(CSRC, fname)).read()
         assert ")CPLJIT" not in text
         body += f'static const char {var}[] = R"CPLJIT(' + text + ')CPLJIT";\n'

@@ -478,7 +478,10 @@ ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* m, ciscvx_op 
       lo = per * (size_t)std::min(N, 32);
       hi = per * (size_t)N;
     }
-  } else if (m->cpl || m->host.aux) {
+  } else if (m->cpl) {  // reverse-mode adjoint of the coupled path
+    lo = cpl_adjoint_bytes(*m->cpl, std::min(N, 32), n_sub, precision);
+    hi = cpl_adjoint_bytes(*m->cpl, N, n_sub, precision);
+  } else if (m->host.aux) {
     lo = contract_bytes(m->host, m->cpl, std::min(N, 32), n_sub, precision);
     hi = contract_bytes(m->host, m->cpl, N, n_sub, precision);
   } else {
@@ -554,7 +557,17 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
   if (st != CISCVX_OK) return st;
   if (!w || (m->host.nc > 0 && !rho)) return fail(CISCVX_EINVAL, "null cotangent array");
   if (!gX || !gs || (m->host.nu > 0 && !gU)) return fail(CISCVX_EINVAL, "null gradient array");
-  if (m->host.aux || m->cpl) {  // linearize-and-contract
+  if (m->cpl) {  // reverse-mode adjoint of the coupled path
+    const size_t need = cpl_adjoint_bytes(*m->cpl, std::min(N, 32), n_sub, precision);
+    if (!workspace || ws_bytes < need)
+      return fail(CISCVX_EINVAL, "workspace of at least %zu bytes needed (got %zu)", need, ws_bytes);
+    if (((uintptr_t)workspace & 15) != 0) return fail(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+    cudaError_t e = launch_coupled_vjp(*m->cpl, N, n_sub, precision, layout, X, U, s, w, rho, gX, gU, gs, L,
+                                       workspace, ws_bytes, m->status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "coupled adjoint launch");
+    return ok();
+  }
+  if (m->host.aux) {  // linearize-and-contract
     const size_t need = contract_bytes(m->host, m->cpl, std::min(N, 32), n_sub, precision);
     if (!workspace || ws_bytes < need)
       return fail(CISCVX_EINVAL, "workspace of at least %zu bytes needed (got %zu)", need, ws_bytes);

@@ -433,6 +433,8 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
   }
   if (!isfinite(chk)) atomicOr(status, ST_NONFINITE);
   // closed-form columns of A: e_p, e_v + s e_p (links without a contact), e_y
+  // (not written by the adjoint's forward pass, which has no A)
+  if (!A) return;
   TP* Ak = A + ad.a;
   auto unit_col = [&](int c, int r2, TP v2) {
     for (int r = 0; r < nxt; ++r) Ak[(size_t)r * nxt + c] = (r == c) ? TP(1) : (r == r2 ? v2 : TP(0));
@@ -757,6 +759,391 @@ cudaError_t run(const CplTab& T, long N, int nsub, int layout, const double* X, 
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Reverse-mode adjoint (VJP) of the coupled path: thread = interval.  The
+// forward pass is k_cpl_nominal (stage data, defects, penalty increments; no
+// A).  This kernel runs the transpose of k_cpl_tangent's stage map backward
+// over the substeps and stages, from the cotangent of x~(1),
+//   lambda = w_k + rho_k on the path-penalty rows,
+// to lambda^T [A | B- | B+ | S] = (dL/dx~_k, dL/du_L, dL/du_R, dL/ds_k) of the
+// interval — the gradient of L = sum_k w_k . defect_k + rho_k . penalty_k
+// without forming a single block.  Per stage, in reverse:
+//  * slopes: k_bar of each live row (h b_j of the substep-end cotangent plus
+//    h a_mj of every later stage's stage-tangent cotangent) and of the
+//    quadrature rows (h b_j, and h^2 s beta_j for the positions of links
+//    without a contact) give the generalized-force cotangent e_bar = M^-1 s
+//    k_bar and the velocity rows' stage cotangents;
+//  * Eq. (3): x_bar = grad C e_bar, a_bar = K^-1 x_bar (K symmetric: the same
+//    recorded factor as the forward solve), then the transposed right-hand
+//    side a(theta, omega, e) adds to the angle / rate cotangents and e_bar;
+//  * contacts: the force, its direction and the signed distance (the
+//    sinusoid's frame derivatives recorded by the nominal kernel), the
+//    penalty and Eq. (12) rows; inputs collect (1 - tau) / tau of their stage
+//    cotangent into dL/du_L / dL/du_R; s collects k_bar . F.
+// Cotangent arrays live in shared memory, element major (per thread).
+
+#define AT(o) am[(o) * bs]
+
+template <typename TP, int SCH>
+__global__ void k_cpl_adjoint(const __grid_constant__ CplTab M, long i0, long n, long N, int nsub,
+                              const double* __restrict__ s, const TP* __restrict__ sd,
+                              const double* __restrict__ w, const double* __restrict__ rho,
+                              double* __restrict__ gX, double* __restrict__ gs,
+                              double* __restrict__ ubar, unsigned* status) {
+  using Sc = Scheme<SCH>;
+  using K = Cst<TP>;
+  constexpr int NS = Sc::S;
+  extern __shared__ __align__(16) unsigned char smem3[];
+  const int bs = blockDim.x;
+  TP* am = reinterpret_cast<TP*>(smem3) + threadIdx.x;
+  const long t = (long)blockIdx.x * bs + threadIdx.x;
+  if (t >= n) return;
+  const long k = i0 + t;
+  const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
+  const int nl = M.nlive, nqd = M.nquad;
+  const int o_pl = 0, o_pq = nl, o_kb = o_pq + nqd, o_xs = o_kb + NS * nl, o_e = o_xs + nl;
+  const int o_x = o_e + 3 * nb, o_ub = o_x + nk;
+  const double* wk = w + k * nxt;
+  const int pen0 = M.pen0;
+  auto lam = [&](int r) {
+    double v = wk[r];
+    if (r >= pen0 && r < pen0 + nc) v += rho[k * nc + (r - pen0)];
+    return v;
+  };
+  for (int r = 0; r < nxt; ++r) {
+    if (M.lrow[r] >= 0) AT(o_pl + M.lrow[r]) = TP(lam(r));
+    else AT(o_pq + M.qrow[r]) = TP(lam(r));
+  }
+  for (int q = 0; q < 2 * nu; ++q) AT(o_ub + q) = TP(0);
+  const TP sk = TP(s[k]);
+  const TP h = TP(1) / TP(nsub);
+  const TP hsk = h * sk;
+  TP sbar = TP(0);
+  const TP* sdk = sd + (size_t)t * nsub * NS * M.sd_size;
+  const int ci0 = M.ci0;
+#define XB(r) AT(o_xs + M.lrow[r])
+#define EB(c) AT(o_e + (c))
+#define KB(r) AT(o_kb + j * nl + M.lrow[r])
+#define PQ(r) AT(o_pq + M.qrow[r])
+
+  for (int i = nsub - 1; i >= 0; --i) {
+    // slope cotangents of every stage start at h b_j (cotangent at the substep end)
+    for (int j = 0; j < NS; ++j) {
+      const TP hb = h * K::b(M, j);
+      for (int l = 0; l < nl; ++l) AT(o_kb + j * nl + l) = hb * AT(o_pl + l);
+    }
+    for (int j = NS - 1; j >= 0; --j) {
+      const TP* D = sdk + (size_t)(i * NS + j) * M.sd_size;
+      const TP* F = D + M.sd_F;
+      const TP bj = K::b(M, j), hbj = h * bj, h2b = h * h * sk * K::beta(M, j);
+      const TP tau = (TP(i) + K::c(M, j)) * h;
+      const TP wl = TP(1) - tau, wr = tau;
+      for (int l = 0; l < nl; ++l) AT(o_xs + l) = TP(0);
+      for (int c = 0; c < 3 * nb; ++c) EB(c) = TP(0);
+      // input cotangent of this stage -> dL/du_L, dL/du_R
+      auto uput = [&](int q, TP v) {
+        AT(o_ub + q) += wl * v;
+        AT(o_ub + nu + q) += wr * v;
+      };
+      // ---- slopes (transposed) ----
+      for (int b = 0; b < nb; ++b) {
+        const TP mi = K::minv(M, b), ii = K::iinv(M, b);
+        {
+          const TP kb = KB(3 * b + 2);  // theta' = s omega
+          XB(nq + 3 * b + 2) += sk * kb;
+          sbar += kb * F[3 * b + 2];
+        }
+        {
+          const TP kb = KB(nq + 3 * b + 2);  // omega' = s e_ang / I
+          EB(3 * b + 2) += sk * kb * ii;
+          sbar += kb * F[nq + 3 * b + 2];
+        }
+        if (M.contact[b] >= 0) {
+          for (int c2 = 0; c2 < 2; ++c2) {
+            const TP kp = KB(3 * b + c2);  // p' = s v
+            XB(nq + 3 * b + c2) += sk * kp;
+            sbar += kp * F[3 * b + c2];
+            const TP kv = KB(nq + 3 * b + c2);  // v' = s e_lin / m
+            EB(3 * b + c2) += sk * kv * mi;
+            sbar += kv * F[nq + 3 * b + c2];
+          }
+        } else {
+          // quadrature rows: v += h b_j k_v, p += h^2 s beta_j k_v
+          for (int c2 = 0; c2 < 2; ++c2) {
+            const TP Pp = PQ(3 * b + c2), Pv = PQ(nq + 3 * b + c2);
+            const TP kvb = h2b * Pp + hbj * Pv;
+            EB(3 * b + c2) += sk * kvb * mi;
+            sbar += kvb * F[nq + 3 * b + c2] + Pp * h2b * F[nq + 3 * b + c2];
+            if (j == 0) sbar += Pp * h * F[3 * b + c2];  // d(h s v_start)/ds
+          }
+        }
+      }
+      // ---- Eq. (3) (transposed): e += grad C^T x, x = K^-1 a(theta, omega, e) ----
+      if (M.jelim && nk > 0) {
+        for (int jj = 0; jj < nj; ++jj) {
+          TP lx = TP(0), ly = TP(0);
+          for (int role = 0; role < 2; ++role) {
+            const int b = role ? M.jpar[jj] : M.jchi[jj];
+            const TP rx = D[M.sd_arm + 4 * jj + 2 * role], ry = D[M.sd_arm + 4 * jj + 2 * role + 1];
+            const TP vx = EB(3 * b) - ry * EB(3 * b + 2), vy = EB(3 * b + 1) + rx * EB(3 * b + 2);
+            if (role) { lx -= vx; ly -= vy; } else { lx += vx; ly += vy; }
+          }
+          AT(o_x + 2 * M.npos[jj]) = lx;
+          AT(o_x + 2 * M.npos[jj] + 1) = ly;
+        }
+        const TP* Kf = D + M.sd_K;
+        for (int ii = 1; ii < nk; ++ii) {
+          TP acc = AT(o_x + ii);
+          const TP* row = Kf + M.noff[ii] - M.nf[ii];
+          for (int kk = M.nf[ii]; kk < ii; ++kk) acc -= row[kk] * AT(o_x + kk);
+          AT(o_x + ii) = acc;
+        }
+        for (int ii = nk - 1; ii >= 0; --ii) {
+          TP acc = AT(o_x + ii) * Kf[M.noff[ii] + ii - M.nf[ii]];
+          for (int kk = ii + 1; kk < nk; ++kk)
+            if (M.nf[kk] <= ii) acc -= Kf[M.noff[kk] + ii - M.nf[kk]] * AT(o_x + kk);
+          AT(o_x + ii) = acc;
+        }
+        for (int jj = 0; jj < nj; ++jj) {
+          const TP a0b = AT(o_x + 2 * M.npos[jj]), a1b = AT(o_x + 2 * M.npos[jj] + 1);
+          for (int role = 0; role < 2; ++role) {
+            const int b = role ? M.jpar[jj] : M.jchi[jj];
+            const TP rx = D[M.sd_arm + 4 * jj + 2 * role], ry = D[M.sd_arm + 4 * jj + 2 * role + 1];
+            const TP om = F[3 * b + 2], omd = F[nq + 3 * b + 2];
+            const TP c0 = role ? -a0b : a0b, c1 = role ? -a1b : a1b;
+            XB(nq + 3 * b + 2) += TP(2) * om * (rx * c0 + ry * c1);
+            XB(3 * b + 2) += (-om * om * ry + omd * rx) * c0 + (om * om * rx + omd * ry) * c1;
+            EB(3 * b) -= K::minv(M, b) * c0;
+            EB(3 * b + 1) -= K::minv(M, b) * c1;
+            EB(3 * b + 2) += K::iinv(M, b) * (ry * c0 - rx * c1);
+          }
+        }
+      }
+      // ---- contacts (transposed): force, frame, signed distance, auxiliary rows ----
+      for (int ic = 0; ic < nc; ++ic) {
+        const int b = M.cbody[ic];
+        const TP* Dc = D + M.sd_con + M.ncf * ic;
+        const TP rx = Dc[0], ry = Dc[1];
+        const TP fxb = EB(3 * b) - ry * EB(3 * b + 2), fyb = EB(3 * b + 1) + rx * EB(3 * b + 2);
+        TP ftb = Dc[2] * fxb + Dc[3] * fyb, fnb = Dc[4] * fxb + Dc[5] * fyb, gab = TP(0);
+        TP xcb = Dc[6] * fxb + Dc[7] * fyb, phib = TP(0);
+        // cotangent of a quadrature row's slope argument dy (kv = s dy + F)
+        auto qrow_bar = [&](int row) {
+          const TP kvb = hbj * PQ(row);
+          sbar += kvb * F[row];
+          return sk * kvb;
+        };
+        const int u0 = ci0 + 3 * ic;
+        if (!M.aux) {
+          const TP yb = qrow_bar(6 * nb + ic);
+          phib = Dc[10] * yb;
+          // inputs (lambda_n, lambda_t+, lambda_t-): force components and penalty slopes
+          uput(u0, fnb + Dc[11] * yb);
+          uput(u0 + 1, ftb + Dc[12] * yb);
+          uput(u0 + 2, -ftb + Dc[13] * yb);
+        } else {
+          const TP y0 = qrow_bar(6 * nb + 4 * ic), y1 = qrow_bar(6 * nb + 4 * ic + 1);
+          const TP y2 = qrow_bar(6 * nb + 4 * ic + 2), y3 = qrow_bar(6 * nb + 4 * ic + 3);
+          const TP y4 = qrow_bar(6 * nb + 4 * nc + ic);
+          fnb += y0 + Dc[20] * y3 + Dc[12] * y4;
+          gab += y2 + Dc[18] * y1 + Dc[13] * y4;
+          ftb += Dc[17] * y1 + Dc[19] * y3 + Dc[11] * y4;
+          xcb += Dc[16] * y1;
+          phib = Dc[10] * y4;
+          // lambda^c's contact-point velocity (v_x - omega r_y, v_y + omega r_x)
+          const TP om = F[3 * b + 2];
+          const TP vxb = Dc[2] * y1, vyb = Dc[3] * y1;
+          XB(nq + 3 * b) += vxb;
+          XB(nq + 3 * b + 1) += vyb;
+          XB(nq + 3 * b + 2) += -ry * vxb + rx * vyb;
+          XB(3 * b + 2) += -om * (rx * vxb + ry * vyb);
+          // inputs (phi_t, phi_n, gamma)
+          uput(u0, ftb);
+          uput(u0 + 1, fnb);
+          uput(u0 + 2, gab);
+        }
+        xcb += Dc[8] * phib;
+        const TP ycb = Dc[9] * phib;
+        XB(3 * b) += xcb;
+        XB(3 * b + 1) += ycb;
+        XB(3 * b + 2) += -ry * xcb + rx * ycb;
+      }
+      // ---- direct inputs: torques, and reaction forces when they are inputs ----
+      for (int jj = 0; jj < nj; ++jj) {
+        uput(jj, EB(3 * M.jchi[jj] + 2) - EB(3 * M.jpar[jj] + 2));
+        if (!M.jelim) {
+          for (int cp = 0; cp < 2; ++cp) {
+            TP v = TP(0);
+            for (int role = 0; role < 2; ++role) {
+              const int b = role ? M.jpar[jj] : M.jchi[jj];
+              const TP rx = D[M.sd_arm + 4 * jj + 2 * role], ry = D[M.sd_arm + 4 * jj + 2 * role + 1];
+              const TP c = EB(3 * b + cp) + (cp ? rx : -ry) * EB(3 * b + 2);
+              v = role ? v - c : v + c;
+            }
+            uput(nj + 2 * jj + cp, v);
+          }
+        }
+      }
+      // ---- moving application points: e_ang = -dtheta QW ----
+      for (int b = 0; b < nb; ++b) XB(3 * b + 2) -= D[M.sd_qw + b] * EB(3 * b + 2);
+      // stage-tangent cotangent -> the substep start and the earlier stages' slopes
+      for (int l = 0; l < nl; ++l) {
+        const TP xb = AT(o_xs + l);
+        AT(o_pl + l) += xb;
+        for (int m = 0; m < j; ++m) {
+          const TP ah = K::a(M, j, m) * h;
+          if (ah != TP(0)) AT(o_kb + m * nl + l) += ah * xb;
+        }
+      }
+    }
+    // p += h s v at the substep start (links without a contact)
+    for (int b = 0; b < nb; ++b) {
+      if (M.contact[b] >= 0) continue;
+      for (int c2 = 0; c2 < 2; ++c2) PQ(nq + 3 * b + c2) += hsk * PQ(3 * b + c2);
+    }
+  }
+#undef XB
+#undef EB
+#undef KB
+#undef PQ
+  // dL/dx~_k = A^T lambda - rho (own penalty rows) - w_{k-1}
+  double chk = 0.0;
+  for (int r = 0; r < nxt; ++r) {
+    double v = widen(M.lrow[r] >= 0 ? AT(o_pl + M.lrow[r]) : AT(o_pq + M.qrow[r]));
+    if (r >= pen0 && r < pen0 + nc) v -= rho[k * nc + (r - pen0)];
+    if (k >= 1) v -= w[(k - 1) * nxt + r];
+    gX[k * nxt + r] = v;
+    if (k == N - 1) gX[N * nxt + r] = -wk[r];
+    chk += v;
+  }
+  gs[k] = widen(sbar);
+  double* ub = ubar + (size_t)t * 2 * nu;
+  for (int q = 0; q < 2 * nu; ++q) ub[q] = widen(AT(o_ub + q));
+  if (!isfinite(chk + widen(sbar))) atomicOr(status, ST_NONFINITE);
+}
+
+#undef AT
+
+// dL/du from the per-interval input cotangents of a chunk [i0, i0 + n):
+// interval layout gU[k] = (u_L bar, u_R bar); node layout gU[k] = u_L bar(k) +
+// u_R bar(k - 1), the term of the chunk's previous interval carried through
+// gU itself across chunk boundaries (chunks run in stream order).
+__global__ void k_cpl_adjoint_u(int nu, long i0, long n, int layout, const double* __restrict__ ubar,
+                                double* __restrict__ gU) {
+  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long t = g / nu;
+  if (t >= n) return;
+  const int q = (int)(g - t * nu);
+  const long k = i0 + t;
+  const double* ub = ubar + (size_t)t * 2 * nu;
+  if (layout == CISCVX_FOH_INTERVAL) {
+    gU[(2 * k) * nu + q] = ub[q];
+    gU[(2 * k + 1) * nu + q] = ub[nu + q];
+  } else {
+    double prev = 0.0;
+    if (t > 0) prev = ubar[(size_t)(t - 1) * 2 * nu + nu + q];
+    else if (k > 0) prev = gU[k * nu + q];
+    gU[k * nu + q] = ub[q] + prev;
+    if (t == n - 1) gU[(k + 1) * nu + q] = ub[nu + q];
+  }
+}
+
+// L over a chunk: one block, a fixed order (deterministic), added to *L.
+__global__ void k_cpl_adjoint_L(int nxt, int nc, long i0, long n, const double* __restrict__ defect,
+                                const double* __restrict__ penalty, const double* __restrict__ w,
+                                const double* __restrict__ rho, double* L) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  const long tot = n * (nxt + nc);
+  for (long e = threadIdx.x; e < tot; e += blockDim.x) {
+    if (e < n * nxt) acc = fma(w[i0 * nxt + e], defect[e], acc);
+    else {
+      const long f = e - n * nxt;
+      acc = fma(rho[i0 * nc + f], penalty[f], acc);
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *L += red[0];
+}
+
+// Adjoint block size: the largest of 128 / 64 / 32 threads whose cotangent
+// scratch fits in 96 KB.
+template <typename TP>
+int adjoint_block(const CplTab& T) {
+  const size_t per = (size_t)(2 * T.nlive + T.nquad + T.stages * T.nlive + 3 * T.nb + T.nk + 2 * T.nu) *
+                     sizeof(TP);
+  for (int bs = 128; bs > 32; bs /= 2)
+    if (bs * per <= 96u * 1024u) return bs;
+  return 32;
+}
+
+template <typename TP, int SCH>
+cudaError_t run_vjp(const CplTab& T, long N, int nsub, int layout, const double* X, const double* U,
+                    const double* s, const double* w, const double* rho, double* gX, double* gU,
+                    double* gs, double* L, void* ws, size_t ws_bytes, unsigned* status, cudaStream_t st) {
+  const int prec = std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI;
+  const CplJit* jnom = cpl_jit_nominal(T, prec);
+  const CplJit* jadj = cpl_jit_adjoint(T, prec);
+  cudaError_t e = prepare<TP, SCH>(T);
+  if (e != cudaSuccess) return e;
+  static bool adj_ready = false;  // raise the adjoint's shared-memory limit once
+  if (!adj_ready) {
+    e = cudaFuncSetAttribute(k_cpl_adjoint<TP, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e != cudaSuccess) return e;
+    adj_ready = true;
+  }
+  const size_t sm1 = (size_t)T.n_size * sizeof(double) * 32;
+  const int bs = adjoint_block<TP>(T);
+  const size_t sm3 = (size_t)bs * (2 * T.nlive + T.nquad + T.stages * T.nlive + 3 * T.nb + T.nk + 2 * T.nu) *
+                     sizeof(TP);
+  long lo = 1, hi = N;  // largest chunk whose workspace fits (the caller checked that min(N, 32) does)
+  while (lo < hi) {
+    const long mid = (lo + hi + 1) / 2;
+    if (cpl_adjoint_bytes(T, mid, nsub, prec) <= ws_bytes) lo = mid; else hi = mid - 1;
+  }
+  const long chunk = lo;
+  const CplAdjLayout Ly = cpl_adjoint_layout(T, chunk, nsub, prec);
+  char* base = (char*)ws;
+  TP* sd = (TP*)(base + Ly.stage);
+  double* defect = (double*)(base + Ly.defect);
+  double* penalty = (double*)(base + Ly.penalty);
+  double* ubar = (double*)(base + Ly.ubar);
+  if (L) e = cudaMemsetAsync(L, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const int nxt = T.nxt, nu = T.nu;
+  for (long i0 = 0; i0 < N; i0 += chunk) {
+    const long n = std::min<long>(chunk, N - i0);
+    const double* Xc = X + i0 * nxt;
+    const double* Uc = U ? (layout == CISCVX_FOH_NODE ? U + i0 * nu : U + 2 * i0 * nu) : nullptr;
+    if (jnom)
+      e = cpl_jit_launch_nominal(*jnom, T, 0, n, nsub, layout, Xc, Uc, s + i0, sd, nullptr, defect, penalty,
+                                 status, st, nullptr, nullptr);
+    else
+      k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
+          T, 0, n, nsub, layout, Xc, Uc, s + i0, sd, (TP*)nullptr, defect, penalty, status, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (jadj) {
+      e = cpl_jit_launch_adjoint(*jadj, T, prec, i0, n, N, nsub, s, sd, w, rho, gX, gs, ubar, status, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      k_cpl_adjoint<TP, SCH><<<(unsigned)((n + bs - 1) / bs), bs, sm3, st>>>(T, i0, n, N, nsub, s, sd, w, rho,
+                                                                           gX, gs, ubar, status);
+    }
+    if (nu > 0)
+      k_cpl_adjoint_u<<<(unsigned)((n * nu + 127) / 128), 128, 0, st>>>(nu, i0, n, layout, ubar, gU);
+    if (L) k_cpl_adjoint_L<<<1, 256, 0, st>>>(nxt, T.nc, i0, n, defect, penalty, w, rho, L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Butcher tableaux: classical RK4 and Fehlberg's 4(5) pair advanced with its
 // fifth-order weights (the published coefficients).
 void set_tableau(int scheme, CplTab& T) {
@@ -922,9 +1309,36 @@ cudaError_t launch_coupled(const CplTab& T, long N, int nsub, int prec, int layo
                   : run<float, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst);
 }
 
+CplAdjLayout cpl_adjoint_layout(const CplTab& T, long n, int nsub, int prec) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  CplAdjLayout Ly;
+  Ly.stage = 0;
+  Ly.defect = al(Ly.stage + (size_t)n * cpl_interval_bytes(T, nsub, prec));
+  Ly.penalty = al(Ly.defect + (size_t)n * T.nxt * sizeof(double));
+  Ly.ubar = al(Ly.penalty + (size_t)n * (T.nc > 0 ? T.nc : 1) * sizeof(double));
+  Ly.total = al(Ly.ubar + (size_t)n * 2 * (T.nu > 0 ? T.nu : 1) * sizeof(double));
+  return Ly;
+}
+
+size_t cpl_adjoint_bytes(const CplTab& T, long n, int nsub, int prec) {
+  return cpl_adjoint_layout(T, n, nsub, prec).total;
+}
+
+cudaError_t launch_coupled_vjp(const CplTab& T, long N, int nsub, int prec, int layout, const double* X,
+                               const double* U, const double* s, const double* w, const double* rho,
+                               double* gX, double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
+                               unsigned* status, cudaStream_t st) {
+  if (prec == CISCVX_FP64)
+    return T.scheme ? run_vjp<double, 1>(T, N, nsub, layout, X, U, s, w, rho, gX, gU, gs, L, ws, ws_bytes, status, st)
+                    : run_vjp<double, 0>(T, N, nsub, layout, X, U, s, w, rho, gX, gU, gs, L, ws, ws_bytes, status, st);
+  return T.scheme ? run_vjp<float, 1>(T, N, nsub, layout, X, U, s, w, rho, gX, gU, gs, L, ws, ws_bytes, status, st)
+                  : run_vjp<float, 0>(T, N, nsub, layout, X, U, s, w, rho, gX, gU, gs, L, ws, ws_bytes, status, st);
+}
+
 cudaError_t cpl_prepare(const CplTab& T, int prec) {
   cpl_jit_tangent(T, prec);
   cpl_jit_nominal(T, prec);
+  cpl_jit_adjoint(T, prec);
   if (prec == CISCVX_FP64) return T.scheme ? prepare<double, 1>(T) : prepare<double, 0>(T);
   return T.scheme ? prepare<float, 1>(T) : prepare<float, 0>(T);
 }

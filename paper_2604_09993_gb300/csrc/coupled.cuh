@@ -110,10 +110,29 @@ cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, lo
                                    void* sd, void* A, double* defect, double* penalty,
                                    unsigned* status, cudaStream_t st, const int2* entries,
                                    const DevInst* inst);
+const CplJit* cpl_jit_adjoint(const CplTab& T, int prec);
+cudaError_t cpl_jit_launch_adjoint(const CplJit& J, const CplTab& T, int prec, long i0, long n, long N, int nsub,
+                                   const double* s, const void* sd, const double* w, const double* rho,
+                                   double* gX, double* gs, double* ubar, unsigned* status, cudaStream_t st);
 cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,
                            const double* s, const void* sd, void* A, void* Bm, void* Bp, void* S,
                            unsigned* status, cudaStream_t st, int layout, const int2* entries,
                            const DevInst* inst);
+
+// Reverse-mode VJP of the coupled path (coupled.cu): the nominal kernel's
+// forward pass into the stage data of a chunk, then the adjoint kernel (thread
+// = interval) backward over the stages; no dense block is formed.  Workspace
+// of a chunk of n intervals: stage data, defects, penalty increments and the
+// per-interval input cotangents (dL/du_L, dL/du_R).
+struct CplAdjLayout {
+  size_t stage, defect, penalty, ubar, total;
+};
+CplAdjLayout cpl_adjoint_layout(const CplTab& T, long n, int nsub, int prec);
+size_t cpl_adjoint_bytes(const CplTab& T, long n, int nsub, int prec);
+cudaError_t launch_coupled_vjp(const CplTab& T, long N, int nsub, int prec, int layout, const double* X,
+                               const double* U, const double* s, const double* w, const double* rho,
+                               double* gX, double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
+                               unsigned* status, cudaStream_t st);
 
 // VJP by linearize-and-contract (contract.cu): workspace bytes for a chunk of
 // n intervals, and the chunked launch (T null for per-link models).

@@ -428,6 +428,8 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
   }
   if (!isfinite(chk)) atomicOr(status, 1u);
   // closed-form columns of A: e_p, e_v + s e_p (links without a contact), e_y
+  // (not written by the adjoint's forward pass, which has no A)
+  if (!A) return;
   TP* Ak = A + ad.a;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {

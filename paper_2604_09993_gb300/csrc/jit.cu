@@ -25,7 +25,7 @@
 #include <vector>
 
 #include "coupled.cuh"
-#include "cpl_jit_src.inc"  // kCplTangentJitSrc, kCplNominalJitSrc (generated from the .cuh sources)
+#include "cpl_jit_src.inc"  // kCplTangentJitSrc, kCplNominalJitSrc, kCplAdjointJitSrc (generated from the .cuh sources)
 
 namespace ciscvx {
 
@@ -209,6 +209,15 @@ const CplJit* cpl_jit_nominal(const CplTab& T, int prec) {
   return compile(src, "cpl_nominal", 32, smem);
 }
 
+const CplJit* cpl_jit_adjoint(const CplTab& T, int prec) {
+  const char* env = std::getenv("CISCVX_COUPLED_JIT");
+  if (env && env[0] == '0') return nullptr;
+  const int bs = prec == CISCVX_FP64 ? 32 : 64;
+  const size_t el = prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+  const size_t smem = T.scheme ? (size_t)6 * T.nlive * bs * el : 0;  // RKF45's stage slope cotangents
+  return compile(prelude(T, prec, bs) + kCplAdjointJitSrc, "cpl_adjoint", bs, smem);
+}
+
 namespace {
 
 const CplJit* compile(const std::string& src0, const char* name, int bs, size_t smem) {
@@ -238,7 +247,7 @@ const CplJit* compile(const std::string& src0, const char* name, int bs, size_t 
     g_nvrtc.log_size(prog, &n);
     std::string log(n, '\0');
     if (n) g_nvrtc.log(prog, &log[0]);
-    std::fprintf(stderr, "ciscvx: coupled tangent kernel compile %s\n%s\n", rc ? "failed" : "log", log.c_str());
+    std::fprintf(stderr, "ciscvx: coupled %s kernel compile %s\n%s\n", name, rc ? "failed" : "log", log.c_str());
   }
   if (rc != 0) { g_nvrtc.destroy(&prog); return nullptr; }
   size_t nb = 0;
@@ -303,6 +312,24 @@ cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, 
   void* args[] = {num, &i0, &n, &nsub, &s, &sd, &A, &Bm, &Bp, &S, &status, &layout, &entries, &inst};
   const long threads = n * T.cnt;
   const unsigned grid = (unsigned)((threads + J.bs - 1) / J.bs);
+  const CUresult r = g_drv.launch((CUfunction)J.fn, grid, 1, 1, J.bs, 1, 1, (unsigned)J.smem, (CUstream)st, args, nullptr);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+cudaError_t cpl_jit_launch_adjoint(const CplJit& J, const CplTab& T, int prec, long i0, long n, long N, int nsub,
+                                   const double* s, const void* sd, const double* w, const double* rho,
+                                   double* gX, double* gs, double* ubar, unsigned* status, cudaStream_t st) {
+  // NumA {TP minv[NB]; TP iinv[NB];}
+  unsigned char num[2 * MAXB * sizeof(double)];
+  if (prec == CISCVX_FP64) {
+    double* d = (double*)num;
+    for (int b = 0; b < T.nb; ++b) { d[b] = T.minv[b]; d[T.nb + b] = T.iinv[b]; }
+  } else {
+    float* f = (float*)num;
+    for (int b = 0; b < T.nb; ++b) { f[b] = T.minvf[b]; f[T.nb + b] = T.iinvf[b]; }
+  }
+  void* args[] = {num, &i0, &n, &N, &nsub, &s, &sd, &w, &rho, &gX, &gs, &ubar, &status};
+  const unsigned grid = (unsigned)((n + J.bs - 1) / J.bs);
   const CUresult r = g_drv.launch((CUfunction)J.fn, grid, 1, 1, J.bs, 1, 1, (unsigned)J.smem, (CUstream)st, args, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }

@@ -4,8 +4,9 @@ against the FP64 oracle, through the C ABI.
 
 Tolerances as for the per-link path: FP64 rel <= 1e-10 on every block
 (block-normwise); FP32-Phi rel <= 1e-4 on A, B-, B+, S and rel <= 1e-10 on
-defect and penalty; the linearize-and-contract VJP against the oracle's
-Phi-contracted gradient at the same tolerances.  Sizes span several warps of
+defect and penalty; the reverse-mode adjoint VJP against the oracle's
+Phi-contracted gradient at the same tolerances and against central
+differences on a tiny case.  Sizes span several warps of
 intervals, thread blocks of tangent columns and a ragged tail; a short
 workspace forces several chunks.
 """
@@ -216,6 +217,90 @@ def test_vjp_matches_oracle(env, precision, tol, layout):
     for g, r, nm in ((gX, rX, "gX"), (gU, rU, "gU"), (gs, rs, "gs")):
         assert block_err(g.cpu().numpy(), r) <= tol, (nm, block_err(g.cpu().numpy(), r))
     assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))
+
+
+FEATURES = [
+    dict(joint_forces=1, scheme=0),                                  # Eq. (3) alone
+    dict(joint_forces=0, scheme=0, terrain=synth.TERRAIN_SINE),      # surface alone
+    dict(joint_forces=0, scheme=1),                                  # RKF45 alone
+    dict(joint_forces=1, scheme=0, terrain=synth.TERRAIN_SINE),
+]
+FEATURE_IDS = ["eliminated", "terrain", "rkf45", "eliminated+terrain"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("feature", FEATURES, ids=FEATURE_IDS)
+def test_vjp_each_feature_matches_oracle(env, precision, tol, feature):
+    """The reverse-mode adjoint under each modelling option alone and combined."""
+    p = _problem("cheetah7", 35, 37, 4, **feature)
+    (gX, gU, gs, L), (rX, rU, rs, rL) = _vjp(env, p, precision)
+    for g, r, nm in ((gX, rX, "gX"), (gU, rU, "gU"), (gs, rs, "gs")):
+        assert block_err(g.cpu().numpy(), r) <= tol, (nm, block_err(g.cpu().numpy(), r))
+    assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("name,N,n_sub,cross", [("hopper", 10, 4, False), ("biped", 40, 3, True),
+                                                ("hopper", 1, 1, True)])
+def test_vjp_robots_and_eq12_state(env, precision, tol, name, N, n_sub, cross):
+    """Other robots, the full Eq. (12) auxiliary state with the paper's dynamics,
+    and the degenerate N = 1, n_sub = 1."""
+    p = _problem(name, 36, N, n_sub, cross=cross, **PAPER)
+    for layout in ("node", "interval"):
+        (gX, gU, gs, L), (rX, rU, rs, rL) = _vjp(env, p, precision, layout)
+        for g, r, nm in ((gX, rX, "gX"), (gU, rU, "gU"), (gs, rs, "gs")):
+            assert block_err(g.cpu().numpy(), r) <= tol, (layout, nm, block_err(g.cpu().numpy(), r))
+        assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))
+
+
+def test_vjp_central_differences(env):
+    """The adjoint's gradient against central differences (h = 1e-6) of
+    L = sum w . defect + rho . penalty, evaluated with the FP64 linearization
+    of the same path, on a tiny case (hopper, N = 2, 2 RKF45 substeps)."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("hopper", 37, 2, 2, **PAPER)
+    m = api.Model(p.robot)
+    rng = np.random.default_rng(38)
+    w = rng.standard_normal((p.N, m.nxt))
+    rho = np.full((p.N, m.nc), 10.0)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    gX, gU, gs, L = api.discretize_vjp(m, t(p.X), t(p.U), t(p.s), t(w), t(rho), p.n_sub, "fp64")
+    gX, gU, gs = gX.cpu().numpy(), gU.cpu().numpy(), gs.cpu().numpy()
+
+    def Lval(X, U, s):
+        o = api.discretize(m, t(X), t(U), t(s), p.n_sub, "fp64")
+        return float((o["defect"].cpu().numpy() * w).sum() + (o["penalty"].cpu().numpy() * rho).sum())
+
+    assert abs(Lval(p.X, p.U, p.s) - L.item()) <= 1e-12 * max(1.0, abs(L.item()))
+    h = 1e-6
+    for arr, g in ((p.X, gX), (p.U, gU), (p.s, gs)):
+        fd = np.zeros(arr.size)
+        for i in range(arr.size):
+            a, b = arr.copy().ravel(), arr.copy().ravel()
+            a[i] += h
+            b[i] -= h
+            args_a = [a.reshape(arr.shape) if x is arr else x for x in (p.X, p.U, p.s)]
+            args_b = [b.reshape(arr.shape) if x is arr else x for x in (p.X, p.U, p.s)]
+            fd[i] = (Lval(*args_a) - Lval(*args_b)) / (2 * h)
+        assert block_err(g.ravel(), fd) <= 1e-6, block_err(g.ravel(), fd)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_phi", 1e-5)])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_specialized_and_generic_adjoint_kernels_agree(env, precision, tol, scheme, monkeypatch):
+    """The run-time specialized adjoint (default) and the generic one
+    (CISCVX_COUPLED_JIT=0) give the same gradient; both meet the oracle."""
+    p = _problem("cheetah7", 39, 41, 3, joint_forces=1, scheme=scheme, terrain=synth.TERRAIN_SINE)
+    a, ref = _vjp(env, p, precision)
+    monkeypatch.setenv("CISCVX_COUPLED_JIT", "0")
+    b, _ = _vjp(env, p, precision)
+    monkeypatch.delenv("CISCVX_COUPLED_JIT")
+    otol = TOL_FP64 if precision == "fp64" else TOL_FP32_PHI
+    for ga, gb, r in zip(a[:3], b[:3], ref[:3]):
+        ga, gb = ga.cpu().numpy(), gb.cpu().numpy()
+        assert block_err(ga, r) <= otol and block_err(gb, r) <= otol
+        assert block_err(ga, gb) <= tol, block_err(ga, gb)
 
 
 def test_vjp_chunking_is_bitwise_equal(env):

@@ -8,8 +8,9 @@ memory held inside the library.  Here it is called twice in a row, through
 the C ABI and through the Python wrapper, and both results are checked against
 ciscvx_discretize_vjp with a caller workspace, within the tolerances the parity
 tests use: the default per-link model in FP64 and FP32-Phi, the Eq. (12)
-auxiliary-state model and a model with coupled links (both linearize-and-
-contract, chunked to what the static array holds).  It must pass alone in a
+auxiliary-state model (linearize-and-contract) and a model with coupled links
+(the reverse-mode adjoint of the coupled path), both chunked to what the
+static array holds.  It must pass alone in a
 fresh process and after the other tests, so it builds and loads everything it
 needs itself.  This file is collected last.
 """
@@ -54,7 +55,7 @@ def _problem(kind):
         N, n_sub = 1000, 10
     else:  # paper dynamics: coupled links (Eq. (3)), RKF45, sinusoidal surface
         R = synth.with_paper_dynamics(synth.cheetah7(rng), terrain=synth.TERRAIN_SINE)
-        N, n_sub = 300, 5
+        N, n_sub = 700, 5
     return synth.draw_instance(R, rng, N, n_sub, q_noise=0.1, u_dist="normal", s_range=(0.01, 0.05),
                                with_cotangents=True)
 
@@ -74,7 +75,7 @@ def test_static_scratch_vjp_matches_workspace_vjp_twice(env, kind, precision):
     X, U, s, w, rho = t(p.X), t(p.U), t(p.s), t(p.w), t(p.rho)
     lo, hi = api.discretize_workspace_size(m, p.N, p.n_sub, precision, api.OP_VJP)
     assert lo <= api.STATIC_SCRATCH_BYTES
-    if kind != "cheetah7":  # linearize-and-contract: more than one chunk of the static array
+    if kind != "cheetah7":  # chunked: more than one chunk of the static array
         assert hi > api.STATIC_SCRATCH_BYTES
     ref = api.discretize_vjp(m, X, U, s, w, rho, p.n_sub, precision)
     tol = TOL_FP64 if precision == "fp64" else TOL_FP32_PHI
