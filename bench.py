@@ -571,7 +571,7 @@ def run_ours(args):
         mp = api.Model(pp.robot)
         t_ = lambda a: torch.tensor(a, device=dev)  # noqa: E731
         Xp, Up, sp = t_(pp.X), t_(pp.U), t_(pp.s)
-        paper = {"metric": "linearized intervals/s (STM), and of the linearize-and-contract VJP",
+        paper = {"metric": "linearized intervals/s (STM), and of the reverse-mode adjoint VJP",
                  "unit": "intervals/s",
                  "workload": f"7-link chain, eliminated joint forces, RKF45, sinusoidal surface "
                              f"{synth.TERRAIN_SINE[0]} sin({synth.TERRAIN_SINE[1]:.4f} x), "

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(FINB) k_batch_vjp_finish(const DevModel* const
                                                            double* gU, double* gs, double* L) {
   __shared__ double red[FINB];
   const DevInst I = inst[blockIdx.x];
-  if (I.contract) return;  // written by the linearize-and-contract pass
+  if (I.contract) return;  // written by the contract pass (coupled adjoint or linearize-and-contract)
   const DevModel& M = *models[I.model];
   const int nu = M.nu, nslot = M.nslot, nb = M.nb, N = I.N;
   const double* P = part + I.part;
@@ -510,17 +510,28 @@ size_t contract_ws_offset(const ciscvx_batch_plan* p) {
   return (sizeof(double) * (p->part_total + 2 * p->pb_total) + 15) & ~(size_t)15;
 }
 
-// The VJP of every contract instance (Eq. (12) state or coupled links) by
-// linearize-and-contract, one instance after another in stream order, each
-// in chunks of what fits in the workspace.
+// The VJP of the contract instances one after another in stream order, each
+// in chunks of what fits in the workspace: the reverse-mode adjoint of the
+// coupled path for coupled-link models, linearize-and-contract for the Eq.
+// (12) state (only the coupled ones when `coupled_only`).
 cudaError_t launch_contract_instances(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, void* ws,
-                                      size_t ws_bytes, cudaStream_t s) {
+                                      size_t ws_bytes, cudaStream_t s, bool coupled_only = false) {
   for (int i = 0; i < p->n_inst; ++i) {
     const DevInst& I = p->inst[i];
     if (!I.contract) continue;
     const ciscvx_model* m = p->models[I.model];
     const bool nu = m->host.nu > 0, nc = m->host.nc > 0;
-    cudaError_t e = launch_contract_vjp(
+    cudaError_t e = cudaSuccess;
+    if (m->cpl) {
+      e = launch_coupled_vjp(*m->cpl, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
+                             io->s + I.s, io->w + I.v, nc ? io->rho + I.p : nullptr, io->gX + I.x,
+                             nu ? io->gU + I.u : nullptr, io->gs + I.s, io->L ? io->L + i : nullptr, ws, ws_bytes,
+                             p->d_status, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    if (coupled_only) continue;
+    e = launch_contract_vjp(
         m->host, m->dev, m->cpl, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
         io->s + I.s, io->w + I.v, nc ? io->rho + I.p : nullptr, io->gX + I.x, nu ? io->gU + I.u : nullptr,
         io->gs + I.s, io->L ? io->L + i : nullptr, ws, ws_bytes, p->d_status, s);
@@ -529,13 +540,14 @@ cudaError_t launch_contract_instances(ciscvx_batch_plan* p, const ciscvx_batch_v
   return cudaSuccess;
 }
 
-// The same for all contract instances at once, when the workspace holds all
-// their dense blocks: one persistent launch of the per-link kernel over the
-// Eq. (12) instances' items and the coupled groups write the blocks at the
-// instances' workspace offsets (d_inst_ws); then one contraction per model
-// and one fixed-order L per instance.
+// The same for all Eq. (12) instances at once, when the workspace holds all
+// their dense blocks: one persistent launch of the per-link kernel over their
+// items writes the blocks at the instances' workspace offsets (d_inst_ws);
+// then one contraction per model and one fixed-order L per instance.  The
+// coupled instances follow, one after another, by the reverse-mode adjoint in
+// the same workspace.
 cudaError_t launch_contract_batched(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, void* ws,
-                                    cudaStream_t st) {
+                                    size_t ws_bytes, cudaStream_t st) {
   const size_t el = p->prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
   auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
   char* base = (char*)ws;
@@ -564,23 +576,16 @@ cudaError_t launch_contract_batched(ciscvx_batch_plan* p, const ciscvx_batch_vjp
       e = cudaGetLastError();
     }
   }
-  for (const auto& g : p->cpl_groups) {
-    if (e != cudaSuccess) break;
-    const CplTab& T = *p->models[g.model]->cpl;
-    const size_t per = cpl_interval_bytes(T, g.nsub, p->prec);
-    const long chunk = (long)std::min<size_t>((size_t)g.count, p->cpl_ws_bytes / per);
-    e = launch_coupled(T, g.count, g.nsub, p->prec, p->layout, io->X, io->U, io->s, A, Bm, Bp, S, defect,
-                       penalty, p->d_cpl_ws, chunk, p->d_status, st, p->d_cpl_entries + g.first, p->d_inst_ws);
-  }
   for (const auto& bk : p->cbuckets) {
     if (e != cudaSuccess) break;
     e = launch_contract_batch(p->models[bk.model]->host, p->d_inst, p->d_inst_ws, p->d_centries + bk.first,
                               bk.count, p->prec, p->layout, A, Bm, Bp, S, io->w, io->rho, io->gX, io->gU,
                               io->gs, st);
   }
-  if (e == cudaSuccess && io->L)
+  if (e == cudaSuccess && io->L && !p->cinst.empty())
     e = launch_contract_L_batch(p->d_models, p->d_inst, p->d_inst_ws, p->d_cinst, (int)p->cinst.size(), defect,
                                 penalty, io->w, io->rho, io->L, st);
+  if (e == cudaSuccess && p->any_cpl) e = launch_contract_instances(p, io, ws, ws_bytes, st, true);
   return e;
 }
 
@@ -741,8 +746,10 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     I.contract = (M.aux || models[model_idx[i]]->cpl) ? 1 : 0;
     if (I.contract) {
       p->any_contract = true;
-      p->contract_ws = std::max(p->contract_ws, contract_bytes(M, models[model_idx[i]]->cpl,
-                                                               std::min<long>(N[i], 4096), n_sub[i], precision));
+      const CplTab* T = models[model_idx[i]]->cpl;
+      p->contract_ws = std::max(p->contract_ws,
+                                T ? cpl_adjoint_bytes(*T, std::min<long>(N[i], 4096), n_sub[i], precision)
+                                  : contract_bytes(M, nullptr, std::min<long>(N[i], 4096), n_sub[i], precision));
     } else {
       p->max_nsub_adj = std::max(p->max_nsub_adj, n_sub[i]);
     }
@@ -769,7 +776,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   std::vector<int2> centries;
   {
     for (int i = 0; i < n_inst; ++i) {
-      if (!p->inst[i].contract) continue;
+      // coupled instances run the reverse-mode adjoint (no dense blocks)
+      if (!p->inst[i].contract || models[p->inst[i].model]->cpl) continue;
       const DevModel& M = models[p->inst[i].model]->host;
       const size_t n = (size_t)p->inst[i].N;
       DevInst& W = inst_ws[i];
@@ -937,7 +945,7 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_bat
   if (e == cudaSuccess && p->any_contract) {
     char* cws = (char*)workspace + contract_ws_offset(p);
     const size_t have = ws_bytes - contract_ws_offset(p);
-    if (have >= p->cws_full) e = launch_contract_batched(p, io, cws, s);
+    if (have >= p->cws_full) e = launch_contract_batched(p, io, cws, have, s);
     else e = launch_contract_instances(p, io, cws, p->contract_ws, s);
   }
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch vjp launch: %s", cudaGetErrorString(e));

@@ -84,7 +84,7 @@ constexpr int A_PER_LINK = 10, A_PER_FOOT = 5, A_PER_CROSS = 7, B_CROSS_FIXED = 
 // into the packed arrays.
 struct DevInst {
   int model, N, nsub;
-  int contract;                   // 1: the VJP is linearize-and-contract (Eq. (12) state or coupled links)
+  int contract;                   // 1: the VJP runs outside the per-link adjoint kernel (coupled links: the coupled adjoint; Eq. (12) state: linearize-and-contract)
   long long x, u, s, a, b, v, p;  // element offsets: X/gX, U/gU, s/gs, A, Bm/Bp, S/defect/w, penalty/rho
   long long part, pb;             // VJP workspace offsets: per-input partials, per-(interval, link) partials
 };
