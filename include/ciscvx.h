@@ -301,10 +301,11 @@ ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* model, ciscvx
  *     trajectory in FP64 (one lane per interval, with the per-stage L D L^T
  *     solve of Eq. (3)), then one tangent column per thread in the
  *     precision's dtype.
+ *   For a model with coupled links or the Eq. (12) auxiliary state, z is
+ *   formed from the stored outputs by a post-pass.
  * Errors: EINVAL (nulls, N < 1, n_sub < 1, unknown layout/precision),
- * EUNSUPPORTED (tensor-core precisions; z for a model with coupled links),
- * EINVAL also for a missing or short workspace of such a model, ECUDA
- * (launch failure). */
+ * EUNSUPPORTED (tensor-core precisions), EINVAL also for a missing or short
+ * workspace of a model with coupled links, ECUDA (launch failure). */
 ciscvx_status ciscvx_discretize(const ciscvx_model* model, int N, int n_sub,
                                 ciscvx_precision precision, ciscvx_u_layout layout,
                                 const double* X, const double* U, const double* s, void* A,
@@ -315,7 +316,10 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* model, int N, int n_sub,
  * Bm/Bp [N][nnz_B] in the precision's dtype, values in ciscvx_model_pattern's
  * order; every other argument as for ciscvx_discretize.  The values are those
  * ciscvx_discretize stores at the pattern's positions (same arithmetic), and
- * no structural zero is written.  Errors: as ciscvx_discretize. */
+ * no structural zero is written.  For the Eq. (12) model z is formed by a
+ * post-pass over the compact values and the pattern by rows.  Errors: as
+ * ciscvx_discretize, and EUNSUPPORTED for a model with coupled links (its
+ * blocks have no sparse pattern to exploit in the coupled rows). */
 ciscvx_status ciscvx_discretize_compact(const ciscvx_model* model, int N, int n_sub,
                                         ciscvx_precision precision, ciscvx_u_layout layout,
                                         const double* X, const double* U, const double* s,
@@ -325,10 +329,14 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* model, int N, int n_
 /* Vector-Jacobian product of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k
  * (defect and penalty as above) with respect to X, U and s, by the discrete
  * adjoint of the RK4 substeps with the state checkpointed at every substep
- * start and the stages recomputed.  For a model with the Eq. (12) auxiliary
- * state (CISCVX_AUX_CROSS) or with coupled links, by linearize-and-contract
- * instead: per chunk of intervals the dense blocks are formed in the
- * workspace (as ciscvx_discretize computes them) and contracted,
+ * start and the stages recomputed.  For a model with coupled links (Eq. (3)
+ * elimination, RKF45, the sinusoidal surface; with either auxiliary model)
+ * by the reverse-mode adjoint of the coupled path: per chunk of intervals the
+ * FP64 nominal pass records its stage data in the workspace, then one thread
+ * per interval runs the transposed stage maps backward; no block is formed.
+ * For a per-link model with the Eq. (12) auxiliary state (CISCVX_AUX_CROSS)
+ * by linearize-and-contract: per chunk of intervals the dense blocks are
+ * formed in the workspace (as ciscvx_discretize computes them) and contracted,
  * dL/dx~_k = A_k^T lambda_k - rho_k (path-penalty rows) - w_{k-1},
  * dL/du = B-_k^T lambda_k / B+_k^T lambda_k (summed per node in the node
  * layout), dL/ds_k = S_k . lambda_k, lambda_k = w_k + rho_k on the

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 #include <new>
 #include <string>
 
@@ -379,14 +380,41 @@ ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** 
   }
   m->dev = nullptr;
   m->status = nullptr;
+  m->zpat = nullptr;
   cudaGetDevice(&m->device);
   cudaError_t e = cudaMalloc(&m->dev, sizeof(DevModel));
   if (e == cudaSuccess) e = cudaMalloc(&m->status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(unsigned));
+  if (e == cudaSuccess && m->host.aux && !m->cpl) {
+    // the compact pattern by rows, for z with compact outputs
+    const DevModel& M = m->host;
+    std::vector<int32_t> ar(M.nnzA), ac(M.nnzA), br(M.nnzB), bc(M.nnzB);
+    fill_pattern(M, ar.data(), ac.data(), br.data(), bc.data());
+    std::vector<int32_t> zp;
+    auto by_rows = [&](const std::vector<int32_t>& rr, const std::vector<int32_t>& cc) {
+      std::vector<int32_t> off(M.nxt + 1, 0);
+      for (int32_t r : rr) ++off[r + 1];
+      for (int r = 0; r < M.nxt; ++r) off[r + 1] += off[r];
+      std::vector<int32_t> ent(2 * rr.size());
+      std::vector<int32_t> pos(off.begin(), off.end() - 1);
+      for (size_t j = 0; j < rr.size(); ++j) {
+        const int32_t at = pos[rr[j]]++;
+        ent[2 * at] = (int32_t)j;
+        ent[2 * at + 1] = cc[j];
+      }
+      zp.insert(zp.end(), off.begin(), off.end());
+      zp.insert(zp.end(), ent.begin(), ent.end());
+    };
+    by_rows(ar, ac);
+    by_rows(br, bc);
+    e = cudaMalloc(&m->zpat, zp.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(m->zpat, zp.data(), zp.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     if (m->dev) cudaFree(m->dev);
     if (m->status) cudaFree(m->status);
+    if (m->zpat) cudaFree(m->zpat);
     delete m->cpl;
     delete m;
     return e == cudaErrorMemoryAllocation ? fail(CISCVX_ENOMEM, "device allocation failed")
@@ -398,6 +426,7 @@ ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** 
 
 void ciscvx_model_destroy(ciscvx_model* m) {
   if (!m) return;
+  if (m->zpat) cudaFree(m->zpat);
   if (m->dev) cudaFree(m->dev);
   if (m->status) cudaFree(m->status);
   delete m->cpl;
@@ -452,8 +481,9 @@ ciscvx_status ciscvx_workspace_size(const ciscvx_model* m, ciscvx_op op, int N,
   }
   else if (op == CISCVX_OP_VJP) {
     if (m->cpl || m->host.aux)
-      return fail(CISCVX_EUNSUPPORTED, "this model's VJP is linearize-and-contract, whose scratch depends on "
-                                       "n_sub and the precision: use ciscvx_discretize_workspace_size");
+      return fail(CISCVX_EUNSUPPORTED, "this model's VJP scratch (coupled-path adjoint or linearize-and-"
+                                       "contract) depends on n_sub and the precision: use "
+                                       "ciscvx_discretize_workspace_size");
     *bytes = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
   }
   else return fail(CISCVX_EINVAL, "unknown op %d", (int)op);
@@ -538,11 +568,15 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* m, int N, int n_sub,
   if (m->host.nnzB > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
   if (m->cpl) return fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for models with coupled links");
-  if (m->host.aux && z)
-    return fail(CISCVX_EUNSUPPORTED, "z with compact outputs is not provided for the Eq. (12) model");
+  // the Eq. (12) model's kernels do not form z: a post-pass over the compact
+  // outputs and the pattern by rows does
+  const bool post_z = m->host.aux && z;
   cudaError_t e = launch_discretize(m->dev, m->host.nb, N, n_sub, precision, layout, true, m->host.aux != 0, X,
-                                    U, s, A, Bm, Bp, S, defect, penalty, z, m->status,
+                                    U, s, A, Bm, Bp, S, defect, penalty, post_z ? nullptr : z, m->status,
                                     (cudaStream_t)stream);
+  if (e == cudaSuccess && post_z)
+    e = launch_affine_z_compact(m->host, N, precision, layout, X, U, s, A, Bm, Bp, S, defect, m->zpat, z,
+                                (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "discretize launch");
   return ok();
 }

@@ -240,6 +240,9 @@ struct ciscvx_model {
   ciscvx::CplTab* cpl;    // coupled-path tables (host), or null for per-link models
   unsigned* status;       // device status word
   int device;             // CUDA device the tables live on
+  // Eq. (12) model: the compact pattern by rows (device), for z with compact
+  // outputs: A rows [nxt + 1] offsets, then (entry, column) pairs; the same for B
+  int32_t* zpat;
 };
 
 // Launchers (defined in disc.cu / vjp.cu), called by the host API in api.cu.
@@ -272,6 +275,11 @@ void model_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int
 cudaError_t launch_affine_z(const DevModel& M, int N, int prec, int layout, const double* X, const double* U,
                             const double* s, const void* A, const void* Bm, const void* Bp, const void* S,
                             const double* defect, double* z, cudaStream_t st);
+// The same from compact outputs, with the pattern by rows (ciscvx_model::zpat).
+cudaError_t launch_affine_z_compact(const DevModel& M, int N, int prec, int layout, const double* X,
+                                    const double* U, const double* s, const void* A, const void* Bm,
+                                    const void* Bp, const void* S, const double* defect, const int32_t* zpat,
+                                    double* z, cudaStream_t st);
 // Psi^{delta,eps} rows per interval, and its launcher (psi.cu).
 int psi_rows(const DevModel& M);
 cudaError_t launch_psi(const DevModel& M, int N, const double* Xp, const double* Xm, double delta,

@@ -1,9 +1,8 @@
 """GPU parity of the full Eq. (12) auxiliary state (CISCVX_AUX_CROSS) against
 the FP64 oracle through the C ABI: single-instance and batched linearization,
 both precisions and both control layouts, mixed batches of the two auxiliary
-models, feasible inputs, the linearize-and-contract VJP, and the entry points
-that return EUNSUPPORTED for it (z with compact outputs), and the affine term z
-formed from the dense outputs.
+models, feasible inputs, the linearize-and-contract VJP, and the affine term
+z formed from the dense and from the compact outputs.
 Tolerances as for the default model (FP64 1e-10; FP32-Phi blocks 1e-4,
 defect and penalty 1e-10)."""
 import numpy as np
@@ -126,17 +125,35 @@ def test_cross_batch_mixed_models(env, precision):
         _check(got, ref, precision)
 
 
-def test_cross_unsupported_entry_points(env):
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("layout", ["node", "interval"])
+def test_cross_affine_term_with_compact_outputs(env, precision, tol, layout):
+    """z with compact outputs (a post-pass over the structural nonzeros by
+    rows) equals z from the oracle's blocks, and the compact values equal the
+    dense outputs at the pattern's positions."""
     torch, oracle, api = env
     dev = torch.device("cuda:0")
-    p = _problem("hopper", 15, 10, 4)
+    p = _problem("biped", 15, 41, 3)
     m = api.Model(p.robot)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
-    X, U, s = t(p.X), t(p.U), t(p.s)
-    # compact outputs are provided (tests/test_gpu_compact.py); z with them is not
-    with pytest.raises(api.CiscvxError) as e:
-        api.discretize_compact(m, X, U, s, p.n_sub, "fp64", want_z=True)
-    assert e.value.status == api.EUNSUPPORTED
+    U = p.U if layout == "node" else p.U_interval()
+    got = api.discretize_compact(m, t(p.X), t(U), t(p.s), p.n_sub, precision, layout, want_z=True)
+    dense = api.discretize(m, t(p.X), t(U), t(p.s), p.n_sub, precision, layout, want_z=True)
+    api.sync_status(m)
+    ref = oracle.discretize(p.robot.as_dict(), p.X, U, p.s, p.n_sub, layout=layout)
+    uL = U[:-1] if layout == "node" else U[:, 0]
+    uR = U[1:] if layout == "node" else U[:, 1]
+    z = ref["defect"] + p.X[1:] - np.einsum("kij,kj->ki", ref["A"], p.X[:-1]) \
+        - np.einsum("kij,kj->ki", ref["Bm"], uL) - np.einsum("kij,kj->ki", ref["Bp"], uR) \
+        - ref["S"] * p.s[:, None]
+    zg = got["z"].cpu().numpy()
+    for k in range(p.N):
+        assert block_err(zg[k], z[k]) <= tol, k
+    # same blocks in both formats, hence the same z up to the summation order
+    assert block_err(zg, dense["z"].cpu().numpy()) <= 1e-12
+    ar, ac, br, bc = m.pattern()
+    Ad = dense["A"].double().cpu().numpy()
+    assert np.array_equal(got["A"].double().cpu().numpy(), Ad[:, ar, ac])
 
 
 def test_cross_node_constraints(env):
