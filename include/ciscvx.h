@@ -192,10 +192,11 @@ typedef struct ciscvx_model ciscvx_model;
  * it is linearized by ciscvx_discretize (dense outputs, z formed from them, a
  * workspace from ciscvx_discretize_workspace_size) or in a batch plan
  * (ciscvx_batch_discretize, dense outputs; the plan groups its instances by
- * n_sub and owns their stage-data workspace), and its VJP by
- * linearize-and-contract (single instance, and in batch plans, where the
- * fused pass runs the linearization and the VJP as two calls).  Its compact
- * outputs and the host executor return CISCVX_EUNSUPPORTED.  *out receives an opaque
+ * n_sub and owns their stage-data workspace, and its host executor takes
+ * them per instance), and its VJP by the coupled path's reverse-mode adjoint
+ * (single instance, and in batch plans, where the fused pass runs the
+ * linearization and the VJP as two calls).  Its compact outputs return
+ * CISCVX_EUNSUPPORTED.  *out receives an opaque
  * handle owned by the caller (free with ciscvx_model_destroy).  Errors:
  * EINVAL (null, counts < 0, n_bodies < 1, bad indices, non-positive mass or
  * inertia, parent == child, non-finite values), EUNSUPPORTED (limits above,
@@ -515,11 +516,15 @@ ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* plan, const ciscvx_batch_
  *   host_vjp / dev_vjp: NULL, or the VJP cotangents (w, rho: host inputs) and
  *     gradients (gX, gU, gs, L: host outputs) with their device buffers; their
  *     X, U, s fields are ignored (host/dev are used).  workspace as for
- *     ciscvx_batch_discretize_vjp.
+ *     ciscvx_batch_discretize_vjp (with coupled-link instances at least the
+ *     minimum of ciscvx_batch_vjp_workspace_sizes).
+ * Coupled-link instances are linearized one after another within their
+ * chunk (and their VJP taken by the coupled path's reverse-mode adjoint).
  * The first call with a new n_chunks builds the chunked work tables and
  * streams (device allocation); later calls with the same n_chunks allocate
  * nothing.  Errors: EINVAL (null buffers, n_chunks outside [1, n_inst], short
- * workspace), EUNSUPPORTED (VJP with n_sub > CISCVX_MAX_VJP_SUBSTEPS), ECUDA. */
+ * workspace), EUNSUPPORTED (VJP with n_sub > CISCVX_MAX_VJP_SUBSTEPS; VJP of
+ * a plan with per-link Eq. (12) instances), ECUDA. */
 ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
                                     const ciscvx_batch_io* host, const ciscvx_batch_io* dev,
                                     const ciscvx_batch_vjp_io* host_vjp,

@@ -1165,6 +1165,38 @@ cudaError_t ensure_chunks(ciscvx_batch_plan* p, int K) {
   return cudaSuccess;
 }
 
+// The coupled-link instances of [i0, i1) one after another (host executor):
+// the linearization into the device outputs at each instance's offsets
+// (stage data in the plan's coupled workspace) and, with `vjp`, the
+// reverse-mode adjoint into the VJP outputs (its scratch in `ws`).
+cudaError_t run_coupled_range(ciscvx_batch_plan* p, const ciscvx_batch_io* io, const ciscvx_batch_vjp_io* vjp,
+                              void* ws, size_t ws_bytes, int i0, int i1, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int i = i0; i < i1 && e == cudaSuccess; ++i) {
+    const DevInst& I = p->inst[i];
+    const ciscvx_model* m = p->models[I.model];
+    if (!m->cpl) continue;
+    const CplTab& T = *m->cpl;
+    const bool nu = T.nu > 0, nc = T.nc > 0;
+    const size_t el = p->prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+    const long chunk = std::max<long>(1, (long)std::min<size_t>((size_t)I.N, p->cpl_ws_bytes /
+                                                                 cpl_interval_bytes(T, I.nsub, p->prec)));
+    char* A = (char*)io->A + I.a * el;
+    char* Bm = nu ? (char*)io->Bm + I.b * el : nullptr;
+    char* Bp = nu ? (char*)io->Bp + I.b * el : nullptr;
+    char* S = (char*)io->S + I.v * el;
+    e = launch_coupled(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr, io->s + I.s,
+                       A, Bm, Bp, S, io->defect + I.v, nc ? io->penalty + I.p : nullptr, p->d_cpl_ws, chunk,
+                       p->d_status, st);
+    if (e == cudaSuccess && vjp)
+      e = launch_coupled_vjp(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
+                             io->s + I.s, vjp->w + I.v, nc ? vjp->rho + I.p : nullptr, vjp->gX + I.x,
+                             nu ? vjp->gU + I.u : nullptr, vjp->gs + I.s, vjp->L ? vjp->L + i : nullptr, ws,
+                             ws_bytes, p->d_status, st);
+  }
+  return e;
+}
+
 cudaError_t copy_range(void* dst, const void* src, size_t elem, size_t lo, size_t hi,
                        cudaMemcpyKind kind, cudaStream_t st) {
   if (hi <= lo || !dst || !src) return cudaSuccess;
@@ -1182,9 +1214,6 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
                                     size_t ws_bytes, void* stream) {
   ciscvx_status st = check_io(p, dev);
   if (st != CISCVX_OK) return st;
-  if (p->any_cpl)
-    return set_error(CISCVX_EUNSUPPORTED, "the host executor is not provided for plans with coupled-link "
-                                          "models (use ciscvx_batch_discretize)");
   if (!host || !host->X || !host->s || !host->A || !host->S || !host->defect)
     return set_error(CISCVX_EINVAL, "null required host buffer");
   if (!p->all_nu0 && (!host->U || !host->Bm || !host->Bp)) return set_error(CISCVX_EINVAL, "null host U / Bm / Bp");
@@ -1202,7 +1231,9 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
     if (p->max_nsub > MAXSUB_VJP)
       return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps", MAXSUB_VJP);
     if (p->any_aux) return set_error(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
-    const size_t need = sizeof(double) * (p->part_total + 2 * p->pb_total);
+    // the adjoint's partial sums; with coupled instances also their adjoint's scratch
+    const size_t need = p->any_cpl ? contract_ws_offset(p) + p->contract_ws
+                                   : sizeof(double) * (p->part_total + 2 * p->pb_total);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 15) != 0)
       return set_error(CISCVX_EINVAL, "16-byte aligned workspace of %zu bytes needed", need);
     part = (double*)workspace;
@@ -1242,6 +1273,9 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
     if (e == cudaSuccess) {
       if (vjp) e = launch_fused_c(p, common_chunk(p, 0, c, p->tune_fused), dev, &dv, part, ps, pL, i0, i1, t.s_comp);
       else e = launch_disc_c(p, common_chunk(p, 0, c, p->tune), dev, t.s_comp);
+      if (e == cudaSuccess && p->any_cpl)
+        e = run_coupled_range(p, dev, vjp ? &dv : nullptr, vjp ? (char*)workspace + contract_ws_offset(p) : nullptr,
+                              vjp ? ws_bytes - contract_ws_offset(p) : 0, i0, i1, t.s_comp);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_comp, t.s_comp);
     // device -> host: this chunk's outputs

@@ -405,6 +405,66 @@ def test_batch_plan_with_coupled_models(env, precision):
         assert torch.equal(out[k], out2[k]), k
 
 
+@pytest.mark.parametrize("n_chunks", [1, 3])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_host_executor_with_coupled_models(env, precision, n_chunks):
+    """ciscvx_batch_run_host on a plan mixing per-link and coupled-link models
+    (linearization, and linearization + VJP): every output equals the device
+    path's to rounding (the executor regroups which intervals share a warp,
+    and warps vote on the angle chain's Taylor tier), and the coupled VJPs
+    meet the oracle."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(40)
+    robots = [synth.cheetah7(rng), synth.with_paper_dynamics(synth.biped(rng), **PAPER)]
+    probs, midx = [], []
+    for i in range(7):
+        mi = i % 2
+        probs.append(synth.draw_instance(robots[mi], rng, int(rng.integers(5, 50)), 3, q_noise=0.1,
+                                         u_dist="normal", s_range=(0.05, 0.15), with_cotangents=True))
+        midx.append(mi)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [q.N for q in probs], [q.n_sub for q in probs], precision=precision)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X = t(plan.pack([q.X for q in probs], "X"))
+    U = t(plan.pack([q.U for q in probs], "U"))
+    sv = t(plan.pack([q.s for q in probs], "s"))
+    w = t(plan.pack([q.w for q in probs], "defect"))
+    rho = t(plan.pack([q.rho for q in probs], "penalty"))
+    ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=dev)
+    ref = plan.discretize(X, U, sv)
+    gref = plan.discretize_vjp(X, U, sv, w, rho, workspace=ws)
+    torch.cuda.synchronize()
+    pin = lambda a: a.cpu().pin_memory()  # noqa: E731
+    host_in = {"X": pin(X), "U": pin(U), "s": pin(sv)}
+    dev_in = {k: torch.empty_like(v) for k, v in (("X", X), ("U", U), ("s", sv))}
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ref.items()}
+    dev_out = {k: torch.empty_like(v) for k, v in ref.items()}
+    host_vjp = {"w": pin(w), "rho": pin(rho)}
+    host_vjp.update({k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in gref.items()})
+    dev_vjp = {"w": torch.empty_like(w), "rho": torch.empty_like(rho)}
+    dev_vjp.update({k: torch.empty_like(v) for k, v in gref.items()})
+    for with_vjp in (False, True):
+        plan.run_host(host_in, host_out, dev_in, dev_out, n_chunks=n_chunks,
+                      host_vjp=host_vjp if with_vjp else None, dev_vjp=dev_vjp if with_vjp else None,
+                      workspace=ws)
+        torch.cuda.current_stream().synchronize()
+        plan.sync_status()
+        for k, v in ref.items():
+            tol = 1e-6 if v.dtype == torch.float32 else 1e-12
+            assert block_err(host_out[k].double().numpy(), v.double().cpu().numpy()) <= tol, k
+        if with_vjp:
+            for k, v in gref.items():
+                assert block_err(host_vjp[k].numpy(), v.cpu().numpy()) <= 1e-12, k
+            tol = TOL_FP64 if precision == "fp64" else TOL_FP32_PHI
+            gX = host_vjp["gX"].numpy()
+            for i, q in enumerate(probs):
+                if midx[i] != 1:
+                    continue
+                rX, rU, rs, rL = oracle.vjp(q.robot.as_dict(), q.X, q.U, q.s, q.w, q.rho, q.n_sub)
+                assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= tol, i
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
 @pytest.mark.parametrize("layout", ["node", "interval"])
 def test_affine_term(env, precision, tol, layout):
