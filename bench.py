@@ -608,7 +608,7 @@ def run_ours(args):
                          "chunks": -(-hi // ws.numel()), "workspace_bytes": ws.numel()}
             del out, ws
             torch.cuda.empty_cache()
-            # the VJP of the same workload (dense blocks per chunk, then A^T lambda, B^T lambda, S . lambda)
+            # the VJP of the same workload (reverse-mode adjoint of the coupled path)
             wv = torch.randn((pp.N, mp.nxt), dtype=torch.float64, device=dev)
             rv = torch.full((pp.N, mp.nc), 10.0, dtype=torch.float64, device=dev)
             lo, hi = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr, api.OP_VJP)
@@ -621,6 +621,39 @@ def run_ours(args):
             tv, = max_over_ranks([tv])
             paper[pr]["vjp"] = {"value": pp.N * world * max(1, args.steps // 2) / tv,
                                 "ms_per_call": tv / max(1, args.steps // 2) * 1e3}
+            if pr == "fp32_phi" and not args.no_e2e:
+                # end to end through the public API: pinned host inputs copied in,
+                # linearization and VJP, every output copied back
+                hin = {k: v.cpu().pin_memory() for k, v in (("X", Xp), ("U", Up), ("s", sp), ("w", wv), ("rho", rv))}
+                lo2, hi2 = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr)
+                wsd = torch.empty(max(lo2, min(hi2, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+                din = {k: torch.empty_like(v, device=dev) for k, v in hin.items()}
+                res = {}
+
+                def e2e_step():
+                    for k, v in hin.items():
+                        din[k].copy_(v, non_blocking=True)
+                    o = api.discretize(mp, din["X"], din["U"], din["s"], pp.n_sub, pr, workspace=wsd,
+                                       out=res.get("out"))
+                    res["out"] = o
+                    g = api.discretize_vjp(mp, din["X"], din["U"], din["s"], din["w"], din["rho"], pp.n_sub, pr,
+                                           workspace=ws)
+                    if "host" not in res:
+                        res["host"] = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                                       for k, v in list(o.items()) + list(zip(("gX", "gU", "gs", "L"), g))}
+                    for k, v in list(o.items()) + list(zip(("gX", "gU", "gs", "L"), g)):
+                        res["host"][k].copy_(v, non_blocking=True)
+
+                e2e_step()
+                torch.cuda.synchronize()
+                te = time_steps(torch, e2e_step, max(1, args.steps // 2), 1, stream, name="paper dynamics: end to end")
+                te, = max_over_ranks([te])
+                h2d = sum(v.numel() * v.element_size() for v in hin.values())
+                d2h = sum(v.numel() * v.element_size() for v in res["host"].values())
+                paper[pr]["e2e"] = {"value": pp.N * world * max(1, args.steps // 2) / te, "unit": "intervals/s",
+                                    "what": "linearization + VJP per interval, host buffers",
+                                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                del hin, din, res, wsd
             del ws, wv, rv
             torch.cuda.empty_cache()
         del Xp, Up, sp, mp
@@ -629,6 +662,47 @@ def run_ours(args):
 
         L2_FLUSH = saved
         return paper
+
+    def measure_psi(robot, n_iv):
+        """Psi^{delta,eps} and its Jacobian (FP64) on n_iv intervals of seeded node states."""
+        rx = synth.with_cross_states(robot)
+        mp = api.Model(rx)
+        npsi, ny = api.psi_rows(mp), mp.ny
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(4321)
+        Xp = torch.rand((n_iv + 1, mp.nxt), generator=gen, device=dev, dtype=torch.float64)
+        Xm = torch.rand((n_iv + 1, mp.nxt), generator=gen, device=dev, dtype=torch.float64)
+        po = api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4)
+        barrier()
+        tp = time_steps(torch, lambda: api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4, out=po), args.steps,
+                        args.warmup, stream, name="Psi")
+        barrier()
+        api.sync_status(mp)
+        tp, = max_over_ranks([tp])
+        # algorithmic bytes per interval: y+ and y- read, Psi and its Jacobian written
+        bpi = 8 * (2 * ny + npsi * (1 + ny))
+        out = {"metric": "linearized intervals/s (Psi^{delta,eps}, Eq. (12) auxiliary state, FP64)",
+               "value": n_iv * world * args.steps / tp, "unit": "intervals/s",
+               "intervals_per_gpu": n_iv, "robot": rx.name, "n_psi": npsi, "n_y": ny,
+               "ms_per_call": tp / args.steps * 1e3, "bytes_per_interval": bpi,
+               "achieved_gbs": bpi * n_iv * args.steps / tp / 1e9}
+        out["hbm_frac_of_measured"] = out["achieved_gbs"] / HBM_GBS if HBM_GBS else None
+        del Xp, Xm, po, mp
+        torch.cuda.empty_cache()
+        return out
+
+    if args.psi_only:
+        rng = np.random.default_rng(rank)
+        psi = measure_psi(synth.cheetah7(rng), args.psi_intervals)
+        if rank == 0:
+            print(json.dumps({
+                "metric": psi["metric"], "value": psi["value"], "unit": "intervals/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": psi["ms_per_call"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded node states)",
+                "config": {"workload": f"Psi, 7-link chain with the Eq. (12) state, {args.psi_intervals} intervals"},
+                "psi": psi}))
+        return
 
     if args.paper_only:
         paper = measure_paper()
@@ -754,30 +828,7 @@ def run_ours(args):
     psi = None
     if spec["kind"] == "batch" and not args.no_nodes:
         wl.free(prec)
-        rx = synth.with_cross_states(wl.batch.robots[0])
-        mp = api.Model(rx)
-        npsi, ny = api.psi_rows(mp), mp.ny
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(4321)
-        Xp = torch.rand((wl.intervals + 1, mp.nxt), generator=gen, device=dev, dtype=torch.float64)
-        Xm = torch.rand((wl.intervals + 1, mp.nxt), generator=gen, device=dev, dtype=torch.float64)
-        po = api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4)
-        barrier()
-        tp = time_steps(torch, lambda: api.psi_linearize(mp, Xp, Xm, 1e-2, 1e-4, out=po), args.steps,
-                        args.warmup, stream, name="Psi")
-        barrier()
-        api.sync_status(mp)
-        tp, = max_over_ranks([tp])
-        # algorithmic bytes per interval: y+ and y- read, Psi and its Jacobian written
-        bpi = 8 * (2 * ny + npsi * (1 + ny))
-        psi = {"metric": "linearized intervals/s (Psi^{delta,eps}, Eq. (12) auxiliary state, FP64)",
-               "value": wl.intervals * world * args.steps / tp, "unit": "intervals/s",
-               "intervals_per_gpu": wl.intervals, "robot": rx.name, "n_psi": npsi, "n_y": ny,
-               "ms_per_call": tp / args.steps * 1e3, "bytes_per_interval": bpi,
-               "achieved_gbs": bpi * wl.intervals * args.steps / tp / 1e9}
-        psi["hbm_frac_of_measured"] = psi["achieved_gbs"] / HBM_GBS if HBM_GBS else None
-        del Xp, Xm, po, mp
-        torch.cuda.empty_cache()
+        psi = measure_psi(wl.batch.robots[0], wl.intervals)
 
     # the SOCP canonicalization of the batch's instances (one shape)
     socp = None
@@ -955,6 +1006,9 @@ def main():
     ap.add_argument("--paper-intervals", type=int, default=65536,
                     help="intervals of the paper-dynamics instance")
     ap.add_argument("--paper-precision", default="both", choices=["both", "fp32_phi", "fp64"])
+    ap.add_argument("--psi-only", action="store_true",
+                    help="run only the Psi^{delta,eps} measurement (its own JSON line)")
+    ap.add_argument("--psi-intervals", type=int, default=1 << 20, help="intervals of the Psi-only measurement")
     ap.add_argument("--cross", action="store_true",
                     help="also time the linearization with the full Eq. (12) auxiliary state")
     args = ap.parse_args()

@@ -1048,14 +1048,20 @@ __global__ void k_cpl_adjoint_u(int nu, long i0, long n, int layout, const doubl
   }
 }
 
-// L over a chunk: one block, a fixed order (deterministic), added to *L.
+// L over a chunk in two fixed-order passes (deterministic): block b sums a
+// contiguous range of w . defect + rho . penalty into part[b], then one block
+// adds the partial sums in order to *L.
+constexpr int ADJ_LRED_BLOCKS = 512;
+
 __global__ void k_cpl_adjoint_L(int nxt, int nc, long i0, long n, const double* __restrict__ defect,
                                 const double* __restrict__ penalty, const double* __restrict__ w,
-                                const double* __restrict__ rho, double* L) {
+                                const double* __restrict__ rho, double* __restrict__ part) {
   __shared__ double red[256];
-  double acc = 0.0;
   const long tot = n * (nxt + nc);
-  for (long e = threadIdx.x; e < tot; e += blockDim.x) {
+  const long per = (tot + gridDim.x - 1) / gridDim.x;
+  const long lo = (long)blockIdx.x * per, hi = lo + per < tot ? lo + per : tot;
+  double acc = 0.0;
+  for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
     if (e < n * nxt) acc = fma(w[i0 * nxt + e], defect[e], acc);
     else {
       const long f = e - n * nxt;
@@ -1068,7 +1074,14 @@ __global__ void k_cpl_adjoint_L(int nxt, int nc, long i0, long n, const double* 
     if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *L += red[0];
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_cpl_adjoint_L_sum(const double* __restrict__ part, int nblk, double* L) {
+  if (threadIdx.x != 0) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += part[b];
+  *L += acc;
 }
 
 // Adjoint block size: the largest of 128 / 64 / 32 threads whose cotangent
@@ -1137,7 +1150,13 @@ cudaError_t run_vjp(const CplTab& T, long N, int nsub, int layout, const double*
     }
     if (nu > 0)
       k_cpl_adjoint_u<<<(unsigned)((n * nu + 127) / 128), 128, 0, st>>>(nu, i0, n, layout, ubar, gU);
-    if (L) k_cpl_adjoint_L<<<1, 256, 0, st>>>(nxt, T.nc, i0, n, defect, penalty, w, rho, L);
+    if (L) {
+      const long tot = n * (nxt + T.nc);
+      const int nblk = (int)std::min<long>(ADJ_LRED_BLOCKS, (tot + 2047) / 2048);
+      double* part = (double*)(base + Ly.lpart);
+      k_cpl_adjoint_L<<<nblk, 256, 0, st>>>(nxt, T.nc, i0, n, defect, penalty, w, rho, part);
+      k_cpl_adjoint_L_sum<<<1, 32, 0, st>>>(part, nblk, L);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1316,7 +1335,8 @@ CplAdjLayout cpl_adjoint_layout(const CplTab& T, long n, int nsub, int prec) {
   Ly.defect = al(Ly.stage + (size_t)n * cpl_interval_bytes(T, nsub, prec));
   Ly.penalty = al(Ly.defect + (size_t)n * T.nxt * sizeof(double));
   Ly.ubar = al(Ly.penalty + (size_t)n * (T.nc > 0 ? T.nc : 1) * sizeof(double));
-  Ly.total = al(Ly.ubar + (size_t)n * 2 * (T.nu > 0 ? T.nu : 1) * sizeof(double));
+  Ly.lpart = al(Ly.ubar + (size_t)n * 2 * (T.nu > 0 ? T.nu : 1) * sizeof(double));
+  Ly.total = al(Ly.lpart + ADJ_LRED_BLOCKS * sizeof(double));
   return Ly;
 }
 

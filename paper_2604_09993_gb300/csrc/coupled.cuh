@@ -125,7 +125,7 @@ cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, 
 // of a chunk of n intervals: stage data, defects, penalty increments and the
 // per-interval input cotangents (dL/du_L, dL/du_R).
 struct CplAdjLayout {
-  size_t stage, defect, penalty, ubar, total;
+  size_t stage, defect, penalty, ubar, lpart, total;
 };
 CplAdjLayout cpl_adjoint_layout(const CplTab& T, long n, int nsub, int prec);
 size_t cpl_adjoint_bytes(const CplTab& T, long n, int nsub, int prec);
