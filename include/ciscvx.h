@@ -390,6 +390,14 @@ typedef struct {
   int occupancy;      /* register cap of the kernels: 0 none (8 warps/SM), 1 <= 168 registers
                          (12 warps/SM), 2 <= 128 registers (16 warps/SM); 1 and 2 need
                          warps_per_cta <= 4 */
+  int split;          /* fused linearization + VJP only (ciscvx_batch_discretize_and_vjp):
+                         0 one warp per work item takes the linearization and the adjoint in
+                         turn, sharing the integrated trajectory; 1 the linearization and the
+                         adjoint of each item run on two warps of the same launch, each
+                         integrating the trajectory itself (more work, but half the path per
+                         warp: for batches too small to fill the GPU, where one warp's
+                         instruction stream sets the time).  1 needs occupancy 0.  The other
+                         entry points ignore it. */
 } ciscvx_tune;
 
 /* Element counts of the packed buffers (or, from ciscvx_batch_offsets, the
@@ -488,7 +496,9 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_
  * those of the two calls (io's A..penalty; vjp's gX, gU, gs, L), equal to
  * them to rounding.  vjp->X, U, s are ignored (io's inputs are used).
  * workspace as for ciscvx_batch_discretize_vjp.  Launched directly (no graph).
- * Errors: as the two calls. */
+ * With the fused tune's split = 1 (small batches) the two run on separate
+ * warps of the same launch, each integrating the trajectory, as the two calls
+ * would.  Errors: as the two calls. */
 ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
                                               const ciscvx_batch_vjp_io* vjp, void* workspace,
                                               size_t ws_bytes, void* stream);
@@ -533,8 +543,11 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
 
 /* As ciscvx_batch_autotune, for the fused pass of ciscvx_batch_discretize_and_vjp
  * (its launch shape is kept apart from the discretization's: the fused kernel
- * holds more state per thread).  Overwrites the outputs; workspace as for
- * ciscvx_batch_discretize_vjp.  Errors: as ciscvx_batch_discretize_and_vjp. */
+ * holds more state per thread).  When the fused pass would run at most one
+ * warp per scheduler (work items <= 4 x SMs), the split form (tune.split = 1,
+ * one warp per item, 1, 2 or 4 warps per CTA) is among the candidates.
+ * Overwrites the outputs; workspace as for ciscvx_batch_discretize_vjp.
+ * Errors: as ciscvx_batch_discretize_and_vjp. */
 ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
                                           const ciscvx_batch_vjp_io* vjp, void* workspace,
                                           size_t ws_bytes, void* stream, ciscvx_tune* chosen);

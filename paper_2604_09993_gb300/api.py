@@ -42,7 +42,8 @@ FORMAT = {"dense": 0, "compact": 1}
 
 class Tune(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("lpt_order", ctypes.c_int), ("use_graph", ctypes.c_int), ("occupancy", ctypes.c_int)]
+                ("lpt_order", ctypes.c_int), ("use_graph", ctypes.c_int), ("occupancy", ctypes.c_int),
+                ("split", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

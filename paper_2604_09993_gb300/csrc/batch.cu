@@ -37,42 +37,11 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCo
                                                     const double* __restrict__ s, TP* A, TP* Bm,
                                                     TP* Bp, TP* S, double* defect,
                                                     double* penalty) {
-  const int lane = threadIdx.x & 31;
   int iter = 0;
   for (;;) {
     const int item = next_item(c, iter);
     if (item >= c.n_items) break;
-    const int2 it = c.items[item];
-    const int4 g = c.groups[it.x];
-    if (lane < g.w) {
-      const DevModel& M = *c.models[g.x];
-      const int b = it.y;
-      const int2 e = c.entries[g.z + lane];
-      const DevInst& I = c.inst[e.x];
-      const long k = e.y;
-      const int nxt = M.nxt, nu = M.nu, nc = M.nc;
-      const double* Xi = X + I.x;
-      const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
-      const double* uR = uL + nu;
-      const size_t sa = CMP ? (size_t)M.nnzA : (size_t)nxt * nxt;
-      const size_t sb = CMP ? (size_t)M.nnzB : (size_t)nxt * nu;
-      TP* Ak = A + I.a + k * sa;
-      TP* Bmk = Bm ? Bm + I.b + k * sb : nullptr;
-      TP* Bpk = Bp ? Bp + I.b + k * sb : nullptr;
-      TP* Sk = S + I.v + (size_t)k * nxt;
-      double* dk = defect + I.v + (size_t)k * nxt;
-      double* pk = penalty ? penalty + I.p + (size_t)k * nc : nullptr;
-      if (AUX && M.aux && M.body[b].contact >= 0)  // Eq. (12) model
-        disc_link<TP, true, CMP, false, AUX>(M, b, g.y, s[I.s + k], Xi + k * nxt,
-                                               Xi + (k + 1) * nxt, uL, uR, Ak, Bmk, Bpk, Sk, dk,
-                                               pk, nullptr, c.status);
-      else if (M.body[b].contact >= 0)
-        disc_link<TP, true, CMP>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
-                                 Ak, Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
-      else
-        disc_link<TP, false, CMP>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
-                                  Ak, Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
-    }
+    disc_item<TP, CMP, AUX>(c, item, X, U, s, A, Bm, Bp, S, defect, penalty);
   }
 }
 
@@ -83,41 +52,11 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_vjp(BatchCom
                                                    const double* __restrict__ w,
                                                    const double* __restrict__ rho, double* gX,
                                                    double* part, double* ps, double* pL) {
-  const int lane = threadIdx.x & 31;
   int iter = 0;
   for (;;) {
     const int item = next_item(c, iter);
     if (item >= c.n_items) break;
-    const int2 it = c.items[item];
-    const int4 g = c.groups[it.x];
-    if (lane < g.w) {
-      const DevModel& M = *c.models[g.x];
-      const int b = it.y;
-      const int2 e = c.entries[g.z + lane];
-      const DevInst& I = c.inst[e.x];
-      const long k = e.y;
-      const int N = I.N, nxt = M.nxt, nu = M.nu, nc = M.nc, nb = M.nb;
-      const double* Xi = X + I.x;
-      const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
-      const double* uR = uL + nu;
-      const double* wi = w + I.v;
-      const DevBody& B = M.body[b];
-      const double rc = (B.contact >= 0) ? rho[I.p + k * nc + B.contact] : 0.0;
-      const double* wkm1 = (k > 0) ? wi + (k - 1) * nxt : nullptr;
-      double* gXi = gX + I.x;
-      double* gXN = (k == N - 1) ? gXi + (size_t)N * nxt : nullptr;
-      double* pp = part + I.part + (size_t)k * M.nslot * 2;
-      double* psk = ps + I.pb + k * nb;
-      double* pLk = pL + I.pb + k * nb;
-      if (B.contact >= 0)
-        vjp_link<TP, true>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
-                           wi + k * nxt, wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk,
-                           c.status);
-      else
-        vjp_link<TP, false>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
-                            wi + k * nxt, wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk,
-                            c.status);
-    }
+    vjp_item<TP>(c, item, X, U, s, w, rho, gX, part, ps, pL);
   }
 }
 
@@ -245,7 +184,7 @@ struct ciscvx_batch_plan {
   int* d_queue = nullptr;  // [0]: discretize, [1]: vjp
   unsigned* d_status = nullptr;
   ciscvx_tune tune{4, 2, 1, 1, 0};
-  ciscvx_tune tune_fused{4, 2, 1, 0, 0};  // launch shape of the fused discretize+VJP pass
+  ciscvx_tune tune_fused{4, 2, 1, 0, 0, 0};  // launch shape of the fused discretize+VJP pass
   ChunkTables chunks;  // tables of the last chunk count used by ciscvx_batch_run_host
   // graph cache
   cudaStream_t cap = nullptr;
@@ -263,7 +202,7 @@ bool tune_ok(const ciscvx_tune& t) {
   return (t.warps_per_cta == 1 || t.warps_per_cta == 2 || t.warps_per_cta == 4 ||
           t.warps_per_cta == 8) &&
          t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && t.occupancy >= 0 && t.occupancy <= 2 &&
-         (t.occupancy == 0 || t.warps_per_cta <= 4);
+         (t.occupancy == 0 || t.warps_per_cta <= 4) && (t.split == 0 || (t.split == 1 && t.occupancy == 0));
 }
 
 void free_chunks(ChunkTables& t) {
@@ -598,6 +537,19 @@ cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const cis
   if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   unsigned blocks, threads;
+  if (p->tune_fused.split) {  // linearization and adjoint of each item on two warps
+    BatchCommon cs = c;
+    cs.n_items = 2 * c.n_items;
+    grid_for(p, p->tune_fused, cs.n_items, blocks, threads);
+    e = launch_disc_vjp_split(cs, c.n_items, p->prec, p->compact, blocks, threads, io->X, io->U,
+                              io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty, vio->w,
+                              vio->rho, vio->gX, part, ps, pL, s);
+    if (e == cudaSuccess && i1 > i0)
+      k_batch_vjp_finish<<<i1 - i0, FINB, 0, s>>>(p->d_models, p->d_inst + i0, p->layout, part, ps,
+                                                  pL, vio->gU, vio->gs, vio->L ? vio->L + i0 : nullptr);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+  }
   grid_for(p, p->tune_fused, c.n_items, blocks, threads);
   // FP32 pass: the checkpoints (4 FP32 anchors per substep and thread) in
   // shared memory when a block's fit in the default 48 KB
@@ -985,9 +937,12 @@ const ciscvx_tune kTuneCandidates[] = {
     {4, 2, 0, 0, 0}, {4, 3, 1, 0, 1}, {2, 6, 1, 0, 1}, {4, 4, 1, 0, 2}, {2, 8, 1, 0, 2},
     {4, 0, 1, 0, 1}, {4, 0, 1, 0, 2},
 };
+// Split-form candidates of the fused pass (small batches only).
+const ciscvx_tune kSplitCandidates[] = {{1, 0, 1, 0, 0, 1}, {2, 0, 1, 0, 0, 1}, {4, 0, 1, 0, 0, 1}};
 
 // The tuner's choices can persist across processes in a text file named by
-// CISCVX_TUNE_CACHE: one line per key, "key<TAB>warps ctas lpt graph occupancy".
+// CISCVX_TUNE_CACHE: one line per key, "key<TAB>warps ctas lpt graph occupancy
+// split" (lines without the split field read as split 0).
 // It is read once, at the first autotune of the process; every new choice is
 // appended.  Lines that do not parse into a valid tune are ignored.
 bool g_tune_file_read = false;
@@ -1010,9 +965,10 @@ void read_tune_file() {  // g_tune_mu held
     if (!tab) continue;
     *tab = '\0';
     ciscvx_tune t{};
-    if (std::sscanf(tab + 1, "%d %d %d %d %d", &t.warps_per_cta, &t.ctas_per_sm, &t.lpt_order, &t.use_graph,
-                    &t.occupancy) == 5 &&
-        tune_ok(t))
+    const int got = std::sscanf(tab + 1, "%d %d %d %d %d %d", &t.warps_per_cta, &t.ctas_per_sm, &t.lpt_order,
+                                &t.use_graph, &t.occupancy, &t.split);
+    if (got == 5) t.split = 0;  // a line written before the split form existed
+    if ((got == 5 || got == 6) && tune_ok(t))
       g_tune_cache[line] = t;
   }
   std::fclose(f);
@@ -1023,17 +979,18 @@ void append_tune_file(const std::string& key, const ciscvx_tune& t) {  // g_tune
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s\t%d %d %d %d %d\n", key.c_str(), t.warps_per_cta, t.ctas_per_sm, t.lpt_order, t.use_graph,
-               t.occupancy);
+  std::fprintf(f, "%s\t%d %d %d %d %d %d\n", key.c_str(), t.warps_per_cta, t.ctas_per_sm, t.lpt_order,
+               t.use_graph, t.occupancy, t.split);
   std::fclose(f);
 }
 
 // Times launch() under every candidate written into *slot (warm-up + 2 timed
-// calls each), keeps the fastest there, caches it under `key` (and in the
-// CISCVX_TUNE_CACHE file, if set).
+// calls each; with_split adds the split-form candidates), keeps the fastest
+// there, caches it under `key` (and in the CISCVX_TUNE_CACHE file, if set).
 template <class Launch>
 ciscvx_status autotune_slot(ciscvx_batch_plan* p, ciscvx_tune* slot, const std::string& tag,
-                            cudaStream_t s, const Launch& launch, ciscvx_tune* chosen) {
+                            cudaStream_t s, const Launch& launch, ciscvx_tune* chosen,
+                            bool with_split = false) {
   const int keep_graph = slot->use_graph;
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, p->device);
@@ -1055,7 +1012,9 @@ ciscvx_status autotune_slot(ciscvx_batch_plan* p, ciscvx_tune* slot, const std::
   float best = 1e30f;
   ciscvx_tune bt = *slot;
   cudaError_t e = cudaSuccess;
-  for (const ciscvx_tune& c : kTuneCandidates) {
+  std::vector<ciscvx_tune> cands(std::begin(kTuneCandidates), std::end(kTuneCandidates));
+  if (with_split) cands.insert(cands.end(), std::begin(kSplitCandidates), std::end(kSplitCandidates));
+  for (const ciscvx_tune& c : cands) {
     *slot = c;
     e = launch();  // warm-up
     if (e != cudaSuccess) break;
@@ -1104,9 +1063,11 @@ ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* p, const ciscvx_bat
   double* part = (double*)workspace;
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
+  // the split form only where the fused pass has at most one warp per scheduler
+  const bool with_split = p->n_items <= 4 * p->sm_count;
   return autotune_slot(p, &p->tune_fused, "|fused", s, [&]() {
     return launch_fused_c(p, common_of(p, 0, p->tune_fused), io, vjp, part, ps, pL, 0, p->n_inst, s);
-  }, chosen);
+  }, chosen, with_split);
 }
 
 ciscvx_status ciscvx_batch_get_tune_fused(const ciscvx_batch_plan* p, ciscvx_tune* out) {

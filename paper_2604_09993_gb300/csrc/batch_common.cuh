@@ -31,6 +31,83 @@ __device__ __forceinline__ int next_item(const BatchCommon& c, int& local_iter) 
   return __shfl_sync(0xffffffffu, it, 0);
 }
 
+// Linearization of work item `item` (its warp's lanes; lanes past the group's
+// width idle).  AUX: the batch holds an Eq. (12) model (its foot links take
+// the CROSS path).
+template <typename TP, bool CMP, bool AUX>
+__device__ __forceinline__ void disc_item(const BatchCommon& c, int item, const double* __restrict__ X,
+                                          const double* __restrict__ U, const double* __restrict__ s,
+                                          TP* A, TP* Bm, TP* Bp, TP* S, double* defect,
+                                          double* penalty) {
+  const int lane = threadIdx.x & 31;
+  const int2 it = c.items[item];
+  const int4 g = c.groups[it.x];
+  if (lane >= g.w) return;
+  const DevModel& M = *c.models[g.x];
+  const int b = it.y;
+  const int2 e = c.entries[g.z + lane];
+  const DevInst& I = c.inst[e.x];
+  const long k = e.y;
+  const int nxt = M.nxt, nu = M.nu, nc = M.nc;
+  const double* Xi = X + I.x;
+  const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
+  const double* uR = uL + nu;
+  const size_t sa = CMP ? (size_t)M.nnzA : (size_t)nxt * nxt;
+  const size_t sb = CMP ? (size_t)M.nnzB : (size_t)nxt * nu;
+  TP* Ak = A + I.a + k * sa;
+  TP* Bmk = Bm ? Bm + I.b + k * sb : nullptr;
+  TP* Bpk = Bp ? Bp + I.b + k * sb : nullptr;
+  TP* Sk = S + I.v + (size_t)k * nxt;
+  double* dk = defect + I.v + (size_t)k * nxt;
+  double* pk = penalty ? penalty + I.p + (size_t)k * nc : nullptr;
+  if (AUX && M.aux && M.body[b].contact >= 0)  // Eq. (12) model
+    disc_link<TP, true, CMP, false, AUX>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL,
+                                         uR, Ak, Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
+  else if (M.body[b].contact >= 0)
+    disc_link<TP, true, CMP>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, Ak, Bmk,
+                             Bpk, Sk, dk, pk, nullptr, c.status);
+  else
+    disc_link<TP, false, CMP>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, Ak,
+                              Bmk, Bpk, Sk, dk, pk, nullptr, c.status);
+}
+
+// Adjoint VJP of work item `item` (its own forward sweep, then the backward
+// sweep), writing the item's partial sums.
+template <typename TP>
+__device__ __forceinline__ void vjp_item(const BatchCommon& c, int item, const double* __restrict__ X,
+                                         const double* __restrict__ U, const double* __restrict__ s,
+                                         const double* __restrict__ w, const double* __restrict__ rho,
+                                         double* gX, double* part, double* ps, double* pL) {
+  const int lane = threadIdx.x & 31;
+  const int2 it = c.items[item];
+  const int4 g = c.groups[it.x];
+  if (lane >= g.w) return;
+  const DevModel& M = *c.models[g.x];
+  const int b = it.y;
+  const int2 e = c.entries[g.z + lane];
+  const DevInst& I = c.inst[e.x];
+  const long k = e.y;
+  const int N = I.N, nxt = M.nxt, nu = M.nu, nc = M.nc, nb = M.nb;
+  const double* Xi = X + I.x;
+  const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
+  const double* uR = uL + nu;
+  const double* wi = w + I.v;
+  const DevBody& B = M.body[b];
+  const double rc = (B.contact >= 0) ? rho[I.p + k * nc + B.contact] : 0.0;
+  const double* wkm1 = (k > 0) ? wi + (k - 1) * nxt : nullptr;
+  double* gXi = gX + I.x;
+  double* gXN = (k == N - 1) ? gXi + (size_t)N * nxt : nullptr;
+  double* pp = part + I.part + (size_t)k * M.nslot * 2;
+  double* psk = ps + I.pb + k * nb;
+  double* pLk = pL + I.pb + k * nb;
+  if (B.contact >= 0)
+    vjp_link<TP, true>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, wi + k * nxt,
+                       wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk, c.status);
+  else
+    vjp_link<TP, false>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, wi + k * nxt,
+                        wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk, c.status);
+}
+
 // Launch bounds per occupancy variant: (threads per CTA, min CTAs per SM).
 template <int OCC> struct Occ;
 template <> struct Occ<0> { static constexpr int T = 256, B = 1; };  // no register cap
@@ -46,5 +123,17 @@ cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool 
                                   void* S, double* defect, double* penalty, const double* w,
                                   const double* rho, double* gX, double* part, double* ps,
                                   double* pL, size_t smem, cudaStream_t st);
+
+// The same outputs with the linearization and the VJP of every item on
+// separate warps of one launch (items [0, n) linearize, [n, 2n) take the
+// adjoint; c.n_items = 2n).  Each warp integrates the trajectory itself: more
+// work than the fused pass, but a shorter path per warp, for batches too
+// small to fill the GPU (batch_split.cu; no register cap).
+cudaError_t launch_disc_vjp_split(const BatchCommon& c, int n, int prec, bool compact,
+                                  unsigned blocks, unsigned threads, const double* X,
+                                  const double* U, const double* s, void* A, void* Bm, void* Bp,
+                                  void* S, double* defect, double* penalty, const double* w,
+                                  const double* rho, double* gX, double* part, double* ps,
+                                  double* pL, cudaStream_t st);
 
 }  // namespace ciscvx

@@ -29,11 +29,13 @@ TUNES = [
 # launch shape the tuner can pick is run by the parity tests below, and the
 # full-size test asserts that its pick is one of them.
 FUSED_CANDIDATES = [
-    (4, 2, 1, 0, 0), (8, 1, 1, 0, 0), (2, 4, 1, 0, 0), (1, 8, 1, 0, 0), (4, 0, 1, 0, 0),
-    (4, 2, 0, 0, 0), (4, 3, 1, 0, 1), (2, 6, 1, 0, 1), (4, 4, 1, 0, 2), (2, 8, 1, 0, 2),
-    (4, 0, 1, 0, 1), (4, 0, 1, 0, 2),
+    (4, 2, 1, 0, 0, 0), (8, 1, 1, 0, 0, 0), (2, 4, 1, 0, 0, 0), (1, 8, 1, 0, 0, 0), (4, 0, 1, 0, 0, 0),
+    (4, 2, 0, 0, 0, 0), (4, 3, 1, 0, 1, 0), (2, 6, 1, 0, 1, 0), (4, 4, 1, 0, 2, 0), (2, 8, 1, 0, 2, 0),
+    (4, 0, 1, 0, 1, 0), (4, 0, 1, 0, 2, 0),
+    # split form (linearization and adjoint of an item on two warps), small batches
+    (1, 0, 1, 0, 0, 1), (2, 0, 1, 0, 0, 1), (4, 0, 1, 0, 0, 1),
 ]
-_TUNE_KEYS = ("warps_per_cta", "ctas_per_sm", "lpt_order", "use_graph", "occupancy")
+_TUNE_KEYS = ("warps_per_cta", "ctas_per_sm", "lpt_order", "use_graph", "occupancy", "split")
 
 
 def _tune_dict(c):
@@ -41,7 +43,7 @@ def _tune_dict(c):
 
 
 def _tune_tuple(t):
-    return tuple(int(t[k]) for k in _TUNE_KEYS)
+    return tuple(int(t.get(k, 0)) for k in _TUNE_KEYS)
 
 
 # oracle results are independent of the launch shape: computed once per input set
@@ -429,6 +431,7 @@ def _fused_check(env, precision, out_format, layout, tune):
     if tune is not None:
         assert _tune_tuple(plan.tune_fused())[:3] == _tune_tuple(tune)[:3]
         assert plan.tune_fused()["occupancy"] == tune["occupancy"]
+        assert plan.tune_fused()["split"] == tune.get("split", 0)
     X, U, s, w, rho = _packed(plan, probs, dev, torch, layout)
     out, g = plan.discretize_and_vjp(X, U, s, w, rho)
     sep = plan.discretize(X, U, s)
@@ -468,7 +471,7 @@ def test_fused_pass_matches_separate_calls_and_oracle(env, precision, out_format
     _fused_check(env, precision, out_format, layout, None)
 
 
-@pytest.mark.parametrize("cand", FUSED_CANDIDATES, ids=lambda c: "w%d-c%d-l%d-g%d-occ%d" % c)
+@pytest.mark.parametrize("cand", FUSED_CANDIDATES, ids=lambda c: "w%d-c%d-l%d-g%d-occ%d-split%d" % c)
 @pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
 @pytest.mark.parametrize("out_format", ["dense", "compact"])
 def test_fused_pass_every_tuner_candidate(env, cand, precision, out_format):
@@ -502,6 +505,47 @@ def test_autotune_fused_keeps_results(env):
         assert block_err(plan.unpack(gX, "X", i, rX.shape), rX) <= 1e-4
         assert block_err(plan.unpack(gU, "U", i, rU.shape), rU) <= 1e-4
         assert abs(L[i] - rL) <= 1e-4 * max(1.0, abs(rL))
+
+
+@pytest.mark.parametrize("robot,N,n_sub", [("hopper", 1, 4), ("hopper", 10, 4), ("cheetah7", 50, 10),
+                                             ("cheetah7", 100, 10)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_single_instance_step_split_and_autotuned(env, robot, N, n_sub, precision):
+    """The single-instance configurations (hopper N = 10 with 4 substeps, the
+    7-link chain at N = 50 and 100 with 10 substeps, and N = 1) through a
+    one-instance plan's discretize_and_vjp, as the bench times them: under
+    each split-form launch shape, and under the fused autotuner's pick (which
+    must come from the candidate list), against the oracle."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    make = synth.hopper_fp64 if robot == "hopper" else synth.cheetah_n50
+    p = make(seed=5, N=N, n_sub=n_sub)
+    m = api.Model(p.robot)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X, U, sv, w, rho = t(p.X), t(p.U), t(p.s), t(p.w), t(p.rho)
+    ref = oracle.discretize(p.robot.as_dict(), p.X, p.U, p.s, p.n_sub)
+    rX, rU, rs, rL = oracle.vjp(p.robot.as_dict(), p.X, p.U, p.s, p.w, p.rho, p.n_sub)
+    tol = TOL_FP32_PHI if precision == "fp32_phi" else TOL_FP64
+    shapes = [c for c in FUSED_CANDIDATES if c[5] == 1] + ["autotune"]
+    for shape in shapes:
+        if shape == "autotune":
+            plan = api.BatchPlan([m], [0], [N], [n_sub], precision=precision)
+            ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=dev)
+            pick = plan.autotune_fused(X, U, sv, w, rho, workspace=ws)
+            assert _tune_tuple(pick) in FUSED_CANDIDATES, pick
+        else:
+            plan = api.BatchPlan([m], [0], [N], [n_sub], precision=precision, tune=_tune_dict(shape))
+            assert plan.tune_fused()["split"] == 1
+            ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=dev)
+        out, g = plan.discretize_and_vjp(X, U, sv, w, rho, workspace=ws)
+        plan.sync_status()
+        host = {k: v.double().cpu().numpy() for k, v in out.items()}
+        _check_instance(plan, host, 0, p, ref, precision)
+        gX, gU, gs, L = (g[k].cpu().numpy() for k in ("gX", "gU", "gs", "L"))
+        assert block_err(plan.unpack(gX, "X", 0, rX.shape), rX) <= tol, shape
+        assert block_err(plan.unpack(gU, "U", 0, rU.shape), rU) <= tol, shape
+        assert block_err(plan.unpack(gs, "s", 0, rs.shape), rs) <= tol, shape
+        assert abs(L[0] - rL) <= tol * max(1.0, abs(rL)), shape
 
 
 _TUNE_SCRIPT = r"""
