@@ -864,12 +864,13 @@ def run_ours(args):
         mx = [api.Model(r) for r in bx.robots]
         px = api.BatchPlan(mx, bx.model_idx, bx.Ns, bx.n_subs, precision=prec)
         probs = (bx.instance(i) for i in range(len(bx)))
-        Xs, Us, ss = [], [], []
+        Xs, Us, ss, ws_, rs_ = [], [], [], [], []
         for pr in probs:
-            Xs.append(pr.X); Us.append(pr.U); ss.append(pr.s)
+            Xs.append(pr.X); Us.append(pr.U); ss.append(pr.s); ws_.append(pr.w); rs_.append(pr.rho)
         t_ = lambda a: torch.tensor(a, device=dev)  # noqa: E731
         Xx, Ux, sx = t_(px.pack(Xs, "X")), t_(px.pack(Us, "U")), t_(px.pack(ss, "s"))
-        del Xs, Us, ss
+        wx, rx = t_(px.pack(ws_, "defect")), t_(px.pack(rs_, "penalty"))
+        del Xs, Us, ss, ws_, rs_
         ox = px.alloc_outputs(dev)
         px.autotune(Xx, Ux, sx, out=ox)
         barrier()
@@ -877,10 +878,22 @@ def run_ours(args):
         barrier()
         px.sync_status()
         tx, = max_over_ranks([tx])
-        cross = {"metric": "linearized intervals/s (STM; this model's VJP is linearize-and-contract)",
+        cross = {"metric": "linearized intervals/s (STM), and of the reverse-mode adjoint VJP",
                  "value": units * args.steps / tx, "unit": "intervals/s",
                  "ms_per_step": tx / args.steps * 1e3, "n_y": mx[0].ny, "tune": px.tune()}
-        del ox, px
+        del ox
+        # the adjoint VJP of the same batch (per-link kernel with the CROSS foot links)
+        wsx = torch.empty(px.vjp_workspace_size(), dtype=torch.uint8, device=dev)
+        gx = px.discretize_vjp(Xx, Ux, sx, wx, rx, workspace=wsx)
+        barrier()
+        tv = time_steps(torch, lambda: px.discretize_vjp(Xx, Ux, sx, wx, rx, workspace=wsx, out=gx),
+                        args.steps, args.warmup, stream, name="Eq. (12) model, VJP")
+        barrier()
+        px.sync_status()
+        tv, = max_over_ranks([tv])
+        cross["vjp"] = {"value": units * args.steps / tv, "ms_per_step": tv / args.steps * 1e3,
+                        "workspace_bytes": px.vjp_workspace_size()}
+        del gx, wsx, wx, rx, px
         torch.cuda.empty_cache()
         # the same with compact outputs (the packing of X, U, s does not depend on the format)
         pxc = api.BatchPlan(mx, bx.model_idx, bx.Ns, bx.n_subs, precision=prec, out_format="compact")

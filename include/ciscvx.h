@@ -144,7 +144,8 @@ typedef struct {
  *     (n_y = 5 n_c).  The penalty output is the increment of the path-penalty
  *     states.  Provided for the dense and compact linearization (single
  *     and batch; z formed from the dense outputs, not provided with compact
- *     ones) and the VJP (linearize-and-contract, also inside batch plans). */
+ *     ones) and the VJP (the per-link discrete adjoint, also inside batch
+ *     plans). */
 typedef enum { CISCVX_AUX_PENALTY = 0, CISCVX_AUX_CROSS = 1 } ciscvx_aux_model;
 
 /* Joint reaction forces (Sec. II-A).
@@ -259,8 +260,8 @@ typedef enum { CISCVX_OP_DISCRETIZE = 0, CISCVX_OP_VJP = 1 } ciscvx_op;
 /* Bytes of device scratch memory that `op` needs for N intervals (0 if none).
  * EINVAL on null pointers, N < 1 or an unknown op/layout.  Where the scratch
  * depends on n_sub and the precision (CISCVX_OP_DISCRETIZE for a model with
- * coupled links; CISCVX_OP_VJP for one with coupled links or the Eq. (12)
- * state) it returns EUNSUPPORTED: use ciscvx_discretize_workspace_size. */
+ * coupled links; CISCVX_OP_VJP for one with coupled links) it returns
+ * EUNSUPPORTED: use ciscvx_discretize_workspace_size. */
 ciscvx_status ciscvx_workspace_size(const ciscvx_model* model, ciscvx_op op, int N,
                                     ciscvx_u_layout layout, size_t* bytes);
 
@@ -272,11 +273,10 @@ ciscvx_status ciscvx_workspace_size(const ciscvx_model* model, ciscvx_op op, int
  *     model with coupled links the stage data of the nominal trajectory
  *     (n_sub x stages x (4 n_j + n_b + n_x~ + skyline(K) + contact fields)
  *     values per interval in the precision's dtype), minimum 32 intervals.
- *   CISCVX_OP_VJP: for the default model (no coupled links, aux model
- *     CISCVX_AUX_PENALTY) min = full = ciscvx_workspace_size(CISCVX_OP_VJP);
- *     otherwise the linearize-and-contract VJP's dense blocks (A, B-, B+, S in
- *     the precision's dtype, defect and penalty in FP64) plus the stage data,
- *     per interval, minimum 32 intervals.
+ *   CISCVX_OP_VJP: for a model without coupled links (either auxiliary
+ *     model) min = full = ciscvx_workspace_size(CISCVX_OP_VJP); for a model
+ *     with coupled links the coupled adjoint's stage data and cotangents per
+ *     interval, minimum 32 intervals.
  * Either pointer may be NULL.  EINVAL on a null model, N < 1, n_sub < 1 or an
  * unknown op, precision or layout. */
 ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* model, ciscvx_op op, int N,
@@ -336,13 +336,11 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* model, int N, int n_
  * FP64 nominal pass records its stage data in the workspace, then one thread
  * per interval runs the transposed stage maps backward; no block is formed.
  * For a per-link model with the Eq. (12) auxiliary state (CISCVX_AUX_CROSS)
- * by linearize-and-contract: per chunk of intervals the dense blocks are
- * formed in the workspace (as ciscvx_discretize computes them) and contracted,
- * dL/dx~_k = A_k^T lambda_k - rho_k (path-penalty rows) - w_{k-1},
- * dL/du = B-_k^T lambda_k / B+_k^T lambda_k (summed per node in the node
- * layout), dL/ds_k = S_k . lambda_k, lambda_k = w_k + rho_k on the
- * path-penalty rows; its workspace comes from
- * ciscvx_discretize_workspace_size(CISCVX_OP_VJP) (no substep limit).
+ * the per-link adjoint covers each contact's four cross-complementarity rows
+ * and its path penalty: lambda^c's integrand v_x - omega (R rho)_y puts
+ * sources on the stage theta, omega and v_x of the backward sweep, and the
+ * rows that integrate the inputs alone contribute their quadrature weights
+ * times the slopes; scratch and substep limit as for the default model.
  *   w [N][n_x~], rho [N][n_c] (FP64, device; rho may be NULL when n_c == 0).
  *   gX [N+1][n_x~], gU like U, gs [N]: FP64 outputs (device), overwritten.
  *   L: optional FP64 scalar on the device (NULL to skip).
@@ -470,21 +468,18 @@ ciscvx_status ciscvx_batch_discretize(ciscvx_batch_plan* plan, const ciscvx_batc
 /* Bytes of device scratch ciscvx_batch_discretize_vjp needs (the minimum). */
 ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* plan, size_t* bytes);
 
-/* The minimum, and the size from which the instances of the Eq. (12) model
- * and with coupled links take the batched linearize-and-contract pass (all
- * their dense blocks in the workspace at once: one launch per kind instead
- * of several per instance).  Equal when the plan has no such instances. */
+/* The minimum and the full size of that scratch; the two are equal (the
+ * coupled instances' adjoint takes the minimum's chunked form). */
 ciscvx_status ciscvx_batch_vjp_workspace_sizes(const ciscvx_batch_plan* plan, size_t* min_bytes,
                                                size_t* full_bytes);
 
 /* VJP (as ciscvx_discretize_vjp) of every instance; L receives one value per
- * instance.  Default-model instances take the batched adjoint kernel;
- * instances of the Eq. (12) model or with coupled links are linearized and
- * contracted: all at once when the workspace reaches the full size of
- * ciscvx_batch_vjp_workspace_sizes, else one after another in stream order
- * (chunked in the last part of the workspace).  workspace: device, >=
- * ciscvx_batch_vjp_workspace_size bytes, 16-byte aligned.  Errors: EINVAL, EUNSUPPORTED (n_sub >
- * CISCVX_MAX_VJP_SUBSTEPS in some default-model instance), ECUDA. */
+ * instance.  Per-link instances (either auxiliary model) take the batched
+ * adjoint kernel; instances with coupled links then take the coupled path's
+ * reverse-mode adjoint one after another in stream order (chunked in the last
+ * part of the workspace).  workspace: device, >= ciscvx_batch_vjp_workspace_size
+ * bytes, 16-byte aligned.  Errors: EINVAL, EUNSUPPORTED (n_sub >
+ * CISCVX_MAX_VJP_SUBSTEPS in some per-link instance), ECUDA. */
 ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_vjp_io* io,
                                           void* workspace, size_t ws_bytes, void* stream);
 
@@ -498,7 +493,8 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_
  * workspace as for ciscvx_batch_discretize_vjp.  Launched directly (no graph).
  * With the fused tune's split = 1 (small batches) the two run on separate
  * warps of the same launch, each integrating the trajectory, as the two calls
- * would.  Errors: as the two calls. */
+ * would.  Plans with an Eq. (12) or a coupled-link instance make the two calls
+ * in turn.  Errors: as the two calls. */
 ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
                                               const ciscvx_batch_vjp_io* vjp, void* workspace,
                                               size_t ws_bytes, void* stream);
@@ -530,11 +526,12 @@ ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* plan, const ciscvx_batch_
  *     minimum of ciscvx_batch_vjp_workspace_sizes).
  * Coupled-link instances are linearized one after another within their
  * chunk (and their VJP taken by the coupled path's reverse-mode adjoint).
+ * In a plan with an Eq. (12) instance each chunk is linearized, then its VJP
+ * taken, by the separate kernels (the fused pass has no Eq. (12) form).
  * The first call with a new n_chunks builds the chunked work tables and
  * streams (device allocation); later calls with the same n_chunks allocate
  * nothing.  Errors: EINVAL (null buffers, n_chunks outside [1, n_inst], short
- * workspace), EUNSUPPORTED (VJP with n_sub > CISCVX_MAX_VJP_SUBSTEPS; VJP of
- * a plan with per-link Eq. (12) instances), ECUDA. */
+ * workspace), EUNSUPPORTED (VJP with n_sub > CISCVX_MAX_VJP_SUBSTEPS), ECUDA. */
 ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
                                     const ciscvx_batch_io* host, const ciscvx_batch_io* dev,
                                     const ciscvx_batch_vjp_io* host_vjp,
@@ -545,7 +542,9 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
  * (its launch shape is kept apart from the discretization's: the fused kernel
  * holds more state per thread).  When the fused pass would run at most one
  * warp per scheduler (work items <= 4 x SMs), the split form (tune.split = 1,
- * one warp per item, 1, 2 or 4 warps per CTA) is among the candidates.
+ * one warp per item, 1, 2 or 4 warps per CTA) is among the candidates.  A
+ * plan with an Eq. (12) instance does not use the fused pass: nothing is
+ * timed and the current shape is returned.
  * Overwrites the outputs; workspace as for ciscvx_batch_discretize_vjp.
  * Errors: as ciscvx_batch_discretize_and_vjp. */
 ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
@@ -857,11 +856,10 @@ ciscvx_status ciscvx_socp_fill(const ciscvx_socp* socp, int n_inst, const ciscvx
  *   run-time specialized kernels (the runtime takes device memory for the
  *   loaded code); make that call, or any ciscvx_discretize /
  *   ciscvx_discretize_vjp call of that model and precision, at set-up.
- *   Models: all of them.  Per-link models with one penalty state per contact
- *   run the adjoint kernel, whose scratch is ciscvx_workspace_size(
- *   CISCVX_OP_VJP) for N intervals.  Models whose VJP is linearize-and-
- *   contract (coupled links, Eq. (12) auxiliary state) run in chunks of the
- *   intervals whose dense blocks fit the array; their minimum is the
+ *   Models: all of them.  Per-link models (either auxiliary model) run the
+ *   adjoint kernel, whose scratch is ciscvx_workspace_size(CISCVX_OP_VJP)
+ *   for N intervals.  Models with coupled links run their adjoint in chunks
+ *   of the intervals whose stage data fit the array; their minimum is the
  *   min_bytes of ciscvx_discretize_workspace_size(CISCVX_OP_VJP).
  * Errors: as ciscvx_discretize_vjp, and CISCVX_EUNSUPPORTED when the minimum
  * scratch of this request (min_bytes of ciscvx_discretize_workspace_size with

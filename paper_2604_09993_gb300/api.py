@@ -360,8 +360,6 @@ def discretize_workspace_size(model: Model, N: int, n_sub: int, precision: str =
 
 # default cap on the scratch a discretize call allocates for a coupled model
 DISCRETIZE_WS_CAP = 2 << 30
-# default cap of the batch VJP scratch for the batched contract pass
-BATCH_VJP_WS_CAP = 16 << 30
 
 
 def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layout: str = "node",
@@ -765,23 +763,18 @@ class BatchPlan:
         return n.value
 
     def vjp_workspace_sizes(self):
-        """(min, full) bytes of VJP scratch: full enables the batched
-        linearize-and-contract pass of Eq. (12) / coupled-link instances."""
+        """(min, full) bytes of VJP scratch (equal: see ciscvx_batch_vjp_workspace_sizes)."""
         lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
         _check(load().ciscvx_batch_vjp_workspace_sizes(self._h, ctypes.byref(lo), ctypes.byref(hi)))
         return lo.value, hi.value
 
     def discretize_vjp(self, X, U, s, w, rho, workspace=None, want_L=True, out=None):
         """ciscvx_batch_discretize_vjp; returns dict gX, gU, gs, L (per instance).
-        A given workspace of at least the minimum is used as it is (the
-        library picks the contract pass by its size); without one (or with a
-        smaller one), one of the full size (batched contract pass) is
-        allocated when that is at most BATCH_VJP_WS_CAP bytes, else of the
-        minimum."""
+        A given workspace of at least the minimum is used as it is (a larger
+        one gives the coupled instances' adjoint larger chunks); without one
+        (or with a smaller one) one of the minimum size is allocated."""
         import torch
-        lo, hi = self.vjp_workspace_sizes()
-        need = lo if workspace is not None and workspace.numel() * workspace.element_size() >= lo else \
-            (hi if hi <= BATCH_VJP_WS_CAP else lo)
+        need = self.vjp_workspace_size()
         if workspace is None or workspace.numel() * workspace.element_size() < need:
             workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
         if out is None:
@@ -796,9 +789,7 @@ class BatchPlan:
 
     def _fused_args(self, X, U, s, w, rho, workspace, out, gout, want_L):
         import torch
-        lo, hi = self.vjp_workspace_sizes()
-        need = lo if workspace is not None and workspace.numel() * workspace.element_size() >= lo else \
-            (hi if hi <= BATCH_VJP_WS_CAP else lo)  # as discretize_vjp
+        need = self.vjp_workspace_size()  # as discretize_vjp
         if workspace is None or workspace.numel() * workspace.element_size() < need:
             workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
         if out is None:

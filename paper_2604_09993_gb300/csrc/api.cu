@@ -480,10 +480,9 @@ ciscvx_status ciscvx_workspace_size(const ciscvx_model* m, ciscvx_op op, int N,
     *bytes = 0;
   }
   else if (op == CISCVX_OP_VJP) {
-    if (m->cpl || m->host.aux)
-      return fail(CISCVX_EUNSUPPORTED, "this model's VJP scratch (coupled-path adjoint or linearize-and-"
-                                       "contract) depends on n_sub and the precision: use "
-                                       "ciscvx_discretize_workspace_size");
+    if (m->cpl)
+      return fail(CISCVX_EUNSUPPORTED, "the scratch of the coupled-path adjoint depends on n_sub and "
+                                       "the precision: use ciscvx_discretize_workspace_size");
     *bytes = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
   }
   else return fail(CISCVX_EINVAL, "unknown op %d", (int)op);
@@ -511,9 +510,6 @@ ciscvx_status ciscvx_discretize_workspace_size(const ciscvx_model* m, ciscvx_op 
   } else if (m->cpl) {  // reverse-mode adjoint of the coupled path
     lo = cpl_adjoint_bytes(*m->cpl, std::min(N, 32), n_sub, precision);
     hi = cpl_adjoint_bytes(*m->cpl, N, n_sub, precision);
-  } else if (m->host.aux) {
-    lo = contract_bytes(m->host, m->cpl, std::min(N, 32), n_sub, precision);
-    hi = contract_bytes(m->host, m->cpl, N, n_sub, precision);
   } else {
     lo = hi = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
   }
@@ -601,17 +597,6 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
     if (e != cudaSuccess) return cuda_fail(e, "coupled adjoint launch");
     return ok();
   }
-  if (m->host.aux) {  // linearize-and-contract
-    const size_t need = contract_bytes(m->host, m->cpl, std::min(N, 32), n_sub, precision);
-    if (!workspace || ws_bytes < need)
-      return fail(CISCVX_EINVAL, "workspace of at least %zu bytes needed (got %zu)", need, ws_bytes);
-    if (((uintptr_t)workspace & 15) != 0) return fail(CISCVX_EINVAL, "workspace must be 16-byte aligned");
-    cudaError_t e = launch_contract_vjp(m->host, m->dev, m->cpl, N, n_sub, precision, layout, X, U, s,
-                                        w, rho, gX, gU, gs, L, workspace, ws_bytes, m->status,
-                                        (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "contract vjp launch");
-    return ok();
-  }
   if (n_sub > MAXSUB_VJP)
     return fail(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (got %d)", MAXSUB_VJP, n_sub);
   const size_t need = vjp_workspace_bytes(m->host.nb, m->host.nu, m->host.nslot, N, layout);
@@ -620,7 +605,7 @@ ciscvx_status ciscvx_discretize_vjp(const ciscvx_model* m, int N, int n_sub,
   if (((uintptr_t)workspace & 15) != 0) return fail(CISCVX_EINVAL, "workspace must be 16-byte aligned");
   cudaError_t e = launch_vjp(m->dev, m->host.nb, m->host.nxt, m->host.nu, m->host.nslot, N, n_sub,
                              precision, layout, X, U, s, w, rho, gX, gU, gs, L, workspace,
-                             m->status, (cudaStream_t)stream);
+                             m->status, m->host.aux != 0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
   return ok();
 }

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_disc(BatchCo
   }
 }
 
-template <typename TP, int OCC>
+template <typename TP, int OCC, bool AUX = false>
 __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_vjp(BatchCommon c, const double* __restrict__ X,
                                                    const double* __restrict__ U,
                                                    const double* __restrict__ s,
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B) k_batch_vjp(BatchCom
   for (;;) {
     const int item = next_item(c, iter);
     if (item >= c.n_items) break;
-    vjp_item<TP>(c, item, X, U, s, w, rho, gX, part, ps, pL);
+    vjp_item<TP, AUX>(c, item, X, U, s, w, rho, gX, part, ps, pL);
   }
 }
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(FINB) k_batch_vjp_finish(const DevModel* const
                                                            double* gU, double* gs, double* L) {
   __shared__ double red[FINB];
   const DevInst I = inst[blockIdx.x];
-  if (I.contract) return;  // written by the contract pass (coupled adjoint or linearize-and-contract)
+  if (I.contract) return;  // written by the coupled path's adjoint
   const DevModel& M = *models[I.model];
   const int nu = M.nu, nslot = M.nslot, nb = M.nb, N = I.N;
   const double* P = part + I.part;
@@ -134,7 +134,7 @@ struct ciscvx_batch_plan {
   int n_inst = 0, n_models = 0, prec = 0, layout = 0, device = 0, sm_count = 0, max_nsub = 0;
   bool compact = false;  // CISCVX_OUT_COMPACT
   bool all_nu0 = true, all_nc0 = true;
-  bool any_aux = false;  // some model uses the Eq. (12) auxiliary state (no VJP, no compact outputs)
+  bool any_aux = false;  // some model uses the Eq. (12) auxiliary state (no fused pass: its VJP runs apart)
   bool any_cpl = false;  // some model has coupled links (coupled path; no VJP, no compact outputs)
   // coupled-path groups: instances of one coupled model with one n_sub, as
   // (instance, k) entries; one stage-data workspace shared in stream order
@@ -151,28 +151,8 @@ struct ciscvx_batch_plan {
   size_t part_total = 0, pb_total = 0;
   int n_items = 0;
   std::vector<int2> items_lpt, items_nat;
-  // the adjoint kernel's items: those of the instances that are not contract instances
-  int n_vitems = 0;
-  int2* d_vitems_lpt = nullptr;
-  int2* d_vitems_nat = nullptr;
-  bool any_contract = false;   // Eq. (12) or coupled-link instances: VJP by linearize-and-contract
-  int max_nsub_adj = 0;        // largest n_sub among the other instances
-  size_t contract_ws = 0;      // bytes of VJP workspace the contract pass needs (after the adjoint's)
-  // batched contract pass (when the workspace holds every contract instance's
-  // dense blocks): the instance table with its output offsets moved into that
-  // region, the Eq. (12) instances' items, (instance, k) entries per model,
-  // and the contract instances
-  DevInst* d_inst_ws = nullptr;
-  int n_citems = 0;
-  int2* d_citems_lpt = nullptr;
-  int2* d_citems_nat = nullptr;
-  struct CBucket { int model; long first, count; };
-  std::vector<CBucket> cbuckets;
-  int2* d_centries = nullptr;
-  std::vector<int> cinst;
-  int* d_cinst = nullptr;
-  size_t cws_A = 0, cws_B = 0, cws_V = 0, cws_P = 0;  // elements of each block region
-  size_t cws_full = 0;                                 // bytes of the region
+  int max_nsub_adj = 0;        // largest n_sub among the per-link instances (the adjoint kernel's)
+  size_t cpl_adj_ws = 0;       // bytes of VJP workspace the coupled adjoint needs (after the partial sums)
   std::string key;
   // device tables
   const DevModel** d_models = nullptr;
@@ -228,13 +208,6 @@ void free_plan(ciscvx_batch_plan* p) {
   cudaFree(p->d_groups);
   cudaFree(p->d_items_lpt);
   cudaFree(p->d_items_nat);
-  cudaFree(p->d_vitems_lpt);
-  cudaFree(p->d_vitems_nat);
-  cudaFree(p->d_inst_ws);
-  cudaFree(p->d_citems_lpt);
-  cudaFree(p->d_citems_nat);
-  cudaFree(p->d_centries);
-  cudaFree(p->d_cinst);
   cudaFree(p->d_queue);
   cudaFree(p->d_status);
   cudaFree(p->d_cpl_entries);
@@ -312,10 +285,6 @@ BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot, const ciscvx_t
   c.groups = p->d_groups;
   c.items = t.lpt_order ? p->d_items_lpt : p->d_items_nat;
   c.n_items = p->n_items;
-  if (queue_slot == 1) {  // the adjoint pass skips the contract instances
-    c.items = t.lpt_order ? p->d_vitems_lpt : p->d_vitems_nat;
-    c.n_items = p->n_vitems;
-  }
   c.persistent = t.ctas_per_sm > 0;
   c.queue = p->d_queue + queue_slot;
   c.status = p->d_status;
@@ -425,7 +394,14 @@ cudaError_t launch_vjp_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscv
   k_batch_vjp<TP, OCC><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho, io->gX, \
                                                   part, ps, pL)
   const int occ = p->tune.occupancy;
-  if (p->prec == CISCVX_FP64) {
+  if (p->any_aux) {  // Eq. (12) model in the batch: no register cap
+    if (p->prec == CISCVX_FP64)
+      k_batch_vjp<double, 0, true><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho,
+                                                              io->gX, part, ps, pL);
+    else
+      k_batch_vjp<float, 0, true><<<blocks, threads, 0, s>>>(c, io->X, io->U, io->s, io->w, io->rho,
+                                                             io->gX, part, ps, pL);
+  } else if (p->prec == CISCVX_FP64) {
     if (occ == 1) CISCVX_VJP(double, 1);
     else if (occ == 2) CISCVX_VJP(double, 2);
     else CISCVX_VJP(double, 0);
@@ -443,89 +419,30 @@ cudaError_t launch_vjp_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscv
   return e;
 }
 
-// Offset of the contract pass's part of the VJP workspace (after the
-// adjoint's partial sums, 16-byte aligned).
-size_t contract_ws_offset(const ciscvx_batch_plan* p) {
+// Offset of the coupled adjoint's part of the VJP workspace (after the
+// per-link adjoint's partial sums, 16-byte aligned).
+size_t cpl_ws_offset(const ciscvx_batch_plan* p) {
   return (sizeof(double) * (p->part_total + 2 * p->pb_total) + 15) & ~(size_t)15;
 }
 
-// The VJP of the contract instances one after another in stream order, each
-// in chunks of what fits in the workspace: the reverse-mode adjoint of the
-// coupled path for coupled-link models, linearize-and-contract for the Eq.
-// (12) state (only the coupled ones when `coupled_only`).
-cudaError_t launch_contract_instances(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, void* ws,
-                                      size_t ws_bytes, cudaStream_t s, bool coupled_only = false) {
+// The reverse-mode adjoint of the coupled path for the coupled-link
+// instances, one after another in stream order, each in chunks of what fits
+// in the workspace.
+cudaError_t launch_coupled_vjps(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, void* ws,
+                                size_t ws_bytes, cudaStream_t s) {
   for (int i = 0; i < p->n_inst; ++i) {
     const DevInst& I = p->inst[i];
     if (!I.contract) continue;
     const ciscvx_model* m = p->models[I.model];
     const bool nu = m->host.nu > 0, nc = m->host.nc > 0;
-    cudaError_t e = cudaSuccess;
-    if (m->cpl) {
-      e = launch_coupled_vjp(*m->cpl, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
-                             io->s + I.s, io->w + I.v, nc ? io->rho + I.p : nullptr, io->gX + I.x,
-                             nu ? io->gU + I.u : nullptr, io->gs + I.s, io->L ? io->L + i : nullptr, ws, ws_bytes,
-                             p->d_status, s);
-      if (e != cudaSuccess) return e;
-      continue;
-    }
-    if (coupled_only) continue;
-    e = launch_contract_vjp(
-        m->host, m->dev, m->cpl, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
-        io->s + I.s, io->w + I.v, nc ? io->rho + I.p : nullptr, io->gX + I.x, nu ? io->gU + I.u : nullptr,
-        io->gs + I.s, io->L ? io->L + i : nullptr, ws, ws_bytes, p->d_status, s);
+    cudaError_t e = launch_coupled_vjp(*m->cpl, I.N, I.nsub, p->prec, p->layout, io->X + I.x,
+                                       nu ? io->U + I.u : nullptr, io->s + I.s, io->w + I.v,
+                                       nc ? io->rho + I.p : nullptr, io->gX + I.x,
+                                       nu ? io->gU + I.u : nullptr, io->gs + I.s, io->L ? io->L + i : nullptr,
+                                       ws, ws_bytes, p->d_status, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
-}
-
-// The same for all Eq. (12) instances at once, when the workspace holds all
-// their dense blocks: one persistent launch of the per-link kernel over their
-// items writes the blocks at the instances' workspace offsets (d_inst_ws);
-// then one contraction per model and one fixed-order L per instance.  The
-// coupled instances follow, one after another, by the reverse-mode adjoint in
-// the same workspace.
-cudaError_t launch_contract_batched(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* io, void* ws,
-                                    size_t ws_bytes, cudaStream_t st) {
-  const size_t el = p->prec == CISCVX_FP64 ? sizeof(double) : sizeof(float);
-  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  char* base = (char*)ws;
-  void* A = base;
-  void* Bm = base + al(p->cws_A * el);
-  void* Bp = (char*)Bm + al(p->cws_B * el);
-  void* S = (char*)Bp + al(p->cws_B * el);
-  double* defect = (double*)((char*)S + al(p->cws_V * el));
-  double* penalty = (double*)((char*)defect + al(p->cws_V * 8));
-  cudaError_t e = cudaSuccess;
-  if (p->n_citems > 0) {
-    BatchCommon c = common_of(p, 0, p->tune);
-    c.items = p->tune.lpt_order ? p->d_citems_lpt : p->d_citems_nat;
-    c.n_items = p->n_citems;
-    c.inst = p->d_inst_ws;
-    if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), st);
-    unsigned blocks, threads;
-    grid_for(p, p->tune, c.n_items, blocks, threads);
-    if (e == cudaSuccess) {
-      if (p->prec == CISCVX_FP64)
-        k_batch_disc<double, 0, false, true><<<blocks, threads, 0, st>>>(
-            c, io->X, io->U, io->s, (double*)A, (double*)Bm, (double*)Bp, (double*)S, defect, penalty);
-      else
-        k_batch_disc<float, 0, false, true><<<blocks, threads, 0, st>>>(
-            c, io->X, io->U, io->s, (float*)A, (float*)Bm, (float*)Bp, (float*)S, defect, penalty);
-      e = cudaGetLastError();
-    }
-  }
-  for (const auto& bk : p->cbuckets) {
-    if (e != cudaSuccess) break;
-    e = launch_contract_batch(p->models[bk.model]->host, p->d_inst, p->d_inst_ws, p->d_centries + bk.first,
-                              bk.count, p->prec, p->layout, A, Bm, Bp, S, io->w, io->rho, io->gX, io->gU,
-                              io->gs, st);
-  }
-  if (e == cudaSuccess && io->L && !p->cinst.empty())
-    e = launch_contract_L_batch(p->d_models, p->d_inst, p->d_inst_ws, p->d_cinst, (int)p->cinst.size(), defect,
-                                penalty, io->w, io->rho, io->L, st);
-  if (e == cudaSuccess && p->any_cpl) e = launch_contract_instances(p, io, ws, ws_bytes, st, true);
-  return e;
 }
 
 // Discretize + VJP of the items of `c` in one pass, then the per-instance
@@ -581,7 +498,7 @@ ciscvx_status check_vjp(const ciscvx_batch_plan* p, const ciscvx_batch_vjp_io* i
   if (p->max_nsub_adj > MAXSUB_VJP)
     return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps (plan has %d)",
                      MAXSUB_VJP, p->max_nsub_adj);
-  const size_t need = contract_ws_offset(p) + p->contract_ws;
+  const size_t need = cpl_ws_offset(p) + p->cpl_adj_ws;
   if (!workspace || ws_bytes < need)
     return set_error(CISCVX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, ws_bytes);
   if (((uintptr_t)workspace & 15) != 0) return set_error(CISCVX_EINVAL, "workspace must be 16-byte aligned");
@@ -695,13 +612,10 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
     if (nc) p->all_nc0 = false;
     if (M.aux && !models[model_idx[i]]->cpl) p->any_aux = true;
     if (models[model_idx[i]]->cpl) p->any_cpl = true;
-    I.contract = (M.aux || models[model_idx[i]]->cpl) ? 1 : 0;
-    if (I.contract) {
-      p->any_contract = true;
+    I.contract = models[model_idx[i]]->cpl ? 1 : 0;
+    if (I.contract) {  // the coupled path's adjoint, chunked to at most 4096 intervals
       const CplTab* T = models[model_idx[i]]->cpl;
-      p->contract_ws = std::max(p->contract_ws,
-                                T ? cpl_adjoint_bytes(*T, std::min<long>(N[i], 4096), n_sub[i], precision)
-                                  : contract_bytes(M, nullptr, std::min<long>(N[i], 4096), n_sub[i], precision));
+      p->cpl_adj_ws = std::max(p->cpl_adj_ws, cpl_adjoint_bytes(*T, std::min<long>(N[i], 4096), n_sub[i], precision));
     } else {
       p->max_nsub_adj = std::max(p->max_nsub_adj, n_sub[i]);
     }
@@ -715,45 +629,6 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   p->n_items = (int)dec.items_lpt.size();
   p->items_lpt = dec.items_lpt;
   p->items_nat = dec.items_nat;
-  std::vector<int2> vitems_lpt, vitems_nat, citems_lpt, citems_nat;
-  for (const int2& it : dec.items_lpt)
-    (models[dec.groups[it.x].x]->host.aux ? citems_lpt : vitems_lpt).push_back(it);
-  for (const int2& it : dec.items_nat)
-    (models[dec.groups[it.x].x]->host.aux ? citems_nat : vitems_nat).push_back(it);
-  p->n_vitems = (int)vitems_lpt.size();
-  p->n_citems = (int)citems_lpt.size();
-  // the batched contract pass: workspace offsets of the contract instances'
-  // dense blocks, and their (instance, k) entries grouped by model
-  std::vector<DevInst> inst_ws = p->inst;
-  std::vector<int2> centries;
-  {
-    for (int i = 0; i < n_inst; ++i) {
-      // coupled instances run the reverse-mode adjoint (no dense blocks)
-      if (!p->inst[i].contract || models[p->inst[i].model]->cpl) continue;
-      const DevModel& M = models[p->inst[i].model]->host;
-      const size_t n = (size_t)p->inst[i].N;
-      DevInst& W = inst_ws[i];
-      W.a = (long long)p->cws_A; W.b = (long long)p->cws_B; W.v = (long long)p->cws_V; W.p = (long long)p->cws_P;
-      p->cws_A += n * M.nxt * M.nxt;
-      p->cws_B += n * M.nxt * M.nu;
-      p->cws_V += n * M.nxt;
-      p->cws_P += n * M.nc;
-      p->cinst.push_back(i);
-    }
-    for (int m = 0; m < n_models; ++m) {
-      ciscvx_batch_plan::CBucket bk{m, (long)centries.size(), 0};
-      for (int i : p->cinst)
-        if (p->inst[i].model == m)
-          for (int k = 0; k < p->inst[i].N; ++k) centries.push_back(make_int2(i, k));
-      bk.count = (long)centries.size() - bk.first;
-      if (bk.count) p->cbuckets.push_back(bk);
-    }
-    const size_t el = precision == CISCVX_FP64 ? sizeof(double) : sizeof(float);
-    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    p->cws_full = p->cinst.empty() ? 0
-                  : al(p->cws_A * el) + 2 * al(p->cws_B * el) + al(p->cws_V * el) + al(p->cws_V * 8) +
-                        al(p->cws_P * 8);
-  }
   const std::vector<int2>& entries = dec.entries;
   const std::vector<int4>& groups = dec.groups;
 
@@ -792,15 +667,6 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (e == cudaSuccess) e = upload(&p->d_groups, groups);
   if (e == cudaSuccess) e = upload(&p->d_items_lpt, p->items_lpt);
   if (e == cudaSuccess) e = upload(&p->d_items_nat, p->items_nat);
-  if (e == cudaSuccess && !vitems_lpt.empty()) e = upload(&p->d_vitems_lpt, vitems_lpt);
-  if (e == cudaSuccess && !vitems_nat.empty()) e = upload(&p->d_vitems_nat, vitems_nat);
-  if (e == cudaSuccess && !p->cinst.empty()) {
-    e = upload(&p->d_inst_ws, inst_ws);
-    if (e == cudaSuccess && !citems_lpt.empty()) e = upload(&p->d_citems_lpt, citems_lpt);
-    if (e == cudaSuccess && !citems_nat.empty()) e = upload(&p->d_citems_nat, citems_nat);
-    if (e == cudaSuccess) e = upload(&p->d_centries, centries);
-    if (e == cudaSuccess) e = upload(&p->d_cinst, p->cinst);
-  }
   if (e == cudaSuccess) e = cudaMalloc(&p->d_queue, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned));
@@ -874,14 +740,14 @@ ciscvx_status ciscvx_batch_discretize(ciscvx_batch_plan* p, const ciscvx_batch_i
 
 ciscvx_status ciscvx_batch_vjp_workspace_size(const ciscvx_batch_plan* p, size_t* bytes) {
   if (!p || !bytes) return set_error(CISCVX_EINVAL, "null argument");
-  *bytes = contract_ws_offset(p) + p->contract_ws;
+  *bytes = cpl_ws_offset(p) + p->cpl_adj_ws;
   return CISCVX_OK;
 }
 
 ciscvx_status ciscvx_batch_vjp_workspace_sizes(const ciscvx_batch_plan* p, size_t* min_bytes, size_t* full_bytes) {
   if (!p || !min_bytes || !full_bytes) return set_error(CISCVX_EINVAL, "null argument");
-  *min_bytes = contract_ws_offset(p) + p->contract_ws;
-  *full_bytes = contract_ws_offset(p) + std::max(p->contract_ws, p->cws_full);
+  *min_bytes = cpl_ws_offset(p) + p->cpl_adj_ws;
+  *full_bytes = *min_bytes;
   return CISCVX_OK;
 }
 
@@ -894,12 +760,8 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* p, const ciscvx_bat
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
   cudaError_t e = launch_vjp_c(p, common_of(p, 1, p->tune), io, part, ps, pL, 0, p->n_inst, s);
-  if (e == cudaSuccess && p->any_contract) {
-    char* cws = (char*)workspace + contract_ws_offset(p);
-    const size_t have = ws_bytes - contract_ws_offset(p);
-    if (have >= p->cws_full) e = launch_contract_batched(p, io, cws, have, s);
-    else e = launch_contract_instances(p, io, cws, p->contract_ws, s);
-  }
+  if (e == cudaSuccess && p->any_cpl)
+    e = launch_coupled_vjps(p, io, (char*)workspace + cpl_ws_offset(p), ws_bytes - cpl_ws_offset(p), s);
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "batch vjp launch: %s", cudaGetErrorString(e));
   return CISCVX_OK;
 }
@@ -910,7 +772,7 @@ ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* p, const ciscvx
   ciscvx_status st = check_io(p, io);
   if (st == CISCVX_OK) st = check_vjp(p, vjp, false, workspace, ws_bytes);
   if (st != CISCVX_OK) return st;
-  if (p->any_contract) {  // the two calls in sequence, on io's inputs
+  if (p->any_cpl || p->any_aux) {  // the two calls in sequence, on io's inputs
     st = ciscvx_batch_discretize(p, io, stream);
     if (st != CISCVX_OK) return st;
     ciscvx_batch_vjp_io v = *vjp;
@@ -1063,6 +925,12 @@ ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* p, const ciscvx_bat
   double* part = (double*)workspace;
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
+  // plans with an Eq. (12) model run the linearization and the VJP in turn:
+  // the fused pass is not used, nothing to tune
+  if (p->any_aux) {
+    if (chosen) *chosen = p->tune_fused;
+    return CISCVX_OK;
+  }
   // the split form only where the fused pass has at most one warp per scheduler
   const bool with_split = p->n_items <= 4 * p->sm_count;
   return autotune_slot(p, &p->tune_fused, "|fused", s, [&]() {
@@ -1191,9 +1059,8 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
     if (!p->all_nc0 && (!host_vjp->rho || !dev_vjp->rho)) return set_error(CISCVX_EINVAL, "null rho");
     if (p->max_nsub > MAXSUB_VJP)
       return set_error(CISCVX_EUNSUPPORTED, "VJP supports at most %d substeps", MAXSUB_VJP);
-    if (p->any_aux) return set_error(CISCVX_EUNSUPPORTED, "the VJP is not provided for the Eq. (12) model");
     // the adjoint's partial sums; with coupled instances also their adjoint's scratch
-    const size_t need = p->any_cpl ? contract_ws_offset(p) + p->contract_ws
+    const size_t need = p->any_cpl ? cpl_ws_offset(p) + p->cpl_adj_ws
                                    : sizeof(double) * (p->part_total + 2 * p->pb_total);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 15) != 0)
       return set_error(CISCVX_EINVAL, "16-byte aligned workspace of %zu bytes needed", need);
@@ -1232,11 +1099,16 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
     // compute
     if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_comp, ev_in, 0);
     if (e == cudaSuccess) {
-      if (vjp) e = launch_fused_c(p, common_chunk(p, 0, c, p->tune_fused), dev, &dv, part, ps, pL, i0, i1, t.s_comp);
-      else e = launch_disc_c(p, common_chunk(p, 0, c, p->tune), dev, t.s_comp);
+      if (vjp && !p->any_aux) {
+        e = launch_fused_c(p, common_chunk(p, 0, c, p->tune_fused), dev, &dv, part, ps, pL, i0, i1, t.s_comp);
+      } else {  // (Eq. (12) model: the linearization, then the adjoint, of the chunk)
+        e = launch_disc_c(p, common_chunk(p, 0, c, p->tune), dev, t.s_comp);
+        if (vjp && e == cudaSuccess)
+          e = launch_vjp_c(p, common_chunk(p, 1, c, p->tune), &dv, part, ps, pL, i0, i1, t.s_comp);
+      }
       if (e == cudaSuccess && p->any_cpl)
-        e = run_coupled_range(p, dev, vjp ? &dv : nullptr, vjp ? (char*)workspace + contract_ws_offset(p) : nullptr,
-                              vjp ? ws_bytes - contract_ws_offset(p) : 0, i0, i1, t.s_comp);
+        e = run_coupled_range(p, dev, vjp ? &dv : nullptr, vjp ? (char*)workspace + cpl_ws_offset(p) : nullptr,
+                              vjp ? ws_bytes - cpl_ws_offset(p) : 0, i0, i1, t.s_comp);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_comp, t.s_comp);
     // device -> host: this chunk's outputs

@@ -72,8 +72,8 @@ __device__ __forceinline__ void disc_item(const BatchCommon& c, int item, const 
 }
 
 // Adjoint VJP of work item `item` (its own forward sweep, then the backward
-// sweep), writing the item's partial sums.
-template <typename TP>
+// sweep), writing the item's partial sums.  AUX: as for disc_item.
+template <typename TP, bool AUX = false>
 __device__ __forceinline__ void vjp_item(const BatchCommon& c, int item, const double* __restrict__ X,
                                          const double* __restrict__ U, const double* __restrict__ s,
                                          const double* __restrict__ w, const double* __restrict__ rho,
@@ -100,7 +100,11 @@ __device__ __forceinline__ void vjp_item(const BatchCommon& c, int item, const d
   double* pp = part + I.part + (size_t)k * M.nslot * 2;
   double* psk = ps + I.pb + k * nb;
   double* pLk = pL + I.pb + k * nb;
-  if (B.contact >= 0)
+  if (AUX && M.aux && B.contact >= 0)  // Eq. (12) model
+    vjp_link<TP, true, false, true>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR,
+                                    wi + k * nxt, wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk,
+                                    c.status);
+  else if (B.contact >= 0)
     vjp_link<TP, true>(M, b, g.y, s[I.s + k], Xi + k * nxt, Xi + (k + 1) * nxt, uL, uR, wi + k * nxt,
                        wkm1, rc, gXi + (size_t)k * nxt, gXN, pp, psk, pLk, c.status);
   else

@@ -84,7 +84,7 @@ constexpr int A_PER_LINK = 10, A_PER_FOOT = 5, A_PER_CROSS = 7, B_CROSS_FIXED = 
 // into the packed arrays.
 struct DevInst {
   int model, N, nsub;
-  int contract;                   // 1: the VJP runs outside the per-link adjoint kernel (coupled links: the coupled adjoint; Eq. (12) state: linearize-and-contract)
+  int contract;                   // 1: the VJP runs outside the per-link adjoint kernel (coupled links: the coupled adjoint)
   long long x, u, s, a, b, v, p;  // element offsets: X/gX, U/gU, s/gs, A, Bm/Bp, S/defect/w, penalty/rho
   long long part, pb;             // VJP workspace offsets: per-input partials, per-(interval, link) partials
 };
@@ -254,7 +254,7 @@ cudaError_t launch_discretize(const DevModel* dM, int nb, int N, int nsub, int p
 cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, int N, int nsub,
                        int prec, int layout, const double* X, const double* U, const double* s,
                        const double* w, const double* rho, double* gX, double* gU, double* gs,
-                       double* L, void* ws, unsigned* status, cudaStream_t st);
+                       double* L, void* ws, unsigned* status, bool aux, cudaStream_t st);
 size_t vjp_workspace_bytes(int nb, int nu, int nslot, int N, int layout);
 // Node constraints (node.cu).
 struct NodeParams {
@@ -271,7 +271,7 @@ cudaError_t launch_node(const DevModel& Mh, const DevModel* dM, int n, const dou
 // without coupled links and without the Eq. (12) state.
 void model_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int32_t* bc);
 // The affine term z_k = x~(1) - A x~_k - B- u_L - B+ u_R - S s_k from the
-// dense outputs (contract.cu), for the models whose kernels do not form it.
+// dense outputs (affine_z.cu), for the models whose kernels do not form it.
 cudaError_t launch_affine_z(const DevModel& M, int N, int prec, int layout, const double* X, const double* U,
                             const double* s, const void* A, const void* Bm, const void* Bp, const void* S,
                             const double* defect, double* z, cudaStream_t st);

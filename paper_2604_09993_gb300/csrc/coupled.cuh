@@ -134,25 +134,4 @@ cudaError_t launch_coupled_vjp(const CplTab& T, long N, int nsub, int prec, int 
                                double* gX, double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
                                unsigned* status, cudaStream_t st);
 
-// VJP by linearize-and-contract (contract.cu): workspace bytes for a chunk of
-// n intervals, and the chunked launch (T null for per-link models).
-size_t contract_bytes(const DevModel& M, const CplTab* T, long n, int nsub, int prec);
-// Batched linearize-and-contract, the contraction and L of many instances
-// whose dense blocks are already in a workspace (batch plans): inst gives each
-// instance's offsets into X/U/s/w/rho/gX/gU/gs, inst_ws its blocks' offsets
-// into A/Bm/Bp/S/defect/penalty; entries are (instance, k) of one model.
-cudaError_t launch_contract_batch(const DevModel& Mh, const DevInst* inst, const DevInst* inst_ws,
-                                  const int2* entries, long n_entries, int prec, int layout, const void* A,
-                                  const void* Bm, const void* Bp, const void* S, const double* w,
-                                  const double* rho, double* gX, double* gU, double* gs, cudaStream_t st);
-// L of each listed instance: sum_k w_k . defect_k + rho_k . penalty_k (fixed order).
-cudaError_t launch_contract_L_batch(const DevModel* const* models, const DevInst* inst, const DevInst* inst_ws,
-                                    const int* list, int n_list, const double* defect, const double* penalty,
-                                    const double* w, const double* rho, double* L, cudaStream_t st);
-cudaError_t launch_contract_vjp(const DevModel& Mh, const DevModel* dM, const CplTab* T, int N,
-                                int nsub, int prec, int layout, const double* X, const double* U,
-                                const double* s, const double* w, const double* rho, double* gX,
-                                double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
-                                unsigned* status, cudaStream_t st);
-
 }  // namespace ciscvx

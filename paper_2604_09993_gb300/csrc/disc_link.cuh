@@ -261,8 +261,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   constexpr bool F32 = std::is_same<TP, float>::value;
   // CROSS: the link carries a contact of the Eq. (12) model (see the header
   // comment of input_cross); the kernels form no z for it (callers form it
-  // from the dense outputs) and no checkpoints (its VJP is
-  // linearize-and-contract).
+  // from the stored outputs) and no checkpoints (its VJP runs its own forward
+  // sweep: vjp_link with CROSS).
   static_assert(!(CROSS && CK), "Eq. (12) model: no checkpoints");
   constexpr bool cross = FOOT && CROSS;
   const unsigned amask = __activemask();  // lanes running this link (they stay converged)

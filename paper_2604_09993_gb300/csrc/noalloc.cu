@@ -26,11 +26,10 @@
 // before reading it, so nothing needs clearing between calls.
 //
 // Sizing: the request is sized with ciscvx_discretize_workspace_size.  For
-// models whose VJP is the adjoint kernel (per-link models with one penalty
-// state per contact) the scratch is one fixed size for N.  For models whose
-// VJP is linearize-and-contract (coupled links, Eq. (12) auxiliary state) the
-// work runs in chunks of intervals that fit the scratch, so only the minimum
-// (a chunk of up to 32 intervals) has to fit.
+// models whose VJP is the per-link adjoint kernel (either auxiliary model)
+// the scratch is one fixed size for N.  For models with coupled links the
+// coupled adjoint runs in chunks of intervals that fit the scratch, so only
+// the minimum (a chunk of up to 32 intervals) has to fit.
 #include <mutex>
 
 #include "common.cuh"

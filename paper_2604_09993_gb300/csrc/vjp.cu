@@ -44,7 +44,10 @@ size_t vjp_workspace_bytes(int nb, int nu, int nslot, int N, int layout) {
   return sizeof(double) * ((size_t)N * nslot * 2 + 2 * (size_t)N * nb + nblk);
 }
 
-template <typename TP>
+// AUX: the model uses the Eq. (12) auxiliary state (its foot links take the
+// CROSS adjoint; a separate instantiation keeps those registers out of the
+// common kernel).
+template <typename TP, bool AUX>
 __global__ void __launch_bounds__(128) k_vjp(const DevModel* __restrict__ Mp, int N, int nsub,
                                              int layout, const double* __restrict__ X,
                                              const double* __restrict__ U,
@@ -68,7 +71,11 @@ __global__ void __launch_bounds__(128) k_vjp(const DevModel* __restrict__ Mp, in
   const double* wkm1 = (k > 0) ? w + (k - 1) * nxt : nullptr;
   double* gXN = (k == N - 1) ? gX + (size_t)N * nxt : nullptr;
   double* part = ws.part + (size_t)k * M.nslot * 2;
-  if (B.contact >= 0)
+  if (AUX && B.contact >= 0)
+    vjp_link<TP, true, false, true>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL, uR,
+                                    w + k * nxt, wkm1, rc, gX + (size_t)k * nxt, gXN, part,
+                                    ws.ps + k * nb, ws.pL + k * nb, status);
+  else if (B.contact >= 0)
     vjp_link<TP, true>(M, b, nsub, s[k], X + k * nxt, X + (k + 1) * nxt, uL, uR, w + k * nxt,
                        wkm1, rc, gX + (size_t)k * nxt, gXN, part, ws.ps + k * nb, ws.pL + k * nb,
                        status);
@@ -143,18 +150,21 @@ __global__ void __launch_bounds__(FIN_THREADS) k_vjp_L(int nblk, const double* _
 cudaError_t launch_vjp(const DevModel* dM, int nb, int nxt, int nu, int nslot, int N, int nsub,
                        int prec, int layout, const double* X, const double* U, const double* s,
                        const double* w, const double* rho, double* gX, double* gU, double* gs,
-                       double* L, void* ws_ptr, unsigned* status, cudaStream_t st) {
+                       double* L, void* ws_ptr, unsigned* status, bool aux, cudaStream_t st) {
   (void)nxt;
   VjpWs ws = vjp_ws_split(ws_ptr, nb, nslot, N);
   const long warps = (long)((N + 31) / 32) * nb;
   const int threads = single_cta_threads(warps);
   const long blocks = (warps * 32 + threads - 1) / threads;
-  if (prec == CISCVX_FP64)
-    k_vjp<double><<<(unsigned)blocks, threads, 0, st>>>(dM, N, nsub, layout, X, U, s, w, rho, gX,
-                                                        ws, status);
-  else
-    k_vjp<float><<<(unsigned)blocks, threads, 0, st>>>(dM, N, nsub, layout, X, U, s, w, rho, gX,
-                                                       ws, status);
+#define CISCVX_KVJP(TP, AUX)                                                                     \
+  k_vjp<TP, AUX><<<(unsigned)blocks, threads, 0, st>>>(dM, N, nsub, layout, X, U, s, w, rho, gX, ws, \
+                                                       status)
+  if (prec == CISCVX_FP64) {
+    if (aux) CISCVX_KVJP(double, true); else CISCVX_KVJP(double, false);
+  } else {
+    if (aux) CISCVX_KVJP(float, true); else CISCVX_KVJP(float, false);
+  }
+#undef CISCVX_KVJP
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (nu > 0) {

@@ -1,9 +1,10 @@
-"""Batched VJPs of plans that hold instances whose VJP is linearize-and-contract
-(the Eq. (12) auxiliary state, coupled links) next to default-model instances
-(the adjoint kernel).  Every instance's gX, gU, gs and L is compared with the
-oracle's Phi-contracted gradient (FP64 1e-10, FP32-Phi 1e-4 for the
-gradients; L in FP64), and the fused entry point gives the same numbers as
-the two calls."""
+"""Batched VJPs of plans that mix the default model, the Eq. (12) auxiliary
+state (the per-link adjoint kernel with its CROSS foot links) and coupled
+links (the coupled path's reverse-mode adjoint, one instance after another).
+Every instance's gX, gU, gs and L is compared with the oracle's
+Phi-contracted gradient (FP64 1e-10, FP32-Phi 1e-4 for the gradients; L in
+FP64), the fused entry point gives the same numbers as the two calls, and the
+pipelined host executor those of the device path."""
 import numpy as np
 import pytest
 
@@ -89,24 +90,44 @@ def test_fused_entry_point_with_contract_instances(env):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
-def test_batched_and_per_instance_contract_paths_agree(env, precision, tol):
-    """A workspace of the full size takes the batched contract pass, one of the
-    minimum size the per-instance one; both meet the oracle and agree."""
+def test_run_host_with_eq12_and_coupled_instances(env, precision, tol):
+    """ciscvx_batch_run_host with the VJP on such a mixed batch (Eq. (12)
+    instances: linearization then adjoint per chunk; coupled instances: their
+    own path) equals the device path, and the oracle."""
     torch, oracle, api = env
     dev = torch.device("cuda:0")
     robots, probs, midx = _batch(43, 14)
     models = [api.Model(r) for r in robots]
     plan = api.BatchPlan(models, midx, [q.N for q in probs], [q.n_sub for q in probs], precision=precision)
     lo, hi = plan.vjp_workspace_sizes()
-    assert hi > lo
+    assert lo == hi  # no dense blocks: one scratch size
     X, U, s, w, rho = _packed(torch, plan, probs, dev)
-    g_full = plan.discretize_vjp(X, U, s, w, rho, workspace=torch.empty(hi, dtype=torch.uint8, device=dev))
-    g_min = plan.discretize_vjp(X, U, s, w, rho, workspace=torch.empty(lo, dtype=torch.uint8, device=dev))
+    ws = torch.empty(lo, dtype=torch.uint8, device=dev)
+    out_d, g_d = plan.discretize_and_vjp(X, U, s, w, rho, workspace=ws)
     plan.sync_status()
+    out_d = {k: v.clone() for k, v in out_d.items()}
+    g_d = {k: v.clone() for k, v in g_d.items()}
+    pin = lambda v: v.cpu().pin_memory()  # noqa: E731
+    host_in = {"X": pin(X), "U": pin(U), "s": pin(s)}
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out_d.items()}
+    hv = {"X": host_in["X"], "U": host_in["U"], "s": host_in["s"], "w": pin(w), "rho": pin(rho)}
+    hv.update({k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in g_d.items()})
+    dev_in = {k: torch.empty_like(v) for k, v in (("X", X), ("U", U), ("s", s))}
+    dev_out = {k: torch.empty_like(v) for k, v in out_d.items()}
+    dv = {"X": dev_in["X"], "U": dev_in["U"], "s": dev_in["s"], "w": torch.empty_like(w),
+          "rho": torch.empty_like(rho)}
+    dv.update({k: torch.empty_like(v) for k, v in g_d.items()})
+    plan.run_host(host_in, host_out, dev_in, dev_out, n_chunks=3, host_vjp=hv, dev_vjp=dv, workspace=ws)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    for k in ("defect", "penalty"):
+        assert block_err(host_out[k].numpy(), out_d[k].cpu().numpy()) <= 1e-13, k
+    for k in ("A", "Bm", "Bp", "S"):
+        assert block_err(host_out[k].double().numpy(), out_d[k].double().cpu().numpy()) <= 1e-6, k
     for k in ("gX", "gU", "gs", "L"):
-        a, b = g_full[k].cpu().numpy(), g_min[k].cpu().numpy()
-        assert block_err(a, b) <= (1e-12 if precision == "fp64" else 1e-5), (k, block_err(a, b))
-    host = {k: v.cpu().numpy() for k, v in g_full.items()}
+        e = block_err(hv[k].numpy(), g_d[k].cpu().numpy())
+        assert e <= (1e-12 if precision == "fp64" else 1e-5), (k, e)
+    host = {k: hv[k].numpy() for k in ("gX", "gU", "gs", "L")}
     for i, q in enumerate(probs):
         rX, rU, rs, rL = oracle.vjp(q.robot.as_dict(), q.X, q.U, q.s, q.w, q.rho, q.n_sub)
         assert block_err(plan.unpack(host["gX"], "X", i, q.X.shape), rX) <= tol, i

@@ -1,7 +1,8 @@
 """GPU parity of the full Eq. (12) auxiliary state (CISCVX_AUX_CROSS) against
 the FP64 oracle through the C ABI: single-instance and batched linearization,
 both precisions and both control layouts, mixed batches of the two auxiliary
-models, feasible inputs, the linearize-and-contract VJP, and the affine term
+models, feasible inputs, the reverse-mode adjoint VJP (against the oracle's
+Phi-contracted gradient and against central differences), and the affine term
 z formed from the dense and from the compact outputs.
 Tolerances as for the default model (FP64 1e-10; FP32-Phi blocks 1e-4,
 defect and penalty 1e-10)."""
@@ -180,8 +181,9 @@ def test_cross_node_constraints(env):
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
 @pytest.mark.parametrize("layout", ["node", "interval"])
 def test_cross_vjp_matches_oracle(env, precision, tol, layout):
-    """The VJP of this model is linearize-and-contract: against the oracle's
-    Phi-contracted gradient, with a workspace of the minimum size (chunks of 32)."""
+    """The reverse-mode adjoint of this model against the oracle's
+    Phi-contracted gradient; its scratch is the default model's (the per-link
+    partial sums), one size whatever n_sub and the precision."""
     torch, oracle, api = env
     dev = torch.device("cuda:0")
     p = _problem("biped", 17, 75, 3)
@@ -192,7 +194,7 @@ def test_cross_vjp_matches_oracle(env, precision, tol, layout):
     U = p.U if layout == "node" else p.U_interval()
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     lo, hi = api.discretize_workspace_size(m, p.N, p.n_sub, precision, api.OP_VJP, layout)
-    assert lo < hi
+    assert lo == hi == api.workspace_size(m, api.OP_VJP, p.N, layout)
     ws = torch.empty(lo, dtype=torch.uint8, device=dev)
     gX, gU, gs, L = api.discretize_vjp(m, t(p.X), t(U), t(p.s), t(w), t(rho), p.n_sub, precision,
                                        layout, workspace=ws)
@@ -201,6 +203,45 @@ def test_cross_vjp_matches_oracle(env, precision, tol, layout):
     for g, r, nm in ((gX, rX, "gX"), (gU, rU, "gU"), (gs, rs, "gs")):
         assert block_err(g.cpu().numpy(), r) <= tol, (nm, block_err(g.cpu().numpy(), r))
     assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))
+
+
+def test_cross_vjp_central_differences(env):
+    """The adjoint's gradient of L = sum_k w_k . defect_k + rho_k . penalty_k
+    against central differences (h = 1e-6) of the oracle's flow map, every
+    entry of X, U and s, on a two-interval Eq. (12) biped."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    p = _problem("biped", 21, 2, 3)
+    rng = np.random.default_rng(22)
+    R = p.robot.as_dict()
+    m = api.Model(p.robot)
+    nxt, nc = m.nxt, m.nc
+    w = rng.standard_normal((p.N, nxt))
+    rho = np.full((p.N, nc), 10.0)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    got = api.discretize_vjp(m, t(p.X), t(p.U), t(p.s), t(w), t(rho), p.n_sub, "fp64")
+    api.sync_status(m)
+    got = [g.cpu().numpy() for g in got[:3]]
+    pen = slice(nxt - nc, nxt)  # the path-penalty rows follow the four cross rows per contact
+
+    def L(X, U, s):
+        tot = 0.0
+        for k in range(p.N):
+            x1 = oracle.flow(R, p.n_sub, X[k], U[k], U[k + 1], s[k])
+            tot += w[k] @ (x1 - X[k + 1]) + rho[k] @ (x1[pen] - X[k, pen])
+        return tot
+
+    e = 1e-6
+    X, U, s = p.X.copy(), p.U.copy(), p.s.copy()
+    for arr, g in ((X, got[0]), (U, got[1]), (s, got[2])):
+        flat, gf = arr.reshape(-1), g.reshape(-1)
+        for i in range(flat.size):
+            v = flat[i]
+            flat[i] = v + e; lp = L(X, U, s)
+            flat[i] = v - e; lm = L(X, U, s)
+            flat[i] = v
+            fd = (lp - lm) / (2 * e)
+            assert abs(fd - gf[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gf[i])
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])

@@ -8,9 +8,9 @@ memory held inside the library.  Here it is called twice in a row, through
 the C ABI and through the Python wrapper, and both results are checked against
 ciscvx_discretize_vjp with a caller workspace, within the tolerances the parity
 tests use: the default per-link model in FP64 and FP32-Phi, the Eq. (12)
-auxiliary-state model (linearize-and-contract) and a model with coupled links
-(the reverse-mode adjoint of the coupled path), both chunked to what the
-static array holds.  It must pass alone in a
+auxiliary-state model (the per-link adjoint, whose scratch does not depend on
+n_sub) and a model with coupled links (the reverse-mode adjoint of the
+coupled path, chunked to what the static array holds).  It must pass alone in a
 fresh process and after the other tests, so it builds and loads everything it
 needs itself.  This file is collected last.
 """
@@ -75,8 +75,10 @@ def test_static_scratch_vjp_matches_workspace_vjp_twice(env, kind, precision):
     X, U, s, w, rho = t(p.X), t(p.U), t(p.s), t(p.w), t(p.rho)
     lo, hi = api.discretize_workspace_size(m, p.N, p.n_sub, precision, api.OP_VJP)
     assert lo <= api.STATIC_SCRATCH_BYTES
-    if kind != "cheetah7":  # chunked: more than one chunk of the static array
+    if kind == "cheetah7-paper":  # chunked: more than one chunk of the static array
         assert hi > api.STATIC_SCRATCH_BYTES
+    else:  # the per-link adjoint: one size
+        assert lo == hi == api.workspace_size(m, api.OP_VJP, p.N)
     ref = api.discretize_vjp(m, X, U, s, w, rho, p.n_sub, precision)
     tol = TOL_FP64 if precision == "fp64" else TOL_FP32_PHI
     for _ in range(2):
