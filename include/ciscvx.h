@@ -242,6 +242,13 @@ ciscvx_status ciscvx_model_dims(const ciscvx_model* model, int* n_x, int* n_y, i
  *      a torque or is phi_t or gamma, then (c0,phi_n) (c2,gamma) (c3,phi_t)
  *      (c3,phi_n).  (gamma exerts no force: it has only the (y,gamma),
  *      (c1,gamma) and (c2,gamma) entries.)
+ * A model with coupled links (joint forces eliminated, RKF45 or the
+ * sinusoidal surface) has this pattern instead, column-major: for each
+ * column c of A in order, every row r (ascending) when c is integrated by
+ * the coupled path (theta and omega of every link, every state of a link
+ * with a contact), else (c - 3n_b, c) (c) for the linear velocity of a link
+ * without a contact and (c,c) for its position and for the auxiliary rows;
+ * B: for each input q in order, every row.
  * Call with NULL arrays to get the counts; then a_row/a_col receive nnz_A
  * and b_row/b_col nnz_B int32 indices (host memory, caller-owned).  Any of
  * nnz_a, nnz_b may be NULL.  Errors: as ciscvx_model_create for the
@@ -315,17 +322,22 @@ ciscvx_status ciscvx_discretize(const ciscvx_model* model, int N, int n_sub,
 
 /* ciscvx_discretize with compact A, Bm, Bp (CISCVX_OUT_COMPACT): A [N][nnz_A],
  * Bm/Bp [N][nnz_B] in the precision's dtype, values in ciscvx_model_pattern's
- * order; every other argument as for ciscvx_discretize.  The values are those
- * ciscvx_discretize stores at the pattern's positions (same arithmetic), and
- * no structural zero is written.  For the Eq. (12) model z is formed by a
- * post-pass over the compact values and the pattern by rows.  Errors: as
- * ciscvx_discretize, and EUNSUPPORTED for a model with coupled links (its
- * blocks have no sparse pattern to exploit in the coupled rows). */
+ * order; every other argument as for ciscvx_discretize (workspace: needed by a
+ * model with coupled links only, as there; may be NULL otherwise).  The values
+ * are those ciscvx_discretize stores at the pattern's positions (same
+ * arithmetic), and no structural zero is written.  For a model with coupled
+ * links the pattern is column-major: the columns the coupled path integrates
+ * are full (every row), the closed-form ones keep their one or two entries
+ * (A e_p = e_p, A e_v = e_v + s e_p for a link without a contact, A e_y =
+ * e_y), and B-/B+ are full, column by column.  For the Eq. (12) model and
+ * for coupled links z is formed by a post-pass over the compact values and
+ * the pattern by rows.  Errors: as ciscvx_discretize. */
 ciscvx_status ciscvx_discretize_compact(const ciscvx_model* model, int N, int n_sub,
                                         ciscvx_precision precision, ciscvx_u_layout layout,
                                         const double* X, const double* U, const double* s,
                                         void* A, void* Bm, void* Bp, void* S, double* defect,
-                                        double* penalty, double* z, void* stream);
+                                        double* penalty, double* z, void* workspace,
+                                        size_t ws_bytes, void* stream);
 
 /* Vector-Jacobian product of L = sum_k w_k . defect_k + sum_k rho_k . penalty_k
  * (defect and penalty as above) with respect to X, U and s, by the discrete
@@ -756,8 +768,7 @@ typedef struct {
   const double* scale_gam; const double* offset_gam;  /* [n_c] */
   /* layout of the A, Bm, Bp inputs of ciscvx_socp_fill: CISCVX_OUT_DENSE, or
    * CISCVX_OUT_COMPACT (their structural nonzeros in ciscvx_model_pattern
-   * order, as ciscvx_discretize_compact writes them; models with a pattern
-   * only) */
+   * order, as ciscvx_discretize_compact writes them) */
   int phi_format;
 } ciscvx_socp_params;
 

@@ -182,7 +182,7 @@ def load(path: str | None = None):
                                      ctypes.POINTER(_SocpOutputs), _vp]
     lib.ciscvx_discretize_compact.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
-                                              _vp, _vp, _vp]
+                                              _vp, _vp, _vp, ctypes.c_size_t, _vp]
     lib.ciscvx_discretize_vjp_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                                  _vp, _vp, _vp]
@@ -362,6 +362,19 @@ def discretize_workspace_size(model: Model, N: int, n_sub: int, precision: str =
 DISCRETIZE_WS_CAP = 2 << 30
 
 
+def _coupled_workspace(model: Model, N: int, n_sub: int, precision: str, layout: str, workspace, dev):
+    """The scratch of a coupled model's linearization: the given one, else one of
+    min(full size, DISCRETIZE_WS_CAP) bytes (at least the minimum); None for
+    the other models."""
+    import torch
+    if not model.coupled:
+        return None
+    if workspace is None:
+        lo, hi = discretize_workspace_size(model, N, n_sub, precision, OP_DISCRETIZE, layout)
+        workspace = torch.empty(max(lo, min(hi, DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+    return workspace
+
+
 def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layout: str = "node",
                want_z: bool = False, out: dict | None = None, workspace=None):
     """ciscvx_discretize on device tensors.  Returns dict A, Bm, Bp, S, defect, penalty (, z).
@@ -385,24 +398,22 @@ def discretize(model: Model, X, U, s, n_sub: int, precision: str = "fp64", layou
         }
         if want_z:
             out["z"] = torch.empty((N, nxt), dtype=f64, device=dev)
-    ws_bytes = 0
-    if model.coupled:
-        lo, hi = discretize_workspace_size(model, N, n_sub, precision, OP_DISCRETIZE, layout)
-        if workspace is None:
-            workspace = torch.empty(max(lo, min(hi, DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
-        ws_bytes = workspace.numel() * workspace.element_size()
+    workspace = _coupled_workspace(model, N, n_sub, precision, layout, workspace, dev)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(load().ciscvx_discretize(
         model.handle, int(N), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X), _ptr(U),
         _ptr(s), _ptr(out["A"]), _ptr(out["Bm"]) if nu else None, _ptr(out["Bp"]) if nu else None,
         _ptr(out["S"]), _ptr(out["defect"]), _ptr(out["penalty"]) if nc else None,
-        _ptr(out.get("z")), _ptr(workspace) if model.coupled else None, ws_bytes, _stream()))
+        _ptr(out.get("z")), _ptr(workspace) if workspace is not None else None, ws_bytes, _stream()))
     return out
 
 
 def discretize_compact(model: Model, X, U, s, n_sub: int, precision: str = "fp64",
-                       layout: str = "node", want_z: bool = False, out: dict | None = None):
+                       layout: str = "node", want_z: bool = False, out: dict | None = None,
+                       workspace=None):
     """ciscvx_discretize_compact: as discretize, with A (N, nnz_a) and Bm/Bp
-    (N, nnz_b) holding the structural nonzeros in Model.pattern() order."""
+    (N, nnz_b) holding the structural nonzeros in Model.pattern() order.  A
+    model with coupled links needs scratch as for discretize."""
     import torch
     f64 = torch.float64
     _need(X, "X", f64); _need(U, "U", f64); _need(s, "s", f64)
@@ -422,11 +433,13 @@ def discretize_compact(model: Model, X, U, s, n_sub: int, precision: str = "fp64
         if want_z:
             out["z"] = torch.empty((N, nxt), dtype=f64, device=dev)
     nzb = model.nnz_b > 0
+    workspace = _coupled_workspace(model, N, n_sub, precision, layout, workspace, dev)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(load().ciscvx_discretize_compact(
         model.handle, int(N), int(n_sub), PRECISION[precision], LAYOUT[layout], _ptr(X), _ptr(U),
         _ptr(s), _ptr(out["A"]), _ptr(out["Bm"]) if nzb else None, _ptr(out["Bp"]) if nzb else None,
         _ptr(out["S"]), _ptr(out["defect"]), _ptr(out["penalty"]) if nc else None,
-        _ptr(out.get("z")), _stream()))
+        _ptr(out.get("z")), _ptr(workspace) if workspace is not None else None, ws_bytes, _stream()))
     return out
 
 

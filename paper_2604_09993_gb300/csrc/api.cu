@@ -241,6 +241,11 @@ ciscvx_status build_tables(const ciscvx_model_desc* d, DevModel& M) {
   }
   M.nnzA = aoff;
   M.nnzB = boff;
+  if (cpl_needed(M)) {  // coupled links: the column-major pattern of fill_pattern
+    M.nnzA = 0;
+    for (int c = 0; c < M.nxt; ++c) M.nnzA += cpl_col_nnz(M, c);
+    M.nnzB = M.nxt * M.nu;
+  }
   node_symbolic(M);
   return CISCVX_OK;
 }
@@ -267,8 +272,22 @@ ciscvx_status check_desc(const ciscvx_model_desc* desc) {
 }
 
 // The compact pattern of the built tables, in the order the kernels store it
-// (see common.cuh); the arrays may be null.
+// (see common.cuh; for a model with coupled links column-major, see
+// cpl_col_kind); the arrays may be null.
 void fill_pattern(const DevModel& M, int32_t* ar, int32_t* ac, int32_t* br, int32_t* bc) {
+  if (cpl_needed(M)) {
+    int j = 0;
+    for (int c = 0; c < M.nxt; ++c) {
+      const int kind = cpl_col_kind(M, c);
+      auto put = [&](int r) { if (ar) ar[j] = r; if (ac) ac[j] = c; ++j; };
+      if (kind == 0) for (int r = 0; r < M.nxt; ++r) put(r);
+      else if (kind == 2) { put(c - 3 * M.nb); put(c); }
+      else put(c);
+    }
+    for (int q = 0, e = 0; q < M.nu; ++q)
+      for (int r = 0; r < M.nxt; ++r, ++e) { if (br) br[e] = r; if (bc) bc[e] = q; }
+    return;
+  }
   const int nb = M.nb;
   for (int b = 0; b < nb; ++b) {
     const DevBody& B = M.body[b];
@@ -386,7 +405,7 @@ ciscvx_status ciscvx_model_create(const ciscvx_model_desc* desc, ciscvx_model** 
   if (e == cudaSuccess) e = cudaMalloc(&m->status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(unsigned));
-  if (e == cudaSuccess && m->host.aux && !m->cpl) {
+  if (e == cudaSuccess && (m->host.aux || m->cpl)) {
     // the compact pattern by rows, for z with compact outputs
     const DevModel& M = m->host;
     std::vector<int32_t> ar(M.nnzA), ac(M.nnzA), br(M.nnzB), bc(M.nnzB);
@@ -442,8 +461,6 @@ ciscvx_status ciscvx_model_pattern(const ciscvx_model_desc* desc, int* nnz_a, in
   DevModel* M = new (std::nothrow) DevModel;
   if (!M) return fail(CISCVX_ENOMEM, "host allocation failed");
   st = build_tables(desc, *M);
-  if (st == CISCVX_OK && cpl_needed(*M))
-    st = fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for models with coupled links");
   if (st == CISCVX_OK) {
     if (nnz_a) *nnz_a = M->nnzA;
     if (nnz_b) *nnz_b = M->nnzB;
@@ -557,13 +574,29 @@ ciscvx_status ciscvx_discretize_compact(const ciscvx_model* m, int N, int n_sub,
                                         ciscvx_precision precision, ciscvx_u_layout layout,
                                         const double* X, const double* U, const double* s,
                                         void* A, void* Bm, void* Bp, void* S, double* defect,
-                                        double* penalty, double* z, void* stream) {
+                                        double* penalty, double* z, void* workspace, size_t ws_bytes,
+                                        void* stream) {
   ciscvx_status st = check_common(m, N, n_sub, precision, layout, X, U, s);
   if (st != CISCVX_OK) return st;
   if (!A || !S || !defect) return fail(CISCVX_EINVAL, "null output array");
   if (m->host.nnzB > 0 && (!Bm || !Bp)) return fail(CISCVX_EINVAL, "null B- / B+");
   if (m->host.nc > 0 && !penalty) return fail(CISCVX_EINVAL, "null penalty");
-  if (m->cpl) return fail(CISCVX_EUNSUPPORTED, "compact outputs are not provided for models with coupled links");
+  if (m->cpl) {  // the coupled path writing the column-major compact layout
+    const size_t per = cpl_interval_bytes(*m->cpl, n_sub, precision);
+    const size_t need = per * (size_t)std::min(N, 32);
+    if (!workspace || ws_bytes < need)
+      return fail(CISCVX_EINVAL, "workspace of at least %zu bytes needed (got %zu)", need, ws_bytes);
+    if (((uintptr_t)workspace & 15) != 0) return fail(CISCVX_EINVAL, "workspace must be 16-byte aligned");
+    const long chunk = (long)std::min<size_t>(ws_bytes / per, (size_t)N);
+    cudaError_t e = launch_coupled(*m->cpl, N, n_sub, precision, layout, X, U, s, A, Bm, Bp, S, defect,
+                                   penalty, workspace, chunk, m->status, (cudaStream_t)stream, nullptr,
+                                   nullptr, true);
+    if (e == cudaSuccess && z)
+      e = launch_affine_z_compact(m->host, N, precision, layout, X, U, s, A, Bm, Bp, S, defect, m->zpat, z,
+                                  (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "coupled discretize launch");
+    return ok();
+  }
   // the Eq. (12) model's kernels do not form z: a post-pass over the compact
   // outputs and the pattern by rows does
   const bool post_z = m->host.aux && z;

@@ -135,7 +135,7 @@ struct ciscvx_batch_plan {
   bool compact = false;  // CISCVX_OUT_COMPACT
   bool all_nu0 = true, all_nc0 = true;
   bool any_aux = false;  // some model uses the Eq. (12) auxiliary state (no fused pass: its VJP runs apart)
-  bool any_cpl = false;  // some model has coupled links (coupled path; no VJP, no compact outputs)
+  bool any_cpl = false;  // some model has coupled links (coupled path, its own adjoint)
   // coupled-path groups: instances of one coupled model with one n_sub, as
   // (instance, k) entries; one stage-data workspace shared in stream order
   struct CplGroup {
@@ -368,7 +368,7 @@ cudaError_t launch_cpl_groups(ciscvx_batch_plan* p, const ciscvx_batch_io* io, c
     const long chunk = (long)std::min<size_t>((size_t)g.count, p->cpl_ws_bytes / per);
     cudaError_t e = launch_coupled(T, g.count, g.nsub, p->prec, p->layout, io->X, io->U, io->s, io->A,
                                    io->Bm, io->Bp, io->S, io->defect, io->penalty, p->d_cpl_ws, chunk,
-                                   p->d_status, st, p->d_cpl_entries + g.first, p->d_inst);
+                                   p->d_status, st, p->d_cpl_entries + g.first, p->d_inst, p->compact);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -554,11 +554,6 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (tune && !tune_ok(*tune)) return set_error(CISCVX_EINVAL, "invalid ciscvx_tune");
   for (int m = 0; m < n_models; ++m)
     if (!models[m]) return set_error(CISCVX_EINVAL, "null model %d", m);
-  for (int m = 0; m < n_models; ++m)
-    if (models[m]->cpl && format == CISCVX_OUT_COMPACT)
-      return set_error(CISCVX_EUNSUPPORTED,
-                       "model %d has coupled links (eliminated joint forces, terrain or RKF45): "
-                       "compact outputs are not provided for it", m);
   for (int i = 0; i < n_inst; ++i) {
     if (model_idx[i] < 0 || model_idx[i] >= n_models)
       return set_error(CISCVX_EINVAL, "instance %d: model index %d out of range", i, model_idx[i]);
@@ -1016,7 +1011,7 @@ cudaError_t run_coupled_range(ciscvx_batch_plan* p, const ciscvx_batch_io* io, c
     char* S = (char*)io->S + I.v * el;
     e = launch_coupled(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr, io->s + I.s,
                        A, Bm, Bp, S, io->defect + I.v, nc ? io->penalty + I.p : nullptr, p->d_cpl_ws, chunk,
-                       p->d_status, st);
+                       p->d_status, st, nullptr, nullptr, p->compact);
     if (e == cudaSuccess && vjp)
       e = launch_coupled_vjp(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
                              io->s + I.s, vjp->w + I.v, nc ? vjp->rho + I.p : nullptr, vjp->gX + I.x,

@@ -82,6 +82,7 @@ struct Cst<float> {
 
 // Where interval e's data live: for a single instance (entries null) interval
 // e itself; in a batch, entry e = (instance, k) of the batch's instance table.
+// a_stride: elements of A per interval (n_x~^2 dense, colptr[n_x~] compact).
 struct IvAddr {
   const double *x0, *x1, *uL, *uR;
   long long s, a, b, v, p;  // element offsets: s, A, Bm/Bp, S/defect, penalty
@@ -89,7 +90,7 @@ struct IvAddr {
 
 __device__ __forceinline__ IvAddr iv_addr(long e, int nxt, int nu, int nc, int layout,
                                           const double* X, const double* U, const int2* entries,
-                                          const DevInst* inst) {
+                                          const DevInst* inst, long long a_stride) {
   long long k = e, xo, uo;
   IvAddr r;
   if (entries) {
@@ -99,7 +100,7 @@ __device__ __forceinline__ IvAddr iv_addr(long e, int nxt, int nu, int nc, int l
     xo = I.x + k * nxt;
     uo = I.u + (layout == 0 ? k : 2 * k) * nu;
     r.s = I.s + k;
-    r.a = I.a + k * nxt * nxt;
+    r.a = I.a + k * a_stride;
     r.b = I.b + k * nxt * nu;
     r.v = I.v + k * nxt;
     r.p = I.p + k * nc;
@@ -107,7 +108,7 @@ __device__ __forceinline__ IvAddr iv_addr(long e, int nxt, int nu, int nc, int l
     xo = k * nxt;
     uo = (layout == 0 ? k : 2 * k) * nu;
     r.s = k;
-    r.a = k * nxt * nxt;
+    r.a = k * a_stride;
     r.b = k * nxt * nu;
     r.v = k * nxt;
     r.p = k * nc;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
                                                     double* __restrict__ defect,
                                                     double* __restrict__ penalty, unsigned* status,
                                                     const int2* __restrict__ entries,
-                                                    const DevInst* __restrict__ inst) {
+                                                    const DevInst* __restrict__ inst, int cmp) {
   using Sc = Scheme<SCH>;
   constexpr int NS = Sc::S;
   extern __shared__ double smem1[];
@@ -141,7 +142,8 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
   double* sm = smem1 + threadIdx.x;
   const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
   const int nl = M.nlive;
-  const IvAddr ad = iv_addr(i0 + t, nxt, nu, nc, layout, X, U, entries, inst);
+  const IvAddr ad = iv_addr(i0 + t, nxt, nu, nc, layout, X, U, entries, inst,
+                            cmp ? (long long)M.colptr[nxt] : (long long)nxt * nxt);
   const double* uL = ad.uL;
   const double* uR = ad.uR;
   const double sk = s[ad.s];
@@ -436,7 +438,14 @@ __global__ void __launch_bounds__(32) k_cpl_nominal(const __grid_constant__ CplT
   // (not written by the adjoint's forward pass, which has no A)
   if (!A) return;
   TP* Ak = A + ad.a;
+  // compact: the column's one or two entries (row r2 < c first)
   auto unit_col = [&](int c, int r2, TP v2) {
+    if (cmp) {
+      TP* o = Ak + M.colptr[c];
+      if (r2 >= 0) *o++ = v2;
+      *o = TP(1);
+      return;
+    }
     for (int r = 0; r < nxt; ++r) Ak[(size_t)r * nxt + c] = (r == c) ? TP(1) : (r == r2 ? v2 : TP(0));
   };
   for (int b = 0; b < nb; ++b) {
@@ -458,7 +467,8 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
                               const double* __restrict__ s, const TP* __restrict__ sd,
                               TP* __restrict__ A, TP* __restrict__ Bm, TP* __restrict__ Bp,
                               TP* __restrict__ S, unsigned* status, int layout,
-                              const int2* __restrict__ entries, const DevInst* __restrict__ inst) {
+                              const int2* __restrict__ entries, const DevInst* __restrict__ inst,
+                              int cmp) {
   using Sc = Scheme<SCH>;
   using K = Cst<TP>;
   constexpr int NS = Sc::S;
@@ -471,7 +481,8 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
   if (t >= n) return;
   const int col = M.cperm[g - t * C];
   const int nb = M.nb, nj = M.nj, nc = M.nc, nxt = M.nxt, nu = M.nu, nq = 3 * nb, nk = M.nk;
-  const IvAddr ad = iv_addr(i0 + t, nxt, nu, nc, layout, nullptr, nullptr, entries, inst);
+  const IvAddr ad = iv_addr(i0 + t, nxt, nu, nc, layout, nullptr, nullptr, entries, inst,
+                            cmp ? (long long)M.colptr[nxt] : (long long)nxt * nxt);
   const int nl = M.nlive, nqd = M.nquad;
   int qin = -1;
   bool right = false, scol = false;
@@ -682,7 +693,12 @@ __global__ void k_cpl_tangent(const __grid_constant__ CplTab M, long i0, long n,
   // column `col` of [A | B- | B+ | S]
   TP* out;
   size_t stride;
-  if (col < nxt) { out = A + ad.a + col; stride = nxt; }
+  if (cmp) {  // compact: column-major, the column's rows contiguous
+    if (col < nxt) out = A + ad.a + M.colptr[col];
+    else if (!scol) out = (right ? Bp : Bm) + ad.b + (size_t)qin * nxt;
+    else out = S + ad.v;
+    stride = 1;
+  } else if (col < nxt) { out = A + ad.a + col; stride = nxt; }
   else if (!scol) { out = (right ? Bp : Bm) + ad.b + qin; stride = nu; }
   else { out = S + ad.v; stride = 1; }
   float chk = 0.0f;
@@ -724,7 +740,7 @@ template <typename TP, int SCH>
 cudaError_t run(const CplTab& T, long N, int nsub, int layout, const double* X, const double* U,
                 const double* s, void* A, void* Bm, void* Bp, void* S, double* defect,
                 double* penalty, void* ws, long chunk, unsigned* status, cudaStream_t st,
-                const int2* entries, const DevInst* inst) {
+                const int2* entries, const DevInst* inst, int cmp) {
   const size_t sm1 = (size_t)T.n_size * sizeof(double) * 32;
   const int prec = std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI;
   const CplJit* jit = cpl_jit_tangent(T, prec);
@@ -737,21 +753,21 @@ cudaError_t run(const CplTab& T, long N, int nsub, int layout, const double* X, 
     const long n = std::min<long>(chunk, N - i0);
     if (jnom)
       e = cpl_jit_launch_nominal(*jnom, T, i0, n, nsub, layout, X, U, s, ws, A, defect, penalty, status, st,
-                                 entries, inst);
+                                 entries, inst, cmp);
     else
       k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
-          T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status, entries, inst);
+          T, i0, n, nsub, layout, X, U, s, (TP*)ws, (TP*)A, defect, penalty, status, entries, inst, cmp);
     if (e != cudaSuccess) return e;
     const long threads = n * T.cnt;
     if (jit) {
       e = cudaGetLastError();
       if (e == cudaSuccess)
         e = cpl_jit_launch(*jit, T, prec, i0, n, nsub, s, ws, A, Bm, Bp, S, status, st, layout, entries,
-                           inst);
+                           inst, cmp);
     } else {
       k_cpl_tangent<TP, SCH><<<(unsigned)((threads + bs - 1) / bs), bs, sm2, st>>>(
           T, i0, n, nsub, s, (const TP*)ws, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status, layout, entries,
-          inst);
+          inst, cmp);
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
@@ -1135,10 +1151,11 @@ cudaError_t run_vjp(const CplTab& T, long N, int nsub, int layout, const double*
     const double* Uc = U ? (layout == CISCVX_FOH_NODE ? U + i0 * nu : U + 2 * i0 * nu) : nullptr;
     if (jnom)
       e = cpl_jit_launch_nominal(*jnom, T, 0, n, nsub, layout, Xc, Uc, s + i0, sd, nullptr, defect, penalty,
-                                 status, st, nullptr, nullptr);
+                                 status, st, nullptr, nullptr, 0);
     else
       k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
-          T, 0, n, nsub, layout, Xc, Uc, s + i0, sd, (TP*)nullptr, defect, penalty, status, nullptr, nullptr);
+          T, 0, n, nsub, layout, Xc, Uc, s + i0, sd, (TP*)nullptr, defect, penalty, status, nullptr, nullptr,
+          0);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (jadj) {
@@ -1261,10 +1278,12 @@ const char* cpl_build(const DevModel& M, CplTab& T) {
   // integrated columns: every column but the closed-form ones
   int cnt = 0;
   for (int c = 0; c < T.C; ++c) {
-    const bool trivial = c < M.nxt && (c >= 6 * nb || (M.body[(c % nq) / 3].contact < 0 && (c % 3) != 2));
+    const bool trivial = c < M.nxt && cpl_col_kind(M, c) != 0;
     if (!trivial) T.cperm[cnt++] = (short)c;
   }
   T.cnt = cnt;
+  T.colptr[0] = 0;
+  for (int c = 0; c < M.nxt; ++c) T.colptr[c + 1] = T.colptr[c] + cpl_col_nnz(M, c);
   // stage data
   T.ncf = M.aux ? CPL_CF1 : CPL_CF0;
   T.sd_arm = 0;
@@ -1320,12 +1339,13 @@ cudaError_t launch_coupled(const CplTab& T, long N, int nsub, int prec, int layo
                            const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
                            double* defect, double* penalty, void* ws, long chunk,
                            unsigned* status, cudaStream_t st, const int2* entries,
-                           const DevInst* inst) {
+                           const DevInst* inst, bool compact) {
+  const int c = compact ? 1 : 0;
   if (prec == CISCVX_FP64)
-    return T.scheme ? run<double, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst)
-                    : run<double, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst);
-  return T.scheme ? run<float, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst)
-                  : run<float, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst);
+    return T.scheme ? run<double, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst, c)
+                    : run<double, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst, c);
+  return T.scheme ? run<float, 1>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst, c)
+                  : run<float, 0>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, ws, chunk, status, st, entries, inst, c);
 }
 
 CplAdjLayout cpl_adjoint_layout(const CplTab& T, long n, int nsub, int prec) {

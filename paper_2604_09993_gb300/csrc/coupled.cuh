@@ -72,7 +72,30 @@ struct CplTab {
   // nominal kernel writes them.
   int cnt;                                   // columns integrated
   short cperm[CPL_MAXROW + 2 * (3 * MAXJ + 3 * MAXB) + 1];  // integrated column index -> column
+  // Compact A (CISCVX_OUT_COMPACT): column-major, column c's structural
+  // nonzeros at [colptr[c], colptr[c + 1]) in ascending rows (every row for an
+  // integrated column; see cpl_col_kind); compact B- / B+ are every entry,
+  // column-major (column q at q n_x~).
+  int colptr[CPL_MAXROW + 1];
 };
+
+// Kind of column c (< n_x~) of A for a model with coupled links: 0 integrated
+// (every row may be nonzero), 1 A e_c = e_c (position of a link without a
+// contact, auxiliary state), 2 A e_c = e_c + s e_{c - 3 n_b} (linear velocity
+// of a link without a contact; its position row comes first).
+inline int cpl_col_kind(const DevModel& M, int c) {
+  const int nb = M.nb, nq = 3 * nb;
+  if (c >= 6 * nb) return 1;
+  if (M.body[(c % nq) / 3].contact >= 0 || (c % 3) == 2) return 0;
+  return c < nq ? 1 : 2;
+}
+
+// Structural nonzeros of A in the compact order (column-major): column c has
+// n_x~ of them when integrated, 1 or 2 otherwise.
+inline int cpl_col_nnz(const DevModel& M, int c) {
+  const int k = cpl_col_kind(M, c);
+  return k == 0 ? M.nxt : (k == 2 ? 2 : 1);
+}
 
 // True when the model needs the coupled path.
 inline bool cpl_needed(const DevModel& M) { return M.jelim || M.scheme != 0 || M.ta != 0.0; }
@@ -87,11 +110,12 @@ size_t cpl_interval_bytes(const CplTab& T, int nsub, int prec);
 // `chunk` intervals through the workspace (stage data of one chunk).  With
 // `entries`, interval e is entry e = (instance, k) of the batch instance
 // table `inst` (element offsets into the packed arrays); else interval e.
+// compact: A, Bm, Bp in the compact layout (CplTab::colptr).
 cudaError_t launch_coupled(const CplTab& T, long N, int nsub, int prec, int layout, const double* X,
                            const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
                            double* defect, double* penalty, void* ws, long chunk,
                            unsigned* status, cudaStream_t st, const int2* entries = nullptr,
-                           const DevInst* inst = nullptr);
+                           const DevInst* inst = nullptr, bool compact = false);
 // Compiles the specialized kernels and sets the generic kernels' limits
 // (before a launch is captured in a graph).
 cudaError_t cpl_prepare(const CplTab& T, int prec);
@@ -109,7 +133,7 @@ cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, lo
                                    int layout, const double* X, const double* U, const double* s,
                                    void* sd, void* A, double* defect, double* penalty,
                                    unsigned* status, cudaStream_t st, const int2* entries,
-                                   const DevInst* inst);
+                                   const DevInst* inst, int cmp);
 const CplJit* cpl_jit_adjoint(const CplTab& T, int prec);
 cudaError_t cpl_jit_launch_adjoint(const CplJit& J, const CplTab& T, int prec, long i0, long n, long N, int nsub,
                                    const double* s, const void* sd, const double* w, const double* rho,
@@ -117,7 +141,7 @@ cudaError_t cpl_jit_launch_adjoint(const CplJit& J, const CplTab& T, int prec, l
 cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,
                            const double* s, const void* sd, void* A, void* Bm, void* Bp, void* S,
                            unsigned* status, cudaStream_t st, int layout, const int2* entries,
-                           const DevInst* inst);
+                           const DevInst* inst, int cmp);
 
 // Reverse-mode VJP of the coupled path (coupled.cu): the nominal kernel's
 // forward pass into the stage data of a chunk, then the adjoint kernel (thread

@@ -56,7 +56,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
                                                              double* __restrict__ penalty,
                                                              unsigned* status,
                                                              const int2* __restrict__ entries,
-                                                             const InstRec* __restrict__ inst) {
+                                                             const InstRec* __restrict__ inst, int cmp) {
   extern __shared__ double jit_sm1[];
   double* sm = jit_sm1 + threadIdx.x;
 #define SE(o) sm[(o) * BLK]
@@ -66,7 +66,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
   const double *uL, *uR, *x0;
   double sk;
   {
-    const IvRef ad = iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst);
+    const IvRef ad = iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst, 0);
     uL = U + ad.u;
     uR = U + ad.u + NU;
     x0 = X + ad.x;
@@ -411,7 +411,8 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
     }
   }
   double chk = 0.0;
-  const IvRef ad = iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst);
+  const IvRef ad = iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst,
+                          cmp ? (long long)COLPTR[NXT] : (long long)NXT * NXT);
   const double* x1 = x0 + NXT;
 #pragma unroll
   for (int r = 0; r < NXT; ++r) {
@@ -431,6 +432,22 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
   // (not written by the adjoint's forward pass, which has no A)
   if (!A) return;
   TP* Ak = A + ad.a;
+  if (cmp) {  // compact (column-major): e_p -> 1; e_v + s e_p -> (s, 1); e_y -> 1
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (CONTACT[b] >= 0) continue;
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2) {
+        const int cp = 3 * b + c2, cv = NQ + 3 * b + c2;
+        Ak[COLPTR[cp]] = TP(1);
+        Ak[COLPTR[cv]] = TP(sk);
+        Ak[COLPTR[cv] + 1] = TP(1);
+      }
+    }
+#pragma unroll
+    for (int c = 6 * NB; c < NXT; ++c) Ak[COLPTR[c]] = TP(1);
+    return;
+  }
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (CONTACT[b] >= 0) continue;

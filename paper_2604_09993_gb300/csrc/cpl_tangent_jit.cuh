@@ -34,7 +34,8 @@ extern "C" __global__ void __launch_bounds__(BS) cpl_tangent(const __grid_consta
                                                             TP* __restrict__ Bp, TP* __restrict__ S,
                                                             unsigned* status, int layout,
                                                             const int2* __restrict__ entries,
-                                                            const ciscvx::InstRec* __restrict__ inst) {
+                                                            const ciscvx::InstRec* __restrict__ inst,
+                                                            int cmp) {
   extern __shared__ __align__(16) unsigned char jit_smem[];
   TP* ksh = reinterpret_cast<TP*>(jit_smem) + threadIdx.x;  // stored slopes (RKF45), element major
   const long g = (long)blockIdx.x * BS + threadIdx.x;
@@ -55,7 +56,8 @@ extern "C" __global__ void __launch_bounds__(BS) cpl_tangent(const __grid_consta
   for (int l = 0; l < NL; ++l) PL[l] = (LINV[l] == col) ? TP(1) : TP(0);
 #pragma unroll
   for (int q = 0; q < NQD; ++q) PQ[q] = (QINV[q] == col) ? TP(1) : TP(0);
-  const TP sk = TP(s[ciscvx::iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst).s]);
+  const long long astride = cmp ? (long long)COLPTR[NXT] : (long long)NXT * NXT;
+  const TP sk = TP(s[ciscvx::iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst, astride).s]);
   const TP h = TP(1) / TP(nsub);
   const TP hsk = h * sk;
   const TP* sdk = sd + (size_t)t * nsub * NSTG * SD_SIZE;
@@ -272,8 +274,13 @@ extern "C" __global__ void __launch_bounds__(BS) cpl_tangent(const __grid_consta
   // column `col` of [A | B- | B+ | S]
   TP* out;
   size_t stride;
-  const ciscvx::IvRef ad = ciscvx::iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst);
-  if (col < NXT) { out = A + ad.a + col; stride = NXT; }
+  const ciscvx::IvRef ad = ciscvx::iv_ref(i0 + t, NXT, NU, NC, layout, entries, inst, astride);
+  if (cmp) {  // compact: column-major, the column's rows contiguous
+    if (col < NXT) out = A + ad.a + COLPTR[col];
+    else if (!scol) out = (right ? Bp : Bm) + ad.b + (size_t)qin * NXT;
+    else out = S + ad.v;
+    stride = 1;
+  } else if (col < NXT) { out = A + ad.a + col; stride = NXT; }
   else if (!scol) { out = (right ? Bp : Bm) + ad.b + qin; stride = NU; }
   else { out = S + ad.v; stride = 1; }
   float chk = 0.0f;

@@ -164,8 +164,11 @@ struct IvRef {
   long long x, u, s, a, b, v, p;
 };
 
+// a_stride: elements of A per interval (n_x~^2 dense; the compact pattern's
+// size for compact outputs).
 __device__ __forceinline__ IvRef iv_ref(long long e, int nxt, int nu, int nc, int layout,
-                                        const int2* entries, const InstRec* inst) {
+                                        const int2* entries, const InstRec* inst,
+                                        long long a_stride) {
   IvRef r;
   long long k = e;
   long long x = 0, u = 0, sv = 0, a = 0, b = 0, v = 0, p = 0;
@@ -178,7 +181,7 @@ __device__ __forceinline__ IvRef iv_ref(long long e, int nxt, int nu, int nc, in
   r.x = x + k * nxt;
   r.u = u + (layout == 0 ? k : 2 * k) * nu;
   r.s = sv + k;
-  r.a = a + k * nxt * nxt;
+  r.a = a + k * a_stride;
   r.b = b + k * nxt * nu;
   r.v = v + k * nxt;
   r.p = p + k * nc;

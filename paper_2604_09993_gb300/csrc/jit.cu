@@ -152,6 +152,7 @@ std::string prelude(const CplTab& T, int prec, int bs) {
   arr(o, "LDYN", ldyn.data(), T.nlive);
   arr(o, "LVEL", lvel.data(), T.nlive);
   arr(o, "CPERM", T.cperm, T.cnt);
+  arr(o, "COLPTR", T.colptr, T.nxt + 1);  // compact A, column-major (CplTab::colptr)
   double a[36];
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) a[6 * i + j] = T.a[i][j];
@@ -275,7 +276,7 @@ cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, lo
                                    int layout, const double* X, const double* U, const double* s,
                                    void* sd, void* A, double* defect, double* penalty,
                                    unsigned* status, cudaStream_t st, const int2* entries,
-                                   const DevInst* inst) {
+                                   const DevInst* inst, int cmp) {
   // NumN {mass, minv, iinv [NB]; jrp, jrc [max(NJ,1)][2]; crho [max(NC,1)][2]; mu [max(NC,1)]; g, ta, tk}
   std::vector<double> num;
   const int nj1 = T.nj > 0 ? T.nj : 1, nc1 = T.nc > 0 ? T.nc : 1;
@@ -290,7 +291,7 @@ cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, lo
   num.push_back(T.ta);
   num.push_back(T.tk);
   void* args[] = {num.data(), &i0, &n, &nsub, &layout, &X, &U, &s, &sd, &A, &defect, &penalty, &status,
-                  &entries, &inst};
+                  &entries, &inst, &cmp};
   const unsigned grid = (unsigned)((n + J.bs - 1) / J.bs);
   const CUresult r = g_drv.launch((CUfunction)J.fn, grid, 1, 1, J.bs, 1, 1, (unsigned)J.smem, (CUstream)st, args, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
@@ -299,7 +300,7 @@ cudaError_t cpl_jit_launch_nominal(const CplJit& J, const CplTab& T, long i0, lo
 cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, long n, int nsub,
                            const double* s, const void* sd, void* A, void* Bm, void* Bp, void* S,
                            unsigned* status, cudaStream_t st, int layout, const int2* entries,
-                           const DevInst* inst) {
+                           const DevInst* inst, int cmp) {
   // Num {TP minv[NB]; TP iinv[NB];}
   unsigned char num[2 * MAXB * sizeof(double)];
   if (prec == CISCVX_FP64) {
@@ -309,7 +310,7 @@ cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, 
     float* f = (float*)num;
     for (int b = 0; b < T.nb; ++b) { f[b] = T.minvf[b]; f[T.nb + b] = T.iinvf[b]; }
   }
-  void* args[] = {num, &i0, &n, &nsub, &s, &sd, &A, &Bm, &Bp, &S, &status, &layout, &entries, &inst};
+  void* args[] = {num, &i0, &n, &nsub, &s, &sd, &A, &Bm, &Bp, &S, &status, &layout, &entries, &inst, &cmp};
   const long threads = n * T.cnt;
   const unsigned grid = (unsigned)((threads + J.bs - 1) / J.bs);
   const CUresult r = g_drv.launch((CUfunction)J.fn, grid, 1, 1, J.bs, 1, 1, (unsigned)J.smem, (CUstream)st, args, nullptr);

@@ -310,7 +310,9 @@ struct Builder {
     aux = M.aux != 0; jelim = M.jelim != 0; terrain = M.ta != 0.0;
     npsi = aux ? 3 * nc : nc;
     node = layout == CISCVX_FOH_NODE;
-    has_pattern = !jelim && M.scheme == 0 && !terrain;  // a model without coupled links
+    // every model has a structural pattern (coupled links: column-major, the
+    // integrated columns full); the dynamics rows take only its entries
+    has_pattern = true;
     if (has_pattern) {
       par.resize(M.nnzA); pac.resize(M.nnzA); pbr.resize(M.nnzB); pbc.resize(M.nnzB);
       model_pattern(M, par.data(), pac.data(), pbr.data(), pbc.data());

@@ -54,7 +54,7 @@ def test_null_arguments_rejected(lib):
     assert lib.ciscvx_node_linearize(None, 4, None, None, None, None, ctypes.byref(prm), None,
                                      None, None, None, None, None, None, None) == api.EINVAL
     assert lib.ciscvx_discretize_compact(None, 10, 4, 0, 0, None, None, None, None, None, None,
-                                         None, None, None, None, None) == api.EINVAL
+                                         None, None, None, None, None, 0, None) == api.EINVAL
     lo, hi = ctypes.c_size_t(), ctypes.c_size_t()
     assert lib.ciscvx_discretize_workspace_size(None, 0, 10, 4, 0, 0, ctypes.byref(lo),
                                                 ctypes.byref(hi)) == api.EINVAL

@@ -167,11 +167,11 @@ def test_compact_argument_errors(env):
     ptr = lambda t: t.data_ptr()  # noqa: E731
     st = lib.ciscvx_discretize_compact(m.handle, p.N, p.n_sub, 0, 0, ptr(X), ptr(U), ptr(s),
                                        ptr(out["A"]), None, ptr(out["Bp"]), ptr(out["S"]),
-                                       ptr(out["defect"]), ptr(out["penalty"]), None, None)
+                                       ptr(out["defect"]), ptr(out["penalty"]), None, None, 0, None)
     assert st == api.EINVAL
     st = lib.ciscvx_discretize_compact(m.handle, p.N, p.n_sub, 3, 0, ptr(X), ptr(U), ptr(s),
                                        ptr(out["A"]), ptr(out["Bm"]), ptr(out["Bp"]), ptr(out["S"]),
-                                       ptr(out["defect"]), ptr(out["penalty"]), None, None)
+                                       ptr(out["defect"]), ptr(out["penalty"]), None, None, 0, None)
     assert st == api.EUNSUPPORTED
     with pytest.raises(KeyError):
         api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="sparse")

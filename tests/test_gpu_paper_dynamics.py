@@ -131,24 +131,117 @@ def test_single_interval_and_no_contacts(env):
         assert block_err(got[k], ref[k]) <= TOL_FP64, k
 
 
-def test_unsupported_entry_points(env):
+def test_short_workspace_is_an_argument_error(env):
     torch, oracle, api = env
     dev = torch.device("cuda:0")
     p = _problem("hopper", 28, 10, 4, **PAPER)
     m = api.Model(p.robot)
     t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
     X, U, s = t(p.X), t(p.U), t(p.s)
-    for call in (lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64"),
-                 lambda: api.model_pattern(p.robot.as_dict()),
-                 lambda: api.BatchPlan([m], [0], [p.N], [p.n_sub], out_format="compact")):
+    tiny = torch.empty(16, dtype=torch.uint8, device=dev)
+    for call in (lambda: api.discretize(m, X, U, s, p.n_sub, "fp64", workspace=tiny),
+                 lambda: api.discretize_compact(m, X, U, s, p.n_sub, "fp64", workspace=tiny)):
         with pytest.raises(api.CiscvxError) as err:
             call()
-        assert err.value.status == api.EUNSUPPORTED
-    # a workspace below the minimum is an argument error
-    tiny = torch.empty(16, dtype=torch.uint8, device=dev)
-    with pytest.raises(api.CiscvxError) as err:
-        api.discretize(m, X, U, s, p.n_sub, "fp64", workspace=tiny)
-    assert err.value.status == api.EINVAL
+        assert err.value.status == api.EINVAL
+
+
+COMPACT_CASES = [("hopper", 70, 3, dict(PAPER), False), ("cheetah7", 45, 2, dict(PAPER), True),
+                 ("biped", 33, 2, dict(joint_forces=0, scheme=0, terrain=synth.TERRAIN_SINE), False),
+                 ("biped", 40, 3, dict(joint_forces=1, scheme=0), True)]
+
+
+def _compact_check(env, p, precision, layout):
+    """Compact A, B-, B+ against the dense blocks of the same call: every
+    pattern entry bit for bit, every entry off the pattern exactly zero; S,
+    defect and penalty identical; z from the compact values against z from the
+    dense ones (the same sums in another order)."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    m = api.Model(p.robot)
+    U = p.U if layout == "node" else p.U_interval()
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X, Ut, s = t(p.X), t(U), t(p.s)
+    dense = api.discretize(m, X, Ut, s, p.n_sub, precision, layout, want_z=True)
+    comp = api.discretize_compact(m, X, Ut, s, p.n_sub, precision, layout, want_z=True)
+    api.sync_status(m)
+    ar, ac, br, bc = (torch.tensor(a.astype(np.int64), device=dev) for a in m.pattern())
+    nxt, nu = m.nxt, m.nu
+    assert comp["A"].shape[1] == len(ar) < nxt * nxt and comp["Bm"].shape[1] == len(br) == nxt * nu
+    assert torch.equal(comp["A"], dense["A"][:, ar, ac])
+    for k in ("Bm", "Bp"):
+        assert torch.equal(comp[k], dense[k][:, br, bc]), k
+    off = torch.ones(nxt, nxt, dtype=torch.bool, device=dev)
+    off[ar, ac] = False
+    assert not torch.any(dense["A"][:, off] != 0)
+    for k in ("S", "defect", "penalty"):
+        assert torch.equal(comp[k], dense[k]), k
+    assert block_err(comp["z"].cpu().numpy(), dense["z"].cpu().numpy()) <= 1e-12
+    ref = oracle.discretize(p.robot.as_dict(), p.X, U, p.s, p.n_sub, layout=layout)
+    got = {k: v.double().cpu().numpy() for k, v in dense.items()}
+    _check(got, ref, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+@pytest.mark.parametrize("case", range(len(COMPACT_CASES)))
+def test_compact_outputs_match_dense_and_oracle(env, precision, case):
+    name, N, n_sub, kw, cross = COMPACT_CASES[case]
+    p = _problem(name, 40 + case, N, n_sub, cross=cross, **kw)
+    _compact_check(env, p, precision, "node" if case % 2 == 0 else "interval")
+
+
+def test_compact_outputs_specialized_and_generic_kernels(env, monkeypatch):
+    """The generic coupled kernels (CISCVX_COUPLED_JIT=0) write the same
+    compact layout as the run-time specialized ones."""
+    p = _problem("biped", 52, 37, 2, cross=True, **PAPER)
+    monkeypatch.setenv("CISCVX_COUPLED_JIT", "0")
+    _compact_check(env, p, "fp32_phi", "node")
+    monkeypatch.delenv("CISCVX_COUPLED_JIT")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
+def test_batch_plan_compact_with_coupled_models(env, precision):
+    """A compact batch plan mixing per-link and coupled models: every
+    instance's compact values equal the single-instance compact call's (to
+    rounding: intervals are grouped differently into warps, and the angle
+    chain's Taylor tier is a warp vote), and the plan's graph replays them."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(53)
+    robots = [synth.hopper(rng),
+              synth.with_paper_dynamics(synth.biped(rng), **PAPER),
+              synth.with_cross_states(synth.with_paper_dynamics(synth.cheetah7(rng), joint_forces=1, scheme=0))]
+    probs, midx = [], []
+    for i in range(9):
+        mi = i % 3
+        probs.append(synth.draw_instance(robots[mi], rng, int(rng.integers(1, 50)), int(rng.choice([1, 3])),
+                                         q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15)))
+        midx.append(mi)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [q.N for q in probs], [q.n_sub for q in probs], precision=precision,
+                         out_format="compact")
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X = t(plan.pack([q.X for q in probs], "X"))
+    U = t(plan.pack([q.U for q in probs], "U"))
+    sv = t(plan.pack([q.s for q in probs], "s"))
+    out = plan.discretize(X, U, sv)
+    plan.sync_status()
+    host = {k: v.double().cpu().numpy() for k, v in out.items()}
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for i, q in enumerate(probs):
+        m = models[midx[i]]
+        c = api.discretize_compact(m, t(q.X), t(q.U), t(q.s), q.n_sub, precision)
+        api.sync_status(m)
+        N, na, nb_ = q.N, m.nnz_a, m.nnz_b
+        got = {"A": plan.unpack(host["A"], "A", i, (N, na)), "Bm": plan.unpack(host["Bm"], "B", i, (N, nb_)),
+               "Bp": plan.unpack(host["Bp"], "B", i, (N, nb_)), "S": plan.unpack(host["S"], "S", i, (N, m.nxt)),
+               "defect": plan.unpack(host["defect"], "defect", i, (N, m.nxt))}
+        for k, v in got.items():
+            assert block_err(v, c[k].double().cpu().numpy()) <= tol, (i, k)
+    out2 = plan.discretize(X, U, sv)
+    plan.sync_status()
+    for k in out:
+        assert torch.equal(out[k], out2[k]), k
 
 
 def test_node_constraints_with_eliminated_joint_forces(env):

@@ -275,7 +275,8 @@ def test_socp_fp32_inputs_widen_exactly(env):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_phi"])
-@pytest.mark.parametrize("layout,variant", [("node", "default"), ("interval", "default"), ("node", "cross")])
+@pytest.mark.parametrize("layout,variant", [("node", "default"), ("interval", "default"), ("node", "cross"),
+                                            ("node", "paper"), ("interval", "sine")])
 def test_socp_from_compact_outputs(env, precision, layout, variant):
     """The fill from compact A / B- / B+ (ciscvx_discretize_compact) equals the
     fill from the dense blocks bit for bit: the same values feed the same
@@ -309,10 +310,3 @@ def test_socp_from_compact_outputs(env, precision, layout, variant):
     o_c = sc.fill(n_inst, comp, precision=precision)
     for k in o_d:
         assert torch.equal(o_d[k], o_c[k]), k
-    # a model with coupled links has no structural pattern: no compact inputs
-    mc = api.Model(_robot("hopper", "sine"))
-    with pytest.raises(api.CiscvxError) as e:
-        api.Socp(mc, N, layout, w_px=1.0, w_ep=1.0, w_torque=0.0, s_min=0.0, s_max=1.0,
-                 torque_max=np.ones(mc.nj), x_init=np.zeros(6 * mc.nb), x_final=np.zeros(6 * mc.nb),
-                 phi_format="compact")
-    assert e.value.status == api.EUNSUPPORTED

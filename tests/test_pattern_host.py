@@ -151,3 +151,71 @@ def test_pattern_rejects_invalid_descriptions(env):
     with pytest.raises(api.CiscvxError) as e:
         api.model_pattern(two)
     assert e.value.status == api.EUNSUPPORTED
+
+
+def _coupled_robots():
+    rng = np.random.default_rng(23)
+    hop, bip = synth.hopper(rng), synth.biped(rng)
+    return {"hopper_paper": synth.with_paper_dynamics(hop, joint_forces=1, scheme=1,
+                                                      terrain=synth.TERRAIN_SINE),
+            "biped_paper_cross": synth.with_cross_states(synth.with_paper_dynamics(bip, joint_forces=1,
+                                                                                   scheme=1)),
+            "biped_sine": synth.with_paper_dynamics(bip, joint_forces=0, scheme=0,
+                                                    terrain=synth.TERRAIN_SINE)}
+
+
+def _coupled_documented_order(R):
+    """The column-major order the header states for models with coupled links."""
+    nb = len(R["mass"])
+    nj, nc = len(R["joint_parent"]), len(R["contact_body"])
+    cb = list(np.asarray(R["contact_body"]))
+    cross = bool(R.get("aux_model", 0))
+    nxt = 6 * nb + (5 if cross else 1) * nc
+    nu = (1 if R.get("joint_forces", 0) else 3) * nj + 3 * nc
+    a = []
+    for c in range(nxt):
+        if c >= 6 * nb:
+            a.append((c, c))
+            continue
+        body = (c % (3 * nb)) // 3
+        if body in cb or c % 3 == 2:
+            a += [(r, c) for r in range(nxt)]
+        elif c < 3 * nb:
+            a.append((c, c))
+        else:
+            a += [(c - 3 * nb, c), (c, c)]
+    b = [(r, q) for q in range(nu) for r in range(nxt)]
+    return a, b, nxt, nu
+
+
+@pytest.mark.parametrize("name", ["hopper_paper", "biped_paper_cross", "biped_sine"])
+def test_coupled_pattern_order_and_oracle_nonzeros(env, name):
+    """Models with coupled links: the pattern follows the documented
+    column-major order and holds every entry the oracle finds nonzero; the
+    entries off it (the closed-form columns' other rows) are exactly zero in
+    the oracle's blocks."""
+    oracle, api = env
+    R = _as_dict(_coupled_robots()[name])
+    ar, ac, br, bc = api.model_pattern(R)
+    a, b, nxt, nu = _coupled_documented_order(R)
+    assert list(zip(ar.tolist(), ac.tolist())) == a
+    assert list(zip(br.tolist(), bc.tolist())) == b
+    nb = len(R["mass"])
+    rng = np.random.default_rng(6)
+    N, n_sub = 5, 2
+    X = rng.uniform(-0.6, 0.6, (N + 1, nxt))
+    X[:, 1:3 * nb:3] = rng.uniform(-0.4, 0.2, (N + 1, nb))
+    U = rng.standard_normal((N + 1, nu))
+    s = rng.uniform(0.05, 0.15, N)
+    ref = oracle.discretize(R, X, U, s, n_sub)
+    pa = np.zeros((nxt, nxt), bool)
+    pa[ar, ac] = True
+    nza = np.any(ref["A"] != 0.0, axis=0)
+    assert not np.any(nza & ~pa), np.argwhere(nza & ~pa)[:5]
+    # the closed-form columns: A e_p = e_p, A e_v = e_v + s e_p, A e_y = e_y
+    for c in range(nxt):
+        if pa[:, c].sum() < nxt:
+            rows = np.flatnonzero(pa[:, c])
+            assert np.all(ref["A"][:, rows[-1], c] == 1.0)
+            if len(rows) == 2:
+                assert np.allclose(ref["A"][:, rows[0], c], s, rtol=0, atol=1e-15)
