@@ -736,6 +736,27 @@ cudaError_t prepare(const CplTab& T) {
   return e;
 }
 
+// The chunk rounded down to whole waves of the nominal kernel (SMs x its
+// resident one-warp blocks x 32 intervals) when it holds more than one: that
+// kernel is latency-bound at a few warps per SM, so a chunk of 1.1 waves takes
+// as long as two.  Chunks stay multiples of 32 intervals past the first wave.
+template <typename TP, int SCH>
+long wave_chunk(const CplJit* jnom, size_t sm1, long chunk) {
+  int bps = jnom ? jnom->blocks_per_sm : 0;
+  if (!jnom && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cpl_nominal<TP, SCH>, 32, sm1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    bps = 0;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return chunk;
+  }
+  const long wave = (long)bps * sms * 32;
+  return (wave > 0 && chunk > wave) ? chunk / wave * wave : chunk;
+}
+
 template <typename TP, int SCH>
 cudaError_t run(const CplTab& T, long N, int nsub, int layout, const double* X, const double* U,
                 const double* s, void* A, void* Bm, void* Bp, void* S, double* defect,
@@ -749,6 +770,7 @@ cudaError_t run(const CplTab& T, long N, int nsub, int layout, const double* X, 
   const size_t sm2 = (size_t)bs * T.t_size * sizeof(TP);
   cudaError_t e = prepare<TP, SCH>(T);
   if (e != cudaSuccess) return e;
+  chunk = wave_chunk<TP, SCH>(jnom, sm1, chunk);
   for (long i0 = 0; i0 < N; i0 += chunk) {
     const long n = std::min<long>(chunk, N - i0);
     if (jnom)
@@ -1135,7 +1157,7 @@ cudaError_t run_vjp(const CplTab& T, long N, int nsub, int layout, const double*
     const long mid = (lo + hi + 1) / 2;
     if (cpl_adjoint_bytes(T, mid, nsub, prec) <= ws_bytes) lo = mid; else hi = mid - 1;
   }
-  const long chunk = lo;
+  const long chunk = wave_chunk<TP, SCH>(jnom, sm1, lo);
   const CplAdjLayout Ly = cpl_adjoint_layout(T, chunk, nsub, prec);
   char* base = (char*)ws;
   TP* sd = (TP*)(base + Ly.stage);

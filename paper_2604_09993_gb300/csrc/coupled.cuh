@@ -126,6 +126,7 @@ struct CplJit {
   void* fn = nullptr;  // CUfunction
   int bs = 0;
   size_t smem = 0;
+  int blocks_per_sm = 0;  // resident blocks per SM at (bs, smem); 0 if unknown
 };
 const CplJit* cpl_jit_tangent(const CplTab& T, int prec);
 const CplJit* cpl_jit_nominal(const CplTab& T, int prec);

@@ -53,6 +53,7 @@ struct Drv {
   CUresult (*set_attr)(CUfunction, CUfunction_attribute, int);
   CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
                      unsigned, CUstream, void**, void**);
+  CUresult (*occ)(int*, CUfunction, int, size_t) = nullptr;  // optional
   bool ok = false;
 };
 
@@ -89,6 +90,7 @@ void load_apis() {
              entry("cuModuleGetFunction", (void**)&g_drv.get_fn) &&
              entry("cuFuncSetAttribute", (void**)&g_drv.set_attr) &&
              entry("cuLaunchKernel", (void**)&g_drv.launch);
+  if (!entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&g_drv.occ)) g_drv.occ = nullptr;
 }
 
 template <typename T>
@@ -267,6 +269,8 @@ const CplJit* compile(const std::string& src0, const char* name, int bs, size_t 
   J.fn = (void*)fn;
   J.bs = bs;
   J.smem = smem;
+  int nblk = 0;
+  if (g_drv.occ && g_drv.occ(&nblk, fn, bs, smem) == CUDA_SUCCESS) J.blocks_per_sm = nblk;
   return &J;
 }
 
