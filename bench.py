@@ -245,7 +245,7 @@ class BatchWorkload:
 
     # end to end through the public API with host buffers: ciscvx_batch_run_host
     # (chunked, H2D / compute / D2H overlapped on three streams)
-    E2E_CHUNKS = 16
+    E2E_CHUNKS = 8
 
     def e2e_setup(self, prec, fmt="dense"):
         torch = self.torch

@@ -395,7 +395,10 @@ typedef struct {
   int warps_per_cta;  /* 1, 2, 4 or 8 */
   int ctas_per_sm;    /* > 0: persistent grid of ctas_per_sm x SMs CTAs pulling items from a
                          queue; 0: one warp per work item */
-  int lpt_order;      /* 1: items ordered by decreasing estimated cost; 0: instance order */
+  int lpt_order;      /* 1: items ordered by decreasing estimated cost; 0: instance order;
+                         2 (persistent grids): two queues, the foot-link items and the others,
+                         each in instance order, a share of the SMs (by estimated cost) taking
+                         each, with the other queue taken over once the own one is empty */
   int use_graph;      /* 1: capture the launch sequence in a CUDA graph and replay it */
   int occupancy;      /* register cap of the kernels: 0 none (8 warps/SM), 1 <= 168 registers
                          (12 warps/SM), 2 <= 128 registers (16 warps/SM); 1 and 2 need

@@ -124,7 +124,10 @@ struct ChunkTables {
   int4* d_groups = nullptr;
   int2* d_items_lpt = nullptr;
   int2* d_items_nat = nullptr;
+  int2* d_items_sm = nullptr;
   std::vector<int> item_off;        // [K+1] items of chunk c: [item_off[c], item_off[c+1])
+  std::vector<int> foot_cnt;        // [K] foot-link items at the head of chunk c's items_sm
+  int split_sm = 0;                 // SMs that take the foot-link queue first (lpt_order 2)
   std::vector<int> inst_off;        // [K+1] instances of chunk c
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
   std::vector<cudaEvent_t> ev;      // 1 start + 3 per chunk
@@ -161,7 +164,9 @@ struct ciscvx_batch_plan {
   int4* d_groups = nullptr;
   int2* d_items_lpt = nullptr;
   int2* d_items_nat = nullptr;
-  int* d_queue = nullptr;  // [0]: discretize, [1]: vjp
+  int* d_queue = nullptr;  // [0..1]: discretize, [2..3]: vjp (two counters each: lpt_order 2 uses both)
+  int2* d_items_sm = nullptr;  // lpt_order 2: foot-link items, then the others (bucket order)
+  int n_foot_items = 0, split_sm = 0;
   unsigned* d_status = nullptr;
   ciscvx_tune tune{4, 2, 1, 1, 0};
   ciscvx_tune tune_fused{4, 2, 1, 0, 0, 0};  // launch shape of the fused discretize+VJP pass
@@ -182,6 +187,7 @@ bool tune_ok(const ciscvx_tune& t) {
   return (t.warps_per_cta == 1 || t.warps_per_cta == 2 || t.warps_per_cta == 4 ||
           t.warps_per_cta == 8) &&
          t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && t.occupancy >= 0 && t.occupancy <= 2 &&
+         t.lpt_order >= 0 && t.lpt_order <= 2 &&
          (t.occupancy == 0 || t.warps_per_cta <= 4) && (t.split == 0 || (t.split == 1 && t.occupancy == 0));
 }
 
@@ -190,6 +196,7 @@ void free_chunks(ChunkTables& t) {
   cudaFree(t.d_groups);
   cudaFree(t.d_items_lpt);
   cudaFree(t.d_items_nat);
+  cudaFree(t.d_items_sm);
   for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
   if (t.s_in) cudaStreamDestroy(t.s_in);
   if (t.s_comp) cudaStreamDestroy(t.s_comp);
@@ -208,6 +215,7 @@ void free_plan(ciscvx_batch_plan* p) {
   cudaFree(p->d_groups);
   cudaFree(p->d_items_lpt);
   cudaFree(p->d_items_nat);
+  cudaFree(p->d_items_sm);
   cudaFree(p->d_queue);
   cudaFree(p->d_status);
   cudaFree(p->d_cpl_entries);
@@ -226,12 +234,16 @@ cudaError_t upload(T** dst, const std::vector<T>& v) {
 
 // Host work decomposition of instances [inst_off[c], inst_off[c+1]) for each
 // chunk c: bucket (model, n_sub) -> entries (instance, k) -> groups of 32 ->
-// items (group x link), items of each chunk contiguous, in cost order (lpt) or
-// in bucket order (nat).  Also returns the tuning key of the whole batch.
+// items (group x link), items of each chunk contiguous, in cost order (lpt),
+// in bucket order (nat), or as two queues (sm: the foot-link items in bucket
+// order, then the others in bucket order; foot_cnt[c] of them are foot-link
+// items).  Also returns the tuning key of the whole batch and the estimated
+// cost of the foot-link and of all items.
 struct HostDecomp {
-  std::vector<int2> entries, items_lpt, items_nat;
+  std::vector<int2> entries, items_lpt, items_nat, items_sm;
   std::vector<int4> groups;
-  std::vector<int> item_off;
+  std::vector<int> item_off, foot_cnt;
+  double foot_cost = 0.0, all_cost = 0.0;
   std::string key;
 };
 
@@ -267,6 +279,17 @@ HostDecomp decompose(const ciscvx_batch_plan* p, const std::vector<int>& inst_of
       }
     }
     for (auto& x : costed) d.items_nat.push_back(x.second);
+    int nfoot = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (auto& x : costed) {
+        const int4 g = d.groups[x.second.x];
+        const bool foot = p->models[g.x]->host.body[x.second.y].contact >= 0;
+        if (foot != (pass == 0)) continue;
+        d.items_sm.push_back(x.second);
+        if (foot) { ++nfoot; d.foot_cost += (double)x.first; }
+        d.all_cost += (double)x.first;
+      }
+    d.foot_cnt.push_back(nfoot);
     std::stable_sort(costed.begin(), costed.end(),
                      [](const std::pair<long long, int2>& a, const std::pair<long long, int2>& b) {
                        return a.first > b.first;
@@ -277,16 +300,28 @@ HostDecomp decompose(const ciscvx_batch_plan* p, const std::vector<int>& inst_of
   return d;
 }
 
+// SMs that take the foot-link queue first under lpt_order 2: their share of
+// the estimated cost, at least one SM for each queue.
+int split_sms(const ciscvx_batch_plan* p, const HostDecomp& d) {
+  if (d.all_cost <= 0.0 || p->sm_count < 2) return 0;
+  const int f = (int)std::lround(p->sm_count * d.foot_cost / d.all_cost);
+  return std::min(std::max(f, 1), p->sm_count - 1);
+}
+
 BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot, const ciscvx_tune& t) {
   BatchCommon c;
   c.models = p->d_models;
   c.inst = p->d_inst;
   c.entries = p->d_entries;
   c.groups = p->d_groups;
-  c.items = t.lpt_order ? p->d_items_lpt : p->d_items_nat;
+  c.items = t.lpt_order == 2 ? p->d_items_sm : (t.lpt_order ? p->d_items_lpt : p->d_items_nat);
   c.n_items = p->n_items;
   c.persistent = t.ctas_per_sm > 0;
-  c.queue = p->d_queue + queue_slot;
+  c.two_q = (t.lpt_order == 2 && c.persistent) ? 1 : 0;
+  c.n_first = p->n_foot_items;
+  c.split_sm = p->split_sm;
+  c.sm_count = p->sm_count;
+  c.queue = p->d_queue + 2 * queue_slot;
   c.status = p->d_status;
   c.layout = p->layout;
   c.ck_smem = 0;
@@ -299,8 +334,10 @@ BatchCommon common_chunk(const ciscvx_batch_plan* p, int queue_slot, int c, cons
   const ChunkTables& t = p->chunks;
   b.entries = t.d_entries;
   b.groups = t.d_groups;
-  b.items = (tu.lpt_order ? t.d_items_lpt : t.d_items_nat) + t.item_off[c];
+  b.items = (tu.lpt_order == 2 ? t.d_items_sm : (tu.lpt_order ? t.d_items_lpt : t.d_items_nat)) + t.item_off[c];
   b.n_items = t.item_off[c + 1] - t.item_off[c];
+  b.n_first = t.foot_cnt[c];
+  b.split_sm = t.split_sm;
   return b;
 }
 
@@ -318,7 +355,7 @@ void grid_for(const ciscvx_batch_plan* p, const ciscvx_tune& t, int n_items, uns
 cudaError_t launch_disc_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_io* io,
                           cudaStream_t st) {
   if (c.persistent) {
-    cudaError_t e = cudaMemsetAsync(c.queue, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(c.queue, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
   }
   unsigned blocks, threads;
@@ -386,7 +423,7 @@ cudaError_t launch_disc(ciscvx_batch_plan* p, const ciscvx_batch_io* io, cudaStr
 cudaError_t launch_vjp_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_vjp_io* io,
                          double* part, double* ps, double* pL, int i0, int i1, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), s);
+  if (c.persistent) e = cudaMemsetAsync(c.queue, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   unsigned blocks, threads;
   grid_for(p, p->tune, c.n_items, blocks, threads);
@@ -451,12 +488,13 @@ cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const cis
                            const ciscvx_batch_vjp_io* vio, double* part, double* ps, double* pL,
                            int i0, int i1, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (c.persistent) e = cudaMemsetAsync(c.queue, 0, sizeof(int), s);
+  if (c.persistent) e = cudaMemsetAsync(c.queue, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   unsigned blocks, threads;
   if (p->tune_fused.split) {  // linearization and adjoint of each item on two warps
     BatchCommon cs = c;
     cs.n_items = 2 * c.n_items;
+    cs.two_q = 0;  // one counter over the doubled item list
     grid_for(p, p->tune_fused, cs.n_items, blocks, threads);
     e = launch_disc_vjp_split(cs, c.n_items, p->prec, p->compact, blocks, threads, io->X, io->U,
                               io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty, vio->w,
@@ -622,6 +660,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   p->key = std::to_string(precision) + "|" + std::to_string(layout) + "|" +
            (p->compact ? "c|" : "d|") + dec.key;
   p->n_items = (int)dec.items_lpt.size();
+  p->n_foot_items = dec.foot_cnt.empty() ? 0 : dec.foot_cnt[0];
+  p->split_sm = split_sms(p, dec);
   p->items_lpt = dec.items_lpt;
   p->items_nat = dec.items_nat;
   const std::vector<int2>& entries = dec.entries;
@@ -662,7 +702,8 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (e == cudaSuccess) e = upload(&p->d_groups, groups);
   if (e == cudaSuccess) e = upload(&p->d_items_lpt, p->items_lpt);
   if (e == cudaSuccess) e = upload(&p->d_items_nat, p->items_nat);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_queue, 2 * sizeof(int));
+  if (e == cudaSuccess) e = upload(&p->d_items_sm, dec.items_sm);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_queue, 4 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
@@ -793,6 +834,8 @@ const ciscvx_tune kTuneCandidates[] = {
     {4, 2, 1, 0, 0}, {8, 1, 1, 0, 0}, {2, 4, 1, 0, 0}, {1, 8, 1, 0, 0}, {4, 0, 1, 0, 0},
     {4, 2, 0, 0, 0}, {4, 3, 1, 0, 1}, {2, 6, 1, 0, 1}, {4, 4, 1, 0, 2}, {2, 8, 1, 0, 2},
     {4, 0, 1, 0, 1}, {4, 0, 1, 0, 2},
+    // SM-partitioned foot-link / other-link queues (lpt_order 2)
+    {4, 3, 2, 0, 1}, {4, 2, 2, 0, 0}, {4, 4, 2, 0, 2},
 };
 // Split-form candidates of the fused pass (small batches only).
 const ciscvx_tune kSplitCandidates[] = {{1, 0, 1, 0, 0, 1}, {2, 0, 1, 0, 0, 1}, {4, 0, 1, 0, 0, 1}};
@@ -974,6 +1017,9 @@ cudaError_t ensure_chunks(ciscvx_batch_plan* p, int K) {
   if (e == cudaSuccess) e = upload(&t.d_groups, d.groups);
   if (e == cudaSuccess) e = upload(&t.d_items_lpt, d.items_lpt);
   if (e == cudaSuccess) e = upload(&t.d_items_nat, d.items_nat);
+  if (e == cudaSuccess) e = upload(&t.d_items_sm, d.items_sm);
+  t.foot_cnt = d.foot_cnt;
+  t.split_sm = split_sms(p, d);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_out, cudaStreamNonBlocking);

@@ -15,6 +15,15 @@ struct BatchCommon {
   const int2* items;     // (group, link)
   int n_items;
   int persistent;
+  // two_q (persistent launches, lpt_order 2): items [0, n_first) are the
+  // foot-link items and [n_first, n_items) the others, each pulled from its
+  // own counter (queue[0], queue[1]); the CTAs on SMs [0, split_sm) take the
+  // foot-link queue, the others the second one, and each moves to the other
+  // queue when its own runs dry.  An SM thus runs one link kind's code (the
+  // instruction cache holds one of them), and the two kinds of an interval
+  // group run at about the same time (its inputs and the output sectors its
+  // links share are still in L2).
+  int two_q, n_first, split_sm, sm_count;
   int* queue;
   unsigned* status;
   int layout;
@@ -25,6 +34,27 @@ __device__ __forceinline__ int next_item(const BatchCommon& c, int& local_iter) 
   if (!c.persistent) {
     const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     return local_iter++ == 0 ? w : c.n_items;
+  }
+  if (c.two_q) {
+    // local_iter: 0 own queue, 1 the other one, 2 both exhausted (warp-uniform)
+    int it = c.n_items;
+    if ((threadIdx.x & 31) == 0) {
+      // SM ids need not be contiguous: compare smid / nsmid with split_sm / sm_count
+      unsigned smid, nsmid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+      const int mine =
+          (unsigned long long)smid * (unsigned)c.sm_count < (unsigned long long)c.split_sm * nsmid ? 0 : 1;
+      while (local_iter < 2) {
+        const int q = local_iter == 0 ? mine : 1 - mine;
+        const int nq = q == 0 ? c.n_first : c.n_items - c.n_first;
+        const int k = atomicAdd(c.queue + q, 1);
+        if (k < nq) { it = (q == 0 ? 0 : c.n_first) + k; break; }
+        ++local_iter;
+      }
+    }
+    local_iter = __shfl_sync(0xffffffffu, local_iter, 0);
+    return __shfl_sync(0xffffffffu, it, 0);
   }
   int it = 0;
   if ((threadIdx.x & 31) == 0) it = atomicAdd(c.queue, 1);

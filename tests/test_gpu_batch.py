@@ -22,6 +22,7 @@ TUNES = [
     {"warps_per_cta": 8, "ctas_per_sm": 1, "lpt_order": 1, "use_graph": 0, "occupancy": 0},
     {"warps_per_cta": 4, "ctas_per_sm": 3, "lpt_order": 1, "use_graph": 1, "occupancy": 1},
     {"warps_per_cta": 2, "ctas_per_sm": 0, "lpt_order": 1, "use_graph": 0, "occupancy": 2},
+    {"warps_per_cta": 4, "ctas_per_sm": 3, "lpt_order": 2, "use_graph": 1, "occupancy": 1},
 ]
 
 # The fused pass's autotuner candidates (warps per CTA, CTAs per SM, item
@@ -32,6 +33,8 @@ FUSED_CANDIDATES = [
     (4, 2, 1, 0, 0, 0), (8, 1, 1, 0, 0, 0), (2, 4, 1, 0, 0, 0), (1, 8, 1, 0, 0, 0), (4, 0, 1, 0, 0, 0),
     (4, 2, 0, 0, 0, 0), (4, 3, 1, 0, 1, 0), (2, 6, 1, 0, 1, 0), (4, 4, 1, 0, 2, 0), (2, 8, 1, 0, 2, 0),
     (4, 0, 1, 0, 1, 0), (4, 0, 1, 0, 2, 0),
+    # SM-partitioned foot-link / other-link queues
+    (4, 3, 2, 0, 1, 0), (4, 2, 2, 0, 0, 0), (4, 4, 2, 0, 2, 0),
     # split form (linearization and adjoint of an item on two warps), small batches
     (1, 0, 1, 0, 0, 1), (2, 0, 1, 0, 0, 1), (4, 0, 1, 0, 0, 1),
 ]
@@ -299,8 +302,8 @@ def test_sweep_4096x400x20_sampled(env, sweep):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("shape", ["autotune", (4, 2, 1, 0, 0), (4, 4, 1, 0, 2), (4, 3, 1, 0, 1)],
-                         ids=["autotuned", "occ0", "occ2", "occ1"])
+@pytest.mark.parametrize("shape", ["autotune", (4, 2, 1, 0, 0), (4, 4, 1, 0, 2), (4, 3, 1, 0, 1), (4, 3, 2, 0, 1)],
+                         ids=["autotuned", "occ0", "occ2", "occ1", "occ1-smqueues"])
 def test_sweep_fused_pass_full_size_sampled(env, sweep, shape):
     """The fused pass (ciscvx_batch_discretize_and_vjp, the bench's step) on the
     full 4096 x 400 x 20 sweep under the autotuner's pick and under each
