@@ -621,27 +621,43 @@ def run_ours(args):
             tv, = max_over_ranks([tv])
             paper[pr]["vjp"] = {"value": pp.N * world * max(1, args.steps // 2) / tv,
                                 "ms_per_call": tv / max(1, args.steps // 2) * 1e3}
+            del ws
+            torch.cuda.empty_cache()
+            # linearization + VJP in one call (one-instance plan): one nominal pass
+            # per chunk feeds both the tangent kernel and the adjoint
+            pl = api.BatchPlan([mp], [0], [pp.N], [pp.n_sub], precision=pr)
+            wsb = torch.empty(max(pl.vjp_workspace_size(), api.DISCRETIZE_WS_CAP), dtype=torch.uint8, device=dev)
+            ob = pl.alloc_outputs(dev)
+            _, gb = pl.discretize_and_vjp(Xp.reshape(-1), Up.reshape(-1), sp, wv.reshape(-1), rv.reshape(-1),
+                                          workspace=wsb, out=ob)
+            fb = lambda: pl.discretize_and_vjp(Xp.reshape(-1), Up.reshape(-1), sp, wv.reshape(-1),  # noqa: E731
+                                               rv.reshape(-1), workspace=wsb, out=ob, gout=gb)
+            barrier()
+            tb = time_steps(torch, fb, max(1, args.steps // 2), args.warmup, stream,
+                            name="paper dynamics: linearization + VJP")
+            barrier()
+            pl.sync_status()
+            tb, = max_over_ranks([tb])
+            paper[pr]["linearization_and_vjp"] = {
+                "value": pp.N * world * max(1, args.steps // 2) / tb, "ms_per_call": tb / max(1, args.steps // 2) * 1e3,
+                "what": "ciscvx_batch_discretize_and_vjp of a one-instance plan (one nominal pass for both)"}
             if pr == "fp32_phi" and not args.no_e2e:
                 # end to end through the public API: pinned host inputs copied in,
                 # linearization and VJP, every output copied back
-                hin = {k: v.cpu().pin_memory() for k, v in (("X", Xp), ("U", Up), ("s", sp), ("w", wv), ("rho", rv))}
-                lo2, hi2 = api.discretize_workspace_size(mp, pp.N, pp.n_sub, pr)
-                wsd = torch.empty(max(lo2, min(hi2, api.DISCRETIZE_WS_CAP)), dtype=torch.uint8, device=dev)
+                hin = {k: v.reshape(-1).cpu().pin_memory()
+                       for k, v in (("X", Xp), ("U", Up), ("s", sp), ("w", wv), ("rho", rv))}
                 din = {k: torch.empty_like(v, device=dev) for k, v in hin.items()}
                 res = {}
 
                 def e2e_step():
                     for k, v in hin.items():
                         din[k].copy_(v, non_blocking=True)
-                    o = api.discretize(mp, din["X"], din["U"], din["s"], pp.n_sub, pr, workspace=wsd,
-                                       out=res.get("out"))
-                    res["out"] = o
-                    g = api.discretize_vjp(mp, din["X"], din["U"], din["s"], din["w"], din["rho"], pp.n_sub, pr,
-                                           workspace=ws)
+                    o, g = pl.discretize_and_vjp(din["X"], din["U"], din["s"], din["w"], din["rho"], workspace=wsb,
+                                                 out=ob, gout=gb)
                     if "host" not in res:
                         res["host"] = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
-                                       for k, v in list(o.items()) + list(zip(("gX", "gU", "gs", "L"), g))}
-                    for k, v in list(o.items()) + list(zip(("gX", "gU", "gs", "L"), g)):
+                                       for k, v in list(o.items()) + list(g.items())}
+                    for k, v in list(o.items()) + list(g.items()):
                         res["host"][k].copy_(v, non_blocking=True)
 
                 e2e_step()
@@ -653,8 +669,8 @@ def run_ours(args):
                 paper[pr]["e2e"] = {"value": pp.N * world * max(1, args.steps // 2) / te, "unit": "intervals/s",
                                     "what": "linearization + VJP per interval, host buffers",
                                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-                del hin, din, res, wsd
-            del ws, wv, rv
+                del hin, din, res
+            del wsb, ob, gb, pl, wv, rv
             torch.cuda.empty_cache()
         del Xp, Up, sp, mp
         if world == 1 and not args.no_cpu_baseline:

@@ -508,7 +508,9 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_
  * workspace as for ciscvx_batch_discretize_vjp.  Launched directly (no graph).
  * With the fused tune's split = 1 (small batches) the two run on separate
  * warps of the same launch, each integrating the trajectory, as the two calls
- * would.  Plans with an Eq. (12) or a coupled-link instance make the two calls
+ * would.  Coupled-link instances take one nominal pass per chunk for both
+ * (its stage data feed the tangent kernel and the adjoint), in the coupled
+ * part of the workspace.  Plans with an Eq. (12) instance make the two calls
  * in turn.  Errors: as the two calls. */
 ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
                                               const ciscvx_batch_vjp_io* vjp, void* workspace,

@@ -482,6 +482,11 @@ cudaError_t launch_coupled_vjps(ciscvx_batch_plan* p, const ciscvx_batch_vjp_io*
   return cudaSuccess;
 }
 
+// The coupled instances of [i0, i1) one after another: linearized, and with
+// `vjp` also their VJP from the same nominal pass (defined below).
+cudaError_t run_coupled_range(ciscvx_batch_plan* p, const ciscvx_batch_io* io, const ciscvx_batch_vjp_io* vjp,
+                              void* ws, size_t ws_bytes, int i0, int i1, cudaStream_t st);
+
 // Discretize + VJP of the items of `c` in one pass, then the per-instance
 // finish over instances [i0, i1).  vio's X, U, s are not used (io's are).
 cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const ciscvx_batch_io* io,
@@ -808,7 +813,7 @@ ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* p, const ciscvx
   ciscvx_status st = check_io(p, io);
   if (st == CISCVX_OK) st = check_vjp(p, vjp, false, workspace, ws_bytes);
   if (st != CISCVX_OK) return st;
-  if (p->any_cpl || p->any_aux) {  // the two calls in sequence, on io's inputs
+  if (p->any_aux) {  // the two calls in sequence, on io's inputs
     st = ciscvx_batch_discretize(p, io, stream);
     if (st != CISCVX_OK) return st;
     ciscvx_batch_vjp_io v = *vjp;
@@ -822,6 +827,11 @@ ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* p, const ciscvx
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
   cudaError_t e = launch_fused_c(p, common_of(p, 0, p->tune_fused), io, vjp, part, ps, pL, 0, p->n_inst, s);
+  // coupled instances: linearization and VJP from one nominal pass each, in
+  // the coupled part of the workspace
+  if (e == cudaSuccess && p->any_cpl)
+    e = run_coupled_range(p, io, vjp, (char*)workspace + cpl_ws_offset(p), ws_bytes - cpl_ws_offset(p), 0,
+                          p->n_inst, s);
   if (e != cudaSuccess) return set_error(CISCVX_ECUDA, "fused launch: %s", cudaGetErrorString(e));
   return CISCVX_OK;
 }
@@ -1055,14 +1065,16 @@ cudaError_t run_coupled_range(ciscvx_batch_plan* p, const ciscvx_batch_io* io, c
     char* Bm = nu ? (char*)io->Bm + I.b * el : nullptr;
     char* Bp = nu ? (char*)io->Bp + I.b * el : nullptr;
     char* S = (char*)io->S + I.v * el;
-    e = launch_coupled(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr, io->s + I.s,
-                       A, Bm, Bp, S, io->defect + I.v, nc ? io->penalty + I.p : nullptr, p->d_cpl_ws, chunk,
-                       p->d_status, st, nullptr, nullptr, p->compact);
-    if (e == cudaSuccess && vjp)
-      e = launch_coupled_vjp(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
-                             io->s + I.s, vjp->w + I.v, nc ? vjp->rho + I.p : nullptr, vjp->gX + I.x,
-                             nu ? vjp->gU + I.u : nullptr, vjp->gs + I.s, vjp->L ? vjp->L + i : nullptr, ws,
-                             ws_bytes, p->d_status, st);
+    if (vjp)  // the linearization and the VJP from one nominal pass per chunk
+      e = launch_coupled_and_vjp(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
+                                 io->s + I.s, A, Bm, Bp, S, io->defect + I.v, nc ? io->penalty + I.p : nullptr,
+                                 vjp->w + I.v, nc ? vjp->rho + I.p : nullptr, vjp->gX + I.x,
+                                 nu ? vjp->gU + I.u : nullptr, vjp->gs + I.s, vjp->L ? vjp->L + i : nullptr, ws,
+                                 ws_bytes, p->d_status, st, p->compact);
+    else
+      e = launch_coupled(T, I.N, I.nsub, p->prec, p->layout, io->X + I.x, nu ? io->U + I.u : nullptr,
+                         io->s + I.s, A, Bm, Bp, S, io->defect + I.v, nc ? io->penalty + I.p : nullptr,
+                         p->d_cpl_ws, chunk, p->d_status, st, nullptr, nullptr, p->compact);
   }
   return e;
 }

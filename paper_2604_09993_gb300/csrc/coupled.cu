@@ -1202,6 +1202,92 @@ cudaError_t run_vjp(const CplTab& T, long N, int nsub, int layout, const double*
   return cudaSuccess;
 }
 
+// The linearization and the reverse-mode VJP of intervals [0, N) of one
+// instance from one nominal pass per chunk: the nominal kernel writes the
+// stage data (and the defects, penalty increments and closed-form columns of
+// A into the outputs), then the tangent kernel forms the integrated columns
+// and the adjoint kernel the gradient from the same stage data.  Workspace as
+// for the VJP (cpl_adjoint_bytes of a chunk; its defect / penalty regions are
+// unused).  Outputs equal those of the two calls.
+template <typename TP, int SCH>
+cudaError_t run_both(const CplTab& T, long N, int nsub, int layout, const double* X, const double* U,
+                     const double* s, void* A, void* Bm, void* Bp, void* S, double* defect, double* penalty,
+                     const double* w, const double* rho, double* gX, double* gU, double* gs, double* L, void* ws,
+                     size_t ws_bytes, unsigned* status, cudaStream_t st, int cmp) {
+  const int prec = std::is_same<TP, double>::value ? CISCVX_FP64 : CISCVX_FP32_PHI;
+  const CplJit* jnom = cpl_jit_nominal(T, prec);
+  const CplJit* jtan = cpl_jit_tangent(T, prec);
+  const CplJit* jadj = cpl_jit_adjoint(T, prec);
+  cudaError_t e = prepare<TP, SCH>(T);
+  if (e != cudaSuccess) return e;
+  static bool adj_ready = false;
+  if (!adj_ready) {
+    e = cudaFuncSetAttribute(k_cpl_adjoint<TP, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e != cudaSuccess) return e;
+    adj_ready = true;
+  }
+  const size_t sm1 = (size_t)T.n_size * sizeof(double) * 32;
+  const int tbs = tangent_block<TP>(T);
+  const size_t sm2 = (size_t)tbs * T.t_size * sizeof(TP);
+  const int bs = adjoint_block<TP>(T);
+  const size_t sm3 = (size_t)bs * (2 * T.nlive + T.nquad + T.stages * T.nlive + 3 * T.nb + T.nk + 2 * T.nu) *
+                     sizeof(TP);
+  long lo = 1, hi = N;
+  while (lo < hi) {
+    const long mid = (lo + hi + 1) / 2;
+    if (cpl_adjoint_bytes(T, mid, nsub, prec) <= ws_bytes) lo = mid; else hi = mid - 1;
+  }
+  const long chunk = wave_chunk<TP, SCH>(jnom, sm1, lo);
+  const CplAdjLayout Ly = cpl_adjoint_layout(T, chunk, nsub, prec);
+  char* base = (char*)ws;
+  TP* sd = (TP*)(base + Ly.stage);
+  double* ubar = (double*)(base + Ly.ubar);
+  if (L) e = cudaMemsetAsync(L, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const int nxt = T.nxt, nu = T.nu, nc = T.nc;
+  for (long i0 = 0; i0 < N; i0 += chunk) {
+    const long n = std::min<long>(chunk, N - i0);
+    if (jnom)
+      e = cpl_jit_launch_nominal(*jnom, T, i0, n, nsub, layout, X, U, s, sd, A, defect, penalty, status, st,
+                                 nullptr, nullptr, cmp);
+    else
+      k_cpl_nominal<TP, SCH><<<(unsigned)((n + 31) / 32), 32, sm1, st>>>(
+          T, i0, n, nsub, layout, X, U, s, sd, (TP*)A, defect, penalty, status, nullptr, nullptr, cmp);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long threads = n * T.cnt;
+    if (jtan)
+      e = cpl_jit_launch(*jtan, T, prec, i0, n, nsub, s, sd, A, Bm, Bp, S, status, st, layout, nullptr, nullptr,
+                         cmp);
+    else
+      k_cpl_tangent<TP, SCH><<<(unsigned)((threads + tbs - 1) / tbs), tbs, sm2, st>>>(
+          T, i0, n, nsub, s, (const TP*)sd, (TP*)A, (TP*)Bm, (TP*)Bp, (TP*)S, status, layout, nullptr, nullptr,
+          cmp);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (jadj)
+      e = cpl_jit_launch_adjoint(*jadj, T, prec, i0, n, N, nsub, s, sd, w, rho, gX, gs, ubar, status, st);
+    else
+      k_cpl_adjoint<TP, SCH><<<(unsigned)((n + bs - 1) / bs), bs, sm3, st>>>(T, i0, n, N, nsub, s, sd, w, rho,
+                                                                           gX, gs, ubar, status);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (nu > 0)
+      k_cpl_adjoint_u<<<(unsigned)((n * nu + 127) / 128), 128, 0, st>>>(nu, i0, n, layout, ubar, gU);
+    if (L) {
+      const long tot = n * (nxt + nc);
+      const int nblk = (int)std::min<long>(ADJ_LRED_BLOCKS, (tot + 2047) / 2048);
+      double* part = (double*)(base + Ly.lpart);
+      k_cpl_adjoint_L<<<nblk, 256, 0, st>>>(nxt, nc, i0, n, defect + i0 * nxt,
+                                            nc > 0 ? penalty + i0 * nc : nullptr, w, rho, part);
+      k_cpl_adjoint_L_sum<<<1, 32, 0, st>>>(part, nblk, L);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Butcher tableaux: classical RK4 and Fehlberg's 4(5) pair advanced with its
 // fifth-order weights (the published coefficients).
 void set_tableau(int scheme, CplTab& T) {
@@ -1395,6 +1481,20 @@ cudaError_t launch_coupled_vjp(const CplTab& T, long N, int nsub, int prec, int 
                     : run_vjp<double, 0>(T, N, nsub, layout, X, U, s, w, rho, gX, gU, gs, L, ws, ws_bytes, status, st);
   return T.scheme ? run_vjp<float, 1>(T, N, nsub, layout, X, U, s, w, rho, gX, gU, gs, L, ws, ws_bytes, status, st)
                   : run_vjp<float, 0>(T, N, nsub, layout, X, U, s, w, rho, gX, gU, gs, L, ws, ws_bytes, status, st);
+}
+
+cudaError_t launch_coupled_and_vjp(const CplTab& T, long N, int nsub, int prec, int layout, const double* X,
+                                   const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
+                                   double* defect, double* penalty, const double* w, const double* rho,
+                                   double* gX, double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
+                                   unsigned* status, cudaStream_t st, bool compact) {
+  const int c = compact ? 1 : 0;
+#define CISCVX_BOTH(TP, SCH)                                                                               \
+  run_both<TP, SCH>(T, N, nsub, layout, X, U, s, A, Bm, Bp, S, defect, penalty, w, rho, gX, gU, gs, L, ws, \
+                    ws_bytes, status, st, c)
+  if (prec == CISCVX_FP64) return T.scheme ? CISCVX_BOTH(double, 1) : CISCVX_BOTH(double, 0);
+  return T.scheme ? CISCVX_BOTH(float, 1) : CISCVX_BOTH(float, 0);
+#undef CISCVX_BOTH
 }
 
 cudaError_t cpl_prepare(const CplTab& T, int prec) {

@@ -144,6 +144,15 @@ cudaError_t cpl_jit_launch(const CplJit& J, const CplTab& T, int prec, long i0, 
                            unsigned* status, cudaStream_t st, int layout, const int2* entries,
                            const DevInst* inst, int cmp);
 
+// The linearization (as launch_coupled, single instance) and the VJP (as
+// launch_coupled_vjp) of the same intervals from one nominal pass per chunk;
+// workspace as for launch_coupled_vjp.
+cudaError_t launch_coupled_and_vjp(const CplTab& T, long N, int nsub, int prec, int layout, const double* X,
+                                   const double* U, const double* s, void* A, void* Bm, void* Bp, void* S,
+                                   double* defect, double* penalty, const double* w, const double* rho,
+                                   double* gX, double* gU, double* gs, double* L, void* ws, size_t ws_bytes,
+                                   unsigned* status, cudaStream_t st, bool compact);
+
 // Reverse-mode VJP of the coupled path (coupled.cu): the nominal kernel's
 // forward pass into the stage data of a chunk, then the adjoint kernel (thread
 // = interval) backward over the stages; no dense block is formed.  Workspace

@@ -83,8 +83,12 @@ def test_fused_entry_point_with_contract_instances(env):
     out2 = plan.discretize(X, U, s)
     g2 = plan.discretize_vjp(X, U, s, w, rho)
     plan.sync_status()
+    # coupled instances: one nominal pass per instance feeds both outputs; the
+    # separate linearization groups the coupled intervals of the plan into
+    # warps differently (the angle chain's Taylor tier is a warp vote), so
+    # the blocks agree to rounding; the gradients take the same chunks
     for k in ("A", "Bm", "Bp", "S", "defect", "penalty"):
-        assert torch.equal(out[k], out2[k]), k
+        assert block_err(out[k].cpu().numpy(), out2[k].cpu().numpy()) <= 1e-13, k
     for k in ("gX", "gU", "gs", "L"):
         assert torch.equal(gout[k], g2[k]), k
 

@@ -580,3 +580,51 @@ def test_affine_term(env, precision, tol, layout):
     zg = got["z"].cpu().numpy()
     for k in range(p.N):
         assert block_err(zg[k], z[k]) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("out_format", ["dense", "compact"])
+def test_shared_nominal_pass_in_the_fused_entry_point(env, precision, tol, out_format):
+    """ciscvx_batch_discretize_and_vjp on a plan of default and coupled models:
+    the coupled instances take one nominal pass for the linearization and the
+    VJP.  Against the two separate calls (to rounding: the separate
+    linearization groups the coupled intervals into warps across instances,
+    and the default-model instances take the fused per-link pass) and against
+    the oracle."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(61)
+    robots = [synth.hopper(rng), synth.with_paper_dynamics(synth.biped(rng), **PAPER),
+              synth.with_paper_dynamics(synth.cheetah7(rng), joint_forces=1, scheme=0)]
+    probs, midx = [], []
+    for i in range(7):
+        mi = i % 3
+        probs.append(synth.draw_instance(robots[mi], rng, int(rng.integers(1, 45)), int(rng.choice([1, 2])),
+                                         q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15), with_cotangents=True))
+        midx.append(mi)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [q.N for q in probs], [q.n_sub for q in probs], precision=precision,
+                         out_format=out_format)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X, U, sv = (t(plan.pack([getattr(q, k) for q in probs], k)) for k in ("X", "U", "s"))
+    w = t(plan.pack([q.w for q in probs], "defect"))
+    rho = t(plan.pack([q.rho for q in probs], "penalty"))
+    out, g = plan.discretize_and_vjp(X, U, sv, w, rho)
+    out = {k: v.clone() for k, v in out.items()}
+    g = {k: v.clone() for k, v in g.items()}
+    out2 = plan.discretize(X, U, sv)
+    g2 = plan.discretize_vjp(X, U, sv, w, rho)
+    plan.sync_status()
+    btol = 1e-13 if precision == "fp64" else 1e-6
+    for k in out:
+        assert block_err(out[k].double().cpu().numpy(), out2[k].double().cpu().numpy()) <= btol, k
+    for k in ("gX", "gU", "gs", "L"):  # (the default-model instances: fused pass against the adjoint kernel)
+        e = block_err(g[k].cpu().numpy(), g2[k].cpu().numpy())
+        assert e <= (1e-12 if precision == "fp64" else 1e-5), (k, e)
+    host = {k: v.cpu().numpy() for k, v in g.items()}
+    for i, q in enumerate(probs):
+        rX, rU, rs, rL = oracle.vjp(q.robot.as_dict(), q.X, q.U, q.s, q.w, q.rho, q.n_sub)
+        assert block_err(plan.unpack(host["gX"], "X", i, q.X.shape), rX) <= tol, i
+        assert block_err(plan.unpack(host["gU"], "U", i, q.U.shape), rU) <= tol, i
+        assert block_err(plan.unpack(host["gs"], "s", i, q.s.shape), rs) <= tol, i
+        assert abs(host["L"][i] - rL) <= TOL_FP64 * max(1.0, abs(rL)) + (0 if precision == "fp64" else tol), i
