@@ -909,7 +909,19 @@ def run_ours(args):
         tv, = max_over_ranks([tv])
         cross["vjp"] = {"value": units * args.steps / tv, "ms_per_step": tv / args.steps * 1e3,
                         "workspace_bytes": px.vjp_workspace_size()}
-        del gx, wsx, wx, rx, px
+        # both in one pass (ciscvx_batch_discretize_and_vjp: one trajectory per interval)
+        ox = px.alloc_outputs(dev)
+        px.autotune_fused(Xx, Ux, sx, wx, rx, workspace=wsx, out=ox)
+        _, gx = px.discretize_and_vjp(Xx, Ux, sx, wx, rx, workspace=wsx, out=ox, gout=gx)
+        barrier()
+        tb = time_steps(torch, lambda: px.discretize_and_vjp(Xx, Ux, sx, wx, rx, workspace=wsx, out=ox, gout=gx),
+                        args.steps, args.warmup, stream, name="Eq. (12) model, linearization + VJP")
+        barrier()
+        px.sync_status()
+        tb, = max_over_ranks([tb])
+        cross["linearization_and_vjp"] = {"value": units * args.steps / tb, "ms_per_step": tb / args.steps * 1e3,
+                                          "tune": px.tune_fused()}
+        del gx, wsx, wx, rx, ox, px
         torch.cuda.empty_cache()
         # the same with compact outputs (the packing of X, U, s does not depend on the format)
         pxc = api.BatchPlan(mx, bx.model_idx, bx.Ns, bx.n_subs, precision=prec, out_format="compact")

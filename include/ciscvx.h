@@ -510,8 +510,7 @@ ciscvx_status ciscvx_batch_discretize_vjp(ciscvx_batch_plan* plan, const ciscvx_
  * warps of the same launch, each integrating the trajectory, as the two calls
  * would.  Coupled-link instances take one nominal pass per chunk for both
  * (its stage data feed the tangent kernel and the adjoint), in the coupled
- * part of the workspace.  Plans with an Eq. (12) instance make the two calls
- * in turn.  Errors: as the two calls. */
+ * part of the workspace.  Errors: as the two calls. */
 ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,
                                               const ciscvx_batch_vjp_io* vjp, void* workspace,
                                               size_t ws_bytes, void* stream);
@@ -543,8 +542,7 @@ ciscvx_status ciscvx_batch_autotune(ciscvx_batch_plan* plan, const ciscvx_batch_
  *     minimum of ciscvx_batch_vjp_workspace_sizes).
  * Coupled-link instances are linearized one after another within their
  * chunk (and their VJP taken by the coupled path's reverse-mode adjoint).
- * In a plan with an Eq. (12) instance each chunk is linearized, then its VJP
- * taken, by the separate kernels (the fused pass has no Eq. (12) form).
+
  * The first call with a new n_chunks builds the chunked work tables and
  * streams (device allocation); later calls with the same n_chunks allocate
  * nothing.  Errors: EINVAL (null buffers, n_chunks outside [1, n_inst], short
@@ -559,9 +557,7 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* plan, int n_chunks,
  * (its launch shape is kept apart from the discretization's: the fused kernel
  * holds more state per thread).  When the fused pass would run at most one
  * warp per scheduler (work items <= 4 x SMs), the split form (tune.split = 1,
- * one warp per item, 1, 2 or 4 warps per CTA) is among the candidates.  A
- * plan with an Eq. (12) instance does not use the fused pass: nothing is
- * timed and the current shape is returned.
+ * one warp per item, 1, 2 or 4 warps per CTA) is among the candidates.
  * Overwrites the outputs; workspace as for ciscvx_batch_discretize_vjp.
  * Errors: as ciscvx_batch_discretize_and_vjp. */
 ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* plan, const ciscvx_batch_io* io,

@@ -137,7 +137,7 @@ struct ciscvx_batch_plan {
   int n_inst = 0, n_models = 0, prec = 0, layout = 0, device = 0, sm_count = 0, max_nsub = 0;
   bool compact = false;  // CISCVX_OUT_COMPACT
   bool all_nu0 = true, all_nc0 = true;
-  bool any_aux = false;  // some model uses the Eq. (12) auxiliary state (no fused pass: its VJP runs apart)
+  bool any_aux = false;  // some model uses the Eq. (12) auxiliary state (AUX kernel instantiations)
   bool any_cpl = false;  // some model has coupled links (coupled path, its own adjoint)
   // coupled-path groups: instances of one coupled model with one n_sub, as
   // (instance, k) entries; one stage-data workspace shared in stream order
@@ -501,7 +501,7 @@ cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const cis
     cs.n_items = 2 * c.n_items;
     cs.two_q = 0;  // one counter over the doubled item list
     grid_for(p, p->tune_fused, cs.n_items, blocks, threads);
-    e = launch_disc_vjp_split(cs, c.n_items, p->prec, p->compact, blocks, threads, io->X, io->U,
+    e = launch_disc_vjp_split(cs, c.n_items, p->prec, p->compact, p->any_aux, blocks, threads, io->X, io->U,
                               io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty, vio->w,
                               vio->rho, vio->gX, part, ps, pL, s);
     if (e == cudaSuccess && i1 > i0)
@@ -520,7 +520,7 @@ cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const cis
     cf.ck_smem = 1;
     smem = ck_bytes;
   }
-  e = launch_disc_vjp_fused(cf, p->prec, p->tune_fused.occupancy, p->compact, blocks, threads, io->X,
+  e = launch_disc_vjp_fused(cf, p->prec, p->tune_fused.occupancy, p->compact, p->any_aux, blocks, threads, io->X,
                             io->U, io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty,
                             vio->w, vio->rho, vio->gX, part, ps, pL, smem, s);
   if (e == cudaSuccess && i1 > i0)
@@ -813,15 +813,6 @@ ciscvx_status ciscvx_batch_discretize_and_vjp(ciscvx_batch_plan* p, const ciscvx
   ciscvx_status st = check_io(p, io);
   if (st == CISCVX_OK) st = check_vjp(p, vjp, false, workspace, ws_bytes);
   if (st != CISCVX_OK) return st;
-  if (p->any_aux) {  // the two calls in sequence, on io's inputs
-    st = ciscvx_batch_discretize(p, io, stream);
-    if (st != CISCVX_OK) return st;
-    ciscvx_batch_vjp_io v = *vjp;
-    v.X = io->X;
-    v.U = io->U;
-    v.s = io->s;
-    return ciscvx_batch_discretize_vjp(p, &v, workspace, ws_bytes, stream);
-  }
   cudaStream_t s = (cudaStream_t)stream;
   double* part = (double*)workspace;
   double* ps = part + p->part_total;
@@ -973,12 +964,6 @@ ciscvx_status ciscvx_batch_autotune_fused(ciscvx_batch_plan* p, const ciscvx_bat
   double* part = (double*)workspace;
   double* ps = part + p->part_total;
   double* pL = ps + p->pb_total;
-  // plans with an Eq. (12) model run the linearization and the VJP in turn:
-  // the fused pass is not used, nothing to tune
-  if (p->any_aux) {
-    if (chosen) *chosen = p->tune_fused;
-    return CISCVX_OK;
-  }
   // the split form only where the fused pass has at most one warp per scheduler
   const bool with_split = p->n_items <= 4 * p->sm_count;
   return autotune_slot(p, &p->tune_fused, "|fused", s, [&]() {
@@ -1152,13 +1137,8 @@ ciscvx_status ciscvx_batch_run_host(ciscvx_batch_plan* p, int n_chunks, const ci
     // compute
     if (e == cudaSuccess) e = cudaStreamWaitEvent(t.s_comp, ev_in, 0);
     if (e == cudaSuccess) {
-      if (vjp && !p->any_aux) {
-        e = launch_fused_c(p, common_chunk(p, 0, c, p->tune_fused), dev, &dv, part, ps, pL, i0, i1, t.s_comp);
-      } else {  // (Eq. (12) model: the linearization, then the adjoint, of the chunk)
-        e = launch_disc_c(p, common_chunk(p, 0, c, p->tune), dev, t.s_comp);
-        if (vjp && e == cudaSuccess)
-          e = launch_vjp_c(p, common_chunk(p, 1, c, p->tune), &dv, part, ps, pL, i0, i1, t.s_comp);
-      }
+      if (vjp) e = launch_fused_c(p, common_chunk(p, 0, c, p->tune_fused), dev, &dv, part, ps, pL, i0, i1, t.s_comp);
+      else e = launch_disc_c(p, common_chunk(p, 0, c, p->tune), dev, t.s_comp);
       if (e == cudaSuccess && p->any_cpl)
         e = run_coupled_range(p, dev, vjp ? &dv : nullptr, vjp ? (char*)workspace + cpl_ws_offset(p) : nullptr,
                               vjp ? ws_bytes - cpl_ws_offset(p) : 0, i0, i1, t.s_comp);

@@ -150,8 +150,9 @@ template <> struct Occ<2> { static constexpr int T = 128, B = 4; };  // <= 128 r
 
 // Discretize and VJP of the items of `c` in one pass (batch_fused.cu): the
 // discretization's forward sweep hands its checkpoints to the adjoint.
-// prec: CISCVX_FP64 / CISCVX_FP32_PHI; occ: register-cap variant; compact outputs.
-cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool compact,
+// prec: CISCVX_FP64 / CISCVX_FP32_PHI; occ: register-cap variant (ignored
+// with aux: an Eq. (12) model in the batch); compact outputs.
+cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool compact, bool aux,
                                   unsigned blocks, unsigned threads, const double* X,
                                   const double* U, const double* s, void* A, void* Bm, void* Bp,
                                   void* S, double* defect, double* penalty, const double* w,
@@ -163,7 +164,7 @@ cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool 
 // adjoint; c.n_items = 2n).  Each warp integrates the trajectory itself: more
 // work than the fused pass, but a shorter path per warp, for batches too
 // small to fill the GPU (batch_split.cu; no register cap).
-cudaError_t launch_disc_vjp_split(const BatchCommon& c, int n, int prec, bool compact,
+cudaError_t launch_disc_vjp_split(const BatchCommon& c, int n, int prec, bool compact, bool aux,
                                   unsigned blocks, unsigned threads, const double* X,
                                   const double* U, const double* s, void* A, void* Bm, void* Bp,
                                   void* S, double* defect, double* penalty, const double* w,

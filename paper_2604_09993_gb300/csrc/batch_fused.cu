@@ -11,7 +11,9 @@ namespace ciscvx {
 
 namespace {
 
-template <typename TP, int OCC, bool CMP>
+// AUX: the batch holds an Eq. (12) model (its foot links take the CROSS
+// forms; a separate instantiation, no register cap).
+template <typename TP, int OCC, bool CMP, bool AUX = false>
 __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B)
     k_batch_disc_vjp(BatchCommon c, const double* __restrict__ X, const double* __restrict__ U,
                      const double* __restrict__ s, TP* A, TP* Bm, TP* Bp, TP* S, double* defect,
@@ -59,7 +61,12 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B)
       Checkpoints ck;
       ck.sm = c.ck_smem ? ck_smem + threadIdx.x : nullptr;
       ck.sst = blockDim.x;
-      if (B.contact >= 0) {
+      if (AUX && M.aux && B.contact >= 0) {  // Eq. (12) model
+        disc_link<TP, true, CMP, true, true>(M, b, g.y, sk, xk, xk1, uL, uR, Ak, Bmk, Bpk, Sk, dk, pk,
+                                             nullptr, c.status, &ck);
+        vjp_link<TP, true, true, true>(M, b, g.y, sk, xk, xk1, uL, uR, wi + k * nxt, wkm1, rc,
+                                       gXi + (size_t)k * nxt, gXN, pp, psk, pLk, c.status, &ck);
+      } else if (B.contact >= 0) {
         disc_link<TP, true, CMP, true>(M, b, g.y, sk, xk, xk1, uL, uR, Ak, Bmk, Bpk, Sk, dk, pk,
                                        nullptr, c.status, &ck);
         vjp_link<TP, true, true>(M, b, g.y, sk, xk, xk1, uL, uR, wi + k * nxt, wkm1, rc,
@@ -76,7 +83,7 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B)
 
 }  // namespace
 
-cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool compact,
+cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool compact, bool aux,
                                   unsigned blocks, unsigned threads, const double* X,
                                   const double* U, const double* s, void* A, void* Bm, void* Bp,
                                   void* S, double* defect, double* penalty, const double* w,
@@ -91,7 +98,18 @@ cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool 
     if (compact) CISCVX_FUSED1(TP, OCC, true);  \
     else CISCVX_FUSED1(TP, OCC, false);         \
   } while (0)
-  if (prec == CISCVX_FP64) {
+  if (aux) {  // no register cap
+#define CISCVX_FUSED_AUX(TP, CMP)                                                                    \
+  k_batch_disc_vjp<TP, 0, CMP, true><<<blocks, threads, smem, st>>>(c, X, U, s, (TP*)A, (TP*)Bm, (TP*)Bp, \
+                                                                    (TP*)S, defect, penalty, w, rho, gX,  \
+                                                                    part, ps, pL)
+    if (prec == CISCVX_FP64) {
+      if (compact) CISCVX_FUSED_AUX(double, true); else CISCVX_FUSED_AUX(double, false);
+    } else {
+      if (compact) CISCVX_FUSED_AUX(float, true); else CISCVX_FUSED_AUX(float, false);
+    }
+#undef CISCVX_FUSED_AUX
+  } else if (prec == CISCVX_FP64) {
     if (occ == 1) CISCVX_FUSED(double, 1);
     else if (occ == 2) CISCVX_FUSED(double, 2);
     else CISCVX_FUSED(double, 0);

@@ -159,6 +159,7 @@ struct Checkpoints {
   // FP32 adjoint: the FP32 anchors of the stage recursion at each substep start
   float thf[MAXSUB_VJP], omf[MAXSUB_VJP], pyf[MAXSUB_VJP], vyf[MAXSUB_VJP];
   double th_end, om_end, Yom;
+  double Il, Ir, Ig;  // Eq. (12) model: lambda^c's state and input parts, rho^c's integral
   // the link's FOH input sums (AxL, AxR, AyL, AyR, PL, PR, QL, QR, TL, TR) and h = 1/n_sub
   double ins[10], h;
   // When sm is set, the FP32 anchors live in shared memory instead of

@@ -261,9 +261,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
   constexpr bool F32 = std::is_same<TP, float>::value;
   // CROSS: the link carries a contact of the Eq. (12) model (see the header
   // comment of input_cross); the kernels form no z for it (callers form it
-  // from the stored outputs) and no checkpoints (its VJP runs its own forward
-  // sweep: vjp_link with CROSS).
-  static_assert(!(CROSS && CK), "Eq. (12) model: no checkpoints");
+  // from the stored outputs).  Its checkpoints add the quadratures Il, Ir,
+  // Ig of the contact's rows.
   constexpr bool cross = FOOT && CROSS;
   const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
@@ -459,8 +458,8 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       const TP thA = anchor<TP>(th), omA = anchor<TP>(om), pyA = anchor<TP>(py), vyA = anchor<TP>(vy);
       const TP vxA = cross ? anchor<TP>(vx) : TP(0);
       if constexpr (CK && F32) {
-        ck->thf[i] = thA; ck->omf[i] = omA;
-        if (foot) { ck->pyf[i] = pyA; ck->vyf[i] = vyA; }
+        ck->put_f(i, 0, thA); ck->put_f(i, 1, omA);
+        if (foot) { ck->put_f(i, 2, pyA); ck->put_f(i, 3, vyA); }
       }
       TP kthA = TP(0), komA = TP(0), kpyA = TP(0), kvyA = TP(0), kvxA = TP(0);
       double kth = 0, kom = 0, ath_ = 0, aom_ = 0, kpy = 0, kvy = 0, apy = 0, avy = 0;
@@ -612,7 +611,10 @@ __device__ __forceinline__ void disc_link(const DevModel& M, int b, int nsub, do
       Yom = fma(-h6, ip0.H, Yom);
     }
   }
-  if constexpr (CK) { ck->th_end = th; ck->om_end = om; ck->Yom = Yom; }
+  if constexpr (CK) {
+    ck->th_end = th; ck->om_end = om; ck->Yom = Yom;
+    if constexpr (cross) { ck->Il = Il; ck->Ir = Ir; ck->Ig = Ig; }
+  }
 
   // ------------------------------------------------------------ outputs ---
   const TP one = TP(1);

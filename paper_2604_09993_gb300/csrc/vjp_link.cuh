@@ -33,7 +33,8 @@ namespace ciscvx {
 // theta, omega and v_x in the backward sweep (v_x gets an adjoint channel of
 // its own, forced like v_y); the other rows are integrals of the inputs
 // alone, whose gradients are their quadrature weights times the slopes.  The
-// forward sweep is the FP64 one in both precisions and takes all quadratures.
+// forward sweep is the FP64 one in both precisions and takes all quadratures
+// (fused: the discretization's sweep, handed over in the checkpoints).
 template <typename TP, bool FOOT, bool FUSED = false, bool CROSS = false>
 __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, double sd,
                                          const double* __restrict__ xk,
@@ -48,7 +49,6 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
                                          const Checkpoints* ckin = nullptr) {
   constexpr bool F32 = std::is_same<TP, float>::value;
   constexpr bool cross = FOOT && CROSS;
-  static_assert(!(CROSS && FUSED), "Eq. (12) model: no fused pass");
   const unsigned amask = __activemask();  // lanes running this link (they stay converged)
   const DevBody& B = M.body[b];
   const int nb = M.nb;
@@ -127,6 +127,7 @@ __device__ __forceinline__ void vjp_link(const DevModel& M, int b, int nsub, dou
     th = ck.th_end;
     om = ck.om_end;
     Yom = ck.Yom;
+    if constexpr (cross) { Il = ck.Il; Ir = ck.Ir; Ig = ck.Ig; }
   } else if constexpr (F32 && !cross) {
     // FP32 adjoint: stage values in float-float, the state accumulated in FP64
     // (state_df.cuh); the anchors at every substep start are the checkpoints,

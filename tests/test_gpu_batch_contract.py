@@ -86,11 +86,12 @@ def test_fused_entry_point_with_contract_instances(env):
     # coupled instances: one nominal pass per instance feeds both outputs; the
     # separate linearization groups the coupled intervals of the plan into
     # warps differently (the angle chain's Taylor tier is a warp vote), so
-    # the blocks agree to rounding; the gradients take the same chunks
+    # the blocks agree to rounding; per-link instances (Eq. (12) ones
+    # included) take the fused per-link pass
     for k in ("A", "Bm", "Bp", "S", "defect", "penalty"):
         assert block_err(out[k].cpu().numpy(), out2[k].cpu().numpy()) <= 1e-13, k
-    for k in ("gX", "gU", "gs", "L"):
-        assert torch.equal(gout[k], g2[k]), k
+    for k in ("gX", "gU", "gs", "L"):  # (per-link instances: fused pass against the adjoint kernel)
+        assert block_err(gout[k].cpu().numpy(), g2[k].cpu().numpy()) <= 1e-12, k
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])

@@ -205,6 +205,55 @@ def test_cross_vjp_matches_oracle(env, precision, tol, layout):
     assert abs(L.item() - rL) <= TOL_FP64 * max(1.0, abs(rL))
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_phi", TOL_FP32_PHI)])
+@pytest.mark.parametrize("out_format", ["dense", "compact"])
+def test_cross_fused_pass_in_mixed_batch(env, precision, tol, out_format):
+    """ciscvx_batch_discretize_and_vjp on a batch mixing the Eq. (12) model with
+    the default one: the fused pass (the Eq. (12) foot links record their
+    checkpoints and quadratures, and the adjoint starts from them) against the
+    two separate calls (to rounding) and the oracle."""
+    torch, oracle, api = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(71)
+    robots = [synth.with_cross_states(synth.biped(rng)), synth.hopper(rng),
+              synth.with_cross_states(synth.cheetah7(rng))]
+    probs, midx = [], []
+    for i in range(8):
+        mi = i % 3
+        probs.append(synth.draw_instance(robots[mi], rng, int(rng.integers(1, 50)), int(rng.choice([1, 3, 5])),
+                                         q_noise=0.1, u_dist="normal", s_range=(0.05, 0.15), with_cotangents=True))
+        midx.append(mi)
+    models = [api.Model(r) for r in robots]
+    plan = api.BatchPlan(models, midx, [q.N for q in probs], [q.n_sub for q in probs], precision=precision,
+                         out_format=out_format)
+    t = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+    X, U, s = (t(plan.pack([getattr(q, k) for q in probs], k)) for k in ("X", "U", "s"))
+    w = t(plan.pack([q.w for q in probs], "defect"))
+    rho = t(plan.pack([q.rho for q in probs], "penalty"))
+    ws = torch.empty(plan.vjp_workspace_size(), dtype=torch.uint8, device=dev)
+    plan.autotune_fused(X, U, s, w, rho, workspace=ws)
+    out, g = plan.discretize_and_vjp(X, U, s, w, rho, workspace=ws)
+    out = {k: v.clone() for k, v in out.items()}
+    g = {k: v.clone() for k, v in g.items()}
+    out2 = plan.discretize(X, U, s)
+    g2 = plan.discretize_vjp(X, U, s, w, rho)
+    plan.sync_status()
+    f32 = precision == "fp32_phi"
+    for k in out:
+        e = block_err(out[k].double().cpu().numpy(), out2[k].double().cpu().numpy())
+        assert e <= (1e-5 if f32 and k in PHI else 1e-13), (k, e)
+    for k in ("gX", "gU", "gs", "L"):
+        e = block_err(g[k].cpu().numpy(), g2[k].cpu().numpy())
+        assert e <= (1e-5 if f32 else 1e-12), (k, e)
+    host = {k: v.cpu().numpy() for k, v in g.items()}
+    for i, q in enumerate(probs):
+        rX, rU, rs, rL = oracle.vjp(q.robot.as_dict(), q.X, q.U, q.s, q.w, q.rho, q.n_sub)
+        assert block_err(plan.unpack(host["gX"], "X", i, q.X.shape), rX) <= tol, i
+        assert block_err(plan.unpack(host["gU"], "U", i, q.U.shape), rU) <= tol, i
+        assert block_err(plan.unpack(host["gs"], "s", i, q.s.shape), rs) <= tol, i
+        assert abs(host["L"][i] - rL) <= TOL_FP64 * max(1.0, abs(rL)), i
+
+
 def test_cross_vjp_central_differences(env):
     """The adjoint's gradient of L = sum_k w_k . defect_k + rho_k . penalty_k
     against central differences (h = 1e-6) of the oracle's flow map, every
