@@ -6,6 +6,7 @@ weight ...), builds it in a temporary directory, and runs the pin suites
 against that build through ``CISCVX_ORACLE_LIB``.  The pins must fail for
 every planted error; the real oracle must pass (the other test files).
 """
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
@@ -134,10 +135,12 @@ MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_reject_planted_error(name, old, new):
+def _run_mutant(name, old, new):
+    """Builds oracle.cpp with one planted error and runs the pin suites against
+    it; returns (pytest return code, end of its output)."""
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
+    if src.count(old) != 1:
+        return None, f"mutation anchor not found once: {name}"
     with tempfile.TemporaryDirectory() as tmp:
         mpath = os.path.join(tmp, "oracle_mut.cpp")
         lpath = os.path.join(tmp, "liboracle_mut.so")
@@ -147,7 +150,28 @@ def test_pins_reject_planted_error(name, old, new):
         env = dict(os.environ, CISCVX_ORACLE_LIB=lpath)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-        assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+        return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(request):
+    """Runs every selected mutation once, several at a time (each is an
+    independent compile plus a pytest subprocess), so the whole set takes
+    about its total time divided by the host's cores."""
+    selected = [it.callspec.params["name"] for it in request.session.items
+                if getattr(it, "originalname", None) == "test_pins_reject_planted_error"]
+    table = {m[0]: m for m in MUTATIONS}
+    workers = max(1, min(len(selected), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {n: ex.submit(_run_mutant, *table[n]) for n in selected}
+        return {n: f.result() for n, f in futs.items()}
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_reject_planted_error(name, old, new, mutant_results):
+    rc, out = mutant_results[name] if name in mutant_results else _run_mutant(name, old, new)
+    assert rc is not None, out
+    assert rc != 0, f"pins did not catch: {name}\n{out}"
 
 
 # Planted errors in the dense SOCP assembly (oracle/socp.py), caught by its pins.
@@ -177,10 +201,12 @@ SOCP_MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new", SOCP_MUTATIONS, ids=[m[0] for m in SOCP_MUTATIONS])
-def test_socp_pins_reject_planted_error(name, old, new, oracle_mod):
+def _run_socp_mutant(name, old, new, lib):
+    """Runs the SOCP pins against a copy of the oracle package whose socp.py
+    carries one planted error; returns (pytest return code, end of its output)."""
     src = open(SOCP_SRC).read()
-    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
+    if src.count(old) != 1:
+        return None, f"mutation anchor not found once: {name}"
     with tempfile.TemporaryDirectory() as tmp:
         # a tree whose oracle package carries the planted error; the built
         # oracle library and the product package are the real ones
@@ -190,8 +216,28 @@ def test_socp_pins_reject_planted_error(name, old, new, oracle_mod):
                         ignore=shutil.ignore_patterns("__pycache__", "*.so", "*.lock"))
         os.symlink(os.path.join(ROOT, "paper_2604_09993_gb300"), os.path.join(tmp, "paper_2604_09993_gb300"))
         open(os.path.join(tmp, "oracle", "socp.py"), "w").write(src.replace(old, new))
-        env = dict(os.environ, CISCVX_ORACLE_LIB=oracle_mod.build())
+        env = dict(os.environ, CISCVX_ORACLE_LIB=lib)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             *SOCP_PINS], cwd=tmp, env=env, capture_output=True, text=True, timeout=600)
-        assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
-        assert "passed" in r.stdout or "failed" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
+        return r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.fixture(scope="module")
+def socp_mutant_results(request, oracle_mod):
+    """The selected SOCP mutations, several at a time (as mutant_results)."""
+    selected = [it.callspec.params["name"] for it in request.session.items
+                if getattr(it, "originalname", None) == "test_socp_pins_reject_planted_error"]
+    table = {m[0]: m for m in SOCP_MUTATIONS}
+    lib = oracle_mod.build()
+    workers = max(1, min(len(selected), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {n: ex.submit(_run_socp_mutant, *table[n], lib) for n in selected}
+        return {n: f.result() for n, f in futs.items()}
+
+
+@pytest.mark.parametrize("name,old,new", SOCP_MUTATIONS, ids=[m[0] for m in SOCP_MUTATIONS])
+def test_socp_pins_reject_planted_error(name, old, new, socp_mutant_results):
+    rc, out = socp_mutant_results[name]
+    assert rc is not None, out
+    assert rc != 0, f"pins did not catch: {name}\n{out}"
+    assert "passed" in out or "failed" in out, out
