@@ -185,28 +185,6 @@ __device__ __forceinline__ double rk_w(int j) {
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
-// FP64 -> FP32 rounded toward zero, on the integer pipe (a conversion
-// instruction takes an FP64-pipe slot on this GPU).  From the two IEEE
-// formats: keep the sign, rebias the exponent (1023 -> 127), keep the top 23
-// of the 52 mantissa bits.  Magnitudes below the smallest normal FP32 number
-// give a signed zero, larger finite magnitudes than the largest FP32 number
-// give that number, infinities stay infinite and NaNs stay NaN.  Used for the
-// FP32 anchors of the tangent recursion, which tolerate one FP32 ulp.
-__device__ __forceinline__ float to_f32_rz(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;          // FP32 biased exponent
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 mantissa bits
-  unsigned r = sign | ((unsigned)e << 23) | m;
-  if (e <= 0) r = sign;
-  if (e >= 255) {
-    const bool special = (hi & 0x7ff00000u) == 0x7ff00000u;
-    const bool nan = special && (((hi & 0xfffffu) | lo) != 0u);
-    r = special ? (sign | (nan ? 0x7fc00000u : 0x7f800000u)) : (sign | 0x7f7fffffu);
-  }
-  return __uint_as_float(r);
-}
-
 // FP32 anchor of an FP64 state value (TP = float), or the value itself (TP = double).
 template <typename TP>
 __device__ __forceinline__ TP anchor(double x) {

@@ -11,7 +11,12 @@
 //    (sincos_step), and those at the substep start from the previous ones;
 //  * K = L D L^T is factored with one reciprocal per row (no square root);
 //  * the penalty values use the a rsqrt(a) - 1 form, and the slopes the
-//    tangents need are taken in the tangent precision.
+//    tangents need are taken in the tangent precision;
+//  * on the sinusoidal surface, sin/cos of tk x at each contact point come
+//    from those at the substep's first stage the same way, and the frame's
+//    normalization is one rsqrt;
+//  * FP32 stage data are narrowed on the integer pipe (to_f32_rz): a
+//    conversion instruction would take an FP64-pipe slot.
 // The stored stage slopes, K, the quadrature rows and the lever arms sit in
 // shared memory (element major); the live rows, stage values, generalized
 // forces and sin/cos stay in registers.  Under RKF45 only the slopes of the
@@ -39,7 +44,16 @@ struct NumN {
 
 using namespace ciscvx;
 
-__device__ __forceinline__ TP ramp_slope(double z) { return huber_slope(TP(z)); }
+// FP64 value -> stage-data precision (FP32: toward zero, on the integer pipe)
+__device__ __forceinline__ void narrow_to(float& d, double x) { d = to_f32_rz(x); }
+__device__ __forceinline__ void narrow_to(double& d, double x) { d = x; }
+__device__ __forceinline__ TP nar(double x) {
+  TP r;
+  narrow_to(r, x);
+  return r;
+}
+
+__device__ __forceinline__ TP ramp_slope(double z) { return huber_slope(nar(z)); }
 // pseudo-Huber absolute value sqrt(1 + x^2) - 1 (FP64) as a rsqrt(a) - 1
 __device__ __forceinline__ double sabs_v(double x) {
   const double a = fma(x, x, 1.0);
@@ -83,6 +97,8 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
 #pragma unroll
   for (int b = 0; b < NB; ++b) sincos(xl[LROW[3 * b + 2]], &sn0[b], &cs0[b]);
   TP* sdk = sd + (size_t)t * nsub * NSTG * SD_SIZE;
+  // sinusoidal surface: tk xc and its sin/cos at each contact, first stage of the substep
+  double targ0[NC > 0 ? NC : 1], tsn0[NC > 0 ? NC : 1], tcs0[NC > 0 ? NC : 1];
 
   for (int i = 0; i < nsub; ++i) {
     // quadrature rows: p += h s v at the substep start
@@ -138,7 +154,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
       auto u_at = [&](int q) { return (1.0 - tau) * uL[q] + tau * uR[q]; };
       // records F_r and integrates row r with the slope s F_r
       auto emit = [&](int r, double Fv) {
-        D[SD_F + r] = TP(Fv);
+        D[SD_F + r] = nar(Fv);
         const double kv = sk * Fv;
         const int l = LROW[r];
         if (l >= 0) {
@@ -183,8 +199,8 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
           const double rx = fma(cs[b], rho[0], -sn[b] * rho[1]), ry = fma(sn[b], rho[0], cs[b] * rho[1]);
           SE(E_ARM + 4 * jj + 2 * role) = rx;
           SE(E_ARM + 4 * jj + 2 * role + 1) = ry;
-          D[SD_ARM + 4 * jj + 2 * role] = TP(rx);
-          D[SD_ARM + 4 * jj + 2 * role + 1] = TP(ry);
+          D[SD_ARM + 4 * jj + 2 * role] = nar(rx);
+          D[SD_ARM + 4 * jj + 2 * role + 1] = nar(ry);
         }
       }
       // generalized forces and QW (the -dtheta coefficient of the torque's derivative)
@@ -221,7 +237,24 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
         const int b = CBODY[ic];
         const double rx = fma(cs[b], P.crho[ic][0], -sn[b] * P.crho[ic][1]);
         const double ry = fma(sn[b], P.crho[ic][0], cs[b] * P.crho[ic][1]);
-        const SurfFrame fr = contact_surface(TERRAIN ? P.ta : 0.0, P.tk, xs[LROW[3 * b]] + rx, xs[LROW[3 * b + 1]] + ry);
+        const double xc = xs[LROW[3 * b]] + rx, yc = xs[LROW[3 * b + 1]] + ry;
+        SurfFrame fr;
+        if (TERRAIN) {
+          // sin/cos of tk xc: evaluated at the substep's first stage, chained
+          // from there at the later stages (tk (xc - xc_0) stays small)
+          double ssn, scs;
+          if (j == 0) {
+            targ0[ic] = P.tk * xc;
+            sincos(targ0[ic], &tsn0[ic], &tcs0[ic]);
+            ssn = tsn0[ic];
+            scs = tcs0[ic];
+          } else {
+            sincos_step(targ0[ic], tsn0[ic], tcs0[ic], fma(P.tk, xc, -targ0[ic]), active, ssn, scs);
+          }
+          fr = contact_surface_sc(P.ta, P.tk, yc, ssn, scs);
+        } else {
+          fr = contact_surface(0.0, P.tk, xc, yc);
+        }
         const double u0 = u_at(CI0 + 3 * ic), u1 = u_at(CI0 + 3 * ic + 1), u2 = u_at(CI0 + 3 * ic + 2);
         const double ft = AUX ? u0 : u1 - u2, fn = AUX ? u1 : u0;
         const double fx = fma(fr.tx, ft, fr.nx * fn), fy = fma(fr.ty, ft, fr.ny * fn);
@@ -230,11 +263,11 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
         f[3 * b + 2] += fma(rx, fy, -ry * fx);
         qw[b] += fma(rx, fx, ry * fy);
         TP* Dc = D + SD_CON + NCF * ic;
-        Dc[0] = TP(rx); Dc[1] = TP(ry);
-        Dc[2] = TP(fr.tx); Dc[3] = TP(fr.ty); Dc[4] = TP(fr.nx); Dc[5] = TP(fr.ny);
-        Dc[6] = TP(fma(fr.dtx, ft, fr.dnx * fn));
-        Dc[7] = TP(fma(fr.dty, ft, fr.dny * fn));
-        Dc[8] = TP(fr.phix); Dc[9] = TP(fr.phiy);
+        Dc[0] = nar(rx); Dc[1] = nar(ry);
+        Dc[2] = nar(fr.tx); Dc[3] = nar(fr.ty); Dc[4] = nar(fr.nx); Dc[5] = nar(fr.ny);
+        Dc[6] = nar(fma(fr.dtx, ft, fr.dnx * fn));
+        Dc[7] = nar(fma(fr.dty, ft, fr.dny * fn));
+        Dc[8] = nar(fr.phix); Dc[9] = nar(fr.phiy);
         const double mu = P.mu[ic];
         if (!AUX) {
           const double zc = u1 + u2 - mu * u0;
@@ -243,7 +276,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
           const TP d1 = ramp_slope(-u0), d2 = ramp_slope(-u1), d3 = ramp_slope(-u2), dp = ramp_slope(-fr.phi),
                    d5 = ramp_slope(zc);
           Dc[10] = -dp;
-          Dc[11] = -d1 - TP(mu) * d5;
+          Dc[11] = -d1 - nar(mu) * d5;
           Dc[12] = -d2 + d5;
           Dc[13] = -d3 + d5;
           emit(6 * NB + ic, H);
@@ -256,18 +289,18 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
           const double rho_c = sabs_v(mu * fn) - fma(at, rt, -1.0);
           const double lam = fma(fr.tx, vcx, fr.ty * vcy) + gam * (ft * rt);
           const double H = huber_value(-fn) + huber_value(-fr.phi) + huber_value(-gam) + huber_value(-rho_c);
-          const TP ftP = TP(ft), mfn = TP(mu * fn);
+          const TP ftP = nar(ft), mfn = nar(mu * fn);
           const TP rtP = TP(1) / sqrt(TP(1) + ftP * ftP);
           const TP dft = ftP * rtP, dmn = mfn / sqrt(TP(1) + mfn * mfn);
           const TP drh = ramp_slope(-rho_c);
-          const TP rho_ft = -dft, rho_fn = TP(mu) * dmn;
+          const TP rho_ft = -dft, rho_fn = nar(mu) * dmn;
           Dc[10] = -ramp_slope(-fr.phi);
           Dc[11] = drh * dft;
           Dc[12] = -ramp_slope(-fn) - drh * rho_fn;
           Dc[13] = -ramp_slope(-gam);
-          Dc[14] = TP(vcx); Dc[15] = TP(vcy);
-          Dc[16] = TP(fma(fr.dtx, vcx, fr.dty * vcy));
-          Dc[17] = TP(gam) * rtP * rtP * rtP;
+          Dc[14] = nar(vcx); Dc[15] = nar(vcy);
+          Dc[16] = nar(fma(fr.dtx, vcx, fr.dty * vcy));
+          Dc[17] = nar(gam) * rtP * rtP * rtP;
           Dc[18] = dft;
           Dc[19] = rho_ft;
           Dc[20] = rho_fn;
@@ -330,7 +363,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
           KS(ii, ii) = 1.0 / dd;
         }
 #pragma unroll
-        for (int e = 0; e < NSKY; ++e) D[SD_K + e] = TP(SE(E_K + e));
+        for (int e = 0; e < NSKY; ++e) D[SD_K + e] = nar(SE(E_K + e));
         double lam[NK > 0 ? NK : 1];
 #pragma unroll
         for (int jj = 0; jj < NJ; ++jj) {
@@ -382,7 +415,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
         }
       }
 #pragma unroll
-      for (int b = 0; b < NB; ++b) D[SD_QW + b] = TP(qw[b]);
+      for (int b = 0; b < NB; ++b) D[SD_QW + b] = nar(qw[b]);
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         emit(3 * b + 2, xs[LROW[NQ + 3 * b + 2]]);
@@ -390,8 +423,8 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
           emit(3 * b, xs[LROW[NQ + 3 * b]]);
           emit(3 * b + 1, xs[LROW[NQ + 3 * b + 1]]);
         } else if (j == 0) {
-          D[SD_F + 3 * b] = TP(SE(E_XQ + QROW[NQ + 3 * b]));
-          D[SD_F + 3 * b + 1] = TP(SE(E_XQ + QROW[NQ + 3 * b + 1]));
+          D[SD_F + 3 * b] = nar(SE(E_XQ + QROW[NQ + 3 * b]));
+          D[SD_F + 3 * b + 1] = nar(SE(E_XQ + QROW[NQ + 3 * b + 1]));
         }
       }
 #pragma unroll

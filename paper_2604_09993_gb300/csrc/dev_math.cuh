@@ -5,6 +5,29 @@
 
 namespace ciscvx {
 
+// FP64 -> FP32 rounded toward zero, on the integer pipe (a conversion
+// instruction takes an FP64-pipe slot on this GPU).  From the two IEEE
+// formats: keep the sign, rebias the exponent (1023 -> 127), keep the top 23
+// of the 52 mantissa bits.  Magnitudes below the smallest normal FP32 number
+// give a signed zero, larger finite magnitudes than the largest FP32 number
+// give that number, infinities stay infinite and NaNs stay NaN.  Used for the
+// FP32 anchors of the tangent recursion and for the FP32 stage data of the
+// coupled path's nominal pass, which tolerate one FP32 ulp.
+__device__ __forceinline__ float to_f32_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;          // FP32 biased exponent
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 mantissa bits
+  unsigned r = sign | ((unsigned)e << 23) | m;
+  if (e <= 0) r = sign;
+  if (e >= 255) {
+    const bool special = (hi & 0x7ff00000u) == 0x7ff00000u;
+    const bool nan = special && (((hi & 0xfffffu) | lo) != 0u);
+    r = special ? (sign | (nan ? 0x7fc00000u : 0x7f800000u)) : (sign | 0x7f7fffffu);
+  }
+  return __uint_as_float(r);
+}
+
 // Pseudo-Huber ramp h(z) = sqrt(1 + p^2) - 1 = p^2 / (1 + sqrt(1 + p^2)),
 // p = max(z, 0), and its derivative h'(z) = p / sqrt(1 + p^2).
 __device__ __forceinline__ void huber(double z, double& H, double& D) {
@@ -125,21 +148,15 @@ struct SurfFrame {
   double phi, tx, ty, nx, ny, phix, phiy, dtx, dty, dnx, dny;
 };
 
-__device__ __forceinline__ SurfFrame contact_surface(double ta, double tk, double xc, double yc) {
+// The same frame from (sk, ck) = (sin, cos)(tk xc), for callers that chain
+// those across stages instead of evaluating them (ta != 0).
+__device__ __forceinline__ SurfFrame contact_surface_sc(double ta, double tk, double yc, double sk,
+                                                       double ck) {
   SurfFrame f;
-  if (ta == 0.0) {
-    f.phi = yc;
-    f.tx = 1.0; f.ty = 0.0; f.nx = 0.0; f.ny = 1.0;
-    f.phix = 0.0; f.phiy = 1.0;
-    f.dtx = f.dty = f.dnx = f.dny = 0.0;
-    return f;
-  }
-  double sk, ck;
-  sincos(tk * xc, &sk, &ck);
   const double hc = fma(-ta, sk, yc);
   const double gx = -(ta * tk) * ck;       // dh^c/dx
   const double gp = (ta * tk * tk) * sk;   // d gx / dx
-  const double w = 1.0 / sqrt(fma(gx, gx, 1.0));
+  const double w = rsqrt(fma(gx, gx, 1.0));
   const double w3g = gp * w * w * w;
   f.phi = hc * w;
   f.nx = gx * w; f.ny = w;
@@ -149,6 +166,20 @@ __device__ __forceinline__ SurfFrame contact_surface(double ta, double tk, doubl
   f.dnx = w3g; f.dny = -gx * w3g;             // dn/dx = gp w^3 (1, -gx)
   f.dtx = -gx * w3g; f.dty = -w3g;            // dt/dx = gp w^3 (-gx, -1)
   return f;
+}
+
+__device__ __forceinline__ SurfFrame contact_surface(double ta, double tk, double xc, double yc) {
+  if (ta == 0.0) {
+    SurfFrame f;
+    f.phi = yc;
+    f.tx = 1.0; f.ty = 0.0; f.nx = 0.0; f.ny = 1.0;
+    f.phix = 0.0; f.phiy = 1.0;
+    f.dtx = f.dty = f.dnx = f.dny = 0.0;
+    return f;
+  }
+  double sk, ck;
+  sincos(tk * xc, &sk, &ck);
+  return contact_surface_sc(ta, tk, yc, sk, ck);
 }
 
 // Where interval e's data live (the library's batch instance table has this

@@ -241,10 +241,12 @@ const CplJit* compile(const std::string& src0, const char* name, int bs, size_t 
   char arch[64];
   std::snprintf(arch, sizeof arch, "--gpu-architecture=sm_%d%d%s", major, minor,
                 (major == 10 && minor == 3) ? "a" : "");
-  const char* opts[] = {arch, "-std=c++17", "-lineinfo"};
+  // CISCVX_JIT_LOG also asks ptxas for the kernel's registers and spills
+  const char* opts[] = {arch, "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
+  const int nopt = std::getenv("CISCVX_JIT_LOG") ? 4 : 3;
   nvrtcProgram_t prog = nullptr;
   if (g_nvrtc.create(&prog, src.c_str(), "cpl_tangent_jit.cu", 0, nullptr, nullptr) != 0) return nullptr;
-  const int rc = g_nvrtc.compile(prog, 3, opts);
+  const int rc = g_nvrtc.compile(prog, nopt, opts);
   if (rc != 0 || std::getenv("CISCVX_JIT_LOG")) {
     size_t n = 0;
     g_nvrtc.log_size(prog, &n);
