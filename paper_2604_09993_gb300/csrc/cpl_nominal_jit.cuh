@@ -9,7 +9,8 @@
 //  * the stage sin/cos of every link angle come from those at the substep
 //    start by angle addition with a Taylor series of the increment
 //    (sincos_step), and those at the substep start from the previous ones;
-//  * K = L D L^T is factored with one reciprocal per row (no square root);
+//  * K = L D L^T is factored with one reciprocal per row (no square root),
+//    an FP32 estimate refined by Newton-Raphson steps in FP64;
 //  * the penalty values use the a rsqrt(a) - 1 form, and the slopes the
 //    tangents need are taken in the tangent precision;
 //  * on the sinusoidal surface, sin/cos of tk x at each contact point come
@@ -54,6 +55,27 @@ __device__ __forceinline__ TP nar(double x) {
 }
 
 __device__ __forceinline__ TP ramp_slope(double z) { return huber_slope(nar(z)); }
+
+// 1 / d for a pivot of K's L D L^T factor: an FP32 estimate (rcp.approx,
+// error about one FP32 ulp, with d narrowed and the estimate widened on the
+// integer pipe) refined by two Newton-Raphson steps r <- r + r (1 - d r) in
+// FP64.  Each step squares the relative error (2^-22 -> 2^-44 -> below FP64
+// rounding), so the result is within a few FP64 ulp of 1 / d; four FP64
+// instructions on the critical path of the factorization instead of a
+// correctly rounded division.  Pivots of magnitude outside 2^-100 .. 2^100
+// (and zeros and non-finite values, whose results are non-finite either way)
+// take the division.
+__device__ __forceinline__ double pivot_inv(double d) {
+  const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7FFu;  // biased exponent
+  if (ex < 1023u - 100u || ex > 1023u + 100u) return 1.0 / d;
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(to_f32_rz(d)));
+  double r = widen(rf);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
 // pseudo-Huber absolute value sqrt(1 + x^2) - 1 (FP64) as a rsqrt(a) - 1
 __device__ __forceinline__ double sabs_v(double x) {
   const double a = fma(x, x, 1.0);
@@ -360,7 +382,7 @@ extern "C" __global__ void __launch_bounds__(BLK) cpl_nominal(const __grid_const
             dd = fma(-tk, l, dd);
             KS(ii, kk) = l;
           }
-          KS(ii, ii) = 1.0 / dd;
+          KS(ii, ii) = pivot_inv(dd);
         }
 #pragma unroll
         for (int e = 0; e < NSKY; ++e) D[SD_K + e] = nar(SE(E_K + e));
