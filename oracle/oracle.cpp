@@ -69,7 +69,7 @@ namespace {
 // ---------------------------------------------------------------------------
 // Forward-mode dual numbers with a run-time number of tangent directions.
 // ---------------------------------------------------------------------------
-constexpr int MAXC = 192;   // max tangent directions (n_x~ + 2 n_u + 1)
+constexpr int MAXC = 400;   // max tangent directions (n_x~ + 2 n_u + 1; 393 for a 32-link chain)
 thread_local int g_nd = 0;  // active directions for this thread
 
 struct Dual {

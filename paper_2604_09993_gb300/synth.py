@@ -151,6 +151,14 @@ def cheetah7(rng):
     return _chain_robot("cheetah7", m, L, torso_horizontal=True, leg_lengths=[3, 3])
 
 
+def chain32(rng):
+    """The largest model the library takes: a torso plus legs of 15 and 16 links
+    (32 links, n_x~ = 194, n_u = 99; every link has six inputs)."""
+    m = rng.uniform(0.5, 6.0, 32)
+    L = rng.uniform(0.1, 0.6, 32)
+    return _chain_robot("chain32", m, L, torso_horizontal=True, leg_lengths=[15, 16])
+
+
 ROBOTS = {"hopper": hopper, "biped": biped, "cheetah7": cheetah7}
 
 
