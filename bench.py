@@ -43,6 +43,8 @@ from paper_2604_09993_gb300 import synth  # noqa: E402
 METRIC = "linearized intervals/s (STM + adjoint VJP) vs plain FP64 GPU path at stated error"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 126 * 2 ** 20
+# impulse-relaxation parameter of the node constraints in the paper-scale leg
+NODE_DELTA_PAPER = 1e-3
 
 
 def _measured_hbm_gbs():
@@ -720,6 +722,82 @@ def run_ours(args):
                 "psi": psi}))
         return
 
+    def measure_paper_scale():
+        """One SCP iteration's transcription at the sizes of the paper's monoped
+        scenario (15 nodes, 10 steps per interval; joint reaction forces
+        eliminated, RKF45, the full Eq. (12) state): the linearization
+        (ciscvx_discretize, coupled path), the node constraints at the 15
+        nodes, Psi^{delta,eps} between them and the canonicalization into
+        the SOCP (ciscvx_socp_fill), each timed alone and all four as one
+        step, per precision; L2 flushed before every timed call."""
+        global L2_FLUSH
+        if L2_FLUSH is None:
+            L2_FLUSH = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+        pp = synth.monoped_paper(seed=rank)
+        m = api.Model(pp.robot)
+        N = pp.N
+        t_ = lambda a: torch.tensor(a, device=dev)  # noqa: E731
+        X, U, s = t_(pp.X), t_(pp.U), t_(pp.s)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(77)
+        Xm = (X + 0.05 * torch.randn(X.shape, generator=gen, device=dev, dtype=torch.float64)).contiguous()
+        Phi = torch.randn((N + 1, 2 * m.nc), generator=gen, device=dev, dtype=torch.float64)
+        Gam = torch.rand((N + 1, m.nc), generator=gen, device=dev, dtype=torch.float64)
+        rest = np.full(m.nc, 0.3)
+        socp = api.Socp(m, N, "node", w_px=2000.0, w_ep=50000.0, w_torque=1.0, s_min=0.005, s_max=0.1,
+                        torque_max=np.full(m.nj, 50.0), x_init=np.zeros(6 * m.nb), x_final=np.zeros(6 * m.nb),
+                        phi_format="dense")
+        res = {"metric": "SCP-iteration transcription latency: linearization + node constraints + Psi + SOCP "
+                         "canonicalization, one instance",
+               "unit": "ms", "higher_is_better": False,
+               "workload": f"2-link monoped, eliminated joint forces, RKF45, flat ground, Eq. (12) state, "
+                           f"{N + 1} nodes x {pp.n_sub} substeps",
+               "dims": dict(socp.dims), "paper": "about 50 ms per SCP iteration for the whole iteration "
+                                                  "(transcription, canonicalization and the QOCO solve; "
+                                                  "hardware not stated)"}
+        for pr in ("fp64", "fp32_phi"):
+            lo, hi = api.discretize_workspace_size(m, N, pp.n_sub, pr)
+            ws = torch.empty(max(lo, hi), dtype=torch.uint8, device=dev)
+            out = api.discretize(m, X, U, s, pp.n_sub, pr, workspace=ws)
+            nd = api.node_linearize(m, X, Xm, Phi, Gam, NODE_DELTA_PAPER, rest)
+            ps = api.psi_linearize(m, X, Xm, NODE_DELTA_PAPER, 1e-4)
+            inp = {"Xp": X, "Xm": Xm, "U": U, "s": s, "Phi": Phi, "Gam": Gam, "A": out["A"], "Bm": out["Bm"],
+                   "Bp": out["Bp"], "S": out["S"], "defect": out["defect"], "g": nd["g"], "Gvm": nd["Gvm"],
+                   "Gth": nd["Gth"], "Gphi": nd["Gphi"], "Gpx": nd["Gpx"], "theta": nd["theta"],
+                   "dtheta": nd["dtheta"], "psi": ps["psi"], "dpsi": ps["dpsi"]}
+            so = socp.fill(1, inp, precision=pr)
+            parts = {
+                "linearization": lambda: api.discretize(m, X, U, s, pp.n_sub, pr, out=out, workspace=ws),
+                "node_constraints": lambda: api.node_linearize(m, X, Xm, Phi, Gam, NODE_DELTA_PAPER, rest,
+                                                               out=nd),
+                "psi": lambda: api.psi_linearize(m, X, Xm, NODE_DELTA_PAPER, 1e-4, out=ps),
+                "socp_fill": lambda: socp.fill(1, inp, out=so, precision=pr),
+            }
+
+            def whole():
+                for f in parts.values():
+                    f()
+
+            r = {k: time_steps(torch, f, args.steps, args.warmup, stream, name=f"paper scale: {k}") /
+                 args.steps * 1e3 for k, f in parts.items()}
+            r["iteration"] = time_steps(torch, whole, args.steps, args.warmup, stream,
+                                        name="paper scale: iteration") / args.steps * 1e3
+            api.sync_status(m)
+            res[pr] = r
+        return res
+
+    if args.paper_scale:
+        ps_res = measure_paper_scale()
+        if rank == 0:
+            f64 = ps_res["fp64"]["iteration"]
+            print(json.dumps({
+                "metric": ps_res["metric"], "value": f64, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": f64, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded robot)",
+                "config": {"workload": ps_res["workload"], "l2": "L2 flushed before every timed call"},
+                "paper_scale": ps_res}))
+        return
+
     if args.paper_only:
         paper = measure_paper()
         if rank == 0:
@@ -1047,6 +1125,8 @@ def main():
     ap.add_argument("--paper-intervals", type=int, default=65536,
                     help="intervals of the paper-dynamics instance")
     ap.add_argument("--paper-precision", default="both", choices=["both", "fp32_phi", "fp64"])
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="run only the per-SCP-iteration latency at the paper's monoped scale (own JSON line)")
     ap.add_argument("--psi-only", action="store_true",
                     help="run only the Psi^{delta,eps} measurement (its own JSON line)")
     ap.add_argument("--psi-intervals", type=int, default=1 << 20, help="intervals of the Psi-only measurement")

@@ -151,6 +151,14 @@ def cheetah7(rng):
     return _chain_robot("cheetah7", m, L, torso_horizontal=True, leg_lengths=[3, 3])
 
 
+def monoped(rng):
+    """Planar 2-link monoped: a body and one leg link carrying the foot contact
+    (n_x~ = 13, n_u = 9 with joint reaction forces as inputs)."""
+    m = rng.uniform(1.0, 5.0, 2)
+    L = rng.uniform(0.2, 0.5, 2)
+    return _chain_robot("monoped", m, L, torso_horizontal=False, leg_lengths=[1])
+
+
 def chain32(rng):
     """The largest model the library takes: a torso plus legs of 15 and 16 links
     (32 links, n_x~ = 194, n_u = 99; every link has six inputs)."""
@@ -376,6 +384,19 @@ def cheetah_sweep(seed=0, n_inst=4096, N=400, n_sub=20):
     return Batch(robots, np.zeros(n_inst, dtype=np.int32), np.full(n_inst, N, dtype=np.int32),
                  np.full(n_inst, n_sub, dtype=np.int32), seed, (0.01, 0.05),
                  [_ROBOT_STYLE["cheetah7"]])
+
+
+def monoped_paper(seed=0, N=14, n_sub=10):
+    """The sizes of the paper's monoped scenario (15 nodes, so N = 14
+    intervals, 10 integration steps per interval, flat ground) with the
+    paper's modelling choices: joint reaction forces eliminated (Eq. (3)),
+    RKF45 substeps and the full Eq. (12) auxiliary state; synthetic link
+    dimensions, pose +- 0.05 about the standing pose, u ~ U[-1, 1],
+    s ~ U[0.05, 0.15]."""
+    rng = np.random.default_rng(seed)
+    robot = with_cross_states(with_paper_dynamics(monoped(rng)))
+    return draw_instance(robot, rng, N, n_sub, s_range=(0.05, 0.15), with_cotangents=True,
+                         q_noise=0.05, u_dist="uniform")
 
 
 def cheetah_paper_sweep(seed=0, N=65536, n_sub=10):
