@@ -78,7 +78,7 @@ typedef enum {
   CISCVX_ECUDA = 3,        /* a CUDA runtime call failed */
   CISCVX_ENONFINITE = 4,   /* the device produced a non-finite state or block */
   CISCVX_ETIMEOUT = 5,     /* reserved: a bounded device wait gave up */
-  CISCVX_EUNSUPPORTED = 6  /* valid request outside this build's limits */
+  CISCVX_EUNSUPPORTED = 6  /* valid request outside the library's limits */
 } ciscvx_status;
 
 typedef enum {
@@ -104,7 +104,7 @@ typedef enum {
                              order of ciscvx_model_pattern; S, defect, penalty, z as for dense */
 } ciscvx_out_format;
 
-/* Limits of this build (ciscvx_model_create / ciscvx_discretize_vjp return
+/* Limits of the library (ciscvx_model_create / ciscvx_discretize_vjp return
  * CISCVX_EUNSUPPORTED beyond them). */
 #define CISCVX_MAX_BODIES 32          /* links per model */
 #define CISCVX_MAX_INPUTS_PER_BODY 15 /* inputs acting on one link (<= 4 joints + 1 contact) */

@@ -342,7 +342,7 @@ ciscvx_status check_common(const ciscvx_model* m, int N, int n_sub, int precisio
   if (n_sub < 1) return fail(CISCVX_EINVAL, "n_sub must be >= 1 (got %d)", n_sub);
   if (!layout_ok(layout)) return fail(CISCVX_EINVAL, "unknown control layout %d", layout);
   if (precision == CISCVX_TF32_TC || precision == CISCVX_BF16_TC)
-    return fail(CISCVX_EUNSUPPORTED, "tensor-core precisions are not provided by this build");
+    return fail(CISCVX_EUNSUPPORTED, "tensor-core precisions are not provided by this library");
   if (precision != CISCVX_FP64 && precision != CISCVX_FP32_PHI)
     return fail(CISCVX_EINVAL, "unknown precision %d", precision);
   if (!X || !s || (m->host.nu > 0 && !U)) return fail(CISCVX_EINVAL, "null input array");

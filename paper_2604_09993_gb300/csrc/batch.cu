@@ -589,7 +589,7 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (layout != CISCVX_FOH_NODE && layout != CISCVX_FOH_INTERVAL)
     return set_error(CISCVX_EINVAL, "unknown control layout %d", (int)layout);
   if (precision == CISCVX_TF32_TC || precision == CISCVX_BF16_TC)
-    return set_error(CISCVX_EUNSUPPORTED, "tensor-core precisions are not provided by this build");
+    return set_error(CISCVX_EUNSUPPORTED, "tensor-core precisions are not provided by this library");
   if (precision != CISCVX_FP64 && precision != CISCVX_FP32_PHI)
     return set_error(CISCVX_EINVAL, "unknown precision %d", (int)precision);
   if (format != CISCVX_OUT_DENSE && format != CISCVX_OUT_COMPACT)
