@@ -91,9 +91,8 @@ FP64_STATE_FLOPS = {("cheetah7", 20, "fused", "fp32_phi"): 30_693}
 # kernel's work; a capped variant executes a few per cent more (spills and
 # recomputation).
 WARP_INSTR_PER_INTERVAL = {
-    ("cheetah7", 20, "fused", "fp32_phi", 0): 1_272_148_413 / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi", 1): 1_326_959_116 / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi", 2): 1_354_123_638 / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 0): 1_275_781_797 / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 1): 1_327_925_910 / 102400,
 }
 # Issue peak: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz.
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -104,9 +103,8 @@ ISSUE_PEAK = 152 * 4 * 2.07e9
 DRAM_BYTES_PER_INTERVAL = {
     ("cheetah7", 20, "discretize", "fp64", 0): (407.3e6 + 3762.1e6) / 102400,
     ("cheetah7", 20, "vjp", "fp64", 0): (258.3e6 + 227.4e6) / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi", 0): (785.2e6 + 2709.5e6) / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi", 1): (1021.1e6 + 2855.4e6) / 102400,
-    ("cheetah7", 20, "fused", "fp32_phi", 2): (1101.8e6 + 2875.5e6) / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 0): (789.4e6 + 2715.6e6) / 102400,
+    ("cheetah7", 20, "fused", "fp32_phi", 1): (1125.6e6 + 2972.9e6) / 102400,
 }
 
 
