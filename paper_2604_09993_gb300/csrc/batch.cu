@@ -126,6 +126,7 @@ struct ChunkTables {
   int2* d_items_nat = nullptr;
   int2* d_items_sm = nullptr;
   std::vector<int> item_off;        // [K+1] items of chunk c: [item_off[c], item_off[c+1])
+  std::vector<int> entry_off;       // [K+1] per-link entries (intervals) of chunk c
   std::vector<int> foot_cnt;        // [K] foot-link items at the head of chunk c's items_sm
   int split_sm = 0;                 // SMs that take the foot-link queue first (lpt_order 2)
   std::vector<int> inst_off;        // [K+1] instances of chunk c
@@ -167,6 +168,16 @@ struct ciscvx_batch_plan {
   int* d_queue = nullptr;  // [0..1]: discretize, [2..3]: vjp (two counters each: lpt_order 2 uses both)
   int2* d_items_sm = nullptr;  // lpt_order 2: foot-link items, then the others (bucket order)
   int n_foot_items = 0, split_sm = 0;
+  int n_entries = 0;  // per-link intervals (entries) of the batch
+  // dense outputs of the fused pass staged as compact values and widened by
+  // k_expand_dense (expand.cu): per model, the compact index of every dense
+  // entry of A and of B-/B+ (-1: structural zero); stage_vals = the largest
+  // nnz_A + 2 nnz_B over the per-link models
+  int* d_maps = nullptr;
+  const int** d_map_a = nullptr;
+  const int** d_map_b = nullptr;
+  int stage_vals = 0;
+  bool stage_ok = false;
   unsigned* d_status = nullptr;
   ciscvx_tune tune{4, 2, 1, 1, 0};
   ciscvx_tune tune_fused{4, 2, 1, 0, 0, 0};  // launch shape of the fused discretize+VJP pass
@@ -216,6 +227,9 @@ void free_plan(ciscvx_batch_plan* p) {
   cudaFree(p->d_items_lpt);
   cudaFree(p->d_items_nat);
   cudaFree(p->d_items_sm);
+  cudaFree(p->d_maps);
+  cudaFree(p->d_map_a);
+  cudaFree(p->d_map_b);
   cudaFree(p->d_queue);
   cudaFree(p->d_status);
   cudaFree(p->d_cpl_entries);
@@ -242,7 +256,7 @@ cudaError_t upload(T** dst, const std::vector<T>& v) {
 struct HostDecomp {
   std::vector<int2> entries, items_lpt, items_nat, items_sm;
   std::vector<int4> groups;
-  std::vector<int> item_off, foot_cnt;
+  std::vector<int> item_off, foot_cnt, entry_off;
   double foot_cost = 0.0, all_cost = 0.0;
   std::string key;
 };
@@ -253,6 +267,7 @@ HostDecomp decompose(const ciscvx_batch_plan* p, const std::vector<int>& inst_of
   HostDecomp d;
   const int K = (int)inst_off.size() - 1;
   d.item_off.push_back(0);
+  d.entry_off.push_back(0);
   for (int c = 0; c < K; ++c) {
     std::map<std::pair<int, int>, std::vector<int>> buckets;
     for (int i = inst_off[c]; i < inst_off[c + 1]; ++i)
@@ -296,6 +311,7 @@ HostDecomp decompose(const ciscvx_batch_plan* p, const std::vector<int>& inst_of
                      });
     for (auto& x : costed) d.items_lpt.push_back(x.second);
     d.item_off.push_back((int)d.items_lpt.size());
+    d.entry_off.push_back((int)d.entries.size());
   }
   return d;
 }
@@ -325,6 +341,9 @@ BatchCommon common_of(const ciscvx_batch_plan* p, int queue_slot, const ciscvx_t
   c.status = p->d_status;
   c.layout = p->layout;
   c.ck_smem = 0;
+  c.stage_dense = 0;
+  c.e0 = 0;
+  c.e1 = p->n_entries;
   return c;
 }
 
@@ -338,6 +357,8 @@ BatchCommon common_chunk(const ciscvx_batch_plan* p, int queue_slot, int c, cons
   b.n_items = t.item_off[c + 1] - t.item_off[c];
   b.n_first = t.foot_cnt[c];
   b.split_sm = t.split_sm;
+  b.e0 = t.entry_off[c];
+  b.e1 = t.entry_off[c + 1];
   return b;
 }
 
@@ -520,9 +541,16 @@ cudaError_t launch_fused_c(ciscvx_batch_plan* p, const BatchCommon& c, const cis
     cf.ck_smem = 1;
     smem = ck_bytes;
   }
-  e = launch_disc_vjp_fused(cf, p->prec, p->tune_fused.occupancy, p->compact, p->any_aux, blocks, threads, io->X,
-                            io->U, io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty,
+  // dense outputs: the kernel stages each interval's compact values at the
+  // start of its dense blocks (one store per structural nonzero) and
+  // k_expand_dense widens them with coalesced stores (expand.cu)
+  const bool stage = !p->compact && p->stage_ok;
+  cf.stage_dense = stage ? 1 : 0;
+  e = launch_disc_vjp_fused(cf, p->prec, p->tune_fused.occupancy, p->compact || stage, p->any_aux, blocks, threads,
+                            io->X, io->U, io->s, io->A, io->Bm, io->Bp, io->S, io->defect, io->penalty,
                             vio->w, vio->rho, vio->gX, part, ps, pL, smem, s);
+  if (e == cudaSuccess && stage)
+    e = launch_expand_dense(cf, p->prec, p->d_map_a, p->d_map_b, p->stage_vals, io->A, io->Bm, io->Bp, s);
   if (e == cudaSuccess && i1 > i0)
     k_batch_vjp_finish<<<i1 - i0, FINB, 0, s>>>(p->d_models, p->d_inst + i0, p->layout, part, ps,
                                                 pL, vio->gU, vio->gs, vio->L ? vio->L + i0 : nullptr);
@@ -669,6 +697,7 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   p->split_sm = split_sms(p, dec);
   p->items_lpt = dec.items_lpt;
   p->items_nat = dec.items_nat;
+  p->n_entries = (int)dec.entries.size();
   const std::vector<int2>& entries = dec.entries;
   const std::vector<int4>& groups = dec.groups;
 
@@ -708,6 +737,40 @@ ciscvx_status ciscvx_batch_plan_create(const ciscvx_model* const* models, int n_
   if (e == cudaSuccess) e = upload(&p->d_items_lpt, p->items_lpt);
   if (e == cudaSuccess) e = upload(&p->d_items_nat, p->items_nat);
   if (e == cudaSuccess) e = upload(&p->d_items_sm, dec.items_sm);
+  if (e == cudaSuccess && !p->compact && p->n_entries > 0 && precision == CISCVX_FP32_PHI) {
+    // dense FP32 outputs: the per-model maps that widen staged compact values
+    // (the FP64 path keeps the in-kernel zeroing: its doubled expand traffic
+    // measured slower, 352 against 342 ms on the 4096 x 400 x 20 sweep)
+    std::vector<int> maps;
+    std::vector<size_t> oa(n_models, 0), ob(n_models, 0);
+    int vals = 0;
+    for (int m = 0; m < n_models; ++m) {
+      const DevModel& M = models[m]->host;
+      if (models[m]->cpl) continue;
+      std::vector<int32_t> ar(M.nnzA), ac(M.nnzA), br(M.nnzB), bc(M.nnzB);
+      model_pattern(M, ar.data(), ac.data(), br.data(), bc.data());
+      maps.resize((maps.size() + 3) / 4 * 4, -1);  // 16-byte aligned map starts
+      oa[m] = maps.size();
+      maps.resize(maps.size() + (size_t)M.nxt * M.nxt, -1);
+      for (int j = 0; j < M.nnzA; ++j) maps[oa[m] + (size_t)ar[j] * M.nxt + ac[j]] = j;
+      maps.resize((maps.size() + 3) / 4 * 4, -1);
+      ob[m] = maps.size();
+      maps.resize(maps.size() + (size_t)M.nxt * M.nu, -1);
+      for (int j = 0; j < M.nnzB; ++j) maps[ob[m] + (size_t)br[j] * M.nu + bc[j]] = j;
+      vals = std::max(vals, M.nnzA + 2 * M.nnzB);
+    }
+    const size_t el = precision == CISCVX_FP64 ? sizeof(double) : sizeof(float);
+    if (vals > 0 && 4u * (size_t)vals * el <= 200u * 1024u) {
+      e = upload(&p->d_maps, maps);
+      std::vector<const int*> pa(n_models, nullptr), pb(n_models, nullptr);
+      for (int m = 0; m < n_models && e == cudaSuccess; ++m)
+        if (!models[m]->cpl) { pa[m] = p->d_maps + oa[m]; pb[m] = p->d_maps + ob[m]; }
+      if (e == cudaSuccess) e = upload(&p->d_map_a, pa);
+      if (e == cudaSuccess) e = upload(&p->d_map_b, pb);
+      p->stage_vals = vals;
+      p->stage_ok = e == cudaSuccess;
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->d_queue, 4 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned));
@@ -1014,6 +1077,7 @@ cudaError_t ensure_chunks(ciscvx_batch_plan* p, int K) {
   if (e == cudaSuccess) e = upload(&t.d_items_nat, d.items_nat);
   if (e == cudaSuccess) e = upload(&t.d_items_sm, d.items_sm);
   t.foot_cnt = d.foot_cnt;
+  t.entry_off = d.entry_off;
   t.split_sm = split_sms(p, d);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t.s_comp, cudaStreamNonBlocking);

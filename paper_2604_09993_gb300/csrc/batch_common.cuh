@@ -28,6 +28,12 @@ struct BatchCommon {
   unsigned* status;
   int layout;
   int ck_smem;  // fused pass: FP32 checkpoints in dynamic shared memory (4 n_sub floats per thread)
+  // fused pass with dense outputs: the kernel writes each interval's compact
+  // values (structural nonzeros, compact order) at the start of that
+  // interval's dense A / B- / B+ blocks, and k_expand_dense then widens them
+  // in place; entries [e0, e1) are the per-link intervals this launch covers
+  int stage_dense;
+  int e0, e1;
 };
 
 __device__ __forceinline__ int next_item(const BatchCommon& c, int& local_iter) {
@@ -158,6 +164,17 @@ cudaError_t launch_disc_vjp_fused(const BatchCommon& c, int prec, int occ, bool 
                                   void* S, double* defect, double* penalty, const double* w,
                                   const double* rho, double* gX, double* part, double* ps,
                                   double* pL, size_t smem, cudaStream_t st);
+
+// Widens the compact values that the fused pass staged at the start of each
+// interval's dense blocks (BatchCommon.stage_dense) into the dense A, B-, B+
+// of entries [c.e0, c.e1): one warp per interval reads its compact values
+// into shared memory, then writes the whole dense blocks, structural zeros
+// included.  map_a / map_b hold, per model, the compact index of every dense
+// entry of A (n_x~ x n_x~) and of B-/B+ (n_x~ x n_u), -1 for a structural
+// zero; smem_vals is the largest nnz_A + 2 nnz_B of the plan's models.
+cudaError_t launch_expand_dense(const BatchCommon& c, int prec, const int* const* map_a,
+                                const int* const* map_b, int smem_vals, void* A, void* Bm, void* Bp,
+                                cudaStream_t st);
 
 // The same outputs with the linearization and the VJP of every item on
 // separate warps of one launch (items [0, n) linearize, [n, 2n) take the

@@ -38,8 +38,9 @@ __global__ void __launch_bounds__(Occ<OCC>::T, Occ<OCC>::B)
       const double* Xi = X + I.x;
       const double* uL = (c.layout == CISCVX_FOH_NODE) ? U + I.u + k * nu : U + I.u + 2 * k * nu;
       const double* uR = uL + nu;
-      const size_t sa = CMP ? (size_t)M.nnzA : (size_t)nxt * nxt;
-      const size_t sb = CMP ? (size_t)M.nnzB : (size_t)nxt * nu;
+      // compact values staged in dense blocks (c.stage_dense) take the dense strides
+      const size_t sa = (CMP && !c.stage_dense) ? (size_t)M.nnzA : (size_t)nxt * nxt;
+      const size_t sb = (CMP && !c.stage_dense) ? (size_t)M.nnzB : (size_t)nxt * nu;
       TP* Ak = A + I.a + k * sa;
       TP* Bmk = Bm ? Bm + I.b + k * sb : nullptr;
       TP* Bpk = Bp ? Bp + I.b + k * sb : nullptr;
